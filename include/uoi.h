@@ -1,0 +1,169 @@
+/*
+ * uoi.h -- C ABI of the GB300 (sm_103a) UoI_LASSO / UoI_VAR(1) hot path.
+ *
+ * Method: Balasubramanian et al., "Optimizing the Union of Intersections LASSO
+ * (UoI_LASSO) and Vector Autoregressive (UoI_VAR) Algorithms for Improved
+ * Statistical Estimation at Scale", arXiv 1808.06992:
+ *   Alg. 1          UoI_LASSO: B1 bootstraps x q lambdas of LASSO (selection),
+ *                   support intersection (Eq. 3), B2 bootstraps of OLS on each
+ *                   support with held-out loss argmin, averaging (Eq. 4).
+ *   Alg. 2, Eq. 6-9 UoI_VAR: the same on the lagged design of a VAR(d) series,
+ *                   vectorised into p LASSOs that share one design.
+ *   Eq. 5           the LASSO is solved by ADMM (x-update, soft-threshold,
+ *                   dual update).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are row-major, float64.  "n x p" means n rows of p values.
+ *  - Every pointer argument may point to host memory or to device memory of
+ *    the current CUDA device; the kind is detected per pointer.  Host inputs
+ *    are copied to the device and outputs copied back before return.
+ *  - The caller owns every buffer it passes.  The library owns its scratch,
+ *    taken from a stream-ordered pool of the current device; uoi_shutdown()
+ *    returns it.
+ *  - Work is issued on prm->stream / the stream argument (NULL = the legacy
+ *    default stream); every entry point returns after the results are in the
+ *    output buffers (it synchronises that stream).
+ *  - Outputs are written only when the status is UOI_OK or
+ *    UOI_OK_WITH_WARNINGS.  No C++ exception crosses the boundary.
+ *  - Not thread-safe per device: calls on one device must not overlap.
+ */
+#ifndef UOI_H
+#define UOI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define UOI_OK                 0
+#define UOI_OK_WITH_WARNINGS   1   /* non-converged ADMM columns or singular OLS supports */
+#define UOI_ERR_INVALID_ARG   -1   /* null pointer, non-positive size, bad parameter       */
+#define UOI_ERR_NONFINITE     -2   /* NaN/Inf in X or y (checked on the device)            */
+#define UOI_ERR_NOT_PD        -3   /* Cholesky pivot <= 0 (only possible with rho <= 0)    */
+#define UOI_ERR_CUDA          -4   /* a CUDA runtime call failed                           */
+#define UOI_ERR_OOM           -5   /* device allocation failed                             */
+#define UOI_ERR_TIMEOUT       -6   /* a bounded device loop ran out of iterations          */
+#define UOI_ERR_UNSUPPORTED   -8   /* e.g. VAR order != 1, learned warm start unavailable  */
+
+/* ---- parameter enums ------------------------------------------------------ */
+#define UOI_BAG_MEDIAN   0   /* coordinate-wise median over the B2 chosen estimates  */
+#define UOI_BAG_MEAN     1   /* the paper's average (Alg. 1 last step, Eq. 4)        */
+#define UOI_SPLIT_PER_BOOTSTRAP 0  /* a fresh train/eval reshuffle per bootstrap     */
+#define UOI_SPLIT_FIXED         1  /* bootstrap 0's reshuffle for every bootstrap    */
+#define UOI_PREC_FP64    0   /* plain FP64 form: every step in FP64                  */
+#define UOI_PREC_MIXED   1   /* tensor-core Gram (split bf16, FP32 accumulate, FP64
+                                chunk sums), FP64 Cholesky and OLS, FP32 ADMM         */
+#define UOI_WARM_NONE    0   /* every (bootstrap, lambda) column starts at z = u = 0 */
+#define UOI_WARM_PATH    1   /* lambda descending; column j starts from j-1's (z,u)  */
+#define UOI_WARM_LEARNED 2   /* learned initial (z,u) (MLP); judged by PATH          */
+
+/* Parameters of a fit (Alg. 1 / Alg. 2 inputs lambda, B1, B2 plus the ADMM
+ * and bootstrap settings).  Zero-initialise, set struct_size = sizeof(uoi_params)
+ * and the fields you need; uoi_params_default() fills the documented defaults. */
+typedef struct uoi_params {
+    uint32_t struct_size;
+    int32_t  B1;                /* selection bootstraps (> 0)                          */
+    int32_t  B2;                /* estimation bootstraps (> 0)                         */
+    int32_t  q;                 /* number of lambdas (> 0)                             */
+    const double* lambdas;      /* q values (host or device), NULL = log grid          */
+    double   lambda_min_ratio;  /* grid: lambda_j = lmax * ratio^(j/(q-1)); 1e-3       */
+    double   rho;               /* ADMM penalty (> 0); 1                               */
+    double   abs_tol, rel_tol;  /* ADMM stopping tolerances; 1e-6, 1e-6                */
+    int32_t  max_iter;          /* ADMM iteration cap per column; 1000                 */
+    double   train_frac;        /* estimation pool fraction in (0,1); 0.8              */
+    uint64_t seed;              /* Philox key word 0; 0                                */
+    uint64_t problem_id;        /* Philox key word 1; 0                                */
+    int64_t  block_len;         /* 0/1 = iid rows, L > 1 = blocks of L lagged rows     */
+    int32_t  bagging;           /* UOI_BAG_*; median                                   */
+    int32_t  split_mode;        /* UOI_SPLIT_*; per bootstrap                          */
+    int32_t  precision;         /* UOI_PREC_*; FP64                                    */
+    int32_t  warm_start;        /* UOI_WARM_*; path                                    */
+    const char* mlp_weights_path; /* learned warm start weights, NULL = none           */
+    void*    stream;            /* cudaStream_t, NULL = default stream                 */
+} uoi_params;
+
+/* Timings and counters of the last fit (every field written when non-NULL). */
+typedef struct uoi_diag {
+    uint32_t struct_size;
+    float    ms_total, ms_bootstrap, ms_gram, ms_factor, ms_admm, ms_support, ms_estimation;
+    int64_t  admm_columns;        /* (bootstrap, equation, lambda) columns solved        */
+    int64_t  admm_nonconverged;   /* columns that stopped at max_iter                    */
+    int64_t  admm_iterations;     /* sum of iterations over all columns                  */
+    int32_t  admm_max_iterations; /* largest per-column iteration count                  */
+    int64_t  ols_singular;        /* supports whose OLS took the regularised fallback    */
+    int64_t  gpu_launches;        /* kernels this library launched during the fit        */
+} uoi_diag;
+
+/* Optional intermediate results of a fit, for testing (every pointer nullable,
+ * host or device).  Shapes use r = response columns (1 for LASSO, p for VAR). */
+typedef struct uoi_trace {
+    double*   lambdas;      /* q                                                  */
+    uint32_t* sel_weights;  /* B1 x m   bootstrap multiplicities of T^k           */
+    uint32_t* est_weights;  /* B2 x m   multiplicities of the training sample T^k */
+    uint8_t*  est_eval;     /* B2 x m   1 = row in the evaluation set E^k         */
+    double*   sel_beta;     /* B1 x q x r x p  LASSO estimates (final z)          */
+    int32_t*  sel_iters;    /* B1 x q x r                                         */
+    uint8_t*  sel_conv;     /* B1 x q x r                                         */
+    uint64_t* family;       /* q x r x ceil(p/64)  supports S_j (Eq. 3)           */
+    double*   est_loss;     /* B2 x q x r  held-out squared-error sums            */
+    int32_t*  est_jstar;    /* B2  chosen support index per bootstrap             */
+    double*   est_beta;     /* B2 x r x p  the chosen OLS estimate per bootstrap  */
+    int32_t*  est_singular; /* B2 x q x r  1 = regularised fallback               */
+} uoi_trace;
+
+/* Fill *prm with the defaults listed above (B1 = B2 = 20, q = 16). */
+void uoi_params_default(uoi_params* prm);
+
+/* UoI_LASSO (Alg. 1).  X: n x p, y: n.  beta_out: p (the bagged estimate,
+ * Alg. 1 "Return").  family_out: q x ceil(p/64) words, bit i of S_j (Eq. 3),
+ * nullable.  diag nullable. */
+int uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p,
+                  const uoi_params* prm, double* beta_out, uint64_t* family_out,
+                  uoi_diag* diag);
+
+/* UoI_VAR(order) (Alg. 2).  series: N x p, time ascending (row t = X_t).
+ * Only order 1 is supported (else UOI_ERR_UNSUPPORTED).  The lagged design
+ * pairs the response X_{t+1} with the regressor X_t (Eq. 7-8, rows in
+ * ascending time) and is solved as p LASSOs sharing that design (Eq. 9).
+ * A_out: order x p x p, A_out[e*p + i] = coefficient of X_{t-1,i} in
+ * equation e (Alg. 2 "Partition ... into A_1 ... A_d").  mu_out: p, the
+ * intercept; no intercept is fitted, so it is zero-filled (nullable). */
+int uoi_var_fit(const double* series, int64_t N, int64_t p, int32_t order,
+                const uoi_params* prm, double* A_out, double* mu_out, uoi_diag* diag);
+
+/* General form used by both fits: r response columns Y (m x r, row stride ldy)
+ * on the design X (m x p, row stride ldx).  beta_out: r x p.  trace nullable. */
+int uoi_fit_traced(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                   int64_t m, int64_t p, int64_t r, const uoi_params* prm,
+                   double* beta_out, uoi_trace* trace, uoi_diag* diag);
+
+/* Batched LASSO by ADMM (Eq. 5) -- the selection step's solver on caller
+ * supplied weights: for every weight vector k < B (weights: B x n counts,
+ * NULL = unweighted, then B must be 1), response column e < r of Y (n x r)
+ * and lambda_j, minimise (1/(2 n_k)) ||y_e - X b||^2_{W_k} + lambda_j ||b||_1
+ * with n_k = sum of weights k.  beta_out: B x q x r x p (final z).
+ * iters_out, converged_out: B x q x r, nullable. precision: UOI_PREC_*,
+ * warm_start: UOI_WARM_NONE or UOI_WARM_PATH.  stream: cudaStream_t or NULL. */
+int lasso_admm_batch(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
+                     const uint32_t* weights, int32_t B, const double* lambdas, int32_t q,
+                     double rho, double abs_tol, double rel_tol, int32_t max_iter,
+                     int32_t precision, int32_t warm_start, double* beta_out,
+                     int32_t* iters_out, uint8_t* converged_out, void* stream);
+
+/* Text of a status code (static storage). */
+const char* uoi_status_string(int status);
+
+/* Copy the detail message of the last error on this thread into buf (NUL
+ * terminated, truncated to len).  Returns the message length. */
+int uoi_get_last_error_detail(char* buf, size_t len);
+
+/* Free the library's device scratch on the current device. */
+void uoi_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

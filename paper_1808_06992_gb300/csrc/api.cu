@@ -1,0 +1,553 @@
+// api.cu -- the C ABI (include/uoi.h) and the host orchestration of one fit.
+//
+// uoi_fit_traced runs Alg. 1 (r = 1) / Alg. 2 with order 1 (r = p) on one GPU:
+//   lambda grid -> selection bootstraps (G0) -> moments (G1) -> factor (G3)
+//   -> ADMM over all (bootstrap, equation, lambda) columns with the support
+//   intersection fused into column completion (G4/G5) -> estimation bootstraps
+//   -> training/evaluation moments -> OLS + held-out loss per (k, j, e) (G6)
+//   -> argmin per bootstrap, chosen OLS, bagging (G7).
+// Inputs may live on the host or the device; host data is copied in once.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace uoi {
+
+int64_t g_launches = 0;
+
+void DevBuf::alloc(size_t n, cudaStream_t s)
+{
+    release();
+    if (n == 0) n = 16;
+    UOI_CUDA(cudaMallocAsync(&ptr, n, s));
+    bytes = n;
+    stream = s;
+}
+
+void DevBuf::release()
+{
+    if (ptr) cudaFreeAsync(ptr, stream);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void ensure_pool()
+{
+    int dev = 0;
+    UOI_CUDA(cudaGetDevice(&dev));
+    static bool done[64] = {};
+    if (dev < 64 && !done[dev]) {
+        cudaMemPool_t pool;
+        UOI_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+        uint64_t thr = UINT64_MAX;
+        UOI_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        done[dev] = true;
+    }
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller input: the pointer itself, or a copy of host data.
+template <typename T>
+const T* dev_in(const T* p, size_t count, DevBuf& hold, cudaStream_t s)
+{
+    if (!p) return nullptr;
+    if (is_device_ptr(p)) return p;
+    hold.alloc(sizeof(T) * count, s);
+    UOI_CUDA(cudaMemcpyAsync(hold.ptr, p, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+    return hold.as<T>();
+}
+
+// Device destination for a caller output; finish() copies back host outputs.
+template <typename T>
+struct DevOut {
+    T* user = nullptr;
+    T* dev = nullptr;
+    size_t count = 0;
+    DevBuf hold;
+    void init(T* p, size_t n, cudaStream_t s)
+    {
+        user = p;
+        count = n;
+        if (!p) { dev = nullptr; return; }
+        if (is_device_ptr(p)) { dev = p; return; }
+        hold.alloc(sizeof(T) * n, s);
+        dev = hold.as<T>();
+    }
+    void finish(cudaStream_t s)
+    {
+        if (user && dev && dev != user)
+            UOI_CUDA(cudaMemcpyAsync(user, dev, sizeof(T) * count, cudaMemcpyDeviceToHost, s));
+    }
+};
+
+struct StageTimer {
+    cudaStream_t s;
+    std::vector<cudaEvent_t> ev;
+    explicit StageTimer(cudaStream_t st) : s(st) {}
+    int mark()
+    {
+        cudaEvent_t e;
+        UOI_CUDA(cudaEventCreate(&e));
+        UOI_CUDA(cudaEventRecord(e, s));
+        ev.push_back(e);
+        return (int)ev.size() - 1;
+    }
+    float ms(int a, int b)
+    {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+    ~StageTimer()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+void check_status(DevStatus* st, cudaStream_t s, const char* what)
+{
+    DevStatus h{};
+    UOI_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    if (h.code != 0)
+        throw Error(h.code, std::string(what) + " failed on batch item " + std::to_string(h.where));
+}
+
+void validate(const uoi_params* prm)
+{
+    if (!prm) throw Error(UOI_ERR_INVALID_ARG, "params is NULL");
+    if (prm->struct_size != 0 && prm->struct_size < sizeof(uoi_params))
+        throw Error(UOI_ERR_INVALID_ARG, "uoi_params.struct_size too small");
+    if (prm->B1 <= 0 || prm->B2 <= 0 || prm->q <= 0)
+        throw Error(UOI_ERR_INVALID_ARG, "B1, B2 and q must be positive");
+    if (!(prm->rho > 0.0)) throw Error(UOI_ERR_INVALID_ARG, "rho must be positive");
+    if (prm->max_iter <= 0) throw Error(UOI_ERR_INVALID_ARG, "max_iter must be positive");
+    if (!(prm->train_frac > 0.0 && prm->train_frac < 1.0))
+        throw Error(UOI_ERR_INVALID_ARG, "train_frac must lie in (0, 1)");
+    if (!(prm->abs_tol >= 0.0) || !(prm->rel_tol >= 0.0))
+        throw Error(UOI_ERR_INVALID_ARG, "tolerances must be non-negative");
+    if (prm->bagging != UOI_BAG_MEDIAN && prm->bagging != UOI_BAG_MEAN)
+        throw Error(UOI_ERR_INVALID_ARG, "unknown bagging mode");
+    if (prm->bagging == UOI_BAG_MEDIAN && prm->B2 > 128)
+        throw Error(UOI_ERR_UNSUPPORTED, "median bagging supports B2 <= 128");
+    if (prm->precision != UOI_PREC_FP64 && prm->precision != UOI_PREC_MIXED)
+        throw Error(UOI_ERR_INVALID_ARG, "unknown precision");
+    if (prm->warm_start == UOI_WARM_LEARNED)
+        throw Error(UOI_ERR_UNSUPPORTED, "learned warm start needs trained weights");
+    if (prm->warm_start != UOI_WARM_NONE && prm->warm_start != UOI_WARM_PATH)
+        throw Error(UOI_ERR_INVALID_ARG, "unknown warm start mode");
+    if (prm->lambda_min_ratio <= 0.0 && !prm->lambdas)
+        throw Error(UOI_ERR_INVALID_ARG, "lambda_min_ratio must be positive");
+}
+
+// Moments for B weight vectors in the precision of the fit.
+void moments(int precision, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+             int64_t m, int64_t p, int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B,
+             double* G, double* Bm, cudaStream_t s)
+{
+    if (precision == UOI_PREC_MIXED && gram_tc_available())
+        moments_tc(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, s);
+    else
+        moments_fp64(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, 0, s);
+}
+
+template <typename T>
+void selection_admm(int precision, const double* Xd, int64_t ldx, const double* Yd, int64_t ldy,
+                    int64_t m, int64_t p, int64_t r, const uint32_t* w, int32_t B,
+                    const double* lam, int32_t q, double rho, double abs_tol, double rel_tol,
+                    int32_t max_iter, int32_t warm, double* beta, int32_t* iters, uint8_t* conv,
+                    uint64_t* family, cudaStream_t s, StageTimer* tm, float* ms)
+{
+    int t0 = tm ? tm->mark() : 0;
+    DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
+    DevBuf nk(sizeof(double) * B, s);
+    moments(precision, Xd, ldx, Yd, ldy, m, p, r, w, nullptr, B, G.as<double>(), Bm.as<double>(), s);
+    if (w) {
+        weight_sums(w, nullptr, m, B, nk.as<double>(), s);
+    } else {
+        const double mm = (double)m;
+        UOI_CUDA(cudaMemcpyAsync(nk.ptr, &mm, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    int t1 = tm ? tm->mark() : 0;
+    DevBuf st(sizeof(DevStatus), s);
+    UOI_CUDA(cudaMemsetAsync(st.ptr, 0, st.bytes, s));
+    build_and_factor(G.as<double>(), nk.as<double>(), rho, p, B, G.as<double>(), st.as<DevStatus>(), s);
+    check_status(st.as<DevStatus>(), s, "Cholesky of G/n + rho I");
+    DevBuf Linv(sizeof(T) * (size_t)(B * p * p), s), M(sizeof(T) * (size_t)(B * p * p), s);
+    DevBuf c(sizeof(T) * (size_t)(B * p * r), s);
+    inverse_and_rhs<T>(G.as<double>(), Bm.as<double>(), nk.as<double>(), p, r, B, Linv.as<T>(),
+                       M.as<T>(), c.as<T>(), s);
+    Linv.release();
+    G.release();
+    int t2 = tm ? tm->mark() : 0;
+    AdmmProblem<T> P;
+    P.G = B; P.p = p; P.r = r; P.q = q;
+    P.M = M.as<T>(); P.c = c.as<T>(); P.lambdas = lam;
+    P.rho = rho; P.abs_tol = abs_tol; P.rel_tol = rel_tol; P.max_iter = max_iter; P.warm = warm;
+    P.beta = beta; P.iters = iters; P.conv = conv; P.family = family;
+    admm_solve<T>(P, s);
+    int t3 = tm ? tm->mark() : 0;
+    if (tm && ms) { ms[0] += tm->ms(t0, t1); ms[1] += tm->ms(t1, t2); ms[2] += tm->ms(t2, t3); }
+}
+
+struct IterStats { int64_t cols = 0, noncon = 0, iters = 0; int32_t maxit = 0; };
+
+IterStats iteration_stats(const int32_t* iters_d, const uint8_t* conv_d, int64_t n, cudaStream_t s)
+{
+    std::vector<int32_t> it((size_t)n);
+    std::vector<uint8_t> cv((size_t)n);
+    UOI_CUDA(cudaMemcpyAsync(it.data(), iters_d, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaMemcpyAsync(cv.data(), conv_d, n, cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    IterStats st;
+    st.cols = n;
+    for (int64_t i = 0; i < n; ++i) {
+        st.iters += it[i];
+        st.maxit = std::max(st.maxit, it[i]);
+        st.noncon += cv[i] ? 0 : 1;
+    }
+    return st;
+}
+
+int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
+             int64_t r, const uoi_params* prm, double* beta_out, uoi_trace* tr, uoi_diag* diag,
+             const double* shared_series = nullptr, int64_t series_count = 0)
+{
+    validate(prm);
+    if (!X || !Y || !beta_out) throw Error(UOI_ERR_INVALID_ARG, "NULL data pointer");
+    if (m <= 0 || p <= 0 || r <= 0) throw Error(UOI_ERR_INVALID_ARG, "sizes must be positive");
+    if (prm->block_len > m) throw Error(UOI_ERR_INVALID_ARG, "block_len exceeds the number of rows");
+    ensure_pool();
+    cudaStream_t s = (cudaStream_t)prm->stream;
+    const int64_t launches0 = g_launches;
+    StageTimer tm(s);
+    const int tstart = tm.mark();
+    const int32_t B1 = prm->B1, B2 = prm->B2, q = prm->q;
+    const int64_t W = (p + 63) / 64;
+    const bool mixed = prm->precision == UOI_PREC_MIXED;
+
+    // inputs (the VAR series is copied once; X and Y are views into it)
+    DevBuf hx, hy;
+    const double* Xd;
+    const double* Yd;
+    if (shared_series) {
+        const double* sd = dev_in(shared_series, (size_t)series_count, hx, s);
+        Xd = sd + (X - shared_series);
+        Yd = sd + (Y - shared_series);
+    } else {
+        Xd = dev_in(X, (size_t)((m - 1) * ldx + p), hx, s);
+        Yd = dev_in(Y, (size_t)((m - 1) * ldy + r), hy, s);
+    }
+    {
+        DevBuf flag(sizeof(int32_t), s);
+        UOI_CUDA(cudaMemsetAsync(flag.ptr, 0, sizeof(int32_t), s));
+        check_finite(Xd, ldx, m, p, flag.as<int32_t>(), s);
+        check_finite(Yd, ldy, m, r, flag.as<int32_t>(), s);
+        int32_t h = 0;
+        UOI_CUDA(cudaMemcpyAsync(&h, flag.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        UOI_CUDA(cudaStreamSynchronize(s));
+        if (h) throw Error(UOI_ERR_NONFINITE, "X or Y holds NaN or Inf");
+    }
+    const PhiloxKey key{ prm->seed, prm->problem_id };
+
+    // lambda grid
+    DevBuf lam(sizeof(double) * q, s), lam_hold;
+    if (prm->lambdas) {
+        const double* ld = dev_in(prm->lambdas, (size_t)q, lam_hold, s);
+        UOI_CUDA(cudaMemcpyAsync(lam.ptr, ld, sizeof(double) * q, cudaMemcpyDeviceToDevice, s));
+    } else {
+        DevBuf xty(sizeof(double) * (size_t)(p * r), s);
+        moments_fp64(Xd, ldx, Yd, ldy, m, p, r, nullptr, nullptr, 1, nullptr, xty.as<double>(), 1, s);
+        lambda_grid(xty.as<double>(), p * r, m, q, prm->lambda_min_ratio, lam.as<double>(), s);
+    }
+
+    // ---- selection ----
+    const int t_sel0 = tm.mark();
+    DevBuf wsel(sizeof(uint32_t) * (size_t)(B1 * m), s);
+    selection_weights(m, prm->block_len, key, B1, wsel.as<uint32_t>(), s);
+    const int t_sel1 = tm.mark();
+    const int64_t ncol = (int64_t)B1 * q * r;
+    DevOut<double> sel_beta;
+    sel_beta.init(tr ? tr->sel_beta : nullptr, (size_t)(ncol * p), s);
+    DevBuf iters_b(sizeof(int32_t) * ncol, s), conv_b(ncol, s);
+    DevBuf fam(sizeof(uint64_t) * (size_t)(q * r * W), s);
+    family_init(fam.as<uint64_t>(), q * r * W, s);
+    float stage_ms[3] = { 0.f, 0.f, 0.f };
+    if (mixed)
+        selection_admm<float>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
+                              lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
+                              prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
+                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, stage_ms);
+    else
+        selection_admm<double>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
+                               lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
+                               prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
+                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, stage_ms);
+    family_mask_tail(fam.as<uint64_t>(), q * r, p, s);
+    const int t_sel2 = tm.mark();
+
+    // ---- estimation ----
+    DevBuf west(sizeof(uint32_t) * (size_t)(B2 * m), s), evm((size_t)(B2 * m), s);
+    estimation_weights(m, prm->block_len, prm->train_frac, prm->split_mode, key, B2,
+                       west.as<uint32_t>(), evm.as<uint8_t>(), s);
+    DevBuf Gt(sizeof(double) * (size_t)(B2 * p * p), s), Bt(sizeof(double) * (size_t)(B2 * p * r), s);
+    DevBuf Ge(sizeof(double) * (size_t)(B2 * p * p), s), Be(sizeof(double) * (size_t)(B2 * p * r), s);
+    DevBuf yye(sizeof(double) * (size_t)(B2 * r), s);
+    moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, west.as<uint32_t>(), nullptr, B2,
+            Gt.as<double>(), Bt.as<double>(), s);
+    moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, nullptr, evm.as<uint8_t>(), B2,
+            Ge.as<double>(), Be.as<double>(), s);
+    masked_sumsq(Yd, ldy, m, r, evm.as<uint8_t>(), B2, yye.as<double>(), s);
+    const int t_est1 = tm.mark();
+    DevOut<double> loss_o;
+    DevBuf loss_b;
+    loss_o.init(tr ? tr->est_loss : nullptr, (size_t)(B2 * q * r), s);
+    double* losses = loss_o.dev;
+    if (!losses) { loss_b.alloc(sizeof(double) * (size_t)(B2 * q * r), s); losses = loss_b.as<double>(); }
+    DevBuf sing(sizeof(int32_t) * (size_t)(B2 * q * r), s);
+    ols_losses(Gt.as<double>(), Bt.as<double>(), Ge.as<double>(), Be.as<double>(), yye.as<double>(),
+               fam.as<uint64_t>(), p, r, q, B2, losses, sing.as<int32_t>(), s);
+    DevBuf jst(sizeof(int32_t) * B2, s);
+    loss_argmin(losses, B2, q, r, jst.as<int32_t>(), s);
+    DevBuf chosen(sizeof(double) * (size_t)(B2 * r * p), s);
+    ols_chosen(Gt.as<double>(), Bt.as<double>(), fam.as<uint64_t>(), jst.as<int32_t>(), p, r, q, B2,
+               chosen.as<double>(), s);
+    DevOut<double> bo;
+    bo.init(beta_out, (size_t)(r * p), s);
+    bagging(chosen.as<double>(), B2, r * p, prm->bagging, bo.dev, s);
+    const int t_end = tm.mark();
+
+    // ---- outputs ----
+    bo.finish(s);
+    if (tr) {
+        auto copy_out = [&](void* dst, const void* src, size_t bytes) {
+            if (!dst) return;
+            UOI_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+        };
+        copy_out(tr->lambdas, lam.ptr, sizeof(double) * q);
+        copy_out(tr->sel_weights, wsel.ptr, sizeof(uint32_t) * (size_t)(B1 * m));
+        copy_out(tr->est_weights, west.ptr, sizeof(uint32_t) * (size_t)(B2 * m));
+        copy_out(tr->est_eval, evm.ptr, (size_t)(B2 * m));
+        copy_out(tr->sel_iters, iters_b.ptr, sizeof(int32_t) * ncol);
+        copy_out(tr->sel_conv, conv_b.ptr, (size_t)ncol);
+        copy_out(tr->family, fam.ptr, sizeof(uint64_t) * (size_t)(q * r * W));
+        copy_out(tr->est_jstar, jst.ptr, sizeof(int32_t) * B2);
+        copy_out(tr->est_beta, chosen.ptr, sizeof(double) * (size_t)(B2 * r * p));
+        copy_out(tr->est_singular, sing.ptr, sizeof(int32_t) * (size_t)(B2 * q * r));
+        sel_beta.finish(s);
+        loss_o.finish(s);
+    }
+    UOI_CUDA(cudaStreamSynchronize(s));
+    IterStats its = iteration_stats(iters_b.as<int32_t>(), conv_b.as<uint8_t>(), ncol, s);
+    std::vector<int32_t> sg((size_t)(B2 * q * r));
+    UOI_CUDA(cudaMemcpyAsync(sg.data(), sing.ptr, sizeof(int32_t) * sg.size(), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    int64_t nsing = 0;
+    for (auto v : sg) nsing += v;
+    if (diag) {
+        diag->ms_total = tm.ms(tstart, t_end);
+        diag->ms_bootstrap = tm.ms(t_sel0, t_sel1);
+        diag->ms_gram = stage_ms[0];
+        diag->ms_factor = stage_ms[1];
+        diag->ms_admm = stage_ms[2];
+        diag->ms_support = 0.f;
+        diag->ms_estimation = tm.ms(t_sel2, t_end);
+        (void)t_est1;
+        diag->admm_columns = its.cols;
+        diag->admm_nonconverged = its.noncon;
+        diag->admm_iterations = its.iters;
+        diag->admm_max_iterations = its.maxit;
+        diag->ols_singular = nsing;
+        diag->gpu_launches = g_launches - launches0;
+    }
+    return (its.noncon > 0 || nsing > 0) ? UOI_OK_WITH_WARNINGS : UOI_OK;
+}
+
+template <typename F>
+int guarded(F&& f)
+{
+    try {
+        g_last_error.clear();
+        return f();
+    } catch (const Error& e) {
+        g_last_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return UOI_ERR_OOM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return UOI_ERR_CUDA;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return UOI_ERR_CUDA;
+    }
+}
+
+}  // namespace
+}  // namespace uoi
+
+using namespace uoi;
+
+extern "C" {
+
+void uoi_params_default(uoi_params* prm)
+{
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->struct_size = sizeof(uoi_params);
+    prm->B1 = 20; prm->B2 = 20; prm->q = 16;
+    prm->lambda_min_ratio = 1e-3;
+    prm->rho = 1.0; prm->abs_tol = 1e-6; prm->rel_tol = 1e-6; prm->max_iter = 1000;
+    prm->train_frac = 0.8;
+    prm->bagging = UOI_BAG_MEDIAN;
+    prm->split_mode = UOI_SPLIT_PER_BOOTSTRAP;
+    prm->precision = UOI_PREC_FP64;
+    prm->warm_start = UOI_WARM_PATH;
+}
+
+int uoi_fit_traced(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
+                   int64_t p, int64_t r, const uoi_params* prm, double* beta_out, uoi_trace* trace,
+                   uoi_diag* diag)
+{
+    return guarded([&] { return fit_core(X, ldx, Y, ldy, m, p, r, prm, beta_out, trace, diag); });
+}
+
+int uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p, const uoi_params* prm,
+                  double* beta_out, uint64_t* family_out, uoi_diag* diag)
+{
+    return guarded([&] {
+        uoi_trace tr;
+        std::memset(&tr, 0, sizeof(tr));
+        tr.family = family_out;
+        return fit_core(X, p, y, 1, n, p, 1, prm, beta_out, family_out ? &tr : nullptr, diag);
+    });
+}
+
+int uoi_var_fit(const double* series, int64_t N, int64_t p, int32_t order, const uoi_params* prm,
+                double* A_out, double* mu_out, uoi_diag* diag)
+{
+    return guarded([&] {
+        if (order != 1) throw Error(UOI_ERR_UNSUPPORTED, "only VAR order 1 is implemented");
+        if (!series || !A_out) throw Error(UOI_ERR_INVALID_ARG, "NULL data pointer");
+        if (N < 3 || p <= 0) throw Error(UOI_ERR_INVALID_ARG, "need N >= 3 and p > 0");
+        // Eq. 7-8 with d = 1, ascending time: row t regresses X_{t+1} on X_t.
+        const int st = fit_core(series, p, series + p, p, N - 1, p, p, prm, A_out, nullptr, diag,
+                                series, N * p);
+        if (mu_out) {
+            cudaStream_t s = (cudaStream_t)prm->stream;
+            if (is_device_ptr(mu_out)) UOI_CUDA(cudaMemsetAsync(mu_out, 0, sizeof(double) * p, s));
+            else std::memset(mu_out, 0, sizeof(double) * p);
+            UOI_CUDA(cudaStreamSynchronize(s));
+        }
+        return st;
+    });
+}
+
+int lasso_admm_batch(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
+                     const uint32_t* weights, int32_t B, const double* lambdas, int32_t q,
+                     double rho, double abs_tol, double rel_tol, int32_t max_iter,
+                     int32_t precision, int32_t warm_start, double* beta_out, int32_t* iters_out,
+                     uint8_t* converged_out, void* stream)
+{
+    return guarded([&] {
+        if (!X || !Y || !lambdas || !beta_out) throw Error(UOI_ERR_INVALID_ARG, "NULL pointer");
+        if (n <= 0 || p <= 0 || r <= 0 || q <= 0 || B <= 0 || max_iter <= 0)
+            throw Error(UOI_ERR_INVALID_ARG, "sizes must be positive");
+        if (!weights && B != 1) throw Error(UOI_ERR_INVALID_ARG, "unweighted call needs B == 1");
+        if (!(rho > 0.0)) throw Error(UOI_ERR_INVALID_ARG, "rho must be positive");
+        if (precision != UOI_PREC_FP64 && precision != UOI_PREC_MIXED)
+            throw Error(UOI_ERR_INVALID_ARG, "unknown precision");
+        if (warm_start != UOI_WARM_NONE && warm_start != UOI_WARM_PATH)
+            throw Error(warm_start == UOI_WARM_LEARNED ? UOI_ERR_UNSUPPORTED : UOI_ERR_INVALID_ARG,
+                        "lasso_admm_batch supports warm_start NONE or PATH");
+        ensure_pool();
+        cudaStream_t s = (cudaStream_t)stream;
+        DevBuf hx, hy, hw, hl;
+        const double* Xd = dev_in(X, (size_t)(n * p), hx, s);
+        const double* Yd = dev_in(Y, (size_t)(n * r), hy, s);
+        const uint32_t* wd = dev_in(weights, (size_t)(B * n), hw, s);
+        const double* ld = dev_in(lambdas, (size_t)q, hl, s);
+        const int64_t ncol = (int64_t)B * q * r;
+        DevOut<double> bo;
+        bo.init(beta_out, (size_t)(ncol * p), s);
+        DevOut<int32_t> io;
+        io.init(iters_out, (size_t)ncol, s);
+        DevOut<uint8_t> co;
+        co.init(converged_out, (size_t)ncol, s);
+        DevBuf ib, cb;
+        int32_t* it_d = io.dev;
+        uint8_t* cv_d = co.dev;
+        if (!it_d) { ib.alloc(sizeof(int32_t) * ncol, s); it_d = ib.as<int32_t>(); }
+        if (!cv_d) { cb.alloc(ncol, s); cv_d = cb.as<uint8_t>(); }
+        if (precision == UOI_PREC_MIXED)
+            selection_admm<float>(precision, Xd, p, Yd, r, n, p, r, wd, B, ld, q, rho, abs_tol,
+                                  rel_tol, max_iter, warm_start, bo.dev, it_d, cv_d, nullptr, s,
+                                  nullptr, nullptr);
+        else
+            selection_admm<double>(precision, Xd, p, Yd, r, n, p, r, wd, B, ld, q, rho, abs_tol,
+                                   rel_tol, max_iter, warm_start, bo.dev, it_d, cv_d, nullptr, s,
+                                   nullptr, nullptr);
+        bo.finish(s);
+        io.finish(s);
+        co.finish(s);
+        UOI_CUDA(cudaStreamSynchronize(s));
+        IterStats its = iteration_stats(it_d, cv_d, ncol, s);
+        return its.noncon > 0 ? UOI_OK_WITH_WARNINGS : UOI_OK;
+    });
+}
+
+const char* uoi_status_string(int status)
+{
+    switch (status) {
+    case UOI_OK: return "ok";
+    case UOI_OK_WITH_WARNINGS: return "ok with warnings (non-converged columns or singular supports)";
+    case UOI_ERR_INVALID_ARG: return "invalid argument";
+    case UOI_ERR_NONFINITE: return "non-finite input";
+    case UOI_ERR_NOT_PD: return "matrix not positive definite";
+    case UOI_ERR_CUDA: return "CUDA error";
+    case UOI_ERR_OOM: return "out of device memory";
+    case UOI_ERR_TIMEOUT: return "bounded device loop ran out of iterations";
+    case UOI_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+    }
+}
+
+int uoi_get_last_error_detail(char* buf, size_t len)
+{
+    const int n = (int)g_last_error.size();
+    if (buf && len > 0) {
+        std::snprintf(buf, len, "%s", g_last_error.c_str());
+    }
+    return n;
+}
+
+void uoi_shutdown(void)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaDeviceSynchronize();
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// common.cuh -- shared device helpers of the GB300 UoI library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "../../include/uoi.h"
+
+namespace uoi {
+
+// ---------------------------------------------------------------------------
+// Errors: host code throws uoi::Error, the C-ABI layer turns it into a status.
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+    int status;
+    Error(int s, const std::string& msg) : std::runtime_error(msg), status(s) {}
+};
+
+#define UOI_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t err__ = (call);                                                     \
+        if (err__ != cudaSuccess)                                                       \
+            throw ::uoi::Error(err__ == cudaErrorMemoryAllocation ? UOI_ERR_OOM         \
+                                                                 : UOI_ERR_CUDA,        \
+                               std::string(#call) + ": " + cudaGetErrorString(err__));  \
+    } while (0)
+
+#define UOI_CHECK_LAUNCH() UOI_CUDA(cudaGetLastError())
+
+// Count of kernels this library launched (reported in uoi_diag.gpu_launches).
+extern int64_t g_launches;
+inline void count_launch(int64_t n = 1) { g_launches += n; }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11), written for the device.  The i-th draw
+// of stream (k, tag) is lane i%4 of Philox(counter=(i/4, k, tag, 0),
+// key=(seed, problem)); index maps use floor(r * n / 2^64).
+// ---------------------------------------------------------------------------
+struct PhiloxKey { uint64_t seed, problem; };
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; k1 += W1; }
+        uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+__device__ __forceinline__ uint64_t philox_draw(PhiloxKey key, uint64_t k, uint64_t tag, uint64_t i)
+{
+    uint64_t c[4] = { i >> 2, k, tag, 0 };
+    philox4x64_10(c, key.seed, key.problem);
+    const uint32_t lane = (uint32_t)(i & 3u);
+    return lane == 0 ? c[0] : lane == 1 ? c[1] : lane == 2 ? c[2] : c[3];
+}
+
+__device__ __forceinline__ uint64_t range_map(uint64_t r, uint64_t n) { return __umul64hi(r, n); }
+
+enum : uint32_t { TAG_SELECTION = 1, TAG_SPLIT = 2, TAG_RESAMPLE = 3 };
+
+// ---------------------------------------------------------------------------
+// Small device utilities
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T soft_threshold(T v, T kappa)
+{
+    return v > kappa ? v - kappa : (v < -kappa ? v + kappa : T(0));
+}
+
+// Device-side error word: kernels record the first error here and return.
+struct DevStatus {
+    int32_t code;      // 0 = ok, else a UOI_ERR_* value
+    int32_t where;     // kernel-specific detail (index)
+};
+
+__device__ __forceinline__ void dev_fail(DevStatus* st, int code, int where)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+}  // namespace uoi

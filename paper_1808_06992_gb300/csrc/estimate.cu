@@ -1,0 +1,307 @@
+// estimate.cu -- G5-G7: support family, support-restricted OLS, held-out loss,
+// argmin over the family and bagging (Alg. 1/2 model estimation, Eq. 3-4).
+//
+// For estimation bootstrap k and family member S_j (per response e):
+//   beta = argmin || W^{1/2} (y_e - X_S b) ||   via Cholesky of G'_k[S,S] (FP64)
+//   L_kje = sum_{t in E^k} (y_te - x_t beta)^2
+//         = y_E'y_E - 2 beta' (X_E'y_E)_S + beta' G^E_k[S,S] beta
+// j*_k = argmin_j sum_e L_kje (ties -> smallest j); beta*_e = median (or mean)
+// over k of the chosen estimates (zero outside the support).
+// Singular supports (a Cholesky pivot <= 1e-12 max diag) are refit with a
+// 1e-10 max-diag ridge and flagged.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace uoi {
+
+namespace {
+
+constexpr int OLS_SMEM_MAX = 160;   // supports up to this size factor in shared memory
+
+struct OlsArgs {
+    const double* Gt; const double* Bt;      // B2 x p x p, B2 x p x r
+    const double* Ge; const double* Be;      // B2 x p x p, B2 x p x r
+    const double* yye;                       // B2 x r
+    const uint64_t* family;                  // q x r x W
+    int64_t p, r; int32_t q, B2, W;
+    const int32_t* jstar;                    // chosen pass: B2 (else null)
+    double* losses;                          // B2 x q x r
+    int32_t* singular;                       // B2 x q x r (nullable)
+    double* chosen;                          // chosen pass: B2 x r x p
+    double* scratch;                         // global factor scratch (per CTA), or null
+    int64_t solves;
+    int smax;                                // max support size
+    bool use_smem;
+};
+
+__global__ void __launch_bounds__(256) k_ols(OlsArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* idx = reinterpret_cast<int*>(smem_raw);                         // p ints
+    double* bs = reinterpret_cast<double*>(smem_raw + sizeof(int) * ((a.p + 1) & ~1));
+    double* red = bs + a.smax + 1;                                       // 32 doubles
+    double* Gs = a.use_smem ? red + 32 : a.scratch + (size_t)blockIdx.x * a.smax * a.smax;
+    __shared__ int s_count;
+    __shared__ int s_bad;
+    __shared__ double s_dmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int64_t t = blockIdx.x; t < a.solves; t += gridDim.x) {
+        int k, j, e;
+        if (a.jstar) { k = (int)(t / a.r); e = (int)(t % a.r); j = a.jstar[k]; }
+        else { k = (int)(t / ((int64_t)a.q * a.r)); const int64_t rem = t % ((int64_t)a.q * a.r);
+               j = (int)(rem / a.r); e = (int)(rem % a.r); }
+        const uint64_t* bits = a.family + ((int64_t)j * a.r + e) * a.W;
+        // support indices (warp 0, ballot compaction in increasing i)
+        if (warp == 0) {
+            int cnt = 0;
+            for (int64_t i0 = 0; i0 < a.p; i0 += 32) {
+                const int64_t i = i0 + lane;
+                const bool in = i < a.p && ((bits[i >> 6] >> (i & 63)) & 1ull);
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (in) idx[cnt + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+                cnt += __popc(bal);
+            }
+            if (lane == 0) { s_count = cnt; s_bad = 0; }
+        }
+        __syncthreads();
+        const int s = s_count;
+        const double* Gk = a.Gt + (size_t)k * a.p * a.p;
+        const double* Bk = a.Bt + (size_t)k * a.p * a.r;
+        double ridge = 0.0;
+        for (int attempt = 0; attempt < 2 && s > 0; ++attempt) {
+            double dm = 0.0;
+            for (int x = threadIdx.x; x < s * s; x += blockDim.x) {
+                const int r0 = x / s, c0 = x % s;
+                const double v = Gk[(size_t)idx[r0] * a.p + idx[c0]];
+                Gs[x] = v + (r0 == c0 ? ridge : 0.0);
+                if (r0 == c0) dm = fmax(dm, v);
+            }
+            for (int x = threadIdx.x; x < s; x += blockDim.x) bs[x] = Bk[(size_t)idx[x] * a.r + e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+            if (lane == 0) red[warp] = dm;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double m = 0.0;
+                for (int w = 0; w < 8; ++w) m = fmax(m, red[w]);
+                s_dmax = m;
+                s_bad = 0;
+            }
+            __syncthreads();
+            const double thr = 1e-12 * s_dmax;
+            // unblocked right-looking Cholesky of Gs (lower)
+            for (int c = 0; c < s; ++c) {
+                if (threadIdx.x == 0) {
+                    const double d = Gs[c * s + c];
+                    if (!(d > thr)) { s_bad = 1; Gs[c * s + c] = 1.0; } else Gs[c * s + c] = sqrt(d);
+                }
+                __syncthreads();
+                const double lcc = Gs[c * s + c];
+                for (int i = c + 1 + threadIdx.x; i < s; i += blockDim.x) Gs[i * s + c] /= lcc;
+                __syncthreads();
+                const int rem = s - c - 1;
+                for (int x = threadIdx.x; x < rem * rem; x += blockDim.x) {
+                    const int i = c + 1 + x / rem, jj = c + 1 + x % rem;
+                    if (jj <= i) Gs[i * s + jj] -= Gs[i * s + c] * Gs[jj * s + c];
+                }
+                __syncthreads();
+            }
+            if (!s_bad) break;
+            ridge = 1e-10 * s_dmax;           // regularised fallback, flagged
+            __syncthreads();
+        }
+        const bool singular = s > 0 && ridge > 0.0;
+        // forward / back substitution by warp 0
+        if (warp == 0 && s > 0) {
+            for (int i = 0; i < s; ++i) {
+                double acc = 0.0;
+                for (int c = lane; c < i; c += 32) acc += Gs[i * s + c] * bs[c];
+                acc = warp_sum(acc);
+                if (lane == 0) bs[i] = (bs[i] - acc) / Gs[i * s + i];
+                __syncwarp();
+            }
+            for (int i = s - 1; i >= 0; --i) {
+                double acc = 0.0;
+                for (int c = i + 1 + lane; c < s; c += 32) acc += Gs[c * s + i] * bs[c];
+                acc = warp_sum(acc);
+                if (lane == 0) bs[i] = (bs[i] - acc) / Gs[i * s + i];
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (a.jstar) {
+            double* out = a.chosen + ((size_t)k * a.r + e) * a.p;
+            for (int x = threadIdx.x; x < s; x += blockDim.x) out[idx[x]] = bs[x];
+        } else {
+            // held-out loss via the evaluation moments
+            const double* Gek = a.Ge + (size_t)k * a.p * a.p;
+            const double* Bek = a.Be + (size_t)k * a.p * a.r;
+            double part = 0.0;
+            for (int x = threadIdx.x; x < s * s; x += blockDim.x) {
+                const int r0 = x / s, c0 = x % s;
+                part += bs[r0] * Gek[(size_t)idx[r0] * a.p + idx[c0]] * bs[c0];
+            }
+            for (int x = threadIdx.x; x < s; x += blockDim.x)
+                part -= 2.0 * bs[x] * Bek[(size_t)idx[x] * a.r + e];
+            part = warp_sum(part);
+            __syncthreads();
+            if (lane == 0) red[warp] = part;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < 8; ++w) tot += red[w];
+                const int64_t o = ((int64_t)k * a.q + j) * a.r + e;
+                a.losses[o] = a.yye[(size_t)k * a.r + e] + tot;
+                if (a.singular) a.singular[o] = singular ? 1 : 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_support_max(const uint64_t* fam, int64_t count, int W, int32_t* out)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int w = 0; w < W; ++w) c += __popcll(fam[t * W + w]);
+        atomicMax(out, c);
+    }
+}
+
+__global__ void k_argmin(const double* losses, int32_t q, int64_t r, int32_t* jstar)
+{
+    const int k = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    int best = 0;
+    double bv = 0.0;
+    for (int j = 0; j < q; ++j) {
+        double s = 0.0;
+        for (int64_t e = 0; e < r; ++e) s += losses[((int64_t)k * q + j) * r + e];
+        if (j == 0 || s < bv) { bv = s; best = j; }
+    }
+    jstar[k] = best;
+}
+
+__global__ void k_bagging(const double* chosen, int32_t B2, int64_t count, int32_t mode, double* out)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < count;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (mode == UOI_BAG_MEAN) {
+            double s = 0.0;
+            for (int k = 0; k < B2; ++k) s += chosen[(int64_t)k * count + c];
+            out[c] = s / (double)B2;
+        } else {
+            double v[128];
+            const int n = B2 < 128 ? B2 : 128;
+            for (int k = 0; k < n; ++k) {            // insertion sort
+                const double x = chosen[(int64_t)k * count + c];
+                int t = k;
+                while (t > 0 && v[t - 1] > x) { v[t] = v[t - 1]; --t; }
+                v[t] = x;
+            }
+            out[c] = (n & 1) ? v[n / 2] : 0.5 * (v[n / 2 - 1] + v[n / 2]);
+        }
+    }
+}
+
+__global__ void k_mask_tail(uint64_t* fam, int64_t count, int W, uint64_t mask)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x)
+        fam[t * W + (W - 1)] &= mask;
+}
+
+void run_ols(OlsArgs a, cudaStream_t s)
+{
+    // largest support decides shared vs global factor storage
+    DevBuf mx(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(mx.ptr, 0, sizeof(int32_t), s));
+    const int64_t fam_count = (int64_t)a.q * a.r;
+    k_support_max<<<(unsigned)std::min<int64_t>(ceil_div(fam_count, 256), 1024), 256, 0, s>>>(
+        a.family, fam_count, a.W, mx.as<int32_t>());
+    UOI_CHECK_LAUNCH();
+    int32_t smax = 0;
+    UOI_CUDA(cudaMemcpyAsync(&smax, mx.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    a.smax = std::max(1, (int)smax);
+    a.use_smem = a.smax <= OLS_SMEM_MAX;
+    size_t smem = sizeof(int) * ((a.p + 1) & ~1) + sizeof(double) * (a.smax + 1 + 32);
+    DevBuf scratch;
+    int grid = (int)std::min<int64_t>(a.solves, 152 * 8);
+    if (a.use_smem) {
+        smem += sizeof(double) * (size_t)a.smax * a.smax;
+    } else {
+        grid = (int)std::min<int64_t>(a.solves, 152 * 2);
+        scratch.alloc(sizeof(double) * (size_t)grid * a.smax * a.smax, s);
+        a.scratch = scratch.as<double>();
+    }
+    UOI_CUDA(cudaFuncSetAttribute(k_ols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (a.solves > 0) {
+        k_ols<<<grid, 256, smem, s>>>(a);
+        UOI_CHECK_LAUNCH();
+    }
+    count_launch(2);
+}
+
+}  // namespace
+
+void family_init(uint64_t* fam, int64_t words, cudaStream_t s)
+{
+    UOI_CUDA(cudaMemsetAsync(fam, 0xFF, sizeof(uint64_t) * (size_t)words, s));
+}
+
+void family_mask_tail(uint64_t* fam, int64_t count, int64_t p, cudaStream_t s)
+{
+    if ((p & 63) == 0) return;
+    const int W = (int)((p + 63) / 64);
+    k_mask_tail<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 1024), 256, 0, s>>>(
+        fam, count, W, (1ull << (p & 63)) - 1ull);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void ols_losses(const double* Gt, const double* Bt, const double* Ge, const double* Be,
+                const double* yye, const uint64_t* family, int64_t p, int64_t r, int32_t q,
+                int32_t B2, double* losses, int32_t* singular, cudaStream_t s)
+{
+    OlsArgs a{};
+    a.Gt = Gt; a.Bt = Bt; a.Ge = Ge; a.Be = Be; a.yye = yye; a.family = family;
+    a.p = p; a.r = r; a.q = q; a.B2 = B2; a.W = (int32_t)((p + 63) / 64);
+    a.losses = losses; a.singular = singular;
+    a.solves = (int64_t)B2 * q * r;
+    run_ols(a, s);
+}
+
+void loss_argmin(const double* losses, int32_t B2, int32_t q, int64_t r, int32_t* jstar,
+                 cudaStream_t s)
+{
+    k_argmin<<<B2, 32, 0, s>>>(losses, q, r, jstar);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, const int32_t* jstar,
+                int64_t p, int64_t r, int32_t q, int32_t B2, double* chosen, cudaStream_t s)
+{
+    UOI_CUDA(cudaMemsetAsync(chosen, 0, sizeof(double) * (size_t)(B2 * r * p), s));
+    OlsArgs a{};
+    a.Gt = Gt; a.Bt = Bt; a.family = family;
+    a.p = p; a.r = r; a.q = q; a.B2 = B2; a.W = (int32_t)((p + 63) / 64);
+    a.jstar = jstar; a.chosen = chosen;
+    a.solves = (int64_t)B2 * r;
+    run_ols(a, s);
+}
+
+void bagging(const double* chosen, int32_t B2, int64_t count, int32_t mode, double* out,
+             cudaStream_t s)
+{
+    k_bagging<<<(unsigned)std::min<int64_t>(ceil_div(count, 128), 4096), 128, 0, s>>>(
+        chosen, B2, count, mode, out);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+}  // namespace uoi

@@ -1,0 +1,332 @@
+// factor.cu -- G3: batched FP64 Cholesky of A_k = G_k/n_k + rho I, inverse and RHS.
+//
+// The ADMM x-update of Eq. 5, x = (G/n_k + rho I)^{-1} (b/n_k + rho (z - u)),
+// has a fixed matrix per bootstrap.  It is factored once (the paper's
+// "triangular solve ... for matrix decomposition", Sec. IV-A-1) and turned
+// into an explicit inverse M_k so that every iteration is one product
+// x = c_k + rho M_k (z - u) with c_k = M_k b_k / n_k.  A_k is symmetric
+// positive definite for rho > 0 and well conditioned, so the explicit
+// inverse loses nothing measurable.
+//
+// Right-looking blocked Cholesky (panel factor, panel solve, trailing update),
+// blocked triangular inverse and the product M = L^{-T} L^{-1}.
+#include "kernels.h"
+#include "tile.cuh"
+
+namespace uoi {
+
+namespace {
+
+constexpr int NB = 32;    // Cholesky panel width
+constexpr int IB = 64;    // inverse block
+
+__global__ void k_build_system(const double* G, const double* nk, double rho, int64_t p,
+                               double* A)
+{
+    const int64_t k = blockIdx.y;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < p * p;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / p, j = t % p;
+        A[k * p * p + t] = G[k * p * p + t] / nk[k] + (i == j ? rho : 0.0);
+    }
+}
+
+// Factor the nb x nb diagonal block at j0 (one block per matrix).
+__global__ void k_chol_diag(double* A, int64_t p, int64_t j0, int nb, DevStatus* st)
+{
+    const int64_t k = blockIdx.x;
+    double* a = A + k * p * p;
+    __shared__ double D[NB][NB + 1];
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        D[i][j] = a[(j0 + i) * p + j0 + j];
+    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
+        if (threadIdx.x == 0) {
+            const double d = D[c][c];
+            if (!(d > 0.0)) { bad = 1; D[c][c] = 1.0; } else D[c][c] = sqrt(d);
+        }
+        __syncthreads();
+        const double lcc = D[c][c];
+        for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][c] /= lcc;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+            const int i = e / nb, j = e % nb;
+            if (j > c && i >= j) D[i][j] -= D[i][c] * D[j][c];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        a[(j0 + i) * p + j0 + j] = j <= i ? D[i][j] : 0.0;
+    }
+    if (threadIdx.x == 0 && bad) dev_fail(st, UOI_ERR_NOT_PD, (int)k);
+}
+
+// Rows below the diagonal block: L[i, j0:j0+nb] = A[i, j0:j0+nb] L_dd^{-T}.
+__global__ void k_chol_panel(double* A, int64_t p, int64_t j0, int nb)
+{
+    const int64_t k = blockIdx.y;
+    double* a = A + k * p * p;
+    __shared__ double D[NB][NB + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        D[i][j] = a[(j0 + i) * p + j0 + j];
+    }
+    __syncthreads();
+    const int64_t i = j0 + nb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= p) return;
+    double x[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) x[c] = c < nb ? a[i * p + j0 + c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+        if (c >= nb) break;
+        double v = x[c];
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+            if (s < c) v -= x[s] * D[c][s];
+        x[c] = v / D[c][c];
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+        if (c < nb) a[i * p + j0 + c] = x[c];
+}
+
+// Trailing update of the lower triangle: A[i][j] -= sum_s L[i][j0+s] L[j][j0+s].
+__global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t p, int64_t j0, int nb)
+{
+    const int64_t k = blockIdx.y;
+    double* a = A + k * p * p;
+    const int64_t base = j0 + nb;
+    int64_t ti, tj;
+    tri_index(blockIdx.x, ti, tj);
+    const int64_t i0 = base + ti * 64, jj0 = base + tj * 64;
+    double acc[4][4] = {};
+    auto fa = [&](int il, int64_t s) {
+        const int64_t i = i0 + il;
+        return i < p ? a[i * p + j0 + s] : 0.0;
+    };
+    auto fb = [&](int64_t s, int jl) {
+        const int64_t j = jj0 + jl;
+        return j < p ? a[j * p + j0 + s] : 0.0;
+    };
+    tile64_acc<double>(acc, fa, fb, 0, nb);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + ty + 16 * u;
+        if (i >= p) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t j = jj0 + tx + 16 * v;
+            if (j < p && j <= i) a[i * p + j] -= acc[u][v];
+        }
+    }
+}
+
+// Inverse of each IB x IB lower-triangular diagonal block, in T.  The block of
+// L is read from global memory (L2); the inverse is built in shared memory.
+template <typename T>
+__global__ void k_trinv_diag(const double* L, int64_t p, T* Linv)
+{
+    const int64_t k = blockIdx.y;
+    const int64_t b0 = (int64_t)blockIdx.x * IB;
+    const int nb = (int)(p - b0 < IB ? p - b0 : IB);
+    const double* l = L + k * p * p + b0 * p + b0;     // l[i * p + j] = L[b0+i][b0+j]
+    T* li = Linv + k * p * p;
+    __shared__ T R[IB][IB + 1];
+    const int j = threadIdx.x;                    // one column of the inverse per thread
+    if (j < nb) {
+        for (int i = 0; i < nb; ++i) {
+            T v;
+            if (i < j) v = T(0);
+            else if (i == j) v = T(1) / (T)l[j * p + j];
+            else {
+                T s = T(0);
+                for (int t = j; t < i; ++t) s = fma((T)l[i * p + t], R[t][j], s);
+                v = -s / (T)l[i * p + i];
+            }
+            R[i][j] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, c = e % nb;
+        li[(b0 + i) * p + b0 + c] = R[i][c];
+    }
+}
+
+// Block row I of L^{-1}: for J < I, Linv_IJ = -Linv_II * sum_{K=J}^{I-1} L_IK Linv_KJ.
+template <typename T>
+__global__ void __launch_bounds__(256) k_trinv_row(const double* L, int64_t p, int64_t I, T* Linv)
+{
+    const int64_t k = blockIdx.y;
+    const int64_t J = blockIdx.x;
+    const double* l = L + k * p * p;
+    T* li = Linv + k * p * p;
+    const int64_t i0 = I * IB, j0 = J * IB;
+    T acc[4][4] = {};
+    auto fa = [&](int il, int64_t s) {
+        const int64_t i = i0 + il;
+        return i < p ? (T)l[i * p + s] : T(0);
+    };
+    auto fb = [&](int64_t s, int jl) {
+        const int64_t jj = j0 + jl;
+        return (T)li[s * p + jj];
+    };
+    tile64_acc<T>(acc, fa, fb, j0, i0);              // T_IJ (64 x 64)
+    __shared__ T Tm[IB][IB + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Tm[ty + 16 * u][tx + 16 * v] = acc[u][v];
+    __syncthreads();
+    T acc2[4][4] = {};
+    auto ga = [&](int il, int64_t s) {
+        const int64_t i = i0 + il, c = i0 + s;
+        return (i < p && c < p && c <= i) ? li[i * p + c] : T(0);
+    };
+    auto gb = [&](int64_t s, int jl) { return Tm[s][jl]; };
+    tile64_acc<T>(acc2, ga, gb, 0, IB);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + ty + 16 * u;
+        if (i >= p) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t jj = j0 + tx + 16 * v;
+            li[i * p + jj] = -acc2[u][v];
+        }
+    }
+}
+
+// M = L^{-T} L^{-1}: M[i][j] = sum_{s >= max(i,j)} Linv[s][i] Linv[s][j], lower tiles + mirror.
+template <typename T>
+__global__ void __launch_bounds__(256) k_inverse_product(const T* Linv, int64_t p, T* M)
+{
+    const int64_t k = blockIdx.y;
+    const T* li = Linv + k * p * p;
+    T* mk = M + k * p * p;
+    int64_t ti, tj;
+    tri_index(blockIdx.x, ti, tj);
+    const int64_t i0 = ti * 64, j0 = tj * 64;
+    T acc[4][4] = {};
+    auto fa = [&](int il, int64_t s) {
+        const int64_t i = i0 + il;
+        return i < p ? li[s * p + i] : T(0);
+    };
+    auto fb = [&](int64_t s, int jl) {
+        const int64_t j = j0 + jl;
+        return j < p ? li[s * p + j] : T(0);
+    };
+    tile64_acc<T>(acc, fa, fb, i0, p);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + ty + 16 * u;
+        if (i >= p) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t j = j0 + tx + 16 * v;
+            if (j >= p || j > i) continue;
+            mk[i * p + j] = acc[u][v];
+            mk[j * p + i] = acc[u][v];
+        }
+    }
+}
+
+// c[k][e][i] = sum_j M[k][i][j] * (Bm[k][j][e] / nk[k]).
+template <typename T>
+__global__ void __launch_bounds__(256) k_rhs(const T* M, const double* Bm, const double* nk,
+                                             int64_t p, int64_t r, T* c)
+{
+    const int64_t k = blockIdx.y;
+    const int64_t tiles_e = (r + 63) / 64;
+    const int64_t i0 = (blockIdx.x / tiles_e) * 64, e0 = (blockIdx.x % tiles_e) * 64;
+    const T* mk = M + k * p * p;
+    const double* bk = Bm + k * p * r;
+    const double n_k = nk[k];
+    T acc[4][4] = {};
+    auto fa = [&](int il, int64_t j) {
+        const int64_t i = i0 + il;
+        return i < p ? mk[i * p + j] : T(0);
+    };
+    auto fb = [&](int64_t j, int el) {
+        const int64_t e = e0 + el;
+        return e < r ? (T)(bk[j * r + e] / n_k) : T(0);
+    };
+    tile64_acc<T>(acc, fa, fb, 0, p);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + ty + 16 * u;
+        if (i >= p) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t e = e0 + tx + 16 * v;
+            if (e < r) c[(k * r + e) * p + i] = acc[u][v];
+        }
+    }
+}
+
+}  // namespace
+
+void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
+                      double* A, DevStatus* status, cudaStream_t s)
+{
+    dim3 gb((unsigned)std::min<int64_t>(ceil_div(p * p, 256), 1024), (unsigned)B);
+    k_build_system<<<gb, 256, 0, s>>>(G, nk, rho, p, A);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    for (int64_t j0 = 0; j0 < p; j0 += NB) {
+        const int nb = (int)std::min<int64_t>(NB, p - j0);
+        k_chol_diag<<<B, 256, 0, s>>>(A, p, j0, nb, status);
+        UOI_CHECK_LAUNCH();
+        count_launch();
+        const int64_t rest = p - j0 - nb;
+        if (rest <= 0) break;
+        dim3 gp((unsigned)ceil_div(rest, 128), (unsigned)B);
+        k_chol_panel<<<gp, 128, 0, s>>>(A, p, j0, nb);
+        UOI_CHECK_LAUNCH();
+        const int64_t tt = ceil_div(rest, 64);
+        dim3 gu((unsigned)(tt * (tt + 1) / 2), (unsigned)B);
+        k_chol_update<<<gu, 256, 0, s>>>(A, p, j0, nb);
+        UOI_CHECK_LAUNCH();
+        count_launch(2);
+    }
+}
+
+template <typename T>
+void inverse_and_rhs(const double* L, const double* Bm, const double* nk, int64_t p, int64_t r,
+                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s)
+{
+    UOI_CUDA(cudaMemsetAsync(Linv, 0, sizeof(T) * (size_t)(p * p * B), s));
+    const int64_t nbk = ceil_div(p, IB);
+    k_trinv_diag<T><<<dim3((unsigned)nbk, (unsigned)B), IB, 0, s>>>(L, p, Linv);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    for (int64_t I = 1; I < nbk; ++I) {
+        k_trinv_row<T><<<dim3((unsigned)I, (unsigned)B), 256, 0, s>>>(L, p, I, Linv);
+        UOI_CHECK_LAUNCH();
+        count_launch();
+    }
+    const int64_t tt = ceil_div(p, 64);
+    k_inverse_product<T><<<dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)B), 256, 0, s>>>(Linv, p, M);
+    UOI_CHECK_LAUNCH();
+    const int64_t te = ceil_div(r, 64);
+    k_rhs<T><<<dim3((unsigned)(tt * te), (unsigned)B), 256, 0, s>>>(M, Bm, nk, p, r, c);
+    UOI_CHECK_LAUNCH();
+    count_launch(2);
+}
+
+template void inverse_and_rhs<double>(const double*, const double*, const double*, int64_t,
+                                      int64_t, int32_t, double*, double*, double*, cudaStream_t);
+template void inverse_and_rhs<float>(const double*, const double*, const double*, int64_t,
+                                     int64_t, int32_t, float*, float*, float*, cudaStream_t);
+
+}  // namespace uoi

@@ -1,0 +1,199 @@
+// gram.cu -- G1 in FP64 on CUDA cores: weighted Gram and moments, lambda grid.
+//
+// For bootstrap k the LASSO of Eq. 2 on T^k only needs G_k = X^T W_k X and
+// B_k = X^T W_k Y (W_k = diag of the bootstrap multiplicities): the ADMM
+// x-update of Eq. 5 then never touches the n rows again.  This is the plain
+// FP64 form; the tensor-core form lives in gram_tc.cu.
+#include "kernels.h"
+
+namespace uoi {
+
+namespace {
+
+constexpr int GT = 64;   // output tile
+constexpr int GK = 16;   // rows per K step
+
+// Output column j of C = X^T W [X | Y]: j < p -> X[:, j], else Y[:, j - p].
+__device__ __forceinline__ double zcol(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                                       int64_t t, int64_t j, int64_t p)
+{
+    return j < p ? X[t * ldx + j] : Y[t * ldy + (j - p)];
+}
+
+// grid: (tiles, B).  Tile list: lower-triangular tiles of G (tj <= ti) and every
+// tile of the B block; b_only restricts to the B block.  256 threads, 4x4 each.
+__global__ void __launch_bounds__(256)
+k_moments_fp64(const double* __restrict__ X, int64_t ldx, const double* __restrict__ Y,
+               int64_t ldy, int64_t m, int64_t p, int64_t r, const uint32_t* __restrict__ w,
+               const uint8_t* __restrict__ mask, double* __restrict__ G, double* __restrict__ Bm,
+               int b_only)
+{
+    const int64_t k = blockIdx.y;
+    const int64_t tp = (p + GT - 1) / GT;          // row tiles (i over features)
+    const int64_t tb = (r + GT - 1) / GT;          // column tiles of the B block
+    int64_t t = blockIdx.x;
+    int64_t ti, j0, jend;
+    bool gpart;
+    const int64_t ng = b_only ? 0 : tp * (tp + 1) / 2;
+    if (t < ng) {                                   // triangular index -> (ti, tj)
+        ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while (ti * (ti + 1) / 2 > t) --ti;
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        const int64_t tj = t - ti * (ti + 1) / 2;
+        j0 = tj * GT;
+        jend = p;
+        gpart = true;
+    } else {
+        t -= ng;
+        ti = t / tb;
+        j0 = p + (t % tb) * GT;
+        jend = p + r;
+        gpart = false;
+    }
+    const int64_t i0 = ti * GT;
+    const uint32_t* wk = w ? w + k * m : nullptr;
+    const uint8_t* mk = mask ? mask + k * m : nullptr;
+
+    __shared__ double As[GK][GT + 1];
+    __shared__ double Bs[GK][GT + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int64_t t0 = 0; t0 < m; t0 += GK) {
+        for (int e = threadIdx.x; e < GK * GT; e += 256) {
+            const int rr = e / GT, cc = e % GT;
+            const int64_t row = t0 + rr;
+            double wt = 0.0, a = 0.0, b = 0.0;
+            if (row < m) {
+                wt = wk ? (double)wk[row] : (mk ? (double)mk[row] : 1.0);
+                if (i0 + cc < p) a = X[row * ldx + i0 + cc];
+                if (j0 + cc < jend) b = zcol(X, ldx, Y, ldy, row, j0 + cc, p);
+            }
+            As[rr][cc] = wt * a;
+            Bs[rr][cc] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty + 16 * u]; b[u] = Bs[kk][tx + 16 * u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + ty + 16 * u;
+        if (i >= p) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t j = j0 + tx + 16 * v;
+            if (j >= jend) continue;
+            if (gpart && j > i) continue;    // lower triangle; the mirror fills the rest
+            if (gpart) {
+                G[k * p * p + i * p + j] = acc[u][v];
+                if (i != j) G[k * p * p + j * p + i] = acc[u][v];   // mirror (j < i tiles only)
+            } else {
+                Bm[k * p * r + i * r + (j - p)] = acc[u][v];
+            }
+        }
+    }
+}
+
+__global__ void k_masked_sumsq(const double* Y, int64_t ldy, int64_t m, int64_t r,
+                               const uint8_t* mask, double* yy)
+{
+    const int64_t k = blockIdx.y;
+    const int64_t e = blockIdx.x;
+    double s = 0.0;
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x)
+        if (mask[k * m + t]) { const double v = Y[t * ldy + e]; s = fma(v, v, s); }
+    s = warp_sum(s);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += part[i];
+        yy[k * r + e] = tot;
+    }
+}
+
+// lambda_max = max |X^T Y| / m, lambda_j = lmax * ratio^(j/(q-1)) (descending).
+__global__ void k_lambda_grid(const double* XtY, int64_t count, int64_t m, int32_t q,
+                              double ratio, double* lambdas)
+{
+    double best = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) best = fmax(best, fabs(XtY[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmax(b, part[i]);
+        part[0] = b / (double)m;
+    }
+    __syncthreads();
+    const double lmax = part[0];
+    for (int j = threadIdx.x; j < q; j += blockDim.x)
+        lambdas[j] = q > 1 ? lmax * pow(ratio, (double)j / (double)(q - 1)) : lmax;
+}
+
+__global__ void k_check_finite(const double* X, int64_t ldx, int64_t m, int64_t cols,
+                               int32_t* flag)
+{
+    const int64_t total = m * cols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / cols, col = t % cols;
+        if (!isfinite(X[row * ldx + col])) { atomicExch(flag, 1); return; }
+    }
+}
+
+}  // namespace
+
+void moments_fp64(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
+                  int64_t p, int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B,
+                  double* G, double* Bm, int b_only, cudaStream_t s)
+{
+    const int64_t tp = (p + GT - 1) / GT, tb = (r + GT - 1) / GT;
+    const int64_t tiles = (b_only ? 0 : tp * (tp + 1) / 2) + tp * tb;
+    dim3 grid((unsigned)tiles, (unsigned)B);
+    k_moments_fp64<<<grid, 256, 0, s>>>(X, ldx, Y, ldy, m, p, r, w, mask, G, Bm, b_only);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void masked_sumsq(const double* Y, int64_t ldy, int64_t m, int64_t r, const uint8_t* mask,
+                  int32_t B, double* yy, cudaStream_t s)
+{
+    dim3 grid((unsigned)r, (unsigned)B);
+    k_masked_sumsq<<<grid, 256, 0, s>>>(Y, ldy, m, r, mask, yy);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void lambda_grid(const double* XtY, int64_t count, int64_t m, int32_t q, double ratio,
+                 double* lambdas, cudaStream_t s)
+{
+    k_lambda_grid<<<1, 1024, 0, s>>>(XtY, count, m, q, ratio, lambdas);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void check_finite(const double* X, int64_t ldx, int64_t m, int64_t cols, int32_t* flag,
+                  cudaStream_t s)
+{
+    int64_t g = (m * cols + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    k_check_finite<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(X, ldx, m, cols, flag);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+}  // namespace uoi

@@ -1,0 +1,122 @@
+// kernels.h -- host launchers of the GB300 UoI kernels (internal interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace uoi {
+
+// ---- memory ------------------------------------------------------------------
+// Stream-ordered device buffer from the device's default memory pool.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf() = default;
+    DevBuf(size_t n, cudaStream_t s) { alloc(n, s); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+    DevBuf& operator=(DevBuf&& o) noexcept
+    {
+        release();
+        ptr = o.ptr; bytes = o.bytes; stream = o.stream;
+        o.ptr = nullptr; o.bytes = 0;
+        return *this;
+    }
+    void alloc(size_t n, cudaStream_t s);
+    void release();
+    ~DevBuf() { release(); }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(ptr); }
+};
+
+// ---- G0: bootstrap indices (bootstrap.cu) -----------------------------------
+// w[k*m + row] = multiplicity of the row in selection bootstrap k, k < B.
+void selection_weights(int64_t m, int64_t block_len, PhiloxKey key, int32_t B, uint32_t* w,
+                       cudaStream_t s);
+// Training multiplicities and evaluation masks of estimation bootstraps k < B.
+void estimation_weights(int64_t m, int64_t block_len, double train_frac, int split_fixed,
+                        PhiloxKey key, int32_t B, uint32_t* w_train, uint8_t* eval,
+                        cudaStream_t s);
+// nk[k] = sum_t w[k*m + t] (as double), and eval counts when w is a mask.
+void weight_sums(const uint32_t* w, const uint8_t* mask, int64_t m, int32_t B, double* nk,
+                 cudaStream_t s);
+
+// ---- G1: moments (gram.cu) ------------------------------------------------------
+// For every k < B: G_k = X^T diag(w_k) X (p x p, full) and Bm_k = X^T diag(w_k) Y
+// (p x r).  Exactly one of w (counts) and mask (0/1) may be non-null; both null
+// means unweighted.  b_only = 1 skips G.  FP64 CUDA-core form.
+void moments_fp64(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
+                  int64_t p, int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B,
+                  double* G, double* Bm, int b_only, cudaStream_t s);
+// yy[k*r + e] = sum_t mask_k[t] Y[t,e]^2.
+void masked_sumsq(const double* Y, int64_t ldy, int64_t m, int64_t r, const uint8_t* mask,
+                  int32_t B, double* yy, cudaStream_t s);
+// lambda_max = max |Bm| / m, then the descending log grid (Eq. 2 scaling).
+void lambda_grid(const double* XtY, int64_t count, int64_t m, int32_t q, double ratio,
+                 double* lambdas, cudaStream_t s);
+// Device check: every value finite; flag[0] = 1 on the first non-finite.
+void check_finite(const double* X, int64_t ldx, int64_t m, int64_t cols, int32_t* flag,
+                  cudaStream_t s);
+
+// Mixed form: split-bf16 tensor-core Gram (gram_tc.cu).
+bool gram_tc_available();
+void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
+                int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
+                double* Bm, cudaStream_t s);
+
+// ---- G3: factor (factor.cu) -------------------------------------------------------
+// A_k = G_k / nk[k] + rho I, lower Cholesky in place (FP64).  status->code set to
+// UOI_ERR_NOT_PD (where = k) on a non-positive pivot.
+void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
+                      double* A, DevStatus* status, cudaStream_t s);
+// M_k = A_k^{-1} from the factor in A (T = double or float), then
+// c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].
+template <typename T>
+void inverse_and_rhs(const double* L, const double* Bm, const double* nk, int64_t p, int64_t r,
+                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s);
+
+// ---- G4: ADMM (admm.cu) -------------------------------------------------------------
+template <typename T>
+struct AdmmProblem {
+    int32_t G = 0;            // groups (bootstraps) sharing p
+    int64_t p = 0, r = 0;     // features, response columns per group
+    int32_t q = 0;            // lambdas
+    const T* M = nullptr;     // G x p x p   (A_g^{-1}, symmetric)
+    const T* c = nullptr;     // G x r x p   (A_g^{-1} b_ge / n_g)
+    const double* lambdas = nullptr;   // q (device)
+    double rho = 1.0, abs_tol = 1e-6, rel_tol = 1e-6;
+    int32_t max_iter = 1000;
+    int32_t warm = 1;         // 0 cold, 1 path
+    // outputs, columns indexed ((g*q + j)*r + e)
+    double* beta = nullptr;   // G x q x r x p (nullable)
+    int32_t* iters = nullptr; // G x q x r     (nullable)
+    uint8_t* conv = nullptr;  // G x q x r     (nullable)
+    uint64_t* family = nullptr;   // q x r x W, AND of the supports (nullable, preset to ~0)
+    int32_t family_offset = 0;    // not used (single problem)
+};
+template <typename T>
+void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
+
+// ---- G5/G6/G7: supports, OLS, loss, bagging (estimate.cu) -----------------------------
+void family_init(uint64_t* fam, int64_t words, cudaStream_t s);
+void family_mask_tail(uint64_t* fam, int64_t count, int64_t p, cudaStream_t s);
+// losses[(k*q + j)*r + e] = held-out squared error sum of the OLS fit on support
+// S_{j,e} from training moments (Gt, Bt) and evaluation moments (Ge, Be, yye);
+// singular[...] = 1 where the fallback ran.
+void ols_losses(const double* Gt, const double* Bt, const double* Ge, const double* Be,
+                const double* yye, const uint64_t* family, int64_t p, int64_t r, int32_t q,
+                int32_t B2, double* losses, int32_t* singular, cudaStream_t s);
+// jstar[k] = argmin_j sum_e losses[k][j][e] (ties -> smallest j).
+void loss_argmin(const double* losses, int32_t B2, int32_t q, int64_t r, int32_t* jstar,
+                 cudaStream_t s);
+// chosen[k][e][:] = OLS on S_{jstar[k], e} from (Gt_k, Bt_k), zero-filled.
+void ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, const int32_t* jstar,
+                int64_t p, int64_t r, int32_t q, int32_t B2, double* chosen, cudaStream_t s);
+// beta_out[e][i] = median (bagging 0) or mean (1) over k of chosen[k][e][i].
+void bagging(const double* chosen, int32_t B2, int64_t count, int32_t mode, double* out,
+             cudaStream_t s);
+
+}  // namespace uoi

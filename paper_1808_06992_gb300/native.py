@@ -1,0 +1,255 @@
+"""Thin ctypes binding of the C ABI in include/uoi.h (argument marshalling only).
+
+Every function here forwards pointers and sizes to libuoi_gb300.so; all the
+arithmetic runs in the CUDA kernels.  Arrays may be numpy arrays (host memory)
+or torch CUDA tensors (device memory); outputs are returned in the same kind as
+the main input.  Importing this module raises if the library is missing: there
+is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, OK_WITH_WARNINGS = 0, 1
+ERR_INVALID_ARG, ERR_NONFINITE, ERR_NOT_PD, ERR_CUDA = -1, -2, -3, -4
+ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = -5, -6, -8
+BAG_MEDIAN, BAG_MEAN = 0, 1
+SPLIT_PER_BOOTSTRAP, SPLIT_FIXED = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+WARM_NONE, WARM_PATH, WARM_LEARNED = 0, 1, 2
+
+
+class UoiParams(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("B1", C.c_int32), ("B2", C.c_int32), ("q", C.c_int32),
+        ("lambdas", C.c_void_p), ("lambda_min_ratio", C.c_double), ("rho", C.c_double),
+        ("abs_tol", C.c_double), ("rel_tol", C.c_double), ("max_iter", C.c_int32),
+        ("train_frac", C.c_double), ("seed", C.c_uint64), ("problem_id", C.c_uint64),
+        ("block_len", C.c_int64), ("bagging", C.c_int32), ("split_mode", C.c_int32),
+        ("precision", C.c_int32), ("warm_start", C.c_int32), ("mlp_weights_path", C.c_char_p),
+        ("stream", C.c_void_p),
+    ]
+
+
+class UoiDiag(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("ms_total", C.c_float), ("ms_bootstrap", C.c_float),
+        ("ms_gram", C.c_float), ("ms_factor", C.c_float), ("ms_admm", C.c_float),
+        ("ms_support", C.c_float), ("ms_estimation", C.c_float),
+        ("admm_columns", C.c_int64), ("admm_nonconverged", C.c_int64),
+        ("admm_iterations", C.c_int64), ("admm_max_iterations", C.c_int32),
+        ("ols_singular", C.c_int64), ("gpu_launches", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "struct_size"}
+
+
+class UoiTrace(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in (
+        "lambdas", "sel_weights", "est_weights", "est_eval", "sel_beta", "sel_iters", "sel_conv",
+        "family", "est_loss", "est_jstar", "est_beta", "est_singular")]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building if needed) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libuoi_gb300.so is missing; the CUDA path cannot run")
+        L = C.CDLL(path)
+        vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        L.uoi_params_default.argtypes = [C.POINTER(UoiParams)]
+        L.uoi_lasso_fit.argtypes = [vp, vp, i64, i64, C.POINTER(UoiParams), vp, vp, C.POINTER(UoiDiag)]
+        L.uoi_var_fit.argtypes = [vp, i64, i64, i32, C.POINTER(UoiParams), vp, vp, C.POINTER(UoiDiag)]
+        L.uoi_fit_traced.argtypes = [vp, i64, vp, i64, i64, i64, i64, C.POINTER(UoiParams), vp,
+                                     C.POINTER(UoiTrace), C.POINTER(UoiDiag)]
+        L.lasso_admm_batch.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d, i32, i32,
+                                       i32, vp, vp, vp, vp]
+        L.uoi_status_string.argtypes = [C.c_int]
+        L.uoi_status_string.restype = C.c_char_p
+        L.uoi_get_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
+        L.uoi_shutdown.argtypes = []
+        _lib = L
+    return _lib
+
+
+EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_var_fit", "uoi_fit_traced",
+            "lasso_admm_batch", "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
+
+
+class UoiError(RuntimeError):
+    def __init__(self, status, detail):
+        super().__init__(f"status {status}: {detail}")
+        self.status = status
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    lib().uoi_get_last_error_detail(buf, 1024)
+    return buf.value.decode()
+
+
+def _check(st):
+    if st < 0:
+        raise UoiError(st, last_error())
+    return st
+
+
+# ----------------------------------------------------------------------------
+# array helpers: numpy (host) or torch CUDA tensors (device)
+# ----------------------------------------------------------------------------
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _prep(a, dtype):
+    if _is_torch(a):
+        import torch
+        tmap = {np.float64: torch.float64, np.uint32: torch.int32, np.uint8: torch.uint8}
+        t = a.contiguous()
+        if dtype is np.uint32:
+            return t.to(torch.int32) if t.dtype != torch.int32 else t
+        return t.to(tmap[dtype])
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _empty(like, shape, dtype):
+    if _is_torch(like):
+        import torch
+        tmap = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8,
+                np.uint32: torch.int32, np.uint64: torch.int64}
+        return torch.empty(shape, dtype=tmap[dtype], device=like.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def make_params(B1=20, B2=20, q=16, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol=1e-6,
+                rel_tol=1e-6, max_iter=1000, train_frac=0.8, seed=0, problem_id=0, block_len=0,
+                bagging=BAG_MEDIAN, split_mode=SPLIT_PER_BOOTSTRAP, precision=PREC_FP64,
+                warm_start=WARM_PATH, stream=None):
+    prm = UoiParams()
+    lib().uoi_params_default(C.byref(prm))
+    prm.B1, prm.B2, prm.q = B1, B2, q
+    keep = None
+    if lambdas is not None:
+        keep = _prep(lambdas, np.float64)
+        prm.lambdas = _ptr(keep)
+    prm.lambda_min_ratio = lambda_min_ratio
+    prm.rho, prm.abs_tol, prm.rel_tol, prm.max_iter = rho, abs_tol, rel_tol, max_iter
+    prm.train_frac, prm.seed, prm.problem_id = train_frac, seed, problem_id
+    prm.block_len, prm.bagging, prm.split_mode = block_len, bagging, split_mode
+    prm.precision, prm.warm_start = precision, warm_start
+    prm.stream = stream
+    return prm, keep
+
+
+def uoi_fit_traced(X, Y, trace=True, **kw):
+    """General fit of Y (m x r) on X (m x p); returns dict(beta, status, diag, trace...)."""
+    X = _prep(X, np.float64)
+    Y = _prep(Y, np.float64)
+    if Y.ndim == 1:
+        Y = Y.reshape(-1, 1)
+    m, p = X.shape
+    r = Y.shape[1]
+    prm, keep = make_params(**kw)
+    B1, B2, q = prm.B1, prm.B2, prm.q
+    W = (p + 63) // 64
+    beta = _empty(X, (r, p), np.float64)
+    out = {}
+    tr = None
+    if trace:
+        shapes = dict(lambdas=((q,), np.float64), sel_weights=((B1, m), np.uint32),
+                      est_weights=((B2, m), np.uint32), est_eval=((B2, m), np.uint8),
+                      sel_beta=((B1, q, r, p), np.float64), sel_iters=((B1, q, r), np.int32),
+                      sel_conv=((B1, q, r), np.uint8), family=((q, r, W), np.uint64),
+                      est_loss=((B2, q, r), np.float64), est_jstar=((B2,), np.int32),
+                      est_beta=((B2, r, p), np.float64), est_singular=((B2, q, r), np.int32))
+        tr = UoiTrace()
+        for name, (shape, dt) in shapes.items():
+            out[name] = _empty(X, shape, dt)
+            setattr(tr, name, _ptr(out[name]))
+    diag = UoiDiag()
+    diag.struct_size = C.sizeof(UoiDiag)
+    st = lib().uoi_fit_traced(_ptr(X), p, _ptr(Y), r, m, p, r, C.byref(prm), _ptr(beta),
+                              C.byref(tr) if tr is not None else None, C.byref(diag))
+    del keep
+    _check(st)
+    out.update(beta=beta, status=st, diag=diag.as_dict())
+    return out
+
+
+def uoi_lasso_fit(X, y, family=False, **kw):
+    X = _prep(X, np.float64)
+    y = _prep(y, np.float64)
+    n, p = X.shape
+    prm, keep = make_params(**kw)
+    beta = _empty(X, (p,), np.float64)
+    fam = _empty(X, (prm.q, (p + 63) // 64), np.uint64) if family else None
+    diag = UoiDiag()
+    diag.struct_size = C.sizeof(UoiDiag)
+    st = lib().uoi_lasso_fit(_ptr(X), _ptr(y), n, p, C.byref(prm), _ptr(beta), _ptr(fam),
+                             C.byref(diag))
+    del keep
+    _check(st)
+    return dict(beta=beta, family=fam, status=st, diag=diag.as_dict())
+
+
+def uoi_var_fit(series, order=1, **kw):
+    S = _prep(series, np.float64)
+    N, p = S.shape
+    prm, keep = make_params(**kw)
+    A = _empty(S, (order, p, p), np.float64)
+    mu = _empty(S, (p,), np.float64)
+    diag = UoiDiag()
+    diag.struct_size = C.sizeof(UoiDiag)
+    st = lib().uoi_var_fit(_ptr(S), N, p, order, C.byref(prm), _ptr(A), _ptr(mu), C.byref(diag))
+    del keep
+    _check(st)
+    return dict(A=A, mu=mu, status=st, diag=diag.as_dict())
+
+
+def lasso_admm_batch(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6, max_iter=1000,
+                     precision=PREC_FP64, warm_start=WARM_PATH, stream=None):
+    X = _prep(X, np.float64)
+    Y = _prep(Y, np.float64)
+    if Y.ndim == 1:
+        Y = Y.reshape(-1, 1)
+    n, p = X.shape
+    r = Y.shape[1]
+    lam = _prep(lambdas, np.float64)
+    q = lam.shape[0]
+    if weights is None:
+        B, w = 1, None
+    else:
+        w = _prep(weights, np.uint32)
+        w = w.reshape(-1, n)
+        B = w.shape[0]
+    beta = _empty(X, (B, q, r, p), np.float64)
+    iters = _empty(X, (B, q, r), np.int32)
+    conv = _empty(X, (B, q, r), np.uint8)
+    st = lib().lasso_admm_batch(_ptr(X), _ptr(Y), n, p, r, _ptr(w), B, _ptr(lam), q, rho, abs_tol,
+                                rel_tol, max_iter, precision, warm_start, _ptr(beta), _ptr(iters),
+                                _ptr(conv), stream)
+    _check(st)
+    return dict(beta=beta, iters=iters, conv=conv, status=st)
+
+
+def shutdown():
+    lib().uoi_shutdown()
