@@ -153,6 +153,17 @@ int lasso_admm_batch(const double* X, const double* Y, int64_t n, int64_t p, int
                      int32_t precision, int32_t warm_start, double* beta_out,
                      int32_t* iters_out, uint8_t* converged_out, void* stream);
 
+/* Weighted moments of the selection step (G1; Alg. 1 "Compute LASSO estimate
+ * ... from T^k" only needs these): for every k < B,
+ *   G_out[k] = X^T diag(w_k) X   (p x p),   B_out[k] = X^T diag(w_k) Y   (p x r)
+ * with X: n x p, Y: n x r, weights: B x n bootstrap multiplicities (not NULL).
+ * precision UOI_PREC_FP64: FP64 CUDA cores.  UOI_PREC_MIXED: split-bf16 tensor
+ * cores (tcgen05) with FP32 accumulation per 4096 sample rows and FP64 sums,
+ * relative error about 1e-6 of the largest diagonal entry. */
+int uoi_weighted_moments(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
+                         const uint32_t* weights, int32_t B, int32_t precision,
+                         double* G_out, double* B_out, void* stream);
+
 /* Text of a status code (static storage). */
 const char* uoi_status_string(int status);
 

@@ -175,7 +175,7 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                     int64_t m, int64_t p, int64_t r, const uint32_t* w, int32_t B,
                     const double* lam, int32_t q, double rho, double abs_tol, double rel_tol,
                     int32_t max_iter, int32_t warm, double* beta, int32_t* iters, uint8_t* conv,
-                    uint64_t* family, cudaStream_t s, StageTimer* tm, float* ms)
+                    uint64_t* family, cudaStream_t s, StageTimer* tm, int* marks)
 {
     int t0 = tm ? tm->mark() : 0;
     DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
@@ -206,7 +206,7 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     P.beta = beta; P.iters = iters; P.conv = conv; P.family = family;
     admm_solve<T>(P, s);
     int t3 = tm ? tm->mark() : 0;
-    if (tm && ms) { ms[0] += tm->ms(t0, t1); ms[1] += tm->ms(t1, t2); ms[2] += tm->ms(t2, t3); }
+    if (marks) { marks[0] = t0; marks[1] = t1; marks[2] = t2; marks[3] = t3; }
 }
 
 struct IterStats { int64_t cols = 0, noncon = 0, iters = 0; int32_t maxit = 0; };
@@ -291,17 +291,17 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     DevBuf iters_b(sizeof(int32_t) * ncol, s), conv_b(ncol, s);
     DevBuf fam(sizeof(uint64_t) * (size_t)(q * r * W), s);
     family_init(fam.as<uint64_t>(), q * r * W, s);
-    float stage_ms[3] = { 0.f, 0.f, 0.f };
+    int marks[4] = { 0, 0, 0, 0 };
     if (mixed)
         selection_admm<float>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                               lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                               prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, stage_ms);
+                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks);
     else
         selection_admm<double>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                                lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                                prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, stage_ms);
+                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks);
     family_mask_tail(fam.as<uint64_t>(), q * r, p, s);
     const int t_sel2 = tm.mark();
 
@@ -366,9 +366,9 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     if (diag) {
         diag->ms_total = tm.ms(tstart, t_end);
         diag->ms_bootstrap = tm.ms(t_sel0, t_sel1);
-        diag->ms_gram = stage_ms[0];
-        diag->ms_factor = stage_ms[1];
-        diag->ms_admm = stage_ms[2];
+        diag->ms_gram = tm.ms(marks[0], marks[1]);
+        diag->ms_factor = tm.ms(marks[1], marks[2]);
+        diag->ms_admm = tm.ms(marks[2], marks[3]);
         diag->ms_support = 0.f;
         diag->ms_estimation = tm.ms(t_sel2, t_end);
         (void)t_est1;
@@ -513,6 +513,35 @@ int lasso_admm_batch(const double* X, const double* Y, int64_t n, int64_t p, int
         UOI_CUDA(cudaStreamSynchronize(s));
         IterStats its = iteration_stats(it_d, cv_d, ncol, s);
         return its.noncon > 0 ? UOI_OK_WITH_WARNINGS : UOI_OK;
+    });
+}
+
+int uoi_weighted_moments(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
+                         const uint32_t* weights, int32_t B, int32_t precision, double* G_out,
+                         double* B_out, void* stream)
+{
+    return guarded([&] {
+        if (!X || !Y || !weights || !G_out || !B_out)
+            throw Error(UOI_ERR_INVALID_ARG, "NULL pointer");
+        if (n <= 0 || p <= 0 || r <= 0 || B <= 0) throw Error(UOI_ERR_INVALID_ARG, "sizes must be positive");
+        if (precision != UOI_PREC_FP64 && precision != UOI_PREC_MIXED)
+            throw Error(UOI_ERR_INVALID_ARG, "unknown precision");
+        if (precision == UOI_PREC_MIXED && !gram_tc_available())
+            throw Error(UOI_ERR_UNSUPPORTED, "tensor-core Gram needs an sm_103 device");
+        ensure_pool();
+        cudaStream_t s = (cudaStream_t)stream;
+        DevBuf hx, hy, hw;
+        const double* Xd = dev_in(X, (size_t)(n * p), hx, s);
+        const double* Yd = dev_in(Y, (size_t)(n * r), hy, s);
+        const uint32_t* wd = dev_in(weights, (size_t)(B * n), hw, s);
+        DevOut<double> go, bo;
+        go.init(G_out, (size_t)(B * p * p), s);
+        bo.init(B_out, (size_t)(B * p * r), s);
+        moments(precision, Xd, p, Yd, r, n, p, r, wd, nullptr, B, go.dev, bo.dev, s);
+        go.finish(s);
+        bo.finish(s);
+        UOI_CUDA(cudaStreamSynchronize(s));
+        return UOI_OK;
     });
 }
 

@@ -1,15 +1,573 @@
-// gram_tc.cu -- G1 on tcgen05 tensor cores (mixed form).  Placeholder until the
-// split-bf16 kernel lands: reports unavailable, so the FP64 kernel is used.
+// gram_tc.cu -- G1 on the 5th-generation tensor cores (tcgen05, TMA, TMEM): the
+// weighted moments of the mixed-precision form.
+//
+// For bootstrap k, G_k = X^T W_k X and B_k = X^T W_k Y are the lower triangle of
+// Z_k^T Z_k with Z_k = diag(sqrt(w_k)) [X | Y] restricted to rows with w > 0.
+// Each FP64 value v of Z_k is split into two bf16 pieces, hi = bf16(v) and
+// lo = bf16(v - hi) (|v - hi - lo| <= 2^-17 |v|), and the product is
+// hi'hi + hi'lo + lo'hi on bf16 tensor cores with FP32 accumulation in TMEM.
+// Every CHUNK_ROWS sample rows the FP32 accumulator is added into the FP64
+// output, which bounds the FP32 accumulation error; the dropped lo'lo term is
+// below 2^-16 relative.  The relative error of the Gram is ~1e-6.
+//
+// Two kernels:
+//  * k_split_transpose: gather rows (with weights), split, and write the two
+//    bf16 pieces transposed (features x rows, rows contiguous = K-major).
+//  * k_gram_tc: one CTA per (128-row x 256-col tile of the lower triangle,
+//    item).  Warp 0 issues TMA loads of K-major SWIZZLE_128B tiles into a
+//    2-stage ring; warp 1 issues tcgen05.mma (M=128, N=256, K=16, bf16 -> f32)
+//    into one of two TMEM accumulators; warps 2-5 drain the other accumulator
+//    (tcgen05.ld) and add it into the FP64 result, which only this CTA writes.
+//    Every wait is bounded (about one second) and reports UOI_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "kernels.h"
 
 namespace uoi {
 
-bool gram_tc_available() { return false; }
+namespace {
 
-void moments_tc(const double*, int64_t, const double*, int64_t, int64_t, int64_t, int64_t,
-                const uint32_t*, const uint8_t*, int32_t, double*, double*, cudaStream_t)
+constexpr int TM = 128;                 // tile rows (UMMA M)
+constexpr int TN = 256;                 // tile cols (UMMA N)
+constexpr int TK = 64;                  // rows of the sample per stage (128 B of bf16)
+constexpr int STAGES = 2;
+constexpr int CHUNK_STAGES = 64;        // 4096 sample rows per FP32 accumulation chunk
+constexpr int A_BYTES = TM * TK * 2;    // 16 KB per piece
+constexpr int B_BYTES = TN * TK * 2;    // 32 KB per piece
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+constexpr uint32_t TMEM_COLS = 512;     // two 256-column FP32 accumulators
+constexpr int THREADS = 192;            // 6 warps
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    throw Error(UOI_ERR_UNSUPPORTED, "tensor-core Gram not built");
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~1 s or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag) return false;
+            if (now_ns() - t0 > 1000000000ull) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint64_t* bar,
+                                            int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of 1 KB.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)2 << 61;                            // SWIZZLE_128B
+    return d;
+}
+
+// kind::f16 instruction descriptor: bf16 x bf16 -> f32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct GramTcArgs {
+    int64_t n_pad;            // K extent of the transposed pieces (multiple of TK)
+    int32_t pz_pad;           // feature extent of the pieces (multiple of TN)
+    int32_t pz;               // Z columns = pz_x + r
+    int32_t pz_x;             // columns of Z that come from X (= p, or |U| with a subset)
+    int32_t r;
+    int32_t p_out;            // leading size of the G / Bm outputs
+    int32_t ntiles;
+    const int32_t* tiles;     // (ti, tj) pairs
+    const int32_t* nrows;     // per item: sample rows (K extent actually used)
+    const int32_t* colmap;    // Z column (< pz_x) -> output feature index, or null
+    double* G;                // items x p_out x p_out
+    double* Bm;               // items x p_out x r
+    int32_t* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          GramTcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.y;
+    const int ti = a.tiles[2 * blockIdx.x], tj = a.tiles[2 * blockIdx.x + 1];
+    const int rows = a.nrows[item];
+    const int kstages = (rows + TK - 1) / TK;
+    const int nchunks = (kstages + CHUNK_STAGES - 1) / CHUNK_STAGES;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0 && kstages > 0) {
+        // ---------------- TMA producer ----------------
+        const int zA = item * 2, zB = item * 2;
+        for (int g = 0; g < kstages; ++g) {
+            const int s = g % STAGES;
+            if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            const uint32_t st = sbase + s * STAGE_BYTES;
+            mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+            const int k0 = g * TK;
+            tma_load_3d(st, &tmA, &full_bar[s], k0, ti * TM, zA);                       // A hi
+            tma_load_3d(st + A_BYTES, &tmA, &full_bar[s], k0, ti * TM, zA + 1);         // A lo
+            tma_load_3d(st + 2 * A_BYTES, &tmB, &full_bar[s], k0, tj * TN, zB);         // B hi
+            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmB, &full_bar[s], k0, tj * TN, zB + 1);  // B lo
+        }
+        if (abort_flag) {
+            // let the copies already issued land before the CTA releases its memory
+            for (int g = max(0, kstages - STAGES); g < kstages; ++g)
+                mbar_wait(&full_bar[g % STAGES], (g / STAGES) & 1, &abort_flag);
+        }
+    } else if (warp == 1 && lane == 0 && kstages > 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idesc = idesc_bf16(TM, TN);
+        int g = 0;
+        for (int c = 0; c < nchunks && !abort_flag; ++c) {
+            const int b = c & 1;
+            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(b * TN);
+            const int gend = min(kstages, (c + 1) * CHUNK_STAGES);
+            bool first = true;
+            for (; g < gend; ++g) {
+                const int s = g % STAGES;
+                if (!mbar_wait(&full_bar[s], (g / STAGES) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + s * STAGE_BYTES;
+                const uint64_t ah = smem_desc_sw128(st), al = smem_desc_sw128(st + A_BYTES);
+                const uint64_t bh = smem_desc_sw128(st + 2 * A_BYTES);
+                const uint64_t bl = smem_desc_sw128(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+                for (int ks = 0; ks < TK / 16; ++ks) {
+                    const uint64_t adv = (uint64_t)(ks * 32 >> 4);   // 16 bf16 = 32 B along K
+                    mma_bf16(d, ah + adv, bh + adv, idesc, first ? 0u : 1u);
+                    mma_bf16(d, ah + adv, bl + adv, idesc, 1u);
+                    mma_bf16(d, al + adv, bh + adv, idesc, 1u);
+                    first = false;
+                }
+                mma_commit(&empty_bar[s]);       // stage s free once these MMAs complete
+            }
+            if (abort_flag) break;
+            mma_commit(&accf_bar[b]);            // accumulator b ready for the epilogue
+        }
+        mma_commit(&done_bar);                   // every MMA issued above has completed
+        int dummy = 0;
+        mbar_wait(&done_bar, 0, &dummy);
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> FP64 accumulation ----------------
+        const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
+        const int iz = ti * TM + quad * 32 + lane;       // Z row of this thread
+        if (kstages == 0 && iz < a.pz) {
+            for (int jz = tj * TN; jz < tj * TN + TN && jz <= iz && jz < a.pz_x; ++jz) {
+                const int jo = a.colmap ? a.colmap[jz] : jz;
+                if (iz < a.pz_x)
+                    a.G[((size_t)item * a.p_out + (a.colmap ? a.colmap[iz] : iz)) * a.p_out + jo] = 0.0;
+                else
+                    a.Bm[((size_t)item * a.p_out + jo) * a.r + (iz - a.pz_x)] = 0.0;
+            }
+        }
+        for (int c = 0; c < nchunks && kstages > 0; ++c) {
+            const int b = c & 1;
+            if (!mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            for (int cb = 0; cb < TN / 32; ++cb) {
+                float v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TN + cb * 32);
+                tmem_ld32(taddr, v);
+                if (iz >= a.pz) continue;
+                const int jz0 = tj * TN + cb * 32;
+#pragma unroll 4
+                for (int t = 0; t < 32; ++t) {
+                    const int jz = jz0 + t;
+                    if (jz > iz || jz >= a.pz_x) continue;           // lower triangle, X columns
+                    const int jo = a.colmap ? a.colmap[jz] : jz;
+                    double* dst;
+                    if (iz < a.pz_x) {
+                        const int io = a.colmap ? a.colmap[iz] : iz;
+                        dst = a.G + ((size_t)item * a.p_out + io) * a.p_out + jo;
+                    } else {
+                        dst = a.Bm + ((size_t)item * a.p_out + jo) * a.r + (iz - a.pz_x);
+                    }
+                    *dst = (c == 0 ? 0.0 : *dst) + (double)v[t];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce_bar[b]);
+        }
+    }
+    // teardown: make sure no MMA is still writing TMEM, then free it
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+    }
+}
+
+// Gather rows with positive weight, scale by sqrt(w), split into bf16 hi/lo and
+// write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].
+__global__ void k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                                  int32_t pz_x, int32_t r, const int32_t* colmap,
+                                  const int32_t* rowlist, const double* rowscale,
+                                  const int32_t* nrows, int64_t m, int64_t n_pad, int32_t pz_pad,
+                                  __nv_bfloat16* out)
+{
+    __shared__ double tile[32][33];
+    const int item = blockIdx.z;
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int nr = nrows[item];
+    const int pz = pz_x + r;
+    // load: thread (ty, tx) reads rows t0 + ty + 8i, column c0 + tx
+    for (int i = 0; i < 4; ++i) {
+        const int tl = threadIdx.y + 8 * i;
+        const int64_t t = t0 + tl;
+        const int c = c0 + threadIdx.x;
+        double v = 0.0;
+        if (t < nr && c < pz) {
+            const int64_t row = rowlist[(int64_t)item * m + t];
+            const double sc = rowscale[(int64_t)item * m + t];
+            if (c < pz_x) v = X[row * ldx + (colmap ? colmap[c] : c)];
+            else v = Y[row * ldy + (c - pz_x)];
+            v *= sc;
+        }
+        tile[tl][threadIdx.x] = v;
+    }
+    __syncthreads();
+    // store: thread (ty, tx) writes column c0 + ty + 8i, rows t0 + tx
+    for (int i = 0; i < 4; ++i) {
+        const int cl = threadIdx.y + 8 * i;
+        const int c = c0 + cl;
+        const int64_t t = t0 + threadIdx.x;
+        if (c >= pz_pad || t >= n_pad) continue;
+        const double v = tile[threadIdx.x][cl];
+        const __nv_bfloat16 hi = __double2bfloat16(v);
+        const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+        out[(((int64_t)item * 2 + 0) * pz_pad + c) * n_pad + t] = hi;
+        out[(((int64_t)item * 2 + 1) * pz_pad + c) * n_pad + t] = lo;
+    }
+}
+
+// Row list of each item: rows with positive weight (in increasing order) and
+// their scale sqrt(w); nrows[item] = count.  One block per item.
+__global__ void k_row_lists(const uint32_t* w, const uint8_t* mask, int64_t m, int32_t* rowlist,
+                            double* rowscale, int32_t* nrows)
+{
+    const int item = blockIdx.x;
+    __shared__ int warp_tot[32];
+    __shared__ int carry, block_total;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < m; base += blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        uint32_t wt = 0;
+        if (t < m) wt = w ? w[(int64_t)item * m + t] : (uint32_t)mask[(int64_t)item * m + t];
+        const int flag = wt > 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+        const int before = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[wid] = __popc(bal);
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = blockDim.x >> 5;
+            int v = lane < nw ? warp_tot[lane] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += n;
+            }
+            if (lane < nw) warp_tot[lane] = incl - v;
+            if (lane == nw - 1) block_total = incl;
+        }
+        __syncthreads();
+        if (flag) {
+            const int pos = carry + warp_tot[wid] + before;
+            rowlist[(int64_t)item * m + pos] = (int32_t)t;
+            rowscale[(int64_t)item * m + pos] = sqrt((double)wt);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += block_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) nrows[item] = carry;
+}
+
+// Fill the upper triangle from the lower one (over the used features only).
+__global__ void k_mirror(double* G, int64_t p_out, const int32_t* colmap, int32_t pz_x)
+{
+    const int item = blockIdx.y;
+    double* g = G + (size_t)item * p_out * p_out;
+    const int64_t total = (int64_t)pz_x * pz_x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / pz_x), j = (int)(t % pz_x);
+        if (j <= i) continue;
+        const int io = colmap ? colmap[i] : i, jo = colmap ? colmap[j] : j;
+        g[(size_t)io * p_out + jo] = g[(size_t)jo * p_out + io];
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+CUtensorMap make_map(void* base, int64_t n_pad, int64_t pz_pad, int64_t depth, int box_rows)
+{
+    CUtensorMap m;
+    cuuint64_t dims[3] = { (cuuint64_t)n_pad, (cuuint64_t)pz_pad, (cuuint64_t)depth };
+    cuuint64_t strides[2] = { (cuuint64_t)(n_pad * 2), (cuuint64_t)(n_pad * 2 * pz_pad) };
+    cuuint32_t box[3] = { (cuuint32_t)TK, (cuuint32_t)box_rows, 1 };
+    cuuint32_t estr[3] = { 1, 1, 1 };
+    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
+}  // namespace
+
+bool gram_tc_available()
+{
+    static int avail = -1;
+    if (avail < 0) {
+        int dev = 0, major = 0, minor = 0;
+        avail = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+            avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+    }
+    return avail == 1;
+}
+
+// Tensor-core moments for B items (weights w or 0/1 mask, or unweighted),
+// optionally restricted to the X columns listed in colmap (pz_x of them).
+void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
+                     int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
+                     const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
+                     cudaStream_t s)
+{
+    if (!gram_tc_available()) throw Error(UOI_ERR_UNSUPPORTED, "tcgen05 Gram needs sm_103a");
+    const int32_t pz = pz_x + (int32_t)r;
+    const int32_t pz_pad = (int32_t)ceil_div(pz, TN) * TN;
+    const int64_t n_pad = ceil_div(m, TK) * TK;
+    // tile list of the lower triangle (rows of Z x X columns)
+    std::vector<int32_t> tiles;
+    const int nti = (int)ceil_div(pz, TM);
+    for (int ti = 0; ti < nti; ++ti) {
+        const int jmax = std::min(ti * TM + TM - 1, pz_x - 1);
+        for (int tj = 0; tj * TN <= jmax; ++tj) { tiles.push_back(ti); tiles.push_back(tj); }
+    }
+    const int ntiles = (int)tiles.size() / 2;
+    DevBuf tl(sizeof(int32_t) * tiles.size(), s);
+    UOI_CUDA(cudaMemcpyAsync(tl.ptr, tiles.data(), sizeof(int32_t) * tiles.size(),
+                             cudaMemcpyHostToDevice, s));
+    DevBuf rows(sizeof(int32_t) * (size_t)(m * B), s), scale(sizeof(double) * (size_t)(m * B), s);
+    DevBuf nrows(sizeof(int32_t) * B, s), err(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
+    if (w || mask) {
+        k_row_lists<<<B, 1024, 0, s>>>(w, mask, m, rows.as<int32_t>(), scale.as<double>(),
+                                        nrows.as<int32_t>());
+        UOI_CHECK_LAUNCH();
+        count_launch();
+    } else {
+        throw Error(UOI_ERR_INVALID_ARG, "tensor-core moments need weights or a mask");
+    }
+    // items per pass bounded by the size of the split copies (<= 8 GB)
+    const size_t per_item = (size_t)2 * pz_pad * n_pad * sizeof(__nv_bfloat16);
+    const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (8ull << 30) / per_item));
+    DevBuf zt(per_item * group, s);
+    auto kern = k_gram_tc;
+    UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    for (int b0 = 0; b0 < B; b0 += group) {
+        const int nb = std::min(group, B - b0);
+        dim3 gs((unsigned)(n_pad / 32), (unsigned)ceil_div(pz_pad, 32), (unsigned)nb);
+        k_split_transpose<<<gs, dim3(32, 8), 0, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
+                                                     rows.as<int32_t>() + (size_t)b0 * m,
+                                                     scale.as<double>() + (size_t)b0 * m,
+                                                     nrows.as<int32_t>() + b0, m, n_pad, pz_pad,
+                                                     zt.as<__nv_bfloat16>());
+        UOI_CHECK_LAUNCH();
+        const CUtensorMap mA = make_map(zt.ptr, n_pad, pz_pad, 2 * nb, TM);
+        const CUtensorMap mB = make_map(zt.ptr, n_pad, pz_pad, 2 * nb, TN);
+        GramTcArgs a;
+        a.n_pad = n_pad; a.pz_pad = pz_pad; a.pz = pz; a.pz_x = pz_x; a.r = (int32_t)r;
+        a.p_out = (int32_t)p_out; a.ntiles = ntiles; a.tiles = tl.as<int32_t>();
+        a.nrows = nrows.as<int32_t>() + b0; a.colmap = colmap;
+        a.G = G + (size_t)b0 * p_out * p_out; a.Bm = Bm + (size_t)b0 * p_out * r;
+        a.err = err.as<int32_t>();
+        k_gram_tc<<<dim3((unsigned)ntiles, (unsigned)nb), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
+        UOI_CHECK_LAUNCH();
+        dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
+        k_mirror<<<gm, 256, 0, s>>>(G + (size_t)b0 * p_out * p_out, p_out, colmap, pz_x);
+        UOI_CHECK_LAUNCH();
+        count_launch(3);
+    }
+    int32_t h = 0;
+    UOI_CUDA(cudaMemcpyAsync(&h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    if (h) throw Error(h, "tensor-core Gram: a bounded pipeline wait expired");
+}
+
+void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
+                int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
+                double* Bm, cudaStream_t s)
+{
+    moments_tc_cols(X, ldx, Y, ldy, m, p, r, (int32_t)p, nullptr, w, mask, B, G, Bm, s);
 }
 
 }  // namespace uoi

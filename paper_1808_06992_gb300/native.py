@@ -75,6 +75,7 @@ def lib():
                                      C.POINTER(UoiTrace), C.POINTER(UoiDiag)]
         L.lasso_admm_batch.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d, i32, i32,
                                        i32, vp, vp, vp, vp]
+        L.uoi_weighted_moments.argtypes = [vp, vp, i64, i64, i64, vp, i32, i32, vp, vp, vp]
         L.uoi_status_string.argtypes = [C.c_int]
         L.uoi_status_string.restype = C.c_char_p
         L.uoi_get_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
@@ -84,7 +85,7 @@ def lib():
 
 
 EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_var_fit", "uoi_fit_traced",
-            "lasso_admm_batch", "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
+            "lasso_admm_batch", "uoi_weighted_moments", "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
 
 
 class UoiError(RuntimeError):
@@ -249,6 +250,23 @@ def lasso_admm_batch(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6
                                 _ptr(conv), stream)
     _check(st)
     return dict(beta=beta, iters=iters, conv=conv, status=st)
+
+
+def weighted_moments(X, Y, weights, precision=PREC_FP64, stream=None):
+    """G_k = X^T diag(w_k) X and B_k = X^T diag(w_k) Y for each weight row k."""
+    X = _prep(X, np.float64)
+    Y = _prep(Y, np.float64)
+    if Y.ndim == 1:
+        Y = Y.reshape(-1, 1)
+    n, p = X.shape
+    r = Y.shape[1]
+    w = _prep(weights, np.uint32).reshape(-1, n)
+    B = w.shape[0]
+    G = _empty(X, (B, p, p), np.float64)
+    Bm = _empty(X, (B, p, r), np.float64)
+    _check(lib().uoi_weighted_moments(_ptr(X), _ptr(Y), n, p, r, _ptr(w), B, precision, _ptr(G),
+                                      _ptr(Bm), stream))
+    return G, Bm
 
 
 def shutdown():
