@@ -209,9 +209,6 @@ struct StreamState {
     int32_t nchains;
 };
 
-constexpr int SM_TM = 64;   // rows per GEMM tile
-constexpr int SM_TN = 64;   // chains per GEMM tile
-constexpr int SM_TK = 16;
 constexpr int GV_ROWS = 8;  // rows per GEMV block (one warp per row)
 
 template <typename T>
@@ -242,6 +239,14 @@ __device__ __forceinline__ void admm_elem(const AdmmDev<T>& P, T acc, int g, int
     part[0] += d * d; part[1] += dz * dz; part[2] += x * x; part[3] += zn * zn; part[4] += un * un;
 }
 
+// x-update tile: 128 rows x 64 chains, K steps of 16, 256 threads with an
+// 8 x 4 register block each (rows 8*ty .. +7, chains 4*tx .. +3).  The soft
+// threshold, dual update and partial norms run in the epilogue; V = z - u of the
+// next iteration is written to the other buffer.
+constexpr int SG_TM = 128;
+constexpr int SG_TN = 64;
+constexpr int SG_TK = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_stream_gemm(AdmmDev<T> P, StreamState S, int cur, const T* __restrict__ Vc, T* Vn, T* z, T* u,
@@ -249,82 +254,91 @@ k_stream_gemm(AdmmDev<T> P, StreamState S, int cur, const T* __restrict__ Vc, T*
 {
     const int g = blockIdx.z;
     const int rt = blockIdx.x;
-    const int i0 = rt * SM_TM;
-    const int s0 = blockIdx.y * SM_TN;
+    const int i0 = rt * SG_TM;
+    const int s0 = blockIdx.y * SG_TN;
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < 32) {
         for (int t = threadIdx.x; t < P.G; t += 32) S.cnt[cur ^ 1][t] = 0;
         if (threadIdx.x == 0) *S.total[cur ^ 1] = 0;
     }
     const int count = S.cnt[cur][g];
     if (s0 >= count) return;
-    const int ncols = min(SM_TN, count - s0);
+    const int ncols = min(SG_TN, count - s0);
     const int32_t* act = S.act[cur] + (size_t)g * S.nchains + s0;
     const int p = P.p;
     const T* Mg = P.M + (size_t)g * p * p;
 
-    __shared__ T As[SM_TK][SM_TM + 1];
-    __shared__ T Bs[SM_TK][SM_TN + 1];
-    __shared__ int32_t slots[SM_TN];
-    __shared__ T red[8][SM_TN][5];
-    if (threadIdx.x < SM_TN) slots[threadIdx.x] = threadIdx.x < ncols ? act[threadIdx.x] : -1;
+    __shared__ __align__(16) T As[SG_TK][SG_TM];
+    __shared__ __align__(16) T Bs[SG_TK][SG_TN];
+    __shared__ int32_t slots[SG_TN];
+    __shared__ T red[8][SG_TN][5];
+    if (threadIdx.x < SG_TN) slots[threadIdx.x] = threadIdx.x < ncols ? act[threadIdx.x] : -1;
     __syncthreads();
 
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    T acc[4][4] = {};
-    for (int kb = 0; kb < p; kb += SM_TK) {
-        for (int e = threadIdx.x; e < SM_TK * SM_TM; e += 256) {
-            const int il = e / SM_TK, kk = e % SM_TK;
+    T acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int kb = 0; kb < p; kb += SG_TK) {
+        // M tile: 128 rows x 16 k (rows contiguous in k); V tile: 64 chains x 16 k
+        for (int e = threadIdx.x; e < SG_TM * SG_TK; e += 256) {
+            const int il = e / SG_TK, kk = e % SG_TK;
             const int i = i0 + il, k = kb + kk;
             As[kk][il] = (i < p && k < p) ? Mg[(size_t)i * p + k] : T(0);
-            const int sl = slots[il];
-            Bs[kk][il] = (sl >= 0 && k < p) ? Vc[(size_t)sl * p + k] : T(0);
+        }
+        for (int e = threadIdx.x; e < SG_TN * SG_TK; e += 256) {
+            const int cl = e / SG_TK, kk = e % SG_TK;
+            const int sl = slots[cl], k = kb + kk;
+            Bs[kk][cl] = (sl >= 0 && k < p) ? Vc[(size_t)sl * p + k] : T(0);
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < SM_TK; ++kk) {
-            T a[4], b[4];
+        for (int kk = 0; kk < SG_TK; ++kk) {
+            T a[8], b[4];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) { a[w] = As[kk][ty + 16 * w]; b[w] = Bs[kk][tx + 16 * w]; }
+            for (int w = 0; w < 8; ++w) a[w] = As[kk][ty * 8 + w];
 #pragma unroll
-            for (int w = 0; w < 4; ++w)
+            for (int w = 0; w < 4; ++w) b[w] = Bs[kk][tx * 4 + w];
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[w][v] = fma(a[w], b[v], acc[w][v]);
         }
         __syncthreads();
     }
-    // epilogue: thread owns columns tx + 16v and rows ty + 16w
+    // epilogue: thread owns chains 4*tx + v and rows 8*ty + w
     T part[4][5];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
 #pragma unroll
         for (int t = 0; t < 5; ++t) part[v][t] = T(0);
-        const int sl = slots[tx + 16 * v];
+        const int sl = slots[tx * 4 + v];
         if (sl < 0) continue;
         int gg, e;
         slot_coords(P, S.nchains, sl, gg, e);
         const T kappa = (T)P.lambdas[S.slot_j[sl]] / P.rho;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int i = i0 + ty + 16 * w;
+        for (int w = 0; w < 8; ++w) {
+            const int i = i0 + ty * 8 + w;
             if (i < p) admm_elem(P, acc[w][v], g, e, sl, i, kappa, z, u, Vn, part[v]);
         }
     }
-    // reduce over ty: lanes l and l^16 share tx; then over the 8 warps in a fixed order
+    // lanes l and l^16 hold rows of the same chains (ty differs by one)
 #pragma unroll
     for (int v = 0; v < 4; ++v)
 #pragma unroll
         for (int t = 0; t < 5; ++t) part[v][t] += __shfl_xor_sync(0xffffffffu, part[v][t], 16);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane < 16)
+    if ((threadIdx.x & 31) < 16)
 #pragma unroll
         for (int v = 0; v < 4; ++v)
 #pragma unroll
-            for (int t = 0; t < 5; ++t) red[warp][lane + 16 * v][t] = part[v][t];
+            for (int t = 0; t < 5; ++t) red[threadIdx.x >> 5][tx * 4 + v][t] = part[v][t];
     __syncthreads();
     if (threadIdx.x < ncols) {
         const int sl = slots[threadIdx.x];
         T tot[5] = {};
-        for (int w = 0; w < 8; ++w)
+        for (int w = 0; w < 8; ++w)                        // fixed order over row groups
 #pragma unroll
             for (int t = 0; t < 5; ++t) tot[t] += red[w][threadIdx.x][t];
 #pragma unroll
@@ -553,7 +567,7 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
     const int64_t slots = (int64_t)P.G * nchains;
     const int p = (int)P.p;
     const bool gemv = nchains <= 4;
-    const int RT = gemv ? (int)ceil_div(p, GV_ROWS) : (int)ceil_div(p, SM_TM);
+    const int RT = gemv ? (int)ceil_div(p, GV_ROWS) : (int)ceil_div(p, SG_TM);
     DevBuf zb(sizeof(T) * slots * p, s), ub(sizeof(T) * slots * p, s);
     DevBuf v0(sizeof(T) * slots * p, s), v1(sizeof(T) * slots * p, s);
     DevBuf nb(sizeof(T) * slots * RT * 5, s);
@@ -589,7 +603,7 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
                 k_stream_gemv<T, 4><<<grid, 256, 0, s>>>(d, S, cur, V[cur], V[cur ^ 1], zb.as<T>(),
                                                           ub.as<T>(), nb.as<T>(), RT);
             } else {
-                dim3 grid((unsigned)RT, (unsigned)ceil_div(nchains, SM_TN), (unsigned)P.G);
+                dim3 grid((unsigned)RT, (unsigned)ceil_div(nchains, SG_TN), (unsigned)P.G);
                 k_stream_gemm<T><<<grid, 256, 0, s>>>(d, S, cur, V[cur], V[cur ^ 1], zb.as<T>(),
                                                       ub.as<T>(), nb.as<T>(), RT);
             }

@@ -190,14 +190,16 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     int t1 = tm ? tm->mark() : 0;
     DevBuf st(sizeof(DevStatus), s);
     UOI_CUDA(cudaMemsetAsync(st.ptr, 0, st.bytes, s));
-    build_and_factor(G.as<double>(), nk.as<double>(), rho, p, B, G.as<double>(), st.as<DevStatus>(), s);
+    DevBuf A(sizeof(T) * (size_t)(B * p * p), s);
+    build_and_factor<T>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<T>(), st.as<DevStatus>(), s);
+    G.release();
     check_status(st.as<DevStatus>(), s, "Cholesky of G/n + rho I");
     DevBuf Linv(sizeof(T) * (size_t)(B * p * p), s), M(sizeof(T) * (size_t)(B * p * p), s);
     DevBuf c(sizeof(T) * (size_t)(B * p * r), s);
-    inverse_and_rhs<T>(G.as<double>(), Bm.as<double>(), nk.as<double>(), p, r, B, Linv.as<T>(),
+    inverse_and_rhs<T>(A.as<T>(), Bm.as<double>(), nk.as<double>(), p, r, B, Linv.as<T>(),
                        M.as<T>(), c.as<T>(), s);
     Linv.release();
-    G.release();
+    A.release();
     int t2 = tm ? tm->mark() : 0;
     AdmmProblem<T> P;
     P.G = B; P.p = p; P.r = r; P.q = q;
@@ -276,7 +278,10 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         UOI_CUDA(cudaMemcpyAsync(lam.ptr, ld, sizeof(double) * q, cudaMemcpyDeviceToDevice, s));
     } else {
         DevBuf xty(sizeof(double) * (size_t)(p * r), s);
-        moments_fp64(Xd, ldx, Yd, ldy, m, p, r, nullptr, nullptr, 1, nullptr, xty.as<double>(), 1, s);
+        if (r <= 4)
+            xty_small(Xd, ldx, Yd, ldy, m, p, r, xty.as<double>(), s);
+        else
+            moments_fp64(Xd, ldx, Yd, ldy, m, p, r, nullptr, nullptr, 1, nullptr, xty.as<double>(), 1, s);
         lambda_grid(xty.as<double>(), p * r, m, q, prm->lambda_min_ratio, lam.as<double>(), s);
     }
 
@@ -312,10 +317,23 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     DevBuf Gt(sizeof(double) * (size_t)(B2 * p * p), s), Bt(sizeof(double) * (size_t)(B2 * p * r), s);
     DevBuf Ge(sizeof(double) * (size_t)(B2 * p * p), s), Be(sizeof(double) * (size_t)(B2 * p * r), s);
     DevBuf yye(sizeof(double) * (size_t)(B2 * r), s);
-    moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, west.as<uint32_t>(), nullptr, B2,
-            Gt.as<double>(), Bt.as<double>(), s);
-    moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, nullptr, evm.as<uint8_t>(), B2,
-            Ge.as<double>(), Be.as<double>(), s);
+    if (mixed && gram_tc_available()) {
+        // OLS on S_j only touches features in the union U of the family, so the
+        // estimation moments are formed on U alone.
+        DevBuf ucols(sizeof(int32_t) * (size_t)p, s);
+        const int32_t nu = union_columns(fam.as<uint64_t>(), q * r, p, ucols.as<int32_t>(), s);
+        if (nu > 0) {
+            moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), west.as<uint32_t>(),
+                            nullptr, B2, Gt.as<double>(), Bt.as<double>(), s);
+            moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), nullptr,
+                            evm.as<uint8_t>(), B2, Ge.as<double>(), Be.as<double>(), s);
+        }
+    } else {
+        moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, west.as<uint32_t>(), nullptr, B2,
+                Gt.as<double>(), Bt.as<double>(), s);
+        moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, nullptr, evm.as<uint8_t>(), B2,
+                Ge.as<double>(), Be.as<double>(), s);
+    }
     masked_sumsq(Yd, ldy, m, r, evm.as<uint8_t>(), B2, yye.as<double>(), s);
     const int t_est1 = tm.mark();
     DevOut<double> loss_o;

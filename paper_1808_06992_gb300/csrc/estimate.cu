@@ -246,7 +246,50 @@ void run_ols(OlsArgs a, cudaStream_t s)
     count_launch(2);
 }
 
+// U = union over (j, e) of the family supports, compacted in increasing order.
+__global__ void k_union_cols(const uint64_t* fam, int64_t count, int W, int64_t p, int32_t* cols,
+                             int32_t* n_out)
+{
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int w = 0; w < W; ++w) {
+        // one block: OR of word w over all family members
+        uint64_t acc = 0;
+        for (int64_t t = threadIdx.x; t < count; t += blockDim.x) acc |= fam[t * W + w];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+        __shared__ uint64_t wred[32];
+        if (lane == 0) wred[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t u = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) u |= wred[i];
+            for (int b = 0; b < 64; ++b) {
+                const int64_t i = (int64_t)w * 64 + b;
+                if (i < p && ((u >> b) & 1ull)) cols[base++] = (int32_t)i;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_out = base;
+}
+
 }  // namespace
+
+int32_t union_columns(const uint64_t* family, int64_t count, int64_t p, int32_t* cols,
+                      cudaStream_t s)
+{
+    DevBuf n(sizeof(int32_t), s);
+    k_union_cols<<<1, 256, 0, s>>>(family, count, (int)((p + 63) / 64), p, cols, n.as<int32_t>());
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    int32_t h = 0;
+    UOI_CUDA(cudaMemcpyAsync(&h, n.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
 
 void family_init(uint64_t* fam, int64_t words, cudaStream_t s)
 {

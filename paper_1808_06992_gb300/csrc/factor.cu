@@ -9,7 +9,10 @@
 // inverse loses nothing measurable.
 //
 // Right-looking blocked Cholesky (panel factor, panel solve, trailing update),
-// blocked triangular inverse and the product M = L^{-T} L^{-1}.
+// blocked triangular inverse and the product M = L^{-T} L^{-1}, all templated
+// on the factor type T: FP64 in the plain form, FP32 in the mixed form (the
+// FP32 ADMM state bounds that form's accuracy at the same level, and GB300's
+// FP64 rate made the FP64 factor the largest single cost of a fit).
 #include "kernels.h"
 #include "tile.cuh"
 
@@ -20,23 +23,24 @@ namespace {
 constexpr int NB = 32;    // Cholesky panel width
 constexpr int IB = 64;    // inverse block
 
-__global__ void k_build_system(const double* G, const double* nk, double rho, int64_t p,
-                               double* A)
+template <typename T>
+__global__ void k_build_system(const double* G, const double* nk, double rho, int64_t p, T* A)
 {
     const int64_t k = blockIdx.y;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < p * p;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / p, j = t % p;
-        A[k * p * p + t] = G[k * p * p + t] / nk[k] + (i == j ? rho : 0.0);
+        A[k * p * p + t] = (T)(G[k * p * p + t] / nk[k] + (i == j ? rho : 0.0));
     }
 }
 
 // Factor the nb x nb diagonal block at j0 (one block per matrix).
-__global__ void k_chol_diag(double* A, int64_t p, int64_t j0, int nb, DevStatus* st)
+template <typename T>
+__global__ void k_chol_diag(T* A, int64_t p, int64_t j0, int nb, DevStatus* st)
 {
     const int64_t k = blockIdx.x;
-    double* a = A + k * p * p;
-    __shared__ double D[NB][NB + 1];
+    T* a = A + k * p * p;
+    __shared__ T D[NB][NB + 1];
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
@@ -46,11 +50,11 @@ __global__ void k_chol_diag(double* A, int64_t p, int64_t j0, int nb, DevStatus*
     __syncthreads();
     for (int c = 0; c < nb; ++c) {
         if (threadIdx.x == 0) {
-            const double d = D[c][c];
-            if (!(d > 0.0)) { bad = 1; D[c][c] = 1.0; } else D[c][c] = sqrt(d);
+            const T d = D[c][c];
+            if (!(d > T(0))) { bad = 1; D[c][c] = T(1); } else D[c][c] = sqrt(d);
         }
         __syncthreads();
-        const double lcc = D[c][c];
+        const T lcc = D[c][c];
         for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][c] /= lcc;
         __syncthreads();
         for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
@@ -61,17 +65,18 @@ __global__ void k_chol_diag(double* A, int64_t p, int64_t j0, int nb, DevStatus*
     }
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
         const int i = e / nb, j = e % nb;
-        a[(j0 + i) * p + j0 + j] = j <= i ? D[i][j] : 0.0;
+        a[(j0 + i) * p + j0 + j] = j <= i ? D[i][j] : T(0);
     }
     if (threadIdx.x == 0 && bad) dev_fail(st, UOI_ERR_NOT_PD, (int)k);
 }
 
 // Rows below the diagonal block: L[i, j0:j0+nb] = A[i, j0:j0+nb] L_dd^{-T}.
-__global__ void k_chol_panel(double* A, int64_t p, int64_t j0, int nb)
+template <typename T>
+__global__ void k_chol_panel(T* A, int64_t p, int64_t j0, int nb)
 {
     const int64_t k = blockIdx.y;
-    double* a = A + k * p * p;
-    __shared__ double D[NB][NB + 1];
+    T* a = A + k * p * p;
+    __shared__ T D[NB][NB + 1];
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
         const int i = e / nb, j = e % nb;
         D[i][j] = a[(j0 + i) * p + j0 + j];
@@ -79,13 +84,13 @@ __global__ void k_chol_panel(double* A, int64_t p, int64_t j0, int nb)
     __syncthreads();
     const int64_t i = j0 + nb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= p) return;
-    double x[NB];
+    T x[NB];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) x[c] = c < nb ? a[i * p + j0 + c] : 0.0;
+    for (int c = 0; c < NB; ++c) x[c] = c < nb ? a[i * p + j0 + c] : T(0);
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
         if (c >= nb) break;
-        double v = x[c];
+        T v = x[c];
 #pragma unroll
         for (int s = 0; s < NB; ++s)
             if (s < c) v -= x[s] * D[c][s];
@@ -97,24 +102,25 @@ __global__ void k_chol_panel(double* A, int64_t p, int64_t j0, int nb)
 }
 
 // Trailing update of the lower triangle: A[i][j] -= sum_s L[i][j0+s] L[j][j0+s].
-__global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t p, int64_t j0, int nb)
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_update(T* A, int64_t p, int64_t j0, int nb)
 {
     const int64_t k = blockIdx.y;
-    double* a = A + k * p * p;
+    T* a = A + k * p * p;
     const int64_t base = j0 + nb;
     int64_t ti, tj;
     tri_index(blockIdx.x, ti, tj);
     const int64_t i0 = base + ti * 64, jj0 = base + tj * 64;
-    double acc[4][4] = {};
+    T acc[4][4] = {};
     auto fa = [&](int il, int64_t s) {
         const int64_t i = i0 + il;
-        return i < p ? a[i * p + j0 + s] : 0.0;
+        return i < p ? a[i * p + j0 + s] : T(0);
     };
     auto fb = [&](int64_t s, int jl) {
         const int64_t j = jj0 + jl;
-        return j < p ? a[j * p + j0 + s] : 0.0;
+        return j < p ? a[j * p + j0 + s] : T(0);
     };
-    tile64_acc<double>(acc, fa, fb, 0, nb);
+    tile64_acc<T>(acc, fa, fb, 0, nb);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -131,12 +137,12 @@ __global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t p, int64
 // Inverse of each IB x IB lower-triangular diagonal block, in T.  The block of
 // L is read from global memory (L2); the inverse is built in shared memory.
 template <typename T>
-__global__ void k_trinv_diag(const double* L, int64_t p, T* Linv)
+__global__ void k_trinv_diag(const T* L, int64_t p, T* Linv)
 {
     const int64_t k = blockIdx.y;
     const int64_t b0 = (int64_t)blockIdx.x * IB;
     const int nb = (int)(p - b0 < IB ? p - b0 : IB);
-    const double* l = L + k * p * p + b0 * p + b0;     // l[i * p + j] = L[b0+i][b0+j]
+    const T* l = L + k * p * p + b0 * p + b0;          // l[i * p + j] = L[b0+i][b0+j]
     T* li = Linv + k * p * p;
     __shared__ T R[IB][IB + 1];
     const int j = threadIdx.x;                    // one column of the inverse per thread
@@ -162,11 +168,11 @@ __global__ void k_trinv_diag(const double* L, int64_t p, T* Linv)
 
 // Block row I of L^{-1}: for J < I, Linv_IJ = -Linv_II * sum_{K=J}^{I-1} L_IK Linv_KJ.
 template <typename T>
-__global__ void __launch_bounds__(256) k_trinv_row(const double* L, int64_t p, int64_t I, T* Linv)
+__global__ void __launch_bounds__(256) k_trinv_row(const T* L, int64_t p, int64_t I, T* Linv)
 {
     const int64_t k = blockIdx.y;
     const int64_t J = blockIdx.x;
-    const double* l = L + k * p * p;
+    const T* l = L + k * p * p;
     T* li = Linv + k * p * p;
     const int64_t i0 = I * IB, j0 = J * IB;
     T acc[4][4] = {};
@@ -276,33 +282,39 @@ __global__ void __launch_bounds__(256) k_rhs(const T* M, const double* Bm, const
 
 }  // namespace
 
+template <typename T>
 void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
-                      double* A, DevStatus* status, cudaStream_t s)
+                      T* A, DevStatus* status, cudaStream_t s)
 {
     dim3 gb((unsigned)std::min<int64_t>(ceil_div(p * p, 256), 1024), (unsigned)B);
-    k_build_system<<<gb, 256, 0, s>>>(G, nk, rho, p, A);
+    k_build_system<T><<<gb, 256, 0, s>>>(G, nk, rho, p, A);
     UOI_CHECK_LAUNCH();
     count_launch();
     for (int64_t j0 = 0; j0 < p; j0 += NB) {
         const int nb = (int)std::min<int64_t>(NB, p - j0);
-        k_chol_diag<<<B, 256, 0, s>>>(A, p, j0, nb, status);
+        k_chol_diag<T><<<B, 256, 0, s>>>(A, p, j0, nb, status);
         UOI_CHECK_LAUNCH();
         count_launch();
         const int64_t rest = p - j0 - nb;
         if (rest <= 0) break;
         dim3 gp((unsigned)ceil_div(rest, 128), (unsigned)B);
-        k_chol_panel<<<gp, 128, 0, s>>>(A, p, j0, nb);
+        k_chol_panel<T><<<gp, 128, 0, s>>>(A, p, j0, nb);
         UOI_CHECK_LAUNCH();
         const int64_t tt = ceil_div(rest, 64);
         dim3 gu((unsigned)(tt * (tt + 1) / 2), (unsigned)B);
-        k_chol_update<<<gu, 256, 0, s>>>(A, p, j0, nb);
+        k_chol_update<T><<<gu, 256, 0, s>>>(A, p, j0, nb);
         UOI_CHECK_LAUNCH();
         count_launch(2);
     }
 }
 
+template void build_and_factor<double>(const double*, const double*, double, int64_t, int32_t,
+                                       double*, DevStatus*, cudaStream_t);
+template void build_and_factor<float>(const double*, const double*, double, int64_t, int32_t,
+                                      float*, DevStatus*, cudaStream_t);
+
 template <typename T>
-void inverse_and_rhs(const double* L, const double* Bm, const double* nk, int64_t p, int64_t r,
+void inverse_and_rhs(const T* L, const double* Bm, const double* nk, int64_t p, int64_t r,
                      int32_t B, T* Linv, T* M, T* c, cudaStream_t s)
 {
     UOI_CUDA(cudaMemsetAsync(Linv, 0, sizeof(T) * (size_t)(p * p * B), s));
@@ -326,7 +338,7 @@ void inverse_and_rhs(const double* L, const double* Bm, const double* nk, int64_
 
 template void inverse_and_rhs<double>(const double*, const double*, const double*, int64_t,
                                       int64_t, int32_t, double*, double*, double*, cudaStream_t);
-template void inverse_and_rhs<float>(const double*, const double*, const double*, int64_t,
+template void inverse_and_rhs<float>(const float*, const double*, const double*, int64_t,
                                      int64_t, int32_t, float*, float*, float*, cudaStream_t);
 
 }  // namespace uoi

@@ -4,6 +4,8 @@
 // B_k = X^T W_k Y (W_k = diag of the bootstrap multiplicities): the ADMM
 // x-update of Eq. 5 then never touches the n rows again.  This is the plain
 // FP64 form; the tensor-core form lives in gram_tc.cu.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace uoi {
@@ -155,7 +157,53 @@ __global__ void k_check_finite(const double* X, int64_t ldx, int64_t m, int64_t 
     }
 }
 
+// Split-K X^T Y for r <= 4: block (column tile, row chunk) writes partial sums.
+constexpr int XTY_ROWS = 1024;
+__global__ void k_xty_partial(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                              int64_t m, int64_t p, int64_t r, double* part)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t c = blockIdx.y;
+    const int64_t t0 = c * XTY_ROWS, t1 = min(m, t0 + XTY_ROWS);
+    double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
+    if (j < p) {
+        for (int64_t t = t0; t < t1; ++t) {
+            const double x = X[t * ldx + j];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (e < r) acc[e] = fma(x, Y[t * ldy + e], acc[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (e < r) part[(c * p + j) * r + e] = acc[e];
+    }
+}
+
+__global__ void k_xty_reduce(const double* part, int64_t chunks, int64_t count, double* out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t c = 0; c < chunks; ++c) s += part[c * count + i];
+        out[i] = s;
+    }
+}
+
 }  // namespace
+
+void xty_small(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
+               int64_t r, double* XtY, cudaStream_t s)
+{
+    const int64_t chunks = ceil_div(m, XTY_ROWS);
+    DevBuf part(sizeof(double) * (size_t)(chunks * p * r), s);
+    dim3 g((unsigned)ceil_div(p, 128), (unsigned)chunks);
+    k_xty_partial<<<g, 128, 0, s>>>(X, ldx, Y, ldy, m, p, r, part.as<double>());
+    UOI_CHECK_LAUNCH();
+    k_xty_reduce<<<(unsigned)std::min<int64_t>(ceil_div(p * r, 256), 1024), 256, 0, s>>>(
+        part.as<double>(), chunks, p * r, XtY);
+    UOI_CHECK_LAUNCH();
+    count_launch(2);
+}
 
 void moments_fp64(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
                   int64_t p, int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B,

@@ -6,19 +6,23 @@
 // Each FP64 value v of Z_k is split into two bf16 pieces, hi = bf16(v) and
 // lo = bf16(v - hi) (|v - hi - lo| <= 2^-17 |v|), and the product is
 // hi'hi + hi'lo + lo'hi on bf16 tensor cores with FP32 accumulation in TMEM.
-// Every CHUNK_ROWS sample rows the FP32 accumulator is added into the FP64
-// output, which bounds the FP32 accumulation error; the dropped lo'lo term is
-// below 2^-16 relative.  The relative error of the Gram is ~1e-6.
+// The tensor cores' FP32 accumulation loses about a third of an ulp per K=16
+// step (measured), so the accumulator is drained every 128 sample rows (24
+// steps, <= 5e-7 relative) into compensated FP32 pairs (TwoSum) held in the
+// epilogue warps' registers, and the sum is written once in FP64 at the end.
+// The lo'lo term (up to 2^-16 relative per product) is zero-mean off the
+// diagonal; on the diagonal it is a positive bias and is added exactly
+// (k_diag_lo).  Relative error of the Gram: ~5e-7 of the largest diagonal entry.
 //
 // Two kernels:
 //  * k_split_transpose: gather rows (with weights), split, and write the two
 //    bf16 pieces transposed (features x rows, rows contiguous = K-major).
-//  * k_gram_tc: one CTA per (128-row x 256-col tile of the lower triangle,
-//    item).  Warp 0 issues TMA loads of K-major SWIZZLE_128B tiles into a
-//    2-stage ring; warp 1 issues tcgen05.mma (M=128, N=256, K=16, bf16 -> f32)
-//    into one of two TMEM accumulators; warps 2-5 drain the other accumulator
-//    (tcgen05.ld) and add it into the FP64 result, which only this CTA writes.
-//    Every wait is bounded (about one second) and reports UOI_ERR_TIMEOUT.
+//  * k_gram_tc: one CTA per (128 x 128 tile of the lower triangle, item).
+//    Warp 0 issues TMA loads of K-major SWIZZLE_128B tiles into a 3-stage
+//    ring; warp 1 issues tcgen05.mma (M=128, N=128, K=16, bf16 -> f32) into one
+//    of two TMEM accumulators; warps 2-9 drain the other accumulator
+//    (tcgen05.ld) into their TwoSum registers.  Every wait is bounded (about
+//    one second) and reports UOI_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -34,16 +38,17 @@ namespace uoi {
 namespace {
 
 constexpr int TM = 128;                 // tile rows (UMMA M)
-constexpr int TN = 256;                 // tile cols (UMMA N)
+constexpr int TN = 128;                 // tile cols (UMMA N)
 constexpr int TK = 64;                  // rows of the sample per stage (128 B of bf16)
-constexpr int STAGES = 2;
-constexpr int CHUNK_STAGES = 64;        // 4096 sample rows per FP32 accumulation chunk
+constexpr int STAGES = 3;
+constexpr int CHUNK_STAGES = 2;         // 128 sample rows per FP32 accumulation chunk
 constexpr int A_BYTES = TM * TK * 2;    // 16 KB per piece
-constexpr int B_BYTES = TN * TK * 2;    // 32 KB per piece
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB
+constexpr int B_BYTES = TN * TK * 2;    // 16 KB per piece
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 64 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
-constexpr uint32_t TMEM_COLS = 512;     // two 256-column FP32 accumulators
-constexpr int THREADS = 192;            // 6 warps
+constexpr uint32_t TMEM_COLS = 256;     // two 128-column FP32 accumulators
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA, 8 epilogue warps
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -205,7 +210,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 32 * EPI_WARPS); }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -289,19 +294,14 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         int dummy = 0;
         mbar_wait(&done_bar, 0, &dummy);
     } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> FP64 accumulation ----------------
+        // ---------------- epilogue: TMEM -> compensated FP32 pairs ----------------
         const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
+        const int half = (warp - 2) >> 2;                // columns 64*half .. +63
         const int iz = ti * TM + quad * 32 + lane;       // Z row of this thread
-        if (kstages == 0 && iz < a.pz) {
-            for (int jz = tj * TN; jz < tj * TN + TN && jz <= iz && jz < a.pz_x; ++jz) {
-                const int jo = a.colmap ? a.colmap[jz] : jz;
-                if (iz < a.pz_x)
-                    a.G[((size_t)item * a.p_out + (a.colmap ? a.colmap[iz] : iz)) * a.p_out + jo] = 0.0;
-                else
-                    a.Bm[((size_t)item * a.p_out + jo) * a.r + (iz - a.pz_x)] = 0.0;
-            }
-        }
-        for (int c = 0; c < nchunks && kstages > 0; ++c) {
+        float acc[64], cmp[64];
+#pragma unroll
+        for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
+        for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
             if (!mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag)) {
                 abort_flag = 1;
@@ -309,29 +309,40 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 break;
             }
             tc_fence_after();
-            for (int cb = 0; cb < TN / 32; ++cb) {
+#pragma unroll
+            for (int cb = 0; cb < 2; ++cb) {
                 float v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * TN + cb * 32);
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) +
+                                       (uint32_t)(b * TN + half * 64 + cb * 32);
                 tmem_ld32(taddr, v);
-                if (iz >= a.pz) continue;
-                const int jz0 = tj * TN + cb * 32;
-#pragma unroll 4
-                for (int t = 0; t < 32; ++t) {
-                    const int jz = jz0 + t;
-                    if (jz > iz || jz >= a.pz_x) continue;           // lower triangle, X columns
-                    const int jo = a.colmap ? a.colmap[jz] : jz;
-                    double* dst;
-                    if (iz < a.pz_x) {
-                        const int io = a.colmap ? a.colmap[iz] : iz;
-                        dst = a.G + ((size_t)item * a.p_out + io) * a.p_out + jo;
-                    } else {
-                        dst = a.Bm + ((size_t)item * a.p_out + jo) * a.r + (iz - a.pz_x);
-                    }
-                    *dst = (c == 0 ? 0.0 : *dst) + (double)v[t];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {           // TwoSum: acc + cmp carries the sum
+                    const float x = v[t], sacc = acc[cb * 32 + t];
+                    const float s = sacc + x;
+                    const float bb = s - sacc;
+                    const float err = (sacc - (s - bb)) + (x - bb);
+                    acc[cb * 32 + t] = s;
+                    cmp[cb * 32 + t] += err;
                 }
             }
             tc_fence_before();
             mbar_arrive(&acce_bar[b]);
+        }
+        if (iz < a.pz && !abort_flag) {
+            const int jz0 = tj * TN + half * 64;
+#pragma unroll
+            for (int t = 0; t < 64; ++t) {
+                const int jz = jz0 + t;
+                if (jz > iz || jz >= a.pz_x) continue;           // lower triangle, X columns
+                const double val = (double)acc[t] + (double)cmp[t];
+                const int jo = a.colmap ? a.colmap[jz] : jz;
+                if (iz < a.pz_x) {
+                    const int io = a.colmap ? a.colmap[iz] : iz;
+                    a.G[((size_t)item * a.p_out + io) * a.p_out + jo] = val;
+                } else {
+                    a.Bm[((size_t)item * a.p_out + jo) * a.r + (iz - a.pz_x)] = val;
+                }
+            }
         }
     }
     // teardown: make sure no MMA is still writing TMEM, then free it
@@ -433,8 +444,32 @@ __global__ void k_row_lists(const uint32_t* w, const uint8_t* mask, int64_t m, i
     if (threadIdx.x == 0) nrows[item] = carry;
 }
 
-// Fill the upper triangle from the lower one (over the used features only).
-__global__ void k_mirror(double* G, int64_t p_out, const int32_t* colmap, int32_t pz_x)
+// corr[item][c] = sum_t lo[c][t]^2: the lo'lo term of the diagonal, which the
+// three-product split leaves out and which is biased (always positive).  The
+// off-diagonal lo'lo terms are zero-mean and stay out.  One warp per column,
+// fixed summation order.
+__global__ void k_diag_lo(const __nv_bfloat16* zt, int64_t n_pad, int32_t pz_pad, int32_t pz_x,
+                          const int32_t* nrows, double* corr)
+{
+    const int item = blockIdx.y;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= pz_x) return;
+    const __nv_bfloat16* lo = zt + (((int64_t)item * 2 + 1) * pz_pad + c) * n_pad;
+    const int nr = nrows[item];
+    double s = 0.0;
+    for (int t = lane; t < nr; t += 32) {
+        const double v = (double)__bfloat162float(lo[t]);
+        s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) corr[(int64_t)item * pz_x + c] = s;
+}
+
+// Add the diagonal correction and fill the upper triangle from the lower one
+// (over the used features only).
+__global__ void k_mirror(double* G, int64_t p_out, const int32_t* colmap, int32_t pz_x,
+                         const double* corr)
 {
     const int item = blockIdx.y;
     double* g = G + (size_t)item * p_out * p_out;
@@ -442,8 +477,9 @@ __global__ void k_mirror(double* G, int64_t p_out, const int32_t* colmap, int32_
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / pz_x), j = (int)(t % pz_x);
-        if (j <= i) continue;
         const int io = colmap ? colmap[i] : i, jo = colmap ? colmap[j] : j;
+        if (j == i) g[(size_t)io * p_out + io] += corr[(int64_t)item * pz_x + i];
+        if (j <= i) continue;
         g[(size_t)io * p_out + jo] = g[(size_t)jo * p_out + io];
     }
 }
@@ -531,6 +567,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     const size_t per_item = (size_t)2 * pz_pad * n_pad * sizeof(__nv_bfloat16);
     const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (8ull << 30) / per_item));
     DevBuf zt(per_item * group, s);
+    DevBuf corr(sizeof(double) * (size_t)group * pz_x, s);
     auto kern = k_gram_tc;
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     for (int b0 = 0; b0 < B; b0 += group) {
@@ -552,10 +589,15 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         a.err = err.as<int32_t>();
         k_gram_tc<<<dim3((unsigned)ntiles, (unsigned)nb), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
         UOI_CHECK_LAUNCH();
-        dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
-        k_mirror<<<gm, 256, 0, s>>>(G + (size_t)b0 * p_out * p_out, p_out, colmap, pz_x);
+        dim3 gd((unsigned)ceil_div(pz_x, 8), (unsigned)nb);
+        k_diag_lo<<<gd, 256, 0, s>>>(zt.as<__nv_bfloat16>(), n_pad, pz_pad, pz_x,
+                                     nrows.as<int32_t>() + b0, corr.as<double>());
         UOI_CHECK_LAUNCH();
-        count_launch(3);
+        dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
+        k_mirror<<<gm, 256, 0, s>>>(G + (size_t)b0 * p_out * p_out, p_out, colmap, pz_x,
+                                    corr.as<double>());
+        UOI_CHECK_LAUNCH();
+        count_launch(4);
     }
     int32_t h = 0;
     UOI_CUDA(cudaMemcpyAsync(&h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -67,16 +67,27 @@ void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int6
                 int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
                 double* Bm, cudaStream_t s);
 
+// Tensor-core moments restricted to the pz_x X columns listed in colmap (written
+// into p_out x p_out / p_out x r outputs at the original feature indices).
+void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
+                     int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
+                     const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
+                     cudaStream_t s);
+
 // ---- G3: factor (factor.cu) -------------------------------------------------------
-// A_k = G_k / nk[k] + rho I, lower Cholesky in place (FP64).  status->code set to
+// A_k = G_k / nk[k] + rho I in T, lower Cholesky in place.  status->code set to
 // UOI_ERR_NOT_PD (where = k) on a non-positive pivot.
+template <typename T>
 void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
-                      double* A, DevStatus* status, cudaStream_t s);
-// M_k = A_k^{-1} from the factor in A (T = double or float), then
+                      T* A, DevStatus* status, cudaStream_t s);
+// M_k = A_k^{-1} from the factor L (lower triangle of A), then
 // c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].
 template <typename T>
-void inverse_and_rhs(const double* L, const double* Bm, const double* nk, int64_t p, int64_t r,
+void inverse_and_rhs(const T* L, const double* Bm, const double* nk, int64_t p, int64_t r,
                      int32_t B, T* Linv, T* M, T* c, cudaStream_t s);
+// XtY[j*r + e] = sum_t X[t,j] Y[t,e] for few responses (split over rows, fixed order).
+void xty_small(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
+               int64_t r, double* XtY, cudaStream_t s);
 
 // ---- G4: ADMM (admm.cu) -------------------------------------------------------------
 template <typename T>
@@ -102,6 +113,9 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
 
 // ---- G5/G6/G7: supports, OLS, loss, bagging (estimate.cu) -----------------------------
 void family_init(uint64_t* fam, int64_t words, cudaStream_t s);
+// Union of all family supports as an increasing column list; returns its size.
+int32_t union_columns(const uint64_t* family, int64_t count, int64_t p, int32_t* cols,
+                      cudaStream_t s);
 void family_mask_tail(uint64_t* fam, int64_t count, int64_t p, cudaStream_t s);
 // losses[(k*q + j)*r + e] = held-out squared error sum of the OLS fit on support
 // S_{j,e} from training moments (Gt, Bt) and evaluation moments (Ge, Be, yye);

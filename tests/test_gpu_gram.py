@@ -1,10 +1,10 @@
 """Weighted moments (G1) through the C ABI against the oracle's triple loops (GPU).
 
 FP64 CUDA-core form: within 1e-13 of the largest entry.  Tensor-core form
-(split bf16, FP32 accumulation per 4096 rows, FP64 sums): within 2e-6 of the
-largest diagonal entry, which is the error budget derived in gram_tc.cu
-(2^-17 split residue, 2^-16 dropped lo*lo term, FP32 accumulation over at
-most 4096 rows).  Sizes span several 128 x 256 tiles, ragged feature counts
+(split bf16, FP32 tensor-core accumulation per 128 rows, compensated sums):
+within 2e-6 of the largest diagonal entry, the budget derived in gram_tc.cu
+(<= 5e-7 from 24 truncating accumulation steps, 2^-17 split residue and the
+zero-mean off-diagonal lo*lo term averaged over the sample).  Sizes span several 128 x 256 tiles, ragged feature counts
 and a sample longer than one accumulation chunk.
 """
 import numpy as np
@@ -49,6 +49,7 @@ def test_moments_tc_zero_weight_rows_and_single_row():
     w[0, 17] = 3                       # one row, weight 3
     w[1, :] = 1
     Gtc, Btc = native.weighted_moments(X, Y, w, precision=native.PREC_MIXED)
-    np.testing.assert_allclose(Gtc[0], 3.0 * np.outer(X[17], X[17]), rtol=2e-6, atol=1e-12)
+    # a single row: the off-diagonal lo*lo term (<= 2^-16 relative) does not average out
+    np.testing.assert_allclose(Gtc[0], 3.0 * np.outer(X[17], X[17]), rtol=4e-5, atol=1e-12)
     Gr, Br = oracle.weighted_moments(X, Y, w[1])
     assert np.max(np.abs(Gtc[1] - Gr)) <= 2e-6 * np.max(np.diag(Gr))
