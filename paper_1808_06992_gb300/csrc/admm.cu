@@ -632,4 +632,14 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
 template void admm_solve<double>(const AdmmProblem<double>&, cudaStream_t);
 template void admm_solve<float>(const AdmmProblem<float>&, cudaStream_t);
 
+template <typename T>
+bool admm_solve_resident_with(const AdmmProblem<T>& P, int32_t* chain_next, cudaStream_t s)
+{
+    if (P.G <= 0 || P.p <= 0 || P.r <= 0 || P.q <= 0) return true;
+    const AdmmDev<T> d = to_dev(P);
+    return try_resident<T>(d, chain_next, s);
+}
+
+template bool admm_solve_resident_with<double>(const AdmmProblem<double>&, int32_t*, cudaStream_t);
+
 }  // namespace uoi

@@ -35,9 +35,9 @@ void DevBuf::release()
     bytes = 0;
 }
 
-namespace {
-
 thread_local std::string g_last_error;
+
+namespace {
 
 void ensure_pool()
 {

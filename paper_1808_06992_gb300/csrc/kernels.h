@@ -6,7 +6,12 @@
 
 #include "common.cuh"
 
+#include <string>
+
 namespace uoi {
+
+// Detail text of the last error on this thread (uoi_get_last_error_detail).
+extern thread_local std::string g_last_error;
 
 // ---- memory ------------------------------------------------------------------
 // Stream-ordered device buffer from the device's default memory pool.
@@ -110,6 +115,10 @@ struct AdmmProblem {
 };
 template <typename T>
 void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
+// Resident schedule only, with the caller's zeroed per-group chain counters
+// (G int32).  Returns false (launching nothing) when p is too large for it.
+template <typename T>
+bool admm_solve_resident_with(const AdmmProblem<T>& P, int32_t* chain_next, cudaStream_t s);
 
 // ---- G5/G6/G7: supports, OLS, loss, bagging (estimate.cu) -----------------------------
 void family_init(uint64_t* fam, int64_t words, cudaStream_t s);

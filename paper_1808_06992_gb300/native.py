@@ -76,6 +76,8 @@ def lib():
         L.lasso_admm_batch.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d, i32, i32,
                                        i32, vp, vp, vp, vp]
         L.uoi_weighted_moments.argtypes = [vp, vp, i64, i64, i64, vp, i32, i32, vp, vp, vp]
+        L.lasso_admm_batch_noalloc.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d,
+                                               i32, i32, vp, vp, vp, vp]
         L.uoi_status_string.argtypes = [C.c_int]
         L.uoi_status_string.restype = C.c_char_p
         L.uoi_get_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
@@ -85,7 +87,8 @@ def lib():
 
 
 EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_var_fit", "uoi_fit_traced",
-            "lasso_admm_batch", "uoi_weighted_moments", "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
+            "lasso_admm_batch", "lasso_admm_batch_noalloc", "uoi_weighted_moments",
+            "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
 
 
 class UoiError(RuntimeError):
@@ -267,6 +270,32 @@ def weighted_moments(X, Y, weights, precision=PREC_FP64, stream=None):
     _check(lib().uoi_weighted_moments(_ptr(X), _ptr(Y), n, p, r, _ptr(w), B, precision, _ptr(G),
                                       _ptr(Bm), stream))
     return G, Bm
+
+
+def lasso_admm_batch_noalloc(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6,
+                             max_iter=1000, warm_start=WARM_PATH, stream=None):
+    """lasso_admm_batch without device allocation; every array must be a CUDA tensor."""
+    X = _prep(X, np.float64)
+    Y = _prep(Y, np.float64)
+    if Y.ndim == 1:
+        Y = Y.reshape(-1, 1)
+    n, p = X.shape
+    r = Y.shape[1]
+    lam = _prep(lambdas, np.float64)
+    q = lam.shape[0]
+    if weights is None:
+        B, w = 1, None
+    else:
+        w = _prep(weights, np.uint32).reshape(-1, n)
+        B = w.shape[0]
+    beta = _empty(X, (B, q, r, p), np.float64)
+    iters = _empty(X, (B, q, r), np.int32)
+    conv = _empty(X, (B, q, r), np.uint8)
+    st = lib().lasso_admm_batch_noalloc(_ptr(X), _ptr(Y), n, p, r, _ptr(w), B, _ptr(lam), q, rho,
+                                        abs_tol, rel_tol, max_iter, warm_start, _ptr(beta),
+                                        _ptr(iters), _ptr(conv), stream)
+    _check(st)
+    return dict(beta=beta, iters=iters, conv=conv, status=st)
 
 
 def shutdown():
