@@ -39,6 +39,12 @@ def parse():
     ap.add_argument("--warm", default="none", choices=["none", "path"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # size overrides for profiling captures on a small case (the line is then not a
+    # bench line: config.overrides says so)
+    ap.add_argument("--B1", type=int)
+    ap.add_argument("--B2", type=int)
+    ap.add_argument("--q", type=int)
+    ap.add_argument("--rows", type=int, help="keep only the first ROWS rows of the design")
     return ap.parse_args()
 
 
@@ -114,9 +120,29 @@ def workload(wid):
 
 def fit_kwargs(w, args):
     from paper_1808_06992_gb300 import native
-    return dict(B1=w.B1, B2=w.B2, q=w.q, block_len=w.block_len, bagging=w.bagging,
+    return dict(B1=args.B1 or w.B1, B2=args.B2 or w.B2, q=args.q or w.q, block_len=w.block_len,
+                bagging=w.bagging,
                 precision=native.PREC_MIXED if args.precision == "mixed" else native.PREC_FP64,
                 warm_start=native.WARM_PATH if args.warm == "path" else native.WARM_NONE)
+
+
+def traffic_per_launch(kernel):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel's source
+    still matches the hash recorded with it (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = {"k_gram_tc": "gram_tc.cu", "k_stream_gemm": "admm.cu"}[kernel]
+    try:
+        with open(os.path.join(ROOT, "paper_1808_06992_gb300", "csrc", src), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(path) as f:
+            for ln in f:
+                fields = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
+                if fields.get("kernel") == kernel and fields.get("source_sha") == sha:
+                    return float(fields["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
 
 
 def algorithmic_gram_flops(m, p, r, rows):
@@ -226,9 +252,12 @@ def main():
     from paper_1808_06992_gb300 import native
     native.lib()
     w, X, Y = workload(args.workload)
+    if args.rows:
+        X, Y = np.ascontiguousarray(X[:args.rows]), np.ascontiguousarray(Y[:args.rows])
     m, p = X.shape
     r = Y.shape[1]
     kw = fit_kwargs(w, args)
+    overrides = {k: getattr(args, k) for k in ("B1", "B2", "q", "rows") if getattr(args, k)}
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream().cuda_stream
@@ -263,32 +292,54 @@ def main():
     ms_step = ms / args.steps
     fits_s = world * args.steps / (ms / 1e3)
     cols = w.B1 * w.q * r
-    # dominant kernel: the tensor-core (mixed) or FP64 Gram, timed by the library's
-    # events on the launch stream
-    gram_ms = float(np.mean([d["ms_gram"] for d in diags]))
-    admm_ms = float(np.mean([d["ms_admm"] for d in diags]))
-    fac_ms = float(np.mean([d["ms_factor"] for d in diags]))
-    est_ms = float(np.mean([d["ms_estimation"] for d in diags]))
-    launches = int(np.mean([d["gpu_launches"] for d in diags]))
+    # Per-kernel live timing: the library records CUDA events on the launch stream
+    # around every tensor-core Gram and streaming x-update launch of the step and
+    # reports their algorithmic work (flops of the math, not of the split products).
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peaks = json.load(f)
     except OSError:
         pass
-    rows_sel = w.B1 * m
-    flops = algorithmic_gram_flops(m, p, r, rows_sel)
-    achieved = flops / (gram_ms / 1e3) / 1e12
-    if args.precision == "mixed":
-        peak = peaks.get("bf16_tflops", 1900.0) / 4.0     # 4 bf16 products per FP32-accurate term
-        peak_note = "measured bf16 burst / 4 (two-piece bf16 split, 4 products)"
-    else:
-        peak = 1.25
-        peak_note = "nominal FP64 rate (no measured FP64 peak)"
-    roofline = {"kernel": "selection Gram (moments)", "bound": "tensor" if args.precision == "mixed" else "alu",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_note,
-                "stage_ms": {"gram": gram_ms, "factor": fac_ms, "admm": admm_ms, "estimation": est_ms}}
+    bf16 = peaks.get("bf16_tflops")
+    hbm = peaks.get("hbm_gbs")
+    smax = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * smax * 1e6 / 1e12      # CUDA-core FP32 FMA rate at max clock
+    fp64_peak = 1.25                                     # nominal GB300 FP64 (no measured figure)
+    kernels = []
+    ms_g = sum(d["ms_gram_tc"] for d in diags)
+    if ms_g > 0:
+        fl = sum(d["flops_gram_tc"] for d in diags)
+        n = sum(d["n_gram_tc"] for d in diags)
+        ach = fl / (ms_g / 1e3) / 1e12
+        peak = (bf16 / 3.0) if bf16 else 1900.0 / 3.0
+        kernels.append({"kernel": "k_gram_tc (tensor-core Gram, split bf16 x3)", "bound": "tensor",
+                        "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "traffic": traffic_per_launch("k_gram_tc"), "launches_per_step": n / args.steps,
+                        "ms_per_step": ms_g / args.steps,
+                        "peak_source": ("measured bf16 burst / 3 (three bf16 products per "
+                                        "FP32-accurate multiply-add)" if bf16 else "fallback 1.9 PF / 3"),
+                        "tensor_pipe_frac": ach * 3.0 / (bf16 or 1900.0)})
+    ms_x = sum(d["ms_xupdate"] for d in diags)
+    if ms_x > 0:
+        fl = sum(d["flops_xupdate"] for d in diags)
+        by = sum(d["bytes_xupdate"] for d in diags)
+        n = sum(d["n_xupdate"] for d in diags)
+        ach = fl / (ms_x / 1e3) / 1e12
+        peak = fp32_peak if args.precision == "mixed" else fp64_peak
+        kernels.append({"kernel": "k_stream_gemm (ADMM x-update + fused epilogue)", "bound": "alu",
+                        "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "traffic": traffic_per_launch("k_stream_gemm"), "launches_per_step": n / args.steps,
+                        "ms_per_step": ms_x / args.steps,
+                        "hbm_gbs_algorithmic": by / (ms_x / 1e3) / 1e9,
+                        "hbm_frac_algorithmic": (by / (ms_x / 1e3) / 1e9) / hbm if hbm else None,
+                        "peak_source": ("152 SMs x 128 FP32 lanes x 2 x sm_max_mhz" if args.precision == "mixed"
+                                        else "nominal FP64 1.25 TFLOP/s")})
+    kernels.sort(key=lambda k: -k["ms_per_step"])
+    roofline = kernels[0] if kernels else None
+    stage_ms = {k: float(np.mean([d[f"ms_{k}"] for d in diags]))
+                for k in ("gram", "factor", "admm", "estimation")}
+    launches = int(np.mean([d["gpu_launches"] for d in diags]))
     # end to end: host (pinned) inputs, result read back, through the public API
     e2e = None
     if args.e2e_steps > 0:
@@ -317,9 +368,11 @@ def main():
                 "config": {"workload": w.name, "n": m, "p": p, "r": r, "B1": w.B1, "q": w.q,
                            "B2": w.B2, "precision": args.precision, "warm_start": args.warm,
                            "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "inputs larger than L2 (X is %.0f MB)" % (X.nbytes / 1e6)},
+                           "l2": "inputs larger than L2 (X is %.0f MB)" % (X.nbytes / 1e6),
+                           **({"overrides": overrides} if overrides else {})},
                 "solves_per_s": fits_s * cols,
-                "roofline": roofline, "clocks": clocks, "gpu_launches": launches * args.steps,
+                "roofline": roofline, "roofline_other": kernels[1:], "stage_ms": stage_ms,
+                "clocks": clocks, "gpu_launches": launches * args.steps,
                 "e2e": e2e, "cpu_baseline": cpu,
                 "diag": diags[-1]}
         print(json.dumps(line), flush=True)

@@ -95,6 +95,16 @@ typedef struct uoi_diag {
     int32_t  admm_max_iterations; /* largest per-column iteration count                  */
     int64_t  ols_singular;        /* supports whose OLS took the regularised fallback    */
     int64_t  gpu_launches;        /* kernels this library launched during the fit        */
+    /* Live timing of the two kernels that bound a fit, from CUDA events on their
+     * launch stream, with their algorithmic work (flops of the math, not of the
+     * split products or padding; bytes of the streams the math must move). */
+    float    ms_gram_tc;          /* tensor-core Gram launches (mixed form)              */
+    int64_t  n_gram_tc;
+    double   flops_gram_tc;       /* 2 n_k (p(p+1)/2 + p r) per bootstrap item           */
+    float    ms_xupdate;          /* streaming ADMM x-update launches                    */
+    int64_t  n_xupdate;
+    double   flops_xupdate;       /* 2 p^2 per active column-iteration                   */
+    double   bytes_xupdate;       /* M once per group-iteration + 6 p-vectors per column */
 } uoi_diag;
 
 /* Optional intermediate results of a fit, for testing (every pointer nullable,

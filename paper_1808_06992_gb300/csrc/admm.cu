@@ -604,8 +604,10 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
                                                           ub.as<T>(), nb.as<T>(), RT);
             } else {
                 dim3 grid((unsigned)RT, (unsigned)ceil_div(nchains, SG_TN), (unsigned)P.G);
+                ktimer_begin(TK_XUPDATE, s);
                 k_stream_gemm<T><<<grid, 256, 0, s>>>(d, S, cur, V[cur], V[cur ^ 1], zb.as<T>(),
                                                       ub.as<T>(), nb.as<T>(), RT);
+                ktimer_end(TK_XUPDATE, s, 0.0, 0.0);
             }
             UOI_CHECK_LAUNCH();
             dim3 gc((unsigned)ceil_div(nchains, 8), (unsigned)P.G);

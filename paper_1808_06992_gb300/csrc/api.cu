@@ -38,6 +38,63 @@ void DevBuf::release()
 thread_local std::string g_last_error;
 
 namespace {
+struct PendingTimes {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    KernelTotals tot;
+    cudaEvent_t open = nullptr;
+};
+PendingTimes g_kt[TK_COUNT];
+}  // namespace
+
+void ktimer_reset()
+{
+    for (auto& k : g_kt) {
+        for (auto& e : k.ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        k.ev.clear();
+        k.tot = KernelTotals{};
+        if (k.open) { cudaEventDestroy(k.open); k.open = nullptr; }
+    }
+}
+
+void ktimer_begin(TimedKernel k, cudaStream_t s)
+{
+    cudaEvent_t e;
+    UOI_CUDA(cudaEventCreate(&e));
+    UOI_CUDA(cudaEventRecord(e, s));
+    g_kt[k].open = e;
+}
+
+void ktimer_end(TimedKernel k, cudaStream_t s, double flops, double bytes)
+{
+    cudaEvent_t e;
+    UOI_CUDA(cudaEventCreate(&e));
+    UOI_CUDA(cudaEventRecord(e, s));
+    g_kt[k].ev.push_back({ g_kt[k].open, e });
+    g_kt[k].open = nullptr;
+    g_kt[k].tot.launches += 1;
+    g_kt[k].tot.flops += flops;
+    g_kt[k].tot.bytes += bytes;
+}
+
+void ktimer_add_work(TimedKernel k, double flops, double bytes)
+{
+    g_kt[k].tot.flops += flops;
+    g_kt[k].tot.bytes += bytes;
+}
+
+KernelTotals ktimer_total(TimedKernel k)
+{
+    KernelTotals t = g_kt[k].tot;
+    t.ms = 0.f;
+    for (auto& e : g_kt[k].ev) {
+        cudaEventSynchronize(e.second);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) t.ms += ms;
+    }
+    return t;
+}
+
+namespace {
 
 void ensure_pool()
 {
@@ -211,9 +268,12 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     if (marks) { marks[0] = t0; marks[1] = t1; marks[2] = t2; marks[3] = t3; }
 }
 
-struct IterStats { int64_t cols = 0, noncon = 0, iters = 0; int32_t maxit = 0; };
+struct IterStats { int64_t cols = 0, noncon = 0, iters = 0, group_iters = 0; int32_t maxit = 0; };
 
-IterStats iteration_stats(const int32_t* iters_d, const uint8_t* conv_d, int64_t n, cudaStream_t s)
+// Column statistics; group_iters = sum over groups of the iterations during which
+// the group had an active column (a path chain runs its lambdas back to back).
+IterStats iteration_stats(const int32_t* iters_d, const uint8_t* conv_d, int64_t n, cudaStream_t s,
+                          int32_t G = 0, int32_t q = 0, int64_t r = 0, int32_t warm = 0)
 {
     std::vector<int32_t> it((size_t)n);
     std::vector<uint8_t> cv((size_t)n);
@@ -226,6 +286,22 @@ IterStats iteration_stats(const int32_t* iters_d, const uint8_t* conv_d, int64_t
         st.iters += it[i];
         st.maxit = std::max(st.maxit, it[i]);
         st.noncon += cv[i] ? 0 : 1;
+    }
+    if (G > 0 && (int64_t)G * q * r == n) {
+        for (int32_t g = 0; g < G; ++g) {
+            int64_t longest = 0;
+            if (warm) {
+                for (int64_t e = 0; e < r; ++e) {
+                    int64_t chain = 0;
+                    for (int32_t j = 0; j < q; ++j) chain += it[((int64_t)g * q + j) * r + e];
+                    longest = std::max(longest, chain);
+                }
+            } else {
+                for (int64_t c = 0; c < (int64_t)q * r; ++c)
+                    longest = std::max<int64_t>(longest, it[(int64_t)g * q * r + c]);
+            }
+            st.group_iters += longest;
+        }
     }
     return st;
 }
@@ -241,6 +317,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     ensure_pool();
     cudaStream_t s = (cudaStream_t)prm->stream;
     const int64_t launches0 = g_launches;
+    ktimer_reset();
     StageTimer tm(s);
     const int tstart = tm.mark();
     const int32_t B1 = prm->B1, B2 = prm->B2, q = prm->q;
@@ -375,7 +452,16 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         loss_o.finish(s);
     }
     UOI_CUDA(cudaStreamSynchronize(s));
-    IterStats its = iteration_stats(iters_b.as<int32_t>(), conv_b.as<uint8_t>(), ncol, s);
+    IterStats its = iteration_stats(iters_b.as<int32_t>(), conv_b.as<uint8_t>(), ncol, s, B1, q, r,
+                                    prm->warm_start);
+    {
+        // algorithmic work of the streaming x-update: 2 p^2 flops per active
+        // column-iteration; M once per group-iteration plus the c, z, u, V reads
+        // and z, u, V writes of each active column-iteration
+        const double tsz = mixed ? 4.0 : 8.0;
+        ktimer_add_work(TK_XUPDATE, 2.0 * (double)p * p * (double)its.iters,
+                        (double)its.group_iters * p * p * tsz + 7.0 * p * tsz * (double)its.iters);
+    }
     std::vector<int32_t> sg((size_t)(B2 * q * r));
     UOI_CUDA(cudaMemcpyAsync(sg.data(), sing.ptr, sizeof(int32_t) * sg.size(), cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));
@@ -396,6 +482,16 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         diag->admm_max_iterations = its.maxit;
         diag->ols_singular = nsing;
         diag->gpu_launches = g_launches - launches0;
+        if (diag->struct_size == 0 || diag->struct_size >= sizeof(uoi_diag)) {
+            const KernelTotals g = ktimer_total(TK_GRAM_TC), x = ktimer_total(TK_XUPDATE);
+            diag->ms_gram_tc = g.ms;
+            diag->n_gram_tc = g.launches;
+            diag->flops_gram_tc = g.flops;
+            diag->ms_xupdate = x.ms;
+            diag->n_xupdate = x.launches;
+            diag->flops_xupdate = x.flops;
+            diag->bytes_xupdate = x.bytes;
+        }
     }
     return (its.noncon > 0 || nsing > 0) ? UOI_OK_WITH_WARNINGS : UOI_OK;
 }

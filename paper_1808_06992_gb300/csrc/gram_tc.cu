@@ -587,8 +587,10 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         a.nrows = nrows.as<int32_t>() + b0; a.colmap = colmap;
         a.G = G + (size_t)b0 * p_out * p_out; a.Bm = Bm + (size_t)b0 * p_out * r;
         a.err = err.as<int32_t>();
+        ktimer_begin(TK_GRAM_TC, s);
         k_gram_tc<<<dim3((unsigned)ntiles, (unsigned)nb), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
         UOI_CHECK_LAUNCH();
+        ktimer_end(TK_GRAM_TC, s, 0.0, 0.0);
         dim3 gd((unsigned)ceil_div(pz_x, 8), (unsigned)nb);
         k_diag_lo<<<gd, 256, 0, s>>>(zt.as<__nv_bfloat16>(), n_pad, pz_pad, pz_x,
                                      nrows.as<int32_t>() + b0, corr.as<double>());
@@ -600,9 +602,17 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         count_launch(4);
     }
     int32_t h = 0;
+    std::vector<int32_t> nr((size_t)B);
     UOI_CUDA(cudaMemcpyAsync(&h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaMemcpyAsync(nr.data(), nrows.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));
     if (h) throw Error(h, "tensor-core Gram: a bounded pipeline wait expired");
+    // algorithmic work: the lower triangle of X^T W X plus X^T W Y over the rows used
+    double used_rows = 0.0;
+    for (int32_t v : nr) used_rows += (double)v;
+    ktimer_add_work(TK_GRAM_TC,
+                    2.0 * used_rows * ((double)pz_x * (pz_x + 1) / 2.0 + (double)pz_x * r),
+                    used_rows * (double)(pz_x + r) * 8.0);
 }
 
 void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,

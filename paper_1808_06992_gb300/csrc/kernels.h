@@ -13,6 +13,18 @@ namespace uoi {
 // Detail text of the last error on this thread (uoi_get_last_error_detail).
 extern thread_local std::string g_last_error;
 
+// ---- per-kernel timing --------------------------------------------------------
+// CUDA events recorded on the launch stream around the launches of the kernels
+// that bound a fit (the tensor-core Gram and the ADMM x-update), with their
+// algorithmic work.  Resolved after the fit's final synchronisation.
+enum TimedKernel { TK_GRAM_TC = 0, TK_XUPDATE = 1, TK_COUNT = 2 };
+struct KernelTotals { float ms = 0.f; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
+void ktimer_reset();
+void ktimer_begin(TimedKernel k, cudaStream_t s);
+void ktimer_end(TimedKernel k, cudaStream_t s, double flops, double bytes);
+void ktimer_add_work(TimedKernel k, double flops, double bytes);
+KernelTotals ktimer_total(TimedKernel k);   // synchronises on the recorded events
+
 // ---- memory ------------------------------------------------------------------
 // Stream-ordered device buffer from the device's default memory pool.
 struct DevBuf {

@@ -44,6 +44,9 @@ class UoiDiag(C.Structure):
         ("admm_columns", C.c_int64), ("admm_nonconverged", C.c_int64),
         ("admm_iterations", C.c_int64), ("admm_max_iterations", C.c_int32),
         ("ols_singular", C.c_int64), ("gpu_launches", C.c_int64),
+        ("ms_gram_tc", C.c_float), ("n_gram_tc", C.c_int64), ("flops_gram_tc", C.c_double),
+        ("ms_xupdate", C.c_float), ("n_xupdate", C.c_int64), ("flops_xupdate", C.c_double),
+        ("bytes_xupdate", C.c_double),
     ]
 
     def as_dict(self):
