@@ -239,19 +239,26 @@ __device__ __forceinline__ void admm_elem(const AdmmDev<T>& P, T acc, int g, int
     part[0] += d * d; part[1] += dz * dz; part[2] += x * x; part[3] += zn * zn; part[4] += un * un;
 }
 
-// x-update tile: 128 rows x 64 chains, K steps of 16, 256 threads with an
-// 8 x 4 register block each (rows 8*ty .. +7, chains 4*tx .. +3).  The soft
-// threshold, dual update and partial norms run in the epilogue; V = z - u of the
-// next iteration is written to the other buffer.
+// x-update tile: 128 rows x 64 chains, 256 threads with an 8 x 4 register block
+// each (rows 8*ty .. +7, chains 4*tx .. +3).  M is symmetric, so the tile's
+// column k (rows i0 .. i0+127) is the contiguous segment M[k][i0 .. i0+127]:
+// it is copied row by row with coalesced loads and conflict-free stores.  The
+// next K step is prefetched into registers while the current one is consumed
+// (two shared-memory buffers).  The soft threshold, dual update and partial
+// norms run in the epilogue; V = z - u of the next iteration goes to the other
+// V buffer.
 constexpr int SG_TM = 128;
 constexpr int SG_TN = 64;
-constexpr int SG_TK = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_stream_gemm(AdmmDev<T> P, StreamState S, int cur, const T* __restrict__ Vc, T* Vn, T* z, T* u,
               T* norms, int RT)
 {
+    constexpr int TK = sizeof(T) == 8 ? 8 : 16;              // K per stage
+    constexpr int LDB = SG_TN + 4;
+    constexpr int A_PER = SG_TM * TK / 256;                  // M elements per thread per stage
+    constexpr int B_PER = SG_TN * TK / 256;                  // V elements per thread per stage
     const int g = blockIdx.z;
     const int rt = blockIdx.x;
     const int i0 = rt * SG_TM;
@@ -265,14 +272,44 @@ k_stream_gemm(AdmmDev<T> P, StreamState S, int cur, const T* __restrict__ Vc, T*
     const int ncols = min(SG_TN, count - s0);
     const int32_t* act = S.act[cur] + (size_t)g * S.nchains + s0;
     const int p = P.p;
-    const T* Mg = P.M + (size_t)g * p * p;
+    const T* __restrict__ Mg = P.M + (size_t)g * p * p;
 
-    __shared__ __align__(16) T As[SG_TK][SG_TM];
-    __shared__ __align__(16) T Bs[SG_TK][SG_TN];
+    __shared__ __align__(16) T As[2][TK][SG_TM];
+    __shared__ __align__(16) T Bs[2][TK][LDB];
     __shared__ int32_t slots[SG_TN];
     __shared__ T red[8][SG_TN][5];
     if (threadIdx.x < SG_TN) slots[threadIdx.x] = threadIdx.x < ncols ? act[threadIdx.x] : -1;
     __syncthreads();
+
+    T ra[A_PER], rb[B_PER];
+    auto fetch = [&](int kb) {
+#pragma unroll
+        for (int h = 0; h < A_PER; ++h) {                    // A: row kb+kk of M, cols i0..
+            const int e = threadIdx.x + 256 * h;
+            const int kk = e / SG_TM, il = e % SG_TM;
+            const int k = kb + kk, i = i0 + il;
+            ra[h] = (k < p && i < p) ? Mg[(size_t)k * p + i] : T(0);
+        }
+#pragma unroll
+        for (int h = 0; h < B_PER; ++h) {                    // B: V[slot][kb .. kb+TK)
+            const int e = threadIdx.x + 256 * h;
+            const int cl = e / TK, kk = e % TK;
+            const int sl = slots[cl], k = kb + kk;
+            rb[h] = (sl >= 0 && k < p) ? Vc[(size_t)sl * p + k] : T(0);
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < A_PER; ++h) {
+            const int e = threadIdx.x + 256 * h;
+            As[buf][e / SG_TM][e % SG_TM] = ra[h];
+        }
+#pragma unroll
+        for (int h = 0; h < B_PER; ++h) {
+            const int e = threadIdx.x + 256 * h;
+            Bs[buf][e % TK][e / TK] = rb[h];
+        }
+    };
 
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     T acc[8][4];
@@ -280,32 +317,28 @@ k_stream_gemm(AdmmDev<T> P, StreamState S, int cur, const T* __restrict__ Vc, T*
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    for (int kb = 0; kb < p; kb += SG_TK) {
-        // M tile: 128 rows x 16 k (rows contiguous in k); V tile: 64 chains x 16 k
-        for (int e = threadIdx.x; e < SG_TM * SG_TK; e += 256) {
-            const int il = e / SG_TK, kk = e % SG_TK;
-            const int i = i0 + il, k = kb + kk;
-            As[kk][il] = (i < p && k < p) ? Mg[(size_t)i * p + k] : T(0);
-        }
-        for (int e = threadIdx.x; e < SG_TN * SG_TK; e += 256) {
-            const int cl = e / SG_TK, kk = e % SG_TK;
-            const int sl = slots[cl], k = kb + kk;
-            Bs[kk][cl] = (sl >= 0 && k < p) ? Vc[(size_t)sl * p + k] : T(0);
-        }
-        __syncthreads();
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int kb = 0; kb < p; kb += TK) {
+        const bool more = kb + TK < p;
+        if (more) fetch(kb + TK);                            // in flight during the FMAs
 #pragma unroll
-        for (int kk = 0; kk < SG_TK; ++kk) {
+        for (int kk = 0; kk < TK; ++kk) {
             T a[8], b[4];
 #pragma unroll
-            for (int w = 0; w < 8; ++w) a[w] = As[kk][ty * 8 + w];
+            for (int w = 0; w < 8; ++w) a[w] = As[buf][kk][ty * 8 + w];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) b[w] = Bs[kk][tx * 4 + w];
+            for (int w = 0; w < 4; ++w) b[w] = Bs[buf][kk][tx * 4 + w];
 #pragma unroll
             for (int w = 0; w < 8; ++w)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[w][v] = fma(a[w], b[v], acc[w][v]);
         }
+        if (more) stash(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
     // epilogue: thread owns chains 4*tx + v and rows 8*ty + w
     T part[4][5];

@@ -356,46 +356,60 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 }
 
 // Gather rows with positive weight, scale by sqrt(w), split into bf16 hi/lo and
-// write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].
-__global__ void k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy,
-                                  int32_t pz_x, int32_t r, const int32_t* colmap,
-                                  const int32_t* rowlist, const double* rowscale,
-                                  const int32_t* nrows, int64_t m, int64_t n_pad, int32_t pz_pad,
-                                  __nv_bfloat16* out)
+// write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].  A block
+// covers 64 sample rows x 32 columns: coalesced FP64 reads along the columns of
+// a row, paired bf16 stores along the rows of a column.  It also writes the sum
+// of lo^2 of each column over its 64 rows (losq[(item*row_tiles + tile)*pz_x + col]),
+// from which the diagonal correction is reduced in a fixed order.
+__global__ void __launch_bounds__(256)
+k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, int32_t pz_x,
+                  int32_t r, const int32_t* colmap, const int32_t* rowlist,
+                  const double* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
+                  int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, double* losq)
 {
-    __shared__ double tile[32][33];
+    __shared__ double tile[64][33];
     const int item = blockIdx.z;
-    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int tile_r = blockIdx.x;
+    const int64_t t0 = (int64_t)tile_r * 64;
     const int c0 = blockIdx.y * 32;
     const int nr = nrows[item];
     const int pz = pz_x + r;
-    // load: thread (ty, tx) reads rows t0 + ty + 8i, column c0 + tx
-    for (int i = 0; i < 4; ++i) {
-        const int tl = threadIdx.y + 8 * i;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = c0 + tx;
+    int src_col = -1;
+    if (c < pz_x) src_col = colmap ? colmap[c] : c;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int tl = ty + 8 * i;
         const int64_t t = t0 + tl;
-        const int c = c0 + threadIdx.x;
         double v = 0.0;
         if (t < nr && c < pz) {
             const int64_t row = rowlist[(int64_t)item * m + t];
             const double sc = rowscale[(int64_t)item * m + t];
-            if (c < pz_x) v = X[row * ldx + (colmap ? colmap[c] : c)];
-            else v = Y[row * ldy + (c - pz_x)];
-            v *= sc;
+            v = (c < pz_x ? X[row * ldx + src_col] : Y[row * ldy + (c - pz_x)]) * sc;
         }
-        tile[tl][threadIdx.x] = v;
+        tile[tl][tx] = v;
     }
     __syncthreads();
-    // store: thread (ty, tx) writes column c0 + ty + 8i, rows t0 + tx
-    for (int i = 0; i < 4; ++i) {
-        const int cl = threadIdx.y + 8 * i;
-        const int c = c0 + cl;
-        const int64_t t = t0 + threadIdx.x;
-        if (c >= pz_pad || t >= n_pad) continue;
-        const double v = tile[threadIdx.x][cl];
-        const __nv_bfloat16 hi = __double2bfloat16(v);
-        const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
-        out[(((int64_t)item * 2 + 0) * pz_pad + c) * n_pad + t] = hi;
-        out[(((int64_t)item * 2 + 1) * pz_pad + c) * n_pad + t] = lo;
+    // warp ty writes columns c0 + ty + 8j; lane covers rows 2*lane, 2*lane + 1
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int cl = ty + 8 * j;
+        const int cc = c0 + cl;
+        if (cc >= pz_pad) continue;
+        const double v0 = tile[2 * tx][cl], v1 = tile[2 * tx + 1][cl];
+        const __nv_bfloat16 h0 = __double2bfloat16(v0), h1 = __double2bfloat16(v1);
+        const __nv_bfloat16 l0 = __double2bfloat16(v0 - (double)__bfloat162float(h0));
+        const __nv_bfloat16 l1 = __double2bfloat16(v1 - (double)__bfloat162float(h1));
+        const int64_t base_hi = (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0 + 2 * tx;
+        const int64_t base_lo = (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0 + 2 * tx;
+        *reinterpret_cast<__nv_bfloat162*>(out + base_hi) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(out + base_lo) = __halves2bfloat162(l0, l1);
+        if (cc < pz_x) {
+            const double f0 = (double)__bfloat162float(l0), f1 = (double)__bfloat162float(l1);
+            const double sq = warp_sum(f0 * f0 + f1 * f1);
+            if (tx == 0) losq[((int64_t)item * row_tiles + tile_r) * pz_x + cc] = sq;
+        }
     }
 }
 
@@ -446,24 +460,18 @@ __global__ void k_row_lists(const uint32_t* w, const uint8_t* mask, int64_t m, i
 
 // corr[item][c] = sum_t lo[c][t]^2: the lo'lo term of the diagonal, which the
 // three-product split leaves out and which is biased (always positive).  The
-// off-diagonal lo'lo terms are zero-mean and stay out.  One warp per column,
-// fixed summation order.
-__global__ void k_diag_lo(const __nv_bfloat16* zt, int64_t n_pad, int32_t pz_pad, int32_t pz_x,
+// off-diagonal lo'lo terms are zero-mean and stay out.  Sums the per-64-row
+// partials of k_split_transpose in a fixed order.
+__global__ void k_diag_lo(const double* losq, int32_t row_tiles, int32_t pz_x,
                           const int32_t* nrows, double* corr)
 {
     const int item = blockIdx.y;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= pz_x) return;
-    const __nv_bfloat16* lo = zt + (((int64_t)item * 2 + 1) * pz_pad + c) * n_pad;
-    const int nr = nrows[item];
+    const int tiles = (nrows[item] + 63) / 64;
     double s = 0.0;
-    for (int t = lane; t < nr; t += 32) {
-        const double v = (double)__bfloat162float(lo[t]);
-        s = fma(v, v, s);
-    }
-    s = warp_sum(s);
-    if (lane == 0) corr[(int64_t)item * pz_x + c] = s;
+    for (int t = 0; t < tiles && t < row_tiles; ++t) s += losq[((int64_t)item * row_tiles + t) * pz_x + c];
+    corr[(int64_t)item * pz_x + c] = s;
 }
 
 // Add the diagonal correction and fill the upper triangle from the lower one
@@ -540,7 +548,6 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     if (!gram_tc_available()) throw Error(UOI_ERR_UNSUPPORTED, "tcgen05 Gram needs sm_103a");
     const int32_t pz = pz_x + (int32_t)r;
     const int32_t pz_pad = (int32_t)ceil_div(pz, TN) * TN;
-    const int64_t n_pad = ceil_div(m, TK) * TK;
     // tile list of the lower triangle (rows of Z x X columns)
     std::vector<int32_t> tiles;
     const int nti = (int)ceil_div(pz, TM);
@@ -563,21 +570,29 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     } else {
         throw Error(UOI_ERR_INVALID_ARG, "tensor-core moments need weights or a mask");
     }
+    std::vector<int32_t> nr((size_t)B);
+    UOI_CUDA(cudaMemcpyAsync(nr.data(), nrows.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    int32_t max_rows = 1;
+    for (int32_t v : nr) max_rows = std::max(max_rows, v);
+    const int64_t n_pad = ceil_div(max_rows, TK) * TK;        // K extent actually used
+    const int32_t row_tiles = (int32_t)(n_pad / 64);
     // items per pass bounded by the size of the split copies (<= 8 GB)
     const size_t per_item = (size_t)2 * pz_pad * n_pad * sizeof(__nv_bfloat16);
     const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (8ull << 30) / per_item));
     DevBuf zt(per_item * group, s);
     DevBuf corr(sizeof(double) * (size_t)group * pz_x, s);
+    DevBuf losq(sizeof(double) * (size_t)group * row_tiles * pz_x, s);
     auto kern = k_gram_tc;
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
-        dim3 gs((unsigned)(n_pad / 32), (unsigned)ceil_div(pz_pad, 32), (unsigned)nb);
-        k_split_transpose<<<gs, dim3(32, 8), 0, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
-                                                     rows.as<int32_t>() + (size_t)b0 * m,
-                                                     scale.as<double>() + (size_t)b0 * m,
-                                                     nrows.as<int32_t>() + b0, m, n_pad, pz_pad,
-                                                     zt.as<__nv_bfloat16>());
+        dim3 gs((unsigned)row_tiles, (unsigned)ceil_div(pz_pad, 32), (unsigned)nb);
+        k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
+                                             rows.as<int32_t>() + (size_t)b0 * m,
+                                             scale.as<double>() + (size_t)b0 * m,
+                                             nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
+                                             zt.as<__nv_bfloat16>(), losq.as<double>());
         UOI_CHECK_LAUNCH();
         const CUtensorMap mA = make_map(zt.ptr, n_pad, pz_pad, 2 * nb, TM);
         const CUtensorMap mB = make_map(zt.ptr, n_pad, pz_pad, 2 * nb, TN);
@@ -591,9 +606,9 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         k_gram_tc<<<dim3((unsigned)ntiles, (unsigned)nb), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
         UOI_CHECK_LAUNCH();
         ktimer_end(TK_GRAM_TC, s, 0.0, 0.0);
-        dim3 gd((unsigned)ceil_div(pz_x, 8), (unsigned)nb);
-        k_diag_lo<<<gd, 256, 0, s>>>(zt.as<__nv_bfloat16>(), n_pad, pz_pad, pz_x,
-                                     nrows.as<int32_t>() + b0, corr.as<double>());
+        dim3 gd((unsigned)ceil_div(pz_x, 256), (unsigned)nb);
+        k_diag_lo<<<gd, 256, 0, s>>>(losq.as<double>(), row_tiles, pz_x, nrows.as<int32_t>() + b0,
+                                     corr.as<double>());
         UOI_CHECK_LAUNCH();
         dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
         k_mirror<<<gm, 256, 0, s>>>(G + (size_t)b0 * p_out * p_out, p_out, colmap, pz_x,
@@ -602,9 +617,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         count_launch(4);
     }
     int32_t h = 0;
-    std::vector<int32_t> nr((size_t)B);
     UOI_CUDA(cudaMemcpyAsync(&h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    UOI_CUDA(cudaMemcpyAsync(nr.data(), nrows.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));
     if (h) throw Error(h, "tensor-core Gram: a bounded pipeline wait expired");
     // algorithmic work: the lower triangle of X^T W X plus X^T W Y over the rows used
