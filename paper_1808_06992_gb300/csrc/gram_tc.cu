@@ -357,58 +357,69 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
 // Gather rows with positive weight, scale by sqrt(w), split into bf16 hi/lo and
 // write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].  A block
-// covers 64 sample rows x 32 columns: coalesced FP64 reads along the columns of
-// a row, paired bf16 stores along the rows of a column.  It also writes the sum
-// of lo^2 of each column over its 64 rows (losq[(item*row_tiles + tile)*pz_x + col]),
-// from which the diagonal correction is reduced in a fixed order.
+// covers 64 sample rows x 128 columns: each warp reads 1 KB row segments (FP64),
+// then writes 128-byte runs of paired bf16 along the rows of each column.  It
+// also writes the sum of lo^2 of each column over its 64 rows
+// (losq[(item*row_tiles + tile)*pz_x + col]), from which the diagonal
+// correction is reduced in a fixed order.
+constexpr int SPLIT_COLS = 128;
 __global__ void __launch_bounds__(256)
 k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, int32_t pz_x,
                   int32_t r, const int32_t* colmap, const int32_t* rowlist,
                   const double* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
                   int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, double* losq)
 {
-    __shared__ double tile[64][33];
+    extern __shared__ __align__(16) double tile[];          // 64 x (SPLIT_COLS + 1)
+    __shared__ int64_t rowoff[64];
+    __shared__ double rowsc[64];
+    constexpr int LD = SPLIT_COLS + 1;
     const int item = blockIdx.z;
     const int tile_r = blockIdx.x;
     const int64_t t0 = (int64_t)tile_r * 64;
-    const int c0 = blockIdx.y * 32;
+    const int c0 = blockIdx.y * SPLIT_COLS;
     const int nr = nrows[item];
     const int pz = pz_x + r;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int c = c0 + tx;
-    int src_col = -1;
-    if (c < pz_x) src_col = colmap ? colmap[c] : c;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int tl = ty + 8 * i;
-        const int64_t t = t0 + tl;
-        double v = 0.0;
-        if (t < nr && c < pz) {
-            const int64_t row = rowlist[(int64_t)item * m + t];
-            const double sc = rowscale[(int64_t)item * m + t];
-            v = (c < pz_x ? X[row * ldx + src_col] : Y[row * ldy + (c - pz_x)]) * sc;
-        }
-        tile[tl][tx] = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 64) {
+        const int64_t t = t0 + threadIdx.x;
+        rowoff[threadIdx.x] = t < nr ? (int64_t)rowlist[(int64_t)item * m + t] : -1;
+        rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.0;
     }
     __syncthreads();
-    // warp ty writes columns c0 + ty + 8j; lane covers rows 2*lane, 2*lane + 1
+    // warp w reads rows w, w+8, ..., columns c0 + lane + 32j
+    for (int i = 0; i < 8; ++i) {
+        const int tl = warp + 8 * i;
+        const int64_t row = rowoff[tl];
+        const double sc = rowsc[tl];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int cl = ty + 8 * j;
+        for (int j = 0; j < SPLIT_COLS / 32; ++j) {
+            const int c = c0 + lane + 32 * j;
+            double v = 0.0;
+            if (row >= 0 && c < pz) {
+                v = c < pz_x ? X[row * ldx + (colmap ? colmap[c] : c)] : Y[row * ldy + (c - pz_x)];
+                v *= sc;
+            }
+            tile[tl * LD + lane + 32 * j] = v;
+        }
+    }
+    __syncthreads();
+    // warp w writes columns c0 + w + 8j; lane covers rows 2*lane, 2*lane + 1
+    for (int j = 0; j < SPLIT_COLS / 8; ++j) {
+        const int cl = warp + 8 * j;
         const int cc = c0 + cl;
-        if (cc >= pz_pad) continue;
-        const double v0 = tile[2 * tx][cl], v1 = tile[2 * tx + 1][cl];
+        if (cc >= pz_pad) break;
+        const double v0 = tile[(2 * lane) * LD + cl], v1 = tile[(2 * lane + 1) * LD + cl];
         const __nv_bfloat16 h0 = __double2bfloat16(v0), h1 = __double2bfloat16(v1);
         const __nv_bfloat16 l0 = __double2bfloat16(v0 - (double)__bfloat162float(h0));
         const __nv_bfloat16 l1 = __double2bfloat16(v1 - (double)__bfloat162float(h1));
-        const int64_t base_hi = (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0 + 2 * tx;
-        const int64_t base_lo = (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0 + 2 * tx;
+        const int64_t base_hi = (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0 + 2 * lane;
+        const int64_t base_lo = (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0 + 2 * lane;
         *reinterpret_cast<__nv_bfloat162*>(out + base_hi) = __halves2bfloat162(h0, h1);
         *reinterpret_cast<__nv_bfloat162*>(out + base_lo) = __halves2bfloat162(l0, l1);
         if (cc < pz_x) {
             const double f0 = (double)__bfloat162float(l0), f1 = (double)__bfloat162float(l1);
             const double sq = warp_sum(f0 * f0 + f1 * f1);
-            if (tx == 0) losq[((int64_t)item * row_tiles + tile_r) * pz_x + cc] = sq;
+            if (lane == 0) losq[((int64_t)item * row_tiles + tile_r) * pz_x + cc] = sq;
         }
     }
 }
@@ -585,10 +596,13 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     DevBuf losq(sizeof(double) * (size_t)group * row_tiles * pz_x, s);
     auto kern = k_gram_tc;
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    const size_t split_smem = sizeof(double) * 64 * (SPLIT_COLS + 1);
+    UOI_CUDA(cudaFuncSetAttribute(k_split_transpose, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)split_smem));
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
-        dim3 gs((unsigned)row_tiles, (unsigned)ceil_div(pz_pad, 32), (unsigned)nb);
-        k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
+        dim3 gs((unsigned)row_tiles, (unsigned)ceil_div(pz_pad, SPLIT_COLS), (unsigned)nb);
+        k_split_transpose<<<gs, 256, split_smem, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
                                              rows.as<int32_t>() + (size_t)b0 * m,
                                              scale.as<double>() + (size_t)b0 * m,
                                              nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
