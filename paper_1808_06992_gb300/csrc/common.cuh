@@ -86,6 +86,28 @@ __device__ __forceinline__ T soft_threshold(T v, T kappa)
     return v > kappa ? v - kappa : (v < -kappa ? v + kappa : T(0));
 }
 
+// FP64 -> FP32 with round-to-nearest-even using integer operations only (the
+// FP64 pipe of this part is ~1/64 of its FP32 rate, and conversions from FP64
+// run on it).  Magnitudes below 2^-126 flush to signed zero.
+__device__ __forceinline__ float f64_to_f32_int(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FFull);
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (mant ? 0x400000u : 0u));
+    int e32 = e - 1023 + 127;
+    if (e32 <= 0) return __uint_as_float(sign);
+    unsigned int m = (unsigned int)(mant >> 29);
+    const unsigned long long rem = mant & ((1ull << 29) - 1ull);
+    const unsigned long long half = 1ull << 28;
+    if (rem > half || (rem == half && (m & 1u))) {
+        if (++m == (1u << 23)) { m = 0; ++e32; }
+    }
+    if (e32 >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned int)e32 << 23) | m);
+}
+
 // Device-side error word: kernels record the first error here and return.
 struct DevStatus {
     int32_t code;      // 0 = ok, else a UOI_ERR_* value

@@ -26,6 +26,7 @@ struct OlsArgs {
     const uint64_t* family;                  // q x r x W
     int64_t p, r; int32_t q, B2, W;
     const int32_t* jstar;                    // chosen pass: B2 (else null)
+    const int32_t* dup;                      // q x r: first j with the same support (or null)
     double* losses;                          // B2 x q x r
     int32_t* singular;                       // B2 x q x r (nullable)
     double* chosen;                          // chosen pass: B2 x r x p
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
         int k, j, e;
         if (a.jstar) { k = (int)(t / a.r); e = (int)(t % a.r); j = a.jstar[k]; }
         else { k = (int)(t / ((int64_t)a.q * a.r)); const int64_t rem = t % ((int64_t)a.q * a.r);
-               j = (int)(rem / a.r); e = (int)(rem % a.r); }
+               j = (int)(rem / a.r); e = (int)(rem % a.r);
+               if (a.dup && a.dup[rem] != j) continue; }       // duplicate support: filled later
         const uint64_t* bits = a.family + ((int64_t)j * a.r + e) * a.W;
         // support indices (warp 0, ballot compaction in increasing i)
         if (warp == 0) {
@@ -158,6 +160,43 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
             }
         }
         __syncthreads();
+    }
+}
+
+// dup[j*r + e] = smallest j' <= j whose support for response e equals S_{j,e}.
+__global__ void k_family_dedup(const uint64_t* fam, int32_t q, int64_t r, int W, int32_t* dup)
+{
+    const int64_t total = (int64_t)q * r;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / r);
+        const int64_t e = t % r;
+        const uint64_t* a = fam + t * W;
+        int first = j;
+        for (int jj = 0; jj < j; ++jj) {
+            const uint64_t* b = fam + ((int64_t)jj * r + e) * W;
+            bool same = true;
+            for (int w = 0; w < W && same; ++w) same = a[w] == b[w];
+            if (same) { first = jj; break; }
+        }
+        dup[t] = first;
+    }
+}
+
+// Copy the loss (and flag) of the representative to every duplicate (k, j, e).
+__global__ void k_fill_duplicates(const int32_t* dup, int32_t B2, int32_t q, int64_t r,
+                                  double* losses, int32_t* singular)
+{
+    const int64_t total = (int64_t)B2 * q * r;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / ((int64_t)q * r), rem = t % ((int64_t)q * r);
+        const int64_t e = rem % r;
+        const int32_t j0 = dup[rem];
+        if (j0 == (int32_t)(rem / r)) continue;
+        const int64_t src = (k * q + j0) * r + e;
+        losses[t] = losses[src];
+        if (singular) singular[t] = singular[src];
     }
 }
 
@@ -315,7 +354,16 @@ void ols_losses(const double* Gt, const double* Bt, const double* Ge, const doub
     a.p = p; a.r = r; a.q = q; a.B2 = B2; a.W = (int32_t)((p + 63) / 64);
     a.losses = losses; a.singular = singular;
     a.solves = (int64_t)B2 * q * r;
+    DevBuf dup(sizeof(int32_t) * (size_t)(q * r), s);
+    const unsigned gd = (unsigned)std::min<int64_t>(ceil_div((int64_t)q * r, 256), 1024);
+    k_family_dedup<<<gd, 256, 0, s>>>(family, q, r, a.W, dup.as<int32_t>());
+    UOI_CHECK_LAUNCH();
+    a.dup = dup.as<int32_t>();
     run_ols(a, s);
+    const unsigned gf = (unsigned)std::min<int64_t>(ceil_div(a.solves, 256), 4096);
+    k_fill_duplicates<<<gf, 256, 0, s>>>(dup.as<int32_t>(), B2, q, r, losses, singular);
+    UOI_CHECK_LAUNCH();
+    count_launch(2);
 }
 
 void loss_argmin(const double* losses, int32_t B2, int32_t q, int64_t r, int32_t* jstar,

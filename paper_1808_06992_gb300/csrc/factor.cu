@@ -24,13 +24,30 @@ constexpr int NB = 32;    // Cholesky panel width
 constexpr int IB = 64;    // inverse block
 
 template <typename T>
+__device__ __forceinline__ T system_entry(double g, double inv_n, double rho, bool diag);
+
+template <>
+__device__ __forceinline__ double system_entry<double>(double g, double inv_n, double rho, bool diag)
+{
+    return g * inv_n + (diag ? rho : 0.0);
+}
+
+// FP32 form: no FP64 arithmetic per element (this part's FP64 rate is ~1/64 of FP32).
+template <>
+__device__ __forceinline__ float system_entry<float>(double g, double inv_n, double rho, bool diag)
+{
+    return f64_to_f32_int(g) * (float)inv_n + (diag ? (float)rho : 0.f);
+}
+
+template <typename T>
 __global__ void k_build_system(const double* G, const double* nk, double rho, int64_t p, T* A)
 {
     const int64_t k = blockIdx.y;
+    const double inv_n = 1.0 / nk[k];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < p * p;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / p, j = t % p;
-        A[k * p * p + t] = (T)(G[k * p * p + t] / nk[k] + (i == j ? rho : 0.0));
+        A[k * p * p + t] = system_entry<T>(G[k * p * p + t], inv_n, rho, i == j);
     }
 }
 

@@ -356,23 +356,23 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 }
 
 // Gather rows with positive weight, scale by sqrt(w), split into bf16 hi/lo and
-// write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].  A block
-// covers 64 sample rows x 128 columns: each warp reads 1 KB row segments (FP64),
-// then writes 128-byte runs of paired bf16 along the rows of each column.  It
-// also writes the sum of lo^2 of each column over its 64 rows
-// (losq[(item*row_tiles + tile)*pz_x + col]), from which the diagonal
-// correction is reduced in a fixed order.
+// write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].  Values
+// are taken to FP32 first (relative error 2^-23 after the scaling, below the
+// 2^-17 residue of the two-piece split).  A block covers 64 sample rows x 128
+// columns: each warp reads 1 KB row segments, then writes 128-byte runs of
+// paired bf16 along the rows of each column.  It also writes the FP32 sum of
+// lo^2 of each column over its 64 rows (losq[(item*row_tiles + tile)*pz_x + col]),
+// from which the diagonal correction is reduced in a fixed order.
 constexpr int SPLIT_COLS = 128;
 __global__ void __launch_bounds__(256)
 k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, int32_t pz_x,
                   int32_t r, const int32_t* colmap, const int32_t* rowlist,
-                  const double* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
-                  int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, double* losq)
+                  const float* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
+                  int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq)
 {
-    extern __shared__ __align__(16) double tile[];          // 64 x (SPLIT_COLS + 1)
+    __shared__ float tile[64][SPLIT_COLS + 1];
     __shared__ int64_t rowoff[64];
-    __shared__ double rowsc[64];
-    constexpr int LD = SPLIT_COLS + 1;
+    __shared__ float rowsc[64];
     const int item = blockIdx.z;
     const int tile_r = blockIdx.x;
     const int64_t t0 = (int64_t)tile_r * 64;
@@ -383,23 +383,24 @@ k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, in
     if (threadIdx.x < 64) {
         const int64_t t = t0 + threadIdx.x;
         rowoff[threadIdx.x] = t < nr ? (int64_t)rowlist[(int64_t)item * m + t] : -1;
-        rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.0;
+        rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.f;
     }
     __syncthreads();
     // warp w reads rows w, w+8, ..., columns c0 + lane + 32j
     for (int i = 0; i < 8; ++i) {
         const int tl = warp + 8 * i;
         const int64_t row = rowoff[tl];
-        const double sc = rowsc[tl];
+        const float sc = rowsc[tl];
 #pragma unroll
         for (int j = 0; j < SPLIT_COLS / 32; ++j) {
             const int c = c0 + lane + 32 * j;
-            double v = 0.0;
+            float v = 0.f;
             if (row >= 0 && c < pz) {
-                v = c < pz_x ? X[row * ldx + (colmap ? colmap[c] : c)] : Y[row * ldy + (c - pz_x)];
-                v *= sc;
+                const double x = c < pz_x ? X[row * ldx + (colmap ? colmap[c] : c)]
+                                          : Y[row * ldy + (c - pz_x)];
+                v = f64_to_f32_int(x) * sc;
             }
-            tile[tl * LD + lane + 32 * j] = v;
+            tile[tl][lane + 32 * j] = v;
         }
     }
     __syncthreads();
@@ -408,17 +409,17 @@ k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, in
         const int cl = warp + 8 * j;
         const int cc = c0 + cl;
         if (cc >= pz_pad) break;
-        const double v0 = tile[(2 * lane) * LD + cl], v1 = tile[(2 * lane + 1) * LD + cl];
-        const __nv_bfloat16 h0 = __double2bfloat16(v0), h1 = __double2bfloat16(v1);
-        const __nv_bfloat16 l0 = __double2bfloat16(v0 - (double)__bfloat162float(h0));
-        const __nv_bfloat16 l1 = __double2bfloat16(v1 - (double)__bfloat162float(h1));
+        const float v0 = tile[2 * lane][cl], v1 = tile[2 * lane + 1][cl];
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+        const float r0 = v0 - __bfloat162float(h0), r1 = v1 - __bfloat162float(h1);   // exact
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(r0), l1 = __float2bfloat16_rn(r1);
         const int64_t base_hi = (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0 + 2 * lane;
         const int64_t base_lo = (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0 + 2 * lane;
         *reinterpret_cast<__nv_bfloat162*>(out + base_hi) = __halves2bfloat162(h0, h1);
         *reinterpret_cast<__nv_bfloat162*>(out + base_lo) = __halves2bfloat162(l0, l1);
         if (cc < pz_x) {
-            const double f0 = (double)__bfloat162float(l0), f1 = (double)__bfloat162float(l1);
-            const double sq = warp_sum(f0 * f0 + f1 * f1);
+            const float f0 = __bfloat162float(l0), f1 = __bfloat162float(l1);
+            const float sq = warp_sum(f0 * f0 + f1 * f1);
             if (lane == 0) losq[((int64_t)item * row_tiles + tile_r) * pz_x + cc] = sq;
         }
     }
@@ -427,7 +428,7 @@ k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, in
 // Row list of each item: rows with positive weight (in increasing order) and
 // their scale sqrt(w); nrows[item] = count.  One block per item.
 __global__ void k_row_lists(const uint32_t* w, const uint8_t* mask, int64_t m, int32_t* rowlist,
-                            double* rowscale, int32_t* nrows)
+                            float* rowscale, int32_t* nrows)
 {
     const int item = blockIdx.x;
     __shared__ int warp_tot[32];
@@ -460,7 +461,7 @@ __global__ void k_row_lists(const uint32_t* w, const uint8_t* mask, int64_t m, i
         if (flag) {
             const int pos = carry + warp_tot[wid] + before;
             rowlist[(int64_t)item * m + pos] = (int32_t)t;
-            rowscale[(int64_t)item * m + pos] = sqrt((double)wt);
+            rowscale[(int64_t)item * m + pos] = sqrtf((float)wt);
         }
         __syncthreads();
         if (threadIdx.x == 0) carry += block_total;
@@ -473,7 +474,7 @@ __global__ void k_row_lists(const uint32_t* w, const uint8_t* mask, int64_t m, i
 // three-product split leaves out and which is biased (always positive).  The
 // off-diagonal lo'lo terms are zero-mean and stay out.  Sums the per-64-row
 // partials of k_split_transpose in a fixed order.
-__global__ void k_diag_lo(const double* losq, int32_t row_tiles, int32_t pz_x,
+__global__ void k_diag_lo(const float* losq, int32_t row_tiles, int32_t pz_x,
                           const int32_t* nrows, double* corr)
 {
     const int item = blockIdx.y;
@@ -481,7 +482,8 @@ __global__ void k_diag_lo(const double* losq, int32_t row_tiles, int32_t pz_x,
     if (c >= pz_x) return;
     const int tiles = (nrows[item] + 63) / 64;
     double s = 0.0;
-    for (int t = 0; t < tiles && t < row_tiles; ++t) s += losq[((int64_t)item * row_tiles + t) * pz_x + c];
+    for (int t = 0; t < tiles && t < row_tiles; ++t)
+        s += (double)losq[((int64_t)item * row_tiles + t) * pz_x + c];
     corr[(int64_t)item * pz_x + c] = s;
 }
 
@@ -570,11 +572,11 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     DevBuf tl(sizeof(int32_t) * tiles.size(), s);
     UOI_CUDA(cudaMemcpyAsync(tl.ptr, tiles.data(), sizeof(int32_t) * tiles.size(),
                              cudaMemcpyHostToDevice, s));
-    DevBuf rows(sizeof(int32_t) * (size_t)(m * B), s), scale(sizeof(double) * (size_t)(m * B), s);
+    DevBuf rows(sizeof(int32_t) * (size_t)(m * B), s), scale(sizeof(float) * (size_t)(m * B), s);
     DevBuf nrows(sizeof(int32_t) * B, s), err(sizeof(int32_t), s);
     UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
     if (w || mask) {
-        k_row_lists<<<B, 1024, 0, s>>>(w, mask, m, rows.as<int32_t>(), scale.as<double>(),
+        k_row_lists<<<B, 1024, 0, s>>>(w, mask, m, rows.as<int32_t>(), scale.as<float>(),
                                         nrows.as<int32_t>());
         UOI_CHECK_LAUNCH();
         count_launch();
@@ -593,20 +595,17 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (8ull << 30) / per_item));
     DevBuf zt(per_item * group, s);
     DevBuf corr(sizeof(double) * (size_t)group * pz_x, s);
-    DevBuf losq(sizeof(double) * (size_t)group * row_tiles * pz_x, s);
+    DevBuf losq(sizeof(float) * (size_t)group * row_tiles * pz_x, s);
     auto kern = k_gram_tc;
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    const size_t split_smem = sizeof(double) * 64 * (SPLIT_COLS + 1);
-    UOI_CUDA(cudaFuncSetAttribute(k_split_transpose, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)split_smem));
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
         dim3 gs((unsigned)row_tiles, (unsigned)ceil_div(pz_pad, SPLIT_COLS), (unsigned)nb);
-        k_split_transpose<<<gs, 256, split_smem, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
+        k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
                                              rows.as<int32_t>() + (size_t)b0 * m,
-                                             scale.as<double>() + (size_t)b0 * m,
+                                             scale.as<float>() + (size_t)b0 * m,
                                              nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
-                                             zt.as<__nv_bfloat16>(), losq.as<double>());
+                                             zt.as<__nv_bfloat16>(), losq.as<float>());
         UOI_CHECK_LAUNCH();
         const CUtensorMap mA = make_map(zt.ptr, n_pad, pz_pad, 2 * nb, TM);
         const CUtensorMap mB = make_map(zt.ptr, n_pad, pz_pad, 2 * nb, TN);
@@ -621,7 +620,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         UOI_CHECK_LAUNCH();
         ktimer_end(TK_GRAM_TC, s, 0.0, 0.0);
         dim3 gd((unsigned)ceil_div(pz_x, 256), (unsigned)nb);
-        k_diag_lo<<<gd, 256, 0, s>>>(losq.as<double>(), row_tiles, pz_x, nrows.as<int32_t>() + b0,
+        k_diag_lo<<<gd, 256, 0, s>>>(losq.as<float>(), row_tiles, pz_x, nrows.as<int32_t>() + b0,
                                      corr.as<double>());
         UOI_CHECK_LAUNCH();
         dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
