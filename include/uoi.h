@@ -105,6 +105,7 @@ typedef struct uoi_diag {
     int64_t  n_xupdate;
     double   flops_xupdate;       /* 2 p^2 per active column-iteration                   */
     double   bytes_xupdate;       /* M once per group-iteration + 6 p-vectors per column */
+    int32_t  warm_start_used;     /* UOI_WARM_* actually used (LEARNED falls back to PATH) */
 } uoi_diag;
 
 /* Optional intermediate results of a fit, for testing (every pointer nullable,
@@ -207,6 +208,47 @@ int lasso_admm_batch_noalloc(const double* X, const double* Y, int64_t n, int64_
                              double rho, double abs_tol, double rel_tol, int32_t max_iter,
                              int32_t warm_start, double* beta_out, int32_t* iters_out,
                              uint8_t* converged_out, void* stream);
+
+/* ---- learned warm start (spec extension; the paper warm-starts nothing) ----
+ * A per-feature network (8 inputs -> 3 hidden layers of 512 with GELU -> 3
+ * outputs, BF16 weights, FP32 accumulation) predicts the converged scaled ADMM
+ * state (scaled z, rho u/lambda, active logit) of every (bootstrap, lambda,
+ * equation, feature) from lambda and moment statistics (see the feature list
+ * in uoi_ws_dataset).  A fit with warm_start = UOI_WARM_LEARNED and
+ * mlp_weights_path set runs the lambda batch cold-scheduled from the
+ * predicted state; without usable weights it falls back to UOI_WARM_PATH.
+ * Parameters are a flat FP32 array: W1 (512x8) b1 W2 (512x512) b2 W3 b3
+ * W4 (3x512) b4, matrices row-major [out][in].  Handles are not thread-safe. */
+typedef struct uoi_ws_model uoi_ws_model;
+int64_t uoi_ws_param_count(void);
+int uoi_ws_create(uint64_t seed, uoi_ws_model** out);          /* Kaiming-uniform init */
+int uoi_ws_load(const char* path, uoi_ws_model** out);
+int uoi_ws_save(uoi_ws_model* model, const char* path);
+void uoi_ws_free(uoi_ws_model* model);
+int uoi_ws_set_params(uoi_ws_model* model, const float* params);  /* host or device */
+int uoi_ws_get_params(uoi_ws_model* model, float* params);
+/* out (N x 3) = network(X (N x 8)); host or device buffers. */
+int uoi_ws_forward(uoi_ws_model* model, const float* X, int64_t N, float* out);
+/* Mean loss over the N rows and its gradient (uoi_ws_param_count floats). */
+int uoi_ws_loss_grad(uoi_ws_model* model, const float* X, const float* T, int64_t N,
+                     double* loss, float* grad);
+/* Adam (lr, beta 0.9/0.999, weight decay 1e-5) over shuffled mini-batches. */
+int uoi_ws_train(uoi_ws_model* model, const float* X, const float* T, int64_t N, int32_t epochs,
+                 int32_t batch, float lr, uint64_t seed, double* final_loss);
+/* Training rows from the method's own solutions: path-warm FP64 ADMM over
+ * B bootstraps (weights B x n) x q lambdas x r responses, then for every
+ * (k, j, e, i) the 8 features
+ *   lambda_j/lambda_0, log(lambda_j/lambda_0)/log(lambda_{q-1}/lambda_0),
+ *   c_i/lambda_j, |c_i|/lambda_j, d_i, S_1(c_i/lambda_j)/d_i, c_i/lambda_{j-1},
+ *   S_1(c_i/lambda_{j-1})/d_i * lambda_{j-1}/lambda_j
+ * (c = X^T W y_e / n_k, d = diag(X^T W X)/n_k) and the 3 targets z_i/s_i with
+ * s_i = lambda_j max(1, min(|c_i|/lambda_j, 50))/d_i, rho u_i/lambda_j and
+ * [z_i != 0].  features_out: N x 8, targets_out: N x 3 floats
+ * (N = B q r p), host or device. */
+int uoi_ws_dataset(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
+                   const uint32_t* weights, int32_t B, const double* lambdas, int32_t q,
+                   double rho, double abs_tol, double rel_tol, int32_t max_iter,
+                   float* features_out, float* targets_out, void* stream);
 
 /* Text of a status code (static storage). */
 const char* uoi_status_string(int status);

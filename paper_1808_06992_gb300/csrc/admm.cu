@@ -42,6 +42,9 @@ struct AdmmDev {
     int32_t* iters;
     uint8_t* conv;
     uint64_t* family;
+    double* u_out;       // final scaled dual per column (nullable)
+    const float* z0;     // initial state per column, cold schedule only (nullable)
+    const float* u0;
 };
 
 template <typename T>
@@ -93,8 +96,14 @@ __global__ void __launch_bounds__(256, 1) k_admm_resident(AdmmDev<T> P, int32_t*
         else        { e_[b] = cid % P.r; j_[b] = cid / P.r; jend_[b] = j_[b] + 1; }
         it_[b] = 0;
         kappa[b] = (T)P.lambdas[j_[b]] / P.rho;
+        const int64_t col0 = ((int64_t)g * P.q + j_[b]) * P.r + e_[b];
 #pragma unroll
-        for (int a = 0; a < A; ++a) { z[a][b] = T(0); u[a][b] = T(0); }
+        for (int a = 0; a < A; ++a) {
+            const int i = lane + 32 * a;
+            const bool init = P.z0 && !P.warm && i < p;
+            z[a][b] = init ? (T)P.z0[col0 * p + i] : T(0);
+            u[a][b] = init ? (T)P.u0[col0 * p + i] : T(0);
+        }
     };
 #pragma unroll
     for (int b = 0; b < SW; ++b) fetch(b);
@@ -170,6 +179,13 @@ __global__ void __launch_bounds__(256, 1) k_admm_resident(AdmmDev<T> P, int32_t*
                     for (int a = 0; a < A; ++a) {
                         const int i = lane + 32 * a;
                         if (i < p) P.beta[col * p + i] = (double)z[a][b];
+                    }
+                }
+                if (P.u_out) {
+#pragma unroll
+                    for (int a = 0; a < A; ++a) {
+                        const int i = lane + 32 * a;
+                        if (i < p) P.u_out[col * p + i] = (double)u[a][b];
                     }
                 }
                 if (P.family) {
@@ -485,10 +501,12 @@ __global__ void k_stream_check(AdmmDev<T> P, StreamState S, int cur, T* z, T* u,
         const int64_t col_je = (int64_t)j * P.r + e;
         const int64_t col = (int64_t)g * P.q * P.r + col_je;
         const T* zs = z + (size_t)sl * p;
+        const T* us = u + (size_t)sl * p;
         for (int a = 0; 32 * a < p; ++a) {
             const int i = lane + 32 * a;
             const T zi = i < p ? zs[i] : T(0);
             if (P.beta && i < p) P.beta[col * p + i] = (double)zi;
+            if (P.u_out && i < p) P.u_out[col * p + i] = (double)us[i];
             if (P.family) {
                 const unsigned bal = __ballot_sync(0xffffffffu, zi != T(0));
                 if (lane == 0) and_family_bits(P, col_je, a, bal);
@@ -513,6 +531,20 @@ __global__ void k_stream_check(AdmmDev<T> P, StreamState S, int cur, T* z, T* u,
             S.act[cur ^ 1][(size_t)g * S.nchains + pos] = sl;
             atomicAdd(S.total[cur ^ 1], 1);
         }
+    }
+}
+
+// Cold schedule with a learned start: slot s is column s, so z, u and
+// V = z - u start from the given state.
+template <typename T>
+__global__ void k_stream_init_state(AdmmDev<T> P, int64_t count, T* z, T* u, T* V)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const T zz = (T)P.z0[t], uu = (T)P.u0[t];
+        z[t] = zz;
+        u[t] = uu;
+        V[t] = zz - uu;
     }
 }
 
@@ -543,6 +575,7 @@ AdmmDev<T> to_dev(const AdmmProblem<T>& P)
     d.rho = (T)P.rho; d.abs_tol = (T)P.abs_tol; d.rel_tol = (T)P.rel_tol;
     d.sqrtp = (T)sqrt((double)P.p);
     d.beta = P.beta; d.iters = P.iters; d.conv = P.conv; d.family = P.family;
+    d.u_out = P.u_out; d.z0 = P.z0; d.u0 = P.u0;
     return d;
 }
 
@@ -621,6 +654,12 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
     k_stream_init<T><<<(unsigned)std::min<int64_t>(ceil_div(slots, 256), 4096), 256, 0, s>>>(d, S);
     UOI_CHECK_LAUNCH();
     count_launch();
+    if (P.z0 && !P.warm) {
+        k_stream_init_state<T><<<(unsigned)std::min<int64_t>(ceil_div(slots * p, 256), 8192), 256, 0, s>>>(
+            d, slots * p, zb.as<T>(), ub.as<T>(), v0.as<T>());
+        UOI_CHECK_LAUNCH();
+        count_launch();
+    }
 
     int32_t* host_total = nullptr;
     UOI_CUDA(cudaMallocHost(&host_total, sizeof(int32_t)));

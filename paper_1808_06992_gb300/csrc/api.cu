@@ -208,9 +208,8 @@ void validate(const uoi_params* prm)
         throw Error(UOI_ERR_UNSUPPORTED, "median bagging supports B2 <= 128");
     if (prm->precision != UOI_PREC_FP64 && prm->precision != UOI_PREC_MIXED)
         throw Error(UOI_ERR_INVALID_ARG, "unknown precision");
-    if (prm->warm_start == UOI_WARM_LEARNED)
-        throw Error(UOI_ERR_UNSUPPORTED, "learned warm start needs trained weights");
-    if (prm->warm_start != UOI_WARM_NONE && prm->warm_start != UOI_WARM_PATH)
+    if (prm->warm_start != UOI_WARM_NONE && prm->warm_start != UOI_WARM_PATH &&
+        prm->warm_start != UOI_WARM_LEARNED)
         throw Error(UOI_ERR_INVALID_ARG, "unknown warm start mode");
     if (prm->lambda_min_ratio <= 0.0 && !prm->lambdas)
         throw Error(UOI_ERR_INVALID_ARG, "lambda_min_ratio must be positive");
@@ -232,7 +231,8 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                     int64_t m, int64_t p, int64_t r, const uint32_t* w, int32_t B,
                     const double* lam, int32_t q, double rho, double abs_tol, double rel_tol,
                     int32_t max_iter, int32_t warm, double* beta, int32_t* iters, uint8_t* conv,
-                    uint64_t* family, cudaStream_t s, StageTimer* tm, int* marks)
+                    uint64_t* family, cudaStream_t s, StageTimer* tm, int* marks,
+                    WsModel* ws = nullptr)
 {
     int t0 = tm ? tm->mark() : 0;
     DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
@@ -243,6 +243,19 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     } else {
         const double mm = (double)m;
         UOI_CUDA(cudaMemcpyAsync(nk.ptr, &mm, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    // learned warm start: predicted (z, u) for every column, then the cold schedule
+    DevBuf z0, u0;
+    if (ws) {
+        const int64_t rows = (int64_t)B * q * r * p;
+        DevBuf F(sizeof(float) * (size_t)rows * 8, s), out(sizeof(float) * (size_t)rows * 3, s);
+        ws_build_features(G.as<double>(), Bm.as<double>(), nk.as<double>(), lam, q, p, r, B, rho,
+                          nullptr, nullptr, F.as<float>(), nullptr, s);
+        ws_forward(ws, F.as<float>(), rows, out.as<float>(), s);
+        z0.alloc(sizeof(float) * (size_t)rows, s);
+        u0.alloc(sizeof(float) * (size_t)rows, s);
+        ws_start_state(out.as<float>(), F.as<float>(), lam, q, p, r, rows, rho, z0.as<float>(),
+                       u0.as<float>(), s);
     }
     int t1 = tm ? tm->mark() : 0;
     DevBuf st(sizeof(DevStatus), s);
@@ -261,8 +274,10 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     AdmmProblem<T> P;
     P.G = B; P.p = p; P.r = r; P.q = q;
     P.M = M.as<T>(); P.c = c.as<T>(); P.lambdas = lam;
-    P.rho = rho; P.abs_tol = abs_tol; P.rel_tol = rel_tol; P.max_iter = max_iter; P.warm = warm;
+    P.rho = rho; P.abs_tol = abs_tol; P.rel_tol = rel_tol; P.max_iter = max_iter;
+    P.warm = ws ? 0 : (warm == UOI_WARM_LEARNED ? 1 : warm);
     P.beta = beta; P.iters = iters; P.conv = conv; P.family = family;
+    if (ws) { P.z0 = z0.as<float>(); P.u0 = u0.as<float>(); }
     admm_solve<T>(P, s);
     int t3 = tm ? tm->mark() : 0;
     if (marks) { marks[0] = t0; marks[1] = t1; marks[2] = t2; marks[3] = t3; }
@@ -304,6 +319,29 @@ IterStats iteration_stats(const int32_t* iters_d, const uint8_t* conv_d, int64_t
         }
     }
     return st;
+}
+
+// Warm-start weights loaded from a file, cached by path for the process.
+struct WsCache {
+    std::string path;
+    WsModel* model = nullptr;
+};
+WsCache g_ws_cache;
+
+WsModel* ws_for_path(const char* path, cudaStream_t s)
+{
+    if (!path || !*path) return nullptr;
+    if (g_ws_cache.model && g_ws_cache.path == path) return g_ws_cache.model;
+    WsModel* m = nullptr;
+    try {
+        m = ws_load(path, s);
+    } catch (const Error&) {
+        return nullptr;                        // unusable weights: path warm start instead
+    }
+    if (g_ws_cache.model) ws_destroy(g_ws_cache.model);
+    g_ws_cache.model = m;
+    g_ws_cache.path = path;
+    return m;
 }
 
 int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
@@ -374,16 +412,19 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     DevBuf fam(sizeof(uint64_t) * (size_t)(q * r * W), s);
     family_init(fam.as<uint64_t>(), q * r * W, s);
     int marks[4] = { 0, 0, 0, 0 };
+    WsModel* ws = prm->warm_start == UOI_WARM_LEARNED ? ws_for_path(prm->mlp_weights_path, s) : nullptr;
+    const int32_t warm_used = prm->warm_start == UOI_WARM_LEARNED ? (ws ? UOI_WARM_LEARNED : UOI_WARM_PATH)
+                                                                  : prm->warm_start;
     if (mixed)
         selection_admm<float>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                               lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                               prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks);
+                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, ws);
     else
         selection_admm<double>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                                lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                                prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks);
+                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, ws);
     family_mask_tail(fam.as<uint64_t>(), q * r, p, s);
     const int t_sel2 = tm.mark();
 
@@ -453,7 +494,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     }
     UOI_CUDA(cudaStreamSynchronize(s));
     IterStats its = iteration_stats(iters_b.as<int32_t>(), conv_b.as<uint8_t>(), ncol, s, B1, q, r,
-                                    prm->warm_start);
+                                    warm_used == UOI_WARM_PATH ? 1 : 0);
     {
         // algorithmic work of the streaming x-update: 2 p^2 flops per active
         // column-iteration; M once per group-iteration plus the c, z, u, V reads
@@ -491,6 +532,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
             diag->n_xupdate = x.launches;
             diag->flops_xupdate = x.flops;
             diag->bytes_xupdate = x.bytes;
+            diag->warm_start_used = warm_used;
         }
     }
     return (its.noncon > 0 || nsing > 0) ? UOI_OK_WITH_WARNINGS : UOI_OK;
@@ -654,6 +696,165 @@ int uoi_weighted_moments(const double* X, const double* Y, int64_t n, int64_t p,
         moments(precision, Xd, p, Yd, r, n, p, r, wd, nullptr, B, go.dev, bo.dev, s);
         go.finish(s);
         bo.finish(s);
+        UOI_CUDA(cudaStreamSynchronize(s));
+        return UOI_OK;
+    });
+}
+
+struct uoi_ws_model {
+    WsModel* m;
+};
+
+int64_t uoi_ws_param_count(void) { return ws_param_count(); }
+
+int uoi_ws_create(uint64_t seed, uoi_ws_model** out)
+{
+    return guarded([&] {
+        if (!out) throw Error(UOI_ERR_INVALID_ARG, "NULL handle pointer");
+        WsModel* m = ws_create(seed, nullptr);
+        UOI_CUDA(cudaStreamSynchronize(nullptr));
+        *out = new uoi_ws_model{ m };
+        return UOI_OK;
+    });
+}
+
+int uoi_ws_load(const char* path, uoi_ws_model** out)
+{
+    return guarded([&] {
+        if (!out || !path) throw Error(UOI_ERR_INVALID_ARG, "NULL argument");
+        *out = new uoi_ws_model{ ws_load(path, nullptr) };
+        return UOI_OK;
+    });
+}
+
+int uoi_ws_save(uoi_ws_model* model, const char* path)
+{
+    return guarded([&] {
+        if (!model || !path) throw Error(UOI_ERR_INVALID_ARG, "NULL argument");
+        ws_save(model->m, path);
+        return UOI_OK;
+    });
+}
+
+void uoi_ws_free(uoi_ws_model* model)
+{
+    if (!model) return;
+    ws_destroy(model->m);
+    delete model;
+}
+
+int uoi_ws_set_params(uoi_ws_model* model, const float* params)
+{
+    return guarded([&] {
+        if (!model || !params) throw Error(UOI_ERR_INVALID_ARG, "NULL argument");
+        ws_set_params(model->m, params, nullptr);
+        UOI_CUDA(cudaStreamSynchronize(nullptr));
+        return UOI_OK;
+    });
+}
+
+int uoi_ws_get_params(uoi_ws_model* model, float* params)
+{
+    return guarded([&] {
+        if (!model || !params) throw Error(UOI_ERR_INVALID_ARG, "NULL argument");
+        ws_get_params(model->m, params, nullptr);
+        return UOI_OK;
+    });
+}
+
+int uoi_ws_forward(uoi_ws_model* model, const float* X, int64_t N, float* out)
+{
+    return guarded([&] {
+        if (!model || !X || !out || N <= 0) throw Error(UOI_ERR_INVALID_ARG, "bad argument");
+        ensure_pool();
+        DevBuf hx;
+        const float* Xd = dev_in(X, (size_t)(N * 8), hx, nullptr);
+        DevOut<float> o;
+        o.init(out, (size_t)(N * 3), nullptr);
+        ws_forward(model->m, Xd, N, o.dev, nullptr);
+        o.finish(nullptr);
+        UOI_CUDA(cudaStreamSynchronize(nullptr));
+        return UOI_OK;
+    });
+}
+
+int uoi_ws_loss_grad(uoi_ws_model* model, const float* X, const float* T, int64_t N, double* loss,
+                     float* grad)
+{
+    return guarded([&] {
+        if (!model || !X || !T || !grad || N <= 0) throw Error(UOI_ERR_INVALID_ARG, "bad argument");
+        ensure_pool();
+        DevBuf hx, ht;
+        const float* Xd = dev_in(X, (size_t)(N * 8), hx, nullptr);
+        const float* Td = dev_in(T, (size_t)(N * 3), ht, nullptr);
+        DevOut<float> g;
+        g.init(grad, (size_t)ws_param_count(), nullptr);
+        const double L = ws_loss_grad(model->m, Xd, Td, N, g.dev, nullptr);
+        g.finish(nullptr);
+        UOI_CUDA(cudaStreamSynchronize(nullptr));
+        if (loss) *loss = L;
+        return UOI_OK;
+    });
+}
+
+int uoi_ws_train(uoi_ws_model* model, const float* X, const float* T, int64_t N, int32_t epochs,
+                 int32_t batch, float lr, uint64_t seed, double* final_loss)
+{
+    return guarded([&] {
+        if (!model || !X || !T || N <= 0 || epochs <= 0 || batch <= 0 || batch > N)
+            throw Error(UOI_ERR_INVALID_ARG, "bad argument");
+        ensure_pool();
+        const double L = ws_train(model->m, X, T, N, epochs, batch, lr, seed, nullptr);
+        if (final_loss) *final_loss = L;
+        return UOI_OK;
+    });
+}
+
+int uoi_ws_dataset(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
+                   const uint32_t* weights, int32_t B, const double* lambdas, int32_t q, double rho,
+                   double abs_tol, double rel_tol, int32_t max_iter, float* features_out,
+                   float* targets_out, void* stream)
+{
+    return guarded([&] {
+        if (!X || !Y || !weights || !lambdas || !features_out || !targets_out)
+            throw Error(UOI_ERR_INVALID_ARG, "NULL pointer");
+        if (n <= 0 || p <= 0 || r <= 0 || q <= 0 || B <= 0 || max_iter <= 0 || !(rho > 0.0))
+            throw Error(UOI_ERR_INVALID_ARG, "bad size or parameter");
+        ensure_pool();
+        cudaStream_t s = (cudaStream_t)stream;
+        DevBuf hx, hy, hw, hl;
+        const double* Xd = dev_in(X, (size_t)(n * p), hx, s);
+        const double* Yd = dev_in(Y, (size_t)(n * r), hy, s);
+        const uint32_t* wd = dev_in(weights, (size_t)(B * n), hw, s);
+        const double* ld = dev_in(lambdas, (size_t)q, hl, s);
+        const int64_t rows = (int64_t)B * q * r * p;
+        DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
+        DevBuf nk(sizeof(double) * B, s), A(sizeof(double) * (size_t)(B * p * p), s);
+        moments_fp64(Xd, p, Yd, r, n, p, r, wd, nullptr, B, G.as<double>(), Bm.as<double>(), 0, s);
+        weight_sums(wd, nullptr, n, B, nk.as<double>(), s);
+        DevBuf st(sizeof(DevStatus), s);
+        UOI_CUDA(cudaMemsetAsync(st.ptr, 0, st.bytes, s));
+        build_and_factor<double>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<double>(),
+                                 st.as<DevStatus>(), s);
+        check_status(st.as<DevStatus>(), s, "Cholesky of G/n + rho I");
+        DevBuf Linv(sizeof(double) * (size_t)(B * p * p), s), M(sizeof(double) * (size_t)(B * p * p), s);
+        DevBuf c(sizeof(double) * (size_t)(B * p * r), s);
+        inverse_and_rhs<double>(A.as<double>(), Bm.as<double>(), nk.as<double>(), p, r, B,
+                                Linv.as<double>(), M.as<double>(), c.as<double>(), s);
+        DevBuf zs(sizeof(double) * (size_t)rows, s), us(sizeof(double) * (size_t)rows, s);
+        AdmmProblem<double> P;
+        P.G = B; P.p = p; P.r = r; P.q = q;
+        P.M = M.as<double>(); P.c = c.as<double>(); P.lambdas = ld;
+        P.rho = rho; P.abs_tol = abs_tol; P.rel_tol = rel_tol; P.max_iter = max_iter; P.warm = 1;
+        P.beta = zs.as<double>(); P.u_out = us.as<double>();
+        admm_solve<double>(P, s);
+        DevOut<float> fo, to;
+        fo.init(features_out, (size_t)rows * 8, s);
+        to.init(targets_out, (size_t)rows * 3, s);
+        ws_build_features(G.as<double>(), Bm.as<double>(), nk.as<double>(), ld, q, p, r, B, rho,
+                          zs.as<double>(), us.as<double>(), fo.dev, to.dev, s);
+        fo.finish(s);
+        to.finish(s);
         UOI_CUDA(cudaStreamSynchronize(s));
         return UOI_OK;
     });

@@ -123,7 +123,9 @@ struct AdmmProblem {
     int32_t* iters = nullptr; // G x q x r     (nullable)
     uint8_t* conv = nullptr;  // G x q x r     (nullable)
     uint64_t* family = nullptr;   // q x r x W, AND of the supports (nullable, preset to ~0)
-    int32_t family_offset = 0;    // not used (single problem)
+    double* u_out = nullptr;  // G x q x r x p final scaled dual (nullable)
+    const float* z0 = nullptr;    // G x q x r x p initial z, cold schedule only (nullable)
+    const float* u0 = nullptr;    // initial u, same layout
 };
 template <typename T>
 void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
@@ -131,6 +133,25 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
 // (G int32).  Returns false (launching nothing) when p is too large for it.
 template <typename T>
 bool admm_solve_resident_with(const AdmmProblem<T>& P, int32_t* chain_next, cudaStream_t s);
+
+// ---- G8: learned warm start (mlp.cu) ------------------------------------------------
+struct WsModel;
+WsModel* ws_create(uint64_t seed, cudaStream_t s);
+void ws_destroy(WsModel* M);
+int64_t ws_param_count();
+void ws_set_params(WsModel* M, const float* params, cudaStream_t s);
+void ws_get_params(WsModel* M, float* params, cudaStream_t s);
+void ws_forward(WsModel* M, const float* X, int64_t N, float* out, cudaStream_t s);
+double ws_loss_grad(WsModel* M, const float* X, const float* T, int64_t N, float* g, cudaStream_t s);
+double ws_train(WsModel* M, const float* X, const float* T, int64_t N, int32_t epochs, int32_t batch,
+                float lr, uint64_t seed, cudaStream_t s);
+void ws_build_features(const double* G, const double* Bm, const double* nk, const double* lam,
+                       int32_t q, int64_t p, int64_t r, int32_t B, double rho, const double* zt,
+                       const double* ut, float* F, float* T, cudaStream_t s);
+void ws_start_state(const float* out, const float* F, const double* lam, int32_t q, int64_t p,
+                    int64_t r, int64_t total, double rho, float* z0, float* u0, cudaStream_t s);
+void ws_save(WsModel* M, const char* path);
+WsModel* ws_load(const char* path, cudaStream_t s);
 
 // ---- G5/G6/G7: supports, OLS, loss, bagging (estimate.cu) -----------------------------
 void family_init(uint64_t* fam, int64_t words, cudaStream_t s);

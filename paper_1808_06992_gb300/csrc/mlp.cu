@@ -1,0 +1,742 @@
+// mlp.cu -- G8: the learned warm start of the ADMM selection step.
+//
+// A per-feature network predicts, for every (bootstrap k, lambda_j, equation e,
+// feature i), the converged scaled ADMM state of column (k, j, e): z_i / s_i with
+// s_i = lambda_j max(1, min(|c_i|/lambda_j, 50)) / d_i (the scale of the
+// soft-threshold proxy solution), rho u_i / lambda_j, and whether z_i != 0.  Inputs (8 per row) are lambda and
+// moment statistics that exist before any iteration: lambda_j / lambda_0,
+// log(lambda_j / lambda_0) / log(lambda_min / lambda_0), the correlation
+// c_i = (X^T W y_e)_i / n_k scaled by lambda_j and by lambda_{j-1}, |c_i| / lambda_j,
+// the Gram diagonal d_i = G_ii / n_k, and the soft-threshold proxy solutions
+// S_1(c_i / lambda) / d_i at lambda_j and at the previous lambda_{j-1}.
+// Network: 8 -> 512 -> 512 -> 512 -> 3 with exact-erf GELU, BF16 weights used
+// by every product (FP32 master copy in the optimizer), FP32 accumulation and
+// FP32 activations.  Loss per row: squared errors of the two state outputs plus
+// the logistic loss of the active logit, averaged over rows.
+//
+// The network only chooses where ADMM starts; the converged answer is the
+// same convex minimiser, which path-warm ADMM checks (tests) and falls back to.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+
+namespace uoi {
+
+constexpr int WS_IN = 8, WS_H = 512, WS_OUT = 3;
+
+namespace {
+
+// parameter offsets in the flat layout W1 b1 W2 b2 W3 b3 W4 b4 (matrices [out][in])
+constexpr int64_t OFF_W1 = 0;
+constexpr int64_t OFF_B1 = OFF_W1 + (int64_t)WS_H * WS_IN;
+constexpr int64_t OFF_W2 = OFF_B1 + WS_H;
+constexpr int64_t OFF_B2 = OFF_W2 + (int64_t)WS_H * WS_H;
+constexpr int64_t OFF_W3 = OFF_B2 + WS_H;
+constexpr int64_t OFF_B3 = OFF_W3 + (int64_t)WS_H * WS_H;
+constexpr int64_t OFF_W4 = OFF_B3 + WS_H;
+constexpr int64_t OFF_B4 = OFF_W4 + (int64_t)WS_OUT * WS_H;
+constexpr int64_t N_PARAMS = OFF_B4 + WS_OUT;
+
+__device__ __forceinline__ float gelu_f(float x)
+{
+    return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+}
+
+__device__ __forceinline__ float gelu_grad_f(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) +
+           x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// ---------------------------------------------------------------------------
+// SIMT tile GEMMs: 128 x 64 output tile, 256 threads, 8 x 4 register block.
+// ---------------------------------------------------------------------------
+constexpr int GM = 128, GN = 64, GK = 16;
+
+template <typename TB>
+__device__ __forceinline__ float tofloat(TB v);
+template <>
+__device__ __forceinline__ float tofloat<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float tofloat<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// C(m, n) = epi(m, n, sum_k A[m*lda + k] * B[n*ldb + k]) over K (both K-contiguous).
+template <typename TB, typename Epi>
+__global__ void __launch_bounds__(256)
+k_gemm_nt(int M, int N, int K, const float* __restrict__ A, int64_t lda, const TB* __restrict__ B,
+          int64_t ldb, Epi epi)
+{
+    __shared__ float As[GK][GM + 4];
+    __shared__ float Bs[GK][GN + 4];
+    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[8][4] = {};
+    for (int kb = 0; kb < K; kb += GK) {
+#pragma unroll
+        for (int h = 0; h < GM * GK / 256; ++h) {
+            const int e = threadIdx.x + 256 * h;
+            const int row = e / GK, kk = e % GK;
+            const int m = m0 + row, k = kb + kk;
+            As[kk][row] = (m < M && k < K) ? A[(int64_t)m * lda + k] : 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < GN * GK / 256; ++h) {
+            const int e = threadIdx.x + 256 * h;
+            const int col = e / GK, kk = e % GK;
+            const int n = n0 + col, k = kb + kk;
+            Bs[kk][col] = (n < N && k < K) ? tofloat<TB>(B[(int64_t)n * ldb + k]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[8], b[4];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) a[w] = As[kk][ty * 8 + w];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[w][v] = fmaf(a[w], b[v], acc[w][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int m = m0 + ty * 8 + w, n = n0 + tx * 4 + v;
+            if (m < M && n < N) epi(m, n, acc[w][v]);
+        }
+}
+
+// Split-K C(m, n) partial = sum_{k in slice} A[k*lda + m] * B[k*ldb + n] (both
+// row-major over k), written to part[slice][m][n].
+__global__ void __launch_bounds__(256)
+k_gemm_tn_partial(int M, int N, int K, int kslice, const float* __restrict__ A, int64_t lda,
+                  const float* __restrict__ B, int64_t ldb, float* part)
+{
+    __shared__ float As[GK][GM + 4];
+    __shared__ float Bs[GK][GN + 4];
+    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
+    const int k_begin = blockIdx.z * kslice, k_end = min(K, k_begin + kslice);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[8][4] = {};
+    for (int kb = k_begin; kb < k_end; kb += GK) {
+#pragma unroll
+        for (int h = 0; h < GM * GK / 256; ++h) {
+            const int e = threadIdx.x + 256 * h;
+            const int kk = e / GM, mm = e % GM;
+            const int k = kb + kk, m = m0 + mm;
+            As[kk][mm] = (k < k_end && m < M) ? A[(int64_t)k * lda + m] : 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < GN * GK / 256; ++h) {
+            const int e = threadIdx.x + 256 * h;
+            const int kk = e / GN, nn = e % GN;
+            const int k = kb + kk, n = n0 + nn;
+            Bs[kk][nn] = (k < k_end && n < N) ? B[(int64_t)k * ldb + n] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[8], b[4];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) a[w] = As[kk][ty * 8 + w];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[w][v] = fmaf(a[w], b[v], acc[w][v]);
+        }
+        __syncthreads();
+    }
+    float* out = part + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int m = m0 + ty * 8 + w, n = n0 + tx * 4 + v;
+            if (m < M && n < N) out[(int64_t)m * N + n] = acc[w][v];
+        }
+}
+
+// dst[i] = sum over slices (fixed order) of part[s][i]
+__global__ void k_sum_slices(const float* part, int slices, int64_t count, float* dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < slices; ++z) s += part[(int64_t)z * count + i];
+        dst[i] = s;
+    }
+}
+
+// column sums of an N x C matrix in a fixed order: dst[c] = sum_n A[n*C + c]
+__global__ void k_col_sums(const float* A, int64_t N, int C, float* dst)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int64_t n = 0; n < N; ++n) s += A[n * C + c];
+    dst[c] = s;
+}
+
+struct EpiBiasGelu {            // pre = acc + b; store pre (optional) and gelu(pre)
+    const float* b; float* pre; float* out; int ldo;
+    __device__ void operator()(int m, int n, float acc) const
+    {
+        const float a = acc + b[n];
+        if (pre) pre[(int64_t)m * ldo + n] = a;
+        out[(int64_t)m * ldo + n] = gelu_f(a);
+    }
+};
+
+struct EpiGeluGrad {            // da = acc * gelu'(pre)
+    const float* pre; float* out; int ldo;
+    __device__ void operator()(int m, int n, float acc) const
+    {
+        out[(int64_t)m * ldo + n] = acc * gelu_grad_f(pre[(int64_t)m * ldo + n]);
+    }
+};
+
+// layer 1 (K = 8): a1 = X W1^T + b1, h1 = gelu(a1)
+__global__ void k_layer_in(const float* X, int64_t N, const __nv_bfloat16* w, const float* master,
+                           float* pre, float* h)
+{
+    const int64_t total = N * WS_H;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = t / WS_H;
+        const int o = (int)(t % WS_H);
+        float a = master[OFF_B1 + o];
+#pragma unroll
+        for (int k = 0; k < WS_IN; ++k)
+            a = fmaf(X[n * WS_IN + k], __bfloat162float(w[OFF_W1 + o * WS_IN + k]), a);
+        if (pre) pre[t] = a;
+        h[t] = gelu_f(a);
+    }
+}
+
+// head: out[n][j] = h3[n] . W4[j] + b4[j]   (one warp per row)
+__global__ void k_head(const float* h3, int64_t N, const __nv_bfloat16* w, const float* master,
+                       float* out)
+{
+    const int64_t n = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (n >= N) return;
+    float s[WS_OUT] = {};
+    for (int k = lane; k < WS_H; k += 32) {
+        const float hv = h3[n * WS_H + k];
+#pragma unroll
+        for (int j = 0; j < WS_OUT; ++j)
+            s[j] = fmaf(hv, __bfloat162float(w[OFF_W4 + j * WS_H + k]), s[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < WS_OUT; ++j) {
+        const float v = warp_sum(s[j]);
+        if (lane == 0) out[n * WS_OUT + j] = v + master[OFF_B4 + j];
+    }
+}
+
+// dOut and per-block loss partials
+__global__ void k_loss_grad(const float* out, const float* T, int64_t N, float* dout, double* loss_part)
+{
+    double local = 0.0;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        const float o0 = out[n * 3], o1 = out[n * 3 + 1], o2 = out[n * 3 + 2];
+        const float t0 = T[n * 3], t1 = T[n * 3 + 1], t2 = T[n * 3 + 2];
+        const float d0 = o0 - t0, d1 = o1 - t1;
+        const float sp = o2 > 0.f ? o2 + log1pf(expf(-o2)) : log1pf(expf(o2));
+        local += (double)(d0 * d0 + d1 * d1 + sp - t2 * o2);
+        const float inv = 1.0f / (float)N;
+        dout[n * 3] = 2.f * d0 * inv;
+        dout[n * 3 + 1] = 2.f * d1 * inv;
+        dout[n * 3 + 2] = (1.f / (1.f + expf(-o2)) - t2) * inv;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = local;
+    __syncthreads();
+    for (int sft = blockDim.x / 2; sft > 0; sft >>= 1) {
+        if (threadIdx.x < sft) red[threadIdx.x] += red[threadIdx.x + sft];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// da3 = (dOut W4) * gelu'(a3)
+__global__ void k_head_back(const float* dout, int64_t N, const __nv_bfloat16* w, const float* pre3,
+                            float* da3)
+{
+    const int64_t total = N * WS_H;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = t / WS_H;
+        const int k = (int)(t % WS_H);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < WS_OUT; ++j)
+            s = fmaf(dout[n * 3 + j], __bfloat162float(w[OFF_W4 + j * WS_H + k]), s);
+        da3[t] = s * gelu_grad_f(pre3[t]);
+    }
+}
+
+// gradient of W1 (K over rows, 8 inputs): g[o][k] = sum_n da1[n][o] X[n][k]
+__global__ void k_grad_w1(const float* da1, const float* X, int64_t N, float* g)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= WS_H) return;
+    float s[WS_IN] = {};
+    for (int64_t n = 0; n < N; ++n) {
+        const float d = da1[n * WS_H + o];
+#pragma unroll
+        for (int k = 0; k < WS_IN; ++k) s[k] = fmaf(d, X[n * WS_IN + k], s[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < WS_IN; ++k) g[OFF_W1 + o * WS_IN + k] = s[k];
+}
+
+// gradient of W4: g[j][k] = sum_n dout[n][j] h3[n][k]
+__global__ void k_grad_w4(const float* dout, const float* h3, int64_t N, float* g)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= WS_H) return;
+    float s[WS_OUT] = {};
+    for (int64_t n = 0; n < N; ++n) {
+        const float hv = h3[n * WS_H + k];
+#pragma unroll
+        for (int j = 0; j < WS_OUT; ++j) s[j] = fmaf(dout[n * 3 + j], hv, s[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < WS_OUT; ++j) g[OFF_W4 + j * WS_H + k] = s[j];
+}
+
+__global__ void k_transpose_bf16(const __nv_bfloat16* src, __nv_bfloat16* dst, int rows, int cols)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[i][threadIdx.x] = src[(int64_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(int64_t)c * rows + r] = t[threadIdx.x][i];
+    }
+}
+
+__global__ void k_to_bf16(const float* src, int64_t n, __nv_bfloat16* dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+__global__ void k_adam(float* master, float* m, float* v, const float* g, int64_t n, float lr,
+                       float b1, float b2, float eps, float wd, float c1, float c2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        master[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * master[i]);
+    }
+}
+
+// Kaiming-uniform initialisation from Philox draws: U(-a, a), a = sqrt(6 / fan_in)
+// for matrices, zero biases.
+__global__ void k_init_params(float* master, uint64_t seed)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N_PARAMS;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int fan_in = 0;
+        if (i < OFF_B1) fan_in = WS_IN;
+        else if (i >= OFF_W2 && i < OFF_B2) fan_in = WS_H;
+        else if (i >= OFF_W3 && i < OFF_B3) fan_in = WS_H;
+        else if (i >= OFF_W4 && i < OFF_B4) fan_in = WS_H;
+        if (fan_in == 0) { master[i] = 0.f; continue; }
+        const uint64_t r = philox_draw(PhiloxKey{ seed, 0x4D4C50ull }, 0, 7, (uint64_t)i);
+        const float u = (float)(r >> 40) * (1.0f / 16777216.0f);          // [0, 1)
+        master[i] = (2.f * u - 1.f) * sqrtf(6.f / (float)fan_in);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Model
+// ---------------------------------------------------------------------------
+struct WsModel {
+    float* master = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    __nv_bfloat16* w = nullptr;       // bf16 copy of every parameter
+    __nv_bfloat16* w2t = nullptr;     // W2^T, W3^T (bf16) for the backward products
+    __nv_bfloat16* w3t = nullptr;
+    int64_t step = 0;
+};
+
+namespace {
+
+void sync_weights(WsModel* M, cudaStream_t s)
+{
+    k_to_bf16<<<256, 256, 0, s>>>(M->master, N_PARAMS, M->w);
+    UOI_CHECK_LAUNCH();
+    dim3 g(WS_H / 32, WS_H / 32), b(32, 8);
+    k_transpose_bf16<<<g, b, 0, s>>>(M->w + OFF_W2, M->w2t, WS_H, WS_H);
+    UOI_CHECK_LAUNCH();
+    k_transpose_bf16<<<g, b, 0, s>>>(M->w + OFF_W3, M->w3t, WS_H, WS_H);
+    UOI_CHECK_LAUNCH();
+    count_launch(3);
+}
+
+unsigned blocks_for(int64_t work) { return (unsigned)std::min<int64_t>(ceil_div(work, 256), 152 * 16); }
+
+struct Acts {
+    DevBuf a1, h1, a2, h2, a3, h3, out;
+};
+
+// Forward over N rows; keeps pre-activations when train is set.
+void forward(WsModel* M, const float* X, int64_t N, Acts& A, bool train, cudaStream_t s)
+{
+    const size_t hsz = sizeof(float) * (size_t)N * WS_H;
+    if (train) { A.a1.alloc(hsz, s); A.a2.alloc(hsz, s); A.a3.alloc(hsz, s); }
+    A.h1.alloc(hsz, s); A.h2.alloc(hsz, s); A.h3.alloc(hsz, s);
+    A.out.alloc(sizeof(float) * (size_t)N * WS_OUT, s);
+    k_layer_in<<<blocks_for(N * WS_H), 256, 0, s>>>(X, N, M->w, M->master,
+                                                   train ? A.a1.as<float>() : nullptr, A.h1.as<float>());
+    UOI_CHECK_LAUNCH();
+    dim3 g((unsigned)ceil_div(N, GM), WS_H / GN);
+    EpiBiasGelu e2{ M->master + OFF_B2, train ? A.a2.as<float>() : nullptr, A.h2.as<float>(), WS_H };
+    k_gemm_nt<__nv_bfloat16, EpiBiasGelu><<<g, 256, 0, s>>>((int)N, WS_H, WS_H, A.h1.as<float>(), WS_H,
+                                                            M->w + OFF_W2, WS_H, e2);
+    UOI_CHECK_LAUNCH();
+    EpiBiasGelu e3{ M->master + OFF_B3, train ? A.a3.as<float>() : nullptr, A.h3.as<float>(), WS_H };
+    k_gemm_nt<__nv_bfloat16, EpiBiasGelu><<<g, 256, 0, s>>>((int)N, WS_H, WS_H, A.h2.as<float>(), WS_H,
+                                                            M->w + OFF_W3, WS_H, e3);
+    UOI_CHECK_LAUNCH();
+    k_head<<<(unsigned)ceil_div(N * 32, 256), 256, 0, s>>>(A.h3.as<float>(), N, M->w, M->master,
+                                                           A.out.as<float>());
+    UOI_CHECK_LAUNCH();
+    count_launch(4);
+}
+
+// Weight gradient g[o][k] = sum_n dA[n][o] H[n][k] (512 x 512) by split-K.
+void grad_square(const float* dA, const float* H, int64_t N, float* g, cudaStream_t s)
+{
+    const int slices = (int)std::min<int64_t>(32, std::max<int64_t>(1, N / 2048));
+    const int kslice = (int)ceil_div(N, slices);
+    DevBuf part(sizeof(float) * (size_t)slices * WS_H * WS_H, s);
+    dim3 gr(WS_H / GM, WS_H / GN, (unsigned)slices);
+    k_gemm_tn_partial<<<gr, 256, 0, s>>>(WS_H, WS_H, (int)N, kslice, dA, WS_H, H, WS_H, part.as<float>());
+    UOI_CHECK_LAUNCH();
+    k_sum_slices<<<blocks_for((int64_t)WS_H * WS_H), 256, 0, s>>>(part.as<float>(), slices,
+                                                                   (int64_t)WS_H * WS_H, g);
+    UOI_CHECK_LAUNCH();
+    count_launch(2);
+}
+
+// Full gradient into g (N_PARAMS floats); returns the mean loss.
+double loss_grad(WsModel* M, const float* X, const float* T, int64_t N, float* g, cudaStream_t s)
+{
+    Acts A;
+    forward(M, X, N, A, true, s);
+    DevBuf dout(sizeof(float) * (size_t)N * 3, s);
+    const int lb = 256;
+    DevBuf lp(sizeof(double) * lb, s);
+    k_loss_grad<<<lb, 256, 0, s>>>(A.out.as<float>(), T, N, dout.as<float>(), lp.as<double>());
+    UOI_CHECK_LAUNCH();
+    const size_t hsz = sizeof(float) * (size_t)N * WS_H;
+    DevBuf da3(hsz, s), dtmp(hsz, s);
+    k_grad_w4<<<WS_H / 128, 128, 0, s>>>(dout.as<float>(), A.h3.as<float>(), N, g);
+    UOI_CHECK_LAUNCH();
+    k_col_sums<<<1, 32, 0, s>>>(dout.as<float>(), N, WS_OUT, g + OFF_B4);
+    UOI_CHECK_LAUNCH();
+    k_head_back<<<blocks_for(N * WS_H), 256, 0, s>>>(dout.as<float>(), N, M->w, A.a3.as<float>(),
+                                                     da3.as<float>());
+    UOI_CHECK_LAUNCH();
+    // layer 3
+    grad_square(da3.as<float>(), A.h2.as<float>(), N, g + OFF_W3, s);
+    k_col_sums<<<WS_H / 128, 128, 0, s>>>(da3.as<float>(), N, WS_H, g + OFF_B3);
+    UOI_CHECK_LAUNCH();
+    dim3 gg((unsigned)ceil_div(N, GM), WS_H / GN);
+    EpiGeluGrad eg2{ A.a2.as<float>(), dtmp.as<float>(), WS_H };           // da2
+    k_gemm_nt<__nv_bfloat16, EpiGeluGrad><<<gg, 256, 0, s>>>((int)N, WS_H, WS_H, da3.as<float>(), WS_H,
+                                                             M->w3t, WS_H, eg2);
+    UOI_CHECK_LAUNCH();
+    // layer 2
+    grad_square(dtmp.as<float>(), A.h1.as<float>(), N, g + OFF_W2, s);
+    k_col_sums<<<WS_H / 128, 128, 0, s>>>(dtmp.as<float>(), N, WS_H, g + OFF_B2);
+    UOI_CHECK_LAUNCH();
+    EpiGeluGrad eg1{ A.a1.as<float>(), da3.as<float>(), WS_H };            // da1 (reuses da3)
+    k_gemm_nt<__nv_bfloat16, EpiGeluGrad><<<gg, 256, 0, s>>>((int)N, WS_H, WS_H, dtmp.as<float>(), WS_H,
+                                                             M->w2t, WS_H, eg1);
+    UOI_CHECK_LAUNCH();
+    // layer 1
+    k_grad_w1<<<WS_H / 128, 128, 0, s>>>(da3.as<float>(), X, N, g);
+    UOI_CHECK_LAUNCH();
+    k_col_sums<<<WS_H / 128, 128, 0, s>>>(da3.as<float>(), N, WS_H, g + OFF_B1);
+    UOI_CHECK_LAUNCH();
+    count_launch(11);
+    std::vector<double> h(lb);
+    UOI_CUDA(cudaMemcpyAsync(h.data(), lp.ptr, sizeof(double) * lb, cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    double L = 0.0;
+    for (double v : h) L += v;
+    return L / (double)N;
+}
+
+// Features of row (k, j, e, i) and, when z/u are given, the targets.
+__global__ void k_ws_features(const double* gdiag, const double* Bm, const double* nk,
+                              const double* lam, int32_t q, int64_t p, int64_t r, int32_t B,
+                              double rho, const double* zt, const double* ut, float* F, float* T)
+{
+    const int64_t total = (int64_t)B * q * r * p;
+    const double l0 = lam[0], lmin = lam[q - 1];
+    const double span = (q > 1 && lmin > 0.0 && lmin < l0) ? log(lmin / l0) : -1.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t % p;
+        const int64_t col = t / p;                        // (k*q + j)*r + e
+        const int64_t e = col % r;
+        const int64_t j = (col / r) % q;
+        const int64_t k = col / (r * q);
+        const double lj = lam[j], lp = lam[j > 0 ? j - 1 : 0];
+        const double c = Bm[(k * p + i) * r + e] / nk[k];
+        const double d = gdiag[k * p + i] / nk[k];
+        const double cj = c / lj, cp = c / lp;
+        const double sj = (cj > 1.0 ? cj - 1.0 : (cj < -1.0 ? cj + 1.0 : 0.0)) / d;
+        const double sp = (cp > 1.0 ? cp - 1.0 : (cp < -1.0 ? cp + 1.0 : 0.0)) / d;
+        float* f = F + t * WS_IN;
+        f[0] = (float)(lj / l0);
+        f[1] = (float)(log(lj / l0) / span);
+        f[2] = (float)fmax(-50.0, fmin(50.0, cj));
+        f[3] = (float)fmin(50.0, fabs(cj));
+        f[4] = (float)d;
+        f[5] = (float)fmax(-50.0, fmin(50.0, sj));
+        f[6] = (float)fmax(-50.0, fmin(50.0, cp));
+        f[7] = (float)fmax(-50.0, fmin(50.0, sp * (lp / lj)));
+        if (T) {
+            // z in units of the proxy solution's scale lambda_j max(1, min(|c|/lambda_j, 50)) / d
+            const double scale = lj * fmax(1.0, fmin(50.0, fabs(cj))) / d;
+            T[t * 3] = (float)(zt[t] / scale);
+            T[t * 3 + 1] = (float)(rho * ut[t] / lj);
+            T[t * 3 + 2] = zt[t] != 0.0 ? 1.f : 0.f;
+        }
+    }
+}
+
+// Predicted start: z0 = o0 times the proxy scale lambda_j max(1, min(|c|/lambda_j, 50)) / d
+// where the active logit is positive, else 0; u0 = (lambda_j / rho) clamp(o1, -1.5, 1.5).
+__global__ void k_ws_start(const float* out, const float* F, const double* lam, int32_t q, int64_t p,
+                           int64_t r, int64_t total, double rho, float* z0, float* u0)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (t / (p * r)) % q;
+        const float lj = (float)lam[j];
+        const float scale = lj * fmaxf(1.f, F[t * WS_IN + 3]) / F[t * WS_IN + 4];
+        const float o0 = out[t * 3], o1 = out[t * 3 + 1], o2 = out[t * 3 + 2];
+        z0[t] = o2 > 0.f ? o0 * scale : 0.f;
+        u0[t] = (lj / (float)rho) * fminf(1.5f, fmaxf(-1.5f, o1));
+    }
+}
+
+__global__ void k_gdiag(const double* G, int64_t p, int32_t B, double* out)
+{
+    const int64_t total = (int64_t)B * p;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / p, i = t % p;
+        out[t] = G[(k * p + i) * p + i];
+    }
+}
+
+}  // namespace
+
+WsModel* ws_create(uint64_t seed, cudaStream_t s)
+{
+    WsModel* M = new WsModel();
+    try {
+        UOI_CUDA(cudaMalloc(&M->master, sizeof(float) * N_PARAMS));
+        UOI_CUDA(cudaMalloc(&M->m, sizeof(float) * N_PARAMS));
+        UOI_CUDA(cudaMalloc(&M->v, sizeof(float) * N_PARAMS));
+        UOI_CUDA(cudaMalloc(&M->w, sizeof(__nv_bfloat16) * N_PARAMS));
+        UOI_CUDA(cudaMalloc(&M->w2t, sizeof(__nv_bfloat16) * WS_H * WS_H));
+        UOI_CUDA(cudaMalloc(&M->w3t, sizeof(__nv_bfloat16) * WS_H * WS_H));
+        UOI_CUDA(cudaMemsetAsync(M->m, 0, sizeof(float) * N_PARAMS, s));
+        UOI_CUDA(cudaMemsetAsync(M->v, 0, sizeof(float) * N_PARAMS, s));
+        k_init_params<<<256, 256, 0, s>>>(M->master, seed);
+        UOI_CHECK_LAUNCH();
+        count_launch();
+        sync_weights(M, s);
+    } catch (...) {
+        ws_destroy(M);
+        throw;
+    }
+    return M;
+}
+
+void ws_destroy(WsModel* M)
+{
+    if (!M) return;
+    cudaFree(M->master); cudaFree(M->m); cudaFree(M->v);
+    cudaFree(M->w); cudaFree(M->w2t); cudaFree(M->w3t);
+    delete M;
+}
+
+int64_t ws_param_count() { return N_PARAMS; }
+
+void ws_set_params(WsModel* M, const float* host_or_dev, cudaStream_t s)
+{
+    UOI_CUDA(cudaMemcpyAsync(M->master, host_or_dev, sizeof(float) * N_PARAMS, cudaMemcpyDefault, s));
+    UOI_CUDA(cudaMemsetAsync(M->m, 0, sizeof(float) * N_PARAMS, s));
+    UOI_CUDA(cudaMemsetAsync(M->v, 0, sizeof(float) * N_PARAMS, s));
+    M->step = 0;
+    sync_weights(M, s);
+}
+
+void ws_get_params(WsModel* M, float* host_or_dev, cudaStream_t s)
+{
+    UOI_CUDA(cudaMemcpyAsync(host_or_dev, M->master, sizeof(float) * N_PARAMS, cudaMemcpyDefault, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+}
+
+void ws_forward(WsModel* M, const float* X, int64_t N, float* out, cudaStream_t s)
+{
+    const int64_t chunk = 1 << 18;
+    for (int64_t n0 = 0; n0 < N; n0 += chunk) {
+        const int64_t nn = std::min(chunk, N - n0);
+        Acts A;
+        forward(M, X + n0 * WS_IN, nn, A, false, s);
+        UOI_CUDA(cudaMemcpyAsync(out + n0 * WS_OUT, A.out.ptr, sizeof(float) * nn * WS_OUT,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+double ws_loss_grad(WsModel* M, const float* X, const float* T, int64_t N, float* g, cudaStream_t s)
+{
+    return loss_grad(M, X, T, N, g, s);
+}
+
+// Adam over shuffled mini-batches (Philox permutation of the rows per epoch).
+double ws_train(WsModel* M, const float* X, const float* T, int64_t N, int32_t epochs, int32_t batch,
+                float lr, uint64_t seed, cudaStream_t s)
+{
+    DevBuf g(sizeof(float) * N_PARAMS, s);
+    DevBuf xb(sizeof(float) * (size_t)batch * WS_IN, s), tb(sizeof(float) * (size_t)batch * 3, s);
+    std::vector<int64_t> order((size_t)N);
+    double last = 0.0;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f, wd = 1e-5f;
+    std::vector<float> hx((size_t)batch * WS_IN), ht((size_t)batch * 3);
+    std::vector<float> allx((size_t)N * WS_IN), allt((size_t)N * 3);
+    UOI_CUDA(cudaMemcpyAsync(allx.data(), X, sizeof(float) * allx.size(), cudaMemcpyDefault, s));
+    UOI_CUDA(cudaMemcpyAsync(allt.data(), T, sizeof(float) * allt.size(), cudaMemcpyDefault, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    for (int32_t ep = 0; ep < epochs; ++ep) {
+        // deterministic shuffle: sort rows by a splitmix of (seed, epoch, row)
+        for (int64_t i = 0; i < N; ++i) order[(size_t)i] = i;
+        uint64_t st = seed * 0x9E3779B97F4A7C15ull + (uint64_t)ep + 1;
+        for (int64_t i = N - 1; i > 0; --i) {
+            st += 0x9E3779B97F4A7C15ull;
+            uint64_t zz = st;
+            zz = (zz ^ (zz >> 30)) * 0xBF58476D1CE4E5B9ull;
+            zz = (zz ^ (zz >> 27)) * 0x94D049BB133111EBull;
+            zz ^= zz >> 31;
+            const int64_t jdx = (int64_t)(zz % (uint64_t)(i + 1));
+            std::swap(order[(size_t)i], order[(size_t)jdx]);
+        }
+        double ep_loss = 0.0;
+        int64_t nb = 0;
+        for (int64_t b0 = 0; b0 + batch <= N; b0 += batch) {
+            for (int32_t t = 0; t < batch; ++t) {
+                const int64_t src = order[(size_t)(b0 + t)];
+                std::memcpy(&hx[(size_t)t * WS_IN], &allx[(size_t)src * WS_IN], sizeof(float) * WS_IN);
+                std::memcpy(&ht[(size_t)t * 3], &allt[(size_t)src * 3], sizeof(float) * 3);
+            }
+            UOI_CUDA(cudaMemcpyAsync(xb.ptr, hx.data(), xb.bytes, cudaMemcpyHostToDevice, s));
+            UOI_CUDA(cudaMemcpyAsync(tb.ptr, ht.data(), tb.bytes, cudaMemcpyHostToDevice, s));
+            ep_loss += loss_grad(M, xb.as<float>(), tb.as<float>(), batch, g.as<float>(), s);
+            ++nb;
+            M->step += 1;
+            const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
+            k_adam<<<256, 256, 0, s>>>(M->master, M->m, M->v, g.as<float>(), N_PARAMS, lr, b1, b2, eps,
+                                       wd, c1, c2);
+            UOI_CHECK_LAUNCH();
+            count_launch();
+            sync_weights(M, s);
+        }
+        last = nb ? ep_loss / (double)nb : 0.0;
+    }
+    UOI_CUDA(cudaStreamSynchronize(s));
+    return last;
+}
+
+// Features (and targets) for all rows of B groups from moments already on the device.
+void ws_build_features(const double* G, const double* Bm, const double* nk, const double* lam,
+                       int32_t q, int64_t p, int64_t r, int32_t B, double rho, const double* zt,
+                       const double* ut, float* F, float* T, cudaStream_t s)
+{
+    DevBuf gd(sizeof(double) * (size_t)(B * p), s);
+    k_gdiag<<<blocks_for(B * p), 256, 0, s>>>(G, p, B, gd.as<double>());
+    UOI_CHECK_LAUNCH();
+    k_ws_features<<<blocks_for((int64_t)B * q * r * p), 256, 0, s>>>(gd.as<double>(), Bm, nk, lam, q, p,
+                                                                   r, B, rho, zt, ut, F, T);
+    UOI_CHECK_LAUNCH();
+    count_launch(2);
+}
+
+void ws_start_state(const float* out, const float* F, const double* lam, int32_t q, int64_t p,
+                    int64_t r, int64_t total, double rho, float* z0, float* u0, cudaStream_t s)
+{
+    k_ws_start<<<blocks_for(total), 256, 0, s>>>(out, F, lam, q, p, r, total, rho, z0, u0);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+// Weights file: "UOIMLP01", int32 in, hidden, out, layers, then the FP32 parameters.
+void ws_save(WsModel* M, const char* path)
+{
+    std::vector<float> h((size_t)N_PARAMS);
+    ws_get_params(M, h.data(), nullptr);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) throw Error(UOI_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    const char magic[8] = { 'U', 'O', 'I', 'M', 'L', 'P', '0', '1' };
+    const int32_t hdr[4] = { WS_IN, WS_H, WS_OUT, 3 };
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int32_t), 4, f) == 4 &&
+              std::fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+    std::fclose(f);
+    if (!ok) throw Error(UOI_ERR_INVALID_ARG, std::string("short write to ") + path);
+}
+
+WsModel* ws_load(const char* path, cudaStream_t s)
+{
+    FILE* f = std::fopen(path, "rb");
+    if (!f) throw Error(UOI_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    char magic[8];
+    int32_t hdr[4];
+    std::vector<float> h((size_t)N_PARAMS);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "UOIMLP01", 8) == 0 &&
+              std::fread(hdr, sizeof(int32_t), 4, f) == 4 && hdr[0] == WS_IN && hdr[1] == WS_H &&
+              hdr[2] == WS_OUT && hdr[3] == 3 &&
+              std::fread(h.data(), sizeof(float), h.size(), f) == h.size();
+    std::fclose(f);
+    if (!ok) throw Error(UOI_ERR_INVALID_ARG, std::string("not a warm-start weights file: ") + path);
+    WsModel* M = ws_create(0, s);
+    ws_set_params(M, h.data(), s);
+    UOI_CUDA(cudaStreamSynchronize(s));
+    return M;
+}
+
+}  // namespace uoi

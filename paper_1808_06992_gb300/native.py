@@ -46,7 +46,7 @@ class UoiDiag(C.Structure):
         ("ols_singular", C.c_int64), ("gpu_launches", C.c_int64),
         ("ms_gram_tc", C.c_float), ("n_gram_tc", C.c_int64), ("flops_gram_tc", C.c_double),
         ("ms_xupdate", C.c_float), ("n_xupdate", C.c_int64), ("flops_xupdate", C.c_double),
-        ("bytes_xupdate", C.c_double),
+        ("bytes_xupdate", C.c_double), ("warm_start_used", C.c_int32),
     ]
 
     def as_dict(self):
@@ -81,6 +81,17 @@ def lib():
         L.uoi_weighted_moments.argtypes = [vp, vp, i64, i64, i64, vp, i32, i32, vp, vp, vp]
         L.lasso_admm_batch_noalloc.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d,
                                                i32, i32, vp, vp, vp, vp]
+        L.uoi_ws_param_count.restype = i64
+        L.uoi_ws_create.argtypes = [C.c_uint64, C.POINTER(vp)]
+        L.uoi_ws_load.argtypes = [C.c_char_p, C.POINTER(vp)]
+        L.uoi_ws_save.argtypes = [vp, C.c_char_p]
+        L.uoi_ws_free.argtypes = [vp]
+        L.uoi_ws_set_params.argtypes = [vp, vp]
+        L.uoi_ws_get_params.argtypes = [vp, vp]
+        L.uoi_ws_forward.argtypes = [vp, vp, i64, vp]
+        L.uoi_ws_loss_grad.argtypes = [vp, vp, vp, i64, C.POINTER(d), vp]
+        L.uoi_ws_train.argtypes = [vp, vp, vp, i64, i32, i32, C.c_float, C.c_uint64, C.POINTER(d)]
+        L.uoi_ws_dataset.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d, i32, vp, vp, vp]
         L.uoi_status_string.argtypes = [C.c_int]
         L.uoi_status_string.restype = C.c_char_p
         L.uoi_get_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
@@ -91,7 +102,9 @@ def lib():
 
 EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_var_fit", "uoi_fit_traced",
             "lasso_admm_batch", "lasso_admm_batch_noalloc", "uoi_weighted_moments",
-            "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
+            "uoi_ws_param_count", "uoi_ws_create", "uoi_ws_load", "uoi_ws_save", "uoi_ws_free",
+            "uoi_ws_set_params", "uoi_ws_get_params", "uoi_ws_forward", "uoi_ws_loss_grad",
+            "uoi_ws_train", "uoi_ws_dataset", "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
 
 
 class UoiError(RuntimeError):
@@ -150,7 +163,7 @@ def _empty(like, shape, dtype):
 def make_params(B1=20, B2=20, q=16, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol=1e-6,
                 rel_tol=1e-6, max_iter=1000, train_frac=0.8, seed=0, problem_id=0, block_len=0,
                 bagging=BAG_MEDIAN, split_mode=SPLIT_PER_BOOTSTRAP, precision=PREC_FP64,
-                warm_start=WARM_PATH, stream=None):
+                warm_start=WARM_PATH, stream=None, mlp_weights_path=None):
     prm = UoiParams()
     lib().uoi_params_default(C.byref(prm))
     prm.B1, prm.B2, prm.q = B1, B2, q
@@ -164,6 +177,8 @@ def make_params(B1=20, B2=20, q=16, lambdas=None, lambda_min_ratio=1e-3, rho=1.0
     prm.block_len, prm.bagging, prm.split_mode = block_len, bagging, split_mode
     prm.precision, prm.warm_start = precision, warm_start
     prm.stream = stream
+    if mlp_weights_path:
+        prm.mlp_weights_path = mlp_weights_path.encode()
     return prm, keep
 
 
@@ -299,6 +314,98 @@ def lasso_admm_batch_noalloc(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_
                                         _ptr(iters), _ptr(conv), stream)
     _check(st)
     return dict(beta=beta, iters=iters, conv=conv, status=st)
+
+
+class WarmStartModel:
+    """The learned warm-start network (device resident), see uoi_ws_* in include/uoi.h."""
+
+    def __init__(self, seed=0, path=None):
+        h = C.c_void_p()
+        if path is not None:
+            _check(lib().uoi_ws_load(path.encode(), C.byref(h)))
+        else:
+            _check(lib().uoi_ws_create(seed, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().uoi_ws_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def param_count():
+        return int(lib().uoi_ws_param_count())
+
+    def get_params(self):
+        out = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib().uoi_ws_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().uoi_ws_set_params(self.h, a.ctypes.data))
+
+    def forward(self, X):
+        if _is_torch(X):
+            import torch
+            X = X.contiguous().float()
+            out = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+        else:
+            X = np.ascontiguousarray(X, dtype=np.float32)
+            out = np.empty((X.shape[0], 3), dtype=np.float32)
+        _check(lib().uoi_ws_forward(self.h, _ptr(X), X.shape[0], _ptr(out)))
+        return out
+
+    def loss_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.empty(self.param_count(), dtype=np.float32)
+        L = C.c_double()
+        _check(lib().uoi_ws_loss_grad(self.h, X.ctypes.data, T.ctypes.data, X.shape[0],
+                                      C.byref(L), g.ctypes.data))
+        return float(L.value), g
+
+    def train(self, X, T, epochs=10, batch=4096, lr=1e-3, seed=0):
+        X = X.contiguous().float() if _is_torch(X) else np.ascontiguousarray(X, dtype=np.float32)
+        T = T.contiguous().float() if _is_torch(T) else np.ascontiguousarray(T, dtype=np.float32)
+        L = C.c_double()
+        _check(lib().uoi_ws_train(self.h, _ptr(X), _ptr(T), X.shape[0], epochs, batch, lr, seed,
+                                  C.byref(L)))
+        return float(L.value)
+
+    def save(self, path):
+        _check(lib().uoi_ws_save(self.h, path.encode()))
+
+
+def ws_dataset(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6, max_iter=1000):
+    """(features N x 8, targets N x 3) from path-warm FP64 ADMM, N = B q r p."""
+    X = _prep(X, np.float64)
+    Y = _prep(Y, np.float64)
+    if Y.ndim == 1:
+        Y = Y.reshape(-1, 1)
+    n, p = X.shape
+    r = Y.shape[1]
+    w = _prep(weights, np.uint32).reshape(-1, n)
+    B = w.shape[0]
+    lam = _prep(lambdas, np.float64)
+    q = lam.shape[0]
+    N = B * q * r * p
+    if _is_torch(X):
+        import torch
+        F = torch.empty((N, 8), dtype=torch.float32, device=X.device)
+        T = torch.empty((N, 3), dtype=torch.float32, device=X.device)
+    else:
+        F = np.empty((N, 8), dtype=np.float32)
+        T = np.empty((N, 3), dtype=np.float32)
+    _check(lib().uoi_ws_dataset(_ptr(X), _ptr(Y), n, p, r, _ptr(w), B, _ptr(lam), q, rho, abs_tol,
+                                rel_tol, max_iter, _ptr(F), _ptr(T), None))
+    return F, T
 
 
 def shutdown():

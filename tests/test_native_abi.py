@@ -60,7 +60,7 @@ def test_params_default():
     (dict(rho=0.0), native.ERR_INVALID_ARG),
     (dict(train_frac=1.0), native.ERR_INVALID_ARG),
     (dict(max_iter=0), native.ERR_INVALID_ARG),
-    (dict(warm_start=native.WARM_LEARNED), native.ERR_UNSUPPORTED),
+    (dict(warm_start=7), native.ERR_INVALID_ARG),
     (dict(B2=200), native.ERR_UNSUPPORTED),
 ])
 def test_invalid_parameters_rejected_on_host(kw, code):
