@@ -237,13 +237,13 @@ int uoi_ws_train(uoi_ws_model* model, const float* X, const float* T, int64_t N,
                  int32_t batch, float lr, uint64_t seed, double* final_loss);
 /* Training rows from the method's own solutions: path-warm FP64 ADMM over
  * B bootstraps (weights B x n) x q lambdas x r responses, then for every
- * (k, j, e, i) the 8 features
+ * (k, j, e, i) the 8 features (c = X^T W y_e / n_k, d = diag(X^T W X)/n_k,
+ * x0 = (X^T W X/n_k + rho I)^{-1} c the ridge solution, a_j = x0 d / lambda_j,
+ * ratios clipped to [-50, 50])
  *   lambda_j/lambda_0, log(lambda_j/lambda_0)/log(lambda_{q-1}/lambda_0),
- *   c_i/lambda_j, |c_i|/lambda_j, d_i, S_1(c_i/lambda_j)/d_i, c_i/lambda_{j-1},
- *   S_1(c_i/lambda_{j-1})/d_i * lambda_{j-1}/lambda_j
- * (c = X^T W y_e / n_k, d = diag(X^T W X)/n_k) and the 3 targets z_i/s_i with
- * s_i = lambda_j max(1, min(|c_i|/lambda_j, 50))/d_i, rho u_i/lambda_j and
- * [z_i != 0].  features_out: N x 8, targets_out: N x 3 floats
+ *   c/lambda_j, d, a_j, |a_j|, c/lambda_{j-1}, a_{j-1}
+ * and the 3 targets z/s clipped to [-4, 4] with s = (lambda_j/d) max(1, |a_j|),
+ * rho u/lambda_j and [z != 0].  features_out: N x 8, targets_out: N x 3 floats
  * (N = B q r p), host or device. */
 int uoi_ws_dataset(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
                    const uint32_t* weights, int32_t B, const double* lambdas, int32_t q,

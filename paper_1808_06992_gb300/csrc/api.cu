@@ -244,25 +244,12 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
         const double mm = (double)m;
         UOI_CUDA(cudaMemcpyAsync(nk.ptr, &mm, sizeof(double), cudaMemcpyHostToDevice, s));
     }
-    // learned warm start: predicted (z, u) for every column, then the cold schedule
-    DevBuf z0, u0;
-    if (ws) {
-        const int64_t rows = (int64_t)B * q * r * p;
-        DevBuf F(sizeof(float) * (size_t)rows * 8, s), out(sizeof(float) * (size_t)rows * 3, s);
-        ws_build_features(G.as<double>(), Bm.as<double>(), nk.as<double>(), lam, q, p, r, B, rho,
-                          nullptr, nullptr, F.as<float>(), nullptr, s);
-        ws_forward(ws, F.as<float>(), rows, out.as<float>(), s);
-        z0.alloc(sizeof(float) * (size_t)rows, s);
-        u0.alloc(sizeof(float) * (size_t)rows, s);
-        ws_start_state(out.as<float>(), F.as<float>(), lam, q, p, r, rows, rho, z0.as<float>(),
-                       u0.as<float>(), s);
-    }
     int t1 = tm ? tm->mark() : 0;
     DevBuf st(sizeof(DevStatus), s);
     UOI_CUDA(cudaMemsetAsync(st.ptr, 0, st.bytes, s));
     DevBuf A(sizeof(T) * (size_t)(B * p * p), s);
     build_and_factor<T>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<T>(), st.as<DevStatus>(), s);
-    G.release();
+    if (!ws) G.release();
     check_status(st.as<DevStatus>(), s, "Cholesky of G/n + rho I");
     DevBuf Linv(sizeof(T) * (size_t)(B * p * p), s), M(sizeof(T) * (size_t)(B * p * p), s);
     DevBuf c(sizeof(T) * (size_t)(B * p * r), s);
@@ -270,6 +257,23 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                        M.as<T>(), c.as<T>(), s);
     Linv.release();
     A.release();
+    // learned warm start: predicted z for every column, the dual consistent with
+    // it, then the cold schedule from that state
+    DevBuf z0, u0;
+    if (ws) {
+        const int64_t rows = (int64_t)B * q * r * p;
+        DevBuf F(sizeof(float) * (size_t)rows * 8, s), out(sizeof(float) * (size_t)rows * 3, s);
+        ws_build_features<T>(G.as<double>(), Bm.as<double>(), nk.as<double>(), c.as<T>(), lam, q, p,
+                             r, B, rho, nullptr, nullptr, F.as<float>(), nullptr, s);
+        ws_forward(ws, F.as<float>(), rows, out.as<float>(), s);
+        z0.alloc(sizeof(float) * (size_t)rows, s);
+        u0.alloc(sizeof(float) * (size_t)rows, s);
+        ws_start_state(out.as<float>(), F.as<float>(), lam, q, p, r, rows, rho, z0.as<float>(),
+                       u0.as<float>(), s);
+        ws_consistent_dual(G.as<double>(), Bm.as<double>(), nk.as<double>(), z0.as<float>(), p, r, q,
+                           B, rho, u0.as<float>(), s);
+        G.release();
+    }
     int t2 = tm ? tm->mark() : 0;
     AdmmProblem<T> P;
     P.G = B; P.p = p; P.r = r; P.q = q;
@@ -851,8 +855,9 @@ int uoi_ws_dataset(const double* X, const double* Y, int64_t n, int64_t p, int64
         DevOut<float> fo, to;
         fo.init(features_out, (size_t)rows * 8, s);
         to.init(targets_out, (size_t)rows * 3, s);
-        ws_build_features(G.as<double>(), Bm.as<double>(), nk.as<double>(), ld, q, p, r, B, rho,
-                          zs.as<double>(), us.as<double>(), fo.dev, to.dev, s);
+        ws_build_features<double>(G.as<double>(), Bm.as<double>(), nk.as<double>(), c.as<double>(),
+                                  ld, q, p, r, B, rho, zs.as<double>(), us.as<double>(), fo.dev,
+                                  to.dev, s);
         fo.finish(s);
         to.finish(s);
         UOI_CUDA(cudaStreamSynchronize(s));

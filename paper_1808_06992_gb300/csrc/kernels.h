@@ -145,11 +145,16 @@ void ws_forward(WsModel* M, const float* X, int64_t N, float* out, cudaStream_t 
 double ws_loss_grad(WsModel* M, const float* X, const float* T, int64_t N, float* g, cudaStream_t s);
 double ws_train(WsModel* M, const float* X, const float* T, int64_t N, int32_t epochs, int32_t batch,
                 float lr, uint64_t seed, cudaStream_t s);
-void ws_build_features(const double* G, const double* Bm, const double* nk, const double* lam,
-                       int32_t q, int64_t p, int64_t r, int32_t B, double rho, const double* zt,
-                       const double* ut, float* F, float* T, cudaStream_t s);
+template <typename TC>
+void ws_build_features(const double* G, const double* Bm, const double* nk, const TC* x0,
+                       const double* lam, int32_t q, int64_t p, int64_t r, int32_t B, double rho,
+                       const double* zt, const double* ut, float* F, float* T, cudaStream_t s);
 void ws_start_state(const float* out, const float* F, const double* lam, int32_t q, int64_t p,
                     int64_t r, int64_t total, double rho, float* z0, float* u0, cudaStream_t s);
+// u0 = (b/n_k - (G/n_k) z0) / rho for every column (the dual consistent with z0).
+void ws_consistent_dual(const double* G, const double* Bm, const double* nk, const float* z0,
+                        int64_t p, int64_t r, int32_t q, int32_t B, double rho, float* u0,
+                        cudaStream_t s);
 void ws_save(WsModel* M, const char* path);
 WsModel* ws_load(const char* path, cudaStream_t s);
 

@@ -1,21 +1,22 @@
 // mlp.cu -- G8: the learned warm start of the ADMM selection step.
 //
 // A per-feature network predicts, for every (bootstrap k, lambda_j, equation e,
-// feature i), the converged scaled ADMM state of column (k, j, e): z_i / s_i with
-// s_i = lambda_j max(1, min(|c_i|/lambda_j, 50)) / d_i (the scale of the
-// soft-threshold proxy solution), rho u_i / lambda_j, and whether z_i != 0.  Inputs (8 per row) are lambda and
-// moment statistics that exist before any iteration: lambda_j / lambda_0,
-// log(lambda_j / lambda_0) / log(lambda_min / lambda_0), the correlation
-// c_i = (X^T W y_e)_i / n_k scaled by lambda_j and by lambda_{j-1}, |c_i| / lambda_j,
-// the Gram diagonal d_i = G_ii / n_k, and the soft-threshold proxy solutions
-// S_1(c_i / lambda) / d_i at lambda_j and at the previous lambda_{j-1}.
+// feature i), the converged scaled ADMM state of column (k, j, e): z_i in units
+// of the ridge proxy's scale, rho u_i / lambda_j, and whether z_i != 0.  Inputs
+// (8 per row, listed at k_ws_features) are lambda and statistics that exist
+// before any iteration: the marginal correlation, the Gram diagonal, and the
+// ridge solution (G/n + rho I)^{-1} b/n -- the first x-update from zero --
+// scaled by lambda_j and by the previous lambda_{j-1}.
 // Network: 8 -> 512 -> 512 -> 512 -> 3 with exact-erf GELU, BF16 weights used
 // by every product (FP32 master copy in the optimizer), FP32 accumulation and
 // FP32 activations.  Loss per row: squared errors of the two state outputs plus
 // the logistic loss of the active logit, averaged over rows.
 //
-// The network only chooses where ADMM starts; the converged answer is the
-// same convex minimiser, which path-warm ADMM checks (tests) and falls back to.
+// The network only chooses where ADMM starts: its z is used, and the dual is
+// set consistent with it (rho u = b/n - (G/n) z, the fixed point of the
+// x-update with x = z), so an exact z starts ADMM at its fixed point.  The
+// converged answer is the same convex minimiser, which path-warm ADMM checks
+// (tests) and falls back to.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -497,10 +498,18 @@ double loss_grad(WsModel* M, const float* X, const float* T, int64_t N, float* g
     return L / (double)N;
 }
 
-// Features of row (k, j, e, i) and, when z/u are given, the targets.
+// Features of row (k, j, e, i) and, when z/u are given, the targets.  x0 is the
+// ridge solution (G/n_k + rho I)^{-1} b/n_k (the first x-update from zero), c the
+// marginal correlation b/n_k, d = G_ii/n_k.  With a_j = x0 d / lambda_j:
+//   f0 lambda_j/lambda_0, f1 log(lambda_j/lambda_0)/log(lambda_{q-1}/lambda_0),
+//   f2 c/lambda_j, f3 d, f4 a_j, f5 |a_j|, f6 c/lambda_{j-1}, f7 a_{j-1}
+// (ratios clipped to [-50, 50]).  Targets: z / s with s = (lambda_j/d) max(1, |f4|)
+// clipped to [-4, 4], rho u / lambda_j, [z != 0].
+template <typename TC>
 __global__ void k_ws_features(const double* gdiag, const double* Bm, const double* nk,
-                              const double* lam, int32_t q, int64_t p, int64_t r, int32_t B,
-                              double rho, const double* zt, const double* ut, float* F, float* T)
+                              const TC* x0, const double* lam, int32_t q, int64_t p, int64_t r,
+                              int32_t B, double rho, const double* zt, const double* ut, float* F,
+                              float* T)
 {
     const int64_t total = (int64_t)B * q * r * p;
     const double l0 = lam[0], lmin = lam[q - 1];
@@ -515,30 +524,30 @@ __global__ void k_ws_features(const double* gdiag, const double* Bm, const doubl
         const double lj = lam[j], lp = lam[j > 0 ? j - 1 : 0];
         const double c = Bm[(k * p + i) * r + e] / nk[k];
         const double d = gdiag[k * p + i] / nk[k];
-        const double cj = c / lj, cp = c / lp;
-        const double sj = (cj > 1.0 ? cj - 1.0 : (cj < -1.0 ? cj + 1.0 : 0.0)) / d;
-        const double sp = (cp > 1.0 ? cp - 1.0 : (cp < -1.0 ? cp + 1.0 : 0.0)) / d;
+        const double xr = (double)x0[(k * r + e) * p + i];
+        auto clip = [](double v) { return fmax(-50.0, fmin(50.0, v)); };
+        const double aj = clip(xr * d / lj), ap = clip(xr * d / lp);
         float* f = F + t * WS_IN;
         f[0] = (float)(lj / l0);
         f[1] = (float)(log(lj / l0) / span);
-        f[2] = (float)fmax(-50.0, fmin(50.0, cj));
-        f[3] = (float)fmin(50.0, fabs(cj));
-        f[4] = (float)d;
-        f[5] = (float)fmax(-50.0, fmin(50.0, sj));
-        f[6] = (float)fmax(-50.0, fmin(50.0, cp));
-        f[7] = (float)fmax(-50.0, fmin(50.0, sp * (lp / lj)));
+        f[2] = (float)clip(c / lj);
+        f[3] = (float)d;
+        f[4] = (float)aj;
+        f[5] = (float)fabs(aj);
+        f[6] = (float)clip(c / lp);
+        f[7] = (float)ap;
         if (T) {
-            // z in units of the proxy solution's scale lambda_j max(1, min(|c|/lambda_j, 50)) / d
-            const double scale = lj * fmax(1.0, fmin(50.0, fabs(cj))) / d;
-            T[t * 3] = (float)(zt[t] / scale);
+            const double scale = (lj / d) * fmax(1.0, fabs((double)(float)aj));
+            T[t * 3] = (float)fmax(-4.0, fmin(4.0, zt[t] / scale));
             T[t * 3 + 1] = (float)(rho * ut[t] / lj);
             T[t * 3 + 2] = zt[t] != 0.0 ? 1.f : 0.f;
         }
     }
 }
 
-// Predicted start: z0 = o0 times the proxy scale lambda_j max(1, min(|c|/lambda_j, 50)) / d
-// where the active logit is positive, else 0; u0 = (lambda_j / rho) clamp(o1, -1.5, 1.5).
+// Predicted start: z0 = o0 (lambda_j / d) max(1, |f4|) where the active logit is
+// positive, else 0; u0 = (lambda_j / rho) clamp(o1, -1.5, 1.5) (replaced by the
+// consistent dual in the fit).
 __global__ void k_ws_start(const float* out, const float* F, const double* lam, int32_t q, int64_t p,
                            int64_t r, int64_t total, double rho, float* z0, float* u0)
 {
@@ -546,10 +555,46 @@ __global__ void k_ws_start(const float* out, const float* F, const double* lam, 
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = (t / (p * r)) % q;
         const float lj = (float)lam[j];
-        const float scale = lj * fmaxf(1.f, F[t * WS_IN + 3]) / F[t * WS_IN + 4];
+        const float scale = (lj / F[t * WS_IN + 3]) * fmaxf(1.f, fabsf(F[t * WS_IN + 4]));
         const float o0 = out[t * 3], o1 = out[t * 3 + 1], o2 = out[t * 3 + 2];
         z0[t] = o2 > 0.f ? o0 * scale : 0.f;
         u0[t] = (lj / (float)rho) * fminf(1.5f, fmaxf(-1.5f, o1));
+    }
+}
+
+// Dual consistent with a start z0 at the x-update's fixed point (x = z):
+// rho u0 = b/n_k - (G/n_k) z0, for every column of every group.  One thread per
+// (feature i, 8 columns); G is symmetric, so G[k][i] is read along k with
+// consecutive i across threads.  FP32 arithmetic (G taken to FP32 with integer
+// operations); the start only decides how many iterations ADMM needs.
+__global__ void __launch_bounds__(128)
+k_ws_dual(const double* G, const double* Bm, const double* nk, const float* z0, int64_t p, int64_t r,
+          int32_t q, double rho, float* u0)
+{
+    const int g = blockIdx.z;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t cols = (int64_t)q * r;
+    const int64_t c0 = (int64_t)blockIdx.y * 8;
+    const double* Gg = G + (size_t)g * p * p;
+    const float inv_n = (float)(1.0 / nk[g]);
+    float acc[8] = {};
+    if (i < p) {
+        for (int64_t k = 0; k < p; ++k) {
+            const float gik = f64_to_f32_int(Gg[k * p + i]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int64_t col = c0 + c;
+                if (col < cols) acc[c] = fmaf(gik, z0[((int64_t)g * cols + col) * p + k], acc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int64_t col = c0 + c;
+            if (col >= cols) continue;
+            const int64_t e = col % r;
+            const float b = f64_to_f32_int(Bm[((int64_t)g * p + i) * r + e]) * inv_n;
+            u0[((int64_t)g * cols + col) * p + i] = (b - acc[c] * inv_n) / (float)rho;
+        }
     }
 }
 
@@ -683,24 +728,44 @@ double ws_train(WsModel* M, const float* X, const float* T, int64_t N, int32_t e
     return last;
 }
 
-// Features (and targets) for all rows of B groups from moments already on the device.
-void ws_build_features(const double* G, const double* Bm, const double* nk, const double* lam,
-                       int32_t q, int64_t p, int64_t r, int32_t B, double rho, const double* zt,
-                       const double* ut, float* F, float* T, cudaStream_t s)
+// Features (and targets) for all rows of B groups from moments and the ridge
+// solution x0 (B x r x p, the ADMM right-hand side c_k) already on the device.
+template <typename TC>
+void ws_build_features(const double* G, const double* Bm, const double* nk, const TC* x0,
+                       const double* lam, int32_t q, int64_t p, int64_t r, int32_t B, double rho,
+                       const double* zt, const double* ut, float* F, float* T, cudaStream_t s)
 {
     DevBuf gd(sizeof(double) * (size_t)(B * p), s);
     k_gdiag<<<blocks_for(B * p), 256, 0, s>>>(G, p, B, gd.as<double>());
     UOI_CHECK_LAUNCH();
-    k_ws_features<<<blocks_for((int64_t)B * q * r * p), 256, 0, s>>>(gd.as<double>(), Bm, nk, lam, q, p,
-                                                                   r, B, rho, zt, ut, F, T);
+    k_ws_features<TC><<<blocks_for((int64_t)B * q * r * p), 256, 0, s>>>(gd.as<double>(), Bm, nk, x0,
+                                                                       lam, q, p, r, B, rho, zt, ut,
+                                                                       F, T);
     UOI_CHECK_LAUNCH();
     count_launch(2);
 }
+
+template void ws_build_features<double>(const double*, const double*, const double*, const double*,
+                                        const double*, int32_t, int64_t, int64_t, int32_t, double,
+                                        const double*, const double*, float*, float*, cudaStream_t);
+template void ws_build_features<float>(const double*, const double*, const double*, const float*,
+                                       const double*, int32_t, int64_t, int64_t, int32_t, double,
+                                       const double*, const double*, float*, float*, cudaStream_t);
 
 void ws_start_state(const float* out, const float* F, const double* lam, int32_t q, int64_t p,
                     int64_t r, int64_t total, double rho, float* z0, float* u0, cudaStream_t s)
 {
     k_ws_start<<<blocks_for(total), 256, 0, s>>>(out, F, lam, q, p, r, total, rho, z0, u0);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void ws_consistent_dual(const double* G, const double* Bm, const double* nk, const float* z0,
+                        int64_t p, int64_t r, int32_t q, int32_t B, double rho, float* u0,
+                        cudaStream_t s)
+{
+    dim3 g((unsigned)ceil_div(p, 128), (unsigned)ceil_div((int64_t)q * r, 8), (unsigned)B);
+    k_ws_dual<<<g, 128, 0, s>>>(G, Bm, nk, z0, p, r, q, rho, u0);
     UOI_CHECK_LAUNCH();
     count_launch();
 }

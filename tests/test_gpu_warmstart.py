@@ -106,7 +106,7 @@ def test_learned_warm_start_trains_gains_and_is_judged(tmp_path):
     assert lw["diag"]["warm_start_used"] == native.WARM_LEARNED
     it_cold, it_path, it_learned = (int(o["sel_iters"].sum()) for o in (cold, pw, lw))
     print(f"ADMM iterations: cold {it_cold}, path {it_path}, learned {it_learned}")
-    assert it_learned < it_cold
+    assert it_learned < 0.95 * it_cold               # measured: about 10 % fewer than cold
     # judge: the learned start reaches the same minimiser as path warm start
     lam = pw["lambdas"]
     worst_l, worst_p = 0.0, 0.0
