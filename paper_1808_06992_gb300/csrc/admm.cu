@@ -629,6 +629,12 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
         UOI_CUDA(cudaMemsetAsync(next.ptr, 0, next.bytes, s));
         if (try_resident<T>(d, next.as<int32_t>(), s)) return;
     }
+    if constexpr (sizeof(T) == 4) {
+        if (admm_tc_available()) {               // FP32 state: x-update on the tensor cores
+            admm_solve_tc(reinterpret_cast<const AdmmProblem<float>&>(P), s);
+            return;
+        }
+    }
     // streaming schedule
     const int64_t slots = (int64_t)P.G * nchains;
     const int p = (int)P.p;

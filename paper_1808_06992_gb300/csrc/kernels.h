@@ -129,6 +129,9 @@ struct AdmmProblem {
 };
 template <typename T>
 void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
+// Streaming schedule with the tensor-core x-update (FP32 state, p > resident limit).
+bool admm_tc_available();
+void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s);
 // Resident schedule only, with the caller's zeroed per-group chain counters
 // (G int32).  Returns false (launching nothing) when p is too large for it.
 template <typename T>

@@ -1,0 +1,494 @@
+// xupdate_tc.cu -- G4 on the tensor cores: the ADMM x-update of the mixed form
+// (x = c + rho M (z - u), Eq. 5 with the cached inverse) as tcgen05 products,
+// with the soft threshold, dual update and residual norms fused into the
+// epilogue.
+//
+// Accuracy: M and V = z - u are each split into three bf16 pieces
+// (v = h + m + l, residue <= 2^-24 |v|) and the six products h.H, h.M, m.H,
+// h.L, m.M, l.H are summed (the dropped terms are below 2^-24).  The large
+// h.H products go to a double-buffered TMEM accumulator that the epilogue drains
+// every 128 k into compensated FP32 pairs (the tensor core's FP32 accumulation
+// truncates about a third of an ulp per K=16 step); the five small products,
+// 2^-8 and 2^-16 smaller, share one accumulator read once at the end.  The
+// x-update is then accurate to ~1e-7 relative, like the FP32 CUDA-core product.
+//
+// Work per launch: every chain of every group (converged chains are skipped in
+// the epilogue and keep their state).  Grid: (row tiles of 128, chain tiles of
+// NT <= 128, groups).  Warp 0: TMA producer (2-stage ring of 96 KB); warp 1:
+// TMEM allocation and MMA issue; warps 2-9: epilogue.  Waits are bounded (~1 s)
+// and report UOI_ERR_TIMEOUT.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace uoi {
+
+namespace {
+using namespace tc;
+
+constexpr int XT_TM = 128;
+constexpr int XT_TK = 64;
+constexpr int XT_STAGES = 2;
+constexpr int XT_A_BYTES = XT_TM * XT_TK * 2;          // 16 KB per piece
+constexpr int XT_B_MAX = 128 * XT_TK * 2;              // 16 KB per piece at NT = 128
+constexpr int XT_STAGE_BYTES = 3 * XT_A_BYTES + 3 * XT_B_MAX;
+constexpr int XT_SMEM = XT_STAGES * XT_STAGE_BYTES + 1024;
+constexpr int XT_THREADS = 320;
+constexpr uint32_t XT_TMEM_COLS = 512;                 // A1[0] at 0, A1[1] at 128, A2 at 256
+constexpr int XT_CHUNK_STAGES = 2;                     // drain h.H every 128 k
+
+struct XtArgs {
+    int32_t G, q, r, p, nchains, NT, kst, RT, warm;
+    int64_t ppad;                 // rows per group in the M pieces (multiple of 128)
+    int64_t kpad;                 // k extent (multiple of 64)
+    int64_t slots;
+    const float* c;               // G x r x p
+    const double* lambdas;
+    float rho;
+    float* z; float* u;           // slots x p
+    __nv_bfloat16* vnext;         // 3 x slots x kpad
+    const int32_t* slot_j;
+    const uint8_t* live;
+    float* norms;                 // slots x RT x 5
+    int32_t* err;
+};
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l)
+{
+    h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+}
+
+__global__ void __launch_bounds__(XT_THREADS, 1)
+k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CUtensorMap tmV,
+             XtArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t full_bar[XT_STAGES], empty_bar[XT_STAGES], accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ float red[2][4][64][5];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rt = blockIdx.x, ct = blockIdx.y, g = blockIdx.z;
+    const int i0 = rt * XT_TM, n0 = ct * a.NT;
+    const int nchunks = (a.kst + XT_CHUNK_STAGES - 1) / XT_CHUNK_STAGES;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t b_bytes = (uint32_t)a.NT * XT_TK * 2;
+    const uint32_t stage_tx = 3u * XT_A_BYTES + 3u * b_bytes;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < XT_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 256); }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(XT_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        const int rowA = (int)((int64_t)g * a.ppad + i0);
+        const int rowB = g * a.nchains + n0;
+        for (int s_ = 0; s_ < a.kst; ++s_) {
+            const int s = s_ % XT_STAGES;
+            if (s_ >= XT_STAGES && !mbar_wait(&empty_bar[s], ((s_ / XT_STAGES) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            const uint32_t st = sbase + s * XT_STAGE_BYTES;
+            mbar_expect_tx(&full_bar[s], stage_tx);
+            const int k0 = s_ * XT_TK;
+            for (int pc = 0; pc < 3; ++pc)
+                tma_load_3d(st + pc * XT_A_BYTES, &tmM, &full_bar[s], k0, rowA, pc);
+            for (int pc = 0; pc < 3; ++pc)
+                tma_load_3d(st + 3 * XT_A_BYTES + pc * b_bytes, &tmV, &full_bar[s], k0, rowB, pc);
+        }
+        if (abort_flag)
+            for (int s_ = max(0, a.kst - XT_STAGES); s_ < a.kst; ++s_)
+                mbar_wait(&full_bar[s_ % XT_STAGES], (s_ / XT_STAGES) & 1, &abort_flag);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_bf16(XT_TM, a.NT);
+        const uint32_t d2 = tmem + 256u;
+        bool first2 = true;
+        int s_ = 0;
+        for (int c = 0; c < nchunks && !abort_flag; ++c) {
+            const int b = c & 1;
+            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d1 = tmem + (uint32_t)(b * 128);
+            const int send = min(a.kst, (c + 1) * XT_CHUNK_STAGES);
+            bool first1 = true;
+            for (; s_ < send; ++s_) {
+                const int s = s_ % XT_STAGES;
+                if (!mbar_wait(&full_bar[s], (s_ / XT_STAGES) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + s * XT_STAGE_BYTES;
+                const uint64_t Ah = smem_desc_sw128(st), Am = smem_desc_sw128(st + XT_A_BYTES);
+                const uint64_t Al = smem_desc_sw128(st + 2 * XT_A_BYTES);
+                const uint32_t bb = st + 3 * XT_A_BYTES;
+                const uint64_t Bh = smem_desc_sw128(bb), Bm = smem_desc_sw128(bb + b_bytes);
+                const uint64_t Bl = smem_desc_sw128(bb + 2 * b_bytes);
+#pragma unroll
+                for (int ks = 0; ks < XT_TK / 16; ++ks) {
+                    const uint64_t adv = (uint64_t)(ks * 32 >> 4);
+                    mma_bf16(d1, Ah + adv, Bh + adv, idesc, first1 ? 0u : 1u);
+                    mma_bf16(d2, Ah + adv, Bm + adv, idesc, first2 ? 0u : 1u);
+                    mma_bf16(d2, Am + adv, Bh + adv, idesc, 1u);
+                    mma_bf16(d2, Ah + adv, Bl + adv, idesc, 1u);
+                    mma_bf16(d2, Am + adv, Bm + adv, idesc, 1u);
+                    mma_bf16(d2, Al + adv, Bh + adv, idesc, 1u);
+                    first1 = false;
+                    first2 = false;
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            if (abort_flag) break;
+            mma_commit(&accf_bar[b]);
+        }
+        mma_commit(&done_bar);
+        int dummy = 0;
+        mbar_wait(&done_bar, 0, &dummy);
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int i = i0 + quad * 32 + lane;
+        float acc[64], cmp[64];
+#pragma unroll
+        for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            if (!mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int cb = 0; cb < 2; ++cb) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 128 + half * 64 + cb * 32), v);
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const float x = v[t], sa = acc[cb * 32 + t];
+                    const float sum = sa + x;
+                    const float bv = sum - sa;
+                    cmp[cb * 32 + t] += (sa - (sum - bv)) + (x - bv);
+                    acc[cb * 32 + t] = sum;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce_bar[b]);
+        }
+        // small products, once all MMAs are done
+        {
+            int dummy = 0;
+            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);
+        }
+        tc_fence_after();
+        float part[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+            float v2[32];
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(256 + half * 64 + cb * 32), v2);
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int n = half * 64 + cb * 32 + t;           // chain within the tile
+                const int chain = n0 + n;
+                float pr[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
+                const bool valid = n < a.NT && chain < a.nchains && i < a.p && !abort_flag;
+                const int64_t sl = (int64_t)g * a.nchains + chain;
+                if (valid && a.live[sl]) {
+                    const int e = a.warm ? chain : chain % a.r;
+                    const float prod = (acc[cb * 32 + t] + cmp[cb * 32 + t]) + v2[t];
+                    const float x = a.c[((int64_t)g * a.r + e) * a.p + i] + a.rho * prod;
+                    const float kappa = (float)a.lambdas[a.slot_j[sl]] / a.rho;
+                    const int64_t o = sl * a.p + i;
+                    const float zp = a.z[o];
+                    const float vv = x + a.u[o];
+                    const float zn = soft_threshold(vv, kappa);
+                    const float un = vv - zn;
+                    a.z[o] = zn;
+                    a.u[o] = un;
+                    __nv_bfloat16 h, m, l;
+                    split3(zn - un, h, m, l);
+                    const int64_t vo = sl * a.kpad + i;
+                    a.vnext[vo] = h;
+                    a.vnext[(int64_t)a.slots * a.kpad + vo] = m;
+                    a.vnext[2 * (int64_t)a.slots * a.kpad + vo] = l;
+                    const float d = x - zn, dz = zn - zp;
+                    pr[0] = d * d; pr[1] = dz * dz; pr[2] = x * x; pr[3] = zn * zn; pr[4] = un * un;
+                }
+                // sum over the 32 rows of this warp (fixed tree), keep in lane 0
+#pragma unroll
+                for (int qq = 0; qq < 5; ++qq) {
+                    const float sv = warp_sum(pr[qq]);
+                    if (lane == 0) red[half][quad][cb * 32 + t][qq] = sv;
+                }
+            }
+        }
+        (void)part;
+    }
+    tc_fence_before();
+    __syncthreads();
+    // norms of this row tile: sum of the four row quarters in a fixed order
+    if (threadIdx.x < 128) {
+        const int n = threadIdx.x;
+        const int half = n >> 6, col = n & 63;
+        const int chain = n0 + n;
+        if (n < a.NT && chain < a.nchains) {
+            const int64_t sl = (int64_t)g * a.nchains + chain;
+            if (a.live[sl]) {
+#pragma unroll
+                for (int qq = 0; qq < 5; ++qq) {
+                    const float tot = ((red[half][0][col][qq] + red[half][1][col][qq]) + red[half][2][col][qq]) +
+                                      red[half][3][col][qq];
+                    a.norms[(sl * a.RT + rt) * 5 + qq] = tot;
+                }
+            }
+        }
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(XT_TMEM_COLS));
+    }
+}
+
+// M_g (FP32, p x p) -> three bf16 pieces at [piece][g*ppad + i][k] (zero padded).
+__global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
+                          __nv_bfloat16* out)
+{
+    const int64_t per = (int64_t)G * ppad * kpad;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t % kpad, row = t / kpad;
+        const int64_t g = row / ppad, i = row % ppad;
+        const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] : 0.f;
+        __nv_bfloat16 h, m, l;
+        split3(x, h, m, l);
+        out[t] = h;
+        out[per + t] = m;
+        out[2 * per + t] = l;
+    }
+}
+
+// Initial state: z, u (zero or the given start), the pieces of V = z - u, live flags.
+__global__ void k_xt_init(int64_t slots, int64_t p, int64_t kpad, const float* z0, const float* u0,
+                          float* z, float* u, __nv_bfloat16* v, uint8_t* live)
+{
+    const int64_t total = slots * kpad;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = t / kpad, i = t % kpad;
+        float zz = 0.f, uu = 0.f;
+        if (i < p) {
+            if (z0) { zz = z0[sl * p + i]; uu = u0[sl * p + i]; }
+            z[sl * p + i] = zz;
+            u[sl * p + i] = uu;
+        }
+        __nv_bfloat16 h, m, l;
+        split3(zz - uu, h, m, l);
+        v[t] = h;
+        v[slots * kpad + t] = m;
+        v[2 * slots * kpad + t] = l;
+        if (i == 0) live[sl] = 1;
+    }
+}
+
+// Convergence check of every live slot (one warp each): fixed-order sum of the
+// row-tile norms, stopping test of Eq. 5's ADMM, output of finished columns,
+// path advance, live count for the host.
+__global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t nchains, int32_t RT,
+                           int32_t warm, int32_t max_iter, float rho, float abs_tol, float rel_tol,
+                           float sqrtp, const float* z, const float* norms, int32_t* slot_j,
+                           const int32_t* slot_jend, int32_t* slot_it, uint8_t* live, double* beta,
+                           int32_t* iters, uint8_t* conv, uint64_t* family, int32_t W,
+                           int32_t* live_count)
+{
+    const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= (int64_t)G * nchains || !live[sl]) return;
+    float tot[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
+    for (int t0 = 0; t0 < RT; t0 += 32) {
+        float loc[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
+        if (t0 + lane < RT)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) loc[c] = norms[(sl * RT + t0 + lane) * 5 + c];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) tot[c] += warp_sum(loc[c]);
+    }
+    int it = slot_it[sl] + 1;
+    const float xn = sqrtf(tot[2]), zn = sqrtf(tot[3]);
+    const float eps_pri = sqrtp * abs_tol + rel_tol * fmaxf(xn, zn);
+    const float eps_dual = sqrtp * abs_tol + rel_tol * rho * sqrtf(tot[4]);
+    const bool converged = sqrtf(tot[0]) <= eps_pri && rho * sqrtf(tot[1]) <= eps_dual;
+    bool still = true;
+    if (converged || it >= max_iter) {
+        const int g = (int)(sl / nchains), cid = (int)(sl % nchains);
+        const int e = warm ? cid : cid % r;
+        const int j = slot_j[sl];
+        const int64_t col_je = (int64_t)j * r + e;
+        const int64_t col = (int64_t)g * q * r + col_je;
+        for (int a0 = 0; 32 * a0 < p; ++a0) {
+            const int i = lane + 32 * a0;
+            const float zi = i < p ? z[sl * p + i] : 0.f;
+            if (beta && i < p) beta[col * p + i] = (double)zi;
+            if (family) {
+                const unsigned bal = __ballot_sync(0xffffffffu, zi != 0.f);
+                if (lane == 0) {
+                    const int shift = (a0 & 1) * 32;
+                    const uint64_t mask = ((uint64_t)bal << shift) | ~(0xFFFFFFFFull << shift);
+                    atomicAnd((unsigned long long*)&family[col_je * W + (a0 >> 1)],
+                              (unsigned long long)mask);
+                }
+            }
+        }
+        if (lane == 0) {
+            if (iters) iters[col] = it;
+            if (conv) conv[col] = converged ? 1 : 0;
+        }
+        if (j + 1 < slot_jend[sl]) {
+            if (lane == 0) slot_j[sl] = j + 1;
+            it = 0;
+        } else {
+            still = false;
+        }
+    }
+    if (lane == 0) {
+        slot_it[sl] = it;
+        if (!still) live[sl] = 0;
+        else atomicAdd(live_count, 1);
+    }
+}
+
+__global__ void k_xt_slots(int32_t G, int32_t nchains, int32_t r, int32_t q, int32_t warm,
+                           int32_t* slot_j, int32_t* slot_jend, int32_t* slot_it)
+{
+    const int64_t total = (int64_t)G * nchains;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int cid = (int)(s % nchains);
+        slot_j[s] = warm ? 0 : cid / r;
+        slot_jend[s] = warm ? q : cid / r + 1;
+        slot_it[s] = 0;
+    }
+}
+
+}  // namespace
+
+bool admm_tc_available() { return gram_tc_available(); }
+
+// Streaming ADMM with the tensor-core x-update (FP32 state).  Same outputs as
+// admm_solve<float>.
+void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
+{
+    const int32_t nchains = P.warm ? (int32_t)P.r : (int32_t)(P.r * P.q);
+    const int64_t slots = (int64_t)P.G * nchains;
+    const int p = (int)P.p;
+    const int64_t ppad = ceil_div(p, XT_TM) * XT_TM;
+    const int64_t kpad = ceil_div(p, XT_TK) * XT_TK;
+    const int RT = (int)(ppad / XT_TM);
+    const int NT = (int)std::min<int64_t>(128, ceil_div(nchains, 16) * 16);
+    const int kst = (int)(kpad / XT_TK);
+    DevBuf mp(sizeof(__nv_bfloat16) * 3 * (size_t)P.G * ppad * kpad, s);
+    k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad, 256), 8192), 256, 0, s>>>(
+        P.M, P.G, p, ppad, kpad, mp.as<__nv_bfloat16>());
+    UOI_CHECK_LAUNCH();
+    DevBuf zb(sizeof(float) * (size_t)slots * p, s), ub(sizeof(float) * (size_t)slots * p, s);
+    DevBuf v0(sizeof(__nv_bfloat16) * 3 * (size_t)slots * kpad, s);
+    DevBuf v1(sizeof(__nv_bfloat16) * 3 * (size_t)slots * kpad, s);
+    DevBuf nb(sizeof(float) * (size_t)slots * RT * 5, s);
+    DevBuf sj(sizeof(int32_t) * slots, s), sje(sizeof(int32_t) * slots, s), sit(sizeof(int32_t) * slots, s);
+    DevBuf live(slots, s), cnt(sizeof(int32_t), s), err(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
+    const bool start = P.z0 && !P.warm;
+    k_xt_init<<<(unsigned)std::min<int64_t>(ceil_div(slots * kpad, 256), 8192), 256, 0, s>>>(
+        slots, p, kpad, start ? P.z0 : nullptr, start ? P.u0 : nullptr, zb.as<float>(), ub.as<float>(),
+        v0.as<__nv_bfloat16>(), live.as<uint8_t>());
+    UOI_CHECK_LAUNCH();
+    // v1 holds the pieces of V for slots that do not change in an iteration
+    UOI_CUDA(cudaMemcpyAsync(v1.ptr, v0.ptr, v0.bytes, cudaMemcpyDeviceToDevice, s));
+    k_xt_slots<<<(unsigned)std::min<int64_t>(ceil_div(slots, 256), 4096), 256, 0, s>>>(
+        P.G, nchains, (int32_t)P.r, P.q, P.warm, sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>());
+    UOI_CHECK_LAUNCH();
+    count_launch(3);
+    const CUtensorMap mM = make_map_bf16_k64(mp.ptr, kpad, (int64_t)P.G * ppad, 3, XT_TM);
+    const CUtensorMap mV0 = make_map_bf16_k64(v0.ptr, kpad, slots, 3, NT);
+    const CUtensorMap mV1 = make_map_bf16_k64(v1.ptr, kpad, slots, 3, NT);
+    UOI_CUDA(cudaFuncSetAttribute(k_xupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM));
+    XtArgs a;
+    a.G = P.G; a.q = P.q; a.r = (int32_t)P.r; a.p = p; a.nchains = nchains; a.NT = NT; a.kst = kst;
+    a.RT = RT; a.warm = P.warm; a.ppad = ppad; a.kpad = kpad; a.slots = slots;
+    a.c = P.c; a.lambdas = P.lambdas; a.rho = (float)P.rho;
+    a.z = zb.as<float>(); a.u = ub.as<float>();
+    a.slot_j = sj.as<int32_t>(); a.live = live.as<uint8_t>(); a.norms = nb.as<float>();
+    a.err = err.as<int32_t>();
+    const dim3 grid((unsigned)RT, (unsigned)ceil_div(nchains, NT), (unsigned)P.G);
+    const dim3 gc((unsigned)ceil_div(slots * 32, 256));
+    int32_t* host_cnt = nullptr;
+    UOI_CUDA(cudaMallocHost(&host_cnt, sizeof(int32_t)));
+    const int64_t bound = (int64_t)(P.warm ? P.q : 1) * P.max_iter + 2;
+    const int W = (int)((p + 63) / 64);
+    bool done = false;
+    try {
+        for (int64_t it = 0; it < bound && !done; ++it) {
+            const bool even = (it & 1) == 0;
+            a.vnext = (even ? v1 : v0).as<__nv_bfloat16>();
+            UOI_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int32_t), s));
+            ktimer_begin(TK_XUPDATE, s);
+            k_xupdate_tc<<<grid, XT_THREADS, XT_SMEM, s>>>(mM, even ? mV0 : mV1, a);
+            UOI_CHECK_LAUNCH();
+            ktimer_end(TK_XUPDATE, s, 0.0, 0.0);
+            k_xt_check<<<gc, 256, 0, s>>>(P.G, P.q, (int32_t)P.r, p, nchains, RT, P.warm, P.max_iter,
+                                          (float)P.rho, (float)P.abs_tol, (float)P.rel_tol,
+                                          (float)sqrt((double)p), zb.as<float>(), nb.as<float>(),
+                                          sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>(),
+                                          live.as<uint8_t>(), P.beta, P.iters, P.conv, P.family, W,
+                                          cnt.as<int32_t>());
+            UOI_CHECK_LAUNCH();
+            count_launch(2);
+            if ((it + 1) % 8 == 0 || it + 1 == bound) {
+                int32_t herr = 0;
+                UOI_CUDA(cudaMemcpyAsync(host_cnt, cnt.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                UOI_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                UOI_CUDA(cudaStreamSynchronize(s));
+                if (herr) throw Error(herr, "tensor-core x-update: a bounded pipeline wait expired");
+                done = *host_cnt == 0;
+            }
+        }
+    } catch (...) {
+        cudaFreeHost(host_cnt);
+        throw;
+    }
+    cudaFreeHost(host_cnt);
+    if (!done) throw Error(UOI_ERR_TIMEOUT, "ADMM loop exceeded its iteration bound");
+}
+
+}  // namespace uoi

@@ -221,3 +221,23 @@ def test_mixed_form_c1_within_1e5():
     fam_r = bits_to_bool(ref["family"], 50)
     assert (fam_g != fam_r).sum() == 0
     assert rel_l2(gpu["beta"], ref["beta"]) <= 1e-5
+
+
+@pytest.mark.parametrize("warm", [0, 1])
+def test_mixed_tensor_core_xupdate_vs_oracle(warm):
+    # p > 192 in the mixed form takes the tensor-core x-update (3-piece bf16 split,
+    # six products, compensated accumulation); it must reach the oracle's ADMM
+    # solutions to the level of the stopping tolerance.
+    d = synth.lasso_problem(1200, 300, 20, seed=31, sigma=0.5, toeplitz_rho=0.5)
+    n = d.X.shape[0]
+    w = np.stack([oracle.selection_weights(n, 0, 0, 0, k) for k in range(3)])
+    lam = oracle.lambda_grid(oracle.lambda_max(d.X, d.y), 8)
+    ref = oracle.lasso_admm_batch(d.X, d.y, w, lam, warm_start=warm)
+    gpu = native.lasso_admm_batch(d.X, d.y, w, lam, warm_start=warm, precision=native.PREC_MIXED)
+    assert gpu["conv"].all()
+    worst = max(rel_l2(gpu["beta"][idx], ref["beta"][idx]) for idx in np.ndindex(*ref["beta"].shape[:3]))
+    assert worst <= 1e-4, worst
+    thr = lam[None, :, None, None]
+    amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
+    assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
+    assert np.abs(gpu["iters"].astype(int) - ref["iters"]).max() <= max(3, int(0.1 * ref["iters"].max()))
