@@ -106,6 +106,9 @@ typedef struct uoi_diag {
     double   flops_xupdate;       /* 2 p^2 per active column-iteration                   */
     double   bytes_xupdate;       /* M once per group-iteration + 6 p-vectors per column */
     int32_t  warm_start_used;     /* UOI_WARM_* actually used (LEARNED falls back to PATH) */
+    int64_t  ols_fp64;            /* OLS solves refused by the FP32-factor + FP64-refinement
+                                     solver (small pivot or stalled refinement) and
+                                     factored in FP64 instead                            */
 } uoi_diag;
 
 /* Optional intermediate results of a fit, for testing (every pointer nullable,

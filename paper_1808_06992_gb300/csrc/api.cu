@@ -464,12 +464,12 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     double* losses = loss_o.dev;
     if (!losses) { loss_b.alloc(sizeof(double) * (size_t)(B2 * q * r), s); losses = loss_b.as<double>(); }
     DevBuf sing(sizeof(int32_t) * (size_t)(B2 * q * r), s);
-    ols_losses(Gt.as<double>(), Bt.as<double>(), Ge.as<double>(), Be.as<double>(), yye.as<double>(),
+    int64_t n_ols64 = ols_losses(Gt.as<double>(), Bt.as<double>(), Ge.as<double>(), Be.as<double>(), yye.as<double>(),
                fam.as<uint64_t>(), p, r, q, B2, losses, sing.as<int32_t>(), s);
     DevBuf jst(sizeof(int32_t) * B2, s);
     loss_argmin(losses, B2, q, r, jst.as<int32_t>(), s);
     DevBuf chosen(sizeof(double) * (size_t)(B2 * r * p), s);
-    ols_chosen(Gt.as<double>(), Bt.as<double>(), fam.as<uint64_t>(), jst.as<int32_t>(), p, r, q, B2,
+    n_ols64 += ols_chosen(Gt.as<double>(), Bt.as<double>(), fam.as<uint64_t>(), jst.as<int32_t>(), p, r, q, B2,
                chosen.as<double>(), s);
     DevOut<double> bo;
     bo.init(beta_out, (size_t)(r * p), s);
@@ -537,6 +537,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
             diag->flops_xupdate = x.flops;
             diag->bytes_xupdate = x.bytes;
             diag->warm_start_used = warm_used;
+            diag->ols_fp64 = n_ols64;
         }
     }
     return (its.noncon > 0 || nsing > 0) ? UOI_OK_WITH_WARNINGS : UOI_OK;

@@ -2,7 +2,9 @@
 // argmin over the family and bagging (Alg. 1/2 model estimation, Eq. 3-4).
 //
 // For estimation bootstrap k and family member S_j (per response e):
-//   beta = argmin || W^{1/2} (y_e - X_S b) ||   via Cholesky of G'_k[S,S] (FP64)
+//   beta = argmin || W^{1/2} (y_e - X_S b) ||   from G'_k[S,S] (FP64 moments):
+//   FP32 Cholesky + FP64 iterative refinement, FP64 Cholesky where FP32 is
+//   not safe (see k_ols_mixed)
 //   L_kje = sum_{t in E^k} (y_te - x_t beta)^2
 //         = y_E'y_E - 2 beta' (X_E'y_E)_S + beta' G^E_k[S,S] beta
 // j*_k = argmin_j sum_e L_kje (ties -> smallest j); beta*_e = median (or mean)
@@ -34,6 +36,10 @@ struct OlsArgs {
     int64_t solves;
     int smax;                                // max support size
     bool use_smem;
+    const int32_t* list;                     // solve indices to run (null: 0 .. solves-1)
+    int32_t* fb_list;                        // mixed pass: solves left to the FP64 kernel
+    int32_t* fb_count;
+    float* fscratch;                         // mixed pass: global packed factor (per CTA), or null
 };
 
 __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
@@ -48,7 +54,8 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
     __shared__ double s_dmax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    for (int64_t t = blockIdx.x; t < a.solves; t += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < a.solves; it += gridDim.x) {
+        const int64_t t = a.list ? a.list[it] : it;
         int k, j, e;
         if (a.jstar) { k = (int)(t / a.r); e = (int)(t % a.r); j = a.jstar[k]; }
         else { k = (int)(t / ((int64_t)a.q * a.r)); const int64_t rem = t % ((int64_t)a.q * a.r);
@@ -163,6 +170,188 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
     }
 }
 
+// Mixed-precision form of the same solve: Cholesky of G'_k[S,S] rounded to FP32
+// (packed lower triangle), then iterative refinement with FP64 residuals
+// r = b - G x until the correction is at FP64 rounding level, so the result
+// agrees with an FP64 factorisation to ~kappa * 1e-16.  A solve whose FP32
+// pivots fall below 1e-3 of the largest diagonal (where FP32 cannot certify the
+// 1e-12 singularity test) or whose refinement stalls is queued for k_ols.
+constexpr float OLS_F32_PIVOT = 1e-3f;
+constexpr int OLS_REFINE_MAX = 8;
+
+__device__ __forceinline__ int64_t packed_row(int i) { return (int64_t)i * (i + 1) / 2; }
+
+// w <- L^{-T} L^{-1} w by warp 0 (row-oriented, warp sums); L packed lower.
+__device__ __forceinline__ void chol_solve_f32(const float* L, float* w, int s, int lane)
+{
+    for (int i = 0; i < s; ++i) {
+        const float* row = L + packed_row(i);
+        float acc = 0.f;
+        for (int c = lane; c < i; c += 32) acc += row[c] * w[c];
+        acc = warp_sum(acc);
+        if (lane == 0) w[i] = (w[i] - acc) / row[i];
+        __syncwarp();
+    }
+    for (int i = s - 1; i >= 0; --i) {
+        float acc = 0.f;
+        for (int c = i + 1 + lane; c < s; c += 32) acc += L[packed_row(c) + i] * w[c];
+        acc = warp_sum(acc);
+        if (lane == 0) w[i] = (w[i] - acc) / L[packed_row(i) + i];
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ double block_max(double v, double* red, int lane, int warp)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double m = red[0];
+    for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+    return m;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red, int lane, int warp)
+{
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int sm2 = (a.smax + 1) & ~1;
+    int* idx = reinterpret_cast<int*>(smem_raw);                        // smax ints
+    double* b64 = reinterpret_cast<double*>(smem_raw + sizeof(int) * sm2);
+    double* x64 = b64 + sm2;
+    double* red = x64 + sm2;                                            // 32 doubles
+    float* w = reinterpret_cast<float*>(red + 32);                      // smax floats
+    float* L = a.fscratch ? a.fscratch + (size_t)blockIdx.x * packed_row(a.smax) : w + sm2;
+    __shared__ int s_count;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+
+    for (int64_t t = blockIdx.x; t < a.solves; t += gridDim.x) {
+        int k, j, e;
+        if (a.jstar) { k = (int)(t / a.r); e = (int)(t % a.r); j = a.jstar[k]; }
+        else { k = (int)(t / ((int64_t)a.q * a.r)); const int64_t rem = t % ((int64_t)a.q * a.r);
+               j = (int)(rem / a.r); e = (int)(rem % a.r);
+               if (a.dup && a.dup[rem] != j) continue; }
+        const uint64_t* bits = a.family + ((int64_t)j * a.r + e) * a.W;
+        if (warp == 0) {
+            int cnt = 0;
+            for (int64_t i0 = 0; i0 < a.p; i0 += 32) {
+                const int64_t i = i0 + lane;
+                const bool in = i < a.p && ((bits[i >> 6] >> (i & 63)) & 1ull);
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (in) idx[cnt + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+                cnt += __popc(bal);
+            }
+            if (lane == 0) s_count = cnt;
+        }
+        __syncthreads();
+        const int s = s_count;
+        const double* Gk = a.Gt + (size_t)k * a.p * a.p;
+        const double* Bk = a.Bt + (size_t)k * a.p * a.r;
+        // gather the packed lower triangle in FP32, b in FP64
+        double dm = 0.0;
+        for (int i = warp; i < s; i += 8) {
+            const double* grow = Gk + (size_t)idx[i] * a.p;
+            float* lrow = L + packed_row(i);
+            for (int c = lane; c <= i; c += 32) {
+                const double v = grow[idx[c]];
+                lrow[c] = f64_to_f32_int(v);
+                if (c == i) dm = fmax(dm, v);
+            }
+        }
+        for (int x = threadIdx.x; x < s; x += blockDim.x) b64[x] = Bk[(size_t)idx[x] * a.r + e];
+        const double dmax = block_max(dm, red, lane, warp);
+        const float thr = OLS_F32_PIVOT * (float)dmax;
+        // right-looking Cholesky, one column per step (2 barriers)
+        bool ok = true;
+        for (int c = 0; c < s; ++c) {
+            const float d = L[packed_row(c) + c];
+            if (!(d > thr)) { ok = false; break; }          // same decision in every thread
+            const float lcc = sqrtf(d);
+            for (int i = c + 1 + threadIdx.x; i < s; i += blockDim.x) L[packed_row(i) + c] /= lcc;
+            __syncthreads();
+            if (threadIdx.x == 0) L[packed_row(c) + c] = lcc;
+            for (int i = c + 1 + ty; i < s; i += 16) {
+                float* lrow = L + packed_row(i);
+                const float lic = lrow[c];
+                for (int jj = c + 1 + tx; jj <= i; jj += 16) lrow[jj] -= lic * L[packed_row(jj) + c];
+            }
+            __syncthreads();
+        }
+        bool done = false;
+        if (ok) {
+            // x = solve(b) in FP32, then x += solve(b - G x) with FP64 residuals
+            for (int x = threadIdx.x; x < s; x += blockDim.x) { w[x] = (float)b64[x]; x64[x] = 0.0; }
+            __syncthreads();
+            for (int itr = 0; itr <= OLS_REFINE_MAX; ++itr) {
+                if (warp == 0) chol_solve_f32(L, w, s, lane);
+                __syncthreads();
+                double dd = 0.0, xx = 0.0;
+                for (int x = threadIdx.x; x < s; x += blockDim.x) {
+                    const double nx = x64[x] + (double)w[x];
+                    dd = fmax(dd, fabs((double)w[x]));
+                    xx = fmax(xx, fabs(nx));
+                    x64[x] = nx;
+                }
+                const double dmx = block_max(dd, red, lane, warp);
+                const double xmx = block_max(xx, red, lane, warp);
+                if (itr > 0 && dmx <= 4.0 * 2.220446049250313e-16 * xmx) { done = true; break; }
+                if (itr == OLS_REFINE_MAX) { done = dmx <= 1e-12 * xmx; break; }
+                // residual r_i = b_i - sum_c G[S_i, S_c] x_c (one warp per row)
+                for (int i = warp; i < s; i += 8) {
+                    const double* grow = Gk + (size_t)idx[i] * a.p;
+                    double acc = 0.0;
+                    for (int c = lane; c < s; c += 32) acc += grow[idx[c]] * x64[c];
+                    acc = warp_sum(acc);
+                    if (lane == 0) w[i] = (float)(b64[i] - acc);
+                }
+                __syncthreads();
+            }
+        }
+        if (s > 0 && !done) {
+            if (threadIdx.x == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)t;
+            __syncthreads();
+            continue;
+        }
+        if (a.jstar) {
+            double* out = a.chosen + ((size_t)k * a.r + e) * a.p;
+            for (int x = threadIdx.x; x < s; x += blockDim.x) out[idx[x]] = x64[x];
+        } else {
+            const double* Gek = a.Ge + (size_t)k * a.p * a.p;
+            const double* Bek = a.Be + (size_t)k * a.p * a.r;
+            double part = 0.0;
+            for (int i = warp; i < s; i += 8) {
+                const double* grow = Gek + (size_t)idx[i] * a.p;
+                double acc = 0.0;
+                for (int c = lane; c < s; c += 32) acc += grow[idx[c]] * x64[c];
+                acc = warp_sum(acc);
+                if (lane == 0) part += x64[i] * acc;
+            }
+            for (int x = threadIdx.x; x < s; x += blockDim.x)
+                part -= 2.0 * x64[x] * Bek[(size_t)idx[x] * a.r + e];
+            const double tot = block_sum(part, red, lane, warp);
+            if (threadIdx.x == 0) {
+                const int64_t o = ((int64_t)k * a.q + j) * a.r + e;
+                a.losses[o] = a.yye[(size_t)k * a.r + e] + tot;
+                if (a.singular) a.singular[o] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // dup[j*r + e] = smallest j' <= j whose support for response e equals S_{j,e}.
 __global__ void k_family_dedup(const uint64_t* fam, int32_t q, int64_t r, int W, int32_t* dup)
 {
@@ -253,19 +442,24 @@ __global__ void k_mask_tail(uint64_t* fam, int64_t count, int W, uint64_t mask)
         fam[t * W + (W - 1)] &= mask;
 }
 
-void run_ols(OlsArgs a, cudaStream_t s)
+int32_t family_support_max(const OlsArgs& a, cudaStream_t s)
 {
-    // largest support decides shared vs global factor storage
     DevBuf mx(sizeof(int32_t), s);
     UOI_CUDA(cudaMemsetAsync(mx.ptr, 0, sizeof(int32_t), s));
     const int64_t fam_count = (int64_t)a.q * a.r;
     k_support_max<<<(unsigned)std::min<int64_t>(ceil_div(fam_count, 256), 1024), 256, 0, s>>>(
         a.family, fam_count, a.W, mx.as<int32_t>());
     UOI_CHECK_LAUNCH();
+    count_launch();
     int32_t smax = 0;
     UOI_CUDA(cudaMemcpyAsync(&smax, mx.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));
-    a.smax = std::max(1, (int)smax);
+    return smax;
+}
+
+// FP64 solves (all of a.solves, or those listed in a.list); a.smax set.
+void launch_ols_fp64(OlsArgs a, cudaStream_t s)
+{
     a.use_smem = a.smax <= OLS_SMEM_MAX;
     size_t smem = sizeof(int) * ((a.p + 1) & ~1) + sizeof(double) * (a.smax + 1 + 32);
     DevBuf scratch;
@@ -281,8 +475,56 @@ void run_ols(OlsArgs a, cudaStream_t s)
     if (a.solves > 0) {
         k_ols<<<grid, 256, smem, s>>>(a);
         UOI_CHECK_LAUNCH();
+        count_launch();
     }
-    count_launch(2);
+}
+
+// Mixed pass: FP32 factor + FP64 refinement for every solve, then the FP64
+// kernel for the solves it handed back.
+int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
+{
+    if (a.solves == 0) return 0;
+    const int sm2 = (a.smax + 1) & ~1;
+    const size_t base = sizeof(int) * sm2 + 2 * sizeof(double) * sm2 + 32 * sizeof(double) +
+                        sizeof(float) * sm2;
+    const size_t lbytes = sizeof(float) * (size_t)a.smax * (a.smax + 1) / 2;
+    const size_t cap = 227 * 1024 - 64;
+    const bool in_smem = base + lbytes <= cap;
+    const size_t smem = base + (in_smem ? lbytes : 0);
+    UOI_CUDA(cudaFuncSetAttribute(k_ols_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, nsm = 0, per = 0;
+    UOI_CUDA(cudaGetDevice(&dev));
+    UOI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    UOI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ols_mixed, 256, smem));
+    const int grid = (int)std::min<int64_t>(a.solves, (int64_t)nsm * std::max(1, per));
+    DevBuf fscratch;
+    if (!in_smem) {
+        fscratch.alloc(lbytes * (size_t)grid, s);
+        a.fscratch = fscratch.as<float>();
+    }
+    DevBuf fbl(sizeof(int32_t) * (size_t)a.solves, s), fbc(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(fbc.ptr, 0, sizeof(int32_t), s));
+    a.fb_list = fbl.as<int32_t>();
+    a.fb_count = fbc.as<int32_t>();
+    k_ols_mixed<<<grid, 256, smem, s>>>(a);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    int32_t nfb = 0;
+    UOI_CUDA(cudaMemcpyAsync(&nfb, fbc.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    if (nfb > 0) {
+        a.list = fbl.as<int32_t>();
+        a.solves = nfb;
+        a.fscratch = nullptr;
+        launch_ols_fp64(a, s);
+    }
+    return nfb;
+}
+
+int64_t run_ols(OlsArgs a, cudaStream_t s)
+{
+    a.smax = std::max(1, (int)family_support_max(a, s));
+    return launch_ols_mixed(a, s);
 }
 
 // U = union over (j, e) of the family supports, compacted in increasing order.
@@ -345,7 +587,7 @@ void family_mask_tail(uint64_t* fam, int64_t count, int64_t p, cudaStream_t s)
     count_launch();
 }
 
-void ols_losses(const double* Gt, const double* Bt, const double* Ge, const double* Be,
+int64_t ols_losses(const double* Gt, const double* Bt, const double* Ge, const double* Be,
                 const double* yye, const uint64_t* family, int64_t p, int64_t r, int32_t q,
                 int32_t B2, double* losses, int32_t* singular, cudaStream_t s)
 {
@@ -359,11 +601,12 @@ void ols_losses(const double* Gt, const double* Bt, const double* Ge, const doub
     k_family_dedup<<<gd, 256, 0, s>>>(family, q, r, a.W, dup.as<int32_t>());
     UOI_CHECK_LAUNCH();
     a.dup = dup.as<int32_t>();
-    run_ols(a, s);
+    const int64_t nfb = run_ols(a, s);
     const unsigned gf = (unsigned)std::min<int64_t>(ceil_div(a.solves, 256), 4096);
     k_fill_duplicates<<<gf, 256, 0, s>>>(dup.as<int32_t>(), B2, q, r, losses, singular);
     UOI_CHECK_LAUNCH();
     count_launch(2);
+    return nfb;
 }
 
 void loss_argmin(const double* losses, int32_t B2, int32_t q, int64_t r, int32_t* jstar,
@@ -374,7 +617,7 @@ void loss_argmin(const double* losses, int32_t B2, int32_t q, int64_t r, int32_t
     count_launch();
 }
 
-void ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, const int32_t* jstar,
+int64_t ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, const int32_t* jstar,
                 int64_t p, int64_t r, int32_t q, int32_t B2, double* chosen, cudaStream_t s)
 {
     UOI_CUDA(cudaMemsetAsync(chosen, 0, sizeof(double) * (size_t)(B2 * r * p), s));
@@ -383,7 +626,7 @@ void ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, cons
     a.p = p; a.r = r; a.q = q; a.B2 = B2; a.W = (int32_t)((p + 63) / 64);
     a.jstar = jstar; a.chosen = chosen;
     a.solves = (int64_t)B2 * r;
-    run_ols(a, s);
+    return run_ols(a, s);
 }
 
 void bagging(const double* chosen, int32_t B2, int64_t count, int32_t mode, double* out,

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_chol_update(T* A, int64_t p, int64_t j0
         const int64_t j = jj0 + jl;
         return j < p ? a[j * p + j0 + s] : T(0);
     };
-    tile64_acc<T>(acc, fa, fb, 0, nb);
+    tile64_acc<T, true, true>(acc, fa, fb, 0, nb);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_trinv_row(const T* L, int64_t p, int64_
         const int64_t jj = j0 + jl;
         return (T)li[s * p + jj];
     };
-    tile64_acc<T>(acc, fa, fb, j0, i0);              // T_IJ (64 x 64)
+    tile64_acc<T, true, false>(acc, fa, fb, j0, i0);   // T_IJ (64 x 64)
     __shared__ T Tm[IB][IB + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) k_trinv_row(const T* L, int64_t p, int64_
         return (i < p && c < p && c <= i) ? li[i * p + c] : T(0);
     };
     auto gb = [&](int64_t s, int jl) { return Tm[s][jl]; };
-    tile64_acc<T>(acc2, ga, gb, 0, IB);
+    tile64_acc<T, true, false>(acc2, ga, gb, 0, IB);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int64_t i = i0 + ty + 16 * u;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) k_rhs(const T* M, const double* Bm, const
         const int64_t e = e0 + el;
         return e < r ? (T)(bk[j * r + e] / n_k) : T(0);
     };
-    tile64_acc<T>(acc, fa, fb, 0, p);
+    tile64_acc<T, true, false>(acc, fa, fb, 0, p);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {

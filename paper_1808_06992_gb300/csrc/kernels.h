@@ -169,15 +169,17 @@ int32_t union_columns(const uint64_t* family, int64_t count, int64_t p, int32_t*
 void family_mask_tail(uint64_t* fam, int64_t count, int64_t p, cudaStream_t s);
 // losses[(k*q + j)*r + e] = held-out squared error sum of the OLS fit on support
 // S_{j,e} from training moments (Gt, Bt) and evaluation moments (Ge, Be, yye);
-// singular[...] = 1 where the fallback ran.
-void ols_losses(const double* Gt, const double* Bt, const double* Ge, const double* Be,
+// singular[...] = 1 where the fallback ran.  Solves use an FP32 factor with FP64
+// iterative refinement (FP64-accurate), an FP64 factor for those it rejects
+// (their number is returned).
+int64_t ols_losses(const double* Gt, const double* Bt, const double* Ge, const double* Be,
                 const double* yye, const uint64_t* family, int64_t p, int64_t r, int32_t q,
                 int32_t B2, double* losses, int32_t* singular, cudaStream_t s);
 // jstar[k] = argmin_j sum_e losses[k][j][e] (ties -> smallest j).
 void loss_argmin(const double* losses, int32_t B2, int32_t q, int64_t r, int32_t* jstar,
                  cudaStream_t s);
 // chosen[k][e][:] = OLS on S_{jstar[k], e} from (Gt_k, Bt_k), zero-filled.
-void ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, const int32_t* jstar,
+int64_t ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, const int32_t* jstar,
                 int64_t p, int64_t r, int32_t q, int32_t B2, double* chosen, cudaStream_t s);
 // beta_out[e][i] = median (bagging 0) or mean (1) over k of chosen[k][e][i].
 void bagging(const double* chosen, int32_t B2, int64_t count, int32_t mode, double* out,

@@ -172,5 +172,22 @@ inline CUtensorMap make_map_bf16_k64(void* base, int64_t k_extent, int64_t rows,
     return m;
 }
 
+// Map over contiguous 128 x 64 bf16 blocks ([block][128][64], 16 KB each, rows of
+// 128 B): a box of `depth` consecutive blocks is one contiguous read.
+inline CUtensorMap make_map_bf16_blocks(void* base, int64_t nblocks, int depth)
+{
+    CUtensorMap m;
+    cuuint64_t dims[3] = { 64u, 128u, (cuuint64_t)nblocks };
+    cuuint64_t strides[2] = { 128u, 128u * 128u };
+    cuuint32_t box[3] = { 64u, 128u, (cuuint32_t)depth };
+    cuuint32_t estr[3] = { 1, 1, 1 };
+    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
 }  // namespace tc
 }  // namespace uoi

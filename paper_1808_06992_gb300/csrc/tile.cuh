@@ -8,7 +8,9 @@ namespace uoi {
 // acc[u][v] += sum_{k in [k0,k1)} A(i0 + ty + 16u, k) * B(k, j0 + tx + 16v)
 // for a 256-thread block (tx = tid % 16, ty = tid / 16).  fa(il, k) and fb(k, jl)
 // return operand values for local row il / column jl in [0, 64) (zero outside).
-template <typename T, typename FA, typename FB>
+// AK / BK: the operand is contiguous along k in memory (rows of K values), so
+// consecutive threads load consecutive k; otherwise consecutive rows/columns.
+template <typename T, bool AK = false, bool BK = false, typename FA, typename FB>
 __device__ __forceinline__ void tile64_acc(T (&acc)[4][4], const FA& fa, const FB& fb, int64_t k0,
                                            int64_t k1)
 {
@@ -18,10 +20,10 @@ __device__ __forceinline__ void tile64_acc(T (&acc)[4][4], const FA& fa, const F
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     for (int64_t kb = k0; kb < k1; kb += TK) {
         for (int e = threadIdx.x; e < TK * 64; e += 256) {
-            const int kk = e / 64, c = e % 64;
-            const int64_t k = kb + kk;
-            As[kk][c] = k < k1 ? fa(c, k) : T(0);
-            Bs[kk][c] = k < k1 ? fb(k, c) : T(0);
+            const int kka = AK ? e % TK : e / 64, ca = AK ? e / TK : e % 64;
+            const int kkb = BK ? e % TK : e / 64, cb = BK ? e / TK : e % 64;
+            As[kka][ca] = kb + kka < k1 ? fa(ca, kb + kka) : T(0);
+            Bs[kkb][cb] = kb + kkb < k1 ? fb(kb + kkb, cb) : T(0);
         }
         __syncthreads();
 #pragma unroll

@@ -14,7 +14,8 @@
 //
 // Work per launch: every chain of every group (converged chains are skipped in
 // the epilogue and keep their state).  Grid: (row tiles of 128, chain tiles of
-// NT <= 128, groups).  Warp 0: TMA producer (2-stage ring of 96 KB); warp 1:
+// NT <= 128, groups).  Warp 0: TMA producer (ring of 2 stages of up to 96 KB,
+// or 3 when NT <= 48); warp 1:
 // TMEM allocation and MMA issue; warps 2-9: epilogue.  Waits are bounded (~1 s)
 // and report UOI_ERR_TIMEOUT.
 #include <cuda_bf16.h>
@@ -32,18 +33,19 @@ using namespace tc;
 
 constexpr int XT_TM = 128;
 constexpr int XT_TK = 64;
-constexpr int XT_STAGES = 2;
+constexpr int XT_STAGES = 3;                           // ring slots (2 used when NT > 48)
 constexpr int XT_A_BYTES = XT_TM * XT_TK * 2;          // 16 KB per piece
 constexpr int XT_B_MAX = 128 * XT_TK * 2;              // 16 KB per piece at NT = 128
-constexpr int XT_STAGE_BYTES = 3 * XT_A_BYTES + 3 * XT_B_MAX;
-constexpr int XT_SMEM = XT_STAGES * XT_STAGE_BYTES + 1024;
+constexpr int XT_STAGE_MAX = 3 * XT_A_BYTES + 3 * XT_B_MAX;   // 96 KB at NT = 128
+constexpr int XT_STAGE_48 = 3 * XT_A_BYTES + 3 * 48 * XT_TK * 2;  // 66 KB at NT = 48
+constexpr int XT_SMEM = (2 * XT_STAGE_MAX > 3 * XT_STAGE_48 ? 2 * XT_STAGE_MAX : 3 * XT_STAGE_48) + 1024;
 constexpr int XT_THREADS = 320;
 constexpr uint32_t XT_TMEM_COLS = 512;                 // A1[0] at 0, A1[1] at 128, A2 at 256
 constexpr int XT_CHUNK_STAGES = 2;                     // drain h.H every 128 k
 
 struct XtArgs {
     int32_t G, q, r, p, nchains, NT, kst, RT, warm;
-    int64_t ppad;                 // rows per group in the M pieces (multiple of 128)
+    int64_t ppad;                 // rows per group (multiple of 128)
     int64_t kpad;                 // k extent (multiple of 64)
     int64_t slots;
     const float* c;               // G x r x p
@@ -75,6 +77,9 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float red[2][4][64][5];
+    __shared__ float s_kappa[128];                 // lambda_j / rho of each chain of the tile
+    __shared__ int s_coff[128];                    // row of c used by the chain
+    __shared__ uint8_t s_live[128];                // chain exists and is still iterating
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rt = blockIdx.x, ct = blockIdx.y, g = blockIdx.z;
@@ -83,6 +88,22 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t b_bytes = (uint32_t)a.NT * XT_TK * 2;
     const uint32_t stage_tx = 3u * XT_A_BYTES + 3u * b_bytes;
+    const uint32_t stage_bytes = (stage_tx + 1023u) & ~1023u;
+    const int nst = a.NT <= 48 ? 3 : 2;                 // stages that fit in the ring
+
+    // A tile whose chains have all stopped has nothing to update: skip it whole.
+    {
+        const int n = threadIdx.x, chain = n0 + n;
+        const int64_t sl = (int64_t)g * a.nchains + chain;
+        const bool mine = n < a.NT && chain < a.nchains && a.live[sl];
+        if (n < 128) {
+            // per-chain scalars of the epilogue, read once instead of per row
+            s_live[n] = mine ? 1 : 0;
+            s_kappa[n] = mine ? (float)a.lambdas[a.slot_j[sl]] / a.rho : 0.f;
+            s_coff[n] = g * a.r + (a.warm ? chain : chain % a.r);
+        }
+        if (!__syncthreads_or(mine)) return;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < XT_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
@@ -105,26 +126,25 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        const int rowA = (int)((int64_t)g * a.ppad + i0);
+        const int blkA = ((g * a.RT + rt) * a.kst) * 3;     // first 16 KB block of this row tile
         const int rowB = g * a.nchains + n0;
         for (int s_ = 0; s_ < a.kst; ++s_) {
-            const int s = s_ % XT_STAGES;
-            if (s_ >= XT_STAGES && !mbar_wait(&empty_bar[s], ((s_ / XT_STAGES) - 1) & 1, &abort_flag)) {
+            const int s = s_ % nst;
+            if (s_ >= nst && !mbar_wait(&empty_bar[s], ((s_ / nst) - 1) & 1, &abort_flag)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
             }
-            const uint32_t st = sbase + s * XT_STAGE_BYTES;
+            const uint32_t st = sbase + s * stage_bytes;
             mbar_expect_tx(&full_bar[s], stage_tx);
             const int k0 = s_ * XT_TK;
-            for (int pc = 0; pc < 3; ++pc)
-                tma_load_3d(st + pc * XT_A_BYTES, &tmM, &full_bar[s], k0, rowA, pc);
+            tma_load_3d(st, &tmM, &full_bar[s], 0, 0, blkA + 3 * s_);   // 3 pieces, 48 KB contiguous
             for (int pc = 0; pc < 3; ++pc)
                 tma_load_3d(st + 3 * XT_A_BYTES + pc * b_bytes, &tmV, &full_bar[s], k0, rowB, pc);
         }
         if (abort_flag)
-            for (int s_ = max(0, a.kst - XT_STAGES); s_ < a.kst; ++s_)
-                mbar_wait(&full_bar[s_ % XT_STAGES], (s_ / XT_STAGES) & 1, &abort_flag);
+            for (int s_ = max(0, a.kst - nst); s_ < a.kst; ++s_)
+                mbar_wait(&full_bar[s_ % nst], (s_ / nst) & 1, &abort_flag);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_bf16(XT_TM, a.NT);
@@ -143,14 +163,14 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             const int send = min(a.kst, (c + 1) * XT_CHUNK_STAGES);
             bool first1 = true;
             for (; s_ < send; ++s_) {
-                const int s = s_ % XT_STAGES;
-                if (!mbar_wait(&full_bar[s], (s_ / XT_STAGES) & 1, &abort_flag)) {
+                const int s = s_ % nst;
+                if (!mbar_wait(&full_bar[s], (s_ / nst) & 1, &abort_flag)) {
                     abort_flag = 1;
                     atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t st = sbase + s * XT_STAGE_BYTES;
+                const uint32_t st = sbase + s * stage_bytes;
                 const uint64_t Ah = smem_desc_sw128(st), Am = smem_desc_sw128(st + XT_A_BYTES);
                 const uint64_t Al = smem_desc_sw128(st + 2 * XT_A_BYTES);
                 const uint32_t bb = st + 3 * XT_A_BYTES;
@@ -180,6 +200,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         // ---------------- epilogue ----------------
         const int quad = warp & 3, half = (warp - 2) >> 2;
         const int i = i0 + quad * 32 + lane;
+        const bool busy = half * 64 < a.NT;             // this half holds chains of the tile
         float acc[64], cmp[64];
 #pragma unroll
         for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
@@ -193,6 +214,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             tc_fence_after();
 #pragma unroll
             for (int cb = 0; cb < 2; ++cb) {
+                if (!busy) break;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 128 + half * 64 + cb * 32), v);
 #pragma unroll
@@ -213,27 +235,38 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);
         }
         tc_fence_after();
-        float part[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
+        const bool rowok = i < a.p && !abort_flag;
 #pragma unroll
         for (int cb = 0; cb < 2; ++cb) {
+            if (!busy || half * 64 + cb * 32 >= a.NT) break;
             float v2[32];
             tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(256 + half * 64 + cb * 32), v2);
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                const int n = half * 64 + cb * 32 + t;           // chain within the tile
-                const int chain = n0 + n;
-                float pr[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
-                const bool valid = n < a.NT && chain < a.nchains && i < a.p && !abort_flag;
-                const int64_t sl = (int64_t)g * a.nchains + chain;
-                if (valid && a.live[sl]) {
-                    const int e = a.warm ? chain : chain % a.r;
-                    const float prod = (acc[cb * 32 + t] + cmp[cb * 32 + t]) + v2[t];
-                    const float x = a.c[((int64_t)g * a.r + e) * a.p + i] + a.rho * prod;
-                    const float kappa = (float)a.lambdas[a.slot_j[sl]] / a.rho;
+            for (int t8 = 0; t8 < 32; t8 += 8) {
+                const int nb = half * 64 + cb * 32 + t8;             // first chain of the group of 8
+                // issue the loads of the 8 chains before any store (they are independent)
+                float zp[8], uo[8], cc[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const bool act = rowok && s_live[nb + t];
+                    const int64_t o = ((int64_t)g * a.nchains + n0 + nb + t) * a.p + i;
+                    zp[t] = act ? a.z[o] : 0.f;
+                    uo[t] = act ? a.u[o] : 0.f;
+                    cc[t] = act ? a.c[(int64_t)s_coff[nb + t] * a.p + i] : 0.f;
+                }
+                float pr[5][8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+#pragma unroll
+                    for (int qq = 0; qq < 5; ++qq) pr[qq][t] = 0.f;
+                    if (!(rowok && s_live[nb + t])) continue;
+                    const int tt = cb * 32 + t8 + t;
+                    const float prod = (acc[tt] + cmp[tt]) + v2[t8 + t];
+                    const float x = cc[t] + a.rho * prod;
+                    const int64_t sl = (int64_t)g * a.nchains + n0 + nb + t;
                     const int64_t o = sl * a.p + i;
-                    const float zp = a.z[o];
-                    const float vv = x + a.u[o];
-                    const float zn = soft_threshold(vv, kappa);
+                    const float vv = x + uo[t];
+                    const float zn = soft_threshold(vv, s_kappa[nb + t]);
                     const float un = vv - zn;
                     a.z[o] = zn;
                     a.u[o] = un;
@@ -243,18 +276,34 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                     a.vnext[vo] = h;
                     a.vnext[(int64_t)a.slots * a.kpad + vo] = m;
                     a.vnext[2 * (int64_t)a.slots * a.kpad + vo] = l;
-                    const float d = x - zn, dz = zn - zp;
-                    pr[0] = d * d; pr[1] = dz * dz; pr[2] = x * x; pr[3] = zn * zn; pr[4] = un * un;
+                    const float d = x - zn, dz = zn - zp[t];
+                    pr[0][t] = d * d; pr[1][t] = dz * dz; pr[2][t] = x * x; pr[3][t] = zn * zn; pr[4][t] = un * un;
                 }
-                // sum over the 32 rows of this warp (fixed tree), keep in lane 0
+                // column sums over the warp's 32 rows: halve the 8 columns per lane at
+                // lane bits 4, 3, 2, then add across bits 1, 0 (fixed order)
+                const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
 #pragma unroll
                 for (int qq = 0; qq < 5; ++qq) {
-                    const float sv = warp_sum(pr[qq]);
-                    if (lane == 0) red[half][quad][cb * 32 + t][qq] = sv;
+                    float w4[4], w3[2];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float send = b4 ? pr[qq][j] : pr[qq][j + 4];
+                        const float keep = b4 ? pr[qq][j + 4] : pr[qq][j];
+                        w4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const float send = b3 ? w4[j] : w4[j + 2];
+                        const float keep = b3 ? w4[j + 2] : w4[j];
+                        w3[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+                    float w2 = (b2 ? w3[1] : w3[0]) + __shfl_xor_sync(0xffffffffu, b2 ? w3[0] : w3[1], 4);
+                    w2 += __shfl_xor_sync(0xffffffffu, w2, 2);
+                    w2 += __shfl_xor_sync(0xffffffffu, w2, 1);
+                    if ((lane & 3) == 0) red[half][quad][cb * 32 + t8 + b4 * 4 + b3 * 2 + b2][qq] = w2;
                 }
             }
         }
-        (void)part;
     }
     tc_fence_before();
     __syncthreads();
@@ -281,11 +330,14 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     }
 }
 
-// M_g (FP32, p x p) -> three bf16 pieces at [piece][g*ppad + i][k] (zero padded).
+// M_g (FP32, p x p) -> three bf16 pieces in 128 x 64 blocks, ordered
+// [g][row tile][k block][piece][128][64] (zero padded), so that the x-update
+// streams each row tile as one contiguous run of 48 KB stages.
 __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
                           __nv_bfloat16* out)
 {
     const int64_t per = (int64_t)G * ppad * kpad;
+    const int64_t RT = ppad / 128, kst = kpad / 64;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = t % kpad, row = t / kpad;
@@ -293,9 +345,11 @@ __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, in
         const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] : 0.f;
         __nv_bfloat16 h, m, l;
         split3(x, h, m, l);
-        out[t] = h;
-        out[per + t] = m;
-        out[2 * per + t] = l;
+        const int64_t blk = ((g * RT + i / 128) * kst + k / 64) * 3;
+        const int64_t o = (blk * 128 + i % 128) * 64 + k % 64;
+        out[o] = h;
+        out[o + 128 * 64] = m;
+        out[o + 2 * 128 * 64] = l;
     }
 }
 
@@ -439,7 +493,7 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
         P.G, nchains, (int32_t)P.r, P.q, P.warm, sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>());
     UOI_CHECK_LAUNCH();
     count_launch(3);
-    const CUtensorMap mM = make_map_bf16_k64(mp.ptr, kpad, (int64_t)P.G * ppad, 3, XT_TM);
+    const CUtensorMap mM = make_map_bf16_blocks(mp.ptr, (int64_t)P.G * RT * kst * 3, 3);
     const CUtensorMap mV0 = make_map_bf16_k64(v0.ptr, kpad, slots, 3, NT);
     const CUtensorMap mV1 = make_map_bf16_k64(v1.ptr, kpad, slots, 3, NT);
     UOI_CUDA(cudaFuncSetAttribute(k_xupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM));

@@ -47,6 +47,7 @@ class UoiDiag(C.Structure):
         ("ms_gram_tc", C.c_float), ("n_gram_tc", C.c_int64), ("flops_gram_tc", C.c_double),
         ("ms_xupdate", C.c_float), ("n_xupdate", C.c_int64), ("flops_xupdate", C.c_double),
         ("bytes_xupdate", C.c_double), ("warm_start_used", C.c_int32),
+        ("ols_fp64", C.c_int64),
     ]
 
     def as_dict(self):

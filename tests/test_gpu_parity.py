@@ -241,3 +241,34 @@ def test_mixed_tensor_core_xupdate_vs_oracle(warm):
     amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
     assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
     assert np.abs(gpu["iters"].astype(int) - ref["iters"]).max() <= max(3, int(0.1 * ref["iters"].max()))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ols_duplicate_column_goes_to_fp64_factor(prec):
+    # With an exact duplicate column every support holding both copies is singular:
+    # the FP32-factor solver must refuse it (pivot far below 1e-3 of the largest
+    # diagonal) and hand it to the FP64 factor, which flags it and refits with the
+    # ridge.  Supports without the pair stay on the refined FP32 factor and agree
+    # with the oracle's FP64 Cholesky to FP64 rounding (FP64 form).
+    d = synth.lasso_problem(500, 20, 6, seed=21, sigma=0.5)
+    X = d.X.copy()
+    X[:, 1] = X[:, 0]
+    kw = dict(B1=4, B2=3, q=10)
+    precision = native.PREC_FP64 if prec == "fp64" else native.PREC_MIXED
+    gpu = native.uoi_fit_traced(X, d.y, precision=precision, **kw)
+    fam = bits_to_bool(gpu["family"], 20)[:, 0, :]
+    pair = fam[:, 0] & fam[:, 1]
+    assert pair.any()
+    assert gpu["diag"]["ols_fp64"] > 0
+    assert np.isfinite(gpu["est_loss"]).all() and np.isfinite(gpu["beta"]).all()
+    if prec == "fp64":
+        # exact FP64 moments: the pair's pivot is at rounding level, below 1e-12
+        # (the mixed form's FP32-accurate Gram leaves a ~1e-7 pivot instead)
+        assert gpu["status"] == native.OK_WITH_WARNINGS
+        sing = gpu["est_singular"][:, :, 0].astype(bool)
+        np.testing.assert_array_equal(sing, np.broadcast_to(pair, sing.shape))
+        ref = oracle.uoi_lasso_fit(X, d.y, **kw)
+        if np.array_equal(bits_to_bool(ref["family"], 20), bits_to_bool(gpu["family"], 20)):
+            ok = ~pair
+            np.testing.assert_allclose(gpu["est_loss"][:, ok, 0], ref["est_loss"][:, ok, 0],
+                                       rtol=1e-9, atol=1e-12)
