@@ -91,6 +91,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
     return d;
 }
 
+// Same for 64-byte swizzle: rows of 64 B (32 bf16 of k), 8-row atoms of 512 B.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
+    d |= (uint64_t)(512 >> 4) << 32;                   // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)4 << 61;                            // SWIZZLE_64B
+    return d;
+}
+
 // kind::f16 instruction descriptor: bf16 x bf16 -> f32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 {
@@ -183,6 +195,40 @@ inline CUtensorMap make_map_bf16_blocks(void* base, int64_t nblocks, int depth)
     cuuint32_t estr[3] = { 1, 1, 1 };
     CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
+// 64-byte-swizzle variants: k tiles of 32 bf16 (rows of 64 B).
+inline CUtensorMap make_map_bf16_k32(void* base, int64_t k_extent, int64_t rows, int64_t depth,
+                                     int box_rows)
+{
+    CUtensorMap m;
+    cuuint64_t dims[3] = { (cuuint64_t)k_extent, (cuuint64_t)rows, (cuuint64_t)depth };
+    cuuint64_t strides[2] = { (cuuint64_t)(k_extent * 2), (cuuint64_t)(k_extent * 2 * rows) };
+    cuuint32_t box[3] = { 32u, (cuuint32_t)box_rows, 1u };
+    cuuint32_t estr[3] = { 1, 1, 1 };
+    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
+// Contiguous 128 x 32 bf16 blocks ([block][128][32], 8 KB each): a box of `depth`
+// consecutive blocks is one contiguous read.
+inline CUtensorMap make_map_bf16_blocks32(void* base, int64_t nblocks, int depth)
+{
+    CUtensorMap m;
+    cuuint64_t dims[3] = { 32u, 128u, (cuuint64_t)nblocks };
+    cuuint64_t strides[2] = { 64u, 64u * 128u };
+    cuuint32_t box[3] = { 32u, 128u, (cuuint32_t)depth };
+    cuuint32_t estr[3] = { 1, 1, 1 };
+    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");

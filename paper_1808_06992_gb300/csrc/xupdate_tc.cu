@@ -13,11 +13,12 @@
 // x-update is then accurate to ~1e-7 relative, like the FP32 CUDA-core product.
 //
 // Work per launch: every chain of every group (converged chains are skipped in
-// the epilogue and keep their state).  Grid: (row tiles of 128, chain tiles of
-// NT <= 128, groups).  Warp 0: TMA producer (ring of 2 stages of up to 96 KB,
-// or 3 when NT <= 48); warp 1:
-// TMEM allocation and MMA issue; warps 2-9: epilogue.  Waits are bounded (~1 s)
-// and report UOI_ERR_TIMEOUT.
+// the epilogue and keep their state; tiles with no live chain exit at once).
+// Grid: (row tiles of 128, chain tiles of NT <= 64, groups), two CTAs per SM so
+// that one CTA's prologue and epilogue overlap the other's stream of M.  Warp 0:
+// TMA producer (ring of 3 stages of k = 32, 2 when NT = 64); warp 1: TMEM
+// allocation and MMA issue; warps 2-5: epilogue (one TMEM lane quarter each).
+// Waits are bounded (~1 s) and report UOI_ERR_TIMEOUT.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -32,21 +33,21 @@ namespace {
 using namespace tc;
 
 constexpr int XT_TM = 128;
-constexpr int XT_TK = 64;
+constexpr int XT_TK = 32;                              // k per stage (64-byte swizzled rows)
+constexpr int XT_NT_MAX = 64;
 constexpr int XT_STAGES = 3;                           // ring slots (2 used when NT > 48)
-constexpr int XT_A_BYTES = XT_TM * XT_TK * 2;          // 16 KB per piece
-constexpr int XT_B_MAX = 128 * XT_TK * 2;              // 16 KB per piece at NT = 128
-constexpr int XT_STAGE_MAX = 3 * XT_A_BYTES + 3 * XT_B_MAX;   // 96 KB at NT = 128
-constexpr int XT_STAGE_48 = 3 * XT_A_BYTES + 3 * 48 * XT_TK * 2;  // 66 KB at NT = 48
-constexpr int XT_SMEM = (2 * XT_STAGE_MAX > 3 * XT_STAGE_48 ? 2 * XT_STAGE_MAX : 3 * XT_STAGE_48) + 1024;
-constexpr int XT_THREADS = 320;
-constexpr uint32_t XT_TMEM_COLS = 512;                 // A1[0] at 0, A1[1] at 128, A2 at 256
-constexpr int XT_CHUNK_STAGES = 2;                     // drain h.H every 128 k
+constexpr int XT_A_BYTES = XT_TM * XT_TK * 2;          // 8 KB per piece
+constexpr int XT_STAGE_48 = 3 * XT_A_BYTES + 3 * 48 * XT_TK * 2;   // 33 KB at NT = 48
+constexpr int XT_STAGE_64 = 3 * XT_A_BYTES + 3 * 64 * XT_TK * 2;   // 36 KB at NT = 64
+constexpr int XT_SMEM = (3 * XT_STAGE_48 > 2 * XT_STAGE_64 ? 3 * XT_STAGE_48 : 2 * XT_STAGE_64) + 1024;
+constexpr int XT_THREADS = 192;
+constexpr uint32_t XT_TMEM_COLS = 256;                 // A1[0] at 0, A1[1] at 64, A2 at 128
+constexpr int XT_CHUNK_STAGES = 4;                     // drain h.H every 128 k
 
 struct XtArgs {
     int32_t G, q, r, p, nchains, NT, kst, RT, warm;
     int64_t ppad;                 // rows per group (multiple of 128)
-    int64_t kpad;                 // k extent (multiple of 64)
+    int64_t kpad;                 // k extent (multiple of 32)
     int64_t slots;
     const float* c;               // G x r x p
     const double* lambdas;
@@ -68,7 +69,7 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16&
     l = __float2bfloat16_rn(r2);
 }
 
-__global__ void __launch_bounds__(XT_THREADS, 1)
+__global__ void __launch_bounds__(XT_THREADS, 2)
 k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CUtensorMap tmV,
              XtArgs a)
 {
@@ -76,10 +77,10 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     __shared__ uint64_t full_bar[XT_STAGES], empty_bar[XT_STAGES], accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    __shared__ float red[2][4][64][5];
-    __shared__ float s_kappa[128];                 // lambda_j / rho of each chain of the tile
-    __shared__ int s_coff[128];                    // row of c used by the chain
-    __shared__ uint8_t s_live[128];                // chain exists and is still iterating
+    __shared__ float red[4][XT_NT_MAX][5];
+    __shared__ float s_kappa[XT_NT_MAX];           // lambda_j / rho of each chain of the tile
+    __shared__ int s_coff[XT_NT_MAX];              // row of c used by the chain
+    __shared__ uint8_t s_live[XT_NT_MAX];          // chain exists and is still iterating
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rt = blockIdx.x, ct = blockIdx.y, g = blockIdx.z;
@@ -96,7 +97,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         const int n = threadIdx.x, chain = n0 + n;
         const int64_t sl = (int64_t)g * a.nchains + chain;
         const bool mine = n < a.NT && chain < a.nchains && a.live[sl];
-        if (n < 128) {
+        if (n < XT_NT_MAX) {
             // per-chain scalars of the epilogue, read once instead of per row
             s_live[n] = mine ? 1 : 0;
             s_kappa[n] = mine ? (float)a.lambdas[a.slot_j[sl]] / a.rho : 0.f;
@@ -107,7 +108,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < XT_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 256); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -126,7 +127,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        const int blkA = ((g * a.RT + rt) * a.kst) * 3;     // first 16 KB block of this row tile
+        const int blkA = ((g * a.RT + rt) * a.kst) * 3;     // first 8 KB block of this row tile
         const int rowB = g * a.nchains + n0;
         for (int s_ = 0; s_ < a.kst; ++s_) {
             const int s = s_ % nst;
@@ -138,7 +139,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             const uint32_t st = sbase + s * stage_bytes;
             mbar_expect_tx(&full_bar[s], stage_tx);
             const int k0 = s_ * XT_TK;
-            tma_load_3d(st, &tmM, &full_bar[s], 0, 0, blkA + 3 * s_);   // 3 pieces, 48 KB contiguous
+            tma_load_3d(st, &tmM, &full_bar[s], 0, 0, blkA + 3 * s_);   // 3 pieces, 24 KB contiguous
             for (int pc = 0; pc < 3; ++pc)
                 tma_load_3d(st + 3 * XT_A_BYTES + pc * b_bytes, &tmV, &full_bar[s], k0, rowB, pc);
         }
@@ -148,7 +149,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_bf16(XT_TM, a.NT);
-        const uint32_t d2 = tmem + 256u;
+        const uint32_t d2 = tmem + 128u;
         bool first2 = true;
         int s_ = 0;
         for (int c = 0; c < nchunks && !abort_flag; ++c) {
@@ -159,7 +160,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                 break;
             }
             tc_fence_after();
-            const uint32_t d1 = tmem + (uint32_t)(b * 128);
+            const uint32_t d1 = tmem + (uint32_t)(b * 64);
             const int send = min(a.kst, (c + 1) * XT_CHUNK_STAGES);
             bool first1 = true;
             for (; s_ < send; ++s_) {
@@ -171,11 +172,11 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                 }
                 tc_fence_after();
                 const uint32_t st = sbase + s * stage_bytes;
-                const uint64_t Ah = smem_desc_sw128(st), Am = smem_desc_sw128(st + XT_A_BYTES);
-                const uint64_t Al = smem_desc_sw128(st + 2 * XT_A_BYTES);
+                const uint64_t Ah = smem_desc_sw64(st), Am = smem_desc_sw64(st + XT_A_BYTES);
+                const uint64_t Al = smem_desc_sw64(st + 2 * XT_A_BYTES);
                 const uint32_t bb = st + 3 * XT_A_BYTES;
-                const uint64_t Bh = smem_desc_sw128(bb), Bm = smem_desc_sw128(bb + b_bytes);
-                const uint64_t Bl = smem_desc_sw128(bb + 2 * b_bytes);
+                const uint64_t Bh = smem_desc_sw64(bb), Bm = smem_desc_sw64(bb + b_bytes);
+                const uint64_t Bl = smem_desc_sw64(bb + 2 * b_bytes);
 #pragma unroll
                 for (int ks = 0; ks < XT_TK / 16; ++ks) {
                     const uint64_t adv = (uint64_t)(ks * 32 >> 4);
@@ -198,9 +199,9 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         mbar_wait(&done_bar, 0, &dummy);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
-        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int quad = warp & 3;
         const int i = i0 + quad * 32 + lane;
-        const bool busy = half * 64 < a.NT;             // this half holds chains of the tile
+        const uint32_t lanes = (uint32_t)(quad * 32) << 16;
         float acc[64], cmp[64];
 #pragma unroll
         for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
@@ -214,9 +215,9 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             tc_fence_after();
 #pragma unroll
             for (int cb = 0; cb < 2; ++cb) {
-                if (!busy) break;
+                if (cb * 32 >= a.NT) break;
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 128 + half * 64 + cb * 32), v);
+                tmem_ld32(tmem + lanes + (uint32_t)(b * 64 + cb * 32), v);
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
                     const float x = v[t], sa = acc[cb * 32 + t];
@@ -229,6 +230,9 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             tc_fence_before();
             mbar_arrive(&acce_bar[b]);
         }
+        // fold the compensation terms (frees their registers for the epilogue)
+#pragma unroll
+        for (int t = 0; t < 64; ++t) acc[t] += cmp[t];
         // small products, once all MMAs are done
         {
             int dummy = 0;
@@ -238,12 +242,12 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         const bool rowok = i < a.p && !abort_flag;
 #pragma unroll
         for (int cb = 0; cb < 2; ++cb) {
-            if (!busy || half * 64 + cb * 32 >= a.NT) break;
+            if (cb * 32 >= a.NT) break;
             float v2[32];
-            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(256 + half * 64 + cb * 32), v2);
+            tmem_ld32(tmem + lanes + (uint32_t)(128 + cb * 32), v2);
 #pragma unroll
             for (int t8 = 0; t8 < 32; t8 += 8) {
-                const int nb = half * 64 + cb * 32 + t8;             // first chain of the group of 8
+                const int nb = cb * 32 + t8;                         // first chain of the group of 8
                 // issue the loads of the 8 chains before any store (they are independent)
                 float zp[8], uo[8], cc[8];
 #pragma unroll
@@ -260,8 +264,8 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
 #pragma unroll
                     for (int qq = 0; qq < 5; ++qq) pr[qq][t] = 0.f;
                     if (!(rowok && s_live[nb + t])) continue;
-                    const int tt = cb * 32 + t8 + t;
-                    const float prod = (acc[tt] + cmp[tt]) + v2[t8 + t];
+                    const int tt = nb + t;
+                    const float prod = acc[tt] + v2[t8 + t];
                     const float x = cc[t] + a.rho * prod;
                     const int64_t sl = (int64_t)g * a.nchains + n0 + nb + t;
                     const int64_t o = sl * a.p + i;
@@ -300,7 +304,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                     float w2 = (b2 ? w3[1] : w3[0]) + __shfl_xor_sync(0xffffffffu, b2 ? w3[0] : w3[1], 4);
                     w2 += __shfl_xor_sync(0xffffffffu, w2, 2);
                     w2 += __shfl_xor_sync(0xffffffffu, w2, 1);
-                    if ((lane & 3) == 0) red[half][quad][cb * 32 + t8 + b4 * 4 + b3 * 2 + b2][qq] = w2;
+                    if ((lane & 3) == 0) red[quad][nb + b4 * 4 + b3 * 2 + b2][qq] = w2;
                 }
             }
         }
@@ -308,19 +312,14 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     tc_fence_before();
     __syncthreads();
     // norms of this row tile: sum of the four row quarters in a fixed order
-    if (threadIdx.x < 128) {
+    if (threadIdx.x < XT_NT_MAX) {
         const int n = threadIdx.x;
-        const int half = n >> 6, col = n & 63;
-        const int chain = n0 + n;
-        if (n < a.NT && chain < a.nchains) {
-            const int64_t sl = (int64_t)g * a.nchains + chain;
-            if (a.live[sl]) {
+        if (n < a.NT && s_live[n]) {
+            const int64_t sl = (int64_t)g * a.nchains + n0 + n;
 #pragma unroll
-                for (int qq = 0; qq < 5; ++qq) {
-                    const float tot = ((red[half][0][col][qq] + red[half][1][col][qq]) + red[half][2][col][qq]) +
-                                      red[half][3][col][qq];
-                    a.norms[(sl * a.RT + rt) * 5 + qq] = tot;
-                }
+            for (int qq = 0; qq < 5; ++qq) {
+                const float tot = ((red[0][n][qq] + red[1][n][qq]) + red[2][n][qq]) + red[3][n][qq];
+                a.norms[(sl * a.RT + rt) * 5 + qq] = tot;
             }
         }
     }
@@ -330,14 +329,14 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     }
 }
 
-// M_g (FP32, p x p) -> three bf16 pieces in 128 x 64 blocks, ordered
-// [g][row tile][k block][piece][128][64] (zero padded), so that the x-update
-// streams each row tile as one contiguous run of 48 KB stages.
+// M_g (FP32, p x p) -> three bf16 pieces in 128 x 32 blocks, ordered
+// [g][row tile][k block][piece][128][32] (zero padded), so that the x-update
+// streams each row tile as one contiguous run of 24 KB stages.
 __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
                           __nv_bfloat16* out)
 {
     const int64_t per = (int64_t)G * ppad * kpad;
-    const int64_t RT = ppad / 128, kst = kpad / 64;
+    const int64_t RT = ppad / XT_TM, kst = kpad / XT_TK;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = t % kpad, row = t / kpad;
@@ -345,11 +344,11 @@ __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, in
         const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] : 0.f;
         __nv_bfloat16 h, m, l;
         split3(x, h, m, l);
-        const int64_t blk = ((g * RT + i / 128) * kst + k / 64) * 3;
-        const int64_t o = (blk * 128 + i % 128) * 64 + k % 64;
+        const int64_t blk = ((g * RT + i / XT_TM) * kst + k / XT_TK) * 3;
+        const int64_t o = (blk * XT_TM + i % XT_TM) * XT_TK + k % XT_TK;
         out[o] = h;
-        out[o + 128 * 64] = m;
-        out[o + 2 * 128 * 64] = l;
+        out[o + XT_TM * XT_TK] = m;
+        out[o + 2 * XT_TM * XT_TK] = l;
     }
 }
 
@@ -469,7 +468,7 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
     const int64_t ppad = ceil_div(p, XT_TM) * XT_TM;
     const int64_t kpad = ceil_div(p, XT_TK) * XT_TK;
     const int RT = (int)(ppad / XT_TM);
-    const int NT = (int)std::min<int64_t>(128, ceil_div(nchains, 16) * 16);
+    const int NT = (int)std::min<int64_t>(XT_NT_MAX, ceil_div(nchains, 16) * 16);
     const int kst = (int)(kpad / XT_TK);
     DevBuf mp(sizeof(__nv_bfloat16) * 3 * (size_t)P.G * ppad * kpad, s);
     k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad, 256), 8192), 256, 0, s>>>(
@@ -493,9 +492,9 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
         P.G, nchains, (int32_t)P.r, P.q, P.warm, sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>());
     UOI_CHECK_LAUNCH();
     count_launch(3);
-    const CUtensorMap mM = make_map_bf16_blocks(mp.ptr, (int64_t)P.G * RT * kst * 3, 3);
-    const CUtensorMap mV0 = make_map_bf16_k64(v0.ptr, kpad, slots, 3, NT);
-    const CUtensorMap mV1 = make_map_bf16_k64(v1.ptr, kpad, slots, 3, NT);
+    const CUtensorMap mM = make_map_bf16_blocks32(mp.ptr, (int64_t)P.G * RT * kst * 3, 3);
+    const CUtensorMap mV0 = make_map_bf16_k32(v0.ptr, kpad, slots, 3, NT);
+    const CUtensorMap mV1 = make_map_bf16_k32(v1.ptr, kpad, slots, 3, NT);
     UOI_CUDA(cudaFuncSetAttribute(k_xupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM));
     XtArgs a;
     a.G = P.G; a.q = P.q; a.r = (int32_t)P.r; a.p = p; a.nchains = nchains; a.NT = NT; a.kst = kst;
