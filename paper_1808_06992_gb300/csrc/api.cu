@@ -248,14 +248,28 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     DevBuf st(sizeof(DevStatus), s);
     UOI_CUDA(cudaMemsetAsync(st.ptr, 0, st.bytes, s));
     DevBuf A(sizeof(T) * (size_t)(B * p * p), s);
-    build_and_factor<T>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<T>(), st.as<DevStatus>(), s);
-    if (!ws) G.release();
-    check_status(st.as<DevStatus>(), s, "Cholesky of G/n + rho I");
-    DevBuf Linv(sizeof(T) * (size_t)(B * p * p), s), M(sizeof(T) * (size_t)(B * p * p), s);
+    DevBuf M(sizeof(T) * (size_t)(B * p * p), s);
     DevBuf c(sizeof(T) * (size_t)(B * p * r), s);
-    inverse_and_rhs<T>(A.as<T>(), Bm.as<double>(), nk.as<double>(), p, r, B, Linv.as<T>(),
-                       M.as<T>(), c.as<T>(), s);
-    Linv.release();
+    bool tc_inverse = false;
+    if constexpr (sizeof(T) == 4) {
+        // mixed form, large p: block inverse with tensor-core GEMMs
+        if (p >= 512 && inverse_tc_available()) {
+            build_system<float>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<float>(), s);
+            if (!ws) G.release();
+            spd_inverse_tc(A.as<float>(), p, B, M.as<float>(), st.as<DevStatus>(), s);
+            check_status(st.as<DevStatus>(), s, "inverse of G/n + rho I");
+            rhs_from_inverse<float>(M.as<float>(), Bm.as<double>(), nk.as<double>(), p, r, B, c.as<float>(), s);
+            tc_inverse = true;
+        }
+    }
+    if (!tc_inverse) {
+        build_and_factor<T>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<T>(), st.as<DevStatus>(), s);
+        if (!ws) G.release();
+        check_status(st.as<DevStatus>(), s, "Cholesky of G/n + rho I");
+        DevBuf Linv(sizeof(T) * (size_t)(B * p * p), s);
+        inverse_and_rhs<T>(A.as<T>(), Bm.as<double>(), nk.as<double>(), p, r, B, Linv.as<T>(),
+                           M.as<T>(), c.as<T>(), s);
+    }
     A.release();
     // learned warm start: predicted z for every column, the dual consistent with
     // it, then the cold schedule from that state

@@ -300,13 +300,18 @@ __global__ void __launch_bounds__(256) k_rhs(const T* M, const double* Bm, const
 }  // namespace
 
 template <typename T>
-void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
-                      T* A, DevStatus* status, cudaStream_t s)
+void build_system(const double* G, const double* nk, double rho, int64_t p, int32_t B, T* A,
+                  cudaStream_t s)
 {
     dim3 gb((unsigned)std::min<int64_t>(ceil_div(p * p, 256), 1024), (unsigned)B);
     k_build_system<T><<<gb, 256, 0, s>>>(G, nk, rho, p, A);
     UOI_CHECK_LAUNCH();
     count_launch();
+}
+
+template <typename T>
+void cholesky_inplace(T* A, int64_t p, int32_t B, DevStatus* status, cudaStream_t s)
+{
     for (int64_t j0 = 0; j0 < p; j0 += NB) {
         const int nb = (int)std::min<int64_t>(NB, p - j0);
         k_chol_diag<T><<<B, 256, 0, s>>>(A, p, j0, nb, status);
@@ -325,14 +330,24 @@ void build_and_factor(const double* G, const double* nk, double rho, int64_t p, 
     }
 }
 
+template <typename T>
+void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
+                      T* A, DevStatus* status, cudaStream_t s)
+{
+    build_system<T>(G, nk, rho, p, B, A, s);
+    cholesky_inplace<T>(A, p, B, status, s);
+}
+
+template void build_system<float>(const double*, const double*, double, int64_t, int32_t, float*,
+                                  cudaStream_t);
+template void cholesky_inplace<float>(float*, int64_t, int32_t, DevStatus*, cudaStream_t);
 template void build_and_factor<double>(const double*, const double*, double, int64_t, int32_t,
                                        double*, DevStatus*, cudaStream_t);
 template void build_and_factor<float>(const double*, const double*, double, int64_t, int32_t,
                                       float*, DevStatus*, cudaStream_t);
 
 template <typename T>
-void inverse_and_rhs(const T* L, const double* Bm, const double* nk, int64_t p, int64_t r,
-                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s)
+void spd_inverse_from_factor(const T* L, int64_t p, int32_t B, T* Linv, T* M, cudaStream_t s)
 {
     UOI_CUDA(cudaMemsetAsync(Linv, 0, sizeof(T) * (size_t)(p * p * B), s));
     const int64_t nbk = ceil_div(p, IB);
@@ -347,12 +362,31 @@ void inverse_and_rhs(const T* L, const double* Bm, const double* nk, int64_t p, 
     const int64_t tt = ceil_div(p, 64);
     k_inverse_product<T><<<dim3((unsigned)(tt * (tt + 1) / 2), (unsigned)B), 256, 0, s>>>(Linv, p, M);
     UOI_CHECK_LAUNCH();
-    const int64_t te = ceil_div(r, 64);
-    k_rhs<T><<<dim3((unsigned)(tt * te), (unsigned)B), 256, 0, s>>>(M, Bm, nk, p, r, c);
-    UOI_CHECK_LAUNCH();
-    count_launch(2);
+    count_launch();
 }
 
+template <typename T>
+void rhs_from_inverse(const T* M, const double* Bm, const double* nk, int64_t p, int64_t r, int32_t B,
+                      T* c, cudaStream_t s)
+{
+    const int64_t tt = ceil_div(p, 64), te = ceil_div(r, 64);
+    k_rhs<T><<<dim3((unsigned)(tt * te), (unsigned)B), 256, 0, s>>>(M, Bm, nk, p, r, c);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+template <typename T>
+void inverse_and_rhs(const T* L, const double* Bm, const double* nk, int64_t p, int64_t r,
+                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s)
+{
+    spd_inverse_from_factor<T>(L, p, B, Linv, M, s);
+    rhs_from_inverse<T>(M, Bm, nk, p, r, B, c, s);
+}
+
+template void spd_inverse_from_factor<float>(const float*, int64_t, int32_t, float*, float*,
+                                             cudaStream_t);
+template void rhs_from_inverse<float>(const float*, const double*, const double*, int64_t, int64_t,
+                                      int32_t, float*, cudaStream_t);
 template void inverse_and_rhs<double>(const double*, const double*, const double*, int64_t,
                                       int64_t, int32_t, double*, double*, double*, cudaStream_t);
 template void inverse_and_rhs<float>(const float*, const double*, const double*, int64_t,

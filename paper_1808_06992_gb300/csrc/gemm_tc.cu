@@ -1,0 +1,432 @@
+// gemm_tc.cu -- FP32-accurate batched GEMM on the tensor cores, and the
+// inverse of a batch of SPD matrices built on it (G3 of the mixed form: the
+// cached inverse M = (G/n + rho I)^{-1} that the ADMM x-update multiplies by).
+//
+// GEMM: D_g = alpha * A_g B_g^T + beta * C_g with A_g (m x k) and B_g (n x k)
+// given as three bf16 pieces each (v = h + m + l, residue <= 2^-24 |v|); the
+// six products h.H, h.M, m.H, h.L, m.M, l.H are summed as in the x-update:
+// h.H in a double-buffered TMEM accumulator drained every 128 k into
+// compensated FP32 pairs, the five small products in a second accumulator.
+// Tiles 128 x 64, k = 32 per stage (64-byte swizzle), 3-stage TMA ring, two
+// CTAs per SM.  Operands are stored as contiguous 128 x 32 (A) or 64 x 32 (B)
+// blocks, [g][row tile][k block][piece][rows][32], so every stage is one TMA
+// copy per operand.
+//
+// Inverse: block (Schur complement) recursion on the SPD matrix
+//   A = [A11 A21^T; A21 A22],  X = A11^{-1},  U = A21 X,  S = A22 - A21 U^T,
+//   Y = S^{-1},  M21 = -Y U,  M11 = X - U^T M21,  M12 = M21^T,
+// which is exact algebra (the block form of the Cholesky-based inverse) with
+// every product a large GEMM; blocks of order <= 256 use the CUDA-core
+// Cholesky / triangular inverse / product.  S stays SPD for SPD A.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace uoi {
+
+namespace {
+using namespace tc;
+
+constexpr int GT_TM = 128;                             // A rows per tile
+constexpr int GT_TN = 64;                              // B rows per tile
+constexpr int GT_TK = 32;
+constexpr int GT_STAGES = 3;
+constexpr int GT_A_BYTES = GT_TM * GT_TK * 2;          // 8 KB per piece
+constexpr int GT_B_BYTES = GT_TN * GT_TK * 2;          // 4 KB per piece
+constexpr int GT_STAGE = 3 * GT_A_BYTES + 3 * GT_B_BYTES;   // 36 KB
+constexpr int GT_SMEM = GT_STAGES * GT_STAGE + 1024;
+constexpr int GT_THREADS = 192;
+constexpr uint32_t GT_TMEM_COLS = 256;                 // A1[0] at 0, A1[1] at 64, A2 at 128
+constexpr int GT_CHUNK_STAGES = 4;                     // drain h.H every 128 k
+constexpr int64_t INV_BASE = 256;                      // CUDA-core inverse at or below this order
+
+struct GemmArgs {
+    int32_t m, n, kst, MT, NT;
+    float alpha, beta;
+    const float* C; int64_t ldc, gsc;                  // C may alias D
+    float* D; int64_t ldd, gsd;
+    int32_t* err;
+};
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l)
+{
+    h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+}
+
+__global__ void __launch_bounds__(GT_THREADS, 2)
+k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t full_bar[GT_STAGES], empty_bar[GT_STAGES], accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.x, nt = blockIdx.y, g = blockIdx.z;
+    const int nchunks = (a.kst + GT_CHUNK_STAGES - 1) / GT_CHUNK_STAGES;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < GT_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(GT_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        const int blkA = ((g * a.MT + mt) * a.kst) * 3;
+        const int blkB = ((g * a.NT + nt) * a.kst) * 3;
+        for (int s_ = 0; s_ < a.kst; ++s_) {
+            const int s = s_ % GT_STAGES;
+            if (s_ >= GT_STAGES && !mbar_wait(&empty_bar[s], ((s_ / GT_STAGES) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            const uint32_t st = sbase + s * GT_STAGE;
+            mbar_expect_tx(&full_bar[s], GT_STAGE);
+            tma_load_3d(st, &tmA, &full_bar[s], 0, 0, blkA + 3 * s_);
+            tma_load_3d(st + 3 * GT_A_BYTES, &tmB, &full_bar[s], 0, 0, blkB + 3 * s_);
+        }
+        if (abort_flag)
+            for (int s_ = max(0, a.kst - GT_STAGES); s_ < a.kst; ++s_)
+                mbar_wait(&full_bar[s_ % GT_STAGES], (s_ / GT_STAGES) & 1, &abort_flag);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_bf16(GT_TM, GT_TN);
+        const uint32_t d2 = tmem + 128u;
+        bool first2 = true;
+        int s_ = 0;
+        for (int c = 0; c < nchunks && !abort_flag; ++c) {
+            const int b = c & 1;
+            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d1 = tmem + (uint32_t)(b * 64);
+            const int send = min(a.kst, (c + 1) * GT_CHUNK_STAGES);
+            bool first1 = true;
+            for (; s_ < send; ++s_) {
+                const int s = s_ % GT_STAGES;
+                if (!mbar_wait(&full_bar[s], (s_ / GT_STAGES) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + s * GT_STAGE;
+                const uint64_t Ah = smem_desc_sw64(st), Am = smem_desc_sw64(st + GT_A_BYTES);
+                const uint64_t Al = smem_desc_sw64(st + 2 * GT_A_BYTES);
+                const uint32_t bb = st + 3 * GT_A_BYTES;
+                const uint64_t Bh = smem_desc_sw64(bb), Bm = smem_desc_sw64(bb + GT_B_BYTES);
+                const uint64_t Bl = smem_desc_sw64(bb + 2 * GT_B_BYTES);
+#pragma unroll
+                for (int ks = 0; ks < GT_TK / 16; ++ks) {
+                    const uint64_t adv = (uint64_t)(ks * 32 >> 4);
+                    mma_bf16(d1, Ah + adv, Bh + adv, idesc, first1 ? 0u : 1u);
+                    mma_bf16(d2, Ah + adv, Bm + adv, idesc, first2 ? 0u : 1u);
+                    mma_bf16(d2, Am + adv, Bh + adv, idesc, 1u);
+                    mma_bf16(d2, Ah + adv, Bl + adv, idesc, 1u);
+                    mma_bf16(d2, Am + adv, Bm + adv, idesc, 1u);
+                    mma_bf16(d2, Al + adv, Bh + adv, idesc, 1u);
+                    first1 = false;
+                    first2 = false;
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            if (abort_flag) break;
+            mma_commit(&accf_bar[b]);
+        }
+        mma_commit(&done_bar);
+        int dummy = 0;
+        mbar_wait(&done_bar, 0, &dummy);
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int quad = warp & 3;
+        const int i = mt * GT_TM + quad * 32 + lane;
+        const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+        float acc[64], cmp[64];
+#pragma unroll
+        for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag);
+            if (!__all_sync(0xffffffffu, okw)) {               // warp-uniform exit
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int cb = 0; cb < 2; ++cb) {
+                float v[32];
+                tmem_ld32(tmem + lanes + (uint32_t)(b * 64 + cb * 32), v);
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const float x = v[t], sa = acc[cb * 32 + t];
+                    const float sum = sa + x;
+                    const float bv = sum - sa;
+                    cmp[cb * 32 + t] += (sa - (sum - bv)) + (x - bv);
+                    acc[cb * 32 + t] = sum;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce_bar[b]);
+        }
+#pragma unroll
+        for (int t = 0; t < 64; ++t) acc[t] += cmp[t];
+        {
+            int dummy = 0;
+            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);
+        }
+        __syncwarp();
+        tc_fence_after();
+        const bool rowok = i < a.m && !abort_flag;
+        const int j0 = nt * GT_TN;
+        float* drow = a.D + (int64_t)g * a.gsd + (int64_t)i * a.ldd;
+        const float* crow = a.C ? a.C + (int64_t)g * a.gsc + (int64_t)i * a.ldc : nullptr;
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+            float v2[32];
+            tmem_ld32(tmem + lanes + (uint32_t)(128 + cb * 32), v2);   // whole warp
+            if (!rowok) continue;
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int j = j0 + cb * 32 + t;
+                if (j < a.n) {
+                    float r = a.alpha * (acc[cb * 32 + t] + v2[t]);
+                    if (crow) r += a.beta * crow[j];
+                    drow[j] = r;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_TMEM_COLS));
+    }
+}
+
+// Three bf16 pieces of op(S_g) (rows x K; op = transpose if trans) in blocks of
+// rt x 32, ordered [g][row tile][k block][piece][rt][32], zero padded to the
+// tile multiples.  S_g element (i, k) is at src[g*gs + i*ld + k] (or
+// src[g*gs + k*ld + i] transposed).
+__global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K,
+                               int32_t trans, int32_t rt, int32_t G, int64_t rpad, int64_t kpad,
+                               __nv_bfloat16* out)
+{
+    const int64_t per = rpad * kpad;
+    const int64_t total = (int64_t)G * per;
+    const int64_t RT = rpad / rt, kst = kpad / GT_TK;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = t / per, rem = t % per;
+        // consecutive threads walk the contiguous dimension of the source
+        int64_t i, k;
+        if (trans) { i = rem % rpad; k = rem / rpad; }
+        else { k = rem % kpad; i = rem / kpad; }
+        float x = 0.f;
+        if (i < rows && k < K) x = trans ? src[g * gs + k * ld + i] : src[g * gs + i * ld + k];
+        __nv_bfloat16 h, m, l;
+        split3(x, h, m, l);
+        const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * 3;
+        const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;
+        out[o] = h;
+        out[o + rt * GT_TK] = m;
+        out[o + 2 * rt * GT_TK] = l;
+    }
+}
+
+// dst block (n1 x n2) = src block^T (n2 x n1), per group.
+__global__ void k_transpose_block(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t gs,
+                                  int32_t n1, int32_t n2)
+{
+    __shared__ float tile[32][33];
+    const int g = blockIdx.z;
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;    // bx over n1 (dst rows), by over n2
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int r = by + yy, c = bx + threadIdx.x;           // src row r (< n2), col c (< n1)
+        if (r < n2 && c < n1) tile[yy][threadIdx.x] = src[(int64_t)g * gs + (int64_t)r * lds + c];
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int r = bx + yy, c = by + threadIdx.x;           // dst row r (< n1), col c (< n2)
+        if (r < n1 && c < n2) dst[(int64_t)g * gs + (int64_t)r * ldd + c] = tile[threadIdx.x][yy];
+    }
+}
+
+// Copy an n x n block between strided storages (per group).
+__global__ void k_copy_block(const float* src, int64_t lds, int64_t gss, float* dst, int64_t ldd,
+                             int64_t gsd, int32_t n)
+{
+    const int g = blockIdx.y;
+    const int64_t total = (int64_t)n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / n, j = t % n;
+        dst[g * gsd + i * ldd + j] = src[g * gss + i * lds + j];
+    }
+}
+
+struct Pieces {
+    DevBuf buf;
+    CUtensorMap map;
+    int32_t tiles = 0, kst = 0;
+};
+
+// Split op(S) into pieces for a GEMM operand with row tiles of rt.
+void make_pieces(Pieces& P, const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K, bool trans,
+                 int32_t rt, int32_t G, cudaStream_t s)
+{
+    const int64_t rpad = ceil_div(rows, rt) * rt, kpad = ceil_div(K, GT_TK) * GT_TK;
+    P.tiles = (int32_t)(rpad / rt);
+    P.kst = (int32_t)(kpad / GT_TK);
+    P.buf.alloc(sizeof(__nv_bfloat16) * 3 * (size_t)G * rpad * kpad, s);
+    const int64_t total = (int64_t)G * rpad * kpad;
+    k_split_blocks<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, s>>>(
+        src, ld, gs, rows, K, trans ? 1 : 0, rt, G, rpad, kpad, P.buf.as<__nv_bfloat16>());
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    // blocks of rt x 32 bf16 (64-byte rows); three consecutive blocks per stage
+    CUtensorMap m;
+    cuuint64_t dims[3] = { 32u, (cuuint64_t)rt, (cuuint64_t)((int64_t)G * P.tiles * P.kst * 3) };
+    cuuint64_t strides[2] = { 64u, (cuuint64_t)rt * 64u };
+    cuuint32_t box[3] = { 32u, (cuuint32_t)rt, 3u };
+    cuuint32_t estr[3] = { 1, 1, 1 };
+    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P.buf.ptr, dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    P.map = m;
+}
+
+// D = alpha A B^T + beta C with A (m x k) and B (n x k) in pieces.
+void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, float alpha, float beta,
+           const float* C, int64_t ldc, int64_t gsc, float* D, int64_t ldd, int64_t gsd, int32_t* err,
+           cudaStream_t s)
+{
+    if (A.kst != B.kst) throw Error(UOI_ERR_INVALID_ARG, "gemm3: operand k extents differ");
+    UOI_CUDA(cudaFuncSetAttribute(k_gemm3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM));
+    GemmArgs a;
+    a.m = m; a.n = n; a.kst = A.kst; a.MT = A.tiles; a.NT = B.tiles;
+    a.alpha = alpha; a.beta = beta;
+    a.C = C; a.ldc = ldc; a.gsc = gsc;
+    a.D = D; a.ldd = ldd; a.gsd = gsd;
+    a.err = err;
+    const dim3 grid((unsigned)ceil_div(m, GT_TM), (unsigned)ceil_div(n, GT_TN), (unsigned)G);
+    k_gemm3_tc<<<grid, GT_THREADS, GT_SMEM, s>>>(A.map, B.map, a);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+// CUDA-core inverse of an n x n SPD block (strided), via a contiguous copy.
+void inv_base(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM, int64_t gsM,
+              int64_t n, int32_t G, DevStatus* st, cudaStream_t s)
+{
+    DevBuf T(sizeof(float) * (size_t)(G * n * n), s), Li(sizeof(float) * (size_t)(G * n * n), s);
+    DevBuf Mi(sizeof(float) * (size_t)(G * n * n), s);
+    const unsigned gx = (unsigned)std::min<int64_t>(ceil_div(n * n, 256), 1024);
+    k_copy_block<<<dim3(gx, (unsigned)G), 256, 0, s>>>(A, ldA, gsA, T.as<float>(), n, n * n, (int32_t)n);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    cholesky_inplace<float>(T.as<float>(), n, G, st, s);
+    spd_inverse_from_factor<float>(T.as<float>(), n, G, Li.as<float>(), Mi.as<float>(), s);
+    k_copy_block<<<dim3(gx, (unsigned)G), 256, 0, s>>>(Mi.as<float>(), n, n * n, Mout, ldM, gsM, (int32_t)n);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void inv_rec(const float* A, int64_t ldA, int64_t gsA, float* M, int64_t ldM, int64_t gsM, int64_t n,
+             int32_t G, DevStatus* st, int32_t* err, cudaStream_t s)
+{
+    if (n <= INV_BASE) {
+        inv_base(A, ldA, gsA, M, ldM, gsM, n, G, st, s);
+        return;
+    }
+    const int64_t p1 = ceil_div(n / 2, GT_TM) * GT_TM, p2 = n - p1;
+    const float* A21 = A + p1 * ldA;
+    const float* A22 = A + p1 * ldA + p1;
+    float* X = M;                                  // M11 block, holds X = A11^{-1} first
+    float* M21 = M + p1 * ldM;
+    float* M12 = M + p1;
+    float* Y = M + p1 * ldM + p1;
+    // X = A11^{-1}
+    inv_rec(A, ldA, gsA, X, ldM, gsM, p1, G, st, err, s);
+    // U = A21 X   (p2 x p1)
+    DevBuf U(sizeof(float) * (size_t)(G * p2 * p1), s), S(sizeof(float) * (size_t)(G * p2 * p2), s);
+    {
+        Pieces pa, pb;
+        make_pieces(pa, A21, ldA, gsA, (int32_t)p2, (int32_t)p1, false, GT_TM, G, s);
+        make_pieces(pb, X, ldM, gsM, (int32_t)p1, (int32_t)p1, false, GT_TN, G, s);
+        gemm3(pa, pb, (int32_t)p2, (int32_t)p1, G, 1.f, 0.f, nullptr, 0, 0, U.as<float>(), p1, p2 * p1,
+              err, s);
+        // S = A22 - A21 U^T   (p2 x p2)
+        Pieces pu;
+        make_pieces(pu, U.as<float>(), p1, p2 * p1, (int32_t)p2, (int32_t)p1, false, GT_TN, G, s);
+        gemm3(pa, pu, (int32_t)p2, (int32_t)p2, G, -1.f, 1.f, A22, ldA, gsA, S.as<float>(), p2, p2 * p2,
+              err, s);
+    }
+    // Y = S^{-1}
+    inv_rec(S.as<float>(), p2, p2 * p2, Y, ldM, gsM, p2, G, st, err, s);
+    S.release();
+    {
+        // M21 = -Y U   (p2 x p1): A = Y (p2 x p2), B rows = columns of U
+        Pieces py, put;
+        make_pieces(py, Y, ldM, gsM, (int32_t)p2, (int32_t)p2, false, GT_TM, G, s);
+        make_pieces(put, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TN, G, s);
+        gemm3(py, put, (int32_t)p2, (int32_t)p1, G, -1.f, 0.f, nullptr, 0, 0, M21, ldM, gsM, err, s);
+    }
+    {
+        // M11 = X - U^T M21   (p1 x p1): A rows = columns of U, B rows = columns of M21
+        Pieces pua, pmt;
+        make_pieces(pua, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TM, G, s);
+        make_pieces(pmt, M21, ldM, gsM, (int32_t)p1, (int32_t)p2, true, GT_TN, G, s);
+        gemm3(pua, pmt, (int32_t)p1, (int32_t)p1, G, -1.f, 1.f, X, ldM, gsM, X, ldM, gsM, err, s);
+    }
+    // M12 = M21^T
+    k_transpose_block<<<dim3((unsigned)ceil_div(p1, 32), (unsigned)ceil_div(p2, 32), (unsigned)G),
+                        dim3(32, 8), 0, s>>>(M21, ldM, M12, ldM, gsM, (int32_t)p1, (int32_t)p2);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+}  // namespace
+
+bool inverse_tc_available() { return gram_tc_available(); }
+
+void spd_inverse_tc(const float* A, int64_t p, int32_t G, float* M, DevStatus* st, cudaStream_t s)
+{
+    DevBuf err(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
+    inv_rec(A, p, p * p, M, p, p * p, p, G, st, err.as<int32_t>(), s);
+    int32_t herr = 0;
+    UOI_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    if (herr) throw Error(herr, "tensor-core inverse: a bounded pipeline wait expired");
+}
+
+}  // namespace uoi

@@ -97,6 +97,23 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
 template <typename T>
 void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
                       T* A, DevStatus* status, cudaStream_t s);
+// The two halves of build_and_factor.
+template <typename T>
+void build_system(const double* G, const double* nk, double rho, int64_t p, int32_t B, T* A,
+                  cudaStream_t s);
+template <typename T>
+void cholesky_inplace(T* A, int64_t p, int32_t B, DevStatus* status, cudaStream_t s);
+// M_k = A_k^{-1} from the factor in the lower triangle of A (Linv: p x p scratch).
+template <typename T>
+void spd_inverse_from_factor(const T* L, int64_t p, int32_t B, T* Linv, T* M, cudaStream_t s);
+// c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].
+template <typename T>
+void rhs_from_inverse(const T* M, const double* Bm, const double* nk, int64_t p, int64_t r, int32_t B,
+                      T* c, cudaStream_t s);
+// M_k = A_k^{-1} for SPD A_k (FP32, p x p each) by block Schur-complement recursion
+// with FP32-accurate tensor-core GEMMs (gemm_tc.cu); A is left unchanged.
+bool inverse_tc_available();
+void spd_inverse_tc(const float* A, int64_t p, int32_t G, float* M, DevStatus* status, cudaStream_t s);
 // M_k = A_k^{-1} from the factor L (lower triangle of A), then
 // c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].
 template <typename T>

@@ -207,7 +207,8 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
-            if (!mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag)) {
+            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag);
+            if (!__all_sync(0xffffffffu, okw)) {               // warp-uniform exit
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -238,6 +239,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             int dummy = 0;
             if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);
         }
+        __syncwarp();
         tc_fence_after();
         const bool rowok = i < a.p && !abort_flag;
 #pragma unroll

@@ -272,3 +272,23 @@ def test_ols_duplicate_column_goes_to_fp64_factor(prec):
             ok = ~pair
             np.testing.assert_allclose(gpu["est_loss"][:, ok, 0], ref["est_loss"][:, ok, 0],
                                        rtol=1e-9, atol=1e-12)
+
+
+def test_mixed_tensor_core_inverse_vs_oracle():
+    # p >= 512 in the mixed form inverts G/n + rho I by the block Schur-complement
+    # recursion on FP32-accurate tensor-core GEMMs (p = 700 recurses twice, with
+    # ragged 316- and 60-order blocks); the ADMM solutions must match the oracle's
+    # Cholesky-based FP64 solutions to the level of the stopping tolerance.
+    d = synth.lasso_problem(2500, 700, 40, seed=33, sigma=0.5, toeplitz_rho=0.5)
+    n = d.X.shape[0]
+    w = np.stack([oracle.selection_weights(n, 0, 0, 0, k) for k in range(3)])
+    lam = oracle.lambda_grid(oracle.lambda_max(d.X, d.y), 8)
+    ref = oracle.lasso_admm_batch(d.X, d.y, w, lam, warm_start=0)
+    gpu = native.lasso_admm_batch(d.X, d.y, w, lam, warm_start=0, precision=native.PREC_MIXED)
+    assert gpu["conv"].all()
+    worst = max(rel_l2(gpu["beta"][idx], ref["beta"][idx]) for idx in np.ndindex(*ref["beta"].shape[:3]))
+    assert worst <= 1e-4, worst
+    thr = lam[None, :, None, None]
+    amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
+    assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
+    assert np.abs(gpu["iters"].astype(int) - ref["iters"]).max() <= max(3, int(0.1 * ref["iters"].max()))
