@@ -37,6 +37,12 @@ struct OlsArgs {
     int smax;                                // max support size
     bool use_smem;
     const int32_t* list;                     // solve indices to run (null: 0 .. solves-1)
+    // Moments restricted to the union U of the family supports: Gt, Ge are
+    // B2 x pu x pu and Bt, Be B2 x pu x r over U's columns; upos[i] = position of
+    // feature i in U, ucols[t] = feature at position t.
+    const int32_t* upos;
+    const int32_t* ucols;
+    int64_t pu;
     int32_t* fb_list;                        // mixed pass: solves left to the FP64 kernel
     int32_t* fb_count;
     float* fscratch;                         // mixed pass: global packed factor (per CTA), or null
@@ -46,7 +52,7 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int* idx = reinterpret_cast<int*>(smem_raw);                         // p ints
-    double* bs = reinterpret_cast<double*>(smem_raw + sizeof(int) * ((a.p + 1) & ~1));
+    double* bs = reinterpret_cast<double*>(smem_raw + sizeof(int) * ((a.smax + 1) & ~1));
     double* red = bs + a.smax + 1;                                       // 32 doubles
     double* Gs = a.use_smem ? red + 32 : a.scratch + (size_t)blockIdx.x * a.smax * a.smax;
     __shared__ int s_count;
@@ -69,21 +75,21 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
                 const int64_t i = i0 + lane;
                 const bool in = i < a.p && ((bits[i >> 6] >> (i & 63)) & 1ull);
                 const unsigned bal = __ballot_sync(0xffffffffu, in);
-                if (in) idx[cnt + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+                if (in) idx[cnt + __popc(bal & ((1u << lane) - 1u))] = a.upos[i];
                 cnt += __popc(bal);
             }
             if (lane == 0) { s_count = cnt; s_bad = 0; }
         }
         __syncthreads();
         const int s = s_count;
-        const double* Gk = a.Gt + (size_t)k * a.p * a.p;
-        const double* Bk = a.Bt + (size_t)k * a.p * a.r;
+        const double* Gk = a.Gt + (size_t)k * a.pu * a.pu;
+        const double* Bk = a.Bt + (size_t)k * a.pu * a.r;
         double ridge = 0.0;
         for (int attempt = 0; attempt < 2 && s > 0; ++attempt) {
             double dm = 0.0;
             for (int x = threadIdx.x; x < s * s; x += blockDim.x) {
                 const int r0 = x / s, c0 = x % s;
-                const double v = Gk[(size_t)idx[r0] * a.p + idx[c0]];
+                const double v = Gk[(size_t)idx[r0] * a.pu + idx[c0]];
                 Gs[x] = v + (r0 == c0 ? ridge : 0.0);
                 if (r0 == c0) dm = fmax(dm, v);
             }
@@ -142,15 +148,15 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
         __syncthreads();
         if (a.jstar) {
             double* out = a.chosen + ((size_t)k * a.r + e) * a.p;
-            for (int x = threadIdx.x; x < s; x += blockDim.x) out[idx[x]] = bs[x];
+            for (int x = threadIdx.x; x < s; x += blockDim.x) out[a.ucols[idx[x]]] = bs[x];
         } else {
             // held-out loss via the evaluation moments
-            const double* Gek = a.Ge + (size_t)k * a.p * a.p;
-            const double* Bek = a.Be + (size_t)k * a.p * a.r;
+            const double* Gek = a.Ge + (size_t)k * a.pu * a.pu;
+            const double* Bek = a.Be + (size_t)k * a.pu * a.r;
             double part = 0.0;
             for (int x = threadIdx.x; x < s * s; x += blockDim.x) {
                 const int r0 = x / s, c0 = x % s;
-                part += bs[r0] * Gek[(size_t)idx[r0] * a.p + idx[c0]] * bs[c0];
+                part += bs[r0] * Gek[(size_t)idx[r0] * a.pu + idx[c0]] * bs[c0];
             }
             for (int x = threadIdx.x; x < s; x += blockDim.x)
                 part -= 2.0 * bs[x] * Bek[(size_t)idx[x] * a.r + e];
@@ -251,20 +257,21 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
                 const int64_t i = i0 + lane;
                 const bool in = i < a.p && ((bits[i >> 6] >> (i & 63)) & 1ull);
                 const unsigned bal = __ballot_sync(0xffffffffu, in);
-                if (in) idx[cnt + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+                if (in) idx[cnt + __popc(bal & ((1u << lane) - 1u))] = a.upos[i];
                 cnt += __popc(bal);
             }
             if (lane == 0) s_count = cnt;
         }
         __syncthreads();
         const int s = s_count;
-        const double* Gk = a.Gt + (size_t)k * a.p * a.p;
-        const double* Bk = a.Bt + (size_t)k * a.p * a.r;
+        const double* Gk = a.Gt + (size_t)k * a.pu * a.pu;
+        const double* Bk = a.Bt + (size_t)k * a.pu * a.r;
         // gather the packed lower triangle in FP32, b in FP64
         double dm = 0.0;
         for (int i = warp; i < s; i += 8) {
-            const double* grow = Gk + (size_t)idx[i] * a.p;
+            const double* grow = Gk + (size_t)idx[i] * a.pu;
             float* lrow = L + packed_row(i);
+#pragma unroll 4
             for (int c = lane; c <= i; c += 32) {
                 const double v = grow[idx[c]];
                 lrow[c] = f64_to_f32_int(v);
@@ -311,8 +318,9 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
                 if (itr == OLS_REFINE_MAX) { done = dmx <= 1e-12 * xmx; break; }
                 // residual r_i = b_i - sum_c G[S_i, S_c] x_c (one warp per row)
                 for (int i = warp; i < s; i += 8) {
-                    const double* grow = Gk + (size_t)idx[i] * a.p;
+                    const double* grow = Gk + (size_t)idx[i] * a.pu;
                     double acc = 0.0;
+#pragma unroll 4
                     for (int c = lane; c < s; c += 32) acc += grow[idx[c]] * x64[c];
                     acc = warp_sum(acc);
                     if (lane == 0) w[i] = (float)(b64[i] - acc);
@@ -327,14 +335,15 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
         }
         if (a.jstar) {
             double* out = a.chosen + ((size_t)k * a.r + e) * a.p;
-            for (int x = threadIdx.x; x < s; x += blockDim.x) out[idx[x]] = x64[x];
+            for (int x = threadIdx.x; x < s; x += blockDim.x) out[a.ucols[idx[x]]] = x64[x];
         } else {
-            const double* Gek = a.Ge + (size_t)k * a.p * a.p;
-            const double* Bek = a.Be + (size_t)k * a.p * a.r;
+            const double* Gek = a.Ge + (size_t)k * a.pu * a.pu;
+            const double* Bek = a.Be + (size_t)k * a.pu * a.r;
             double part = 0.0;
             for (int i = warp; i < s; i += 8) {
-                const double* grow = Gek + (size_t)idx[i] * a.p;
+                const double* grow = Gek + (size_t)idx[i] * a.pu;
                 double acc = 0.0;
+#pragma unroll 4
                 for (int c = lane; c < s; c += 32) acc += grow[idx[c]] * x64[c];
                 acc = warp_sum(acc);
                 if (lane == 0) part += x64[i] * acc;
@@ -350,6 +359,37 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
         }
         __syncthreads();
     }
+}
+
+// out[k][a][b] = G[k][cols[a]][cols[b]] (restriction to the union U).
+__global__ void k_gather_gram(const double* G, int64_t p, const int32_t* cols, int64_t u, int32_t B,
+                              double* out)
+{
+    const int64_t per = u * u, total = (int64_t)B * per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / per, rem = t % per;
+        out[t] = G[(k * p + cols[rem / u]) * p + cols[rem % u]];
+    }
+}
+
+// out[k][a][e] = Bm[k][cols[a]][e].
+__global__ void k_gather_rhs(const double* Bm, int64_t p, int64_t r, const int32_t* cols, int64_t u,
+                             int32_t B, double* out)
+{
+    const int64_t per = u * r, total = (int64_t)B * per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / per, rem = t % per;
+        out[t] = Bm[(k * p + cols[rem / r]) * r + rem % r];
+    }
+}
+
+__global__ void k_union_pos(const int32_t* cols, int64_t u, int32_t* pos)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < u;
+         t += (int64_t)gridDim.x * blockDim.x)
+        pos[cols[t]] = (int32_t)t;
 }
 
 // dup[j*r + e] = smallest j' <= j whose support for response e equals S_{j,e}.
@@ -461,7 +501,7 @@ int32_t family_support_max(const OlsArgs& a, cudaStream_t s)
 void launch_ols_fp64(OlsArgs a, cudaStream_t s)
 {
     a.use_smem = a.smax <= OLS_SMEM_MAX;
-    size_t smem = sizeof(int) * ((a.p + 1) & ~1) + sizeof(double) * (a.smax + 1 + 32);
+    size_t smem = sizeof(int) * ((a.smax + 1) & ~1) + sizeof(double) * (a.smax + 1 + 32);
     DevBuf scratch;
     int grid = (int)std::min<int64_t>(a.solves, 152 * 8);
     if (a.use_smem) {
@@ -587,12 +627,71 @@ void family_mask_tail(uint64_t* fam, int64_t count, int64_t p, cudaStream_t s)
     count_launch();
 }
 
+namespace {
+
+// The OLS solves only touch rows and columns in the union U of the family
+// supports: restricting the moments to U once per call makes every later
+// access a read of a small, L2-resident matrix.
+struct UnionMoments {
+    DevBuf cols, pos, Gt, Bt, Ge, Be;
+    int64_t pu = 0;
+};
+
+void restrict_to_union(const uint64_t* family, int64_t p, int64_t r, int32_t q, int32_t B2,
+                       const double* Gt, const double* Bt, const double* Ge, const double* Be,
+                       UnionMoments& U, cudaStream_t s)
+{
+    U.cols.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(p, 1), s);
+    U.pu = union_columns(family, (int64_t)q * r, p, U.cols.as<int32_t>(), s);
+    const int64_t u1 = std::max<int64_t>(U.pu, 1);
+    U.pos.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(p, 1), s);
+    UOI_CUDA(cudaMemsetAsync(U.pos.ptr, 0xFF, sizeof(int32_t) * (size_t)p, s));
+    k_union_pos<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(U.pu, 256), 64)), 256, 0, s>>>(
+        U.cols.as<int32_t>(), U.pu, U.pos.as<int32_t>());
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    auto gram = [&](const double* G, DevBuf& out) {
+        out.alloc(sizeof(double) * (size_t)(B2 * u1 * u1), s);
+        const int64_t total = (int64_t)B2 * U.pu * U.pu;
+        if (total == 0) return;
+        k_gather_gram<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, s>>>(
+            G, p, U.cols.as<int32_t>(), U.pu, B2, out.as<double>());
+        UOI_CHECK_LAUNCH();
+        count_launch();
+    };
+    auto rhs = [&](const double* Bm, DevBuf& out) {
+        out.alloc(sizeof(double) * (size_t)(B2 * u1 * r), s);
+        const int64_t total = (int64_t)B2 * U.pu * r;
+        if (total == 0) return;
+        k_gather_rhs<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, s>>>(
+            Bm, p, r, U.cols.as<int32_t>(), U.pu, B2, out.as<double>());
+        UOI_CHECK_LAUNCH();
+        count_launch();
+    };
+    gram(Gt, U.Gt);
+    rhs(Bt, U.Bt);
+    if (Ge) { gram(Ge, U.Ge); rhs(Be, U.Be); }
+}
+
+void use_union(OlsArgs& a, const UnionMoments& U)
+{
+    a.Gt = U.Gt.as<double>(); a.Bt = U.Bt.as<double>();
+    a.Ge = U.Ge.ptr ? U.Ge.as<double>() : nullptr;
+    a.Be = U.Be.ptr ? U.Be.as<double>() : nullptr;
+    a.upos = U.pos.as<int32_t>(); a.ucols = U.cols.as<int32_t>(); a.pu = U.pu;
+}
+
+}  // namespace
+
 int64_t ols_losses(const double* Gt, const double* Bt, const double* Ge, const double* Be,
                 const double* yye, const uint64_t* family, int64_t p, int64_t r, int32_t q,
                 int32_t B2, double* losses, int32_t* singular, cudaStream_t s)
 {
+    UnionMoments U;
+    restrict_to_union(family, p, r, q, B2, Gt, Bt, Ge, Be, U, s);
     OlsArgs a{};
-    a.Gt = Gt; a.Bt = Bt; a.Ge = Ge; a.Be = Be; a.yye = yye; a.family = family;
+    use_union(a, U);
+    a.yye = yye; a.family = family;
     a.p = p; a.r = r; a.q = q; a.B2 = B2; a.W = (int32_t)((p + 63) / 64);
     a.losses = losses; a.singular = singular;
     a.solves = (int64_t)B2 * q * r;
@@ -621,8 +720,11 @@ int64_t ols_chosen(const double* Gt, const double* Bt, const uint64_t* family, c
                 int64_t p, int64_t r, int32_t q, int32_t B2, double* chosen, cudaStream_t s)
 {
     UOI_CUDA(cudaMemsetAsync(chosen, 0, sizeof(double) * (size_t)(B2 * r * p), s));
+    UnionMoments U;
+    restrict_to_union(family, p, r, q, B2, Gt, Bt, nullptr, nullptr, U, s);
     OlsArgs a{};
-    a.Gt = Gt; a.Bt = Bt; a.family = family;
+    use_union(a, U);
+    a.family = family;
     a.p = p; a.r = r; a.q = q; a.B2 = B2; a.W = (int32_t)((p + 63) / 64);
     a.jstar = jstar; a.chosen = chosen;
     a.solves = (int64_t)B2 * r;

@@ -297,6 +297,42 @@ __global__ void __launch_bounds__(256) k_rhs(const T* M, const double* Bm, const
     }
 }
 
+// b_k[j][e] / nk[k] in T, once per system (keeps FP64 division off the GEMV).
+template <typename T>
+__global__ void k_scale_rhs(const double* Bm, const double* nk, int64_t pr, int32_t B, T* out)
+{
+    const int64_t total = (int64_t)B * pr;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (T)(Bm[t] / nk[t / pr]);
+}
+
+// c[k][e][i] = sum_j M[k][i][j] bs[k][j][e] for few responses: one warp per row
+// (M streamed once, coalesced).
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_rhs_gemv(const T* M, const T* bs, int64_t p, T* c)
+{
+    const int64_t k = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= p) return;
+    const T* row = M + (k * p + i) * p;
+    const T* b = bs + k * p * R;
+    T acc[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) acc[e] = T(0);
+    for (int64_t j = lane; j < p; j += 32) {
+        const T mv = row[j];
+#pragma unroll
+        for (int e = 0; e < R; ++e) acc[e] += mv * b[j * R + e];
+    }
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const T v = warp_sum(acc[e]);
+        if (lane == 0) c[(k * R + e) * p + i] = v;
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -369,6 +405,16 @@ template <typename T>
 void rhs_from_inverse(const T* M, const double* Bm, const double* nk, int64_t p, int64_t r, int32_t B,
                       T* c, cudaStream_t s)
 {
+    if (r == 1) {
+        DevBuf bs(sizeof(T) * (size_t)(B * p), s);
+        k_scale_rhs<T><<<(unsigned)std::min<int64_t>(ceil_div(B * p, 256), 4096), 256, 0, s>>>(
+            Bm, nk, p, B, bs.as<T>());
+        UOI_CHECK_LAUNCH();
+        k_rhs_gemv<T, 1><<<dim3((unsigned)ceil_div(p, 8), (unsigned)B), 256, 0, s>>>(M, bs.as<T>(), p, c);
+        UOI_CHECK_LAUNCH();
+        count_launch(2);
+        return;
+    }
     const int64_t tt = ceil_div(p, 64), te = ceil_div(r, 64);
     k_rhs<T><<<dim3((unsigned)(tt * te), (unsigned)B), 256, 0, s>>>(M, Bm, nk, p, r, c);
     UOI_CHECK_LAUNCH();

@@ -234,25 +234,34 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 // Three bf16 pieces of op(S_g) (rows x K; op = transpose if trans) in blocks of
 // rt x 32, ordered [g][row tile][k block][piece][rt][32], zero padded to the
 // tile multiples.  S_g element (i, k) is at src[g*gs + i*ld + k] (or
-// src[g*gs + k*ld + i] transposed).
+// src[g*gs + k*ld + i] transposed).  32 x 32 tiles through shared memory, so
+// that both the read (along the source's contiguous index) and the write
+// (along k) are coalesced.  Block (32, 8); grid (rpad/32, kpad/32, G).
 __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K,
-                               int32_t trans, int32_t rt, int32_t G, int64_t rpad, int64_t kpad,
+                               int32_t trans, int32_t rt, int64_t rpad, int64_t kpad,
                                __nv_bfloat16* out)
 {
-    const int64_t per = rpad * kpad;
-    const int64_t total = (int64_t)G * per;
+    __shared__ float tile[32][33];                      // [k local][i local]
+    const int64_t g = blockIdx.z;
+    const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const float* sg = src + g * gs;
+    for (int j = ty; j < 32; j += 8) {
+        if (trans) {
+            const int64_t i = i0 + tx, k = k0 + j;
+            tile[j][tx] = (i < rows && k < K) ? sg[k * ld + i] : 0.f;
+        } else {
+            const int64_t i = i0 + j, k = k0 + tx;
+            tile[tx][j] = (i < rows && k < K) ? sg[i * ld + k] : 0.f;
+        }
+    }
+    __syncthreads();
     const int64_t RT = rpad / rt, kst = kpad / GT_TK;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = t / per, rem = t % per;
-        // consecutive threads walk the contiguous dimension of the source
-        int64_t i, k;
-        if (trans) { i = rem % rpad; k = rem / rpad; }
-        else { k = rem % kpad; i = rem / kpad; }
-        float x = 0.f;
-        if (i < rows && k < K) x = trans ? src[g * gs + k * ld + i] : src[g * gs + i * ld + k];
+    const int64_t k = k0 + tx;
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t i = i0 + j;
         __nv_bfloat16 h, m, l;
-        split3(x, h, m, l);
+        split3(tile[tx][j], h, m, l);
         const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * 3;
         const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;
         out[o] = h;
@@ -306,9 +315,8 @@ void make_pieces(Pieces& P, const float* src, int64_t ld, int64_t gs, int32_t ro
     P.tiles = (int32_t)(rpad / rt);
     P.kst = (int32_t)(kpad / GT_TK);
     P.buf.alloc(sizeof(__nv_bfloat16) * 3 * (size_t)G * rpad * kpad, s);
-    const int64_t total = (int64_t)G * rpad * kpad;
-    k_split_blocks<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, s>>>(
-        src, ld, gs, rows, K, trans ? 1 : 0, rt, G, rpad, kpad, P.buf.as<__nv_bfloat16>());
+    k_split_blocks<<<dim3((unsigned)(rpad / 32), (unsigned)(kpad / 32), (unsigned)G), dim3(32, 8), 0, s>>>(
+        src, ld, gs, rows, K, trans ? 1 : 0, rt, rpad, kpad, P.buf.as<__nv_bfloat16>());
     UOI_CHECK_LAUNCH();
     count_launch();
     // blocks of rt x 32 bf16 (64-byte rows); three consecutive blocks per stage
