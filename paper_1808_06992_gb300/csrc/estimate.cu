@@ -185,25 +185,51 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
 constexpr float OLS_F32_PIVOT = 1e-3f;
 constexpr int OLS_REFINE_MAX = 8;
 
-__device__ __forceinline__ int64_t packed_row(int i) { return (int64_t)i * (i + 1) / 2; }
+__device__ __forceinline__ int packed_row(int i) { return (i * (i + 1)) >> 1; }
 
-// w <- L^{-T} L^{-1} w by warp 0 (row-oriented, warp sums); L packed lower.
-__device__ __forceinline__ void chol_solve_f32(const float* L, float* w, int s, int lane)
+// w <- L^{-T} L^{-1} w with L packed lower, by the whole block: 32-row diagonal
+// blocks are solved by warp 0 in registers (one shuffle per column), the rows
+// beyond them are updated by all threads.
+__device__ __forceinline__ void chol_solve_f32(const float* L, float* w, int s, int warp, int lane)
 {
-    for (int i = 0; i < s; ++i) {
-        const float* row = L + packed_row(i);
-        float acc = 0.f;
-        for (int c = lane; c < i; c += 32) acc += row[c] * w[c];
-        acc = warp_sum(acc);
-        if (lane == 0) w[i] = (w[i] - acc) / row[i];
-        __syncwarp();
+    for (int c0 = 0; c0 < s; c0 += 32) {
+        const int nb = min(32, s - c0);
+        if (warp == 0) {
+            float wi = lane < nb ? w[c0 + lane] : 0.f;
+            for (int c = 0; c < nb; ++c) {
+                if (lane == c) wi = wi / L[packed_row(c0 + c) + c0 + c];
+                const float wc = __shfl_sync(0xffffffffu, wi, c);
+                if (lane > c && lane < nb) wi -= L[packed_row(c0 + lane) + c0 + c] * wc;
+            }
+            if (lane < nb) w[c0 + lane] = wi;
+        }
+        __syncthreads();
+        for (int i = c0 + nb + threadIdx.x; i < s; i += blockDim.x) {
+            const float* row = L + packed_row(i) + c0;
+            float acc = 0.f;
+            for (int c = 0; c < nb; ++c) acc += row[c] * w[c0 + c];
+            w[i] -= acc;
+        }
+        __syncthreads();
     }
-    for (int i = s - 1; i >= 0; --i) {
-        float acc = 0.f;
-        for (int c = i + 1 + lane; c < s; c += 32) acc += L[packed_row(c) + i] * w[c];
-        acc = warp_sum(acc);
-        if (lane == 0) w[i] = (w[i] - acc) / L[packed_row(i) + i];
-        __syncwarp();
+    for (int c0 = ((s - 1) / 32) * 32; c0 >= 0; c0 -= 32) {
+        const int nb = min(32, s - c0);
+        if (warp == 0) {
+            float xi = lane < nb ? w[c0 + lane] : 0.f;
+            for (int c = nb - 1; c >= 0; --c) {
+                if (lane == c) xi = xi / L[packed_row(c0 + c) + c0 + c];
+                const float xc = __shfl_sync(0xffffffffu, xi, c);
+                if (lane < c) xi -= L[packed_row(c0 + c) + c0 + lane] * xc;
+            }
+            if (lane < nb) w[c0 + lane] = xi;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < c0; i += blockDim.x) {
+            float acc = 0.f;
+            for (int c = 0; c < nb; ++c) acc += L[packed_row(c0 + c) + i] * w[c0 + c];
+            w[i] -= acc;
+        }
+        __syncthreads();
     }
 }
 
@@ -239,7 +265,7 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
     double* x64 = b64 + sm2;
     double* red = x64 + sm2;                                            // 32 doubles
     float* w = reinterpret_cast<float*>(red + 32);                      // smax floats
-    float* L = a.fscratch ? a.fscratch + (size_t)blockIdx.x * packed_row(a.smax) : w + sm2;
+    float* L = a.fscratch ? a.fscratch + (size_t)blockIdx.x * ((size_t)a.smax * (a.smax + 1) / 2) : w + sm2;
     __shared__ int s_count;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -302,9 +328,9 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
             // x = solve(b) in FP32, then x += solve(b - G x) with FP64 residuals
             for (int x = threadIdx.x; x < s; x += blockDim.x) { w[x] = (float)b64[x]; x64[x] = 0.0; }
             __syncthreads();
+            double prev = 0.0;
             for (int itr = 0; itr <= OLS_REFINE_MAX; ++itr) {
-                if (warp == 0) chol_solve_f32(L, w, s, lane);
-                __syncthreads();
+                chol_solve_f32(L, w, s, warp, lane);
                 double dd = 0.0, xx = 0.0;
                 for (int x = threadIdx.x; x < s; x += blockDim.x) {
                     const double nx = x64[x] + (double)w[x];
@@ -314,8 +340,14 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
                 }
                 const double dmx = block_max(dd, red, lane, warp);
                 const double xmx = block_max(xx, red, lane, warp);
-                if (itr > 0 && dmx <= 4.0 * 2.220446049250313e-16 * xmx) { done = true; break; }
+                // converged: the correction is at the level of FP64 rounding of the
+                // residual, or it no longer shrinks (the residual is rounding noise)
+                if (itr > 0 && (dmx <= 1e-14 * xmx || (dmx > 0.5 * prev && dmx <= 1e-12 * xmx))) {
+                    done = true;
+                    break;
+                }
                 if (itr == OLS_REFINE_MAX) { done = dmx <= 1e-12 * xmx; break; }
+                prev = dmx;
                 // residual r_i = b_i - sum_c G[S_i, S_c] x_c (one warp per row)
                 for (int i = warp; i < s; i += 8) {
                     const double* grow = Gk + (size_t)idx[i] * a.pu;
@@ -564,6 +596,7 @@ int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
 int64_t run_ols(OlsArgs a, cudaStream_t s)
 {
     a.smax = std::max(1, (int)family_support_max(a, s));
+    if (a.smax > 46000) throw Error(UOI_ERR_UNSUPPORTED, "OLS support larger than 46000 columns");
     return launch_ols_mixed(a, s);
 }
 
