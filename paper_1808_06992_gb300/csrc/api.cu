@@ -218,10 +218,10 @@ void validate(const uoi_params* prm)
 // Moments for B weight vectors in the precision of the fit.
 void moments(int precision, const double* X, int64_t ldx, const double* Y, int64_t ldy,
              int64_t m, int64_t p, int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B,
-             double* G, double* Bm, cudaStream_t s)
+             double* G, double* Bm, cudaStream_t s, const float* X32 = nullptr)
 {
     if (precision == UOI_PREC_MIXED && gram_tc_available())
-        moments_tc(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, s);
+        moments_tc(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, s, X32);
     else
         moments_fp64(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, 0, s);
 }
@@ -232,12 +232,12 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                     const double* lam, int32_t q, double rho, double abs_tol, double rel_tol,
                     int32_t max_iter, int32_t warm, double* beta, int32_t* iters, uint8_t* conv,
                     uint64_t* family, cudaStream_t s, StageTimer* tm, int* marks,
-                    WsModel* ws = nullptr)
+                    WsModel* ws = nullptr, const float* X32 = nullptr)
 {
     int t0 = tm ? tm->mark() : 0;
     DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
     DevBuf nk(sizeof(double) * B, s);
-    moments(precision, Xd, ldx, Yd, ldy, m, p, r, w, nullptr, B, G.as<double>(), Bm.as<double>(), s);
+    moments(precision, Xd, ldx, Yd, ldy, m, p, r, w, nullptr, B, G.as<double>(), Bm.as<double>(), s, X32);
     if (w) {
         weight_sums(w, nullptr, m, B, nk.as<double>(), s);
     } else {
@@ -433,11 +433,18 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     WsModel* ws = prm->warm_start == UOI_WARM_LEARNED ? ws_for_path(prm->mlp_weights_path, s) : nullptr;
     const int32_t warm_used = prm->warm_start == UOI_WARM_LEARNED ? (ws ? UOI_WARM_LEARNED : UOI_WARM_PATH)
                                                                   : prm->warm_start;
+    // mixed form: one FP32 copy of X feeds every tensor-core moment pass
+    DevBuf X32;
+    if (mixed && gram_tc_available()) {
+        X32.alloc(sizeof(float) * (size_t)(m * ldx), s);
+        to_f32(Xd, ldx, m, p, X32.as<float>(), s);
+    }
     if (mixed)
         selection_admm<float>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                               lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                               prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, ws);
+                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, ws,
+                              X32.ptr ? X32.as<float>() : nullptr);
     else
         selection_admm<double>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                                lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
@@ -460,9 +467,9 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         const int32_t nu = union_columns(fam.as<uint64_t>(), q * r, p, ucols.as<int32_t>(), s);
         if (nu > 0) {
             moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), west.as<uint32_t>(),
-                            nullptr, B2, Gt.as<double>(), Bt.as<double>(), s);
+                            nullptr, B2, Gt.as<double>(), Bt.as<double>(), s, X32.as<float>());
             moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), nullptr,
-                            evm.as<uint8_t>(), B2, Ge.as<double>(), Be.as<double>(), s);
+                            evm.as<uint8_t>(), B2, Ge.as<double>(), Be.as<double>(), s, X32.as<float>());
         }
     } else {
         moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, west.as<uint32_t>(), nullptr, B2,

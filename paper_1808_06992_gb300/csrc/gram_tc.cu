@@ -242,8 +242,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // from which the diagonal correction is reduced in a fixed order.
 constexpr int SPLIT_COLS = 128;
 __global__ void __launch_bounds__(256)
-k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, int32_t pz_x,
-                  int32_t r, const int32_t* colmap, const int32_t* rowlist,
+k_split_transpose(const double* X, int64_t ldx, const float* X32, const double* Y, int64_t ldy,
+                  int32_t pz_x, int32_t r, const int32_t* colmap, const int32_t* rowlist,
                   const float* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
                   int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq)
 {
@@ -273,9 +273,11 @@ k_split_transpose(const double* X, int64_t ldx, const double* Y, int64_t ldy, in
             const int c = c0 + lane + 32 * j;
             float v = 0.f;
             if (row >= 0 && c < pz) {
-                const double x = c < pz_x ? X[row * ldx + (colmap ? colmap[c] : c)]
-                                          : Y[row * ldy + (c - pz_x)];
-                v = f64_to_f32_int(x) * sc;
+                const int64_t col = colmap && c < pz_x ? colmap[c] : c;
+                if (c < pz_x)
+                    v = (X32 ? X32[row * ldx + col] : f64_to_f32_int(X[row * ldx + col])) * sc;
+                else
+                    v = f64_to_f32_int(Y[row * ldy + (c - pz_x)]) * sc;
             }
             tile[tl][lane + 32 * j] = v;
         }
@@ -403,7 +405,7 @@ bool gram_tc_available()
 void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
                      int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
                      const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
-                     cudaStream_t s)
+                     cudaStream_t s, const float* X32)
 {
     if (!gram_tc_available()) throw Error(UOI_ERR_UNSUPPORTED, "tcgen05 Gram needs sm_103a");
     const int32_t pz = pz_x + (int32_t)r;
@@ -448,7 +450,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
         dim3 gs((unsigned)row_tiles, (unsigned)ceil_div(pz_pad, SPLIT_COLS), (unsigned)nb);
-        k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, Y, ldy, pz_x, (int32_t)r, colmap,
+        k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, X32, Y, ldy, pz_x, (int32_t)r, colmap,
                                              rows.as<int32_t>() + (size_t)b0 * m,
                                              scale.as<float>() + (size_t)b0 * m,
                                              nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
@@ -490,9 +492,26 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
 
 void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
                 int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
-                double* Bm, cudaStream_t s)
+                double* Bm, cudaStream_t s, const float* X32)
 {
-    moments_tc_cols(X, ldx, Y, ldy, m, p, r, (int32_t)p, nullptr, w, mask, B, G, Bm, s);
+    moments_tc_cols(X, ldx, Y, ldy, m, p, r, (int32_t)p, nullptr, w, mask, B, G, Bm, s, X32);
+}
+
+namespace {
+__global__ void k_to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out)
+{
+    const int64_t total = m * p;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        out[(t / p) * ldx + t % p] = f64_to_f32_int(X[(t / p) * ldx + t % p]);
+}
+}  // namespace
+
+void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cudaStream_t s)
+{
+    k_to_f32<<<(unsigned)std::min<int64_t>(ceil_div(m * p, 256), 152 * 64), 256, 0, s>>>(X, ldx, m, p, out);
+    UOI_CHECK_LAUNCH();
+    count_launch();
 }
 
 }  // namespace uoi

@@ -80,16 +80,19 @@ void check_finite(const double* X, int64_t ldx, int64_t m, int64_t cols, int32_t
 
 // Mixed form: split-bf16 tensor-core Gram (gram_tc.cu).
 bool gram_tc_available();
+// X32: optional FP32 copy of X (same leading dimension), read instead of X.
 void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
                 int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
-                double* Bm, cudaStream_t s);
+                double* Bm, cudaStream_t s, const float* X32 = nullptr);
+// out[i*ldx + j] = X[i*ldx + j] rounded to FP32, i < m, j < p.
+void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cudaStream_t s);
 
 // Tensor-core moments restricted to the pz_x X columns listed in colmap (written
 // into p_out x p_out / p_out x r outputs at the original feature indices).
 void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
                      int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
                      const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
-                     cudaStream_t s);
+                     cudaStream_t s, const float* X32 = nullptr);
 
 // ---- G3: factor (factor.cu) -------------------------------------------------------
 // A_k = G_k / nk[k] + rho I in T, lower Cholesky in place.  status->code set to
