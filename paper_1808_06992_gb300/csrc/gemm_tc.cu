@@ -16,8 +16,9 @@
 //   A = [A11 A21^T; A21 A22],  X = A11^{-1},  U = A21 X,  S = A22 - A21 U^T,
 //   Y = S^{-1},  M21 = -Y U,  M11 = X - U^T M21,  M12 = M21^T,
 // which is exact algebra (the block form of the Cholesky-based inverse) with
-// every product a large GEMM; blocks of order <= 256 use the CUDA-core
-// Cholesky / triangular inverse / product.  S stays SPD for SPD A.
+// every product a large GEMM; blocks of order <= 192 are inverted in shared
+// memory by Gauss-Jordan elimination (no pivoting: the pivots are the Schur
+// complements' diagonals, positive for SPD A).  S stays SPD for SPD A.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,7 +42,7 @@ constexpr int GT_SMEM = GT_STAGES * GT_STAGE + 1024;
 constexpr int GT_THREADS = 192;
 constexpr uint32_t GT_TMEM_COLS = 256;                 // A1[0] at 0, A1[1] at 64, A2 at 128
 constexpr int GT_CHUNK_STAGES = 4;                     // drain h.H every 128 k
-constexpr int64_t INV_BASE = 256;                      // CUDA-core inverse at or below this order
+constexpr int64_t INV_BASE = 192;                      // shared-memory inverse at or below this order
 
 struct GemmArgs {
     int32_t m, n, kst, MT, NT;
@@ -165,7 +166,6 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
         const int quad = warp & 3;
-        const int i = mt * GT_TM + quad * 32 + lane;
         const uint32_t lanes = (uint32_t)(quad * 32) << 16;
         float acc[64], cmp[64];
 #pragma unroll
@@ -203,22 +203,32 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         }
         __syncwarp();
         tc_fence_after();
-        const bool rowok = i < a.m && !abort_flag;
-        const int j0 = nt * GT_TN;
-        float* drow = a.D + (int64_t)g * a.gsd + (int64_t)i * a.ldd;
-        const float* crow = a.C ? a.C + (int64_t)g * a.gsc + (int64_t)i * a.ldc : nullptr;
+        // stage the warp's 32 x 64 results in shared memory (the operand ring is
+        // idle once every MMA is done), then write whole rows: coalesced
+        float* stage = reinterpret_cast<float*>(smem_raw + (sbase - smem_u32(smem_raw))) + quad * 32 * 65;
 #pragma unroll
         for (int cb = 0; cb < 2; ++cb) {
             float v2[32];
             tmem_ld32(tmem + lanes + (uint32_t)(128 + cb * 32), v2);   // whole warp
-            if (!rowok) continue;
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                const int j = j0 + cb * 32 + t;
-                if (j < a.n) {
-                    float r = a.alpha * (acc[cb * 32 + t] + v2[t]);
-                    if (crow) r += a.beta * crow[j];
-                    drow[j] = r;
+            for (int t = 0; t < 32; ++t) stage[lane * 65 + cb * 32 + t] = acc[cb * 32 + t] + v2[t];
+        }
+        __syncwarp();
+        if (!abort_flag) {
+            const int j0 = nt * GT_TN;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int ii = mt * GT_TM + quad * 32 + rr;
+                if (ii >= a.m) break;
+                float* drow = a.D + (int64_t)g * a.gsd + (int64_t)ii * a.ldd;
+                const float* crow = a.C ? a.C + (int64_t)g * a.gsc + (int64_t)ii * a.ldc : nullptr;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j0 + h * 32 + lane;
+                    if (j < a.n) {
+                        float r = a.alpha * stage[rr * 65 + h * 32 + lane];
+                        if (crow) r += a.beta * crow[j];
+                        drow[j] = r;
+                    }
                 }
             }
         }
@@ -288,19 +298,6 @@ __global__ void k_transpose_block(const float* src, int64_t lds, float* dst, int
     }
 }
 
-// Copy an n x n block between strided storages (per group).
-__global__ void k_copy_block(const float* src, int64_t lds, int64_t gss, float* dst, int64_t ldd,
-                             int64_t gsd, int32_t n)
-{
-    const int g = blockIdx.y;
-    const int64_t total = (int64_t)n * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / n, j = t % n;
-        dst[g * gsd + i * ldd + j] = src[g * gss + i * lds + j];
-    }
-}
-
 struct Pieces {
     DevBuf buf;
     CUtensorMap map;
@@ -351,19 +348,79 @@ void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, fl
     count_launch();
 }
 
-// CUDA-core inverse of an n x n SPD block (strided), via a contiguous copy.
+// In-place Gauss-Jordan inverse of one SPD block per CTA, in shared memory
+// (n <= INV_BASE = 192).  1024 threads; thread (ty, tx) owns the elements
+// (ty + 32u, tx + 32v), held in registers across each elimination step.  A
+// pivot <= 0 sets status UOI_ERR_NOT_PD (where = group).
+constexpr int GJ_R = (int)(INV_BASE + 31) / 32;      // 6 rows / columns per thread
+
+__global__ void __launch_bounds__(1024) k_spd_inverse_smem(const float* A, int64_t lda, int64_t gsa,
+                                                           float* M, int64_t ldm, int64_t gsm, int n,
+                                                           DevStatus* st)
+{
+    extern __shared__ float sm[];
+    float* T = sm;                          // n x n
+    float* col = T + n * n;                 // column k before the step
+    float* row = col + n;                   // row k / pivot
+    const int g = blockIdx.x;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const float* a = A + (int64_t)g * gsa;
+    float v[GJ_R][GJ_R];
+#pragma unroll
+    for (int u = 0; u < GJ_R; ++u)
+#pragma unroll
+        for (int w = 0; w < GJ_R; ++w) {
+            const int i = ty + 32 * u, j = tx + 32 * w;
+            v[u][w] = (i < n && j < n) ? a[(int64_t)i * lda + j] : 0.f;
+            if (i < n && j < n) T[i * n + j] = v[u][w];
+        }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const float piv = T[k * n + k];
+        if (!(piv > 0.f)) {
+            if (threadIdx.x == 0) dev_fail(st, UOI_ERR_NOT_PD, g);
+            return;                         // same decision in every thread
+        }
+        const float inv = 1.f / piv;
+        if (threadIdx.x < n) {
+            col[threadIdx.x] = T[threadIdx.x * n + k];
+            row[threadIdx.x] = T[k * n + threadIdx.x] * inv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < GJ_R; ++u) {
+            const int i = ty + 32 * u;
+            if (i >= n) break;
+            const float ci = col[i];
+#pragma unroll
+            for (int w = 0; w < GJ_R; ++w) {
+                const int j = tx + 32 * w;
+                if (j >= n) break;
+                float x;
+                if (i == k) x = j == k ? inv : row[j];
+                else x = j == k ? -ci * inv : v[u][w] - ci * row[j];
+                v[u][w] = x;
+                T[i * n + j] = x;
+            }
+        }
+        __syncthreads();
+    }
+    float* mo = M + (int64_t)g * gsm;
+#pragma unroll
+    for (int u = 0; u < GJ_R; ++u)
+#pragma unroll
+        for (int w = 0; w < GJ_R; ++w) {
+            const int i = ty + 32 * u, j = tx + 32 * w;
+            if (i < n && j < n) mo[(int64_t)i * ldm + j] = v[u][w];
+        }
+}
+
 void inv_base(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM, int64_t gsM,
               int64_t n, int32_t G, DevStatus* st, cudaStream_t s)
 {
-    DevBuf T(sizeof(float) * (size_t)(G * n * n), s), Li(sizeof(float) * (size_t)(G * n * n), s);
-    DevBuf Mi(sizeof(float) * (size_t)(G * n * n), s);
-    const unsigned gx = (unsigned)std::min<int64_t>(ceil_div(n * n, 256), 1024);
-    k_copy_block<<<dim3(gx, (unsigned)G), 256, 0, s>>>(A, ldA, gsA, T.as<float>(), n, n * n, (int32_t)n);
-    UOI_CHECK_LAUNCH();
-    count_launch();
-    cholesky_inplace<float>(T.as<float>(), n, G, st, s);
-    spd_inverse_from_factor<float>(T.as<float>(), n, G, Li.as<float>(), Mi.as<float>(), s);
-    k_copy_block<<<dim3(gx, (unsigned)G), 256, 0, s>>>(Mi.as<float>(), n, n * n, Mout, ldM, gsM, (int32_t)n);
+    const size_t smem = sizeof(float) * (size_t)(n * n + 2 * n);
+    UOI_CUDA(cudaFuncSetAttribute(k_spd_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spd_inverse_smem<<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
     UOI_CHECK_LAUNCH();
     count_launch();
 }
