@@ -263,23 +263,51 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, const double* 
         rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.f;
     }
     __syncthreads();
-    // warp w reads rows w, w+8, ..., columns c0 + lane + 32j
-    for (int i = 0; i < 8; ++i) {
-        const int tl = warp + 8 * i;
-        const int64_t row = rowoff[tl];
-        const float sc = rowsc[tl];
+    // warp w reads rows w, w+8, ...: with the FP32 copy one 16-byte load per lane
+    // covers the block's 128 columns of a row; all loads are issued before the
+    // shared-memory stores
+    if (X32 && c0 + SPLIT_COLS <= pz_x && ((ldx & 3) == 0) && !colmap) {
+        float4 q[8];
 #pragma unroll
-        for (int j = 0; j < SPLIT_COLS / 32; ++j) {
-            const int c = c0 + lane + 32 * j;
-            float v = 0.f;
-            if (row >= 0 && c < pz) {
-                const int64_t col = colmap && c < pz_x ? colmap[c] : c;
-                if (c < pz_x)
-                    v = (X32 ? X32[row * ldx + col] : f64_to_f32_int(X[row * ldx + col])) * sc;
-                else
-                    v = f64_to_f32_int(Y[row * ldy + (c - pz_x)]) * sc;
+        for (int i = 0; i < 8; ++i) {
+            const int64_t row = rowoff[warp + 8 * i];
+            q[i] = row >= 0 ? __ldg(reinterpret_cast<const float4*>(X32 + row * ldx + c0) + lane)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int tl = warp + 8 * i;
+            const float sc = rowsc[tl];
+            tile[tl][4 * lane + 0] = q[i].x * sc;
+            tile[tl][4 * lane + 1] = q[i].y * sc;
+            tile[tl][4 * lane + 2] = q[i].z * sc;
+            tile[tl][4 * lane + 3] = q[i].w * sc;
+        }
+    } else {
+        float q[8][SPLIT_COLS / 32];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t row = rowoff[warp + 8 * i];
+#pragma unroll
+            for (int j = 0; j < SPLIT_COLS / 32; ++j) {
+                const int c = c0 + lane + 32 * j;
+                float v = 0.f;
+                if (row >= 0 && c < pz) {
+                    const int64_t col = colmap && c < pz_x ? colmap[c] : c;
+                    if (c < pz_x)
+                        v = X32 ? __ldg(X32 + row * ldx + col) : f64_to_f32_int(__ldg(X + row * ldx + col));
+                    else
+                        v = f64_to_f32_int(__ldg(Y + row * ldy + (c - pz_x)));
+                }
+                q[i][j] = v;
             }
-            tile[tl][lane + 32 * j] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int tl = warp + 8 * i;
+            const float sc = rowsc[tl];
+#pragma unroll
+            for (int j = 0; j < SPLIT_COLS / 32; ++j) tile[tl][lane + 32 * j] = q[i][j] * sc;
         }
     }
     __syncthreads();
