@@ -8,8 +8,9 @@
 // hi'hi + hi'lo + lo'hi on bf16 tensor cores with FP32 accumulation in TMEM.
 // The tensor cores' FP32 accumulation loses about a third of an ulp per K=16
 // step (measured), so the accumulator is drained every 128 sample rows (24
-// steps, <= 5e-7 relative) into compensated FP32 pairs (TwoSum) held in the
-// epilogue warps' registers, and the sum is written once in FP64 at the end.
+// steps, <= 5e-7 relative) into FP32 running sums held in the epilogue warps'
+// registers (the rounding of those few hundred additions is ~1e-7 relative),
+// and the sum is written once in FP64 at the end.
 // The lo'lo term (up to 2^-16 relative per product) is zero-mean off the
 // diagonal; on the diagonal it is a positive bias and is added exactly
 // (k_diag_lo).  Relative error of the Gram: ~5e-7 of the largest diagonal entry.
@@ -17,12 +18,13 @@
 // Two kernels:
 //  * k_split_transpose: gather rows (with weights), split, and write the two
 //    bf16 pieces transposed (features x rows, rows contiguous = K-major).
-//  * k_gram_tc: one CTA per (128 x 128 tile of the lower triangle, item).
-//    Warp 0 issues TMA loads of K-major SWIZZLE_128B tiles into a 3-stage
-//    ring; warp 1 issues tcgen05.mma (M=128, N=128, K=16, bf16 -> f32) into one
-//    of two TMEM accumulators; warps 2-9 drain the other accumulator
-//    (tcgen05.ld) into their TwoSum registers.  Every wait is bounded (about
-//    one second) and reports UOI_ERR_TIMEOUT.
+//  * k_gram_tc: one CTA per (128 x 256 tile of the lower triangle, item).
+//    Warp 0 issues TMA loads of K-major SWIZZLE_128B tiles into a 2-stage
+//    ring; warp 1 issues tcgen05.mma (M=128, N=256, K=16, bf16 -> f32: the wide
+//    N keeps the shared-memory operand traffic below what the tensor core
+//    consumes) into one of two TMEM accumulators; warps 2-9 drain the other
+//    accumulator (tcgen05.ld) into their registers.  Every wait is bounded
+//    (about one second) and reports UOI_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -40,15 +42,15 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;                 // tile rows (UMMA M)
-constexpr int TN = 128;                 // tile cols (UMMA N)
+constexpr int TN = 256;                 // tile cols (UMMA N): 12 KB of operands per 128 cycles
 constexpr int TK = 64;                  // rows of the sample per stage (128 B of bf16)
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int CHUNK_STAGES = 2;         // 128 sample rows per FP32 accumulation chunk
 constexpr int A_BYTES = TM * TK * 2;    // 16 KB per piece
-constexpr int B_BYTES = TN * TK * 2;    // 16 KB per piece
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 64 KB
+constexpr int B_BYTES = TN * TK * 2;    // 32 KB per piece
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
-constexpr uint32_t TMEM_COLS = 256;     // two 128-column FP32 accumulators
+constexpr uint32_t TMEM_COLS = 512;     // two 256-column FP32 accumulators
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA, 8 epilogue warps
 
@@ -171,47 +173,41 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         int dummy = 0;
         mbar_wait(&done_bar, 0, &dummy);
     } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> compensated FP32 pairs ----------------
+        // ---------------- epilogue: TMEM -> FP32 running sums ----------------
         const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
-        const int half = (warp - 2) >> 2;                // columns 64*half .. +63
+        const int half = (warp - 2) >> 2;                // columns 128*half .. +127
         const int iz = ti * TM + quad * 32 + lane;       // Z row of this thread
-        float acc[64], cmp[64];
+        float acc[128];
 #pragma unroll
-        for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
+        for (int t = 0; t < 128; ++t) acc[t] = 0.f;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
-            if (!mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag)) {
+            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag);
+            if (!__all_sync(0xffffffffu, okw)) {               // warp-uniform exit
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
             }
             tc_fence_after();
 #pragma unroll
-            for (int cb = 0; cb < 2; ++cb) {
-                float v[32];
+            for (int cb = 0; cb < 8; ++cb) {
+                float v[16];
                 const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) +
-                                       (uint32_t)(b * TN + half * 64 + cb * 32);
-                tmem_ld32(taddr, v);
+                                       (uint32_t)(b * TN + half * 128 + cb * 16);
+                tmem_ld16(taddr, v);
 #pragma unroll
-                for (int t = 0; t < 32; ++t) {           // TwoSum: acc + cmp carries the sum
-                    const float x = v[t], sacc = acc[cb * 32 + t];
-                    const float s = sacc + x;
-                    const float bb = s - sacc;
-                    const float err = (sacc - (s - bb)) + (x - bb);
-                    acc[cb * 32 + t] = s;
-                    cmp[cb * 32 + t] += err;
-                }
+                for (int t = 0; t < 16; ++t) acc[cb * 16 + t] += v[t];
             }
             tc_fence_before();
             mbar_arrive(&acce_bar[b]);
         }
         if (iz < a.pz && !abort_flag) {
-            const int jz0 = tj * TN + half * 64;
+            const int jz0 = tj * TN + half * 128;
 #pragma unroll
-            for (int t = 0; t < 64; ++t) {
+            for (int t = 0; t < 128; ++t) {
                 const int jz = jz0 + t;
                 if (jz > iz || jz >= a.pz_x) continue;           // lower triangle, X columns
-                const double val = (double)acc[t] + (double)cmp[t];
+                const double val = (double)acc[t];
                 const int jo = a.colmap ? a.colmap[jz] : jz;
                 if (iz < a.pz_x) {
                     const int io = a.colmap ? a.colmap[iz] : iz;
