@@ -126,10 +126,13 @@ def fit_kwargs(w, args):
                 warm_start=native.WARM_PATH if args.warm == "path" else native.WARM_NONE)
 
 
-def traffic_per_launch(kernel):
+def traffic_per_launch(kernel, applies=True):
     """DRAM bytes per launch from the committed ncu capture, if the kernel's source
-    still matches the hash recorded with it (else None)."""
+    still matches the hash recorded with it and the run is the workload the figure
+    was scaled to (else None)."""
     import hashlib
+    if not applies:
+        return None
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = {"k_gram_tc": "gram_tc.cu", "k_stream_gemm": "admm.cu", "k_xupdate_tc": "xupdate_tc.cu"}[kernel]
     try:
@@ -304,6 +307,9 @@ def main():
     bf16 = peaks.get("bf16_tflops")
     hbm = peaks.get("hbm_gbs")
     fp64_peak = 1.25                                     # nominal GB300 FP64 (no measured figure)
+    # the committed traffic figures are scaled to the default workload and form
+    default_run = (not overrides and args.workload == 2 and args.precision == "mixed"
+                   and args.warm == "none")
     kernels = []
     ms_g = sum(d["ms_gram_tc"] for d in diags)
     if ms_g > 0:
@@ -313,7 +319,7 @@ def main():
         peak = (bf16 / 3.0) if bf16 else 1900.0 / 3.0
         kernels.append({"kernel": "k_gram_tc (tensor-core Gram, split bf16 x3)", "bound": "tensor",
                         "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                        "traffic": traffic_per_launch("k_gram_tc"), "launches_per_step": n / args.steps,
+                        "traffic": traffic_per_launch("k_gram_tc", default_run), "launches_per_step": n / args.steps,
                         "ms_per_step": ms_g / args.steps,
                         "peak_source": ("measured bf16 burst / 3 (three bf16 products per "
                                         "FP32-accurate multiply-add)" if bf16 else "fallback 1.9 PF / 3"),
@@ -331,14 +337,14 @@ def main():
             hpeak = hbm or 6800.0
             kernels.append({"kernel": "k_xupdate_tc (ADMM x-update on tcgen05, fused z/u/norm epilogue)",
                             "bound": "hbm", "achieved": gbs, "peak": hpeak, "unit": "GB/s",
-                            "frac": gbs / hpeak, "traffic": traffic_per_launch("k_xupdate_tc"),
+                            "frac": gbs / hpeak, "traffic": traffic_per_launch("k_xupdate_tc", default_run),
                             "launches_per_step": n / args.steps, "ms_per_step": ms_x / args.steps,
                             "tflops_algorithmic": ach,
                             "peak_source": "measured HBM copy" if hbm else "fallback 6.8 TB/s"})
         else:
             kernels.append({"kernel": "k_stream_gemm (FP64 ADMM x-update + fused epilogue)", "bound": "alu",
                             "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                            "traffic": traffic_per_launch("k_stream_gemm"), "launches_per_step": n / args.steps,
+                            "traffic": traffic_per_launch("k_stream_gemm", False), "launches_per_step": n / args.steps,
                             "ms_per_step": ms_x / args.steps,
                             "hbm_gbs_algorithmic": gbs,
                             "hbm_frac_algorithmic": gbs / hbm if hbm else None,
