@@ -12,6 +12,7 @@
 // Singular supports (a Cholesky pivot <= 1e-12 max diag) are refit with a
 // 1e-10 max-diag ridge and flagged.
 #include <algorithm>
+#include <vector>
 
 #include "kernels.h"
 
@@ -19,7 +20,8 @@ namespace uoi {
 
 namespace {
 
-constexpr int OLS_SMEM_MAX = 160;   // supports up to this size factor in shared memory
+constexpr int OLS_SMEM_MAX = 160;   // supports up to this size factor in shared memory (FP64 path)
+constexpr int OLS_SMALL = 128;      // mixed path: supports up to this size form the small class
 
 struct OlsArgs {
     const double* Gt; const double* Bt;      // B2 x p x p, B2 x p x r
@@ -46,6 +48,8 @@ struct OlsArgs {
     int32_t* fb_list;                        // mixed pass: solves left to the FP64 kernel
     int32_t* fb_count;
     float* fscratch;                         // mixed pass: global packed factor (per CTA), or null
+    const int32_t* je_list;                  // mixed loss pass: the (j*r + e) it covers (else all)
+    int32_t n_je;
 };
 
 __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
@@ -273,9 +277,15 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
     for (int64_t t = blockIdx.x; t < a.solves; t += gridDim.x) {
         int k, j, e;
         if (a.jstar) { k = (int)(t / a.r); e = (int)(t % a.r); j = a.jstar[k]; }
-        else { k = (int)(t / ((int64_t)a.q * a.r)); const int64_t rem = t % ((int64_t)a.q * a.r);
+        else if (a.je_list) {
+            k = (int)(t / a.n_je);
+            const int32_t je = a.je_list[t % a.n_je];
+            j = (int)(je / a.r); e = (int)(je % a.r);
+        } else { k = (int)(t / ((int64_t)a.q * a.r)); const int64_t rem = t % ((int64_t)a.q * a.r);
                j = (int)(rem / a.r); e = (int)(rem % a.r);
                if (a.dup && a.dup[rem] != j) continue; }
+        // the solve's index in the numbering of k_ols (for the FP64 hand-over)
+        const int64_t tg = a.jstar ? t : ((int64_t)k * a.q + j) * a.r + e;
         const uint64_t* bits = a.family + ((int64_t)j * a.r + e) * a.W;
         if (warp == 0) {
             int cnt = 0;
@@ -361,7 +371,7 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
             }
         }
         if (s > 0 && !done) {
-            if (threadIdx.x == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)t;
+            if (threadIdx.x == 0) a.fb_list[atomicAdd(a.fb_count, 1)] = (int32_t)tg;
             __syncthreads();
             continue;
         }
@@ -458,6 +468,16 @@ __global__ void k_fill_duplicates(const int32_t* dup, int32_t B2, int32_t q, int
         const int64_t src = (k * q + j0) * r + e;
         losses[t] = losses[src];
         if (singular) singular[t] = singular[src];
+    }
+}
+
+__global__ void k_support_sizes(const uint64_t* fam, int64_t count, int W, int32_t* out)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int w = 0; w < W; ++w) c += __popcll(fam[t * W + w]);
+        out[t] = c;
     }
 }
 
@@ -574,7 +594,8 @@ int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
         fscratch.alloc(lbytes * (size_t)grid, s);
         a.fscratch = fscratch.as<float>();
     }
-    DevBuf fbl(sizeof(int32_t) * (size_t)a.solves, s), fbc(sizeof(int32_t), s);
+    DevBuf fbl(sizeof(int32_t) * (size_t)std::max<int64_t>(a.solves, (int64_t)a.B2 * a.q * a.r), s);
+    DevBuf fbc(sizeof(int32_t), s);
     UOI_CUDA(cudaMemsetAsync(fbc.ptr, 0, sizeof(int32_t), s));
     a.fb_list = fbl.as<int32_t>();
     a.fb_count = fbc.as<int32_t>();
@@ -733,7 +754,41 @@ int64_t ols_losses(const double* Gt, const double* Bt, const double* Ge, const d
     k_family_dedup<<<gd, 256, 0, s>>>(family, q, r, a.W, dup.as<int32_t>());
     UOI_CHECK_LAUNCH();
     a.dup = dup.as<int32_t>();
-    const int64_t nfb = run_ols(a, s);
+    // Size classes: small supports run with little shared memory per CTA (many
+    // CTAs per SM hide the latency of their short dependent steps); large ones
+    // with room for their factor.  Only first occurrences of a support are listed.
+    const int64_t qr = (int64_t)q * r;
+    DevBuf sizes(sizeof(int32_t) * (size_t)qr, s);
+    k_support_sizes<<<(unsigned)std::min<int64_t>(ceil_div(qr, 256), 1024), 256, 0, s>>>(
+        family, qr, a.W, sizes.as<int32_t>());
+    UOI_CHECK_LAUNCH();
+    count_launch();
+    std::vector<int32_t> hsz((size_t)qr), hdup((size_t)qr);
+    UOI_CUDA(cudaMemcpyAsync(hsz.data(), sizes.ptr, sizeof(int32_t) * qr, cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaMemcpyAsync(hdup.data(), dup.ptr, sizeof(int32_t) * qr, cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> small_je, large_je;
+    int32_t smax_small = 1, smax_large = 1;
+    for (int64_t t = 0; t < qr; ++t) {
+        if (hdup[t] != (int32_t)(t / r)) continue;
+        if (hsz[t] <= OLS_SMALL) { small_je.push_back((int32_t)t); smax_small = std::max(smax_small, hsz[t]); }
+        else { large_je.push_back((int32_t)t); smax_large = std::max(smax_large, hsz[t]); }
+    }
+    if (std::max(smax_small, smax_large) > 46000)
+        throw Error(UOI_ERR_UNSUPPORTED, "OLS support larger than 46000 columns");
+    int64_t nfb = 0;
+    for (int cls = 0; cls < 2; ++cls) {
+        const std::vector<int32_t>& lst = cls == 0 ? small_je : large_je;
+        if (lst.empty()) continue;
+        DevBuf jl(sizeof(int32_t) * lst.size(), s);
+        UOI_CUDA(cudaMemcpyAsync(jl.ptr, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, s));
+        OlsArgs b = a;
+        b.je_list = jl.as<int32_t>();
+        b.n_je = (int32_t)lst.size();
+        b.solves = (int64_t)B2 * b.n_je;
+        b.smax = cls == 0 ? smax_small : smax_large;
+        nfb += launch_ols_mixed(b, s);
+    }
     const unsigned gf = (unsigned)std::min<int64_t>(ceil_div(a.solves, 256), 4096);
     k_fill_duplicates<<<gf, 256, 0, s>>>(dup.as<int32_t>(), B2, q, r, losses, singular);
     UOI_CHECK_LAUNCH();
