@@ -348,20 +348,21 @@ void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, fl
     count_launch();
 }
 
-// In-place Gauss-Jordan inverse of one SPD block per CTA, in shared memory
-// (n <= INV_BASE = 192).  1024 threads; thread (ty, tx) owns the elements
-// (ty + 32u, tx + 32v), held in registers across each elimination step.  A
-// pivot <= 0 sets status UOI_ERR_NOT_PD (where = group).
-constexpr int GJ_R = (int)(INV_BASE + 31) / 32;      // 6 rows / columns per thread
-
+// In-place Gauss-Jordan inverse of one SPD block per CTA (n <= INV_BASE = 192).
+// 1024 threads; thread (ty, tx) owns the elements (ty + 32u, tx + 32v), held in
+// registers.  A pivot <= 0 sets status UOI_ERR_NOT_PD (where = group).
+// GJ_R rows / columns per thread: 2 (n <= 64), 4 (n <= 128) or 6 (n <= 192).
+template <int GJ_R>
 __global__ void __launch_bounds__(1024) k_spd_inverse_smem(const float* A, int64_t lda, int64_t gsa,
                                                            float* M, int64_t ldm, int64_t gsm, int n,
                                                            DevStatus* st)
 {
+    // The matrix lives in the threads' registers; step k needs only row k and
+    // column k (before the step), which their owners publish into shared
+    // memory, double-buffered so one barrier per step suffices.
     extern __shared__ float sm[];
-    float* T = sm;                          // n x n
-    float* col = T + n * n;                 // column k before the step
-    float* row = col + n;                   // row k / pivot
+    float* colb = sm;                       // [2][n] column k
+    float* rowb = sm + 2 * n;               // [2][n] row k
     const int g = blockIdx.x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const float* a = A + (int64_t)g * gsa;
@@ -372,35 +373,66 @@ __global__ void __launch_bounds__(1024) k_spd_inverse_smem(const float* A, int64
         for (int w = 0; w < GJ_R; ++w) {
             const int i = ty + 32 * u, j = tx + 32 * w;
             v[u][w] = (i < n && j < n) ? a[(int64_t)i * lda + j] : 0.f;
-            if (i < n && j < n) T[i * n + j] = v[u][w];
+            if (i == 0 && j < n) rowb[j] = v[u][w];
+            if (j == 0 && i < n) colb[i] = v[u][w];
         }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        const float piv = T[k * n + k];
+        const float* col = colb + (k & 1) * n;
+        const float* row = rowb + (k & 1) * n;
+        float* ncol = colb + ((k + 1) & 1) * n;
+        float* nrow = rowb + ((k + 1) & 1) * n;
+        const float piv = col[k];
         if (!(piv > 0.f)) {
             if (threadIdx.x == 0) dev_fail(st, UOI_ERR_NOT_PD, g);
             return;                         // same decision in every thread
         }
         const float inv = 1.f / piv;
-        if (threadIdx.x < n) {
-            col[threadIdx.x] = T[threadIdx.x * n + k];
-            row[threadIdx.x] = T[k * n + threadIdx.x] * inv;
+        // r = row k / pivot (with 1 / pivot at column k), c = column k; then
+        // every element: (column k reset to 0) - c_i r_j, and row k := r
+        float r[GJ_R], c[GJ_R];
+#pragma unroll
+        for (int w = 0; w < GJ_R; ++w) {
+            const int j = tx + 32 * w;
+            r[w] = j < n ? (j == k ? inv : row[j] * inv) : 0.f;
         }
-        __syncthreads();
 #pragma unroll
         for (int u = 0; u < GJ_R; ++u) {
             const int i = ty + 32 * u;
-            if (i >= n) break;
-            const float ci = col[i];
+            c[u] = i < n ? col[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < GJ_R; ++u) {
+            const bool own_row = ty + 32 * u == k;
 #pragma unroll
             for (int w = 0; w < GJ_R; ++w) {
-                const int j = tx + 32 * w;
-                if (j >= n) break;
-                float x;
-                if (i == k) x = j == k ? inv : row[j];
-                else x = j == k ? -ci * inv : v[u][w] - ci * row[j];
-                v[u][w] = x;
-                T[i * n + j] = x;
+                const float base = (tx + 32 * w == k) ? 0.f : v[u][w];
+                const float x = fmaf(-c[u], r[w], base);
+                v[u][w] = own_row ? r[w] : x;
+            }
+        }
+        // publish row and column k + 1 for the next step
+        const int k1 = k + 1;
+        if (ty == (k1 & 31)) {                       // the warp holding row k + 1
+#pragma unroll
+            for (int u = 0; u < GJ_R; ++u) {
+                if (ty + 32 * u != k1) continue;
+#pragma unroll
+                for (int w = 0; w < GJ_R; ++w) {
+                    const int j = tx + 32 * w;
+                    if (j < n) nrow[j] = v[u][w];
+                }
+            }
+        }
+        if (tx == (k1 & 31)) {                       // the lane holding column k + 1
+#pragma unroll
+            for (int w = 0; w < GJ_R; ++w) {
+                if (tx + 32 * w != k1) continue;
+#pragma unroll
+                for (int u = 0; u < GJ_R; ++u) {
+                    const int i = ty + 32 * u;
+                    if (i < n) ncol[i] = v[u][w];
+                }
             }
         }
         __syncthreads();
@@ -418,9 +450,13 @@ __global__ void __launch_bounds__(1024) k_spd_inverse_smem(const float* A, int64
 void inv_base(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM, int64_t gsM,
               int64_t n, int32_t G, DevStatus* st, cudaStream_t s)
 {
-    const size_t smem = sizeof(float) * (size_t)(n * n + 2 * n);
-    UOI_CUDA(cudaFuncSetAttribute(k_spd_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_spd_inverse_smem<<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
+    const size_t smem = sizeof(float) * (size_t)(4 * n);
+    if (n <= 64)
+        k_spd_inverse_smem<2><<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
+    else if (n <= 128)
+        k_spd_inverse_smem<4><<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
+    else
+        k_spd_inverse_smem<6><<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
     UOI_CHECK_LAUNCH();
     count_launch();
 }
