@@ -138,6 +138,24 @@ int uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p,
                   const uoi_params* prm, double* beta_out, uint64_t* family_out,
                   uoi_diag* diag);
 
+/* Many independent UoI_LASSO problems of uneven n and p in one call (the
+ * "batched" workload: Alg. 1 applied to each problem separately).  Problem i is
+ * X[i] (n[i] x p[i], row-major), y[i] (n[i]) -> beta_out[i] (p[i]); pointers host
+ * or device, per problem.  One parameter set for all; prm->lambdas must be NULL
+ * (each problem gets its own grid from its lambda_max) and problem i draws its
+ * bootstraps with problem_id = prm->problem_id + i, so its result equals
+ * uoi_lasso_fit on that problem with that problem_id.  The problems run on
+ * `streams` worker streams of the calling thread's device (0 = 4), largest n*p^2
+ * first, each worker fitting one problem at a time; the call returns once all
+ * are done.  status_out (count, nullable) receives each problem's status and
+ * diags (count, nullable) each problem's diagnostics.  Returns UOI_OK, or
+ * UOI_OK_WITH_WARNINGS if any problem warned, or the first failing problem's
+ * error (the others still ran and their outputs are valid). */
+int uoi_lasso_fit_batch(int32_t count, const double* const* X, const double* const* y,
+                        const int64_t* n, const int64_t* p, const uoi_params* prm,
+                        double* const* beta_out, int32_t* status_out, uoi_diag* diags,
+                        int32_t streams);
+
 /* UoI_VAR(order) (Alg. 2).  series: N x p, time ascending (row t = X_t).
  * Only order 1 is supported (else UOI_ERR_UNSUPPORTED).  The lagged design
  * pairs the response X_{t+1} with the regressor X_t (Eq. 7-8, rows in

@@ -585,7 +585,7 @@ void launch_resident(const AdmmDev<T>& d, int32_t* chain_next, cudaStream_t s)
     const int p4 = (d.p + 3) & ~3;
     const size_t smem = sizeof(T) * ((size_t)p4 * A * 32 + (size_t)8 * SW * A * 32);
     auto kern = k_admm_resident<T, A, SW>;
-    UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_dynamic_smem((const void*)kern);
     const int nchains = d.warm ? d.r : d.r * d.q;
     const int per_cta = 8 * SW;
     int ctas = (int)ceil_div(nchains, per_cta);

@@ -7,17 +7,21 @@
 //   -> training/evaluation moments -> OLS + held-out loss per (k, j, e) (G6)
 //   -> argmin per bootstrap, chosen OLS, bagging (G7).
 // Inputs may live on the host or the device; host data is copied in once.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.h"
 
 namespace uoi {
 
-int64_t g_launches = 0;
+thread_local int64_t g_launches = 0;
 
 void DevBuf::alloc(size_t n, cudaStream_t s)
 {
@@ -37,13 +41,24 @@ void DevBuf::release()
 
 thread_local std::string g_last_error;
 
+void allow_max_dynamic_smem(const void* kern)
+{
+    int dev = 0, optin = 0;
+    UOI_CUDA(cudaGetDevice(&dev));
+    UOI_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    UOI_CUDA(cudaFuncGetAttributes(&fa, kern));
+    UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes));
+}
+
 namespace {
 struct PendingTimes {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     KernelTotals tot;
     cudaEvent_t open = nullptr;
 };
-PendingTimes g_kt[TK_COUNT];
+thread_local PendingTimes g_kt[TK_COUNT];   // per host thread, like the fit using it
 }  // namespace
 
 void ktimer_reset()
@@ -101,6 +116,8 @@ void ensure_pool()
     int dev = 0;
     UOI_CUDA(cudaGetDevice(&dev));
     static bool done[64] = {};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     if (dev < 64 && !done[dev]) {
         cudaMemPool_t pool;
         UOI_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
@@ -344,7 +361,7 @@ struct WsCache {
     std::string path;
     WsModel* model = nullptr;
 };
-WsCache g_ws_cache;
+thread_local WsCache g_ws_cache;          // per host thread (batch workers load their own)
 
 WsModel* ws_for_path(const char* path, cudaStream_t s)
 {
@@ -622,6 +639,67 @@ int uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p, const 
         std::memset(&tr, 0, sizeof(tr));
         tr.family = family_out;
         return fit_core(X, p, y, 1, n, p, 1, prm, beta_out, family_out ? &tr : nullptr, diag);
+    });
+}
+
+int uoi_lasso_fit_batch(int32_t count, const double* const* X, const double* const* y, const int64_t* n,
+                        const int64_t* p, const uoi_params* prm, double* const* beta_out, int32_t* status_out,
+                        uoi_diag* diags, int32_t streams)
+{
+    return guarded([&] {
+        if (count < 0) throw uoi::Error(UOI_ERR_INVALID_ARG, "count must be >= 0");
+        if (count == 0) return (int)UOI_OK;
+        if (!X || !y || !n || !p || !prm || !beta_out)
+            throw uoi::Error(UOI_ERR_INVALID_ARG, "NULL array argument");
+        if (prm->lambdas) throw uoi::Error(UOI_ERR_INVALID_ARG, "a batch takes each problem's own lambda grid");
+        uoi::validate(prm);
+        int dev = 0;
+        UOI_CUDA(cudaGetDevice(&dev));
+        // largest problems first (n p^2 orders the Gram and the inverse)
+        std::vector<int32_t> order((size_t)count);
+        for (int32_t i = 0; i < count; ++i) order[(size_t)i] = i;
+        std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return (double)n[a] * p[a] * p[a] > (double)n[b] * p[b] * p[b];
+        });
+        const int nw = std::max(1, std::min<int32_t>(streams > 0 ? streams : 4, count));
+        std::vector<int32_t> st((size_t)count, UOI_OK);
+        std::vector<std::string> detail((size_t)count);
+        std::atomic<int32_t> next(0);
+        auto worker = [&]() {
+            cudaSetDevice(dev);
+            cudaStream_t ws = nullptr;
+            if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+                for (int32_t t; (t = next.fetch_add(1)) < count;) st[(size_t)order[(size_t)t]] = UOI_ERR_CUDA;
+                return;
+            }
+            for (int32_t t; (t = next.fetch_add(1)) < count;) {
+                const int32_t i = order[(size_t)t];
+                uoi_params q = *prm;
+                q.stream = ws;
+                q.problem_id = prm->problem_id + (uint64_t)i;
+                st[(size_t)i] = uoi::guarded([&] {
+                    return uoi::fit_core(X[i], p[i], y[i], 1, n[i], p[i], 1, &q, beta_out[i], nullptr,
+                                         diags ? &diags[i] : nullptr);
+                });
+                if (st[(size_t)i] < 0) detail[(size_t)i] = uoi::g_last_error;
+            }
+            cudaStreamSynchronize(ws);
+            cudaStreamDestroy(ws);
+        };
+        std::vector<std::thread> pool;
+        for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+        for (auto& th : pool) th.join();
+        int ret = UOI_OK;
+        int32_t first_bad = -1;
+        for (int32_t i = 0; i < count; ++i) {
+            if (status_out) status_out[i] = st[(size_t)i];
+            if (st[(size_t)i] < 0 && ret >= 0) { ret = st[(size_t)i]; first_bad = i; }
+            else if (st[(size_t)i] == UOI_OK_WITH_WARNINGS && ret == UOI_OK) ret = UOI_OK_WITH_WARNINGS;
+        }
+        if (ret < 0)
+            throw uoi::Error(ret, "problem " + std::to_string(first_bad) + " of the batch failed: " +
+                                      detail[(size_t)first_bad]);
+        return ret;
     });
 }
 

@@ -30,8 +30,9 @@ struct Error : std::runtime_error {
 
 #define UOI_CHECK_LAUNCH() UOI_CUDA(cudaGetLastError())
 
-// Count of kernels this library launched (reported in uoi_diag.gpu_launches).
-extern int64_t g_launches;
+// Count of kernels this library launched on the calling host thread (reported in
+// uoi_diag.gpu_launches; one fit runs on one thread).
+extern thread_local int64_t g_launches;
 inline void count_launch(int64_t n = 1) { g_launches += n; }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

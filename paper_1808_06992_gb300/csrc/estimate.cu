@@ -563,7 +563,7 @@ void launch_ols_fp64(OlsArgs a, cudaStream_t s)
         scratch.alloc(sizeof(double) * (size_t)grid * a.smax * a.smax, s);
         a.scratch = scratch.as<double>();
     }
-    UOI_CUDA(cudaFuncSetAttribute(k_ols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_dynamic_smem((const void*)k_ols);
     if (a.solves > 0) {
         k_ols<<<grid, 256, smem, s>>>(a);
         UOI_CHECK_LAUNCH();
@@ -583,7 +583,7 @@ int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
     const size_t cap = 227 * 1024 - 64;
     const bool in_smem = base + lbytes <= cap;
     const size_t smem = base + (in_smem ? lbytes : 0);
-    UOI_CUDA(cudaFuncSetAttribute(k_ols_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_dynamic_smem((const void*)k_ols_mixed);
     int dev = 0, nsm = 0, per = 0;
     UOI_CUDA(cudaGetDevice(&dev));
     UOI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -49,6 +49,12 @@ struct DevBuf {
     template <typename T> T* as() const { return reinterpret_cast<T*>(ptr); }
 };
 
+// Allow `kern` the largest dynamic shared memory the current device opts in to (its
+// static shared memory deducted).  Kernels launched with a size that varies by call
+// use this, so that every caller sets the same value and concurrent callers on
+// other streams cannot undercut each other.
+void allow_max_dynamic_smem(const void* kern);
+
 // ---- G0: bootstrap indices (bootstrap.cu) -----------------------------------
 // w[k*m + row] = multiplicity of the row in selection bootstrap k, k < B.
 void selection_weights(int64_t m, int64_t block_len, PhiloxKey key, int32_t B, uint32_t* w,

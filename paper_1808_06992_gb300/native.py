@@ -75,6 +75,7 @@ def lib():
         L.uoi_params_default.argtypes = [C.POINTER(UoiParams)]
         L.uoi_lasso_fit.argtypes = [vp, vp, i64, i64, C.POINTER(UoiParams), vp, vp, C.POINTER(UoiDiag)]
         L.uoi_var_fit.argtypes = [vp, i64, i64, i32, C.POINTER(UoiParams), vp, vp, C.POINTER(UoiDiag)]
+        L.uoi_lasso_fit_batch.argtypes = [i32, vp, vp, vp, vp, C.POINTER(UoiParams), vp, vp, vp, i32]
         L.uoi_fit_traced.argtypes = [vp, i64, vp, i64, i64, i64, i64, C.POINTER(UoiParams), vp,
                                      C.POINTER(UoiTrace), C.POINTER(UoiDiag)]
         L.lasso_admm_batch.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d, i32, i32,
@@ -101,7 +102,7 @@ def lib():
     return _lib
 
 
-EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_var_fit", "uoi_fit_traced",
+EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_lasso_fit_batch", "uoi_var_fit", "uoi_fit_traced",
             "lasso_admm_batch", "lasso_admm_batch_noalloc", "uoi_weighted_moments",
             "uoi_ws_param_count", "uoi_ws_create", "uoi_ws_load", "uoi_ws_save", "uoi_ws_free",
             "uoi_ws_set_params", "uoi_ws_get_params", "uoi_ws_forward", "uoi_ws_loss_grad",
@@ -216,6 +217,32 @@ def uoi_fit_traced(X, Y, trace=True, **kw):
     _check(st)
     out.update(beta=beta, status=st, diag=diag.as_dict())
     return out
+
+
+def uoi_lasso_fit_batch(Xs, ys, streams=0, **kw):
+    """Independent UoI_LASSO problems (uneven n, p) in one call; returns a list of
+    dicts (beta, status, diag) in input order.  Problem i uses problem_id + i."""
+    count = len(Xs)
+    Xs = [_prep(X, np.float64) for X in Xs]
+    ys = [_prep(y, np.float64) for y in ys]
+    prm, keep = make_params(**kw)
+    betas = [_empty(X, (X.shape[1],), np.float64) for X in Xs]
+    xa = (C.c_void_p * count)(*[_ptr(X) for X in Xs])
+    ya = (C.c_void_p * count)(*[_ptr(y) for y in ys])
+    na = (C.c_int64 * count)(*[X.shape[0] for X in Xs])
+    pa = (C.c_int64 * count)(*[X.shape[1] for X in Xs])
+    ba = (C.c_void_p * count)(*[_ptr(b) for b in betas])
+    sta = (C.c_int32 * count)()
+    diags = (UoiDiag * count)()
+    for dg in diags:
+        dg.struct_size = C.sizeof(UoiDiag)
+    st = lib().uoi_lasso_fit_batch(count, C.cast(xa, C.c_void_p), C.cast(ya, C.c_void_p),
+                                   C.cast(na, C.c_void_p), C.cast(pa, C.c_void_p), C.byref(prm),
+                                   C.cast(ba, C.c_void_p), C.cast(sta, C.c_void_p),
+                                   C.cast(diags, C.c_void_p), streams)
+    del keep
+    _check(st)
+    return [dict(beta=betas[i], status=int(sta[i]), diag=diags[i].as_dict()) for i in range(count)]
 
 
 def uoi_lasso_fit(X, y, family=False, **kw):
