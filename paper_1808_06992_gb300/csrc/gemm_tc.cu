@@ -4,13 +4,14 @@
 //
 // GEMM: D_g = alpha * A_g B_g^T + beta * C_g with A_g (m x k) and B_g (n x k)
 // given as three bf16 pieces each (v = h + m + l, residue <= 2^-24 |v|); the
-// six products h.H, h.M, m.H, h.L, m.M, l.H are summed as in the x-update:
-// h.H in a double-buffered TMEM accumulator drained every 128 k into
-// compensated FP32 pairs, the five small products in a second accumulator.
-// Tiles 128 x 64, k = 32 per stage (64-byte swizzle), 3-stage TMA ring, two
-// CTAs per SM.  Operands are stored as contiguous 128 x 32 (A) or 64 x 32 (B)
-// blocks, [g][row tile][k block][piece][rows][32], so every stage is one TMA
-// copy per operand.
+// six products h.H, h.M, m.H, h.L, m.M, l.H all accumulate into a
+// double-buffered TMEM accumulator (2 x 256 columns) that 8 epilogue warps drain
+// every 64 k (24 accumulation steps, the same truncation budget as the Gram)
+// into FP32 running sums.  Tiles 128 x 256 (the wide N keeps shared-memory
+// operand traffic below the tensor rate), k = 32 per stage (64-byte swizzle),
+// 2-stage TMA ring of 72 KB, one CTA per SM.  Operands are stored as contiguous
+// 128 x 32 (A) or 256 x 32 (B) blocks, [g][row tile][k block][piece][rows][32],
+// so every stage is one TMA copy per operand.
 //
 // Inverse: block (Schur complement) recursion on the SPD matrix
 //   A = [A11 A21^T; A21 A22],  X = A11^{-1},  U = A21 X,  S = A22 - A21 U^T,
@@ -32,16 +33,19 @@ namespace {
 using namespace tc;
 
 constexpr int GT_TM = 128;                             // A rows per tile
-constexpr int GT_TN = 64;                              // B rows per tile
+constexpr int GT_TN = 256;                             // B rows per tile (UMMA N)
 constexpr int GT_TK = 32;
-constexpr int GT_STAGES = 3;
+constexpr int GT_STAGES = 2;
 constexpr int GT_A_BYTES = GT_TM * GT_TK * 2;          // 8 KB per piece
-constexpr int GT_B_BYTES = GT_TN * GT_TK * 2;          // 4 KB per piece
-constexpr int GT_STAGE = 3 * GT_A_BYTES + 3 * GT_B_BYTES;   // 36 KB
+constexpr int GT_B_BYTES = GT_TN * GT_TK * 2;          // 16 KB per piece
+constexpr int GT_STAGE = 3 * GT_A_BYTES + 3 * GT_B_BYTES;   // 72 KB
 constexpr int GT_SMEM = GT_STAGES * GT_STAGE + 1024;
-constexpr int GT_THREADS = 192;
-constexpr uint32_t GT_TMEM_COLS = 256;                 // A1[0] at 0, A1[1] at 64, A2 at 128
-constexpr int GT_CHUNK_STAGES = 4;                     // drain h.H every 128 k
+constexpr int GT_EPI_WARPS = 8;
+constexpr int GT_THREADS = 64 + 32 * GT_EPI_WARPS;     // producer, MMA, 8 epilogue warps
+constexpr uint32_t GT_TMEM_COLS = 512;                 // two 256-column accumulators
+constexpr int GT_CHUNK_STAGES = 2;                     // drain every 64 k
+constexpr int GT_STG = 132;                            // epilogue staging row (floats)
+static_assert(GT_EPI_WARPS * 32 * GT_STG * 4 <= GT_STAGES * GT_STAGE, "staging fits the ring");
 constexpr int64_t INV_BASE = 192;                      // shared-memory inverse at or below this order
 
 struct GemmArgs {
@@ -61,7 +65,7 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16&
     l = __float2bfloat16_rn(r2);
 }
 
-__global__ void __launch_bounds__(GT_THREADS, 2)
+__global__ void __launch_bounds__(GT_THREADS, 1)
 k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -76,7 +80,7 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < GT_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 32 * GT_EPI_WARPS); }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -113,10 +117,8 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             for (int s_ = max(0, a.kst - GT_STAGES); s_ < a.kst; ++s_)
                 mbar_wait(&full_bar[s_ % GT_STAGES], (s_ / GT_STAGES) & 1, &abort_flag);
     } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer: all six products into accumulator b ----------------
         const uint32_t idesc = idesc_bf16(GT_TM, GT_TN);
-        const uint32_t d2 = tmem + 128u;
-        bool first2 = true;
         int s_ = 0;
         for (int c = 0; c < nchunks && !abort_flag; ++c) {
             const int b = c & 1;
@@ -126,9 +128,9 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 break;
             }
             tc_fence_after();
-            const uint32_t d1 = tmem + (uint32_t)(b * 64);
+            const uint32_t d = tmem + (uint32_t)(b * GT_TN);
             const int send = min(a.kst, (c + 1) * GT_CHUNK_STAGES);
-            bool first1 = true;
+            bool first = true;
             for (; s_ < send; ++s_) {
                 const int s = s_ % GT_STAGES;
                 if (!mbar_wait(&full_bar[s], (s_ / GT_STAGES) & 1, &abort_flag)) {
@@ -146,14 +148,14 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 #pragma unroll
                 for (int ks = 0; ks < GT_TK / 16; ++ks) {
                     const uint64_t adv = (uint64_t)(ks * 32 >> 4);
-                    mma_bf16(d1, Ah + adv, Bh + adv, idesc, first1 ? 0u : 1u);
-                    mma_bf16(d2, Ah + adv, Bm + adv, idesc, first2 ? 0u : 1u);
-                    mma_bf16(d2, Am + adv, Bh + adv, idesc, 1u);
-                    mma_bf16(d2, Ah + adv, Bl + adv, idesc, 1u);
-                    mma_bf16(d2, Am + adv, Bm + adv, idesc, 1u);
-                    mma_bf16(d2, Al + adv, Bh + adv, idesc, 1u);
-                    first1 = false;
-                    first2 = false;
+                    // small products first, h.H last (adds the largest term to the smallest sum)
+                    mma_bf16(d, Ah + adv, Bm + adv, idesc, first ? 0u : 1u);
+                    mma_bf16(d, Am + adv, Bh + adv, idesc, 1u);
+                    mma_bf16(d, Ah + adv, Bl + adv, idesc, 1u);
+                    mma_bf16(d, Am + adv, Bm + adv, idesc, 1u);
+                    mma_bf16(d, Al + adv, Bh + adv, idesc, 1u);
+                    mma_bf16(d, Ah + adv, Bh + adv, idesc, 1u);
+                    first = false;
                 }
                 mma_commit(&empty_bar[s]);
             }
@@ -164,12 +166,12 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         int dummy = 0;
         mbar_wait(&done_bar, 0, &dummy);
     } else if (warp >= 2) {
-        // ---------------- epilogue ----------------
-        const int quad = warp & 3;
-        const uint32_t lanes = (uint32_t)(quad * 32) << 16;
-        float acc[64], cmp[64];
+        // ---------------- epilogue: TMEM -> FP32 running sums -> D ----------------
+        const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
+        const int half = (warp - 2) >> 2;                // columns 128*half .. +127
+        float acc[128];
 #pragma unroll
-        for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
+        for (int t = 0; t < 128; ++t) acc[t] = 0.f;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
             const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag);
@@ -180,54 +182,43 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             }
             tc_fence_after();
 #pragma unroll
-            for (int cb = 0; cb < 2; ++cb) {
-                float v[32];
-                tmem_ld32(tmem + lanes + (uint32_t)(b * 64 + cb * 32), v);
+            for (int cb = 0; cb < 8; ++cb) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * GT_TN + half * 128 + cb * 16), v);
 #pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    const float x = v[t], sa = acc[cb * 32 + t];
-                    const float sum = sa + x;
-                    const float bv = sum - sa;
-                    cmp[cb * 32 + t] += (sa - (sum - bv)) + (x - bv);
-                    acc[cb * 32 + t] = sum;
-                }
+                for (int t = 0; t < 16; ++t) acc[cb * 16 + t] += v[t];
             }
             tc_fence_before();
             mbar_arrive(&acce_bar[b]);
         }
-#pragma unroll
-        for (int t = 0; t < 64; ++t) acc[t] += cmp[t];
         {
             int dummy = 0;
-            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);
+            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);   // the ring is idle from here
         }
         __syncwarp();
-        tc_fence_after();
-        // stage the warp's 32 x 64 results in shared memory (the operand ring is
-        // idle once every MMA is done), then write whole rows: coalesced
-        float* stage = reinterpret_cast<float*>(smem_raw + (sbase - smem_u32(smem_raw))) + quad * 32 * 65;
+        // stage the warp's 32 x 128 block in shared memory, then write whole rows
+        float* stage = reinterpret_cast<float*>(smem_raw + (sbase - smem_u32(smem_raw))) +
+                       (warp - 2) * 32 * GT_STG;
 #pragma unroll
-        for (int cb = 0; cb < 2; ++cb) {
-            float v2[32];
-            tmem_ld32(tmem + lanes + (uint32_t)(128 + cb * 32), v2);   // whole warp
-#pragma unroll
-            for (int t = 0; t < 32; ++t) stage[lane * 65 + cb * 32 + t] = acc[cb * 32 + t] + v2[t];
-        }
+        for (int c4 = 0; c4 < 32; ++c4)
+            *reinterpret_cast<float4*>(stage + lane * GT_STG + 4 * c4) =
+                make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
         __syncwarp();
         if (!abort_flag) {
-            const int j0 = nt * GT_TN;
+            const int j = nt * GT_TN + half * 128 + 4 * lane;
             for (int rr = 0; rr < 32; ++rr) {
                 const int ii = mt * GT_TM + quad * 32 + rr;
                 if (ii >= a.m) break;
+                const float4 v = *reinterpret_cast<const float4*>(stage + rr * GT_STG + 4 * lane);
+                float r4[4] = { v.x, v.y, v.z, v.w };
                 float* drow = a.D + (int64_t)g * a.gsd + (int64_t)ii * a.ldd;
                 const float* crow = a.C ? a.C + (int64_t)g * a.gsc + (int64_t)ii * a.ldc : nullptr;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = j0 + h * 32 + lane;
-                    if (j < a.n) {
-                        float r = a.alpha * stage[rr * 65 + h * 32 + lane];
-                        if (crow) r += a.beta * crow[j];
-                        drow[j] = r;
+                for (int t = 0; t < 4; ++t) {
+                    if (j + t < a.n) {
+                        float r = a.alpha * r4[t];
+                        if (crow) r += a.beta * crow[j + t];
+                        drow[j + t] = r;
                     }
                 }
             }
