@@ -292,3 +292,36 @@ def test_mixed_tensor_core_inverse_vs_oracle():
     amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
     assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
     assert np.abs(gpu["iters"].astype(int) - ref["iters"]).max() <= max(3, int(0.1 * ref["iters"].max()))
+
+
+def test_mixed_tensor_core_xupdate_many_chain_tiles():
+    # r = 40 responses x 4 lambdas = 160 chains per bootstrap group: the
+    # tensor-core x-update runs 3 chain tiles of <= 64 per group (the VAR layout)
+    d = synth.lasso_problem(1500, 300, 20, seed=41, sigma=0.5, toeplitz_rho=0.5)
+    g = np.random.Generator(np.random.PCG64(42))
+    B = g.standard_normal((300, 40)) * (g.random((300, 40)) < 0.05)
+    Y = d.X @ B + 0.5 * g.standard_normal((1500, 40))
+    n = d.X.shape[0]
+    w = np.stack([oracle.selection_weights(n, 0, 0, 0, k) for k in range(2)])
+    lam = oracle.lambda_grid(oracle.lambda_max(d.X, Y), 4)
+    ref = oracle.lasso_admm_batch(d.X, Y, w, lam, warm_start=0)
+    gpu = native.lasso_admm_batch(d.X, Y, w, lam, warm_start=0, precision=native.PREC_MIXED)
+    assert gpu["conv"].all()
+    worst = max(rel_l2(gpu["beta"][idx], ref["beta"][idx]) for idx in np.ndindex(*ref["beta"].shape[:3]))
+    assert worst <= 1e-4, worst
+    thr = lam[None, :, None, None]
+    amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
+    assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
+
+
+def test_large_supports_factor_outside_shared_memory():
+    # Two selection bootstraps and a small lambda_min leave supports of ~390
+    # features: beyond the shared-memory factor of the refined OLS (~330), so the
+    # factor lives in global scratch.  Plain form: losses and the fit as the oracle.
+    d = synth.lasso_problem(4000, 400, 60, seed=43, sigma=0.5)
+    kw = dict(B1=2, B2=2, q=5, lambda_min_ratio=1e-4)
+    ref = oracle.uoi_lasso_fit(d.X, d.y, **kw)
+    gpu = native.uoi_fit_traced(d.X, d.y, precision=native.PREC_FP64, **kw)
+    fam = bits_to_bool(gpu["family"], 400)[:, 0, :]
+    assert fam.sum(axis=1).max() > 330
+    compare_fit(ref, gpu, d.X, d.y.reshape(-1, 1), **kw)
