@@ -231,99 +231,83 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // Gather rows with positive weight, scale by sqrt(w), split into bf16 hi/lo and
 // write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].  Values
 // are taken to FP32 first (relative error 2^-23 after the scaling, below the
-// 2^-17 residue of the two-piece split).  A block covers 64 sample rows x 128
-// columns: each warp reads 1 KB row segments, then writes 128-byte runs of
-// paired bf16 along the rows of each column.  It also writes the FP32 sum of
-// lo^2 of each column over its 64 rows (losq[(item*row_tiles + tile)*pz_x + col]),
-// from which the diagonal correction is reduced in a fixed order.
-constexpr int SPLIT_COLS = 128;
+// 2^-17 residue of the two-piece split).  A block covers 128 sample rows x 32
+// columns: each warp reads 16 row segments of 128 B (all loads issued before
+// any shared-memory store) into a column-major tile whose odd row length keeps
+// both phases free of bank conflicts, then writes 128-byte runs of paired bf16
+// along the rows of each column.  It also writes the FP32 sum of lo^2 of each
+// column over each 64 rows (losq[(item*row_tiles + tile)*pz_x + col]), from
+// which the diagonal correction is reduced in a fixed order.
+constexpr int SPLIT_ROWS = 128;
+constexpr int SPLIT_COLS = 32;
 __global__ void __launch_bounds__(256)
 k_split_transpose(const double* X, int64_t ldx, const float* X32, const double* Y, int64_t ldy,
                   int32_t pz_x, int32_t r, const int32_t* colmap, const int32_t* rowlist,
                   const float* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
                   int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq)
 {
-    __shared__ float tile[64][SPLIT_COLS + 1];
-    __shared__ int64_t rowoff[64];
-    __shared__ float rowsc[64];
+    __shared__ float tile[SPLIT_COLS][SPLIT_ROWS + 1];      // [column][row]
+    __shared__ int64_t rowoff[SPLIT_ROWS];
+    __shared__ float rowsc[SPLIT_ROWS];
     const int item = blockIdx.z;
-    const int tile_r = blockIdx.x;
-    const int64_t t0 = (int64_t)tile_r * 64;
+    const int64_t t0 = (int64_t)blockIdx.x * SPLIT_ROWS;
     const int c0 = blockIdx.y * SPLIT_COLS;
     const int nr = nrows[item];
     const int pz = pz_x + r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 64) {
+    if (threadIdx.x < SPLIT_ROWS) {
         const int64_t t = t0 + threadIdx.x;
         rowoff[threadIdx.x] = t < nr ? (int64_t)rowlist[(int64_t)item * m + t] : -1;
         rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.f;
     }
     __syncthreads();
-    // warp w reads rows w, w+8, ...: with the FP32 copy one 16-byte load per lane
-    // covers the block's 128 columns of a row; all loads are issued before the
-    // shared-memory stores
-    if (X32 && c0 + SPLIT_COLS <= pz_x && ((ldx & 3) == 0) && !colmap) {
-        float4 q[8];
+    // read: warp w takes rows w, w + 8, ...; lane = column
+    {
+        const int c = c0 + lane;
+        const int64_t col = colmap && c < pz_x ? colmap[c] : c;
+        float q[SPLIT_ROWS / 8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < SPLIT_ROWS / 8; ++i) {
             const int64_t row = rowoff[warp + 8 * i];
-            q[i] = row >= 0 ? __ldg(reinterpret_cast<const float4*>(X32 + row * ldx + c0) + lane)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int tl = warp + 8 * i;
-            const float sc = rowsc[tl];
-            tile[tl][4 * lane + 0] = q[i].x * sc;
-            tile[tl][4 * lane + 1] = q[i].y * sc;
-            tile[tl][4 * lane + 2] = q[i].z * sc;
-            tile[tl][4 * lane + 3] = q[i].w * sc;
-        }
-    } else {
-        float q[8][SPLIT_COLS / 32];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t row = rowoff[warp + 8 * i];
-#pragma unroll
-            for (int j = 0; j < SPLIT_COLS / 32; ++j) {
-                const int c = c0 + lane + 32 * j;
-                float v = 0.f;
-                if (row >= 0 && c < pz) {
-                    const int64_t col = colmap && c < pz_x ? colmap[c] : c;
-                    if (c < pz_x)
-                        v = X32 ? __ldg(X32 + row * ldx + col) : f64_to_f32_int(__ldg(X + row * ldx + col));
-                    else
-                        v = f64_to_f32_int(__ldg(Y + row * ldy + (c - pz_x)));
-                }
-                q[i][j] = v;
+            float v = 0.f;
+            if (row >= 0 && c < pz) {
+                if (c < pz_x)
+                    v = X32 ? __ldg(X32 + row * ldx + col) : f64_to_f32_int(__ldg(X + row * ldx + col));
+                else
+                    v = f64_to_f32_int(__ldg(Y + row * ldy + (c - pz_x)));
             }
+            q[i] = v;
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < SPLIT_ROWS / 8; ++i) {
             const int tl = warp + 8 * i;
-            const float sc = rowsc[tl];
-#pragma unroll
-            for (int j = 0; j < SPLIT_COLS / 32; ++j) tile[tl][lane + 32 * j] = q[i][j] * sc;
+            tile[lane][tl] = q[i] * rowsc[tl];
         }
     }
     __syncthreads();
-    // warp w writes columns c0 + w + 8j; lane covers rows 2*lane, 2*lane + 1
+    // write: warp w takes columns w, w + 8, w + 16, w + 24; lane covers rows
+    // 2*lane, 2*lane + 1 of each half of the 128 rows
+#pragma unroll
     for (int j = 0; j < SPLIT_COLS / 8; ++j) {
         const int cl = warp + 8 * j;
         const int cc = c0 + cl;
         if (cc >= pz_pad) break;
-        const float v0 = tile[2 * lane][cl], v1 = tile[2 * lane + 1][cl];
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-        const float r0 = v0 - __bfloat162float(h0), r1 = v1 - __bfloat162float(h1);   // exact
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(r0), l1 = __float2bfloat16_rn(r1);
-        const int64_t base_hi = (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0 + 2 * lane;
-        const int64_t base_lo = (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0 + 2 * lane;
-        *reinterpret_cast<__nv_bfloat162*>(out + base_hi) = __halves2bfloat162(h0, h1);
-        *reinterpret_cast<__nv_bfloat162*>(out + base_lo) = __halves2bfloat162(l0, l1);
-        if (cc < pz_x) {
-            const float f0 = __bfloat162float(l0), f1 = __bfloat162float(l1);
-            const float sq = warp_sum(f0 * f0 + f1 * f1);
-            if (lane == 0) losq[((int64_t)item * row_tiles + tile_r) * pz_x + cc] = sq;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int r0 = hh * 64 + 2 * lane;
+            const float v0 = tile[cl][r0], v1 = tile[cl][r0 + 1];
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+            const float e0 = v0 - __bfloat162float(h0), e1 = v1 - __bfloat162float(h1);   // exact
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(e0), l1 = __float2bfloat16_rn(e1);
+            const int64_t base_hi = (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0 + r0;
+            const int64_t base_lo = (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0 + r0;
+            *reinterpret_cast<__nv_bfloat162*>(out + base_hi) = __halves2bfloat162(h0, h1);
+            *reinterpret_cast<__nv_bfloat162*>(out + base_lo) = __halves2bfloat162(l0, l1);
+            if (cc < pz_x) {
+                const float f0 = __bfloat162float(l0), f1 = __bfloat162float(l1);
+                const float sq = warp_sum(f0 * f0 + f1 * f1);
+                if (lane == 0) losq[((int64_t)item * row_tiles + (t0 / 64) + hh) * pz_x + cc] = sq;
+            }
         }
     }
 }
@@ -461,7 +445,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     UOI_CUDA(cudaStreamSynchronize(s));
     int32_t max_rows = 1;
     for (int32_t v : nr) max_rows = std::max(max_rows, v);
-    const int64_t n_pad = ceil_div(max_rows, TK) * TK;        // K extent actually used
+    const int64_t n_pad = ceil_div(max_rows, 128) * 128;      // K extent (whole split blocks)
     const int32_t row_tiles = (int32_t)(n_pad / 64);
     // items per pass bounded by the size of the split copies (<= 8 GB)
     const size_t per_item = (size_t)2 * pz_pad * n_pad * sizeof(__nv_bfloat16);
@@ -473,7 +457,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
-        dim3 gs((unsigned)row_tiles, (unsigned)ceil_div(pz_pad, SPLIT_COLS), (unsigned)nb);
+        dim3 gs((unsigned)(n_pad / SPLIT_ROWS), (unsigned)ceil_div(pz_pad, SPLIT_COLS), (unsigned)nb);
         k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, X32, Y, ldy, pz_x, (int32_t)r, colmap,
                                              rows.as<int32_t>() + (size_t)b0 * m,
                                              scale.as<float>() + (size_t)b0 * m,
