@@ -19,7 +19,7 @@
 //  * k_split_transpose: gather rows (with weights), split, and write the two
 //    bf16 pieces transposed (features x rows, rows contiguous = K-major).
 //  * k_gram_tc: one CTA per (128 x 256 tile of the lower triangle, item).
-//    Warp 0 issues TMA loads of K-major SWIZZLE_128B tiles into a 2-stage
+//    Warp 0 issues TMA loads of K-major SWIZZLE_64B tiles into a 4-stage
 //    ring; warp 1 issues tcgen05.mma (M=128, N=256, K=16, bf16 -> f32: the wide
 //    N keeps the shared-memory operand traffic below what the tensor core
 //    consumes) into one of two TMEM accumulators; warps 2-9 drain the other
@@ -43,12 +43,12 @@ using namespace tc;
 
 constexpr int TM = 128;                 // tile rows (UMMA M)
 constexpr int TN = 256;                 // tile cols (UMMA N): 12 KB of operands per 128 cycles
-constexpr int TK = 64;                  // rows of the sample per stage (128 B of bf16)
-constexpr int STAGES = 2;
-constexpr int CHUNK_STAGES = 2;         // 128 sample rows per FP32 accumulation chunk
-constexpr int A_BYTES = TM * TK * 2;    // 16 KB per piece
-constexpr int B_BYTES = TN * TK * 2;    // 32 KB per piece
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB
+constexpr int TK = 32;                  // rows of the sample per stage (64 B of bf16, 64-byte swizzle)
+constexpr int STAGES = 4;
+constexpr int CHUNK_STAGES = 4;         // 128 sample rows per FP32 accumulation chunk
+constexpr int A_BYTES = TM * TK * 2;    // 8 KB per piece
+constexpr int B_BYTES = TN * TK * 2;    // 16 KB per piece
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;     // two 256-column FP32 accumulators
 constexpr int EPI_WARPS = 8;
@@ -153,9 +153,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 }
                 tc_fence_after();
                 const uint32_t st = sbase + s * STAGE_BYTES;
-                const uint64_t ah = smem_desc_sw128(st), al = smem_desc_sw128(st + A_BYTES);
-                const uint64_t bh = smem_desc_sw128(st + 2 * A_BYTES);
-                const uint64_t bl = smem_desc_sw128(st + 2 * A_BYTES + B_BYTES);
+                const uint64_t ah = smem_desc_sw64(st), al = smem_desc_sw64(st + A_BYTES);
+                const uint64_t bh = smem_desc_sw64(st + 2 * A_BYTES);
+                const uint64_t bl = smem_desc_sw64(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
                 for (int ks = 0; ks < TK / 16; ++ks) {
                     const uint64_t adv = (uint64_t)(ks * 32 >> 4);   // 16 bf16 = 32 B along K
@@ -464,8 +464,8 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                                              nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
                                              zt.as<__nv_bfloat16>(), losq.as<float>());
         UOI_CHECK_LAUNCH();
-        const CUtensorMap mA = tc::make_map_bf16_k64(zt.ptr, n_pad, pz_pad, 2 * nb, TM);
-        const CUtensorMap mB = tc::make_map_bf16_k64(zt.ptr, n_pad, pz_pad, 2 * nb, TN);
+        const CUtensorMap mA = tc::make_map_bf16_k32(zt.ptr, n_pad, pz_pad, 2 * nb, TM);
+        const CUtensorMap mB = tc::make_map_bf16_k32(zt.ptr, n_pad, pz_pad, 2 * nb, TN);
         GramTcArgs a;
         a.n_pad = n_pad; a.pz_pad = pz_pad; a.pz = pz; a.pz_x = pz_x; a.r = (int32_t)r;
         a.p_out = (int32_t)p_out; a.ntiles = ntiles; a.tiles = tl.as<int32_t>();
