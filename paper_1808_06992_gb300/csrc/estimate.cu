@@ -194,14 +194,15 @@ __device__ __forceinline__ int packed_row(int i) { return (i * (i + 1)) >> 1; }
 // w <- L^{-T} L^{-1} w with L packed lower, by the whole block: 32-row diagonal
 // blocks are solved by warp 0 in registers (one shuffle per column), the rows
 // beyond them are updated by all threads.
-__device__ __forceinline__ void chol_solve_f32(const float* L, float* w, int s, int warp, int lane)
+__device__ __forceinline__ void chol_solve_f32(const float* L, const float* dinv, float* w, int s, int warp,
+                                               int lane)
 {
     for (int c0 = 0; c0 < s; c0 += 32) {
         const int nb = min(32, s - c0);
         if (warp == 0) {
             float wi = lane < nb ? w[c0 + lane] : 0.f;
             for (int c = 0; c < nb; ++c) {
-                if (lane == c) wi = wi / L[packed_row(c0 + c) + c0 + c];
+                if (lane == c) wi *= dinv[c0 + c];
                 const float wc = __shfl_sync(0xffffffffu, wi, c);
                 if (lane > c && lane < nb) wi -= L[packed_row(c0 + lane) + c0 + c] * wc;
             }
@@ -221,7 +222,7 @@ __device__ __forceinline__ void chol_solve_f32(const float* L, float* w, int s, 
         if (warp == 0) {
             float xi = lane < nb ? w[c0 + lane] : 0.f;
             for (int c = nb - 1; c >= 0; --c) {
-                if (lane == c) xi = xi / L[packed_row(c0 + c) + c0 + c];
+                if (lane == c) xi *= dinv[c0 + c];
                 const float xc = __shfl_sync(0xffffffffu, xi, c);
                 if (lane < c) xi -= L[packed_row(c0 + c) + c0 + lane] * xc;
             }
@@ -260,7 +261,10 @@ __device__ __forceinline__ double block_sum(double v, double* red, int lane, int
     return t;
 }
 
-__global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
+// PB: panel width of the blocked Cholesky (register tiles of 4 x 4 x PB);
+// MINB: CTAs per SM the registers must allow (small supports want many).
+template <int PB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ols_mixed(OlsArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int sm2 = (a.smax + 1) & ~1;
@@ -269,7 +273,8 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
     double* x64 = b64 + sm2;
     double* red = x64 + sm2;                                            // 32 doubles
     float* w = reinterpret_cast<float*>(red + 32);                      // smax floats
-    float* L = a.fscratch ? a.fscratch + (size_t)blockIdx.x * ((size_t)a.smax * (a.smax + 1) / 2) : w + sm2;
+    float* dinv = w + sm2;                                              // 1 / diagonal of the factor
+    float* L = a.fscratch ? a.fscratch + (size_t)blockIdx.x * ((size_t)a.smax * (a.smax + 1) / 2) : dinv + sm2;
     __shared__ int s_count;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -317,19 +322,61 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
         for (int x = threadIdx.x; x < s; x += blockDim.x) b64[x] = Bk[(size_t)idx[x] * a.r + e];
         const double dmax = block_max(dm, red, lane, warp);
         const float thr = OLS_F32_PIVOT * (float)dmax;
-        // right-looking Cholesky, one column per step (2 barriers)
+        // blocked right-looking Cholesky: panels of PB columns factored column by
+        // column, then one rank-PB update of the trailing triangle in 4 x 4
+        // register tiles (64 x 64 blocks of 16 x 16 threads)
         bool ok = true;
-        for (int c = 0; c < s; ++c) {
-            const float d = L[packed_row(c) + c];
-            if (!(d > thr)) { ok = false; break; }          // same decision in every thread
-            const float lcc = sqrtf(d);
-            for (int i = c + 1 + threadIdx.x; i < s; i += blockDim.x) L[packed_row(i) + c] /= lcc;
-            __syncthreads();
-            if (threadIdx.x == 0) L[packed_row(c) + c] = lcc;
-            for (int i = c + 1 + ty; i < s; i += 16) {
-                float* lrow = L + packed_row(i);
-                const float lic = lrow[c];
-                for (int jj = c + 1 + tx; jj <= i; jj += 16) lrow[jj] -= lic * L[packed_row(jj) + c];
+        for (int c0 = 0; c0 < s && ok; c0 += PB) {
+            const int c1 = min(s, c0 + PB);
+            for (int c = c0; c < c1; ++c) {
+                const float d = L[packed_row(c) + c];
+                if (!(d > thr)) { ok = false; break; }      // same decision in every thread
+                const float lcc = sqrtf(d);
+                for (int i = c + 1 + threadIdx.x; i < s; i += blockDim.x) L[packed_row(i) + c] /= lcc;
+                __syncthreads();
+                if (threadIdx.x == 0) { L[packed_row(c) + c] = lcc; dinv[c] = 1.f / lcc; }
+                const int pw = c1 - c - 1;                  // panel columns right of c
+                if (pw > 0)
+                    for (int e = threadIdx.x; e < (s - c - 1) * pw; e += blockDim.x) {
+                        const int i = c + 1 + e / pw, j = c + 1 + e % pw;
+                        if (j <= i) L[packed_row(i) + j] -= L[packed_row(i) + c] * L[packed_row(j) + c];
+                    }
+                __syncthreads();
+            }
+            if (!ok) break;
+            const int T = s - c1;
+            const int nbk = (T + 63) / 64;
+            for (int pr = 0; pr < nbk * (nbk + 1) / 2; ++pr) {
+                int bi = (int)((sqrtf(8.f * pr + 1.f) - 1.f) * 0.5f);
+                while ((bi + 1) * (bi + 2) / 2 <= pr) ++bi;
+                while (bi * (bi + 1) / 2 > pr) --bi;
+                const int bj = pr - bi * (bi + 1) / 2;
+                const int i0 = c1 + bi * 64, j0 = c1 + bj * 64;
+                float li[4][PB], lj[4][PB];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * u;
+#pragma unroll
+                    for (int t = 0; t < PB; ++t) {
+                        li[u][t] = (i < s && c0 + t < c1) ? L[packed_row(i) + c0 + t] : 0.f;
+                        lj[u][t] = (j < s && c0 + t < c1) ? L[packed_row(j) + c0 + t] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + ty + 16 * u;
+                    if (i >= s) break;
+                    float* lrow = L + packed_row(i);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int j = j0 + tx + 16 * v;
+                        if (j > i) break;
+                        float acc = 0.f;
+#pragma unroll
+                        for (int t = 0; t < PB; ++t) acc += li[u][t] * lj[v][t];
+                        lrow[j] -= acc;
+                    }
+                }
             }
             __syncthreads();
         }
@@ -340,7 +387,7 @@ __global__ void __launch_bounds__(256) k_ols_mixed(OlsArgs a)
             __syncthreads();
             double prev = 0.0;
             for (int itr = 0; itr <= OLS_REFINE_MAX; ++itr) {
-                chol_solve_f32(L, w, s, warp, lane);
+                chol_solve_f32(L, dinv, w, s, warp, lane);
                 double dd = 0.0, xx = 0.0;
                 for (int x = threadIdx.x; x < s; x += blockDim.x) {
                     const double nx = x64[x] + (double)w[x];
@@ -578,16 +625,20 @@ int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
     if (a.solves == 0) return 0;
     const int sm2 = (a.smax + 1) & ~1;
     const size_t base = sizeof(int) * sm2 + 2 * sizeof(double) * sm2 + 32 * sizeof(double) +
-                        sizeof(float) * sm2;
+                        2 * sizeof(float) * sm2;
     const size_t lbytes = sizeof(float) * (size_t)a.smax * (a.smax + 1) / 2;
     const size_t cap = 227 * 1024 - 64;
     const bool in_smem = base + lbytes <= cap;
     const size_t smem = base + (in_smem ? lbytes : 0);
-    allow_max_dynamic_smem((const void*)k_ols_mixed);
+    // small supports: narrow panels and few registers, many CTAs per SM (their
+    // steps are short and latency-bound); large ones: wide register tiles
+    const bool small = a.smax <= OLS_SMALL;
+    const void* kern = small ? (const void*)k_ols_mixed<2, 4> : (const void*)k_ols_mixed<8, 1>;
+    allow_max_dynamic_smem(kern);
     int dev = 0, nsm = 0, per = 0;
     UOI_CUDA(cudaGetDevice(&dev));
     UOI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    UOI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ols_mixed, 256, smem));
+    UOI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
     const int grid = (int)std::min<int64_t>(a.solves, (int64_t)nsm * std::max(1, per));
     DevBuf fscratch;
     if (!in_smem) {
@@ -599,7 +650,8 @@ int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
     UOI_CUDA(cudaMemsetAsync(fbc.ptr, 0, sizeof(int32_t), s));
     a.fb_list = fbl.as<int32_t>();
     a.fb_count = fbc.as<int32_t>();
-    k_ols_mixed<<<grid, 256, smem, s>>>(a);
+    if (small) k_ols_mixed<2, 4><<<grid, 256, smem, s>>>(a);
+    else k_ols_mixed<8, 1><<<grid, 256, smem, s>>>(a);
     UOI_CHECK_LAUNCH();
     count_launch();
     int32_t nfb = 0;
