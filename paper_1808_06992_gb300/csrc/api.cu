@@ -483,10 +483,14 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         DevBuf ucols(sizeof(int32_t) * (size_t)p, s);
         const int32_t nu = union_columns(fam.as<uint64_t>(), q * r, p, ucols.as<int32_t>(), s);
         if (nu > 0) {
+            // the design restricted to U once, so both passes read contiguous rows
+            DevBuf Xu(sizeof(float) * (size_t)(m * nu), s);
+            gather_cols_f32(X32.as<float>(), ldx, m, ucols.as<int32_t>(), nu, Xu.as<float>(), s);
             moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), west.as<uint32_t>(),
-                            nullptr, B2, Gt.as<double>(), Bt.as<double>(), s, X32.as<float>());
+                            nullptr, B2, Gt.as<double>(), Bt.as<double>(), s, Xu.as<float>(), nu, true);
             moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), nullptr,
-                            evm.as<uint8_t>(), B2, Ge.as<double>(), Be.as<double>(), s, X32.as<float>());
+                            evm.as<uint8_t>(), B2, Ge.as<double>(), Be.as<double>(), s, Xu.as<float>(), nu,
+                            true);
         }
     } else {
         moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, west.as<uint32_t>(), nullptr, B2,

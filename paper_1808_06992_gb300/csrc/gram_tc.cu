@@ -241,8 +241,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 constexpr int SPLIT_ROWS = 128;
 constexpr int SPLIT_COLS = 32;
 __global__ void __launch_bounds__(256)
-k_split_transpose(const double* X, int64_t ldx, const float* X32, const double* Y, int64_t ldy,
-                  int32_t pz_x, int32_t r, const int32_t* colmap, const int32_t* rowlist,
+k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, int32_t x32_compact,
+                  const double* Y, int64_t ldy, int32_t pz_x, int32_t r, const int32_t* colmap,
+                  const int32_t* rowlist,
                   const float* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
                   int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq)
 {
@@ -264,7 +265,8 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, const double* 
     // read: warp w takes rows w, w + 8, ...; lane = column
     {
         const int c = c0 + lane;
-        const int64_t col = colmap && c < pz_x ? colmap[c] : c;
+        const int64_t col = colmap && c < pz_x ? colmap[c] : c;      // column of X
+        const int64_t col32 = x32_compact ? c : col;                 // column of the FP32 copy
         float q[SPLIT_ROWS / 8];
 #pragma unroll
         for (int i = 0; i < SPLIT_ROWS / 8; ++i) {
@@ -272,7 +274,7 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, const double* 
             float v = 0.f;
             if (row >= 0 && c < pz) {
                 if (c < pz_x)
-                    v = X32 ? __ldg(X32 + row * ldx + col) : f64_to_f32_int(__ldg(X + row * ldx + col));
+                    v = X32 ? __ldg(X32 + row * ld32 + col32) : f64_to_f32_int(__ldg(X + row * ldx + col));
                 else
                     v = f64_to_f32_int(__ldg(Y + row * ldy + (c - pz_x)));
             }
@@ -413,8 +415,9 @@ bool gram_tc_available()
 void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
                      int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
                      const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
-                     cudaStream_t s, const float* X32)
+                     cudaStream_t s, const float* X32, int64_t ld32, bool x32_compact)
 {
+    if (ld32 == 0) ld32 = ldx;
     if (!gram_tc_available()) throw Error(UOI_ERR_UNSUPPORTED, "tcgen05 Gram needs sm_103a");
     const int32_t pz = pz_x + (int32_t)r;
     const int32_t pz_pad = (int32_t)ceil_div(pz, TN) * TN;
@@ -458,7 +461,8 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
         dim3 gs((unsigned)(n_pad / SPLIT_ROWS), (unsigned)ceil_div(pz_pad, SPLIT_COLS), (unsigned)nb);
-        k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, X32, Y, ldy, pz_x, (int32_t)r, colmap,
+        k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, X32, ld32, x32_compact ? 1 : 0, Y, ldy, pz_x,
+                                             (int32_t)r, colmap,
                                              rows.as<int32_t>() + (size_t)b0 * m,
                                              scale.as<float>() + (size_t)b0 * m,
                                              nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
@@ -502,7 +506,27 @@ void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int6
                 int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
                 double* Bm, cudaStream_t s, const float* X32)
 {
-    moments_tc_cols(X, ldx, Y, ldy, m, p, r, (int32_t)p, nullptr, w, mask, B, G, Bm, s, X32);
+    moments_tc_cols(X, ldx, Y, ldy, m, p, r, (int32_t)p, nullptr, w, mask, B, G, Bm, s, X32, 0, false);
+}
+
+namespace {
+__global__ void k_gather_cols_f32(const float* X32, int64_t ld, int64_t m, const int32_t* cols, int64_t nu,
+                                  float* out)
+{
+    const int64_t total = m * nu;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = X32[(t / nu) * ld + cols[t % nu]];
+}
+}  // namespace
+
+void gather_cols_f32(const float* X32, int64_t ld, int64_t m, const int32_t* cols, int64_t nu, float* out,
+                     cudaStream_t s)
+{
+    k_gather_cols_f32<<<(unsigned)std::min<int64_t>(ceil_div(m * nu, 256), 152 * 32), 256, 0, s>>>(
+        X32, ld, m, cols, nu, out);
+    UOI_CHECK_LAUNCH();
+    count_launch();
 }
 
 namespace {

@@ -98,7 +98,12 @@ void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cuda
 void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
                      int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
                      const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
-                     cudaStream_t s, const float* X32 = nullptr);
+                     cudaStream_t s, const float* X32 = nullptr, int64_t ld32 = 0,
+                     bool x32_compact = false);
+// out[i*nu + t] = X32[i*ld + cols[t]]: the FP32 design restricted to the listed columns
+// (X32_compact form for moments_tc_cols: column t of the copy is colmap[t] of X).
+void gather_cols_f32(const float* X32, int64_t ld, int64_t m, const int32_t* cols, int64_t nu, float* out,
+                     cudaStream_t s);
 
 // ---- G3: factor (factor.cu) -------------------------------------------------------
 // A_k = G_k / nk[k] + rho I in T, lower Cholesky in place.  status->code set to
