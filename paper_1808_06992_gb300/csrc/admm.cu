@@ -667,8 +667,7 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
         count_launch();
     }
 
-    int32_t* host_total = nullptr;
-    UOI_CUDA(cudaMallocHost(&host_total, sizeof(int32_t)));
+    int32_t* host_total = pinned_scratch_i32();
     const int64_t bound = (int64_t)(P.warm ? P.q : 1) * P.max_iter + 2;
     const int check_every = 8;
     T* V[2] = { v0.as<T>(), v1.as<T>() };
@@ -702,10 +701,8 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
             }
         }
     } catch (...) {
-        cudaFreeHost(host_total);
         throw;
     }
-    cudaFreeHost(host_total);
     if (!done) throw Error(UOI_ERR_TIMEOUT, "ADMM streaming loop exceeded its iteration bound");
 }
 

@@ -41,6 +41,13 @@ void DevBuf::release()
 
 thread_local std::string g_last_error;
 
+int32_t* pinned_scratch_i32()
+{
+    thread_local int32_t* buf = nullptr;
+    if (!buf) UOI_CUDA(cudaMallocHost(&buf, 64 * sizeof(int32_t)));
+    return buf;
+}
+
 void allow_max_dynamic_smem(const void* kern)
 {
     int dev = 0, optin = 0;

@@ -54,6 +54,10 @@ struct DevBuf {
 // use this, so that every caller sets the same value and concurrent callers on
 // other streams cannot undercut each other.
 void allow_max_dynamic_smem(const void* kern);
+// A small pinned host buffer owned by the calling thread (allocated on first use,
+// kept until exit): device-to-host polling without a pinned allocation and free
+// (and their synchronisation) per call.
+int32_t* pinned_scratch_i32();
 
 // ---- G0: bootstrap indices (bootstrap.cu) -----------------------------------
 // w[k*m + row] = multiplicity of the row in selection bootstrap k, k < B.
