@@ -54,84 +54,11 @@ struct XtArgs {
     float rho;
     float* z; float* u;           // slots x p
     __nv_bfloat16* vnext;         // 3 x slots x kpad
-    int32_t* slot_j;
-    uint8_t* live;
+    const int32_t* slot_j;
+    const uint8_t* live;
     float* norms;                 // slots x RT x 5
     int32_t* err;
-    // convergence test of Eq. 5's ADMM, run by the last row-tile CTA of each
-    // (group, chain tile) once the tile's norms are all written
-    int32_t* tile_done;           // G x CT arrival counters (zero between launches)
-    int32_t CT;
-    int32_t max_iter;
-    float abs_tol, rel_tol, sqrtp;
-    const int32_t* slot_jend;
-    int32_t* slot_it;
-    double* beta;
-    int32_t* iters;
-    uint8_t* conv;
-    uint64_t* family;
-    int32_t W;
-    int32_t* live_count;
 };
-
-// Stopping test of one slot (one warp): fixed-order sum of its row-tile norms,
-// output of a finished column (z as the estimate, its support ANDed into the
-// family), path advance, live count for the host.
-__device__ __forceinline__ void xt_check_slot(const XtArgs& a, int64_t sl, int lane)
-{
-    const int RT = a.RT;
-    float tot[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
-    for (int t0 = 0; t0 < RT; t0 += 32) {
-        float loc[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
-        if (t0 + lane < RT)
-#pragma unroll
-            for (int c = 0; c < 5; ++c) loc[c] = a.norms[(sl * RT + t0 + lane) * 5 + c];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) tot[c] += warp_sum(loc[c]);
-    }
-    int it = a.slot_it[sl] + 1;
-    const float xn = sqrtf(tot[2]), zn = sqrtf(tot[3]);
-    const float eps_pri = a.sqrtp * a.abs_tol + a.rel_tol * fmaxf(xn, zn);
-    const float eps_dual = a.sqrtp * a.abs_tol + a.rel_tol * a.rho * sqrtf(tot[4]);
-    const bool converged = sqrtf(tot[0]) <= eps_pri && a.rho * sqrtf(tot[1]) <= eps_dual;
-    bool still = true;
-    if (converged || it >= a.max_iter) {
-        const int g = (int)(sl / a.nchains), cid = (int)(sl % a.nchains);
-        const int e = a.warm ? cid : cid % a.r;
-        const int j = a.slot_j[sl];
-        const int64_t col_je = (int64_t)j * a.r + e;
-        const int64_t col = (int64_t)g * a.q * a.r + col_je;
-        for (int a0 = 0; 32 * a0 < a.p; ++a0) {
-            const int i = lane + 32 * a0;
-            const float zi = i < a.p ? a.z[sl * a.p + i] : 0.f;
-            if (a.beta && i < a.p) a.beta[col * a.p + i] = (double)zi;
-            if (a.family) {
-                const unsigned bal = __ballot_sync(0xffffffffu, zi != 0.f);
-                if (lane == 0) {
-                    const int shift = (a0 & 1) * 32;
-                    const uint64_t mask = ((uint64_t)bal << shift) | ~(0xFFFFFFFFull << shift);
-                    atomicAnd((unsigned long long*)&a.family[col_je * a.W + (a0 >> 1)],
-                              (unsigned long long)mask);
-                }
-            }
-        }
-        if (lane == 0) {
-            if (a.iters) a.iters[col] = it;
-            if (a.conv) a.conv[col] = converged ? 1 : 0;
-        }
-        if (j + 1 < a.slot_jend[sl]) {
-            if (lane == 0) a.slot_j[sl] = j + 1;
-            it = 0;
-        } else {
-            still = false;
-        }
-    }
-    if (lane == 0) {
-        a.slot_it[sl] = it;
-        if (!still) a.live[sl] = 0;
-        else atomicAdd(a.live_count, 1);
-    }
-}
 
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l)
 {
@@ -402,23 +329,6 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(XT_TMEM_COLS));
     }
-    // the last of the tile's RT row-tile CTAs runs the stopping test of its chains
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int prev = atomicAdd(&a.tile_done[g * a.CT + ct], 1);
-        s_last = prev == a.RT - 1;
-        if (s_last) a.tile_done[g * a.CT + ct] = 0;       // ready for the next launch
-    }
-    __syncthreads();
-    if (!s_last || abort_flag) return;
-    __threadfence();
-    for (int n = warp; n < a.NT; n += XT_THREADS / 32) {
-        if (n0 + n >= a.nchains) break;
-        if (!s_live[n]) continue;
-        xt_check_slot(a, (int64_t)g * a.nchains + n0 + n, lane);
-    }
 }
 
 // M_g (FP32, p x p) -> three bf16 pieces in 128 x 32 blocks, ordered
@@ -464,6 +374,72 @@ __global__ void k_xt_init(int64_t slots, int64_t p, int64_t kpad, const float* z
         v[slots * kpad + t] = m;
         v[2 * slots * kpad + t] = l;
         if (i == 0) live[sl] = 1;
+    }
+}
+
+// Convergence check of every live slot (one warp each): fixed-order sum of the
+// row-tile norms, stopping test of Eq. 5's ADMM, output of finished columns,
+// path advance, live count for the host.
+__global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t nchains, int32_t RT,
+                           int32_t warm, int32_t max_iter, float rho, float abs_tol, float rel_tol,
+                           float sqrtp, const float* z, const float* norms, int32_t* slot_j,
+                           const int32_t* slot_jend, int32_t* slot_it, uint8_t* live, double* beta,
+                           int32_t* iters, uint8_t* conv, uint64_t* family, int32_t W,
+                           int32_t* live_count)
+{
+    const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= (int64_t)G * nchains || !live[sl]) return;
+    float tot[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
+    for (int t0 = 0; t0 < RT; t0 += 32) {
+        float loc[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
+        if (t0 + lane < RT)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) loc[c] = norms[(sl * RT + t0 + lane) * 5 + c];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) tot[c] += warp_sum(loc[c]);
+    }
+    int it = slot_it[sl] + 1;
+    const float xn = sqrtf(tot[2]), zn = sqrtf(tot[3]);
+    const float eps_pri = sqrtp * abs_tol + rel_tol * fmaxf(xn, zn);
+    const float eps_dual = sqrtp * abs_tol + rel_tol * rho * sqrtf(tot[4]);
+    const bool converged = sqrtf(tot[0]) <= eps_pri && rho * sqrtf(tot[1]) <= eps_dual;
+    bool still = true;
+    if (converged || it >= max_iter) {
+        const int g = (int)(sl / nchains), cid = (int)(sl % nchains);
+        const int e = warm ? cid : cid % r;
+        const int j = slot_j[sl];
+        const int64_t col_je = (int64_t)j * r + e;
+        const int64_t col = (int64_t)g * q * r + col_je;
+        for (int a0 = 0; 32 * a0 < p; ++a0) {
+            const int i = lane + 32 * a0;
+            const float zi = i < p ? z[sl * p + i] : 0.f;
+            if (beta && i < p) beta[col * p + i] = (double)zi;
+            if (family) {
+                const unsigned bal = __ballot_sync(0xffffffffu, zi != 0.f);
+                if (lane == 0) {
+                    const int shift = (a0 & 1) * 32;
+                    const uint64_t mask = ((uint64_t)bal << shift) | ~(0xFFFFFFFFull << shift);
+                    atomicAnd((unsigned long long*)&family[col_je * W + (a0 >> 1)],
+                              (unsigned long long)mask);
+                }
+            }
+        }
+        if (lane == 0) {
+            if (iters) iters[col] = it;
+            if (conv) conv[col] = converged ? 1 : 0;
+        }
+        if (j + 1 < slot_jend[sl]) {
+            if (lane == 0) slot_j[sl] = j + 1;
+            it = 0;
+        } else {
+            still = false;
+        }
+    }
+    if (lane == 0) {
+        slot_it[sl] = it;
+        if (!still) live[sl] = 0;
+        else atomicAdd(live_count, 1);
     }
 }
 
@@ -529,18 +505,11 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
     a.z = zb.as<float>(); a.u = ub.as<float>();
     a.slot_j = sj.as<int32_t>(); a.live = live.as<uint8_t>(); a.norms = nb.as<float>();
     a.err = err.as<int32_t>();
-    const int CT = (int)ceil_div(nchains, NT);
-    DevBuf tdone(sizeof(int32_t) * (size_t)P.G * CT, s);
-    UOI_CUDA(cudaMemsetAsync(tdone.ptr, 0, tdone.bytes, s));
-    a.tile_done = tdone.as<int32_t>(); a.CT = CT;
-    a.max_iter = P.max_iter; a.abs_tol = (float)P.abs_tol; a.rel_tol = (float)P.rel_tol;
-    a.sqrtp = (float)sqrt((double)p);
-    a.slot_jend = sje.as<int32_t>(); a.slot_it = sit.as<int32_t>();
-    a.beta = P.beta; a.iters = P.iters; a.conv = P.conv; a.family = P.family;
-    a.W = (int32_t)((p + 63) / 64); a.live_count = cnt.as<int32_t>();
-    const dim3 grid((unsigned)RT, (unsigned)CT, (unsigned)P.G);
+    const dim3 grid((unsigned)RT, (unsigned)ceil_div(nchains, NT), (unsigned)P.G);
+    const dim3 gc((unsigned)ceil_div(slots * 32, 256));
     int32_t* host_cnt = pinned_scratch_i32();
     const int64_t bound = (int64_t)(P.warm ? P.q : 1) * P.max_iter + 2;
+    const int W = (int)((p + 63) / 64);
     bool done = false;
     try {
         for (int64_t it = 0; it < bound && !done; ++it) {
@@ -551,7 +520,14 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
             k_xupdate_tc<<<grid, XT_THREADS, XT_SMEM, s>>>(mM, even ? mV0 : mV1, a);
             UOI_CHECK_LAUNCH();
             ktimer_end(TK_XUPDATE, s, 0.0, 0.0);
-            count_launch();
+            k_xt_check<<<gc, 256, 0, s>>>(P.G, P.q, (int32_t)P.r, p, nchains, RT, P.warm, P.max_iter,
+                                          (float)P.rho, (float)P.abs_tol, (float)P.rel_tol,
+                                          (float)sqrt((double)p), zb.as<float>(), nb.as<float>(),
+                                          sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>(),
+                                          live.as<uint8_t>(), P.beta, P.iters, P.conv, P.family, W,
+                                          cnt.as<int32_t>());
+            UOI_CHECK_LAUNCH();
+            count_launch(2);
             if ((it + 1) % 8 == 0 || it + 1 == bound) {
                 int32_t herr = 0;
                 UOI_CUDA(cudaMemcpyAsync(host_cnt, cnt.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
