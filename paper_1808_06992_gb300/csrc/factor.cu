@@ -39,15 +39,17 @@ __device__ __forceinline__ float system_entry<float>(double g, double inv_n, dou
     return f64_to_f32_int(g) * (float)inv_n + (diag ? (float)rho : 0.f);
 }
 
+// One row per block-row step (no index division per element).
 template <typename T>
 __global__ void k_build_system(const double* G, const double* nk, double rho, int64_t p, T* A)
 {
     const int64_t k = blockIdx.y;
     const double inv_n = 1.0 / nk[k];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < p * p;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / p, j = t % p;
-        A[k * p * p + t] = system_entry<T>(G[k * p * p + t], inv_n, rho, i == j);
+    for (int64_t i = blockIdx.x; i < p; i += gridDim.x) {
+        const double* grow = G + (k * p + i) * p;
+        T* arow = A + (k * p + i) * p;
+        for (int64_t j = threadIdx.x; j < p; j += blockDim.x)
+            arow[j] = system_entry<T>(grow[j], inv_n, rho, i == j);
     }
 }
 
@@ -339,7 +341,7 @@ template <typename T>
 void build_system(const double* G, const double* nk, double rho, int64_t p, int32_t B, T* A,
                   cudaStream_t s)
 {
-    dim3 gb((unsigned)std::min<int64_t>(ceil_div(p * p, 256), 1024), (unsigned)B);
+    dim3 gb((unsigned)std::min<int64_t>(p, 1024), (unsigned)B);
     k_build_system<T><<<gb, 256, 0, s>>>(G, nk, rho, p, A);
     UOI_CHECK_LAUNCH();
     count_launch();

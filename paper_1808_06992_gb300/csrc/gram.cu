@@ -158,7 +158,7 @@ __global__ void k_check_finite(const double* X, int64_t ldx, int64_t m, int64_t 
 }
 
 // Split-K X^T Y for r <= 4: block (column tile, row chunk) writes partial sums.
-constexpr int XTY_ROWS = 1024;
+constexpr int XTY_ROWS = 128;      // short row chunks: many blocks in flight
 __global__ void k_xty_partial(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                               int64_t m, int64_t p, int64_t r, double* part)
 {
@@ -167,6 +167,7 @@ __global__ void k_xty_partial(const double* X, int64_t ldx, const double* Y, int
     const int64_t t0 = c * XTY_ROWS, t1 = min(m, t0 + XTY_ROWS);
     double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
     if (j < p) {
+#pragma unroll 8
         for (int64_t t = t0; t < t1; ++t) {
             const double x = X[t * ldx + j];
 #pragma unroll

@@ -363,6 +363,29 @@ __global__ void k_row_lists(const uint32_t* w, const uint8_t* mask, int64_t m, i
 // three-product split leaves out and which is biased (always positive).  The
 // off-diagonal lo'lo terms are zero-mean and stay out.  Sums the per-64-row
 // partials of k_split_transpose in a fixed order.
+// Same for an output without a column map: 32 x 32 tiles through shared memory,
+// so the lower triangle is read and the upper written along rows.  Block (32, 8).
+__global__ void k_mirror_tiled(double* G, int64_t p_out, int32_t pz_x, const double* corr)
+{
+    __shared__ double tile[32][33];
+    const int item = blockIdx.z;
+    const int bx = blockIdx.x, by = blockIdx.y;       // target tile: rows by*32.., columns bx*32..
+    if (bx < by) return;                              // lower tiles are the source
+    double* g = G + (size_t)item * p_out * p_out;
+    const int tx = threadIdx.x;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {    // source rows bx*32 + yy, columns by*32 + tx
+        const int r = bx * 32 + yy, c = by * 32 + tx;
+        tile[yy][tx] = (r < pz_x && c < pz_x) ? g[(size_t)r * p_out + c] : 0.0;
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {    // target rows by*32 + yy, columns bx*32 + tx
+        const int r = by * 32 + yy, c = bx * 32 + tx;
+        if (r >= pz_x || c >= pz_x) continue;
+        if (c > r) g[(size_t)r * p_out + c] = tile[tx][yy];
+        else if (c == r) g[(size_t)r * p_out + c] += corr[(int64_t)item * pz_x + r];
+    }
+}
+
 __global__ void k_diag_lo(const float* losq, int32_t row_tiles, int32_t pz_x,
                           const int32_t* nrows, double* corr)
 {
@@ -484,9 +507,15 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         k_diag_lo<<<gd, 256, 0, s>>>(losq.as<float>(), row_tiles, pz_x, nrows.as<int32_t>() + b0,
                                      corr.as<double>());
         UOI_CHECK_LAUNCH();
-        dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
-        k_mirror<<<gm, 256, 0, s>>>(G + (size_t)b0 * p_out * p_out, p_out, colmap, pz_x,
-                                    corr.as<double>());
+        if (colmap) {
+            dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
+            k_mirror<<<gm, 256, 0, s>>>(G + (size_t)b0 * p_out * p_out, p_out, colmap, pz_x,
+                                        corr.as<double>());
+        } else {
+            const unsigned tt = (unsigned)ceil_div(pz_x, 32);
+            k_mirror_tiled<<<dim3(tt, tt, (unsigned)nb), dim3(32, 8), 0, s>>>(
+                G + (size_t)b0 * p_out * p_out, p_out, pz_x, corr.as<double>());
+        }
         UOI_CHECK_LAUNCH();
         count_launch(4);
     }

@@ -333,24 +333,36 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
 
 // M_g (FP32, p x p) -> three bf16 pieces in 128 x 32 blocks, ordered
 // [g][row tile][k block][piece][128][32] (zero padded), so that the x-update
-// streams each row tile as one contiguous run of 24 KB stages.
+// streams each row tile as one contiguous run of 24 KB stages.  One thread per
+// 8 consecutive k: a 32-byte read and one 16-byte write per piece.
 __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
                           __nv_bfloat16* out)
 {
-    const int64_t per = (int64_t)G * ppad * kpad;
+    const int64_t per8 = (int64_t)G * ppad * (kpad / 8);
     const int64_t RT = ppad / XT_TM, kst = kpad / XT_TK;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per8;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = t % kpad, row = t / kpad;
+        const int64_t k8 = (t % (kpad / 8)) * 8, row = t / (kpad / 8);
         const int64_t g = row / ppad, i = row % ppad;
-        const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] : 0.f;
-        __nv_bfloat16 h, m, l;
-        split3(x, h, m, l);
-        const int64_t blk = ((g * RT + i / XT_TM) * kst + k / XT_TK) * 3;
-        const int64_t o = (blk * XT_TM + i % XT_TM) * XT_TK + k % XT_TK;
-        out[o] = h;
-        out[o + XT_TM * XT_TK] = m;
-        out[o + 2 * XT_TM * XT_TK] = l;
+        uint32_t ph[4], pm[4], pl[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t k = k8 + 2 * q + u;
+                const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] : 0.f;
+                split3(x, h[u], m[u], l[u]);
+            }
+            ph[q] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+            pm[q] = (uint32_t)__bfloat16_as_ushort(m[0]) | ((uint32_t)__bfloat16_as_ushort(m[1]) << 16);
+            pl[q] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+        }
+        const int64_t blk = ((g * RT + i / XT_TM) * kst + k8 / XT_TK) * 3;
+        const int64_t o = (blk * XT_TM + i % XT_TM) * XT_TK + k8 % XT_TK;    // multiple of 8: 16 B aligned
+        *reinterpret_cast<uint4*>(out + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+        *reinterpret_cast<uint4*>(out + o + XT_TM * XT_TK) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+        *reinterpret_cast<uint4*>(out + o + 2 * XT_TM * XT_TK) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
     }
 }
 
@@ -473,7 +485,7 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
     const int NT = (int)std::min<int64_t>(XT_NT_MAX, ceil_div(nchains, 16) * 16);
     const int kst = (int)(kpad / XT_TK);
     DevBuf mp(sizeof(__nv_bfloat16) * 3 * (size_t)P.G * ppad * kpad, s);
-    k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad, 256), 8192), 256, 0, s>>>(
+    k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad / 8, 256), 8192), 256, 0, s>>>(
         P.M, P.G, p, ppad, kpad, mp.as<__nv_bfloat16>());
     UOI_CHECK_LAUNCH();
     DevBuf zb(sizeof(float) * (size_t)slots * p, s), ub(sizeof(float) * (size_t)slots * p, s);
