@@ -261,8 +261,8 @@ __device__ __forceinline__ double block_sum(double v, double* red, int lane, int
     return t;
 }
 
-// PB: panel width of the blocked Cholesky (register tiles of 4 x 4 x PB);
-// MINB: CTAs per SM the registers must allow (small supports want many).
+// PB: k chunk of the trailing update's 4 x 4 register tiles; MINB: CTAs per SM
+// the registers must allow (small supports want many).
 template <int PB, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_ols_mixed(OlsArgs a)
 {
@@ -322,28 +322,63 @@ __global__ void __launch_bounds__(256, MINB) k_ols_mixed(OlsArgs a)
         for (int x = threadIdx.x; x < s; x += blockDim.x) b64[x] = Bk[(size_t)idx[x] * a.r + e];
         const double dmax = block_max(dm, red, lane, warp);
         const float thr = OLS_F32_PIVOT * (float)dmax;
-        // blocked right-looking Cholesky: panels of PB columns factored column by
-        // column, then one rank-PB update of the trailing triangle in 4 x 4
-        // register tiles (64 x 64 blocks of 16 x 16 threads)
+        // blocked right-looking Cholesky with 32-column panels: warp 0 factors the
+        // diagonal block in registers (no block barrier per column), every
+        // thread solves one row of the panel below it against that block, then the
+        // trailing triangle takes the rank-32 update in 4 x 4 register tiles
+        // (k chunks of PB) over 64 x 64 blocks of 16 x 16 threads: three barriers
+        // per 32 columns
+        __shared__ int s_ok;
         bool ok = true;
-        for (int c0 = 0; c0 < s && ok; c0 += PB) {
-            const int c1 = min(s, c0 + PB);
-            for (int c = c0; c < c1; ++c) {
-                const float d = L[packed_row(c) + c];
-                if (!(d > thr)) { ok = false; break; }      // same decision in every thread
-                const float lcc = sqrtf(d);
-                for (int i = c + 1 + threadIdx.x; i < s; i += blockDim.x) L[packed_row(i) + c] /= lcc;
-                __syncthreads();
-                if (threadIdx.x == 0) { L[packed_row(c) + c] = lcc; dinv[c] = 1.f / lcc; }
-                const int pw = c1 - c - 1;                  // panel columns right of c
-                if (pw > 0)
-                    for (int e = threadIdx.x; e < (s - c - 1) * pw; e += blockDim.x) {
-                        const int i = c + 1 + e / pw, j = c + 1 + e % pw;
-                        if (j <= i) L[packed_row(i) + j] -= L[packed_row(i) + c] * L[packed_row(j) + c];
+        for (int c0 = 0; c0 < s; c0 += 32) {
+            const int c1 = min(s, c0 + 32);
+            if (warp == 0) {
+                // lane i holds row c0 + i of the diagonal block in registers;
+                // column c of the factor travels between lanes by shuffles
+                const int nb = c1 - c0;
+                const bool has = lane < nb;
+                float* lrow = L + packed_row(c0 + (has ? lane : 0)) + c0;
+                float a[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) a[j] = (has && j <= lane) ? lrow[j] : 0.f;
+                bool wok = true;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    if (c >= nb || !wok) continue;                   // same in every lane
+                    const float d = __shfl_sync(0xffffffffu, a[c], c);
+                    if (!(d > thr)) { wok = false; continue; }
+                    const float lcc = sqrtf(d);
+                    const float inv = 1.f / lcc;
+                    const float lic = lane > c ? a[c] * inv : 0.f;
+                    if (lane == c) a[c] = lcc;
+                    else if (lane > c) a[c] = lic;
+                    if (lane == 0) dinv[c0 + c] = inv;
+#pragma unroll
+                    for (int j = c + 1; j < 32; ++j) {
+                        const float ljc = __shfl_sync(0xffffffffu, lic, j);
+                        if (lane >= j) a[j] -= lic * ljc;
                     }
-                __syncthreads();
+                }
+                if (wok && has) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j <= lane) lrow[j] = a[j];
+                }
+                if (lane == 0) s_ok = wok ? 1 : 0;
             }
-            if (!ok) break;
+            __syncthreads();
+            if (!s_ok) { ok = false; break; }
+            // panel rows below the block: L21 = A21 L11^{-T}, one row per thread
+            for (int r = c1 + threadIdx.x; r < s; r += blockDim.x) {
+                float* lr = L + packed_row(r);
+                for (int c = c0; c < c1; ++c) {
+                    const float* lc = L + packed_row(c);
+                    float acc = lr[c];
+                    for (int t = c0; t < c; ++t) acc -= lr[t] * lc[t];
+                    lr[c] = acc * dinv[c];
+                }
+            }
+            __syncthreads();
             const int T = s - c1;
             const int nbk = (T + 63) / 64;
             for (int pr = 0; pr < nbk * (nbk + 1) / 2; ++pr) {
@@ -352,15 +387,29 @@ __global__ void __launch_bounds__(256, MINB) k_ols_mixed(OlsArgs a)
                 while (bi * (bi + 1) / 2 > pr) --bi;
                 const int bj = pr - bi * (bi + 1) / 2;
                 const int i0 = c1 + bi * 64, j0 = c1 + bj * 64;
-                float li[4][PB], lj[4][PB];
+                float acc[4][4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * u;
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int t = 0; t < PB; ++t) {
-                        li[u][t] = (i < s && c0 + t < c1) ? L[packed_row(i) + c0 + t] : 0.f;
-                        lj[u][t] = (j < s && c0 + t < c1) ? L[packed_row(j) + c0 + t] : 0.f;
+                    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+                for (int k0 = c0; k0 < c1; k0 += PB) {
+                    float li[4][PB], lj[4][PB];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * u;
+#pragma unroll
+                        for (int t = 0; t < PB; ++t) {
+                            const bool kin = k0 + t < c1;
+                            li[u][t] = (i < s && kin) ? L[packed_row(i) + k0 + t] : 0.f;
+                            lj[u][t] = (j < s && kin) ? L[packed_row(j) + k0 + t] : 0.f;
+                        }
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+#pragma unroll
+                            for (int t = 0; t < PB; ++t) acc[u][v] += li[u][t] * lj[v][t];
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -371,10 +420,7 @@ __global__ void __launch_bounds__(256, MINB) k_ols_mixed(OlsArgs a)
                     for (int v = 0; v < 4; ++v) {
                         const int j = j0 + tx + 16 * v;
                         if (j > i) break;
-                        float acc = 0.f;
-#pragma unroll
-                        for (int t = 0; t < PB; ++t) acc += li[u][t] * lj[v][t];
-                        lrow[j] -= acc;
+                        lrow[j] -= acc[u][v];
                     }
                 }
             }
