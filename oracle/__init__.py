@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the UoI_LASSO / UoI_VAR(1) hot path -- TEST INFRASTRUCTURE.
+"""FP64 CPU oracle for the UoI_LASSO / UoI_VAR(d) hot path -- TEST INFRASTRUCTURE.
 
 Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
 (and its ``--impl reference`` arm) may import this package.  The CUDA library
@@ -60,6 +60,7 @@ class RefParams(C.Structure):
         ("block_len", C.c_int64),
         ("bagging", C.c_int32), ("split_fixed", C.c_int32), ("warm_start", C.c_int32),
         ("n_threads", C.c_int32),
+        ("intercept", C.c_int32),
     ]
 
 
@@ -113,6 +114,12 @@ def lib():
                                                P(C.c_uint32), i32, P(d), i32, d, d, d, i32, i32,
                                                P(i64), i64, P(d), P(i32), P(C.c_uint8), P(d)]
             L.ref_ols_support.argtypes = [P(d), P(d), i64, i64, P(u64), P(d)]
+            L.ref_lasso_admm_intercept.argtypes = [P(d), i64, P(d), i64, i64, i64, i64,
+                                                   P(C.c_uint32), P(d), i32, d, d, d, i32, i32,
+                                                   P(d), P(d), P(i32), P(C.c_uint8), P(d)]
+            L.ref_lagged_design.argtypes = [P(d), i64, i64, i32, P(d), P(d)]
+            L.ref_uoi_var_fit.argtypes = [P(d), i64, i64, i32, P(RefParams), P(d), P(d),
+                                          P(RefTrace)]
             L.ref_uoi_fit.argtypes = [P(d), i64, P(d), i64, i64, i64, i64,
                                       P(RefParams), P(d), P(RefTrace)]
             _lib = L
@@ -257,6 +264,42 @@ def lasso_admm_batch(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6
     return dict(beta=beta, iters=iters, conv=conv.astype(bool), v=v, status=int(st))
 
 
+def lasso_admm_intercept(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6,
+                         max_iter=1000, warm_start=1):
+    """LASSO with an unpenalised intercept for one weight vector (or None).
+    Returns dict(beta (q,r,p), mu (q,r), iters, conv, v, status)."""
+    X = _f64(X)
+    Y = _f64(Y)
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    m, p = X.shape
+    r = Y.shape[1]
+    lam = _f64(lambdas)
+    q = lam.shape[0]
+    wa = None if weights is None else np.ascontiguousarray(weights, dtype=np.uint32).reshape(m)
+    beta = np.zeros((q, r, p))
+    mu = np.zeros((q, r))
+    v = np.zeros((q, r, p))
+    iters = np.zeros((q, r), dtype=np.int32)
+    conv = np.zeros((q, r), dtype=np.uint8)
+    st = lib().ref_lasso_admm_intercept(_p(X, C.c_double), p, _p(Y, C.c_double), r, m, p, r,
+                                        _p(wa, C.c_uint32), _p(lam, C.c_double), q, rho, abs_tol,
+                                        rel_tol, max_iter, warm_start, _p(beta, C.c_double),
+                                        _p(mu, C.c_double), _p(iters, C.c_int32),
+                                        _p(conv, C.c_uint8), _p(v, C.c_double))
+    return dict(beta=beta, mu=mu, iters=iters, conv=conv.astype(bool), v=v, status=int(st))
+
+
+def lagged_design(series, order):
+    """(X, Y) of Eq. 7-8 for a VAR(order), rows in ascending time."""
+    S = _f64(series)
+    N, p = S.shape
+    X = np.zeros((N - order, order * p))
+    Y = np.zeros((N - order, p))
+    lib().ref_lagged_design(_p(S, C.c_double), N, p, order, _p(X, C.c_double), _p(Y, C.c_double))
+    return X, Y
+
+
 def ols_support(G, b, support_bits):
     G = _f64(G)
     b = _f64(b).reshape(-1)
@@ -270,7 +313,7 @@ def ols_support(G, b, support_bits):
 
 def make_params(B1, B2, q, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol=1e-6,
                 rel_tol=1e-6, max_iter=1000, train_frac=0.8, seed=0, problem_id=0, block_len=0,
-                bagging=0, split_fixed=0, warm_start=1, n_threads=1):
+                bagging=0, split_fixed=0, warm_start=1, n_threads=1, intercept=0):
     keep = None
     prm = RefParams()
     prm.B1, prm.B2, prm.q = B1, B2, q
@@ -285,13 +328,15 @@ def make_params(B1, B2, q, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol
     prm.block_len = block_len
     prm.bagging, prm.split_fixed, prm.warm_start = bagging, split_fixed, warm_start
     prm.n_threads = n_threads
+    prm.intercept = int(bool(intercept))
     return prm, keep
 
 
 def uoi_fit(X, Y, B1, B2, q, trace=True, **kw):
     """Full UoI fit of the responses Y (m x r) on X (m x p).
 
-    Returns dict(beta (r, p), status, and the trace arrays when trace=True)."""
+    Returns dict(beta (r, pa), status, and the trace arrays when trace=True);
+    pa = p + 1 with an intercept (the last column is mu), else p."""
     X = _f64(X)
     Y = _f64(Y)
     if Y.ndim == 1:
@@ -300,7 +345,8 @@ def uoi_fit(X, Y, B1, B2, q, trace=True, **kw):
     r = Y.shape[1]
     W = (p + 63) // 64
     prm, keep = make_params(B1, B2, q, **kw)
-    beta = np.zeros((r, p))
+    pa = p + prm.intercept
+    beta = np.zeros((r, pa))
     out = dict()
     tr = None
     if trace:
@@ -308,7 +354,7 @@ def uoi_fit(X, Y, B1, B2, q, trace=True, **kw):
             lambdas=np.zeros(q), sel_beta=np.zeros((B1, q, r, p)), sel_v=np.zeros((B1, q, r, p)),
             sel_iters=np.zeros((B1, q, r), dtype=np.int32),
             sel_conv=np.zeros((B1, q, r), dtype=np.uint8),
-            family=np.zeros((q, r, W), dtype=np.uint64), est_beta=np.zeros((B2, q, r, p)),
+            family=np.zeros((q, r, W), dtype=np.uint64), est_beta=np.zeros((B2, q, r, pa)),
             est_loss=np.zeros((B2, q, r)), est_jstar=np.zeros(B2, dtype=np.int32),
             est_fallback=np.zeros((B2, q, r), dtype=np.int32),
             eval_count=np.zeros(B2, dtype=np.int32))
@@ -327,7 +373,28 @@ def uoi_lasso_fit(X, y, B1, B2, q, **kw):
     return uoi_fit(X, np.asarray(y).reshape(-1, 1), B1, B2, q, **kw)
 
 
-def uoi_var_fit(series, B1, B2, q, **kw):
-    """VAR(1): rows t = 0..N-2 regress X_{t+1} on X_t (Eq. 7-9, ascending time)."""
-    s = _f64(series)
-    return uoi_fit(s[:-1], s[1:], B1, B2, q, **kw)
+def uoi_var_fit(series, B1, B2, q, order=1, **kw):
+    """VAR(order) (Alg. 2, Eq. 6-9): the lagged design of ``lagged_design``
+    fitted as p LASSOs sharing it, then beta* partitioned into A (order, p, p),
+    A[j-1][e, i] = coefficient of X_{t-j,i} in equation e, and mu (p)."""
+    X, Y = lagged_design(series, order)
+    out = uoi_fit(X, Y, B1, B2, q, **kw)
+    p = Y.shape[1]
+    b = out["beta"]
+    out["A"] = b[:, :order * p].reshape(p, order, p).transpose(1, 0, 2).copy()
+    out["mu"] = b[:, order * p].copy() if b.shape[1] > order * p else np.zeros(p)
+    return out
+
+
+def uoi_var_fit_c(series, B1, B2, q, order=1, **kw):
+    """The same fit through the C entry point, which builds the design and
+    partitions beta* itself.  Returns (A, mu, status)."""
+    S = _f64(series)
+    N, p = S.shape
+    prm, keep = make_params(B1, B2, q, **kw)
+    A = np.zeros((max(order, 1), p, p))
+    mu = np.zeros(p)
+    st = lib().ref_uoi_var_fit(_p(S, C.c_double), N, p, order, C.byref(prm), _p(A, C.c_double),
+                               _p(mu, C.c_double), None)
+    del keep
+    return A, mu, int(st)

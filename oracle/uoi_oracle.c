@@ -1,5 +1,5 @@
 /*
- * uoi_oracle.c -- FP64 CPU oracle for the UoI_LASSO / UoI_VAR(1) hot path.
+ * uoi_oracle.c -- FP64 CPU oracle for the UoI_LASSO / UoI_VAR(d) hot path.
  *
  * TEST INFRASTRUCTURE ONLY (see uoi_oracle.h).  Plain loops in the paper's
  * order; no blocking, fusion or reordering beyond what the definitions state.
@@ -442,7 +442,84 @@ int ref_ols_support(const double* G, const double* b, int64_t ldb, int64_t p,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Full fit: Alg. 1 (r = 1) and Alg. 2 with order 1 (r = p)                  */
+/* Unpenalised intercept (Alg. 2 returns mu next to A_1..A_d; the paper does  */
+/* not say how it is fitted).  Reading: the objective of every fit gains a    */
+/* free offset, (1/(2 nk)) sum_t w_t (y_t - mu - x_t^T b)^2 + lambda ||b||_1.  */
+/* For fixed b the best mu is ybar_w - xbar_w^T b (w-weighted means), and     */
+/* putting it back leaves the plain LASSO of the w-centred data.              */
+/* ------------------------------------------------------------------------- */
+static int weighted_means(const double* A, int64_t lda, int64_t m, int64_t c, const uint32_t* w,
+                          double* mean)
+{
+    double n = 0.0;
+    for (int64_t i = 0; i < c; ++i) mean[i] = 0.0;
+    for (int64_t t = 0; t < m; ++t) {
+        double wt = w ? (double)w[t] : 1.0;
+        if (wt == 0.0) continue;
+        n += wt;
+        for (int64_t i = 0; i < c; ++i) mean[i] += wt * A[t * lda + i];
+    }
+    if (!(n > 0.0)) return -1;
+    for (int64_t i = 0; i < c; ++i) mean[i] /= n;
+    return 0;
+}
+
+static double* centred_copy(const double* A, int64_t lda, int64_t m, int64_t c, const double* mean)
+{
+    double* out = (double*)malloc((size_t)(m * c) * sizeof(double));
+    for (int64_t t = 0; t < m; ++t)
+        for (int64_t i = 0; i < c; ++i) out[t * c + i] = A[t * lda + i] - mean[i];
+    return out;
+}
+
+int ref_lasso_admm_intercept(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                             int64_t m, int64_t p, int64_t r, const uint32_t* w,
+                             const double* lambdas, int32_t q, double rho, double abs_tol,
+                             double rel_tol, int32_t max_iter, int32_t warm_start,
+                             double* beta_out, double* mu_out, int32_t* iters_out,
+                             uint8_t* conv_out, double* v_out)
+{
+    if (!X || !Y || !lambdas || !beta_out || m <= 0 || p <= 0 || r <= 0 || q <= 0)
+        return REF_ERR_INVALID_ARG;
+    double* xbar = (double*)malloc((size_t)p * sizeof(double));
+    double* ybar = (double*)malloc((size_t)r * sizeof(double));
+    if (weighted_means(X, ldx, m, p, w, xbar) || weighted_means(Y, ldy, m, r, w, ybar)) {
+        free(xbar); free(ybar);
+        return REF_ERR_INVALID_ARG;                  /* every weight zero */
+    }
+    double* Xc = centred_copy(X, ldx, m, p, xbar);
+    double* Yc = centred_copy(Y, ldy, m, r, ybar);
+    int st = ref_lasso_admm_batch(Xc, p, Yc, r, m, p, r, w, 1, lambdas, q, rho, abs_tol, rel_tol,
+                                  max_iter, warm_start, NULL, 0, beta_out, iters_out, conv_out, v_out);
+    if (st >= 0 && mu_out)
+        for (int32_t j = 0; j < q; ++j)
+            for (int64_t e = 0; e < r; ++e) {
+                const double* b = beta_out + ((int64_t)j * r + e) * p;
+                double mu = ybar[e];
+                for (int64_t i = 0; i < p; ++i) mu -= xbar[i] * b[i];
+                mu_out[(int64_t)j * r + e] = mu;
+            }
+    free(xbar); free(ybar); free(Xc); free(Yc);
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lagged design of a VAR(d) (Eq. 7-8), rows in ascending time               */
+/* ------------------------------------------------------------------------- */
+void ref_lagged_design(const double* series, int64_t N, int64_t p, int32_t d, double* X, double* Y)
+{
+    const int64_t P = (int64_t)d * p;
+    for (int64_t t = d; t < N; ++t) {
+        const int64_t row = t - d;
+        for (int64_t e = 0; e < p; ++e) Y[row * p + e] = series[t * p + e];       /* X_t      */
+        for (int32_t j = 1; j <= d; ++j)                                            /* X_{t-j}  */
+            for (int64_t c = 0; c < p; ++c)
+                X[row * P + (int64_t)(j - 1) * p + c] = series[(t - j) * p + c];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Full fit: Alg. 1 (r = 1) and Alg. 2 (r = p, lagged design)                */
 /* ------------------------------------------------------------------------- */
 static int cmp_double(const void* a, const void* b)
 {
@@ -465,12 +542,27 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     }
     const int32_t B1 = prm->B1, B2 = prm->B2, q = prm->q;
     const int64_t W = (p + 63) / 64;
+    /* with an intercept the estimation works on pa = p + 1 coordinates: the p
+     * features, then mu (a column of ones that every support contains) */
+    const int icpt = prm->intercept != 0;
+    const int64_t pa = p + icpt;
+    const int64_t Wa = (pa + 63) / 64;
     int status = REF_OK;
 
     /* lambda grid (Eq. 2 scaled by 1/(2 nk); descending) */
     double* lam = (double*)malloc((size_t)q * sizeof(double));
     if (prm->lambdas) {
         memcpy(lam, prm->lambdas, (size_t)q * sizeof(double));
+    } else if (icpt) {
+        /* Reading: with an intercept, lambda_max of the (unweighted) centred data */
+        double* xbar = (double*)malloc((size_t)p * sizeof(double));
+        double* ybar = (double*)malloc((size_t)r * sizeof(double));
+        weighted_means(X, ldx, m, p, NULL, xbar);
+        weighted_means(Y, ldy, m, r, NULL, ybar);
+        double* Xc = centred_copy(X, ldx, m, p, xbar);
+        double* Yc = centred_copy(Y, ldy, m, r, ybar);
+        ref_lambda_grid(ref_lambda_max(Xc, p, Yc, r, m, p, r), q, prm->lambda_min_ratio, lam);
+        free(xbar); free(ybar); free(Xc); free(Yc);
     } else {
         double lmax = ref_lambda_max(X, ldx, Y, ldy, m, p, r);
         ref_lambda_grid(lmax, q, prm->lambda_min_ratio, lam);
@@ -490,9 +582,12 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         int32_t* its = (int32_t*)malloc((size_t)q * r * sizeof(int32_t));
         uint8_t* cv = (uint8_t*)malloc((size_t)q * r);
         ref_selection_weights(m, prm->block_len, prm->seed, prm->problem_id, k, w);
-        int st = ref_lasso_admm_batch(X, ldx, Y, ldy, m, p, r, w, 1, lam, q, prm->rho,
-                                      prm->abs_tol, prm->rel_tol, prm->max_iter,
-                                      prm->warm_start, NULL, 0, beta, its, cv, v);
+        int st = icpt ? ref_lasso_admm_intercept(X, ldx, Y, ldy, m, p, r, w, lam, q, prm->rho,
+                                                 prm->abs_tol, prm->rel_tol, prm->max_iter,
+                                                 prm->warm_start, beta, NULL, its, cv, v)
+                      : ref_lasso_admm_batch(X, ldx, Y, ldy, m, p, r, w, 1, lam, q, prm->rho,
+                                             prm->abs_tol, prm->rel_tol, prm->max_iter,
+                                             prm->warm_start, NULL, 0, beta, its, cv, v);
 #ifdef _OPENMP
 #pragma omp critical
 #endif
@@ -530,7 +625,27 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     if (trace && trace->family) memcpy(trace->family, fam, (size_t)q * r * W * sizeof(uint64_t));
 
     /* ---- Model estimation (Alg. 1 estimation loop, Eq. 4) ---- */
-    double* chosen = (double*)malloc((size_t)B2 * r * p * sizeof(double));
+    /* design and supports of the estimation: X and S_j, or [X 1] and S_j + {mu} */
+    const double* Xe = X;
+    int64_t lde = ldx;
+    const uint64_t* fe = fam;
+    double* Xa = NULL;
+    uint64_t* fa = NULL;
+    if (icpt) {
+        Xa = (double*)malloc((size_t)(m * pa) * sizeof(double));
+        for (int64_t t = 0; t < m; ++t) {
+            for (int64_t i = 0; i < p; ++i) Xa[t * pa + i] = X[t * ldx + i];
+            Xa[t * pa + p] = 1.0;
+        }
+        fa = (uint64_t*)calloc((size_t)((int64_t)q * r * Wa), sizeof(uint64_t));
+        for (int64_t c = 0; c < (int64_t)q * r; ++c) {
+            for (int64_t wd = 0; wd < W; ++wd) fa[c * Wa + wd] = fam[c * W + wd];
+            fa[c * Wa + (p >> 6)] |= 1ull << (p & 63);
+        }
+        Xe = Xa; lde = pa; fe = fa;
+    }
+    const int64_t We = icpt ? Wa : W;
+    double* chosen = (double*)malloc((size_t)B2 * r * pa * sizeof(double));
     int est_status = REF_OK;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(prm->n_threads > 1 ? prm->n_threads : 1)
@@ -538,22 +653,22 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     for (int32_t k = 0; k < B2; ++k) {
         uint32_t* wt = (uint32_t*)malloc((size_t)m * sizeof(uint32_t));
         uint8_t* ev = (uint8_t*)malloc((size_t)m);
-        double* G = (double*)malloc((size_t)(p * p) * sizeof(double));
-        double* Bm = (double*)malloc((size_t)(p * r) * sizeof(double));
-        double* ols = (double*)malloc((size_t)q * r * p * sizeof(double));
+        double* G = (double*)malloc((size_t)(pa * pa) * sizeof(double));
+        double* Bm = (double*)malloc((size_t)(pa * r) * sizeof(double));
+        double* ols = (double*)malloc((size_t)q * r * pa * sizeof(double));
         double* loss = (double*)malloc((size_t)q * sizeof(double));
         int st = ref_estimation_weights(m, prm->block_len, prm->train_frac, prm->split_fixed,
                                         prm->seed, prm->problem_id, k, wt, ev, NULL);
         int32_t n_eval = 0;
         for (int64_t t = 0; t < m; ++t) n_eval += ev[t];
         if (st == REF_OK) {
-            ref_weighted_moments(X, ldx, Y, ldy, m, p, r, wt, G, Bm, NULL);
+            ref_weighted_moments(Xe, lde, Y, ldy, m, pa, r, wt, G, Bm, NULL);
             for (int32_t j = 0; j < q; ++j) {
                 loss[j] = 0.0;
                 for (int64_t e = 0; e < r; ++e) {
                     int64_t col = (int64_t)j * r + e;
-                    double* bj = ols + col * p;
-                    int fb = ref_ols_support(G, Bm + e, r, p, fam + col * W, bj);
+                    double* bj = ols + col * pa;
+                    int fb = ref_ols_support(G, Bm + e, r, pa, fe + col * We, bj);
                     if (fb) {
 #ifdef _OPENMP
 #pragma omp critical
@@ -565,7 +680,7 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                     for (int64_t t = 0; t < m; ++t) {
                         if (!ev[t]) continue;
                         double pred = 0.0;
-                        for (int64_t i = 0; i < p; ++i) pred += X[t * ldx + i] * bj[i];
+                        for (int64_t i = 0; i < pa; ++i) pred += Xe[t * lde + i] * bj[i];
                         double res = Y[t * ldy + e] - pred;
                         le += res * res;
                     }
@@ -575,15 +690,15 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                     if (trace && trace->est_fallback)
                         trace->est_fallback[((int64_t)k * q + j) * r + e] = fb;
                     if (trace && trace->est_beta)
-                        memcpy(trace->est_beta + (((int64_t)k * q + j) * r + e) * p, bj,
-                               (size_t)p * sizeof(double));
+                        memcpy(trace->est_beta + (((int64_t)k * q + j) * r + e) * pa, bj,
+                               (size_t)pa * sizeof(double));
                 }
             }
             /* best model for this bootstrap: argmin over j, ties -> smallest j */
             int32_t jbest = 0;
             for (int32_t j = 1; j < q; ++j) if (loss[j] < loss[jbest]) jbest = j;
-            memcpy(chosen + (int64_t)k * r * p, ols + (int64_t)jbest * r * p,
-                   (size_t)r * p * sizeof(double));
+            memcpy(chosen + (int64_t)k * r * pa, ols + (int64_t)jbest * r * pa,
+                   (size_t)r * pa * sizeof(double));
             if (trace && trace->est_jstar) trace->est_jstar[k] = jbest;
         } else {
 #ifdef _OPENMP
@@ -594,13 +709,14 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         if (trace && trace->eval_count) trace->eval_count[k] = n_eval;
         free(wt); free(ev); free(G); free(Bm); free(ols); free(loss);
     }
+    free(Xa); free(fa);
     if (est_status < 0) { free(lam); free(sup); free(fam); free(chosen); return est_status; }
     if (est_status > status) status = est_status;
 
     /* bagging over the B2 chosen estimates (median or mean, Eq. 4) */
     double* col = (double*)malloc((size_t)B2 * sizeof(double));
-    for (int64_t c = 0; c < r * p; ++c) {
-        for (int32_t k = 0; k < B2; ++k) col[k] = chosen[(int64_t)k * r * p + c];
+    for (int64_t c = 0; c < r * pa; ++c) {
+        for (int32_t k = 0; k < B2; ++k) col[k] = chosen[(int64_t)k * r * pa + c];
         double out;
         if (prm->bagging == 1) {
             double s = 0.0;
@@ -623,12 +739,30 @@ int ref_uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p,
 }
 
 int ref_uoi_var_fit(const double* series, int64_t N, int64_t p, int32_t order,
-                    const ref_params* prm, double* A_out, ref_trace* trace)
+                    const ref_params* prm, double* A_out, double* mu_out, ref_trace* trace)
 {
-    if (order != 1) return REF_ERR_UNSUPPORTED;
-    if (!series || N < 3 || p <= 0) return REF_ERR_INVALID_ARG;
-    /* Eq. 7-8 with d = 1, rows in ascending time: row t pairs the response
-     * X_{t+1} with the regressor X_t (t = 0..N-2).  Row order does not change
+    if (!series || !prm || !A_out || p <= 0 || order < 1) return REF_ERR_INVALID_ARG;
+    if (N - order < 2) return REF_ERR_INVALID_ARG;
+    /* Eq. 7-9: row t - d of the design pairs the response X_t with the
+     * regressors (X_{t-1}, ..., X_{t-d}), t = d..N-1.  Row order does not change
      * any Gram; it fixes which rows a block of the block bootstrap holds. */
-    return ref_uoi_fit(series, p, series + p, p, N - 1, p, p, prm, A_out, trace);
+    const int64_t m = N - order, P = (int64_t)order * p;
+    const int icpt = prm->intercept != 0;
+    const int64_t pa = P + icpt;
+    double* X = (double*)malloc((size_t)(m * P) * sizeof(double));
+    double* Y = (double*)malloc((size_t)(m * p) * sizeof(double));
+    double* beta = (double*)malloc((size_t)(p * pa) * sizeof(double));
+    ref_lagged_design(series, N, p, order, X, Y);
+    int st = ref_uoi_fit(X, P, Y, p, m, P, p, prm, beta, trace);
+    if (st >= 0) {
+        /* Alg. 2: partition beta* into A_1..A_d and mu */
+        for (int32_t j = 0; j < order; ++j)
+            for (int64_t e = 0; e < p; ++e)
+                for (int64_t c = 0; c < p; ++c)
+                    A_out[((int64_t)j * p + e) * p + c] = beta[e * pa + (int64_t)j * p + c];
+        if (mu_out)
+            for (int64_t e = 0; e < p; ++e) mu_out[e] = icpt ? beta[e * pa + P] : 0.0;
+    }
+    free(X); free(Y); free(beta);
+    return st;
 }

@@ -1,5 +1,5 @@
 /*
- * uoi_oracle.h -- FP64 CPU oracle for the UoI_LASSO / UoI_VAR(1) hot path.
+ * uoi_oracle.h -- FP64 CPU oracle for the UoI_LASSO / UoI_VAR(d) hot path.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline leg may load this library.  It shares no code,
@@ -129,6 +129,26 @@ int ref_lasso_admm_batch(const double* X, int64_t ldx, const double* Y, int64_t 
                          const int64_t* eq_list, int64_t r_sel,
                          double* beta_out, int32_t* iters_out, uint8_t* conv_out, double* v_out);
 
+/* LASSO with an unpenalised intercept for one weight vector w (m, NULL = ones):
+ * minimises (1/(2 nk)) sum_t w_t (y_t - mu - x_t^T b)^2 + lambda ||b||_1 per
+ * column.  The optimal mu for any b is ybar_w - xbar_w^T b, so this is the
+ * plain LASSO (ref_lasso_admm_batch, B = 1) of the w-centred data, followed by
+ * mu_out[j*r + e] = ybar_w[e] - xbar_w^T beta_{j,e}.  beta_out: q x r x p;
+ * mu_out, iters_out, conv_out: q x r; v_out: q x r x p (all but beta nullable).
+ * REF_ERR_INVALID_ARG when every weight is zero. */
+int ref_lasso_admm_intercept(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                             int64_t m, int64_t p, int64_t r, const uint32_t* w,
+                             const double* lambdas, int32_t q, double rho, double abs_tol,
+                             double rel_tol, int32_t max_iter, int32_t warm_start,
+                             double* beta_out, double* mu_out, int32_t* iters_out,
+                             uint8_t* conv_out, double* v_out);
+
+/* Lagged design of a VAR(d) (Eq. 7-8) from series (N x p, time ascending),
+ * rows in ascending time: row t - d (t = d..N-1) holds Y = X_t and
+ * X = (X_{t-1}, X_{t-2}, ..., X_{t-d}), lag j in columns (j-1)p .. jp-1.
+ * X: (N-d) x dp, Y: (N-d) x p, both row-major and contiguous. */
+void ref_lagged_design(const double* series, int64_t N, int64_t p, int32_t d, double* X, double* Y);
+
 /* Least squares restricted to the support S (bitset of ceil(p/64) words):
  * beta_S = argmin || W^{1/2} (y - X_S beta) ||, minimum-norm when X_S is rank
  * deficient, zero outside S.  Uses Cholesky of G[S,S] when every pivot exceeds
@@ -152,6 +172,7 @@ typedef struct {
     int32_t split_fixed;       /* 0 per-bootstrap reshuffle, 1 fixed */
     int32_t warm_start;        /* 0 cold, 1 path */
     int32_t n_threads;         /* <= 1: sequential */
+    int32_t intercept;         /* 1: every fit gains an unpenalised offset mu */
 } ref_params;
 
 /* Optional intermediate outputs (every pointer nullable). */
@@ -162,7 +183,7 @@ typedef struct {
     int32_t*  sel_iters;   /* B1 x q x r                           */
     uint8_t*  sel_conv;    /* B1 x q x r                           */
     uint64_t* family;      /* q x r x ceil(p/64)  S_j (Eq. 3)      */
-    double*   est_beta;    /* B2 x q x r x p  OLS on S_j from T^k  */
+    double*   est_beta;    /* B2 x q x r x pa  OLS on S_j from T^k (pa = p + intercept) */
     double*   est_loss;    /* B2 x q x r  held-out squared error sums per equation */
     int32_t*  est_jstar;   /* B2                                   */
     int32_t*  est_fallback;/* B2 x q x r  1 = min-norm fallback    */
@@ -170,9 +191,13 @@ typedef struct {
 } ref_trace;
 
 /* Full UoI fit of r response columns that share the design X (m x p):
- * UoI_LASSO is r = 1 (Alg. 1); UoI_VAR(1) is X = series rows 0..N-2,
- * Y = rows 1..N-1, r = p (Alg. 2 with Eq. 9 solved as p LASSOs).
- * beta_out: r x p (row e = the bagged coefficients of response e). */
+ * UoI_LASSO is r = 1 (Alg. 1); UoI_VAR(d) is the lagged design of Eq. 8 with
+ * r = p (Alg. 2 with Eq. 9 solved as p LASSOs sharing that design).
+ * beta_out: r x pa, pa = p + intercept (row e = the bagged coefficients of
+ * response e, then its intercept when prm->intercept).  With an intercept the
+ * selection fits are ref_lasso_admm_intercept, lambda_max comes from the
+ * unweighted centred data, and the estimation OLS and held-out loss use the
+ * design [X 1] with the ones column in every support. */
 int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                 int64_t m, int64_t p, int64_t r, const ref_params* prm,
                 double* beta_out, ref_trace* trace);
@@ -181,10 +206,13 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
 int ref_uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p,
                       const ref_params* prm, double* beta_out, ref_trace* trace);
 
-/* UoI_VAR(order) (Alg. 2): series N x p, time ascending.  Only order 1 is
- * supported.  A_out[e*p + i] = coefficient of X_{t-1,i} in equation e. */
+/* UoI_VAR(order) (Alg. 2): series N x p, time ascending, order >= 1 and
+ * N - order >= 2.  Fits the lagged design of ref_lagged_design, then
+ * partitions beta* (Alg. 2, last step): A_out (order x p x p),
+ * A_out[(j-1)*p*p + e*p + i] = coefficient of X_{t-j,i} in equation e;
+ * mu_out (p, nullable) = the intercepts, zero when prm->intercept is 0. */
 int ref_uoi_var_fit(const double* series, int64_t N, int64_t p, int32_t order,
-                    const ref_params* prm, double* A_out, ref_trace* trace);
+                    const ref_params* prm, double* A_out, double* mu_out, ref_trace* trace);
 
 #ifdef __cplusplus
 }

@@ -92,6 +92,44 @@ def var_problem(p: int, T: int, density: float, spectral_radius: float, *, seed:
     return VarProblem(np.ascontiguousarray(S[burn_in:]), A, burn_in)
 
 
+@dataclass
+class VarDProblem:
+    series: np.ndarray      # T x p, time ascending
+    A: np.ndarray           # order x p x p, A[j-1] = A_j
+    mu: np.ndarray          # p
+    burn_in: int
+
+
+def var_d_problem(p: int, T: int, order: int, density: float, spectral_radius: float, *, seed: int,
+                  mu_scale: float = 1.0, burn_in: int = 500) -> VarDProblem:
+    """X_t = mu + sum_j A_j X_{t-j} + U_t, U_t ~ N(0, I): each A_j sparse with
+    N(0,1) entries at random positions, then A_j scaled by c^j so that the
+    companion matrix has the requested spectral radius (its eigenvalues scale
+    by exactly c); mu ~ mu_scale * N(0, I)."""
+    g = _rng(seed)
+    nnz = max(1, int(round(density * p * p)))
+    A = np.zeros((order, p * p))
+    for j in range(order):
+        A[j, g.choice(p * p, size=nnz, replace=False)] = g.standard_normal(nnz)
+    A = A.reshape(order, p, p)
+    comp = np.zeros((order * p, order * p))
+    comp[:p] = np.concatenate(list(A), axis=1)
+    comp[p:, :-p] = np.eye((order - 1) * p)
+    rad = float(np.max(np.abs(np.linalg.eigvals(comp))))
+    if rad > 0:
+        c = spectral_radius / rad
+        A *= (c ** np.arange(1, order + 1))[:, None, None]
+    mu = mu_scale * g.standard_normal(p)
+    total = T + burn_in
+    U = g.standard_normal((total, p))
+    S = np.zeros((total, p))
+    for t in range(total):
+        S[t] = mu + U[t]
+        for j in range(1, min(order, t) + 1):
+            S[t] += A[j - 1] @ S[t - j]
+    return VarDProblem(np.ascontiguousarray(S[burn_in:]), A, mu, burn_in)
+
+
 # ----------------------------------------------------------------------------
 # The five workloads (data seed = 1000 + workload number)
 # ----------------------------------------------------------------------------
