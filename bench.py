@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--q", type=int)
     ap.add_argument("--rows", type=int, help="keep only the first ROWS rows of the design")
     ap.add_argument("--streams", type=int, default=4, help="worker streams of the batched workload")
+    ap.add_argument("--order", type=int, default=1, help="VAR workloads: lag order d of the design")
+    ap.add_argument("--intercept", type=int, default=0, choices=[0, 1],
+                    help="VAR workloads: fit the unpenalised intercept mu")
     return ap.parse_args()
 
 
@@ -106,14 +109,18 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------
-def workload(wid):
+def workload(wid, order=1):
     from paper_1808_06992_gb300 import synth
     w = synth.WORKLOADS[wid]
     d = synth.workload_data(wid)
     if w.kind == "lasso":
         X, Y = d.X, d.y.reshape(-1, 1)
     elif w.kind == "var":
-        X, Y = d.series[:-1], d.series[1:]
+        # lagged design of a VAR(order): response X_t, regressors X_{t-1} .. X_{t-order}
+        S = d.series
+        N = S.shape[0]
+        X = np.concatenate([S[order - j:N - j] for j in range(1, order + 1)], axis=1)
+        Y = S[order:]
     else:
         raise ValueError("the batched workload is timed by bench_batch")
     return w, np.ascontiguousarray(X), np.ascontiguousarray(Y)
@@ -124,7 +131,8 @@ def fit_kwargs(w, args):
     return dict(B1=args.B1 or w.B1, B2=args.B2 or w.B2, q=args.q or w.q, block_len=w.block_len,
                 bagging=w.bagging,
                 precision=native.PREC_MIXED if args.precision == "mixed" else native.PREC_FP64,
-                warm_start=native.WARM_PATH if args.warm == "path" else native.WARM_NONE)
+                warm_start=native.WARM_PATH if args.warm == "path" else native.WARM_NONE,
+                intercept=args.intercept if w.kind == "var" else 0)
 
 
 def traffic_per_launch(kernel, applies=True):
@@ -219,7 +227,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w, X, Y = workload(args.workload)
+    from paper_1808_06992_gb300 import synth
+    w, X, Y = workload(args.workload, args.order if synth.WORKLOADS[args.workload].kind == "var" else 1)
     import oracle
     oracle.build_oracle()
     vals = []
@@ -257,13 +266,15 @@ def main():
     native.lib()
     if synth.WORKLOADS[args.workload].kind == "batch":
         return bench_batch(args, torch, rank, world, local, dist)
-    w, X, Y = workload(args.workload)
+    w, X, Y = workload(args.workload, args.order if synth.WORKLOADS[args.workload].kind == "var" else 1)
     if args.rows:
         X, Y = np.ascontiguousarray(X[:args.rows]), np.ascontiguousarray(Y[:args.rows])
     m, p = X.shape
     r = Y.shape[1]
     kw = fit_kwargs(w, args)
     overrides = {k: getattr(args, k) for k in ("B1", "B2", "q", "rows") if getattr(args, k)}
+    if w.kind == "var" and (args.order != 1 or args.intercept):
+        overrides.update(order=args.order, intercept=args.intercept)
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream().cuda_stream

@@ -1,5 +1,5 @@
 /*
- * uoi.h -- C ABI of the GB300 (sm_103a) UoI_LASSO / UoI_VAR(1) hot path.
+ * uoi.h -- C ABI of the GB300 (sm_103a) UoI_LASSO / UoI_VAR(d) hot path.
  *
  * Method: Balasubramanian et al., "Optimizing the Union of Intersections LASSO
  * (UoI_LASSO) and Vector Autoregressive (UoI_VAR) Algorithms for Improved
@@ -46,7 +46,7 @@ extern "C" {
 #define UOI_ERR_CUDA          -4   /* a CUDA runtime call failed                           */
 #define UOI_ERR_OOM           -5   /* device allocation failed                             */
 #define UOI_ERR_TIMEOUT       -6   /* a bounded device loop ran out of iterations          */
-#define UOI_ERR_UNSUPPORTED   -8   /* e.g. VAR order != 1, learned warm start unavailable  */
+#define UOI_ERR_UNSUPPORTED   -8   /* e.g. an intercept on an entry with no output for it  */
 
 /* ---- parameter enums ------------------------------------------------------ */
 #define UOI_BAG_MEDIAN   0   /* coordinate-wise median over the B2 chosen estimates  */
@@ -83,6 +83,9 @@ typedef struct uoi_params {
     int32_t  warm_start;        /* UOI_WARM_*; path                                    */
     const char* mlp_weights_path; /* learned warm start weights, NULL = none           */
     void*    stream;            /* cudaStream_t, NULL = default stream                 */
+    int32_t  intercept;         /* 1 = fit an unpenalised offset mu per response       */
+                                /* (uoi_var_fit and uoi_fit_traced; 0 = none).         */
+                                /* A struct_size that ends before this field reads 0.  */
 } uoi_params;
 
 /* Timings and counters of the last fit (every field written when non-NULL). */
@@ -124,15 +127,16 @@ typedef struct uoi_trace {
     uint64_t* family;       /* q x r x ceil(p/64)  supports S_j (Eq. 3)           */
     double*   est_loss;     /* B2 x q x r  held-out squared-error sums            */
     int32_t*  est_jstar;    /* B2  chosen support index per bootstrap             */
-    double*   est_beta;     /* B2 x r x p  the chosen OLS estimate per bootstrap  */
+    double*   est_beta;     /* B2 x r x pe the chosen OLS estimate per bootstrap, */
+                            /* pe = p + intercept (mu last, original coordinates) */
     int32_t*  est_singular; /* B2 x q x r  1 = regularised fallback               */
 } uoi_trace;
 
 /* Fill *prm with the defaults listed above (B1 = B2 = 20, q = 16). */
 void uoi_params_default(uoi_params* prm);
 
-/* UoI_LASSO (Alg. 1).  X: n x p, y: n.  beta_out: p (the bagged estimate,
- * Alg. 1 "Return").  family_out: q x ceil(p/64) words, bit i of S_j (Eq. 3),
+/* UoI_LASSO (Alg. 1).  X: n x p, y: n.  beta_out: p (the bagged estimate that
+ * Alg. 1 returns); prm->intercept must be 0 (UOI_ERR_UNSUPPORTED).  family_out: q x ceil(p/64) words, bit i of S_j (Eq. 3),
  * nullable.  diag nullable. */
 int uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p,
                   const uoi_params* prm, double* beta_out, uint64_t* family_out,
@@ -156,18 +160,24 @@ int uoi_lasso_fit_batch(int32_t count, const double* const* X, const double* con
                         double* const* beta_out, int32_t* status_out, uoi_diag* diags,
                         int32_t streams);
 
-/* UoI_VAR(order) (Alg. 2).  series: N x p, time ascending (row t = X_t).
- * Only order 1 is supported (else UOI_ERR_UNSUPPORTED).  The lagged design
- * pairs the response X_{t+1} with the regressor X_t (Eq. 7-8, rows in
- * ascending time) and is solved as p LASSOs sharing that design (Eq. 9).
- * A_out: order x p x p, A_out[e*p + i] = coefficient of X_{t-1,i} in
- * equation e (Alg. 2 "Partition ... into A_1 ... A_d").  mu_out: p, the
- * intercept; no intercept is fitted, so it is zero-filled (nullable). */
+/* UoI_VAR(order) (Alg. 2).  series: N x p, time ascending (row t = X_t),
+ * order >= 1, N - order >= 2 (else UOI_ERR_INVALID_ARG).  The lagged design
+ * pairs the response X_t (Eq. 7) with the regressors X_{t-1} .. X_{t-order}
+ * (Eq. 8), rows t = order .. N-1 in ascending time, and is solved as p LASSOs
+ * sharing that design (Eq. 9); a block of the block bootstrap holds block_len
+ * consecutive such rows.  A_out: order x p x p,
+ * A_out[(j-1)*p*p + e*p + i] = coefficient of X_{t-j,i} in equation e (the
+ * last step of Alg. 2 splits beta* into A_1 .. A_d and mu).  mu_out: p
+ * (nullable), the intercepts when prm->intercept = 1 (each fit then has an
+ * unpenalised offset: the LASSO of the bootstrap-weighted centred data in the
+ * selection, [X 1] in the estimation OLS and held-out loss, lambda_max of the
+ * centred data), else zero-filled. */
 int uoi_var_fit(const double* series, int64_t N, int64_t p, int32_t order,
                 const uoi_params* prm, double* A_out, double* mu_out, uoi_diag* diag);
 
 /* General form used by both fits: r response columns Y (m x r, row stride ldy)
- * on the design X (m x p, row stride ldx).  beta_out: r x p.  trace nullable. */
+ * on the design X (m x p, row stride ldx).  beta_out: r x pe, pe = p + 1 when
+ * prm->intercept = 1 (row e: p coefficients, then mu_e) else p.  trace nullable. */
 int uoi_fit_traced(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                    int64_t m, int64_t p, int64_t r, const uoi_params* prm,
                    double* beta_out, uoi_trace* trace, uoi_diag* diag);

@@ -213,11 +213,21 @@ void check_status(DevStatus* st, cudaStream_t s, const char* what)
         throw Error(h.code, std::string(what) + " failed on batch item " + std::to_string(h.where));
 }
 
+// prm->intercept, or 0 for a caller whose struct ends before that field.
+int32_t param_intercept(const uoi_params* prm)
+{
+    if (prm->struct_size != 0 && prm->struct_size < offsetof(uoi_params, intercept) + sizeof(int32_t))
+        return 0;
+    return prm->intercept;
+}
+
 void validate(const uoi_params* prm)
 {
     if (!prm) throw Error(UOI_ERR_INVALID_ARG, "params is NULL");
-    if (prm->struct_size != 0 && prm->struct_size < sizeof(uoi_params))
+    if (prm->struct_size != 0 && prm->struct_size < offsetof(uoi_params, intercept))
         throw Error(UOI_ERR_INVALID_ARG, "uoi_params.struct_size too small");
+    if (param_intercept(prm) != 0 && param_intercept(prm) != 1)
+        throw Error(UOI_ERR_INVALID_ARG, "intercept must be 0 or 1");
     if (prm->B1 <= 0 || prm->B2 <= 0 || prm->q <= 0)
         throw Error(UOI_ERR_INVALID_ARG, "B1, B2 and q must be positive");
     if (!(prm->rho > 0.0)) throw Error(UOI_ERR_INVALID_ARG, "rho must be positive");
@@ -255,18 +265,29 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                     int64_t m, int64_t p, int64_t r, const uint32_t* w, int32_t B,
                     const double* lam, int32_t q, double rho, double abs_tol, double rel_tol,
                     int32_t max_iter, int32_t warm, double* beta, int32_t* iters, uint8_t* conv,
-                    uint64_t* family, cudaStream_t s, StageTimer* tm, int* marks,
+                    uint64_t* family, cudaStream_t s, StageTimer* tm, int* marks, bool icpt,
                     WsModel* ws = nullptr, const float* X32 = nullptr)
 {
     int t0 = tm ? tm->mark() : 0;
     DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
     DevBuf nk(sizeof(double) * B, s);
-    moments(precision, Xd, ldx, Yd, ldy, m, p, r, w, nullptr, B, G.as<double>(), Bm.as<double>(), s, X32);
     if (w) {
         weight_sums(w, nullptr, m, B, nk.as<double>(), s);
     } else {
         const double mm = (double)m;
         UOI_CUDA(cudaMemcpyAsync(nk.ptr, &mm, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    if (icpt) {
+        // moments of [X~ 1] (column p = ones), then the ones coordinate eliminated:
+        // the moments of the bootstrap-weighted centred data
+        const int64_t pa = p + 1;
+        DevBuf Ga(sizeof(double) * (size_t)(B * pa * pa), s), Ba(sizeof(double) * (size_t)(B * pa * r), s);
+        moments(precision, Xd, ldx, Yd, ldy, m, pa, r, w, nullptr, B, Ga.as<double>(), Ba.as<double>(), s,
+                X32);
+        schur_intercept(Ga.as<double>(), Ba.as<double>(), nk.as<double>(), w ? B : 1, p, r, B, G.as<double>(),
+                        Bm.as<double>(), s);
+    } else {
+        moments(precision, Xd, ldx, Yd, ldy, m, p, r, w, nullptr, B, G.as<double>(), Bm.as<double>(), s, X32);
     }
     int t1 = tm ? tm->mark() : 0;
     DevBuf st(sizeof(DevStatus), s);
@@ -403,6 +424,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     const int32_t B1 = prm->B1, B2 = prm->B2, q = prm->q;
     const int64_t W = (p + 63) / 64;
     const bool mixed = prm->precision == UOI_PREC_MIXED;
+    const bool tc_moments = mixed && gram_tc_available();   // one decision for the whole fit
 
     // inputs (the VAR series is copied once; X and Y are views into it)
     DevBuf hx, hy;
@@ -427,6 +449,24 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         if (h) throw Error(UOI_ERR_NONFINITE, "X or Y holds NaN or Inf");
     }
     const PhiloxKey key{ prm->seed, prm->problem_id };
+
+    // intercept: the design centred by its column means with a ones column
+    // appended (index p), the responses centred; xbar, ybar map mu back
+    const bool icpt = param_intercept(prm) != 0;
+    const int64_t pe = p + (icpt ? 1 : 0);            // estimation coordinates
+    DevBuf xa, ya, xbar, ybar;
+    if (icpt) {
+        xa.alloc(sizeof(double) * (size_t)(m * pe), s);
+        ya.alloc(sizeof(double) * (size_t)(m * r), s);
+        xbar.alloc(sizeof(double) * (size_t)p, s);
+        ybar.alloc(sizeof(double) * (size_t)r, s);
+        center_with_ones(Xd, ldx, Yd, ldy, m, p, r, xa.as<double>(), ya.as<double>(), xbar.as<double>(),
+                         ybar.as<double>(), s);
+        Xd = xa.as<double>();
+        ldx = pe;
+        Yd = ya.as<double>();
+        ldy = r;
+    }
 
     // lambda grid
     DevBuf lam(sizeof(double) * q, s), lam_hold;
@@ -459,50 +499,59 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
                                                                   : prm->warm_start;
     // mixed form: one FP32 copy of X feeds every tensor-core moment pass
     DevBuf X32;
-    if (mixed && gram_tc_available()) {
+    if (tc_moments) {
         X32.alloc(sizeof(float) * (size_t)(m * ldx), s);
-        to_f32(Xd, ldx, m, p, X32.as<float>(), s);
+        to_f32(Xd, ldx, m, pe, X32.as<float>(), s);
     }
     if (mixed)
         selection_admm<float>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                               lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                               prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, ws,
+                              conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, icpt, ws,
                               X32.ptr ? X32.as<float>() : nullptr);
     else
         selection_admm<double>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                                lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                                prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, ws);
+                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, icpt, ws);
     family_mask_tail(fam.as<uint64_t>(), q * r, p, s);
     const int t_sel2 = tm.mark();
 
     // ---- estimation ----
+    // with an intercept every support also holds the ones column (index p)
+    DevBuf fam_e;
+    const uint64_t* fe = fam.as<uint64_t>();
+    if (icpt) {
+        const int64_t We = (pe + 63) / 64;
+        fam_e.alloc(sizeof(uint64_t) * (size_t)(q * r * We), s);
+        family_add_bit(fam.as<uint64_t>(), q * r, W, We, p, fam_e.as<uint64_t>(), s);
+        fe = fam_e.as<uint64_t>();
+    }
     DevBuf west(sizeof(uint32_t) * (size_t)(B2 * m), s), evm((size_t)(B2 * m), s);
     estimation_weights(m, prm->block_len, prm->train_frac, prm->split_mode, key, B2,
                        west.as<uint32_t>(), evm.as<uint8_t>(), s);
-    DevBuf Gt(sizeof(double) * (size_t)(B2 * p * p), s), Bt(sizeof(double) * (size_t)(B2 * p * r), s);
-    DevBuf Ge(sizeof(double) * (size_t)(B2 * p * p), s), Be(sizeof(double) * (size_t)(B2 * p * r), s);
+    DevBuf Gt(sizeof(double) * (size_t)(B2 * pe * pe), s), Bt(sizeof(double) * (size_t)(B2 * pe * r), s);
+    DevBuf Ge(sizeof(double) * (size_t)(B2 * pe * pe), s), Be(sizeof(double) * (size_t)(B2 * pe * r), s);
     DevBuf yye(sizeof(double) * (size_t)(B2 * r), s);
-    if (mixed && gram_tc_available()) {
+    if (tc_moments) {
         // OLS on S_j only touches features in the union U of the family, so the
         // estimation moments are formed on U alone.
-        DevBuf ucols(sizeof(int32_t) * (size_t)p, s);
-        const int32_t nu = union_columns(fam.as<uint64_t>(), q * r, p, ucols.as<int32_t>(), s);
+        DevBuf ucols(sizeof(int32_t) * (size_t)pe, s);
+        const int32_t nu = union_columns(fe, q * r, pe, ucols.as<int32_t>(), s);
         if (nu > 0) {
             // the design restricted to U once, so both passes read contiguous rows
             DevBuf Xu(sizeof(float) * (size_t)(m * nu), s);
             gather_cols_f32(X32.as<float>(), ldx, m, ucols.as<int32_t>(), nu, Xu.as<float>(), s);
-            moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), west.as<uint32_t>(),
+            moments_tc_cols(Xd, ldx, Yd, ldy, m, pe, r, nu, ucols.as<int32_t>(), west.as<uint32_t>(),
                             nullptr, B2, Gt.as<double>(), Bt.as<double>(), s, Xu.as<float>(), nu, true);
-            moments_tc_cols(Xd, ldx, Yd, ldy, m, p, r, nu, ucols.as<int32_t>(), nullptr,
+            moments_tc_cols(Xd, ldx, Yd, ldy, m, pe, r, nu, ucols.as<int32_t>(), nullptr,
                             evm.as<uint8_t>(), B2, Ge.as<double>(), Be.as<double>(), s, Xu.as<float>(), nu,
                             true);
         }
     } else {
-        moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, west.as<uint32_t>(), nullptr, B2,
+        moments(prm->precision, Xd, ldx, Yd, ldy, m, pe, r, west.as<uint32_t>(), nullptr, B2,
                 Gt.as<double>(), Bt.as<double>(), s);
-        moments(prm->precision, Xd, ldx, Yd, ldy, m, p, r, nullptr, evm.as<uint8_t>(), B2,
+        moments(prm->precision, Xd, ldx, Yd, ldy, m, pe, r, nullptr, evm.as<uint8_t>(), B2,
                 Ge.as<double>(), Be.as<double>(), s);
     }
     masked_sumsq(Yd, ldy, m, r, evm.as<uint8_t>(), B2, yye.as<double>(), s);
@@ -514,15 +563,18 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     if (!losses) { loss_b.alloc(sizeof(double) * (size_t)(B2 * q * r), s); losses = loss_b.as<double>(); }
     DevBuf sing(sizeof(int32_t) * (size_t)(B2 * q * r), s);
     int64_t n_ols64 = ols_losses(Gt.as<double>(), Bt.as<double>(), Ge.as<double>(), Be.as<double>(), yye.as<double>(),
-               fam.as<uint64_t>(), p, r, q, B2, losses, sing.as<int32_t>(), s);
+               fe, pe, r, q, B2, losses, sing.as<int32_t>(), s);
     DevBuf jst(sizeof(int32_t) * B2, s);
     loss_argmin(losses, B2, q, r, jst.as<int32_t>(), s);
-    DevBuf chosen(sizeof(double) * (size_t)(B2 * r * p), s);
-    n_ols64 += ols_chosen(Gt.as<double>(), Bt.as<double>(), fam.as<uint64_t>(), jst.as<int32_t>(), p, r, q, B2,
+    DevBuf chosen(sizeof(double) * (size_t)(B2 * r * pe), s);
+    n_ols64 += ols_chosen(Gt.as<double>(), Bt.as<double>(), fe, jst.as<int32_t>(), pe, r, q, B2,
                chosen.as<double>(), s);
+    if (icpt)
+        intercept_to_original(chosen.as<double>(), (int64_t)B2 * r, r, p, xbar.as<double>(), ybar.as<double>(),
+                              s);
     DevOut<double> bo;
-    bo.init(beta_out, (size_t)(r * p), s);
-    bagging(chosen.as<double>(), B2, r * p, prm->bagging, bo.dev, s);
+    bo.init(beta_out, (size_t)(r * pe), s);
+    bagging(chosen.as<double>(), B2, r * pe, prm->bagging, bo.dev, s);
     const int t_end = tm.mark();
 
     // ---- outputs ----
@@ -540,7 +592,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         copy_out(tr->sel_conv, conv_b.ptr, (size_t)ncol);
         copy_out(tr->family, fam.ptr, sizeof(uint64_t) * (size_t)(q * r * W));
         copy_out(tr->est_jstar, jst.ptr, sizeof(int32_t) * B2);
-        copy_out(tr->est_beta, chosen.ptr, sizeof(double) * (size_t)(B2 * r * p));
+        copy_out(tr->est_beta, chosen.ptr, sizeof(double) * (size_t)(B2 * r * pe));
         copy_out(tr->est_singular, sing.ptr, sizeof(int32_t) * (size_t)(B2 * q * r));
         sel_beta.finish(s);
         loss_o.finish(s);
@@ -646,6 +698,8 @@ int uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p, const 
                   double* beta_out, uint64_t* family_out, uoi_diag* diag)
 {
     return guarded([&] {
+        if (prm && param_intercept(prm))
+            throw Error(UOI_ERR_UNSUPPORTED, "uoi_lasso_fit has no output for an intercept (use uoi_fit_traced)");
         uoi_trace tr;
         std::memset(&tr, 0, sizeof(tr));
         tr.family = family_out;
@@ -663,6 +717,8 @@ int uoi_lasso_fit_batch(int32_t count, const double* const* X, const double* con
         if (!X || !y || !n || !p || !prm || !beta_out)
             throw uoi::Error(UOI_ERR_INVALID_ARG, "NULL array argument");
         if (prm->lambdas) throw uoi::Error(UOI_ERR_INVALID_ARG, "a batch takes each problem's own lambda grid");
+        if (uoi::param_intercept(prm))
+            throw uoi::Error(UOI_ERR_UNSUPPORTED, "the batch has no output for an intercept");
         uoi::validate(prm);
         int dev = 0;
         UOI_CUDA(cudaGetDevice(&dev));
@@ -718,18 +774,41 @@ int uoi_var_fit(const double* series, int64_t N, int64_t p, int32_t order, const
                 double* A_out, double* mu_out, uoi_diag* diag)
 {
     return guarded([&] {
-        if (order != 1) throw Error(UOI_ERR_UNSUPPORTED, "only VAR order 1 is implemented");
-        if (!series || !A_out) throw Error(UOI_ERR_INVALID_ARG, "NULL data pointer");
-        if (N < 3 || p <= 0) throw Error(UOI_ERR_INVALID_ARG, "need N >= 3 and p > 0");
-        // Eq. 7-8 with d = 1, ascending time: row t regresses X_{t+1} on X_t.
-        const int st = fit_core(series, p, series + p, p, N - 1, p, p, prm, A_out, nullptr, diag,
-                                series, N * p);
-        if (mu_out) {
-            cudaStream_t s = (cudaStream_t)prm->stream;
-            if (is_device_ptr(mu_out)) UOI_CUDA(cudaMemsetAsync(mu_out, 0, sizeof(double) * p, s));
-            else std::memset(mu_out, 0, sizeof(double) * p);
-            UOI_CUDA(cudaStreamSynchronize(s));
+        if (!series || !A_out || !prm) throw Error(UOI_ERR_INVALID_ARG, "NULL data pointer");
+        if (order < 1) throw Error(UOI_ERR_INVALID_ARG, "VAR order must be >= 1");
+        if (p <= 0 || N - order < 2) throw Error(UOI_ERR_INVALID_ARG, "need N - order >= 2 and p > 0");
+        validate(prm);
+        cudaStream_t s = (cudaStream_t)prm->stream;
+        const bool icpt = param_intercept(prm) != 0;
+        if (order == 1 && !icpt) {
+            // Eq. 7-8 with d = 1, ascending time: row t regresses X_{t+1} on X_t; the
+            // design and the responses are views of one device copy of the series.
+            const int st = fit_core(series, p, series + p, p, N - 1, p, p, prm, A_out, nullptr, diag,
+                                    series, N * p);
+            if (mu_out) {
+                if (is_device_ptr(mu_out)) UOI_CUDA(cudaMemsetAsync(mu_out, 0, sizeof(double) * p, s));
+                else std::memset(mu_out, 0, sizeof(double) * p);
+                UOI_CUDA(cudaStreamSynchronize(s));
+            }
+            return st;
         }
+        ensure_pool();
+        // Eq. 7-8: rows t = order..N-1 of (X_t ; X_{t-1} .. X_{t-order}) built on the device
+        const int64_t m = N - order, P = (int64_t)order * p, pe = P + (icpt ? 1 : 0);
+        DevBuf hs;
+        const double* sd = dev_in(series, (size_t)(N * p), hs, s);
+        DevBuf X(sizeof(double) * (size_t)(m * P), s), Y(sizeof(double) * (size_t)(m * p), s);
+        lagged_design(sd, N, p, order, X.as<double>(), P, Y.as<double>(), p, s);
+        DevBuf beta(sizeof(double) * (size_t)(p * pe), s);
+        const int st = fit_core(X.as<double>(), P, Y.as<double>(), p, m, P, p, prm, beta.as<double>(), nullptr,
+                                diag);
+        DevOut<double> ao, mo;
+        ao.init(A_out, (size_t)(order * p * p), s);
+        mo.init(mu_out, (size_t)p, s);
+        partition_var(beta.as<double>(), p, order, icpt ? 1 : 0, ao.dev, mo.dev, s);
+        ao.finish(s);
+        mo.finish(s);
+        UOI_CUDA(cudaStreamSynchronize(s));
         return st;
     });
 }
@@ -773,11 +852,11 @@ int lasso_admm_batch(const double* X, const double* Y, int64_t n, int64_t p, int
         if (precision == UOI_PREC_MIXED)
             selection_admm<float>(precision, Xd, p, Yd, r, n, p, r, wd, B, ld, q, rho, abs_tol,
                                   rel_tol, max_iter, warm_start, bo.dev, it_d, cv_d, nullptr, s,
-                                  nullptr, nullptr);
+                                  nullptr, nullptr, false);
         else
             selection_admm<double>(precision, Xd, p, Yd, r, n, p, r, wd, B, ld, q, rho, abs_tol,
                                    rel_tol, max_iter, warm_start, bo.dev, it_d, cv_d, nullptr, s,
-                                   nullptr, nullptr);
+                                   nullptr, nullptr, false);
         bo.finish(s);
         io.finish(s);
         co.finish(s);

@@ -196,6 +196,31 @@ void ws_consistent_dual(const double* G, const double* Bm, const double* nk, con
 void ws_save(WsModel* M, const char* path);
 WsModel* ws_load(const char* path, cudaStream_t s);
 
+// ---- VAR(d) lagged design and the intercept (design.cu) ------------------------------
+// Rows t - d, t = d..N-1, of Eq. 7-8 from the series S (N x p, time ascending):
+// Y[i, :] = X_t, X[i, (j-1)p .. jp-1] = X_{t-j}, j = 1..d.
+void lagged_design(const double* S, int64_t N, int64_t p, int32_t d, double* X, int64_t ldx,
+                   double* Y, int64_t ldy, cudaStream_t s);
+// xbar, ybar = unweighted column means of X (m x p) and Y (m x r); Xa (m x (p+1),
+// contiguous) = [X - xbar, 1], Ya (m x r, contiguous) = Y - ybar.
+void center_with_ones(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
+                      int64_t r, double* Xa, double* Ya, double* xbar, double* ybar, cudaStream_t s);
+// Eliminates the ones coordinate (index p) from the (p+1)-column moments Ga, Ba of
+// each of the B items: G = Ga[:p,:p] - g g^T / n_k, Bm = Ba[:p,:] - g Ba[p,:] / n_k,
+// g = Ga[:p, p].  nk holds nk_count values (1 = shared by all items).
+void schur_intercept(const double* Ga, const double* Ba, const double* nk, int nk_count, int64_t p,
+                     int64_t r, int32_t B, double* G, double* Bm, cudaStream_t s);
+// out (count x Wa words) = fam (count x W words) with bit `bit` set in every member.
+void family_add_bit(const uint64_t* fam, int64_t count, int64_t W, int64_t Wa, int64_t bit,
+                    uint64_t* out, cudaStream_t s);
+// chosen: count rows of p + 1 (coefficients, then the intercept of the centred
+// data); row c's intercept becomes ybar[c % r] + mu~ - xbar^T b.
+void intercept_to_original(double* chosen, int64_t count, int64_t r, int64_t p, const double* xbar,
+                           const double* ybar, cudaStream_t s);
+// A (d x p x p), mu (p, nullable) from beta (p rows of d p + icpt): Alg. 2's partition.
+void partition_var(const double* beta, int64_t p, int32_t d, int icpt, double* A, double* mu,
+                   cudaStream_t s);
+
 // ---- G5/G6/G7: supports, OLS, loss, bagging (estimate.cu) -----------------------------
 void family_init(uint64_t* fam, int64_t words, cudaStream_t s);
 // Union of all family supports as an increasing column list; returns its size.

@@ -32,7 +32,7 @@ class UoiParams(C.Structure):
         ("train_frac", C.c_double), ("seed", C.c_uint64), ("problem_id", C.c_uint64),
         ("block_len", C.c_int64), ("bagging", C.c_int32), ("split_mode", C.c_int32),
         ("precision", C.c_int32), ("warm_start", C.c_int32), ("mlp_weights_path", C.c_char_p),
-        ("stream", C.c_void_p),
+        ("stream", C.c_void_p), ("intercept", C.c_int32),
     ]
 
 
@@ -165,7 +165,7 @@ def _empty(like, shape, dtype):
 def make_params(B1=20, B2=20, q=16, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol=1e-6,
                 rel_tol=1e-6, max_iter=1000, train_frac=0.8, seed=0, problem_id=0, block_len=0,
                 bagging=BAG_MEDIAN, split_mode=SPLIT_PER_BOOTSTRAP, precision=PREC_FP64,
-                warm_start=WARM_PATH, stream=None, mlp_weights_path=None):
+                warm_start=WARM_PATH, stream=None, mlp_weights_path=None, intercept=0):
     prm = UoiParams()
     lib().uoi_params_default(C.byref(prm))
     prm.B1, prm.B2, prm.q = B1, B2, q
@@ -179,13 +179,15 @@ def make_params(B1=20, B2=20, q=16, lambdas=None, lambda_min_ratio=1e-3, rho=1.0
     prm.block_len, prm.bagging, prm.split_mode = block_len, bagging, split_mode
     prm.precision, prm.warm_start = precision, warm_start
     prm.stream = stream
+    prm.intercept = int(intercept)
     if mlp_weights_path:
         prm.mlp_weights_path = mlp_weights_path.encode()
     return prm, keep
 
 
 def uoi_fit_traced(X, Y, trace=True, **kw):
-    """General fit of Y (m x r) on X (m x p); returns dict(beta, status, diag, trace...)."""
+    """General fit of Y (m x r) on X (m x p); returns dict(beta, status, diag, trace...).
+    beta and est_beta hold p + 1 values per response with intercept=1 (mu last)."""
     X = _prep(X, np.float64)
     Y = _prep(Y, np.float64)
     if Y.ndim == 1:
@@ -195,7 +197,8 @@ def uoi_fit_traced(X, Y, trace=True, **kw):
     prm, keep = make_params(**kw)
     B1, B2, q = prm.B1, prm.B2, prm.q
     W = (p + 63) // 64
-    beta = _empty(X, (r, p), np.float64)
+    pe = p + (1 if prm.intercept else 0)
+    beta = _empty(X, (r, pe), np.float64)
     out = {}
     tr = None
     if trace:
@@ -204,7 +207,7 @@ def uoi_fit_traced(X, Y, trace=True, **kw):
                       sel_beta=((B1, q, r, p), np.float64), sel_iters=((B1, q, r), np.int32),
                       sel_conv=((B1, q, r), np.uint8), family=((q, r, W), np.uint64),
                       est_loss=((B2, q, r), np.float64), est_jstar=((B2,), np.int32),
-                      est_beta=((B2, r, p), np.float64), est_singular=((B2, q, r), np.int32))
+                      est_beta=((B2, r, pe), np.float64), est_singular=((B2, q, r), np.int32))
         tr = UoiTrace()
         for name, (shape, dt) in shapes.items():
             out[name] = _empty(X, shape, dt)
@@ -265,7 +268,7 @@ def uoi_var_fit(series, order=1, **kw):
     S = _prep(series, np.float64)
     N, p = S.shape
     prm, keep = make_params(**kw)
-    A = _empty(S, (order, p, p), np.float64)
+    A = _empty(S, (max(int(order), 1), p, p), np.float64)
     mu = _empty(S, (p,), np.float64)
     diag = UoiDiag()
     diag.struct_size = C.sizeof(UoiDiag)

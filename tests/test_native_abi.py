@@ -71,10 +71,29 @@ def test_invalid_parameters_rejected_on_host(kw, code):
     assert ei.value.status == code
 
 
-def test_var_order_unsupported():
+@pytest.mark.parametrize("N,order", [(10, 0), (10, -1), (4, 3), (2, 1)])
+def test_var_order_and_length_rejected(N, order):
+    # rejected before any device work: order >= 1 and N - order >= 2
     with pytest.raises(native.UoiError) as ei:
-        native.uoi_var_fit(np.zeros((10, 3)), order=2, B1=2, B2=2, q=2)
+        native.uoi_var_fit(np.zeros((N, 3)), order=order, B1=2, B2=2, q=2)
+    assert ei.value.status == native.ERR_INVALID_ARG
+
+
+def test_intercept_argument_checks():
+    # only 0/1, and only on entries that have an output for mu
+    with pytest.raises(native.UoiError) as ei:
+        native.uoi_var_fit(np.zeros((10, 3)), order=2, B1=2, B2=2, q=2, intercept=2)
+    assert ei.value.status == native.ERR_INVALID_ARG
+    with pytest.raises(native.UoiError) as ei:
+        native.uoi_lasso_fit(np.zeros((10, 3)), np.zeros(10), B1=2, B2=2, q=2, intercept=1)
     assert ei.value.status == native.ERR_UNSUPPORTED
+
+
+def test_params_struct_matches_header():
+    # the binding's struct ends with the intercept field, as uoi.h declares it
+    prm, _ = native.make_params()
+    assert prm.struct_size == C.sizeof(native.UoiParams)
+    assert native.UoiParams.intercept.offset + 4 <= C.sizeof(native.UoiParams)
 
 
 def test_null_pointer_rejected():
