@@ -421,16 +421,16 @@ __global__ void k_mirror(double* G, int64_t p_out, const int32_t* colmap, int32_
 
 bool gram_tc_available()
 {
-    static int avail = -1;
-    if (avail < 0) {
+    // decided once per process; the initialisation of a function-local static is
+    // thread-safe, so concurrent first callers (batch workers) all see one answer
+    static const bool avail = [] {
         int dev = 0, major = 0, minor = 0;
-        avail = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
-            avail = (major == 10 && minor == 3 && tc::encode_fn() != nullptr) ? 1 : 0;
-    }
-    return avail == 1;
+        return cudaGetDevice(&dev) == cudaSuccess &&
+               cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+               cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess &&
+               major == 10 && minor == 3 && tc::encode_fn() != nullptr;
+    }();
+    return avail;
 }
 
 // Tensor-core moments for B items (weights w or 0/1 mask, or unweighted),
