@@ -9,8 +9,11 @@
 //         = y_E'y_E - 2 beta' (X_E'y_E)_S + beta' G^E_k[S,S] beta
 // j*_k = argmin_j sum_e L_kje (ties -> smallest j); beta*_e = median (or mean)
 // over k of the chosen estimates (zero outside the support).
-// Singular supports (a Cholesky pivot <= 1e-12 max diag) are refit with a
-// 1e-10 max-diag ridge and flagged.
+// Singular supports (a Cholesky pivot <= 1e-12 max diag) are solved as the
+// paper states OLS, the LASSO ADMM at lambda = 0: with no threshold z = x and
+// u stays 0, so the iteration is x_{t+1} = (G + rho I)^{-1} (b + rho x_t) from
+// x_0 = 0, whose iterates stay in the range of G and converge to the
+// minimum-norm least-squares solution; they are flagged.
 #include <algorithm>
 #include <vector>
 
@@ -22,6 +25,12 @@ namespace {
 
 constexpr int OLS_SMEM_MAX = 160;   // supports up to this size factor in shared memory (FP64 path)
 constexpr int OLS_SMALL = 128;      // mixed path: supports up to this size form the small class
+// ADMM at lambda = 0 for singular supports: rho relative to the largest diagonal
+// (directions with eigenvalue >> rho converge in a few steps), the stopping
+// test on the relative change, and the iteration cap.
+constexpr double OLS_PROX_RHO = 1e-6;
+constexpr double OLS_PROX_TOL = 1e-14;
+constexpr int OLS_PROX_MAX = 500;
 
 struct OlsArgs {
     const double* Gt; const double* Bt;      // B2 x p x p, B2 x p x r
@@ -57,10 +66,13 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int* idx = reinterpret_cast<int*>(smem_raw);                         // p ints
     double* bs = reinterpret_cast<double*>(smem_raw + sizeof(int) * ((a.smax + 1) & ~1));
-    double* red = bs + a.smax + 1;                                       // 32 doubles
+    double* xs = bs + a.smax + 1;                                        // solution
+    double* ws = xs + a.smax + 1;                                        // work vector
+    double* red = ws + a.smax + 1;                                       // 32 doubles
     double* Gs = a.use_smem ? red + 32 : a.scratch + (size_t)blockIdx.x * a.smax * a.smax;
     __shared__ int s_count;
     __shared__ int s_bad;
+    __shared__ int s_done;
     __shared__ double s_dmax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -88,7 +100,7 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
         const int s = s_count;
         const double* Gk = a.Gt + (size_t)k * a.pu * a.pu;
         const double* Bk = a.Bt + (size_t)k * a.pu * a.r;
-        double ridge = 0.0;
+        double ridge = 0.0;                   // rho of the lambda = 0 ADMM (0: plain solve)
         for (int attempt = 0; attempt < 2 && s > 0; ++attempt) {
             double dm = 0.0;
             for (int x = threadIdx.x; x < s * s; x += blockDim.x) {
@@ -128,31 +140,59 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
                 __syncthreads();
             }
             if (!s_bad) break;
-            ridge = 1e-10 * s_dmax;           // regularised fallback, flagged
+            ridge = OLS_PROX_RHO * s_dmax;    // factor G + rho I for the lambda = 0 ADMM
             __syncthreads();
         }
         const bool singular = s > 0 && ridge > 0.0;
-        // forward / back substitution by warp 0
-        if (warp == 0 && s > 0) {
-            for (int i = 0; i < s; ++i) {
-                double acc = 0.0;
-                for (int c = lane; c < i; c += 32) acc += Gs[i * s + c] * bs[c];
-                acc = warp_sum(acc);
-                if (lane == 0) bs[i] = (bs[i] - acc) / Gs[i * s + i];
-                __syncwarp();
+        // x = (G + rho I)^{-1} (b + rho x): once with rho = 0 (plain Cholesky solve),
+        // else the lambda = 0 ADMM iterations from x = 0
+        for (int x = threadIdx.x; x < s; x += blockDim.x) xs[x] = 0.0;
+        for (int itp = 0; s > 0; ++itp) {
+            for (int x = threadIdx.x; x < s; x += blockDim.x) ws[x] = bs[x] + ridge * xs[x];
+            __syncthreads();
+            // forward / back substitution by warp 0
+            if (warp == 0) {
+                for (int i = 0; i < s; ++i) {
+                    double acc = 0.0;
+                    for (int c = lane; c < i; c += 32) acc += Gs[i * s + c] * ws[c];
+                    acc = warp_sum(acc);
+                    if (lane == 0) ws[i] = (ws[i] - acc) / Gs[i * s + i];
+                    __syncwarp();
+                }
+                for (int i = s - 1; i >= 0; --i) {
+                    double acc = 0.0;
+                    for (int c = i + 1 + lane; c < s; c += 32) acc += Gs[c * s + i] * ws[c];
+                    acc = warp_sum(acc);
+                    if (lane == 0) ws[i] = (ws[i] - acc) / Gs[i * s + i];
+                    __syncwarp();
+                }
             }
-            for (int i = s - 1; i >= 0; --i) {
-                double acc = 0.0;
-                for (int c = i + 1 + lane; c < s; c += 32) acc += Gs[c * s + i] * bs[c];
-                acc = warp_sum(acc);
-                if (lane == 0) bs[i] = (bs[i] - acc) / Gs[i * s + i];
-                __syncwarp();
+            __syncthreads();
+            double dmx = 0.0, xmx = 0.0;
+            for (int x = threadIdx.x; x < s; x += blockDim.x) {
+                dmx = fmax(dmx, fabs(ws[x] - xs[x]));
+                xmx = fmax(xmx, fabs(ws[x]));
+                xs[x] = ws[x];
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dmx = fmax(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+                xmx = fmax(xmx, __shfl_xor_sync(0xffffffffu, xmx, o));
+            }
+            if (lane == 0) { red[warp] = dmx; red[8 + warp] = xmx; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double d = 0.0, xm = 0.0;
+                for (int w = 0; w < 8; ++w) { d = fmax(d, red[w]); xm = fmax(xm, red[8 + w]); }
+                s_done = (!singular || d <= OLS_PROX_TOL * xm || itp + 1 >= OLS_PROX_MAX) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_done) break;
         }
         __syncthreads();
         if (a.jstar) {
             double* out = a.chosen + ((size_t)k * a.r + e) * a.p;
-            for (int x = threadIdx.x; x < s; x += blockDim.x) out[a.ucols[idx[x]]] = bs[x];
+            for (int x = threadIdx.x; x < s; x += blockDim.x) out[a.ucols[idx[x]]] = xs[x];
         } else {
             // held-out loss via the evaluation moments
             const double* Gek = a.Ge + (size_t)k * a.pu * a.pu;
@@ -160,10 +200,10 @@ __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
             double part = 0.0;
             for (int x = threadIdx.x; x < s * s; x += blockDim.x) {
                 const int r0 = x / s, c0 = x % s;
-                part += bs[r0] * Gek[(size_t)idx[r0] * a.pu + idx[c0]] * bs[c0];
+                part += xs[r0] * Gek[(size_t)idx[r0] * a.pu + idx[c0]] * xs[c0];
             }
             for (int x = threadIdx.x; x < s; x += blockDim.x)
-                part -= 2.0 * bs[x] * Bek[(size_t)idx[x] * a.r + e];
+                part -= 2.0 * xs[x] * Bek[(size_t)idx[x] * a.r + e];
             part = warp_sum(part);
             __syncthreads();
             if (lane == 0) red[warp] = part;
@@ -646,7 +686,7 @@ int32_t family_support_max(const OlsArgs& a, cudaStream_t s)
 void launch_ols_fp64(OlsArgs a, cudaStream_t s)
 {
     a.use_smem = a.smax <= OLS_SMEM_MAX;
-    size_t smem = sizeof(int) * ((a.smax + 1) & ~1) + sizeof(double) * (a.smax + 1 + 32);
+    size_t smem = sizeof(int) * ((a.smax + 1) & ~1) + sizeof(double) * (3 * (a.smax + 1) + 32);
     DevBuf scratch;
     int grid = (int)std::min<int64_t>(a.solves, 152 * 8);
     if (a.use_smem) {

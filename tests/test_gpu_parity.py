@@ -247,9 +247,10 @@ def test_mixed_tensor_core_xupdate_vs_oracle(warm):
 def test_ols_duplicate_column_goes_to_fp64_factor(prec):
     # With an exact duplicate column every support holding both copies is singular:
     # the FP32-factor solver must refuse it (pivot far below 1e-3 of the largest
-    # diagonal) and hand it to the FP64 factor, which flags it and refits with the
-    # ridge.  Supports without the pair stay on the refined FP32 factor and agree
-    # with the oracle's FP64 Cholesky to FP64 rounding (FP64 form).
+    # diagonal) and hand it to the FP64 factor, which flags it and solves it by the
+    # ADMM at lambda = 0 (the minimum-norm solution: the pair shares the weight).
+    # Supports without the pair stay on the refined FP32 factor and agree with the
+    # oracle's FP64 Cholesky to FP64 rounding (FP64 form).
     d = synth.lasso_problem(500, 20, 6, seed=21, sigma=0.5)
     X = d.X.copy()
     X[:, 1] = X[:, 0]
@@ -268,10 +269,17 @@ def test_ols_duplicate_column_goes_to_fp64_factor(prec):
         sing = gpu["est_singular"][:, :, 0].astype(bool)
         np.testing.assert_array_equal(sing, np.broadcast_to(pair, sing.shape))
         ref = oracle.uoi_lasso_fit(X, d.y, **kw)
-        if np.array_equal(bits_to_bool(ref["family"], 20), bits_to_bool(gpu["family"], 20)):
-            ok = ~pair
-            np.testing.assert_allclose(gpu["est_loss"][:, ok, 0], ref["est_loss"][:, ok, 0],
-                                       rtol=1e-9, atol=1e-12)
+        assert np.array_equal(bits_to_bool(ref["family"], 20), bits_to_bool(gpu["family"], 20))
+        # every loss (singular supports included: the duplicates agree on every row)
+        np.testing.assert_allclose(gpu["est_loss"], ref["est_loss"], rtol=1e-9, atol=1e-12)
+        np.testing.assert_array_equal(gpu["est_jstar"], ref["est_jstar"])
+        # chosen estimates, singular or not, against the oracle's minimum-norm solutions
+        for k in range(3):
+            want = ref["est_beta"][k, ref["est_jstar"][k], 0]
+            assert rel_l2(gpu["est_beta"][k, 0], want) <= 1e-9
+            if pair[ref["est_jstar"][k]]:
+                assert abs(gpu["est_beta"][k, 0, 0] - gpu["est_beta"][k, 0, 1]) <= 1e-8 * abs(want[0])
+        assert rel_l2(gpu["beta"], ref["beta"]) <= 1e-9
 
 
 def test_mixed_tensor_core_inverse_vs_oracle():
