@@ -103,6 +103,12 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
     return d;
 }
 
+// kind::f16 instruction descriptor, fp16 x fp16 -> f32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // kind::f16 instruction descriptor: bf16 x bf16 -> f32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 {
@@ -216,16 +222,18 @@ inline CUtensorMap make_map_bf16_blocks(void* base, int64_t nblocks, int depth)
     return m;
 }
 
-// 64-byte-swizzle variants: k tiles of 32 bf16 (rows of 64 B).
+// 64-byte-swizzle variants: k tiles of 32 16-bit values (rows of 64 B); dt is
+// the 16-bit element type (bf16 or fp16: the copy is the same bytes).
 inline CUtensorMap make_map_bf16_k32(void* base, int64_t k_extent, int64_t rows, int64_t depth,
-                                     int box_rows)
+                                     int box_rows,
+                                     CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)
 {
     CUtensorMap m;
     cuuint64_t dims[3] = { (cuuint64_t)k_extent, (cuuint64_t)rows, (cuuint64_t)depth };
     cuuint64_t strides[2] = { (cuuint64_t)(k_extent * 2), (cuuint64_t)(k_extent * 2 * rows) };
     cuuint32_t box[3] = { 32u, (cuuint32_t)box_rows, 1u };
     cuuint32_t estr[3] = { 1, 1, 1 };
-    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+    CUresult res = encode_fn()(&m, dt, 3, base, dims, strides, box,
                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -233,16 +241,17 @@ inline CUtensorMap make_map_bf16_k32(void* base, int64_t k_extent, int64_t rows,
     return m;
 }
 
-// Contiguous 128 x 32 bf16 blocks ([block][128][32], 8 KB each): a box of `depth`
+// Contiguous 128 x 32 16-bit blocks ([block][128][32], 8 KB each): a box of `depth`
 // consecutive blocks is one contiguous read.
-inline CUtensorMap make_map_bf16_blocks32(void* base, int64_t nblocks, int depth)
+inline CUtensorMap make_map_bf16_blocks32(void* base, int64_t nblocks, int depth,
+                                          CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)
 {
     CUtensorMap m;
     cuuint64_t dims[3] = { 32u, 128u, (cuuint64_t)nblocks };
     cuuint64_t strides[2] = { 64u, 64u * 128u };
     cuuint32_t box[3] = { 32u, 128u, (cuuint32_t)depth };
     cuuint32_t estr[3] = { 1, 1, 1 };
-    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+    CUresult res = encode_fn()(&m, dt, 3, base, dims, strides, box,
                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

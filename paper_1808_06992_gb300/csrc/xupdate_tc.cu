@@ -3,23 +3,30 @@
 // with the soft threshold, dual update and residual norms fused into the
 // epilogue.
 //
-// Accuracy: M and V = z - u are each split into three bf16 pieces
-// (v = h + m + l, residue <= 2^-24 |v|) and the six products h.H, h.M, m.H,
-// h.L, m.M, l.H are summed (the dropped terms are below 2^-24).  The large
-// h.H products go to a double-buffered TMEM accumulator that the epilogue drains
-// every 128 k into compensated FP32 pairs (the tensor core's FP32 accumulation
-// truncates about a third of an ulp per K=16 step); the five small products,
-// 2^-8 and 2^-16 smaller, share one accumulator read once at the end.  The
-// x-update is then accurate to ~1e-7 relative, like the FP32 CUDA-core product.
+// Accuracy: M and V = z - u are each scaled by an exact power of two and split
+// into two fp16 pieces (v = h + l, residue <= 2^-22 |v|); the three products
+// h.H, h.L, l.H are summed (the dropped l.L is below 2^-22).  The scale keeps
+// every scaled value below 2^10, far from fp16's overflow, and puts the
+// underflow floor at 2^-34 of the largest value: each row of M gets its own
+// scale (from its largest entry, M is fixed for the solve), each chain of V one
+// from a bound on ||V|| that holds for every ADMM step:
+//   V' = 2 z' - v with v = x' + u and |z'| <= |v|, x' = c + rho M V, rho ||M|| <= 1
+//   => ||V'|| <= 3 (||c|| + ||z|| + 2 ||u||),
+// evaluated from the norms of the previous step (times 2 for rounding).  The
+// large h.H products go to a double-buffered TMEM accumulator that the epilogue
+// drains every 128 k into compensated FP32 pairs (the tensor core's FP32
+// accumulation truncates about a third of an ulp per K=16 step); the two small
+// products, 2^-11 smaller, share one accumulator read once at the end.  The
+// x-update is then accurate to a few 1e-7 relative.
 //
 // Work per launch: every chain of every group (converged chains are skipped in
 // the epilogue and keep their state; tiles with no live chain exit at once).
 // Grid: (row tiles of 128, chain tiles of NT <= 64, groups), two CTAs per SM so
 // that one CTA's prologue and epilogue overlap the other's stream of M.  Warp 0:
-// TMA producer (ring of 3 stages of k = 32, 2 when NT = 64); warp 1: TMEM
-// allocation and MMA issue; warps 2-5: epilogue (one TMEM lane quarter each).
+// TMA producer (ring of 4 stages of k = 32); warp 1: TMEM allocation and MMA
+// issue; warps 2-5: epilogue (one TMEM lane quarter each).
 // Waits are bounded (~1 s) and report UOI_ERR_TIMEOUT.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <vector>
@@ -35,14 +42,15 @@ using namespace tc;
 constexpr int XT_TM = 128;
 constexpr int XT_TK = 32;                              // k per stage (64-byte swizzled rows)
 constexpr int XT_NT_MAX = 64;
-constexpr int XT_STAGES = 3;                           // ring slots (2 used when NT > 48)
+constexpr int XT_PIECES = 2;                           // fp16 pieces of M and of V
+constexpr int XT_STAGES = 4;                           // ring slots
 constexpr int XT_A_BYTES = XT_TM * XT_TK * 2;          // 8 KB per piece
-constexpr int XT_STAGE_48 = 3 * XT_A_BYTES + 3 * 48 * XT_TK * 2;   // 33 KB at NT = 48
-constexpr int XT_STAGE_64 = 3 * XT_A_BYTES + 3 * 64 * XT_TK * 2;   // 36 KB at NT = 64
-constexpr int XT_SMEM = (3 * XT_STAGE_48 > 2 * XT_STAGE_64 ? 3 * XT_STAGE_48 : 2 * XT_STAGE_64) + 1024;
+constexpr int XT_STAGE_MAX = XT_PIECES * XT_A_BYTES + XT_PIECES * XT_NT_MAX * XT_TK * 2;   // 24 KB
+constexpr int XT_SMEM = XT_STAGES * XT_STAGE_MAX + 1024;
 constexpr int XT_THREADS = 192;
 constexpr uint32_t XT_TMEM_COLS = 256;                 // A1[0] at 0, A1[1] at 64, A2 at 128
 constexpr int XT_CHUNK_STAGES = 4;                     // drain h.H every 128 k
+constexpr int XT_SCALE_EXP = 10;                       // scaled magnitudes stay below 2^10
 
 struct XtArgs {
     int32_t G, q, r, p, nchains, NT, kst, RT, warm;
@@ -53,20 +61,29 @@ struct XtArgs {
     const double* lambdas;
     float rho;
     float* z; float* u;           // slots x p
-    __nv_bfloat16* vnext;         // 3 x slots x kpad
+    __half* vnext;                // 2 x slots x kpad
+    const float* row_inv;         // G x ppad: 1 / scale of the row of M
+    const float* vs_r;            // slots: scale of the V pieces read
+    const float* vs_w;            // slots: scale for the V pieces written
     const int32_t* slot_j;
     const uint8_t* live;
     float* norms;                 // slots x RT x 5
     int32_t* err;
 };
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l)
+__device__ __forceinline__ void split2(float x, __half& h, __half& l)
 {
-    h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    l = __float2bfloat16_rn(r2);
+    h = __float2half_rn(x);
+    l = __float2half_rn(x - __half2float(h));
+}
+
+// 2^(XT_SCALE_EXP - e) for bound = f 2^e, f in [0.5, 1): bound * scale < 2^XT_SCALE_EXP.
+__device__ __forceinline__ float pow2_scale(float bound)
+{
+    if (!(bound > 0.f) || !(bound < 3.0e38f)) return 1.f;
+    int e;
+    frexpf(bound, &e);
+    return ldexpf(1.f, min(120, max(-120, XT_SCALE_EXP - e)));
 }
 
 __global__ void __launch_bounds__(XT_THREADS, 2)
@@ -79,6 +96,8 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     __shared__ int abort_flag;
     __shared__ float red[4][XT_NT_MAX][5];
     __shared__ float s_kappa[XT_NT_MAX];           // lambda_j / rho of each chain of the tile
+    __shared__ float s_vrinv[XT_NT_MAX];           // 1 / scale of the chain's V pieces read
+    __shared__ float s_vw[XT_NT_MAX];              // scale of the chain's V pieces written
     __shared__ int s_coff[XT_NT_MAX];              // row of c used by the chain
     __shared__ uint8_t s_live[XT_NT_MAX];          // chain exists and is still iterating
 
@@ -88,9 +107,9 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     const int nchunks = (a.kst + XT_CHUNK_STAGES - 1) / XT_CHUNK_STAGES;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t b_bytes = (uint32_t)a.NT * XT_TK * 2;
-    const uint32_t stage_tx = 3u * XT_A_BYTES + 3u * b_bytes;
+    const uint32_t stage_tx = XT_PIECES * XT_A_BYTES + XT_PIECES * b_bytes;
     const uint32_t stage_bytes = (stage_tx + 1023u) & ~1023u;
-    const int nst = a.NT <= 48 ? 3 : 2;                 // stages that fit in the ring
+    const int nst = XT_STAGES;
 
     // A tile whose chains have all stopped has nothing to update: skip it whole.
     {
@@ -101,6 +120,8 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             // per-chain scalars of the epilogue, read once instead of per row
             s_live[n] = mine ? 1 : 0;
             s_kappa[n] = mine ? (float)a.lambdas[a.slot_j[sl]] / a.rho : 0.f;
+            s_vrinv[n] = mine ? 1.f / a.vs_r[sl] : 0.f;
+            s_vw[n] = mine ? a.vs_w[sl] : 0.f;
             s_coff[n] = g * a.r + (a.warm ? chain : chain % a.r);
         }
         if (!__syncthreads_or(mine)) return;
@@ -127,7 +148,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        const int blkA = ((g * a.RT + rt) * a.kst) * 3;     // first 8 KB block of this row tile
+        const int blkA = ((g * a.RT + rt) * a.kst) * XT_PIECES;   // first 8 KB block of this row tile
         const int rowB = g * a.nchains + n0;
         for (int s_ = 0; s_ < a.kst; ++s_) {
             const int s = s_ % nst;
@@ -139,16 +160,16 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             const uint32_t st = sbase + s * stage_bytes;
             mbar_expect_tx(&full_bar[s], stage_tx);
             const int k0 = s_ * XT_TK;
-            tma_load_3d(st, &tmM, &full_bar[s], 0, 0, blkA + 3 * s_);   // 3 pieces, 24 KB contiguous
-            for (int pc = 0; pc < 3; ++pc)
-                tma_load_3d(st + 3 * XT_A_BYTES + pc * b_bytes, &tmV, &full_bar[s], k0, rowB, pc);
+            tma_load_3d(st, &tmM, &full_bar[s], 0, 0, blkA + XT_PIECES * s_);   // 2 pieces, 16 KB contiguous
+            for (int pc = 0; pc < XT_PIECES; ++pc)
+                tma_load_3d(st + XT_PIECES * XT_A_BYTES + pc * b_bytes, &tmV, &full_bar[s], k0, rowB, pc);
         }
         if (abort_flag)
             for (int s_ = max(0, a.kst - nst); s_ < a.kst; ++s_)
                 mbar_wait(&full_bar[s_ % nst], (s_ / nst) & 1, &abort_flag);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc = idesc_bf16(XT_TM, a.NT);
+        const uint32_t idesc = idesc_f16(XT_TM, a.NT);
         const uint32_t d2 = tmem + 128u;
         bool first2 = true;
         int s_ = 0;
@@ -172,19 +193,14 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                 }
                 tc_fence_after();
                 const uint32_t st = sbase + s * stage_bytes;
-                const uint64_t Ah = smem_desc_sw64(st), Am = smem_desc_sw64(st + XT_A_BYTES);
-                const uint64_t Al = smem_desc_sw64(st + 2 * XT_A_BYTES);
-                const uint32_t bb = st + 3 * XT_A_BYTES;
-                const uint64_t Bh = smem_desc_sw64(bb), Bm = smem_desc_sw64(bb + b_bytes);
-                const uint64_t Bl = smem_desc_sw64(bb + 2 * b_bytes);
+                const uint64_t Ah = smem_desc_sw64(st), Al = smem_desc_sw64(st + XT_A_BYTES);
+                const uint32_t bb = st + XT_PIECES * XT_A_BYTES;
+                const uint64_t Bh = smem_desc_sw64(bb), Bl = smem_desc_sw64(bb + b_bytes);
 #pragma unroll
                 for (int ks = 0; ks < XT_TK / 16; ++ks) {
                     const uint64_t adv = (uint64_t)(ks * 32 >> 4);
                     mma_bf16(d1, Ah + adv, Bh + adv, idesc, first1 ? 0u : 1u);
-                    mma_bf16(d2, Ah + adv, Bm + adv, idesc, first2 ? 0u : 1u);
-                    mma_bf16(d2, Am + adv, Bh + adv, idesc, 1u);
-                    mma_bf16(d2, Ah + adv, Bl + adv, idesc, 1u);
-                    mma_bf16(d2, Am + adv, Bm + adv, idesc, 1u);
+                    mma_bf16(d2, Ah + adv, Bl + adv, idesc, first2 ? 0u : 1u);
                     mma_bf16(d2, Al + adv, Bh + adv, idesc, 1u);
                     first1 = false;
                     first2 = false;
@@ -242,6 +258,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         __syncwarp();
         tc_fence_after();
         const bool rowok = i < a.p && !abort_flag;
+        const float rinv = rowok ? a.row_inv[(int64_t)g * a.ppad + i] : 0.f;
 #pragma unroll
         for (int cb = 0; cb < 2; ++cb) {
             if (cb * 32 >= a.NT) break;
@@ -267,7 +284,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                     for (int qq = 0; qq < 5; ++qq) pr[qq][t] = 0.f;
                     if (!(rowok && s_live[nb + t])) continue;
                     const int tt = nb + t;
-                    const float prod = acc[tt] + v2[t8 + t];
+                    const float prod = (acc[tt] + v2[t8 + t]) * (rinv * s_vrinv[tt]);
                     const float x = cc[t] + a.rho * prod;
                     const int64_t sl = (int64_t)g * a.nchains + n0 + nb + t;
                     const int64_t o = sl * a.p + i;
@@ -276,12 +293,11 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                     const float un = vv - zn;
                     a.z[o] = zn;
                     a.u[o] = un;
-                    __nv_bfloat16 h, m, l;
-                    split3(zn - un, h, m, l);
+                    __half h, l;
+                    split2((zn - un) * s_vw[tt], h, l);
                     const int64_t vo = sl * a.kpad + i;
                     a.vnext[vo] = h;
-                    a.vnext[(int64_t)a.slots * a.kpad + vo] = m;
-                    a.vnext[2 * (int64_t)a.slots * a.kpad + vo] = l;
+                    a.vnext[(int64_t)a.slots * a.kpad + vo] = l;
                     const float d = x - zn, dz = zn - zp[t];
                     pr[0][t] = d * d; pr[1][t] = dz * dz; pr[2][t] = x * x; pr[3][t] = zn * zn; pr[4][t] = un * un;
                 }
@@ -331,12 +347,33 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     }
 }
 
-// M_g (FP32, p x p) -> three bf16 pieces in 128 x 32 blocks, ordered
-// [g][row tile][k block][piece][128][32] (zero padded), so that the x-update
-// streams each row tile as one contiguous run of 24 KB stages.  One thread per
-// 8 consecutive k: a 32-byte read and one 16-byte write per piece.
+// Per-row scale of M_g: row_scale = 2^(10 - e) for the row's largest |M_ik| =
+// f 2^e (1 for an all-zero or padding row), row_inv = 1 / row_scale.  One warp per row.
+__global__ void k_row_scale(const float* M, int32_t G, int64_t p, int64_t ppad, float* row_scale,
+                            float* row_inv)
+{
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= (int64_t)G * ppad) return;
+    const int64_t g = row / ppad, i = row % ppad;
+    float mx = 0.f;
+    if (i < p)
+        for (int64_t k = lane; k < p; k += 32) mx = fmaxf(mx, fabsf(M[((size_t)g * p + i) * p + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        const float sc = pow2_scale(mx);
+        row_scale[row] = sc;
+        row_inv[row] = 1.f / sc;
+    }
+}
+
+// M_g (FP32, p x p), each row times its scale -> two fp16 pieces in 128 x 32
+// blocks, ordered [g][row tile][k block][piece][128][32] (zero padded), so that
+// the x-update streams each row tile as one contiguous run of 16 KB stages.  One
+// thread per 8 consecutive k: a 32-byte read and one 16-byte write per piece.
 __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
-                          __nv_bfloat16* out)
+                          const float* row_scale, __half* out)
 {
     const int64_t per8 = (int64_t)G * ppad * (kpad / 8);
     const int64_t RT = ppad / XT_TM, kst = kpad / XT_TK;
@@ -344,31 +381,76 @@ __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, in
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k8 = (t % (kpad / 8)) * 8, row = t / (kpad / 8);
         const int64_t g = row / ppad, i = row % ppad;
-        uint32_t ph[4], pm[4], pl[4];
+        const float sc = row_scale[row];
+        uint32_t ph[4], pl[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            __nv_bfloat16 h[2], m[2], l[2];
+            __half h[2], l[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int64_t k = k8 + 2 * q + u;
-                const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] : 0.f;
-                split3(x, h[u], m[u], l[u]);
+                const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] * sc : 0.f;
+                split2(x, h[u], l[u]);
             }
-            ph[q] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
-            pm[q] = (uint32_t)__bfloat16_as_ushort(m[0]) | ((uint32_t)__bfloat16_as_ushort(m[1]) << 16);
-            pl[q] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+            ph[q] = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+            pl[q] = (uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16);
         }
-        const int64_t blk = ((g * RT + i / XT_TM) * kst + k8 / XT_TK) * 3;
+        const int64_t blk = ((g * RT + i / XT_TM) * kst + k8 / XT_TK) * XT_PIECES;
         const int64_t o = (blk * XT_TM + i % XT_TM) * XT_TK + k8 % XT_TK;    // multiple of 8: 16 B aligned
         *reinterpret_cast<uint4*>(out + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-        *reinterpret_cast<uint4*>(out + o + XT_TM * XT_TK) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
-        *reinterpret_cast<uint4*>(out + o + 2 * XT_TM * XT_TK) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        *reinterpret_cast<uint4*>(out + o + XT_TM * XT_TK) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
     }
 }
 
-// Initial state: z, u (zero or the given start), the pieces of V = z - u, live flags.
+// Per (group, equation): ||c_ge||_2 (one warp each).
+__global__ void k_c_norms(const float* c, int64_t count, int64_t p, float* cn)
+{
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= count) return;
+    float acc = 0.f;
+    for (int64_t i = lane; i < p; i += 32) {
+        const float v = c[row * p + i];
+        acc += v * v;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) cn[row] = sqrtf(acc);
+}
+
+// Scales of the first two V buffers of every slot (one warp each): vs0 for
+// V_0 = z0 - u0 from its largest entry, vs1 for V_1 (written by the first
+// x-update) from the step bound 2 * 3 (||c|| + ||z0|| + 2 ||u0||).
+__global__ void k_xt_vscale_init(int64_t slots, int64_t p, int32_t nchains, int32_t r, int32_t warm,
+                                 const float* z0, const float* u0, const float* cn, float* vs0,
+                                 float* vs1)
+{
+    const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= slots) return;
+    float mx = 0.f, zz = 0.f, uu = 0.f;
+    if (z0)
+        for (int64_t i = lane; i < p; i += 32) {
+            const float zi = z0[sl * p + i], ui = u0[sl * p + i];
+            mx = fmaxf(mx, fabsf(zi - ui));
+            zz += zi * zi;
+            uu += ui * ui;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    zz = warp_sum(zz);
+    uu = warp_sum(uu);
+    if (lane == 0) {
+        const int64_t g = sl / nchains, chain = sl % nchains;
+        const float cnorm = cn[g * r + (warm ? chain : chain % r)];
+        vs0[sl] = pow2_scale(mx);
+        vs1[sl] = pow2_scale(6.f * (cnorm + sqrtf(zz) + 2.f * sqrtf(uu)));
+    }
+}
+
+// Initial state: z, u (zero or the given start), the pieces of V = z - u
+// (scaled by vs0), live flags.
 __global__ void k_xt_init(int64_t slots, int64_t p, int64_t kpad, const float* z0, const float* u0,
-                          float* z, float* u, __nv_bfloat16* v, uint8_t* live)
+                          const float* vs0, float* z, float* u, __half* v, uint8_t* live)
 {
     const int64_t total = slots * kpad;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -380,11 +462,10 @@ __global__ void k_xt_init(int64_t slots, int64_t p, int64_t kpad, const float* z
             z[sl * p + i] = zz;
             u[sl * p + i] = uu;
         }
-        __nv_bfloat16 h, m, l;
-        split3(zz - uu, h, m, l);
+        __half h, l;
+        split2((zz - uu) * vs0[sl], h, l);
         v[t] = h;
-        v[slots * kpad + t] = m;
-        v[2 * slots * kpad + t] = l;
+        v[slots * kpad + t] = l;
         if (i == 0) live[sl] = 1;
     }
 }
@@ -397,7 +478,7 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
                            float sqrtp, const float* z, const float* norms, int32_t* slot_j,
                            const int32_t* slot_jend, int32_t* slot_it, uint8_t* live, double* beta,
                            int32_t* iters, uint8_t* conv, uint64_t* family, int32_t W,
-                           int32_t* live_count)
+                           int32_t* live_count, const float* cn, float* vs_next)
 {
     const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -450,8 +531,15 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
     }
     if (lane == 0) {
         slot_it[sl] = it;
-        if (!still) live[sl] = 0;
-        else atomicAdd(live_count, 1);
+        if (!still) {
+            live[sl] = 0;
+        } else {
+            atomicAdd(live_count, 1);
+            // scale of the V pieces the next x-update writes: step bound on ||V||
+            const int64_t g = sl / nchains, chain = sl % nchains;
+            const float cnorm = cn[g * r + (warm ? chain : chain % r)];
+            vs_next[sl] = pow2_scale(6.f * (cnorm + zn + 2.f * sqrtf(tot[4])));
+        }
     }
 }
 
@@ -484,37 +572,52 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
     const int RT = (int)(ppad / XT_TM);
     const int NT = (int)std::min<int64_t>(XT_NT_MAX, ceil_div(nchains, 16) * 16);
     const int kst = (int)(kpad / XT_TK);
-    DevBuf mp(sizeof(__nv_bfloat16) * 3 * (size_t)P.G * ppad * kpad, s);
+    DevBuf rs(sizeof(float) * (size_t)P.G * ppad, s), rinv(sizeof(float) * (size_t)P.G * ppad, s);
+    k_row_scale<<<(unsigned)ceil_div((int64_t)P.G * ppad * 32, 256), 256, 0, s>>>(P.M, P.G, p, ppad,
+                                                                                rs.as<float>(), rinv.as<float>());
+    UOI_CHECK_LAUNCH();
+    DevBuf mp(sizeof(__half) * XT_PIECES * (size_t)P.G * ppad * kpad, s);
     k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad / 8, 256), 8192), 256, 0, s>>>(
-        P.M, P.G, p, ppad, kpad, mp.as<__nv_bfloat16>());
+        P.M, P.G, p, ppad, kpad, rs.as<float>(), mp.as<__half>());
     UOI_CHECK_LAUNCH();
     DevBuf zb(sizeof(float) * (size_t)slots * p, s), ub(sizeof(float) * (size_t)slots * p, s);
-    DevBuf v0(sizeof(__nv_bfloat16) * 3 * (size_t)slots * kpad, s);
-    DevBuf v1(sizeof(__nv_bfloat16) * 3 * (size_t)slots * kpad, s);
+    DevBuf v0(sizeof(__half) * XT_PIECES * (size_t)slots * kpad, s);
+    DevBuf v1(sizeof(__half) * XT_PIECES * (size_t)slots * kpad, s);
+    DevBuf vs0(sizeof(float) * (size_t)slots, s), vs1(sizeof(float) * (size_t)slots, s);
+    DevBuf cn(sizeof(float) * (size_t)P.G * P.r, s);
     DevBuf nb(sizeof(float) * (size_t)slots * RT * 5, s);
     DevBuf sj(sizeof(int32_t) * slots, s), sje(sizeof(int32_t) * slots, s), sit(sizeof(int32_t) * slots, s);
     DevBuf live(slots, s), cnt(sizeof(int32_t), s), err(sizeof(int32_t), s);
     UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
     const bool start = P.z0 && !P.warm;
+    k_c_norms<<<(unsigned)ceil_div((int64_t)P.G * P.r * 32, 256), 256, 0, s>>>(P.c, (int64_t)P.G * P.r, p,
+                                                                               cn.as<float>());
+    UOI_CHECK_LAUNCH();
+    k_xt_vscale_init<<<(unsigned)ceil_div(slots * 32, 256), 256, 0, s>>>(
+        slots, p, nchains, (int32_t)P.r, P.warm, start ? P.z0 : nullptr, start ? P.u0 : nullptr,
+        cn.as<float>(), vs0.as<float>(), vs1.as<float>());
+    UOI_CHECK_LAUNCH();
     k_xt_init<<<(unsigned)std::min<int64_t>(ceil_div(slots * kpad, 256), 8192), 256, 0, s>>>(
-        slots, p, kpad, start ? P.z0 : nullptr, start ? P.u0 : nullptr, zb.as<float>(), ub.as<float>(),
-        v0.as<__nv_bfloat16>(), live.as<uint8_t>());
+        slots, p, kpad, start ? P.z0 : nullptr, start ? P.u0 : nullptr, vs0.as<float>(), zb.as<float>(),
+        ub.as<float>(), v0.as<__half>(), live.as<uint8_t>());
     UOI_CHECK_LAUNCH();
     // v1 holds the pieces of V for slots that do not change in an iteration
     UOI_CUDA(cudaMemcpyAsync(v1.ptr, v0.ptr, v0.bytes, cudaMemcpyDeviceToDevice, s));
     k_xt_slots<<<(unsigned)std::min<int64_t>(ceil_div(slots, 256), 4096), 256, 0, s>>>(
         P.G, nchains, (int32_t)P.r, P.q, P.warm, sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>());
     UOI_CHECK_LAUNCH();
-    count_launch(3);
-    const CUtensorMap mM = make_map_bf16_blocks32(mp.ptr, (int64_t)P.G * RT * kst * 3, 3);
-    const CUtensorMap mV0 = make_map_bf16_k32(v0.ptr, kpad, slots, 3, NT);
-    const CUtensorMap mV1 = make_map_bf16_k32(v1.ptr, kpad, slots, 3, NT);
+    count_launch(6);
+    const CUtensorMap mM = make_map_bf16_blocks32(mp.ptr, (int64_t)P.G * RT * kst * XT_PIECES, XT_PIECES,
+                                                   CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const CUtensorMap mV0 = make_map_bf16_k32(v0.ptr, kpad, slots, XT_PIECES, NT, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const CUtensorMap mV1 = make_map_bf16_k32(v1.ptr, kpad, slots, XT_PIECES, NT, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
     UOI_CUDA(cudaFuncSetAttribute(k_xupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM));
     XtArgs a;
     a.G = P.G; a.q = P.q; a.r = (int32_t)P.r; a.p = p; a.nchains = nchains; a.NT = NT; a.kst = kst;
     a.RT = RT; a.warm = P.warm; a.ppad = ppad; a.kpad = kpad; a.slots = slots;
     a.c = P.c; a.lambdas = P.lambdas; a.rho = (float)P.rho;
     a.z = zb.as<float>(); a.u = ub.as<float>();
+    a.row_inv = rinv.as<float>();
     a.slot_j = sj.as<int32_t>(); a.live = live.as<uint8_t>(); a.norms = nb.as<float>();
     a.err = err.as<int32_t>();
     const dim3 grid((unsigned)RT, (unsigned)ceil_div(nchains, NT), (unsigned)P.G);
@@ -526,7 +629,10 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
     try {
         for (int64_t it = 0; it < bound && !done; ++it) {
             const bool even = (it & 1) == 0;
-            a.vnext = (even ? v1 : v0).as<__nv_bfloat16>();
+            // read V_t (buffer 0 on even steps) with its scale, write V_{t+1} into the other
+            a.vnext = (even ? v1 : v0).as<__half>();
+            a.vs_r = (even ? vs0 : vs1).as<float>();
+            a.vs_w = (even ? vs1 : vs0).as<float>();
             UOI_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int32_t), s));
             ktimer_begin(TK_XUPDATE, s);
             k_xupdate_tc<<<grid, XT_THREADS, XT_SMEM, s>>>(mM, even ? mV0 : mV1, a);
@@ -537,7 +643,8 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
                                           (float)sqrt((double)p), zb.as<float>(), nb.as<float>(),
                                           sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>(),
                                           live.as<uint8_t>(), P.beta, P.iters, P.conv, P.family, W,
-                                          cnt.as<int32_t>());
+                                          cnt.as<int32_t>(), cn.as<float>(),
+                                          (even ? vs0 : vs1).as<float>());
             UOI_CHECK_LAUNCH();
             count_launch(2);
             if ((it + 1) % 8 == 0 || it + 1 == bound) {
