@@ -3,15 +3,17 @@
 // cached inverse M = (G/n + rho I)^{-1} that the ADMM x-update multiplies by).
 //
 // GEMM: D_g = alpha * A_g B_g^T + beta * C_g with A_g (m x k) and B_g (n x k)
-// given as three bf16 pieces each (v = h + m + l, residue <= 2^-24 |v|); the
-// six products h.H, h.M, m.H, h.L, m.M, l.H all accumulate into a
+// given as two fp16 pieces each: every matrix scaled by an exact power of two
+// that puts its largest entry just below 2^10, then v = h + l (residue <=
+// 2^-22 |v|); the three products l.H, h.L, h.H (small first) accumulate into a
 // double-buffered TMEM accumulator (2 x 256 columns) that 8 epilogue warps drain
-// every 64 k (24 accumulation steps, the same truncation budget as the Gram)
-// into FP32 running sums.  Tiles 128 x 256 (the wide N keeps shared-memory
-// operand traffic below the tensor rate), k = 32 per stage (64-byte swizzle),
-// 2-stage TMA ring of 72 KB, one CTA per SM.  Operands are stored as contiguous
-// 128 x 32 (A) or 256 x 32 (B) blocks, [g][row tile][k block][piece][rows][32],
-// so every stage is one TMA copy per operand.
+// every 64 k into FP32 running sums; the epilogue undoes the two scales.  The
+// largest entries come for free: an SPD matrix's largest entry is its largest
+// diagonal entry, and the GEMM epilogue reports the largest |D| it writes.  Tiles 128 x 256 (the wide N keeps shared-memory operand traffic below the
+// tensor rate), k = 32 per stage (64-byte swizzle), 4-stage TMA ring of 48 KB
+// stages, one CTA per SM.  Operands are stored as contiguous 128 x 32 (A) or
+// 256 x 32 (B) blocks, [g][row tile][k block][piece][rows][32], so every stage
+// is one TMA copy per operand.
 //
 // Inverse: block (Schur complement) recursion on the SPD matrix
 //   A = [A11 A21^T; A21 A22],  X = A11^{-1},  U = A21 X,  S = A22 - A21 U^T,
@@ -20,7 +22,7 @@
 // every product a large GEMM; blocks of order <= 192 are inverted in shared
 // memory by Gauss-Jordan elimination (no pivoting: the pivots are the Schur
 // complements' diagonals, positive for SPD A).  S stays SPD for SPD A.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -35,10 +37,11 @@ using namespace tc;
 constexpr int GT_TM = 128;                             // A rows per tile
 constexpr int GT_TN = 256;                             // B rows per tile (UMMA N)
 constexpr int GT_TK = 32;
-constexpr int GT_STAGES = 2;
+constexpr int GT_PIECES = 2;                           // fp16 pieces per operand
+constexpr int GT_STAGES = 4;
 constexpr int GT_A_BYTES = GT_TM * GT_TK * 2;          // 8 KB per piece
 constexpr int GT_B_BYTES = GT_TN * GT_TK * 2;          // 16 KB per piece
-constexpr int GT_STAGE = 3 * GT_A_BYTES + 3 * GT_B_BYTES;   // 72 KB
+constexpr int GT_STAGE = GT_PIECES * GT_A_BYTES + GT_PIECES * GT_B_BYTES;   // 48 KB
 constexpr int GT_SMEM = GT_STAGES * GT_STAGE + 1024;
 constexpr int GT_EPI_WARPS = 8;
 constexpr int GT_THREADS = 64 + 32 * GT_EPI_WARPS;     // producer, MMA, 8 epilogue warps
@@ -47,22 +50,32 @@ constexpr int GT_CHUNK_STAGES = 2;                     // drain every 64 k
 constexpr int GT_STG = 132;                            // epilogue staging row (floats)
 static_assert(GT_EPI_WARPS * 32 * GT_STG * 4 <= GT_STAGES * GT_STAGE, "staging fits the ring");
 constexpr int64_t INV_BASE = 192;                      // shared-memory inverse at or below this order
+constexpr int GT_SCALE_EXP = 10;                       // scaled magnitudes stay below 2^10
 
 struct GemmArgs {
     int32_t m, n, kst, MT, NT;
     float alpha, beta;
     const float* C; int64_t ldc, gsc;                  // C may alias D
     float* D; int64_t ldd, gsd;
+    const float* ainv;                                 // G: 1 / scale of A_g
+    const float* binv;                                 // G: 1 / scale of B_g
+    uint32_t* dmax;                                    // G: largest |D_g| (float bits), nullable
     int32_t* err;
 };
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l)
+__device__ __forceinline__ void split2(float x, __half& h, __half& l)
 {
-    h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    l = __float2bfloat16_rn(r2);
+    h = __float2half_rn(x);
+    l = __float2half_rn(x - __half2float(h));
+}
+
+// 2^(GT_SCALE_EXP - e) for m = f 2^e, f in [0.5, 1) (1 for m = 0).
+__device__ __forceinline__ float pow2_scale(float m)
+{
+    if (!(m > 0.f) || !(m < 3.0e38f)) return 1.f;
+    int e;
+    frexpf(m, &e);
+    return ldexpf(1.f, min(120, max(-120, GT_SCALE_EXP - e)));
 }
 
 __global__ void __launch_bounds__(GT_THREADS, 1)
@@ -99,8 +112,8 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        const int blkA = ((g * a.MT + mt) * a.kst) * 3;
-        const int blkB = ((g * a.NT + nt) * a.kst) * 3;
+        const int blkA = ((g * a.MT + mt) * a.kst) * GT_PIECES;
+        const int blkB = ((g * a.NT + nt) * a.kst) * GT_PIECES;
         for (int s_ = 0; s_ < a.kst; ++s_) {
             const int s = s_ % GT_STAGES;
             if (s_ >= GT_STAGES && !mbar_wait(&empty_bar[s], ((s_ / GT_STAGES) - 1) & 1, &abort_flag)) {
@@ -110,15 +123,15 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             }
             const uint32_t st = sbase + s * GT_STAGE;
             mbar_expect_tx(&full_bar[s], GT_STAGE);
-            tma_load_3d(st, &tmA, &full_bar[s], 0, 0, blkA + 3 * s_);
-            tma_load_3d(st + 3 * GT_A_BYTES, &tmB, &full_bar[s], 0, 0, blkB + 3 * s_);
+            tma_load_3d(st, &tmA, &full_bar[s], 0, 0, blkA + GT_PIECES * s_);
+            tma_load_3d(st + GT_PIECES * GT_A_BYTES, &tmB, &full_bar[s], 0, 0, blkB + GT_PIECES * s_);
         }
         if (abort_flag)
             for (int s_ = max(0, a.kst - GT_STAGES); s_ < a.kst; ++s_)
                 mbar_wait(&full_bar[s_ % GT_STAGES], (s_ / GT_STAGES) & 1, &abort_flag);
     } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer: all six products into accumulator b ----------------
-        const uint32_t idesc = idesc_bf16(GT_TM, GT_TN);
+        // ---------------- MMA issuer: all three products into accumulator b ----------------
+        const uint32_t idesc = idesc_f16(GT_TM, GT_TN);
         int s_ = 0;
         for (int c = 0; c < nchunks && !abort_flag; ++c) {
             const int b = c & 1;
@@ -140,20 +153,15 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 }
                 tc_fence_after();
                 const uint32_t st = sbase + s * GT_STAGE;
-                const uint64_t Ah = smem_desc_sw64(st), Am = smem_desc_sw64(st + GT_A_BYTES);
-                const uint64_t Al = smem_desc_sw64(st + 2 * GT_A_BYTES);
-                const uint32_t bb = st + 3 * GT_A_BYTES;
-                const uint64_t Bh = smem_desc_sw64(bb), Bm = smem_desc_sw64(bb + GT_B_BYTES);
-                const uint64_t Bl = smem_desc_sw64(bb + 2 * GT_B_BYTES);
+                const uint64_t Ah = smem_desc_sw64(st), Al = smem_desc_sw64(st + GT_A_BYTES);
+                const uint32_t bb = st + GT_PIECES * GT_A_BYTES;
+                const uint64_t Bh = smem_desc_sw64(bb), Bl = smem_desc_sw64(bb + GT_B_BYTES);
 #pragma unroll
                 for (int ks = 0; ks < GT_TK / 16; ++ks) {
                     const uint64_t adv = (uint64_t)(ks * 32 >> 4);
                     // small products first, h.H last (adds the largest term to the smallest sum)
-                    mma_bf16(d, Ah + adv, Bm + adv, idesc, first ? 0u : 1u);
-                    mma_bf16(d, Am + adv, Bh + adv, idesc, 1u);
+                    mma_bf16(d, Al + adv, Bh + adv, idesc, first ? 0u : 1u);
                     mma_bf16(d, Ah + adv, Bl + adv, idesc, 1u);
-                    mma_bf16(d, Am + adv, Bm + adv, idesc, 1u);
-                    mma_bf16(d, Al + adv, Bh + adv, idesc, 1u);
                     mma_bf16(d, Ah + adv, Bh + adv, idesc, 1u);
                     first = false;
                 }
@@ -206,6 +214,8 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         __syncwarp();
         if (!abort_flag) {
             const int j = nt * GT_TN + half * 128 + 4 * lane;
+            const float ar = a.alpha * (a.ainv[g] * a.binv[g]);
+            float dm = 0.f;
             for (int rr = 0; rr < 32; ++rr) {
                 const int ii = mt * GT_TM + quad * 32 + rr;
                 if (ii >= a.m) break;
@@ -216,11 +226,17 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     if (j + t < a.n) {
-                        float r = a.alpha * r4[t];
+                        float r = ar * r4[t];
                         if (crow) r += a.beta * crow[j + t];
                         drow[j + t] = r;
+                        dm = fmaxf(dm, fabsf(r));
                     }
                 }
+            }
+            if (a.dmax) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+                if (lane == 0 && dm > 0.f) atomicMax(&a.dmax[g], __float_as_uint(dm));
             }
         }
     }
@@ -232,21 +248,24 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
 }
 
-// Three bf16 pieces of op(S_g) (rows x K; op = transpose if trans) in blocks of
-// rt x 32, ordered [g][row tile][k block][piece][rt][32], zero padded to the
-// tile multiples.  S_g element (i, k) is at src[g*gs + i*ld + k] (or
-// src[g*gs + k*ld + i] transposed).  32 x 32 tiles through shared memory, so
-// that both the read (along the source's contiguous index) and the write
-// (along k) are coalesced.  Block (32, 8); grid (rpad/32, kpad/32, G).
+// Two fp16 pieces of op(S_g) (rows x K; op = transpose if trans), scaled by the
+// power of two of S_g's largest magnitude smax[g] (float bits), in blocks of
+// rt x 32, ordered [g][row tile][k block][piece][rt][32], zero padded to the tile
+// multiples; sinv[g] = 1 / scale.  S_g element (i, k) is at src[g*gs + i*ld + k]
+// (or src[g*gs + k*ld + i] transposed).  32 x 32 tiles through shared memory, so
+// that both the read (along the source's contiguous index) and the write (along
+// k) are coalesced.  Block (32, 8); grid (rpad/32, kpad/32, G).
 __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K,
                                int32_t trans, int32_t rt, int64_t rpad, int64_t kpad,
-                               __nv_bfloat16* out)
+                               const uint32_t* smax, float* sinv, __half* out)
 {
     __shared__ float tile[32][33];                      // [k local][i local]
     const int64_t g = blockIdx.z;
     const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const float* sg = src + g * gs;
+    const float sc = pow2_scale(__uint_as_float(smax[g]));
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0 && ty == 0) sinv[g] = 1.f / sc;
     for (int j = ty; j < 32; j += 8) {
         if (trans) {
             const int64_t i = i0 + tx, k = k0 + j;
@@ -261,13 +280,30 @@ __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t
     const int64_t k = k0 + tx;
     for (int j = ty; j < 32; j += 8) {
         const int64_t i = i0 + j;
-        __nv_bfloat16 h, m, l;
-        split3(tile[tx][j], h, m, l);
-        const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * 3;
+        __half h, l;
+        split2(tile[tx][j] * sc, h, l);
+        const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * GT_PIECES;
         const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;
         out[o] = h;
-        out[o + rt * GT_TK] = m;
-        out[o + 2 * rt * GT_TK] = l;
+        out[o + rt * GT_TK] = l;
+    }
+}
+
+// out[g] = largest diagonal entry of the SPD block A_g (n x n), as float bits:
+// the largest magnitude of an SPD matrix (|a_ij| <= sqrt(a_ii a_jj)).
+__global__ void k_diag_max(const float* A, int64_t lda, int64_t gsa, int64_t n, uint32_t* out)
+{
+    __shared__ float red[32];
+    const int64_t g = blockIdx.x;
+    float m = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(A[g * gsa + i * lda + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+        out[g] = __float_as_uint(fmaxf(m, red[0]));
     }
 }
 
@@ -291,39 +327,43 @@ __global__ void k_transpose_block(const float* src, int64_t lds, float* dst, int
 
 struct Pieces {
     DevBuf buf;
+    DevBuf sinv;                   // G: 1 / scale
     CUtensorMap map;
     int32_t tiles = 0, kst = 0;
 };
 
-// Split op(S) into pieces for a GEMM operand with row tiles of rt.
+// Split op(S) into scaled pieces for a GEMM operand with row tiles of rt; smax
+// (G, float bits) holds each S_g's largest magnitude.
 void make_pieces(Pieces& P, const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K, bool trans,
-                 int32_t rt, int32_t G, cudaStream_t s)
+                 int32_t rt, int32_t G, const uint32_t* smax, cudaStream_t s)
 {
     const int64_t rpad = ceil_div(rows, rt) * rt, kpad = ceil_div(K, GT_TK) * GT_TK;
     P.tiles = (int32_t)(rpad / rt);
     P.kst = (int32_t)(kpad / GT_TK);
-    P.buf.alloc(sizeof(__nv_bfloat16) * 3 * (size_t)G * rpad * kpad, s);
+    P.buf.alloc(sizeof(__half) * GT_PIECES * (size_t)G * rpad * kpad, s);
+    P.sinv.alloc(sizeof(float) * (size_t)G, s);
     k_split_blocks<<<dim3((unsigned)(rpad / 32), (unsigned)(kpad / 32), (unsigned)G), dim3(32, 8), 0, s>>>(
-        src, ld, gs, rows, K, trans ? 1 : 0, rt, rpad, kpad, P.buf.as<__nv_bfloat16>());
+        src, ld, gs, rows, K, trans ? 1 : 0, rt, rpad, kpad, smax, P.sinv.as<float>(), P.buf.as<__half>());
     UOI_CHECK_LAUNCH();
     count_launch();
-    // blocks of rt x 32 bf16 (64-byte rows); three consecutive blocks per stage
+    // blocks of rt x 32 fp16 (64-byte rows); two consecutive blocks per stage
     CUtensorMap m;
-    cuuint64_t dims[3] = { 32u, (cuuint64_t)rt, (cuuint64_t)((int64_t)G * P.tiles * P.kst * 3) };
+    cuuint64_t dims[3] = { 32u, (cuuint64_t)rt, (cuuint64_t)((int64_t)G * P.tiles * P.kst * GT_PIECES) };
     cuuint64_t strides[2] = { 64u, (cuuint64_t)rt * 64u };
-    cuuint32_t box[3] = { 32u, (cuuint32_t)rt, 3u };
+    cuuint32_t box[3] = { 32u, (cuuint32_t)rt, (cuuint32_t)GT_PIECES };
     cuuint32_t estr[3] = { 1, 1, 1 };
-    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, P.buf.ptr, dims, strides, box,
+    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P.buf.ptr, dims, strides, box,
                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     P.map = m;
 }
 
-// D = alpha A B^T + beta C with A (m x k) and B (n x k) in pieces.
+// D = alpha A B^T + beta C with A (m x k) and B (n x k) in pieces; dmax (G,
+// nullable, zeroed by the caller) receives the largest |D_g| as float bits.
 void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, float alpha, float beta,
            const float* C, int64_t ldc, int64_t gsc, float* D, int64_t ldd, int64_t gsd, int32_t* err,
-           cudaStream_t s)
+           cudaStream_t s, uint32_t* dmax = nullptr)
 {
     if (A.kst != B.kst) throw Error(UOI_ERR_INVALID_ARG, "gemm3: operand k extents differ");
     UOI_CUDA(cudaFuncSetAttribute(k_gemm3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM));
@@ -332,6 +372,9 @@ void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, fl
     a.alpha = alpha; a.beta = beta;
     a.C = C; a.ldc = ldc; a.gsc = gsc;
     a.D = D; a.ldd = ldd; a.gsd = gsd;
+    a.ainv = A.sinv.as<float>();
+    a.binv = B.sinv.as<float>();
+    a.dmax = dmax;
     a.err = err;
     const dim3 grid((unsigned)ceil_div(m, GT_TM), (unsigned)ceil_div(n, GT_TN), (unsigned)G);
     k_gemm3_tc<<<grid, GT_THREADS, GT_SMEM, s>>>(A.map, B.map, a);
@@ -452,6 +495,13 @@ void inv_base(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM
     count_launch();
 }
 
+void diag_max(const float* A, int64_t lda, int64_t gsa, int64_t n, int32_t G, uint32_t* out, cudaStream_t s)
+{
+    k_diag_max<<<(unsigned)G, 256, 0, s>>>(A, lda, gsa, n, out);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
 void inv_rec(const float* A, int64_t ldA, int64_t gsA, float* M, int64_t ldM, int64_t gsM, int64_t n,
              int32_t G, DevStatus* st, int32_t* err, cudaStream_t s)
 {
@@ -466,37 +516,49 @@ void inv_rec(const float* A, int64_t ldA, int64_t gsA, float* M, int64_t ldM, in
     float* M21 = M + p1 * ldM;
     float* M12 = M + p1;
     float* Y = M + p1 * ldM + p1;
+    // largest magnitudes of the split operands (float bits per group): A, X, Y are
+    // SPD (their largest diagonal entry), U and M21 come from the GEMM epilogues
+    DevBuf mx(sizeof(uint32_t) * 5 * (size_t)G, s);
+    UOI_CUDA(cudaMemsetAsync(mx.ptr, 0, mx.bytes, s));
+    uint32_t* mA = mx.as<uint32_t>();
+    uint32_t* mX = mA + G;
+    uint32_t* mU = mA + 2 * G;
+    uint32_t* mY = mA + 3 * G;
+    uint32_t* mM21 = mA + 4 * G;
+    diag_max(A, ldA, gsA, n, G, mA, s);
     // X = A11^{-1}
     inv_rec(A, ldA, gsA, X, ldM, gsM, p1, G, st, err, s);
+    diag_max(X, ldM, gsM, p1, G, mX, s);
     // U = A21 X   (p2 x p1)
     DevBuf U(sizeof(float) * (size_t)(G * p2 * p1), s), S(sizeof(float) * (size_t)(G * p2 * p2), s);
     {
         Pieces pa, pb;
-        make_pieces(pa, A21, ldA, gsA, (int32_t)p2, (int32_t)p1, false, GT_TM, G, s);
-        make_pieces(pb, X, ldM, gsM, (int32_t)p1, (int32_t)p1, false, GT_TN, G, s);
+        make_pieces(pa, A21, ldA, gsA, (int32_t)p2, (int32_t)p1, false, GT_TM, G, mA, s);
+        make_pieces(pb, X, ldM, gsM, (int32_t)p1, (int32_t)p1, false, GT_TN, G, mX, s);
         gemm3(pa, pb, (int32_t)p2, (int32_t)p1, G, 1.f, 0.f, nullptr, 0, 0, U.as<float>(), p1, p2 * p1,
-              err, s);
+              err, s, mU);
         // S = A22 - A21 U^T   (p2 x p2)
         Pieces pu;
-        make_pieces(pu, U.as<float>(), p1, p2 * p1, (int32_t)p2, (int32_t)p1, false, GT_TN, G, s);
+        make_pieces(pu, U.as<float>(), p1, p2 * p1, (int32_t)p2, (int32_t)p1, false, GT_TN, G, mU, s);
         gemm3(pa, pu, (int32_t)p2, (int32_t)p2, G, -1.f, 1.f, A22, ldA, gsA, S.as<float>(), p2, p2 * p2,
               err, s);
     }
     // Y = S^{-1}
     inv_rec(S.as<float>(), p2, p2 * p2, Y, ldM, gsM, p2, G, st, err, s);
     S.release();
+    diag_max(Y, ldM, gsM, p2, G, mY, s);
     {
         // M21 = -Y U   (p2 x p1): A = Y (p2 x p2), B rows = columns of U
         Pieces py, put;
-        make_pieces(py, Y, ldM, gsM, (int32_t)p2, (int32_t)p2, false, GT_TM, G, s);
-        make_pieces(put, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TN, G, s);
-        gemm3(py, put, (int32_t)p2, (int32_t)p1, G, -1.f, 0.f, nullptr, 0, 0, M21, ldM, gsM, err, s);
+        make_pieces(py, Y, ldM, gsM, (int32_t)p2, (int32_t)p2, false, GT_TM, G, mY, s);
+        make_pieces(put, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mU, s);
+        gemm3(py, put, (int32_t)p2, (int32_t)p1, G, -1.f, 0.f, nullptr, 0, 0, M21, ldM, gsM, err, s, mM21);
     }
     {
         // M11 = X - U^T M21   (p1 x p1): A rows = columns of U, B rows = columns of M21
         Pieces pua, pmt;
-        make_pieces(pua, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TM, G, s);
-        make_pieces(pmt, M21, ldM, gsM, (int32_t)p1, (int32_t)p2, true, GT_TN, G, s);
+        make_pieces(pua, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TM, G, mU, s);
+        make_pieces(pmt, M21, ldM, gsM, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mM21, s);
         gemm3(pua, pmt, (int32_t)p1, (int32_t)p1, G, -1.f, 1.f, X, ldM, gsM, X, ldM, gsM, err, s);
     }
     // M12 = M21^T
