@@ -51,6 +51,7 @@ constexpr int XT_THREADS = 192;
 constexpr uint32_t XT_TMEM_COLS = 256;                 // A1[0] at 0, A1[1] at 64, A2 at 128
 constexpr int XT_CHUNK_STAGES = 4;                     // drain h.H every 128 k
 constexpr int XT_SCALE_EXP = 10;                       // scaled magnitudes stay below 2^10
+static_assert(3 * XT_NT_MAX * XT_TM * 4 <= XT_STAGES * XT_STAGE_MAX, "epilogue staging fits the ring");
 
 struct XtArgs {
     int32_t G, q, r, p, nchains, NT, kst, RT, warm;
@@ -70,6 +71,12 @@ struct XtArgs {
     float* norms;                 // slots x RT x 5
     int32_t* err;
 };
+
+// 4-byte asynchronous copy global -> shared (completion waited for by the issuing thread).
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
 
 __device__ __forceinline__ void split2(float x, __half& h, __half& l)
 {
@@ -259,6 +266,22 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         tc_fence_after();
         const bool rowok = i < a.p && !abort_flag;
         const float rinv = rowok ? a.row_inv[(int64_t)g * a.ppad + i] : 0.f;
+        // The ring is idle now: stage this row's z, u and c of every live chain in
+        // it with asynchronous copies, all in flight at once, so the update below
+        // reads shared memory instead of waiting on DRAM once per group of chains.
+        // Each thread copies (and later reads) only its own row: no barrier needed.
+        float* stg = reinterpret_cast<float*>(smem_raw + (sbase - smem_u32(smem_raw)));   // [3][NT][128]
+        const int r128 = quad * 32 + lane;
+        if (rowok) {
+            for (int n = 0; n < a.NT; ++n) {
+                if (!s_live[n]) continue;
+                const int64_t o = ((int64_t)g * a.nchains + n0 + n) * a.p + i;
+                cp_async4(smem_u32(stg + (0 * a.NT + n) * XT_TM + r128), a.z + o);
+                cp_async4(smem_u32(stg + (1 * a.NT + n) * XT_TM + r128), a.u + o);
+                cp_async4(smem_u32(stg + (2 * a.NT + n) * XT_TM + r128), a.c + (int64_t)s_coff[n] * a.p + i);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 #pragma unroll
         for (int cb = 0; cb < 2; ++cb) {
             if (cb * 32 >= a.NT) break;
@@ -267,15 +290,13 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
 #pragma unroll
             for (int t8 = 0; t8 < 32; t8 += 8) {
                 const int nb = cb * 32 + t8;                         // first chain of the group of 8
-                // issue the loads of the 8 chains before any store (they are independent)
                 float zp[8], uo[8], cc[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const bool act = rowok && s_live[nb + t];
-                    const int64_t o = ((int64_t)g * a.nchains + n0 + nb + t) * a.p + i;
-                    zp[t] = act ? a.z[o] : 0.f;
-                    uo[t] = act ? a.u[o] : 0.f;
-                    cc[t] = act ? a.c[(int64_t)s_coff[nb + t] * a.p + i] : 0.f;
+                    zp[t] = act ? stg[(0 * a.NT + nb + t) * XT_TM + r128] : 0.f;
+                    uo[t] = act ? stg[(1 * a.NT + nb + t) * XT_TM + r128] : 0.f;
+                    cc[t] = act ? stg[(2 * a.NT + nb + t) * XT_TM + r128] : 0.f;
                 }
                 float pr[5][8];
 #pragma unroll
