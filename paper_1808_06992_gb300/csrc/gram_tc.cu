@@ -250,9 +250,11 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
     __shared__ float tile[SPLIT_COLS][SPLIT_ROWS + 1];      // [column][row]
     __shared__ int64_t rowoff[SPLIT_ROWS];
     __shared__ float rowsc[SPLIT_ROWS];
-    const int item = blockIdx.z;
-    const int64_t t0 = (int64_t)blockIdx.x * SPLIT_ROWS;
-    const int c0 = blockIdx.y * SPLIT_COLS;
+    // items vary fastest: the items' sorted row lists advance through X at nearly
+    // the same pace, so CTAs launched together read the same rows (L2 hits)
+    const int item = blockIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.y * SPLIT_ROWS;
+    const int c0 = blockIdx.z * SPLIT_COLS;
     const int nr = nrows[item];
     const int pz = pz_x + r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -483,7 +485,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
-        dim3 gs((unsigned)(n_pad / SPLIT_ROWS), (unsigned)ceil_div(pz_pad, SPLIT_COLS), (unsigned)nb);
+        dim3 gs((unsigned)nb, (unsigned)(n_pad / SPLIT_ROWS), (unsigned)ceil_div(pz_pad, SPLIT_COLS));
         k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, X32, ld32, x32_compact ? 1 : 0, Y, ldy, pz_x,
                                              (int32_t)r, colmap,
                                              rows.as<int32_t>() + (size_t)b0 * m,
