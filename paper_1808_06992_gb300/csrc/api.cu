@@ -549,10 +549,13 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
                             true);
         }
     } else {
-        moments(prm->precision, Xd, ldx, Yd, ldy, m, pe, r, west.as<uint32_t>(), nullptr, B2,
-                Gt.as<double>(), Bt.as<double>(), s);
-        moments(prm->precision, Xd, ldx, Yd, ldy, m, pe, r, nullptr, evm.as<uint8_t>(), B2,
-                Ge.as<double>(), Be.as<double>(), s);
+        // FP64 form: the same restriction to U, on the CUDA cores
+        DevBuf ucols(sizeof(int32_t) * (size_t)pe, s);
+        const int32_t nu = union_columns(fe, q * r, pe, ucols.as<int32_t>(), s);
+        moments_fp64_cols(Xd, ldx, Yd, ldy, m, pe, r, nu, ucols.as<int32_t>(), west.as<uint32_t>(), nullptr, B2,
+                          Gt.as<double>(), Bt.as<double>(), s);
+        moments_fp64_cols(Xd, ldx, Yd, ldy, m, pe, r, nu, ucols.as<int32_t>(), nullptr, evm.as<uint8_t>(), B2,
+                          Ge.as<double>(), Be.as<double>(), s);
     }
     masked_sumsq(Yd, ldy, m, r, evm.as<uint8_t>(), B2, yye.as<double>(), s);
     const int t_est1 = tm.mark();

@@ -245,4 +245,51 @@ void check_finite(const double* X, int64_t ldx, int64_t m, int64_t cols, int32_t
     count_launch();
 }
 
+namespace {
+__global__ void k_gather_cols_f64(const double* X, int64_t ldx, int64_t m, const int32_t* cols, int64_t nu,
+                                  double* out)
+{
+    const int64_t total = m * nu;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = X[(t / nu) * ldx + cols[t % nu]];
+}
+
+// G[k][cols[a]][cols[b]] = Gu[k][a][b], Bm[k][cols[a]][e] = Bu[k][a][e].
+__global__ void k_scatter_moments(const double* Gu, const double* Bu, int64_t nu, int64_t r, int32_t B,
+                                  const int32_t* cols, int64_t p_out, double* G, double* Bm)
+{
+    const int64_t per = nu * nu + nu * r, total = per * B;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / per, o = t % per;
+        if (o < nu * nu) {
+            const int64_t a = o / nu, b = o % nu;
+            G[(k * p_out + cols[a]) * p_out + cols[b]] = Gu[k * nu * nu + o];
+        } else {
+            const int64_t q = o - nu * nu, a = q / r, e = q % r;
+            Bm[(k * p_out + cols[a]) * r + e] = Bu[k * nu * r + q];
+        }
+    }
+}
+}  // namespace
+
+void moments_fp64_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p_out,
+                       int64_t r, int64_t nu, const int32_t* cols, const uint32_t* w, const uint8_t* mask,
+                       int32_t B, double* G, double* Bm, cudaStream_t s)
+{
+    if (nu <= 0) return;
+    DevBuf Xu(sizeof(double) * (size_t)(m * nu), s);
+    k_gather_cols_f64<<<(unsigned)std::min<int64_t>(ceil_div(m * nu, 256), 152 * 32), 256, 0, s>>>(
+        X, ldx, m, cols, nu, Xu.as<double>());
+    UOI_CHECK_LAUNCH();
+    DevBuf Gu(sizeof(double) * (size_t)(B * nu * nu), s), Bu(sizeof(double) * (size_t)(B * nu * r), s);
+    moments_fp64(Xu.as<double>(), nu, Y, ldy, m, nu, r, w, mask, B, Gu.as<double>(), Bu.as<double>(), 0, s);
+    const int64_t total = (nu * nu + nu * r) * B;
+    k_scatter_moments<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, s>>>(
+        Gu.as<double>(), Bu.as<double>(), nu, r, B, cols, p_out, G, Bm);
+    UOI_CHECK_LAUNCH();
+    count_launch(2);
+}
+
 }  // namespace uoi

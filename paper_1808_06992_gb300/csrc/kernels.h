@@ -78,6 +78,12 @@ void weight_sums(const uint32_t* w, const uint8_t* mask, int64_t m, int32_t B, d
 void moments_fp64(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
                   int64_t p, int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B,
                   double* G, double* Bm, int b_only, cudaStream_t s);
+// moments_fp64 restricted to the nu X columns listed in cols, written into the
+// p_out x p_out / p_out x r outputs at the original feature indices (other
+// entries untouched).
+void moments_fp64_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p_out,
+                       int64_t r, int64_t nu, const int32_t* cols, const uint32_t* w, const uint8_t* mask,
+                       int32_t B, double* G, double* Bm, cudaStream_t s);
 // yy[k*r + e] = sum_t mask_k[t] Y[t,e]^2.
 void masked_sumsq(const double* Y, int64_t ldy, int64_t m, int64_t r, const uint8_t* mask,
                   int32_t B, double* yy, cudaStream_t s);
