@@ -70,6 +70,9 @@ struct XtArgs {
     const uint8_t* live;
     float* norms;                 // slots x RT x 5
     int32_t* err;
+    const int32_t* tiles;         // live (group, chain tile) list, or null: grid y, z = tile, group
+    const int32_t* ntiles;        // entries of the list in use
+    int32_t nct;                  // chain tiles per group
 };
 
 // 4-byte asynchronous copy global -> shared (completion waited for by the issuing thread).
@@ -109,7 +112,14 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     __shared__ uint8_t s_live[XT_NT_MAX];          // chain exists and is still iterating
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rt = blockIdx.x, ct = blockIdx.y, g = blockIdx.z;
+    int ct = blockIdx.y, g = blockIdx.z;
+    if (a.tiles) {                                     // only the tiles with a live chain
+        if ((int)blockIdx.y >= *a.ntiles) return;
+        const int tl = a.tiles[blockIdx.y];
+        g = tl / a.nct;
+        ct = tl % a.nct;
+    }
+    const int rt = blockIdx.x;
     const int i0 = rt * XT_TM, n0 = ct * a.NT;
     const int nchunks = (a.kst + XT_CHUNK_STAGES - 1) / XT_CHUNK_STAGES;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -564,6 +574,19 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
     }
 }
 
+// List of the (group, chain tile) pairs with a live chain (order unspecified:
+// tiles are independent), one thread per pair.
+__global__ void k_xt_tiles(int32_t G, int32_t nchains, int32_t NT, int32_t nct, const uint8_t* live,
+                           int32_t* tiles, int32_t* ntiles)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)G * nct) return;
+    const int64_t g = t / nct, c0 = (t % nct) * NT;
+    bool any = false;
+    for (int64_t c = c0; c < c0 + NT && c < nchains && !any; ++c) any = live[g * nchains + c] != 0;
+    if (any) tiles[atomicAdd(ntiles, 1)] = (int32_t)t;
+}
+
 __global__ void k_xt_slots(int32_t G, int32_t nchains, int32_t r, int32_t q, int32_t warm,
                            int32_t* slot_j, int32_t* slot_jend, int32_t* slot_it)
 {
@@ -641,7 +664,25 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
     a.row_inv = rinv.as<float>();
     a.slot_j = sj.as<int32_t>(); a.live = live.as<uint8_t>(); a.norms = nb.as<float>();
     a.err = err.as<int32_t>();
-    const dim3 grid((unsigned)RT, (unsigned)ceil_div(nchains, NT), (unsigned)P.G);
+    const int32_t nct = (int32_t)ceil_div(nchains, NT);
+    // wide right-hand sides: launch only the tiles that still have a live chain
+    const bool use_list = nct >= 4 && (int64_t)P.G * nct <= 65535;
+    DevBuf tlist, tcount;
+    int64_t tiles_bound = (int64_t)P.G * nct;
+    a.nct = nct;
+    a.tiles = nullptr;
+    a.ntiles = nullptr;
+    if (use_list) {
+        tlist.alloc(sizeof(int32_t) * (size_t)P.G * nct, s);
+        tcount.alloc(sizeof(int32_t), s);
+        UOI_CUDA(cudaMemsetAsync(tcount.ptr, 0, sizeof(int32_t), s));
+        k_xt_tiles<<<(unsigned)ceil_div((int64_t)P.G * nct, 256), 256, 0, s>>>(
+            P.G, nchains, NT, nct, live.as<uint8_t>(), tlist.as<int32_t>(), tcount.as<int32_t>());
+        UOI_CHECK_LAUNCH();
+        count_launch();
+        a.tiles = tlist.as<int32_t>();
+        a.ntiles = tcount.as<int32_t>();
+    }
     const dim3 gc((unsigned)ceil_div(slots * 32, 256));
     int32_t* host_cnt = pinned_scratch_i32();
     const int64_t bound = (int64_t)(P.warm ? P.q : 1) * P.max_iter + 2;
@@ -656,6 +697,8 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
             a.vs_w = (even ? vs1 : vs0).as<float>();
             UOI_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int32_t), s));
             ktimer_begin(TK_XUPDATE, s);
+            const dim3 grid = use_list ? dim3((unsigned)RT, (unsigned)std::max<int64_t>(1, tiles_bound), 1u)
+                                       : dim3((unsigned)RT, (unsigned)nct, (unsigned)P.G);
             k_xupdate_tc<<<grid, XT_THREADS, XT_SMEM, s>>>(mM, even ? mV0 : mV1, a);
             UOI_CHECK_LAUNCH();
             ktimer_end(TK_XUPDATE, s, 0.0, 0.0);
@@ -668,13 +711,23 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
                                           (even ? vs0 : vs1).as<float>());
             UOI_CHECK_LAUNCH();
             count_launch(2);
+            if (use_list) {
+                UOI_CUDA(cudaMemsetAsync(tcount.ptr, 0, sizeof(int32_t), s));
+                k_xt_tiles<<<(unsigned)ceil_div((int64_t)P.G * nct, 256), 256, 0, s>>>(
+                    P.G, nchains, NT, nct, live.as<uint8_t>(), tlist.as<int32_t>(), tcount.as<int32_t>());
+                UOI_CHECK_LAUNCH();
+                count_launch();
+            }
             if ((it + 1) % 8 == 0 || it + 1 == bound) {
                 int32_t herr = 0;
                 UOI_CUDA(cudaMemcpyAsync(host_cnt, cnt.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                if (use_list)
+                    UOI_CUDA(cudaMemcpyAsync(host_cnt + 1, tcount.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 UOI_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 UOI_CUDA(cudaStreamSynchronize(s));
                 if (herr) throw Error(herr, "tensor-core x-update: a bounded pipeline wait expired");
                 done = *host_cnt == 0;
+                if (use_list) tiles_bound = host_cnt[1];       // tiles only die: a bound for later steps
             }
         }
     } catch (...) {

@@ -102,3 +102,15 @@ def test_var_intercept_tensor_core_xupdate_mixed():
     out = native.uoi_var_fit(v.series, order=2, precision=native.PREC_MIXED, **kw)
     assert rel_l2(out["A"], ref["A"]) <= 1e-5
     assert rel_l2(out["mu"], ref["mu"]) <= 1e-5
+
+
+@pytest.mark.parametrize("p,order,N", [(1, 2, 40), (5, 3, 15)])
+def test_var_small_and_short_series_fp64(p, order, N):
+    # one channel, and a series only a few rows longer than the order
+    v = synth.var_d_problem(p, N, order, 0.5, 0.7, seed=100 + p, mu_scale=1.0, burn_in=30)
+    kw = dict(B1=4, B2=3, q=6, intercept=1)
+    ref = oracle.uoi_var_fit(v.series, order=order, **kw)
+    out = native.uoi_var_fit(v.series, order=order, **kw)
+    assert ref["status"] >= 0
+    assert rel_l2(out["A"], ref["A"]) <= 1e-6
+    assert rel_l2(out["mu"], ref["mu"]) <= 1e-6

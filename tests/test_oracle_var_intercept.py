@@ -219,3 +219,15 @@ def test_var_fit_argument_errors():
     S = np.zeros((5, 3))
     assert oracle.uoi_var_fit_c(S, 2, 2, 2, order=0)[2] == oracle.ERR_INVALID_ARG
     assert oracle.uoi_var_fit_c(S, 2, 2, 2, order=4)[2] == oracle.ERR_INVALID_ARG
+
+
+def test_scalar_ar2_with_intercept_noiseless_recovery():
+    # p = 1, d = 2: s_t = mu + 2 cos(theta) s_{t-1} - s_{t-2}, roots exp(+-i theta)
+    theta, mu = 0.9, 1.5
+    S = np.zeros((60, 1))
+    S[0, 0], S[1, 0] = 2.0, -1.0
+    for t in range(2, 60):
+        S[t, 0] = mu + 2 * np.cos(theta) * S[t - 1, 0] - S[t - 2, 0]
+    out = oracle.uoi_var_fit(S, 4, 3, 8, order=2, intercept=1, block_len=4)
+    np.testing.assert_allclose(out["A"][:, 0, 0], [2 * np.cos(theta), -1.0], atol=1e-10)
+    np.testing.assert_allclose(out["mu"], [mu], atol=1e-10)
