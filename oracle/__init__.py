@@ -60,7 +60,7 @@ class RefParams(C.Structure):
         ("block_len", C.c_int64),
         ("bagging", C.c_int32), ("split_fixed", C.c_int32), ("warm_start", C.c_int32),
         ("n_threads", C.c_int32),
-        ("intercept", C.c_int32),
+        ("intercept", C.c_int32), ("block_mode", C.c_int32),
     ]
 
 
@@ -99,6 +99,7 @@ def lib():
             L.ref_range_map.argtypes = [u64, u64]
             L.ref_range_map.restype = u64
             L.ref_selection_weights.argtypes = [i64, i64, u64, u64, i64, P(C.c_uint32)]
+            L.ref_selection_weights_moving.argtypes = [i64, i64, u64, u64, i64, P(C.c_uint32)]
             L.ref_estimation_weights.argtypes = [i64, i64, d, C.c_int, u64, u64, i64,
                                                  P(C.c_uint32), P(C.c_uint8), P(i64)]
             L.ref_weighted_moments.argtypes = [P(d), i64, P(d), i64, i64, i64, i64,
@@ -152,6 +153,12 @@ def range_map(r, n):
 def selection_weights(m, block_len, seed, problem, k):
     w = np.zeros(m, dtype=np.uint32)
     lib().ref_selection_weights(m, block_len, seed, problem, k, _p(w, C.c_uint32))
+    return w
+
+
+def selection_weights_moving(m, block_len, seed, problem, k):
+    w = np.zeros(m, dtype=np.uint32)
+    lib().ref_selection_weights_moving(m, block_len, seed, problem, k, _p(w, C.c_uint32))
     return w
 
 
@@ -313,7 +320,7 @@ def ols_support(G, b, support_bits):
 
 def make_params(B1, B2, q, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol=1e-6,
                 rel_tol=1e-6, max_iter=1000, train_frac=0.8, seed=0, problem_id=0, block_len=0,
-                bagging=0, split_fixed=0, warm_start=1, n_threads=1, intercept=0):
+                bagging=0, split_fixed=0, warm_start=1, n_threads=1, intercept=0, block_mode=0):
     keep = None
     prm = RefParams()
     prm.B1, prm.B2, prm.q = B1, B2, q
@@ -329,6 +336,7 @@ def make_params(B1, B2, q, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol
     prm.bagging, prm.split_fixed, prm.warm_start = bagging, split_fixed, warm_start
     prm.n_threads = n_threads
     prm.intercept = int(bool(intercept))
+    prm.block_mode = int(block_mode)
     return prm, keep
 
 

@@ -93,6 +93,23 @@ void ref_selection_weights(int64_t m, int64_t block_len, uint64_t seed, uint64_t
     }
 }
 
+/* Moving-block variant (Kunsch's overlapping blocks): ceil(m/L) block starts
+ * drawn uniformly from 0..m-L, each adding one to the L rows it covers.
+ * Reading: an alternative to the non-overlapping blocks of Sec. III-A-2 for
+ * the selection bootstrap only; with L <= 1 it is the row bootstrap. */
+void ref_selection_weights_moving(int64_t m, int64_t block_len, uint64_t seed, uint64_t problem,
+                                  int64_t k, uint32_t* w)
+{
+    int64_t L = unit_len(block_len);
+    int64_t units = (m + L - 1) / L;
+    memset(w, 0, (size_t)m * sizeof(uint32_t));
+    for (int64_t i = 0; i < units; ++i) {
+        uint64_t r = ref_draw(seed, problem, (uint64_t)k, REF_TAG_SELECTION, (uint64_t)i);
+        int64_t start = (int64_t)ref_range_map(r, (uint64_t)(m - L + 1));
+        for (int64_t row = start; row < start + L; ++row) w[row] += 1u;
+    }
+}
+
 typedef struct { uint64_t key; int64_t unit; } keyed_unit;
 
 static int cmp_keyed_unit(const void* a, const void* b)
@@ -581,7 +598,10 @@ int ref_uoi_fit(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         double* v = (double*)malloc((size_t)q * r * p * sizeof(double));
         int32_t* its = (int32_t*)malloc((size_t)q * r * sizeof(int32_t));
         uint8_t* cv = (uint8_t*)malloc((size_t)q * r);
-        ref_selection_weights(m, prm->block_len, prm->seed, prm->problem_id, k, w);
+        if (prm->block_mode == 1)
+            ref_selection_weights_moving(m, prm->block_len, prm->seed, prm->problem_id, k, w);
+        else
+            ref_selection_weights(m, prm->block_len, prm->seed, prm->problem_id, k, w);
         int st = icpt ? ref_lasso_admm_intercept(X, ldx, Y, ldy, m, p, r, w, lam, q, prm->rho,
                                                  prm->abs_tol, prm->rel_tol, prm->max_iter,
                                                  prm->warm_start, beta, NULL, its, cv, v)

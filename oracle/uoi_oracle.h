@@ -68,6 +68,14 @@ uint64_t ref_range_map(uint64_t r, uint64_t n);
 void ref_selection_weights(int64_t m, int64_t block_len, uint64_t seed, uint64_t problem,
                            int64_t k, uint32_t* w);
 
+/* Moving-block selection bootstrap (Kunsch's overlapping blocks, the
+ * alternative to the non-overlapping blocks above): ceil(m/L) starts, start i =
+ * floor(r_i (m - L + 1) / 2^64) from draw i of stream (k, REF_TAG_SELECTION);
+ * each adds one to rows start .. start+L-1.  L <= 1: identical to
+ * ref_selection_weights.  Requires L <= m. */
+void ref_selection_weights_moving(int64_t m, int64_t block_len, uint64_t seed, uint64_t problem,
+                                  int64_t k, uint32_t* w);
+
 /* Estimation split for bootstrap k (Alg. 1/2 estimation loop, Fig. 1(c)):
  * units (rows or blocks) are reshuffled by sorting (draw, unit index); the
  * first floor(train_frac * units) units form the training pool, the rest the
@@ -173,6 +181,7 @@ typedef struct {
     int32_t warm_start;        /* 0 cold, 1 path */
     int32_t n_threads;         /* <= 1: sequential */
     int32_t intercept;         /* 1: every fit gains an unpenalised offset mu */
+    int32_t block_mode;        /* selection blocks: 0 non-overlapping, 1 moving */
 } ref_params;
 
 /* Optional intermediate outputs (every pointer nullable). */
