@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--order", type=int, default=1, help="VAR workloads: lag order d of the design")
     ap.add_argument("--intercept", type=int, default=0, choices=[0, 1],
                     help="VAR workloads: fit the unpenalised intercept mu")
+    ap.add_argument("--block-mode", default="fixed", choices=["fixed", "moving"],
+                    help="selection blocks of the block bootstrap: non-overlapping or moving")
+    ap.add_argument("--split", default="per_bootstrap", choices=["per_bootstrap", "fixed"],
+                    help="estimation split: a fresh reshuffle per bootstrap or one for all")
+    ap.add_argument("--bagging", default=None, choices=["median", "mean"],
+                    help="bagging of the chosen estimates (default: the workload's)")
     return ap.parse_args()
 
 
@@ -128,8 +134,10 @@ def workload(wid, order=1):
 
 def fit_kwargs(w, args):
     from paper_1808_06992_gb300 import native
+    bag = w.bagging if args.bagging is None else (1 if args.bagging == "mean" else 0)
     return dict(B1=args.B1 or w.B1, B2=args.B2 or w.B2, q=args.q or w.q, block_len=w.block_len,
-                bagging=w.bagging,
+                bagging=bag, block_mode=1 if args.block_mode == "moving" else 0,
+                split_mode=native.SPLIT_FIXED if args.split == "fixed" else native.SPLIT_PER_BOOTSTRAP,
                 precision=native.PREC_MIXED if args.precision == "mixed" else native.PREC_FP64,
                 warm_start=native.WARM_PATH if args.warm == "path" else native.WARM_NONE,
                 intercept=args.intercept if w.kind == "var" else 0)
@@ -275,6 +283,11 @@ def main():
     overrides = {k: getattr(args, k) for k in ("B1", "B2", "q", "rows") if getattr(args, k)}
     if w.kind == "var" and (args.order != 1 or args.intercept):
         overrides.update(order=args.order, intercept=args.intercept)
+    for k, dflt in (("block_mode", "fixed"), ("split", "per_bootstrap")):
+        if getattr(args, k) != dflt:
+            overrides[k] = getattr(args, k)
+    if args.bagging is not None:
+        overrides["bagging"] = args.bagging
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream().cuda_stream

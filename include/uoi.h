@@ -59,6 +59,10 @@ extern "C" {
 #define UOI_WARM_NONE    0   /* every (bootstrap, lambda) column starts at z = u = 0 */
 #define UOI_WARM_PATH    1   /* lambda descending; column j starts from j-1's (z,u)  */
 #define UOI_WARM_LEARNED 2   /* learned initial (z,u) (MLP); judged by PATH          */
+#define UOI_BLOCKS_FIXED  0  /* selection units: consecutive non-overlapping blocks */
+#define UOI_BLOCKS_MOVING 1  /* selection units: ceil(m/L) blocks starting anywhere
+                                in 0..m-L (overlapping, Kunsch); estimation split
+                                keeps the non-overlapping units                       */
 
 /* Parameters of a fit (Alg. 1 / Alg. 2 inputs lambda, B1, B2 plus the ADMM
  * and bootstrap settings).  Zero-initialise, set struct_size = sizeof(uoi_params)
@@ -86,6 +90,9 @@ typedef struct uoi_params {
     int32_t  intercept;         /* 1 = fit an unpenalised offset mu per response       */
                                 /* (uoi_var_fit and uoi_fit_traced; 0 = none).         */
                                 /* A struct_size that ends before this field reads 0.  */
+    int32_t  block_mode;        /* UOI_BLOCKS_*: selection blocks of block_len rows,   */
+                                /* non-overlapping (0) or moving (1); read as 0 when   */
+                                /* struct_size ends before this field.                 */
 } uoi_params;
 
 /* Timings and counters of the last fit (every field written when non-NULL). */

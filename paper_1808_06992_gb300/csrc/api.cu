@@ -221,6 +221,14 @@ int32_t param_intercept(const uoi_params* prm)
     return prm->intercept;
 }
 
+// prm->block_mode, or 0 for a caller whose struct ends before that field.
+int32_t param_block_mode(const uoi_params* prm)
+{
+    if (prm->struct_size != 0 && prm->struct_size < offsetof(uoi_params, block_mode) + sizeof(int32_t))
+        return 0;
+    return prm->block_mode;
+}
+
 void validate(const uoi_params* prm)
 {
     if (!prm) throw Error(UOI_ERR_INVALID_ARG, "params is NULL");
@@ -228,6 +236,8 @@ void validate(const uoi_params* prm)
         throw Error(UOI_ERR_INVALID_ARG, "uoi_params.struct_size too small");
     if (param_intercept(prm) != 0 && param_intercept(prm) != 1)
         throw Error(UOI_ERR_INVALID_ARG, "intercept must be 0 or 1");
+    if (param_block_mode(prm) != UOI_BLOCKS_FIXED && param_block_mode(prm) != UOI_BLOCKS_MOVING)
+        throw Error(UOI_ERR_INVALID_ARG, "unknown block mode");
     if (prm->B1 <= 0 || prm->B2 <= 0 || prm->q <= 0)
         throw Error(UOI_ERR_INVALID_ARG, "B1, B2 and q must be positive");
     if (!(prm->rho > 0.0)) throw Error(UOI_ERR_INVALID_ARG, "rho must be positive");
@@ -485,7 +495,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     // ---- selection ----
     const int t_sel0 = tm.mark();
     DevBuf wsel(sizeof(uint32_t) * (size_t)(B1 * m), s);
-    selection_weights(m, prm->block_len, key, B1, wsel.as<uint32_t>(), s);
+    selection_weights(m, prm->block_len, key, B1, wsel.as<uint32_t>(), s, param_block_mode(prm));
     const int t_sel1 = tm.mark();
     const int64_t ncol = (int64_t)B1 * q * r;
     DevOut<double> sel_beta;

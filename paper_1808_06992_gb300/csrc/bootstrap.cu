@@ -39,6 +39,29 @@ __global__ void k_selection(int64_t m, int64_t L, int64_t units, PhiloxKey key, 
     }
 }
 
+// Moving blocks: draw i of bootstrap k starts a run of L rows at
+// floor(r_i (m - L + 1) / 2^64); one thread per Philox block of 4 draws.
+__global__ void k_selection_moving(int64_t m, int64_t L, int64_t units, PhiloxKey key, int32_t B,
+                                   uint32_t* w)
+{
+    const int64_t blocks = (units + 3) / 4;
+    const int64_t total = blocks * B;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / blocks, blk = t % blocks;
+        uint64_t c[4] = { (uint64_t)blk, (uint64_t)k, TAG_SELECTION, 0 };
+        philox4x64_10(c, key.seed, key.problem);
+        uint32_t* wk = w + k * m;
+#pragma unroll
+        for (int lane = 0; lane < 4; ++lane) {
+            const int64_t i = blk * 4 + lane;
+            if (i >= units) continue;
+            const int64_t start = (int64_t)range_map(c[lane], (uint64_t)(m - L + 1));
+            for (int64_t row = start; row < start + L; ++row) atomicAdd(&wk[row], 1u);
+        }
+    }
+}
+
 // Reshuffle keys: key[k][u] and bucket counts (bucket = floor(key * units / 2^64)).
 __global__ void k_split_keys(int64_t units, PhiloxKey key, int32_t Bk, int split_fixed,
                              uint64_t* keys, uint32_t* counts)
@@ -191,13 +214,16 @@ int grid_for(int64_t work, int threads)
 }  // namespace
 
 void selection_weights(int64_t m, int64_t block_len, PhiloxKey key, int32_t B, uint32_t* w,
-                       cudaStream_t s)
+                       cudaStream_t s, int32_t block_mode)
 {
     const int64_t L = block_len > 1 ? block_len : 1;
     const int64_t units = (m + L - 1) / L;
     UOI_CUDA(cudaMemsetAsync(w, 0, sizeof(uint32_t) * (size_t)(m * B), s));
     const int64_t work = ((units + 3) / 4) * B;
-    k_selection<<<grid_for(work, 256), 256, 0, s>>>(m, L, units, key, B, w);
+    if (block_mode == 1 && L > 1)
+        k_selection_moving<<<grid_for(work, 256), 256, 0, s>>>(m, L, units, key, B, w);
+    else
+        k_selection<<<grid_for(work, 256), 256, 0, s>>>(m, L, units, key, B, w);
     UOI_CHECK_LAUNCH();
     count_launch();
 }

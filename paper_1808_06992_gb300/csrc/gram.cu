@@ -167,8 +167,19 @@ __global__ void k_xty_partial(const double* X, int64_t ldx, const double* Y, int
     const int64_t t0 = c * XTY_ROWS, t1 = min(m, t0 + XTY_ROWS);
     double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
     if (j < p) {
-#pragma unroll 8
-        for (int64_t t = t0; t < t1; ++t) {
+        // batches of 8 rows: all eight loads issued before the multiply-adds
+        int64_t t = t0;
+        for (; t + 8 <= t1; t += 8) {
+            double xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xv[u] = __ldg(X + (t + u) * ldx + j);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e < r) acc[e] = fma(xv[u], __ldg(Y + (t + u) * ldy + e), acc[e]);
+        }
+        for (; t < t1; ++t) {
             const double x = X[t * ldx + j];
 #pragma unroll
             for (int e = 0; e < 4; ++e)

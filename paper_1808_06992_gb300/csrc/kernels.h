@@ -61,8 +61,9 @@ int32_t* pinned_scratch_i32();
 
 // ---- G0: bootstrap indices (bootstrap.cu) -----------------------------------
 // w[k*m + row] = multiplicity of the row in selection bootstrap k, k < B.
+// block_mode 1: moving blocks (starts uniform on 0..m-L) instead of non-overlapping.
 void selection_weights(int64_t m, int64_t block_len, PhiloxKey key, int32_t B, uint32_t* w,
-                       cudaStream_t s);
+                       cudaStream_t s, int32_t block_mode = 0);
 // Training multiplicities and evaluation masks of estimation bootstraps k < B.
 void estimation_weights(int64_t m, int64_t block_len, double train_frac, int split_fixed,
                         PhiloxKey key, int32_t B, uint32_t* w_train, uint8_t* eval,

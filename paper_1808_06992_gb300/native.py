@@ -32,7 +32,7 @@ class UoiParams(C.Structure):
         ("train_frac", C.c_double), ("seed", C.c_uint64), ("problem_id", C.c_uint64),
         ("block_len", C.c_int64), ("bagging", C.c_int32), ("split_mode", C.c_int32),
         ("precision", C.c_int32), ("warm_start", C.c_int32), ("mlp_weights_path", C.c_char_p),
-        ("stream", C.c_void_p), ("intercept", C.c_int32),
+        ("stream", C.c_void_p), ("intercept", C.c_int32), ("block_mode", C.c_int32),
     ]
 
 
@@ -165,7 +165,7 @@ def _empty(like, shape, dtype):
 def make_params(B1=20, B2=20, q=16, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol=1e-6,
                 rel_tol=1e-6, max_iter=1000, train_frac=0.8, seed=0, problem_id=0, block_len=0,
                 bagging=BAG_MEDIAN, split_mode=SPLIT_PER_BOOTSTRAP, precision=PREC_FP64,
-                warm_start=WARM_PATH, stream=None, mlp_weights_path=None, intercept=0):
+                warm_start=WARM_PATH, stream=None, mlp_weights_path=None, intercept=0, block_mode=0):
     prm = UoiParams()
     lib().uoi_params_default(C.byref(prm))
     prm.B1, prm.B2, prm.q = B1, B2, q
@@ -180,6 +180,7 @@ def make_params(B1=20, B2=20, q=16, lambdas=None, lambda_min_ratio=1e-3, rho=1.0
     prm.precision, prm.warm_start = precision, warm_start
     prm.stream = stream
     prm.intercept = int(intercept)
+    prm.block_mode = int(block_mode)
     if mlp_weights_path:
         prm.mlp_weights_path = mlp_weights_path.encode()
     return prm, keep

@@ -48,8 +48,9 @@ def compare_fit(ref, gpu, X, Y, lam_tol=1e-13, coef_tol=1e-6, check_weights=True
     # bootstrap indices: bit-exact
     if check_weights:
         blk = kw.get("block_len", 0)
+        sel = oracle.selection_weights_moving if kw.get("block_mode", 0) == 1 else oracle.selection_weights
         for k in range(B1):
-            want = oracle.selection_weights(m, blk, kw.get("seed", 0), kw.get("problem_id", 0), k)
+            want = sel(m, blk, kw.get("seed", 0), kw.get("problem_id", 0), k)
             np.testing.assert_array_equal(gpu["sel_weights"][k], want)
         B2 = ref["est_loss"].shape[0]
         for k in range(B2):

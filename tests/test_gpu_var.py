@@ -114,3 +114,17 @@ def test_var_small_and_short_series_fp64(p, order, N):
     assert ref["status"] >= 0
     assert rel_l2(out["A"], ref["A"]) <= 1e-6
     assert rel_l2(out["mu"], ref["mu"]) <= 1e-6
+
+
+@pytest.mark.parametrize("order,icpt", [(1, 0), (2, 1)])
+def test_moving_block_bootstrap_full_trace_fp64(order, icpt):
+    # moving (overlapping) selection blocks: weights bit-exact, then the whole trace
+    v = synth.var_d_problem(10, 300, order, 0.15, 0.85, seed=110 + order, mu_scale=1.0, burn_in=100)
+    X, Y = lagged(v.series, order)
+    kw = dict(B1=5, B2=4, q=8, block_len=23, intercept=icpt, block_mode=1)
+    ref = oracle.uoi_fit(X, Y, **kw)
+    gpu = native.uoi_fit_traced(X, Y, precision=native.PREC_FP64, **kw)
+    rep = compare_fit(ref, gpu, X, Y, **kw)
+    assert rep["family_clean"]
+    fixed = native.uoi_fit_traced(X, Y, precision=native.PREC_FP64, **dict(kw, block_mode=0))
+    assert not np.array_equal(fixed["sel_weights"], gpu["sel_weights"])

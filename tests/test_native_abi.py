@@ -89,11 +89,18 @@ def test_intercept_argument_checks():
     assert ei.value.status == native.ERR_UNSUPPORTED
 
 
+def test_block_mode_checked():
+    with pytest.raises(native.UoiError) as ei:
+        native.uoi_var_fit(np.zeros((10, 3)), order=1, B1=2, B2=2, q=2, block_mode=2)
+    assert ei.value.status == native.ERR_INVALID_ARG
+
+
 def test_params_struct_matches_header():
     # the binding's struct ends with the intercept field, as uoi.h declares it
     prm, _ = native.make_params()
     assert prm.struct_size == C.sizeof(native.UoiParams)
     assert native.UoiParams.intercept.offset + 4 <= C.sizeof(native.UoiParams)
+    assert native.UoiParams.block_mode.offset == native.UoiParams.intercept.offset + 4
 
 
 def test_null_pointer_rejected():
