@@ -232,14 +232,17 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // write transposed: out[((item*2 + piece) * pz_pad + col) * n_pad + t].  Values
 // are taken to FP32 first (relative error 2^-23 after the scaling, below the
 // 2^-17 residue of the two-piece split).  A block covers 128 sample rows x 32
-// columns: each warp reads 16 row segments of 128 B (all loads issued before
-// any shared-memory store) into a column-major tile whose odd row length keeps
-// both phases free of bank conflicts, then writes 128-byte runs of paired bf16
-// along the rows of each column.  It also writes the FP32 sum of lo^2 of each
-// column over each 64 rows (losq[(item*row_tiles + tile)*pz_x + col]), from
-// which the diagonal correction is reduced in a fixed order.
+// columns: warp w reads rows 16w .. 16w+15 (16 row segments of 128 B, all loads
+// issued before any shared-memory store) and stores each column's 16 values as
+// four 16-byte vectors into a column-major tile; with a row length of 132 floats
+// both the vector stores and the vector reads of the second phase are free of
+// bank conflicts.  Then each lane turns four consecutive rows of a column into
+// 8-byte runs of bf16 hi and lo.  It also writes the FP32 sum of lo^2 of each
+// column over each 64 rows (losq[(item*row_tiles + tile)*pz_x + col], a fixed
+// order), from which the diagonal correction is reduced in a fixed order.
 constexpr int SPLIT_ROWS = 128;
 constexpr int SPLIT_COLS = 32;
+constexpr int SPLIT_LD = SPLIT_ROWS + 4;
 __global__ void __launch_bounds__(256)
 k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, int32_t x32_compact,
                   const double* Y, int64_t ldy, int32_t pz_x, int32_t r, const int32_t* colmap,
@@ -247,7 +250,7 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
                   const float* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
                   int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq)
 {
-    __shared__ float tile[SPLIT_COLS][SPLIT_ROWS + 1];      // [column][row]
+    __shared__ __align__(16) float tile[SPLIT_COLS][SPLIT_LD];      // [column][row]
     __shared__ int64_t rowoff[SPLIT_ROWS];
     __shared__ float rowsc[SPLIT_ROWS];
     // items vary fastest: the items' sorted row lists advance through X at nearly
@@ -264,15 +267,15 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
         rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.f;
     }
     __syncthreads();
-    // read: warp w takes rows w, w + 8, ...; lane = column
+    // read: warp w takes rows 16w .. 16w + 15; lane = column
     {
         const int c = c0 + lane;
         const int64_t col = colmap && c < pz_x ? colmap[c] : c;      // column of X
         const int64_t col32 = x32_compact ? c : col;                 // column of the FP32 copy
-        float q[SPLIT_ROWS / 8];
+        float q[16];
 #pragma unroll
-        for (int i = 0; i < SPLIT_ROWS / 8; ++i) {
-            const int64_t row = rowoff[warp + 8 * i];
+        for (int i = 0; i < 16; ++i) {
+            const int64_t row = rowoff[16 * warp + i];
             float v = 0.f;
             if (row >= 0 && c < pz) {
                 if (c < pz_x)
@@ -283,35 +286,45 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
             q[i] = v;
         }
 #pragma unroll
-        for (int i = 0; i < SPLIT_ROWS / 8; ++i) {
-            const int tl = warp + 8 * i;
-            tile[lane][tl] = q[i] * rowsc[tl];
+        for (int i4 = 0; i4 < 4; ++i4) {
+            const int tl = 16 * warp + 4 * i4;
+            *reinterpret_cast<float4*>(&tile[lane][tl]) =
+                make_float4(q[4 * i4] * rowsc[tl], q[4 * i4 + 1] * rowsc[tl + 1], q[4 * i4 + 2] * rowsc[tl + 2],
+                            q[4 * i4 + 3] * rowsc[tl + 3]);
         }
     }
     __syncthreads();
     // write: warp w takes columns w, w + 8, w + 16, w + 24; lane covers rows
-    // 2*lane, 2*lane + 1 of each half of the 128 rows
+    // 4*lane .. 4*lane + 3 (lanes 0-15: the first 64 rows, 16-31: the second)
 #pragma unroll
     for (int j = 0; j < SPLIT_COLS / 8; ++j) {
         const int cl = warp + 8 * j;
         const int cc = c0 + cl;
         if (cc >= pz_pad) break;
+        const float4 v = *reinterpret_cast<const float4*>(&tile[cl][4 * lane]);
+        const float vv[4] = { v.x, v.y, v.z, v.w };
+        __nv_bfloat16 h[4], l[4];
+        float sq = 0.f;
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int r0 = hh * 64 + 2 * lane;
-            const float v0 = tile[cl][r0], v1 = tile[cl][r0 + 1];
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-            const float e0 = v0 - __bfloat162float(h0), e1 = v1 - __bfloat162float(h1);   // exact
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(e0), l1 = __float2bfloat16_rn(e1);
-            const int64_t base_hi = (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0 + r0;
-            const int64_t base_lo = (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0 + r0;
-            *reinterpret_cast<__nv_bfloat162*>(out + base_hi) = __halves2bfloat162(h0, h1);
-            *reinterpret_cast<__nv_bfloat162*>(out + base_lo) = __halves2bfloat162(l0, l1);
-            if (cc < pz_x) {
-                const float f0 = __bfloat162float(l0), f1 = __bfloat162float(l1);
-                const float sq = warp_sum(f0 * f0 + f1 * f1);
-                if (lane == 0) losq[((int64_t)item * row_tiles + (t0 / 64) + hh) * pz_x + cc] = sq;
-            }
+        for (int t = 0; t < 4; ++t) {
+            h[t] = __float2bfloat16_rn(vv[t]);
+            l[t] = __float2bfloat16_rn(vv[t] - __bfloat162float(h[t]));   // exact difference
+            const float f = __bfloat162float(l[t]);
+            sq += f * f;
+        }
+        __nv_bfloat16* base_hi = out + (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0;
+        __nv_bfloat16* base_lo = out + (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0;
+        const __nv_bfloat162 h01 = __halves2bfloat162(h[0], h[1]), h23 = __halves2bfloat162(h[2], h[3]);
+        const __nv_bfloat162 l01 = __halves2bfloat162(l[0], l[1]), l23 = __halves2bfloat162(l[2], l[3]);
+        *reinterpret_cast<uint2*>(base_hi + 4 * lane) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+        *reinterpret_cast<uint2*>(base_lo + 4 * lane) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+        if (cc < pz_x) {
+            // sum over the 16 lanes of each 64-row half (fixed order)
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if ((lane & 15) == 0) losq[((int64_t)item * row_tiles + (t0 / 64) + (lane >> 4)) * pz_x + cc] = sq;
         }
     }
 }
