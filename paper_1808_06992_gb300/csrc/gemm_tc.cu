@@ -276,17 +276,22 @@ __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t
         }
     }
     __syncthreads();
+    // write: thread (row jj, k quad kq) splits four consecutive k of one row and
+    // stores 8-byte runs of each piece (conflict-free reads: bank = kq + u + jj)
     const int64_t RT = rpad / rt, kst = kpad / GT_TK;
-    const int64_t k = k0 + tx;
-    for (int j = ty; j < 32; j += 8) {
-        const int64_t i = i0 + j;
-        __half h, l;
-        split2(tile[tx][j] * sc, h, l);
-        const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * GT_PIECES;
-        const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;
-        out[o] = h;
-        out[o + rt * GT_TK] = l;
-    }
+    const int t = ty * 32 + tx, jj = t >> 3, kq = (t & 7) << 2;
+    const int64_t i = i0 + jj, k = k0 + kq;
+    __half h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) split2(tile[kq + u][jj] * sc, h[u], l[u]);
+    const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * GT_PIECES;
+    const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;             // multiple of 4
+    const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
+    const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
+    *reinterpret_cast<uint2*>(out + o) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    *reinterpret_cast<uint2*>(out + o + rt * GT_TK) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
 }
 
 // out[g] = largest diagonal entry of the SPD block A_g (n x n), as float bits:
