@@ -247,7 +247,7 @@ int lasso_admm_batch_noalloc(const double* X, const double* Y, int64_t n, int64_
                              int32_t warm_start, double* beta_out, int32_t* iters_out,
                              uint8_t* converged_out, void* stream);
 
-/* ---- learned warm start (spec extension; the paper warm-starts nothing) ----
+/* ---- learned warm start (an extension: the paper warm-starts nothing) ----
  * A per-feature network (8 inputs -> 3 hidden layers of 512 with GELU -> 3
  * outputs, BF16 weights, FP32 accumulation) predicts the converged scaled ADMM
  * state (scaled z, rho u/lambda, active logit) of every (bootstrap, lambda,
