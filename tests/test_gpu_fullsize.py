@@ -160,3 +160,51 @@ def test_lasso_50000x2000_mixed_fullsize_sampled():
         beta = np.zeros(p)
         beta[S] = np.linalg.solve(Gs, bs)
         assert rel_l2(out["est_beta"][k2, 0], beta) <= 1e-5
+
+
+def test_var2_intercept_p192_fullsize_sampled_mixed():
+    # workload 3's series as a VAR(2) with intercept: P = 384 > 192 runs the
+    # tensor-core x-update on the eliminated moments of [X~ 1]
+    w = synth.WORKLOADS[3]
+    S = synth.workload_data(3).series
+    N, p = S.shape
+    X = np.ascontiguousarray(np.concatenate([S[1:N - 1], S[0:N - 2]], axis=1))
+    Y = np.ascontiguousarray(S[2:])
+    m, P = X.shape
+    kw = dict(B1=w.B1, B2=w.B2, q=w.q, block_len=w.block_len, intercept=1, warm_start=native.WARM_NONE)
+    out = _gpu_fit(X, Y, native.PREC_MIXED, **kw)
+    assert out["beta"].shape == (p, P + 1)
+    _check_properties(out, P, p)
+    # selection columns of sampled (bootstrap, equation) pairs vs the oracle's
+    # intercept LASSO on the same bootstrap weights
+    mism, worst = 0, 0.0
+    for k in (0, w.B1 - 1):
+        wk = out["sel_weights"][k]
+        np.testing.assert_array_equal(wk, oracle.selection_weights(m, w.block_len, 0, 0, k))
+        for e in (3, 150):
+            ref = oracle.lasso_admm_intercept(X, Y[:, e], wk, out["lambdas"], warm_start=0)
+            for j in range(w.q):
+                g = out["sel_beta"][k, j, e]
+                rz = ref["beta"][j, 0]
+                worst = max(worst, rel_l2(g, rz))
+                amb = (np.abs(np.abs(ref["v"][j, 0]) - out["lambdas"][j]) <= 1e-6) | ((np.abs(rz) <= 1e-6) & (rz != 0))
+                mism += int(((g != 0) != (rz != 0))[~amb].sum())
+    assert worst <= 1e-3, worst
+    assert mism <= 4, mism
+    # estimation: OLS with the intercept and held-out losses of sampled (k, j, e)
+    Xa = np.concatenate([X, np.ones((m, 1))], axis=1)
+    Wa = (P + 1 + 63) // 64
+    for k in (0, w.B2 - 1):
+        wt = out["est_weights"][k]
+        ev = out["est_eval"][k].astype(bool)
+        G, B = oracle.weighted_moments(Xa, Y, wt)
+        for j in (0, w.q // 2, w.q - 1):
+            for e in (3, 150):
+                bits = np.zeros(Wa, dtype=np.uint64)
+                fam = out["family"][j, e].astype(np.uint64)
+                bits[:fam.shape[0]] = fam
+                bits[P // 64] |= np.uint64(1) << np.uint64(P % 64)
+                beta, _ = oracle.ols_support(G, B[:, e], bits)
+                res = Y[ev, e] - Xa[ev] @ beta
+                want = float(res @ res)
+                assert abs(out["est_loss"][k, j, e] - want) <= 2e-5 * max(want, 1e-12)
