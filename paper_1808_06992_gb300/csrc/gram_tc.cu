@@ -18,13 +18,17 @@
 // Two kernels:
 //  * k_split_transpose: gather rows (with weights), split, and write the two
 //    bf16 pieces transposed (features x rows, rows contiguous = K-major).
-//  * k_gram_tc: one CTA per (128 x 256 tile of the lower triangle, item).
-//    Warp 0 issues TMA loads of K-major SWIZZLE_64B tiles into a 4-stage
-//    ring; warp 1 issues tcgen05.mma (M=128, N=256, K=16, bf16 -> f32: the wide
-//    N keeps the shared-memory operand traffic below what the tensor core
-//    consumes) into one of two TMEM accumulators; warps 2-9 drain the other
-//    accumulator (tcgen05.ld) into their registers.  Every wait is bounded
-//    (about one second) and reports UOI_ERR_TIMEOUT.
+//  * k_gram_tc: one cluster of two CTAs per (256 x 256 block of the lower
+//    triangle, item): row tiles 2m and 2m+1 need the same column tiles, and the
+//    pair computes both with M = 256 products (tcgen05 cta_group::2).  Each CTA
+//    stages its own 128 rows of A and one half (128 columns) of B, so a stage
+//    is 32 KB per SM instead of 48 and six fit in shared memory; the first CTA
+//    issues the pair's MMAs and each CTA's TMEM receives its own 128 x 256
+//    tile.  Warp 0 issues TMA loads of K-major SWIZZLE_64B tiles (completion
+//    counted on the first CTA's barrier); warp 1 of the first CTA issues
+//    tcgen05.mma (bf16 -> f32) into one of two TMEM accumulators; warps 2-9 of
+//    both CTAs drain the other accumulator (tcgen05.ld) into their registers.
+//    Every wait is bounded (about one second) and reports UOI_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -41,15 +45,16 @@ namespace uoi {
 namespace {
 using namespace tc;
 
-constexpr int TM = 128;                 // tile rows (UMMA M)
-constexpr int TN = 256;                 // tile cols (UMMA N): 12 KB of operands per 128 cycles
+constexpr int TM = 128;                 // tile rows per CTA (the pair's UMMA M is 256)
+constexpr int TN = 256;                 // tile cols (UMMA N), 128 staged by each CTA
 constexpr int TK = 32;                  // rows of the sample per stage (64 B of bf16, 64-byte swizzle)
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int CHUNK_STAGES = 4;         // 128 sample rows per FP32 accumulation chunk
 constexpr int A_BYTES = TM * TK * 2;    // 8 KB per piece
-constexpr int B_BYTES = TN * TK * 2;    // 16 KB per piece
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
+constexpr int BH_BYTES = (TN / 2) * TK * 2;              // this CTA's half of B: 8 KB per piece
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * BH_BYTES;  // 32 KB per CTA
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+static_assert(TN == 2 * TM, "a pair of row tiles spans one column tile");
 constexpr uint32_t TMEM_COLS = 512;     // two 256-column FP32 accumulators
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA, 8 epilogue warps
@@ -61,8 +66,8 @@ struct GramTcArgs {
     int32_t pz_x;             // columns of Z that come from X (= p, or |U| with a subset)
     int32_t r;
     int32_t p_out;            // leading size of the G / Bm outputs
-    int32_t ntiles;
-    const int32_t* tiles;     // (ti, tj) pairs
+    int32_t ntiles;           // tile pairs (clusters per item)
+    const int32_t* tiles;     // (m, tj): row tiles 2m (first CTA) and 2m+1, column tile tj
     const int32_t* nrows;     // per item: sample rows (K extent actually used)
     const int32_t* colmap;    // Z column (< pz_x) -> output feature index, or null
     double* G;                // items x p_out x p_out
@@ -71,8 +76,7 @@ struct GramTcArgs {
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
-k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          GramTcArgs a)
+k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], done_bar;
@@ -80,35 +84,43 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = blockIdx.x & 1;                 // 0: the CTA that issues the pair's MMAs
+    const int pr = blockIdx.x >> 1;                  // the cluster (2 CTAs along x)
     const int item = blockIdx.y;
-    const int ti = a.tiles[2 * blockIdx.x], tj = a.tiles[2 * blockIdx.x + 1];
+    const int ti = 2 * a.tiles[2 * pr] + rank, tj = a.tiles[2 * pr + 1];
     const int rows = a.nrows[item];
     const int kstages = (rows + TK - 1) / TK;
     const int nchunks = (kstages + CHUNK_STAGES - 1) / CHUNK_STAGES;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
     if (threadIdx.x == 0) {
+        // full: the first CTA's arrival plus the bytes of both CTAs' loads;
+        // empty / accumulator ready / done: one arrival from the pair's commit;
+        // accumulator drained: every epilogue thread of both CTAs
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 32 * EPI_WARPS); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 2 * 32 * EPI_WARPS); }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+        // the same TMEM columns in both CTAs (one warp of each allocates)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
                      "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();                  // both CTAs' barriers and TMEM exist before either uses the other's
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
     if (warp == 0 && lane == 0 && kstages > 0) {
-        // ---------------- TMA producer ----------------
-        const int zA = item * 2, zB = item * 2;
+        // ---------------- TMA producer (both CTAs) ----------------
+        const int zA = item * 2;
+        const int jb = tj * TN + rank * (TN / 2);    // this CTA's half of the column tile
         for (int g = 0; g < kstages; ++g) {
             const int s = g % STAGES;
             if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1, &abort_flag)) {
@@ -117,25 +129,26 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 break;
             }
             const uint32_t st = sbase + s * STAGE_BYTES;
-            mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+            if (rank == 0) mbar_expect_tx(&full_bar[s], 2 * STAGE_BYTES);
+            const uint32_t fb = cluster_addr(&full_bar[s], 0);
             const int k0 = g * TK;
-            tma_load_3d(st, &tmA, &full_bar[s], k0, ti * TM, zA);                       // A hi
-            tma_load_3d(st + A_BYTES, &tmA, &full_bar[s], k0, ti * TM, zA + 1);         // A lo
-            tma_load_3d(st + 2 * A_BYTES, &tmB, &full_bar[s], k0, tj * TN, zB);         // B hi
-            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tmB, &full_bar[s], k0, tj * TN, zB + 1);  // B lo
+            tma_load_3d_pair(st, &tmA, fb, k0, ti * TM, zA);                              // A hi
+            tma_load_3d_pair(st + A_BYTES, &tmA, fb, k0, ti * TM, zA + 1);                // A lo
+            tma_load_3d_pair(st + 2 * A_BYTES, &tmA, fb, k0, jb, zA);                     // B hi (half)
+            tma_load_3d_pair(st + 2 * A_BYTES + BH_BYTES, &tmA, fb, k0, jb, zA + 1);      // B lo (half)
         }
-        if (abort_flag) {
+        if (abort_flag && rank == 0) {
             // let the copies already issued land before the CTA releases its memory
             for (int g = max(0, kstages - STAGES); g < kstages; ++g)
                 mbar_wait(&full_bar[g % STAGES], (g / STAGES) & 1, &abort_flag);
         }
-    } else if (warp == 1 && lane == 0 && kstages > 0) {
-        // ---------------- MMA issuer ----------------
-        constexpr uint32_t idesc = idesc_bf16(TM, TN);
+    } else if (warp == 1 && lane == 0 && kstages > 0 && rank == 0) {
+        // ---------------- MMA issuer (first CTA, for the pair) ----------------
+        constexpr uint32_t idesc = idesc_bf16(2 * TM, TN);
         int g = 0;
         for (int c = 0; c < nchunks && !abort_flag; ++c) {
             const int b = c & 1;
-            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
+            if (c >= 2 && !mbar_wait_cluster(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -155,28 +168,33 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const uint32_t st = sbase + s * STAGE_BYTES;
                 const uint64_t ah = smem_desc_sw64(st), al = smem_desc_sw64(st + A_BYTES);
                 const uint64_t bh = smem_desc_sw64(st + 2 * A_BYTES);
-                const uint64_t bl = smem_desc_sw64(st + 2 * A_BYTES + B_BYTES);
+                const uint64_t bl = smem_desc_sw64(st + 2 * A_BYTES + BH_BYTES);
 #pragma unroll
                 for (int ks = 0; ks < TK / 16; ++ks) {
                     const uint64_t adv = (uint64_t)(ks * 32 >> 4);   // 16 bf16 = 32 B along K
-                    mma_bf16(d, ah + adv, bh + adv, idesc, first ? 0u : 1u);
-                    mma_bf16(d, ah + adv, bl + adv, idesc, 1u);
-                    mma_bf16(d, al + adv, bh + adv, idesc, 1u);
+                    mma_bf16_pair(d, ah + adv, bh + adv, idesc, first ? 0u : 1u);
+                    mma_bf16_pair(d, ah + adv, bl + adv, idesc, 1u);
+                    mma_bf16_pair(d, al + adv, bh + adv, idesc, 1u);
                     first = false;
                 }
-                mma_commit(&empty_bar[s]);       // stage s free once these MMAs complete
+                mma_commit_pair(&empty_bar[s]);     // slot s of both CTAs free once these complete
             }
             if (abort_flag) break;
-            mma_commit(&accf_bar[b]);            // accumulator b ready for the epilogue
+            mma_commit_pair(&accf_bar[b]);          // accumulator b ready in both CTAs
         }
-        mma_commit(&done_bar);                   // every MMA issued above has completed
+        mma_commit_pair(&done_bar);                 // every MMA issued above has completed
+        int dummy = 0;
+        mbar_wait(&done_bar, 0, &dummy);
+    } else if (warp == 1 && lane == 0 && kstages > 0) {
+        // second CTA: its TMEM is written by the first CTA's MMAs until this arrives
         int dummy = 0;
         mbar_wait(&done_bar, 0, &dummy);
     } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> FP32 running sums ----------------
+        // ---------------- epilogue: TMEM -> FP32 running sums (both CTAs) ----------------
         const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
         const int half = (warp - 2) >> 2;                // columns 128*half .. +127
         const int iz = ti * TM + quad * 32 + lane;       // Z row of this thread
+        const uint32_t drained[2] = { cluster_addr(&acce_bar[0], 0), cluster_addr(&acce_bar[1], 0) };
         float acc[128];
 #pragma unroll
         for (int t = 0; t < 128; ++t) acc[t] = 0.f;
@@ -199,7 +217,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 for (int t = 0; t < 16; ++t) acc[cb * 16 + t] += v[t];
             }
             tc_fence_before();
-            mbar_arrive(&acce_bar[b]);
+            mbar_arrive_cluster(drained[b]);             // on the first CTA's barrier
         }
         if (iz < a.pz && !abort_flag) {
             const int jz0 = tj * TN + half * 128;
@@ -218,14 +236,18 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
         }
     }
-    // teardown: make sure no MMA is still writing TMEM, then free it
+    // teardown: no MMA writes TMEM any more (done waited for above) and both
+    // CTAs have finished reading their TMEM before the pair frees it; neither
+    // CTA leaves while the other may still signal its barriers
     tc_fence_before();
     __syncthreads();
+    cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
     }
+    cluster_sync();
 }
 
 // Gather rows with positive weight, scale by sqrt(w), split into bf16 hi/lo and
@@ -267,8 +289,27 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
         rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.f;
     }
     __syncthreads();
-    // read: warp w takes rows 16w .. 16w + 15; lane = column
-    {
+    // read: warp w takes rows 16w .. 16w + 15; lane = column.  Blocks whose 32
+    // columns all come from the FP32 copy without a column map (all but the last
+    // block of a fit) take a path with no per-element branch.
+    const bool fast = X32 != nullptr && (colmap == nullptr || x32_compact) && c0 + SPLIT_COLS <= pz_x;
+    if (fast) {
+        const float* src = X32 + c0 + lane;
+        float q[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int64_t row = rowoff[16 * warp + i];
+            const float v = __ldg(src + (row > 0 ? row : 0) * ld32);
+            q[i] = row >= 0 ? v : 0.f;
+        }
+#pragma unroll
+        for (int i4 = 0; i4 < 4; ++i4) {
+            const int tl = 16 * warp + 4 * i4;
+            *reinterpret_cast<float4*>(&tile[lane][tl]) =
+                make_float4(q[4 * i4] * rowsc[tl], q[4 * i4 + 1] * rowsc[tl + 1], q[4 * i4 + 2] * rowsc[tl + 2],
+                            q[4 * i4 + 3] * rowsc[tl + 3]);
+        }
+    } else {
         const int c = c0 + lane;
         const int64_t col = colmap && c < pz_x ? colmap[c] : c;      // column of X
         const int64_t col32 = x32_compact ? c : col;                 // column of the FP32 copy
@@ -302,20 +343,19 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
         const int cc = c0 + cl;
         if (cc >= pz_pad) break;
         const float4 v = *reinterpret_cast<const float4*>(&tile[cl][4 * lane]);
-        const float vv[4] = { v.x, v.y, v.z, v.w };
-        __nv_bfloat16 h[4], l[4];
+        // two values per conversion (round to nearest even, as one at a time)
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+        const float2 hf01 = __bfloat1622float2(h01), hf23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - hf01.x, v.y - hf01.y);   // exact differences
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - hf23.x, v.w - hf23.y);
+        const float2 lf01 = __bfloat1622float2(l01), lf23 = __bfloat1622float2(l23);
         float sq = 0.f;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            h[t] = __float2bfloat16_rn(vv[t]);
-            l[t] = __float2bfloat16_rn(vv[t] - __bfloat162float(h[t]));   // exact difference
-            const float f = __bfloat162float(l[t]);
-            sq += f * f;
-        }
+        sq += lf01.x * lf01.x;
+        sq += lf01.y * lf01.y;
+        sq += lf23.x * lf23.x;
+        sq += lf23.y * lf23.y;
         __nv_bfloat16* base_hi = out + (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0;
         __nv_bfloat16* base_lo = out + (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0;
-        const __nv_bfloat162 h01 = __halves2bfloat162(h[0], h[1]), h23 = __halves2bfloat162(h[2], h[3]);
-        const __nv_bfloat162 l01 = __halves2bfloat162(l[0], l[1]), l23 = __halves2bfloat162(l[2], l[3]);
         *reinterpret_cast<uint2*>(base_hi + 4 * lane) =
             make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
         *reinterpret_cast<uint2*>(base_lo + 4 * lane) =
@@ -459,12 +499,15 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     if (!gram_tc_available()) throw Error(UOI_ERR_UNSUPPORTED, "tcgen05 Gram needs sm_103a");
     const int32_t pz = pz_x + (int32_t)r;
     const int32_t pz_pad = (int32_t)ceil_div(pz, TN) * TN;
-    // tile list of the lower triangle (rows of Z x X columns)
+    // tile list of the lower triangle (rows of Z x X columns), by pairs of row tiles
+    // 2m, 2m+1: both need the column tiles tj <= floor(min(256m + 255, pz_x - 1) / 256).
+    // With an odd count the last pair's second tile lies past pz: it reads the zero
+    // padding of the pieces (pz_pad is a multiple of TN) and writes nothing.
     std::vector<int32_t> tiles;
     const int nti = (int)ceil_div(pz, TM);
-    for (int ti = 0; ti < nti; ++ti) {
-        const int jmax = std::min(ti * TM + TM - 1, pz_x - 1);
-        for (int tj = 0; tj * TN <= jmax; ++tj) { tiles.push_back(ti); tiles.push_back(tj); }
+    for (int m2 = 0; 2 * m2 < nti; ++m2) {
+        const int jmax = std::min(m2 * TN + TN - 1, pz_x - 1);
+        for (int tj = 0; tj * TN <= jmax; ++tj) { tiles.push_back(m2); tiles.push_back(tj); }
     }
     const int ntiles = (int)tiles.size() / 2;
     DevBuf tl(sizeof(int32_t) * tiles.size(), s);
@@ -488,9 +531,11 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     for (int32_t v : nr) max_rows = std::max(max_rows, v);
     const int64_t n_pad = ceil_div(max_rows, 128) * 128;      // K extent (whole split blocks)
     const int32_t row_tiles = (int32_t)(n_pad / 64);
-    // items per pass bounded by the size of the split copies (<= 8 GB)
+    // items per pass bounded by the size of the split copies (<= 16 GB: the 48
+    // selection items of a 50000 x 2000 fit in one pass, 22.7 waves of 152 CTAs
+    // instead of 15 + 9 in two)
     const size_t per_item = (size_t)2 * pz_pad * n_pad * sizeof(__nv_bfloat16);
-    const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (8ull << 30) / per_item));
+    const int group = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (16ull << 30) / per_item));
     DevBuf zt(per_item * group, s);
     DevBuf corr(sizeof(double) * (size_t)group * pz_x, s);
     DevBuf losq(sizeof(float) * (size_t)group * row_tiles * pz_x, s);
@@ -506,8 +551,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                                              nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
                                              zt.as<__nv_bfloat16>(), losq.as<float>());
         UOI_CHECK_LAUNCH();
-        const CUtensorMap mA = tc::make_map_bf16_k32(zt.ptr, n_pad, pz_pad, 2 * nb, TM);
-        const CUtensorMap mB = tc::make_map_bf16_k32(zt.ptr, n_pad, pz_pad, 2 * nb, TN);
+        const CUtensorMap mA = tc::make_map_bf16_k32(zt.ptr, n_pad, pz_pad, 2 * nb, TM);   // 128-row boxes
         GramTcArgs a;
         a.n_pad = n_pad; a.pz_pad = pz_pad; a.pz = pz; a.pz_x = pz_x; a.r = (int32_t)r;
         a.p_out = (int32_t)p_out; a.ntiles = ntiles; a.tiles = tl.as<int32_t>();
@@ -515,7 +559,21 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         a.G = G + (size_t)b0 * p_out * p_out; a.Bm = Bm + (size_t)b0 * p_out * r;
         a.err = err.as<int32_t>();
         ktimer_begin(TK_GRAM_TC, s);
-        k_gram_tc<<<dim3((unsigned)ntiles, (unsigned)nb), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
+        {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(2 * ntiles), (unsigned)nb);
+            cfg.blockDim = dim3(THREADS);
+            cfg.dynamicSmemBytes = SMEM_BYTES;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            UOI_CUDA(cudaLaunchKernelEx(&cfg, k_gram_tc, mA, a));
+        }
         UOI_CHECK_LAUNCH();
         ktimer_end(TK_GRAM_TC, s, 0.0, 0.0);
         dim3 gd((unsigned)ceil_div(pz_x, 256), (unsigned)nb);
