@@ -270,10 +270,12 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
                   const double* Y, int64_t ldy, int32_t pz_x, int32_t r, const int32_t* colmap,
                   const int32_t* rowlist,
                   const float* rowscale, const int32_t* nrows, int64_t m, int64_t n_pad,
-                  int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq)
+                  int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq,
+                  const float* zrow)
 {
     __shared__ __align__(16) float tile[SPLIT_COLS][SPLIT_LD];      // [column][row]
     __shared__ int64_t rowoff[SPLIT_ROWS];
+    __shared__ const float* rowptr[SPLIT_ROWS];     // row of the FP32 copy, or a row of zeros
     __shared__ float rowsc[SPLIT_ROWS];
     // items vary fastest: the items' sorted row lists advance through X at nearly
     // the same pace, so CTAs launched together read the same rows (L2 hits)
@@ -285,7 +287,9 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < SPLIT_ROWS) {
         const int64_t t = t0 + threadIdx.x;
-        rowoff[threadIdx.x] = t < nr ? (int64_t)rowlist[(int64_t)item * m + t] : -1;
+        const int64_t row = t < nr ? (int64_t)rowlist[(int64_t)item * m + t] : -1;
+        rowoff[threadIdx.x] = row;
+        rowptr[threadIdx.x] = row >= 0 && X32 ? X32 + row * ld32 : zrow;
         rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.f;
     }
     __syncthreads();
@@ -294,14 +298,9 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
     // block of a fit) take a path with no per-element branch.
     const bool fast = X32 != nullptr && (colmap == nullptr || x32_compact) && c0 + SPLIT_COLS <= pz_x;
     if (fast) {
-        const float* src = X32 + c0 + lane;
         float q[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int64_t row = rowoff[16 * warp + i];
-            const float v = __ldg(src + (row > 0 ? row : 0) * ld32);
-            q[i] = row >= 0 ? v : 0.f;
-        }
+        for (int i = 0; i < 16; ++i) q[i] = __ldg(rowptr[16 * warp + i] + c0 + lane);
 #pragma unroll
         for (int i4 = 0; i4 < 4; ++i4) {
             const int tl = 16 * warp + 4 * i4;
@@ -337,6 +336,9 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
     __syncthreads();
     // write: warp w takes columns w, w + 8, w + 16, w + 24; lane covers rows
     // 4*lane .. 4*lane + 3 (lanes 0-15: the first 64 rows, 16-31: the second)
+    const int64_t piece = (int64_t)pz_pad * n_pad;                 // elements per piece
+    __nv_bfloat16* out_hi = out + ((int64_t)item * 2 * pz_pad + c0 + warp) * n_pad + t0 + 4 * lane;
+    float* losq_c = losq + ((int64_t)item * row_tiles + (t0 / 64) + (lane >> 4)) * pz_x + c0 + warp;
 #pragma unroll
     for (int j = 0; j < SPLIT_COLS / 8; ++j) {
         const int cl = warp + 8 * j;
@@ -354,17 +356,16 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
         sq += lf01.y * lf01.y;
         sq += lf23.x * lf23.x;
         sq += lf23.y * lf23.y;
-        __nv_bfloat16* base_hi = out + (((int64_t)item * 2 + 0) * pz_pad + cc) * n_pad + t0;
-        __nv_bfloat16* base_lo = out + (((int64_t)item * 2 + 1) * pz_pad + cc) * n_pad + t0;
-        *reinterpret_cast<uint2*>(base_hi + 4 * lane) =
+        __nv_bfloat16* base_hi = out_hi + (int64_t)(8 * j) * n_pad;
+        *reinterpret_cast<uint2*>(base_hi) =
             make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
-        *reinterpret_cast<uint2*>(base_lo + 4 * lane) =
+        *reinterpret_cast<uint2*>(base_hi + piece) =
             make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
         if (cc < pz_x) {
             // sum over the 16 lanes of each 64-row half (fixed order)
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if ((lane & 15) == 0) losq[((int64_t)item * row_tiles + (t0 / 64) + (lane >> 4)) * pz_x + cc] = sq;
+            if ((lane & 15) == 0) losq_c[8 * j] = sq;
         }
     }
 }
@@ -539,6 +540,8 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     DevBuf zt(per_item * group, s);
     DevBuf corr(sizeof(double) * (size_t)group * pz_x, s);
     DevBuf losq(sizeof(float) * (size_t)group * row_tiles * pz_x, s);
+    DevBuf zrow(sizeof(float) * (size_t)pz_pad, s);               // read for the padding rows
+    UOI_CUDA(cudaMemsetAsync(zrow.ptr, 0, sizeof(float) * (size_t)pz_pad, s));
     auto kern = k_gram_tc;
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     for (int b0 = 0; b0 < B; b0 += group) {
@@ -549,7 +552,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                                              rows.as<int32_t>() + (size_t)b0 * m,
                                              scale.as<float>() + (size_t)b0 * m,
                                              nrows.as<int32_t>() + b0, m, n_pad, pz_pad, row_tiles,
-                                             zt.as<__nv_bfloat16>(), losq.as<float>());
+                                             zt.as<__nv_bfloat16>(), losq.as<float>(), zrow.as<float>());
         UOI_CHECK_LAUNCH();
         const CUtensorMap mA = tc::make_map_bf16_k32(zt.ptr, n_pad, pz_pad, 2 * nb, TM);   // 128-row boxes
         GramTcArgs a;
