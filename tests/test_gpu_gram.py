@@ -26,8 +26,13 @@ def _case(n, p, r, B, seed, wmax=4):
     return X, Y, w.astype(np.uint32)
 
 
+# Row tiles of 128 run in pairs (2m, 2m+1) on one 256-column tile: odd counts of
+# row tiles (51, 78, 301, 516, 520 columns of Z) leave the last pair's second tile
+# past the end; 251 and 1101 columns give even and odd counts with several column
+# tiles per pair.
 @pytest.mark.parametrize("n,p,r,B", [(200, 50, 1, 3), (1000, 77, 1, 2), (5000, 300, 1, 2),
-                                     (9000, 513, 3, 1), (700, 260, 260, 2)])
+                                     (9000, 513, 3, 1), (700, 260, 260, 2), (3000, 250, 1, 2),
+                                     (2500, 1100, 1, 1)])
 def test_moments_fp64_and_tc_vs_oracle(n, p, r, B):
     X, Y, w = _case(n, p, r, B, seed=n + p)
     G64, B64 = native.weighted_moments(X, Y, w, precision=native.PREC_FP64)
@@ -53,3 +58,17 @@ def test_moments_tc_zero_weight_rows_and_single_row():
     np.testing.assert_allclose(Gtc[0], 3.0 * np.outer(X[17], X[17]), rtol=4e-5, atol=1e-12)
     Gr, Br = oracle.weighted_moments(X, Y, w[1])
     assert np.max(np.abs(Gtc[1] - Gr)) <= 2e-6 * np.max(np.diag(Gr))
+
+
+def test_moments_tc_item_without_rows():
+    # an item whose weights are all zero has no sample rows: its moments are exactly zero,
+    # and the other items of the same launch are unaffected
+    X, Y, w = _case(2000, 300, 1, 3, seed=11)
+    w[1, :] = 0
+    Gtc, Btc = native.weighted_moments(X, Y, w, precision=native.PREC_MIXED)
+    assert not Gtc[1].any() and not Btc[1].any()
+    for k in (0, 2):
+        Gr, Br = oracle.weighted_moments(X, Y, w[k])
+        scale = np.max(np.abs(np.diag(Gr)))
+        assert np.max(np.abs(Gtc[k] - Gr)) <= 2e-6 * scale
+        assert np.max(np.abs(Btc[k] - Br)) <= 2e-6 * max(scale, np.max(np.abs(Br)))
