@@ -146,15 +146,28 @@ __global__ void k_lambda_grid(const double* XtY, int64_t count, int64_t m, int32
         lambdas[j] = q > 1 ? lmax * pow(ratio, (double)j / (double)(q - 1)) : lmax;
 }
 
-__global__ void k_check_finite(const double* X, int64_t ldx, int64_t m, int64_t cols,
+// Exponent field all ones = Inf or NaN.  Contiguous rows (ldx == cols): one flat
+// loop; otherwise rows over blocks and columns over threads.  No division per
+// element; one flag write per warp that saw a non-finite value.
+__global__ void k_check_finite(const double* __restrict__ X, int64_t ldx, int64_t m, int64_t cols,
                                int32_t* flag)
 {
-    const int64_t total = m * cols;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = t / cols, col = t % cols;
-        if (!isfinite(X[row * ldx + col])) { atomicExch(flag, 1); return; }
+    bool bad = false;
+    if (ldx == cols) {
+        const int64_t total = m * cols;
+#pragma unroll 4
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x)
+            bad |= ((__double_as_longlong(__ldg(X + t)) >> 52) & 0x7FF) == 0x7FF;
+    } else {
+        for (int64_t row = blockIdx.x; row < m; row += gridDim.x) {
+            const double* xr = X + row * ldx;
+#pragma unroll 4
+            for (int64_t j = threadIdx.x; j < cols; j += blockDim.x)
+                bad |= ((__double_as_longlong(__ldg(xr + j)) >> 52) & 0x7FF) == 0x7FF;
+        }
     }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
 }
 
 // Split-K X^T Y for r <= 4: block (column tile, row chunk) writes partial sums.

@@ -635,12 +635,25 @@ void gather_cols_f32(const float* X32, int64_t ld, int64_t m, const int32_t* col
 }
 
 namespace {
-__global__ void k_to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out)
+// Contiguous rows (ldx == p): one flat loop; otherwise rows over blocks and
+// columns over threads.  No division per element.
+__global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, int64_t m, int64_t p,
+                         float* __restrict__ out)
 {
-    const int64_t total = m * p;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x)
-        out[(t / p) * ldx + t % p] = f64_to_f32_int(X[(t / p) * ldx + t % p]);
+    if (ldx == p) {
+        const int64_t total = m * p;
+#pragma unroll 4
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x)
+            out[t] = f64_to_f32_int(__ldg(X + t));
+        return;
+    }
+    for (int64_t row = blockIdx.x; row < m; row += gridDim.x) {
+        const double* xr = X + row * ldx;
+        float* orow = out + row * ldx;
+#pragma unroll 4
+        for (int64_t j = threadIdx.x; j < p; j += blockDim.x) orow[j] = f64_to_f32_int(__ldg(xr + j));
+    }
 }
 }  // namespace
 
