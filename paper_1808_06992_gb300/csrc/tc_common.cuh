@@ -165,19 +165,8 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar)
         : "memory");
 }
 
-// K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of 1 KB.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
-    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                            // descriptor version
-    d |= (uint64_t)2 << 61;                            // SWIZZLE_128B
-    return d;
-}
-
-// Same for 64-byte swizzle: rows of 64 B (32 bf16 of k), 8-row atoms of 512 B.
+// K-major operand tile with 64-byte swizzle: rows of 64 B (32 16-bit values of k), 8-row
+// atoms of 512 B.
 __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
 {
     uint64_t d = 0;
@@ -273,43 +262,9 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 3D bf16 tensor map over [depth][rows][k] (k contiguous), box {64, box_rows, 1},
-// 128-byte swizzle: K-major UMMA operand tiles.
-inline CUtensorMap make_map_bf16_k64(void* base, int64_t k_extent, int64_t rows, int64_t depth,
-                                     int box_rows)
-{
-    CUtensorMap m;
-    cuuint64_t dims[3] = { (cuuint64_t)k_extent, (cuuint64_t)rows, (cuuint64_t)depth };
-    cuuint64_t strides[2] = { (cuuint64_t)(k_extent * 2), (cuuint64_t)(k_extent * 2 * rows) };
-    cuuint32_t box[3] = { 64u, (cuuint32_t)box_rows, 1u };
-    cuuint32_t estr[3] = { 1, 1, 1 };
-    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
-                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    return m;
-}
-
-// Map over contiguous 128 x 64 bf16 blocks ([block][128][64], 16 KB each, rows of
-// 128 B): a box of `depth` consecutive blocks is one contiguous read.
-inline CUtensorMap make_map_bf16_blocks(void* base, int64_t nblocks, int depth)
-{
-    CUtensorMap m;
-    cuuint64_t dims[3] = { 64u, 128u, (cuuint64_t)nblocks };
-    cuuint64_t strides[2] = { 128u, 128u * 128u };
-    cuuint32_t box[3] = { 64u, 128u, (cuuint32_t)depth };
-    cuuint32_t estr[3] = { 1, 1, 1 };
-    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
-                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    return m;
-}
-
-// 64-byte-swizzle variants: k tiles of 32 16-bit values (rows of 64 B); dt is
-// the 16-bit element type (bf16 or fp16: the copy is the same bytes).
+// 3D tensor map over [depth][rows][k] of 16-bit values (k contiguous), box
+// {32, box_rows, 1}, 64-byte swizzle: K-major UMMA operand tiles.  dt is the
+// 16-bit element type (bf16 or fp16: the copy is the same bytes).
 inline CUtensorMap make_map_bf16_k32(void* base, int64_t k_extent, int64_t rows, int64_t depth,
                                      int box_rows,
                                      CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16)
