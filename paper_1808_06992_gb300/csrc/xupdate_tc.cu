@@ -129,18 +129,13 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     const int nst = XT_STAGES;
 
     // A tile whose chains have all stopped has nothing to update: skip it whole.
+    // (Only the live flags are read before the pipeline starts; the epilogue
+    // warps read the other per-chain scalars while M streams in.)
     {
         const int n = threadIdx.x, chain = n0 + n;
         const int64_t sl = (int64_t)g * a.nchains + chain;
         const bool mine = n < a.NT && chain < a.nchains && a.live[sl];
-        if (n < XT_NT_MAX) {
-            // per-chain scalars of the epilogue, read once instead of per row
-            s_live[n] = mine ? 1 : 0;
-            s_kappa[n] = mine ? (float)a.lambdas[a.slot_j[sl]] / a.rho : 0.f;
-            s_vrinv[n] = mine ? 1.f / a.vs_r[sl] : 0.f;
-            s_vw[n] = mine ? a.vs_w[sl] : 0.f;
-            s_coff[n] = g * a.r + (a.warm ? chain : chain % a.r);
-        }
+        if (n < XT_NT_MAX) s_live[n] = mine ? 1 : 0;
         if (!__syncthreads_or(mine)) return;
     }
 
@@ -235,6 +230,22 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         const int quad = warp & 3;
         const int i = i0 + quad * 32 + lane;
         const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+        {
+            // per-chain scalars of the update, read once instead of per row, while the
+            // products run; then a barrier of the four epilogue warps
+            const int n = threadIdx.x - 64;
+            if (n < XT_NT_MAX) {
+                const int chain = n0 + n;
+                const int64_t sl = (int64_t)g * a.nchains + chain;
+                const bool mine = s_live[n] != 0;
+                s_kappa[n] = mine ? (float)a.lambdas[a.slot_j[sl]] / a.rho : 0.f;
+                s_vrinv[n] = mine ? 1.f / a.vs_r[sl] : 0.f;
+                s_vw[n] = mine ? a.vs_w[sl] : 0.f;
+                s_coff[n] = g * a.r + (a.warm ? chain : chain % a.r);
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+        const float rinv_row = i < a.p ? a.row_inv[(int64_t)g * a.ppad + i] : 0.f;
         float acc[64], cmp[64];
 #pragma unroll
         for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
@@ -275,7 +286,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         __syncwarp();
         tc_fence_after();
         const bool rowok = i < a.p && !abort_flag;
-        const float rinv = rowok ? a.row_inv[(int64_t)g * a.ppad + i] : 0.f;
+        const float rinv = rowok ? rinv_row : 0.f;
         // The ring is idle now: stage this row's z, u and c of every live chain in
         // it with asynchronous copies, all in flight at once, so the update below
         // reads shared memory instead of waiting on DRAM once per group of chains.
