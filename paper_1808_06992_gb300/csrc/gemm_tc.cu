@@ -177,6 +177,7 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         // ---------------- epilogue: TMEM -> FP32 running sums -> D ----------------
         const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
         const int half = (warp - 2) >> 2;                // columns 128*half .. +127
+        const float ar = a.alpha * (a.ainv[g] * a.binv[g]);   // read while the products run
         float acc[128];
 #pragma unroll
         for (int t = 0; t < 128; ++t) acc[t] = 0.f;
@@ -214,22 +215,35 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         __syncwarp();
         if (!abort_flag) {
             const int j = nt * GT_TN + half * 128 + 4 * lane;
-            const float ar = a.alpha * (a.ainv[g] * a.binv[g]);
+            const int i0 = mt * GT_TM + quad * 32;
+            const int nrow = max(0, min(32, a.m - i0));
             float dm = 0.f;
-            for (int rr = 0; rr < 32; ++rr) {
-                const int ii = mt * GT_TM + quad * 32 + rr;
-                if (ii >= a.m) break;
-                const float4 v = *reinterpret_cast<const float4*>(stage + rr * GT_STG + 4 * lane);
-                float r4[4] = { v.x, v.y, v.z, v.w };
-                float* drow = a.D + (int64_t)g * a.gsd + (int64_t)ii * a.ldd;
-                const float* crow = a.C ? a.C + (int64_t)g * a.gsc + (int64_t)ii * a.ldc : nullptr;
+            for (int r0 = 0; r0 < nrow; r0 += 8) {
+                // C of eight rows read before any of them is written (all loads in
+                // flight at once; D may be C itself, element for element)
+                float cv[8][4];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    if (j + t < a.n) {
-                        float r = ar * r4[t];
-                        if (crow) r += a.beta * crow[j + t];
-                        drow[j + t] = r;
-                        dm = fmaxf(dm, fabsf(r));
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        cv[u][t] = (a.C && r0 + u < nrow && j + t < a.n)
+                                       ? a.C[(int64_t)g * a.gsc + (int64_t)(i0 + r0 + u) * a.ldc + j + t]
+                                       : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int rr = r0 + u;
+                    if (rr >= nrow) break;
+                    const float4 v = *reinterpret_cast<const float4*>(stage + rr * GT_STG + 4 * lane);
+                    float r4[4] = { v.x, v.y, v.z, v.w };
+                    float* drow = a.D + (int64_t)g * a.gsd + (int64_t)(i0 + rr) * a.ldd;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (j + t < a.n) {
+                            float r = ar * r4[t];
+                            if (a.C) r += a.beta * cv[u][t];
+                            drow[j + t] = r;
+                            dm = fmaxf(dm, fabsf(r));
+                        }
                     }
                 }
             }
