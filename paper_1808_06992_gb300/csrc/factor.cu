@@ -39,17 +39,20 @@ __device__ __forceinline__ float system_entry<float>(double g, double inv_n, dou
     return f64_to_f32_int(g) * (float)inv_n + (diag ? (float)rho : 0.f);
 }
 
-// One row per block-row step (no index division per element).
+// One row per block-row step (no index division per element); the loads of four
+// iterations are issued before their stores.
 template <typename T>
-__global__ void k_build_system(const double* G, const double* nk, double rho, int64_t p, T* A)
+__global__ void k_build_system(const double* __restrict__ G, const double* nk, double rho, int64_t p,
+                               T* __restrict__ A)
 {
     const int64_t k = blockIdx.y;
     const double inv_n = 1.0 / nk[k];
     for (int64_t i = blockIdx.x; i < p; i += gridDim.x) {
         const double* grow = G + (k * p + i) * p;
         T* arow = A + (k * p + i) * p;
+#pragma unroll 4
         for (int64_t j = threadIdx.x; j < p; j += blockDim.x)
-            arow[j] = system_entry<T>(grow[j], inv_n, rho, i == j);
+            arow[j] = system_entry<T>(__ldg(grow + j), inv_n, rho, i == j);
     }
 }
 
