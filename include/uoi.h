@@ -54,8 +54,10 @@ extern "C" {
 #define UOI_SPLIT_PER_BOOTSTRAP 0  /* a fresh train/eval reshuffle per bootstrap     */
 #define UOI_SPLIT_FIXED         1  /* bootstrap 0's reshuffle for every bootstrap    */
 #define UOI_PREC_FP64    0   /* plain FP64 form: every step in FP64                  */
-#define UOI_PREC_MIXED   1   /* tensor-core Gram (split bf16, FP32 accumulate, FP64
-                                chunk sums), FP64 Cholesky and OLS, FP32 ADMM         */
+#define UOI_PREC_MIXED   1   /* tensor-core Gram (two-piece bf16, FP32 accumulation
+                                drained every 128 rows), FP32-accurate inverse,
+                                FP32 ADMM (tensor-core x-update for p > 192), OLS by
+                                FP32 factor + FP64 refinement                        */
 #define UOI_WARM_NONE    0   /* every (bootstrap, lambda) column starts at z = u = 0 */
 #define UOI_WARM_PATH    1   /* lambda descending; column j starts from j-1's (z,u)  */
 #define UOI_WARM_LEARNED 2   /* learned initial (z,u) (MLP); judged by PATH          */
@@ -206,9 +208,10 @@ int lasso_admm_batch(const double* X, const double* Y, int64_t n, int64_t p, int
  * ... from T^k" only needs these): for every k < B,
  *   G_out[k] = X^T diag(w_k) X   (p x p),   B_out[k] = X^T diag(w_k) Y   (p x r)
  * with X: n x p, Y: n x r, weights: B x n bootstrap multiplicities (not NULL).
- * precision UOI_PREC_FP64: FP64 CUDA cores.  UOI_PREC_MIXED: split-bf16 tensor
- * cores (tcgen05) with FP32 accumulation per 4096 sample rows and FP64 sums,
- * relative error about 1e-6 of the largest diagonal entry. */
+ * precision UOI_PREC_FP64: FP64 CUDA cores.  UOI_PREC_MIXED: two-piece bf16 on
+ * tensor cores (tcgen05), FP32 accumulation drained every 128 sample rows into
+ * FP32 running sums, written in FP64; error within about 5e-7 of the largest
+ * diagonal entry (2e-6 is the tested bound). */
 int uoi_weighted_moments(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,
                          const uint32_t* weights, int32_t B, int32_t precision,
                          double* G_out, double* B_out, void* stream);
