@@ -8,9 +8,11 @@ Eq. 1-9) plus Philox4x64-10 (Salmon et al., SC'11), loaded here with ctypes.
 
 Parity status: every stage function is pinned by ``tests/test_oracle_pins.py``
 (numpy Philox, closed forms, KKT, lambda_max, brute force over supports,
-sklearn, lstsq, brute-force set logic).  ``uoi_fit`` as a whole is "parity
-unpinned" beyond the composition of those pinned parts and the noiseless
-recovery special case.
+sklearn, lstsq, brute-force set logic).  ``uoi_fit`` as a whole is pinned
+through those parts, the noiseless recovery special case and the cases whose
+selection is decided in advance (``tests/test_oracle_whole_fit.py``: least
+squares on the training draws, held-out losses, argmin and bagging by an
+independent numpy route); beyond those it is "parity unpinned".
 """
 from __future__ import annotations
 

@@ -24,8 +24,10 @@
  *
  * Parity status per function: every function is pinned by a test in
  * tests/test_oracle_pins.py except ref_uoi_fit as a whole, which is pinned
- * only through its parts plus the noiseless-recovery special case
- * ("parity unpinned" beyond the composition of pinned parts).
+ * through its parts, the noiseless-recovery special case and the cases whose
+ * selection is decided in advance (tests/test_oracle_whole_fit.py: least
+ * squares on the training draws, held-out losses, argmin and bagging by an
+ * independent numpy route); beyond those it is "parity unpinned".
  */
 #ifndef UOI_ORACLE_H
 #define UOI_ORACLE_H

@@ -1,0 +1,79 @@
+"""Pins of the oracle's whole UoI_LASSO fit (Alg. 1) in cases where the selection
+step is decided in advance, so that the estimation step has an independent
+route: at an explicit lambda far below every |Xᵀy|/n the LASSO keeps every
+feature in every bootstrap (the intersection, Eq. 3, is the full set); at a
+lambda above lambda_max it keeps none.  Then each estimation bootstrap's
+coefficients are the least-squares fit on its training draws (numpy lstsq on
+the rows scaled by sqrt(w), not the oracle's Cholesky), its held-out loss is the
+sum of squared residuals on the evaluation rows (the traced loss: the 1/|E|
+factor does not change the argmin), j* is the argmin, and beta* the
+median (or mean) over bootstraps.  The bootstrap and split weights come from
+the oracle's Philox functions, pinned separately by known-answer vectors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+SEED = 5
+
+
+def _problem(n=300, p=6, seed=3):
+    g = np.random.Generator(np.random.PCG64(seed))
+    X = g.standard_normal((n, p))
+    beta = g.uniform(0.5, 2.0, size=p) * g.choice([-1.0, 1.0], size=p)
+    y = X @ beta + 0.3 * g.standard_normal(n)
+    return X, y
+
+
+def _train_eval(m, B2):
+    out = []
+    for k in range(B2):
+        w, ev, _ = oracle.estimation_weights(m, 0, 0.8, 0, SEED, 0, k)
+        out.append((w.astype(np.float64), ev.astype(bool)))
+    return out
+
+
+def _wls(X, y, w):
+    sw = np.sqrt(w)
+    return np.linalg.lstsq(X * sw[:, None], y * sw, rcond=None)[0]
+
+
+@pytest.mark.parametrize("bagging", [0, 1])          # 0: median, 1: mean
+def test_dense_support_reduces_to_least_squares_on_the_training_draws(bagging):
+    X, y = _problem()
+    n, p = X.shape
+    B1, B2 = 4, 3
+    fit = oracle.uoi_lasso_fit(X, y, B1, B2, 1, lambdas=np.array([1e-9]), bagging=bagging, seed=SEED,
+                               max_iter=5000)
+    assert fit["status"] >= 0
+    # every selection bootstrap keeps every feature: the family is the full set
+    assert np.all(fit["sel_beta"] != 0.0)
+    assert int(fit["family"][0, 0, 0]) == (1 << p) - 1
+    ests = np.stack([_wls(X, y, w) for w, _ in _train_eval(n, B2)])
+    np.testing.assert_allclose(fit["est_beta"][:, 0, 0, :], ests, rtol=1e-9, atol=1e-12)
+    want = np.median(ests, axis=0) if bagging == 0 else np.mean(ests, axis=0)
+    np.testing.assert_allclose(fit["beta"][0], want, rtol=1e-9, atol=1e-12)
+
+
+def test_argmin_takes_the_full_support_over_the_empty_one():
+    X, y = _problem(seed=4)
+    n, p = X.shape
+    B1, B2 = 3, 4
+    lmax = np.max(np.abs(X.T @ y)) / n
+    lambdas = np.array([100.0 * lmax, 1e-9])          # descending: empty support, then all
+    fit = oracle.uoi_lasso_fit(X, y, B1, B2, 2, lambdas=lambdas, seed=SEED, max_iter=5000)
+    assert fit["status"] >= 0
+    assert np.all(fit["sel_beta"][:, 0] == 0.0) and np.all(fit["sel_beta"][:, 1] != 0.0)
+    assert int(fit["family"][0, 0, 0]) == 0 and int(fit["family"][1, 0, 0]) == (1 << p) - 1
+    ests = []
+    for k, (w, ev) in enumerate(_train_eval(n, B2)):
+        b = _wls(X, y, w)
+        loss_empty = np.sum(y[ev] ** 2)
+        loss_full = np.sum((y[ev] - X[ev] @ b) ** 2)
+        np.testing.assert_allclose(fit["est_loss"][k, 0, 0], loss_empty, rtol=1e-12)
+        np.testing.assert_allclose(fit["est_loss"][k, 1, 0], loss_full, rtol=1e-8)
+        assert loss_full < loss_empty
+        assert fit["est_jstar"][k] == 1
+        ests.append(b)
+    np.testing.assert_allclose(fit["beta"][0], np.median(np.stack(ests), axis=0), rtol=1e-9, atol=1e-12)
