@@ -7,8 +7,11 @@ coefficients are the least-squares fit on its training draws (numpy lstsq on
 the rows scaled by sqrt(w), not the oracle's Cholesky), its held-out loss is the
 sum of squared residuals on the evaluation rows (the traced loss: the 1/|E|
 factor does not change the argmin), j* is the argmin, and beta* the
-median (or mean) over bootstraps.  The bootstrap and split weights come from
-the oracle's Philox functions, pinned separately by known-answer vectors.
+median (or mean) over bootstraps.  For VAR(d) (Alg. 2) the same holds per
+equation on the lagged design of Eq. 7-8 (built here with numpy), with block
+bootstrap draws and, with an intercept, a ones column whose coefficient is mu.
+The bootstrap and split weights come from the oracle's Philox functions,
+pinned separately by known-answer vectors.
 """
 import numpy as np
 import pytest
@@ -77,3 +80,41 @@ def test_argmin_takes_the_full_support_over_the_empty_one():
         assert fit["est_jstar"][k] == 1
         ests.append(b)
     np.testing.assert_allclose(fit["beta"][0], np.median(np.stack(ests), axis=0), rtol=1e-9, atol=1e-12)
+
+
+def _lagged(S, order):
+    """Eq. 7-8 written out: row t holds X_{t-1}, ..., X_{t-order} (lag 1 first), response X_t."""
+    N = S.shape[0]
+    X = np.hstack([S[order - j:N - j] for j in range(1, order + 1)])
+    return X, S[order:]
+
+
+@pytest.mark.parametrize("order,intercept", [(1, 0), (2, 1)])
+def test_var_dense_support_reduces_to_per_equation_least_squares(order, intercept):
+    # Alg. 2 with every lag kept in every bootstrap: each equation's estimate is the
+    # least-squares fit on the block-bootstrap training draws of the lagged design
+    g = np.random.Generator(np.random.PCG64(9))
+    p, N = 4, 420
+    A_true = 0.3 * g.standard_normal((order, p, p))
+    S = np.zeros((N, p))
+    for t in range(N):
+        S[t] = 0.5 + g.standard_normal(p)
+        for j in range(1, min(order, t) + 1):
+            S[t] += A_true[j - 1] @ S[t - j]
+    B1, B2, L = 3, 3, 20
+    fit = oracle.uoi_var_fit(S, B1, B2, 1, order=order, lambdas=np.array([1e-9]), block_len=L, seed=SEED,
+                             intercept=intercept, max_iter=5000)
+    assert fit["status"] >= 0
+    X, Y = _lagged(S, order)
+    m = X.shape[0]
+    Z = np.hstack([X, np.ones((m, 1))]) if intercept else X
+    ests = []
+    for k in range(B2):
+        w, _, _ = oracle.estimation_weights(m, L, 0.8, 0, SEED, 0, k)
+        sw = np.sqrt(w.astype(np.float64))
+        ests.append(np.linalg.lstsq(Z * sw[:, None], Y * sw[:, None], rcond=None)[0].T)   # (p, cols)
+    want = np.median(np.stack(ests), axis=0)
+    A_want = want[:, :order * p].reshape(p, order, p).transpose(1, 0, 2)
+    np.testing.assert_allclose(fit["A"], A_want, rtol=1e-8, atol=1e-10)
+    if intercept:
+        np.testing.assert_allclose(fit["mu"], want[:, order * p], rtol=1e-8, atol=1e-10)
