@@ -231,6 +231,17 @@ def cpu_sample(w, X, Y, support_size=100):
     return 1.0 / t_fit, n_cols / t_fit, desc
 
 
+def max_over_ranks(value, dist, device="cuda"):
+    """The largest of every rank's value (the value itself on one rank): the
+    step time a multi-rank run reports is the slowest rank's."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -314,11 +325,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
     ms_step = ms / args.steps
     fits_s = world * args.steps / (ms / 1e3)
     cols = w.B1 * w.q * r
@@ -453,11 +460,7 @@ def bench_batch(args, torch, rank, world, local, dist):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
     fits_s = world * args.steps * count / (ms / 1e3)
     diags = [o["diag"] for o in outs[-1]]
     peaks = {}
