@@ -62,8 +62,6 @@ constexpr int GM = 128, GN = 64, GK = 16;
 template <typename TB>
 __device__ __forceinline__ float tofloat(TB v);
 template <>
-__device__ __forceinline__ float tofloat<float>(float v) { return v; }
-template <>
 __device__ __forceinline__ float tofloat<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 // C(m, n) = epi(m, n, sum_k A[m*lda + k] * B[n*ldb + k]) over K (both K-contiguous).
