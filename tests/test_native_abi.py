@@ -109,3 +109,13 @@ def test_null_pointer_rejected():
     st = lib.uoi_lasso_fit(None, None, 10, 3, C.byref(prm), None, None, None)
     assert st == native.ERR_INVALID_ARG
     assert "NULL" in native.last_error()
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the CUDA library the loader and every entry point raise
+    monkeypatch.setattr(native, "_lib", None)
+    monkeypatch.setattr(native._build, "build", lambda *a, **k: str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        native.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        native.uoi_lasso_fit(np.zeros((10, 3)), np.zeros(10), B1=2, B2=2, q=2)
