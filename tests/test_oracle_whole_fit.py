@@ -29,10 +29,10 @@ def _problem(n=300, p=6, seed=3):
     return X, y
 
 
-def _train_eval(m, B2):
+def _train_eval(m, B2, split_fixed=0):
     out = []
     for k in range(B2):
-        w, ev, _ = oracle.estimation_weights(m, 0, 0.8, 0, SEED, 0, k)
+        w, ev, _ = oracle.estimation_weights(m, 0, 0.8, split_fixed, SEED, 0, k)
         out.append((w.astype(np.float64), ev.astype(bool)))
     return out
 
@@ -42,18 +42,21 @@ def _wls(X, y, w):
     return np.linalg.lstsq(X * sw[:, None], y * sw, rcond=None)[0]
 
 
-@pytest.mark.parametrize("bagging", [0, 1])          # 0: median, 1: mean
-def test_dense_support_reduces_to_least_squares_on_the_training_draws(bagging):
+@pytest.mark.parametrize("bagging,split_fixed", [(0, 0), (1, 0), (0, 1)])   # median / mean; per-bootstrap / fixed split
+def test_dense_support_reduces_to_least_squares_on_the_training_draws(bagging, split_fixed):
     X, y = _problem()
     n, p = X.shape
     B1, B2 = 4, 3
     fit = oracle.uoi_lasso_fit(X, y, B1, B2, 1, lambdas=np.array([1e-9]), bagging=bagging, seed=SEED,
-                               max_iter=5000)
+                               max_iter=5000, split_fixed=split_fixed)
     assert fit["status"] >= 0
     # every selection bootstrap keeps every feature: the family is the full set
     assert np.all(fit["sel_beta"] != 0.0)
     assert int(fit["family"][0, 0, 0]) == (1 << p) - 1
-    ests = np.stack([_wls(X, y, w) for w, _ in _train_eval(n, B2)])
+    splits = _train_eval(n, B2, split_fixed)
+    if split_fixed:                                   # one evaluation set for every bootstrap
+        assert all(np.array_equal(splits[0][1], ev) for _, ev in splits)
+    ests = np.stack([_wls(X, y, w) for w, _ in splits])
     np.testing.assert_allclose(fit["est_beta"][:, 0, 0, :], ests, rtol=1e-9, atol=1e-12)
     want = np.median(ests, axis=0) if bagging == 0 else np.mean(ests, axis=0)
     np.testing.assert_allclose(fit["beta"][0], want, rtol=1e-9, atol=1e-12)
