@@ -219,29 +219,31 @@ int uoi_weighted_moments(const double* X, const double* Y, int64_t n, int64_t p,
 /* Batched LASSO-ADMM for callers that cannot allocate device memory.
  *
  * lasso_admm_batch obtains its working memory from the device's memory pool.
- * Some callers cannot allow that: code inside a stream capture that forbids
- * allocation, applications that hand all device memory to their own allocator
- * up front, and latency-critical loops that cannot absorb an allocation or the
- * device-wide synchronisation that freeing memory implies.  This variant
- * allocates nothing: it works in one fixed scratch array of
- * UOI_NOALLOC_SCRATCH_BYTES that is part of the library's device image, so
- * every GPU that loads the library holds that array until the process exits.
+ * Some callers cannot allow that: applications that reserve all of the
+ * device's memory at start-up for their own allocator, hosts that run under a
+ * fixed device-memory quota, and latency-critical loops where an allocation
+ * may block and a free synchronises the device.  This variant allocates
+ * nothing: it works in one fixed scratch array of UOI_NOALLOC_SCRATCH_BYTES
+ * that is part of the library's device image, so every GPU that loads the
+ * library holds that array until the process exits.
  * (The paper has no counterpart of this entry point.)
  *
  * Same arguments and results as lasso_admm_batch with precision UOI_PREC_FP64,
  * with these limits:
- *  - every pointer must be device memory of the current device (else
- *    UOI_ERR_INVALID_ARG);
+ *  - every pointer must be device memory of the current device, or managed
+ *    memory (else UOI_ERR_INVALID_ARG);
  *  - p <= UOI_NOALLOC_MAX_P, and the working set
- *    3*B*p*p*8 + 2*B*p*r*8 + B*q*r bytes (plus a few KB) must fit in the
- *    scratch array; larger problems return UOI_ERR_INVALID_ARG with a message
- *    from uoi_get_last_error_detail.
- * Set-up: the first call on a device looks up the array's device address and
- * caches it; make that first call before any stream capture.
+ *    3*B*p*p*8 + 2*B*p*r*8 + B*p*8 + B*q*r bytes (plus a few KB) must fit in
+ *    the scratch array; larger problems return UOI_ERR_INVALID_ARG with a
+ *    message from uoi_get_last_error_detail.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device) and caches it; make that first call
+ * before any stream capture.
  * Every call shares the one array and overwrites it: calls that overlap on the
  * GPU (different streams or threads) race and must be serialised by the
  * caller.  Each call clears the counters it needs, so back-to-back calls on
- * one stream are independent. */
+ * one stream are independent.  Like every entry point, the call returns after
+ * its results are in the output buffers (it synchronises the stream). */
 #define UOI_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 #define UOI_NOALLOC_MAX_P 128
 int lasso_admm_batch_noalloc(const double* X, const double* Y, int64_t n, int64_t p, int64_t r,

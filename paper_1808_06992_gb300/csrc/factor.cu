@@ -408,14 +408,20 @@ void spd_inverse_from_factor(const T* L, int64_t p, int32_t B, T* Linv, T* M, cu
 
 template <typename T>
 void rhs_from_inverse(const T* M, const double* Bm, const double* nk, int64_t p, int64_t r, int32_t B,
-                      T* c, cudaStream_t s)
+                      T* c, cudaStream_t s, T* rhs_scratch)
 {
     if (r == 1) {
-        DevBuf bs(sizeof(T) * (size_t)(B * p), s);
+        // b_k / n_k in T, from the caller's scratch when given (else a pool buffer)
+        DevBuf bs;
+        T* bsc = rhs_scratch;
+        if (!bsc) {
+            bs.alloc(sizeof(T) * (size_t)(B * p), s);
+            bsc = bs.as<T>();
+        }
         k_scale_rhs<T><<<(unsigned)std::min<int64_t>(ceil_div(B * p, 256), 4096), 256, 0, s>>>(
-            Bm, nk, p, B, bs.as<T>());
+            Bm, nk, p, B, bsc);
         UOI_CHECK_LAUNCH();
-        k_rhs_gemv<T, 1><<<dim3((unsigned)ceil_div(p, 8), (unsigned)B), 256, 0, s>>>(M, bs.as<T>(), p, c);
+        k_rhs_gemv<T, 1><<<dim3((unsigned)ceil_div(p, 8), (unsigned)B), 256, 0, s>>>(M, bsc, p, c);
         UOI_CHECK_LAUNCH();
         count_launch(2);
         return;
@@ -428,19 +434,19 @@ void rhs_from_inverse(const T* M, const double* Bm, const double* nk, int64_t p,
 
 template <typename T>
 void inverse_and_rhs(const T* L, const double* Bm, const double* nk, int64_t p, int64_t r,
-                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s)
+                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s, T* rhs_scratch)
 {
     spd_inverse_from_factor<T>(L, p, B, Linv, M, s);
-    rhs_from_inverse<T>(M, Bm, nk, p, r, B, c, s);
+    rhs_from_inverse<T>(M, Bm, nk, p, r, B, c, s, rhs_scratch);
 }
 
 template void spd_inverse_from_factor<float>(const float*, int64_t, int32_t, float*, float*,
                                              cudaStream_t);
 template void rhs_from_inverse<float>(const float*, const double*, const double*, int64_t, int64_t,
-                                      int32_t, float*, cudaStream_t);
+                                      int32_t, float*, cudaStream_t, float*);
 template void inverse_and_rhs<double>(const double*, const double*, const double*, int64_t,
-                                      int64_t, int32_t, double*, double*, double*, cudaStream_t);
+                                      int64_t, int32_t, double*, double*, double*, cudaStream_t, double*);
 template void inverse_and_rhs<float>(const float*, const double*, const double*, int64_t,
-                                     int64_t, int32_t, float*, float*, float*, cudaStream_t);
+                                     int64_t, int32_t, float*, float*, float*, cudaStream_t, float*);
 
 }  // namespace uoi

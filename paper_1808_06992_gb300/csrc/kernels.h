@@ -131,10 +131,11 @@ void cholesky_inplace(T* A, int64_t p, int32_t B, DevStatus* status, cudaStream_
 // M_k = A_k^{-1} from the factor in the lower triangle of A (Linv: p x p scratch).
 template <typename T>
 void spd_inverse_from_factor(const T* L, int64_t p, int32_t B, T* Linv, T* M, cudaStream_t s);
-// c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].
+// c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].  rhs_scratch: B*p elements of T used for
+// r == 1 (nullptr = a buffer from the device's memory pool).
 template <typename T>
 void rhs_from_inverse(const T* M, const double* Bm, const double* nk, int64_t p, int64_t r, int32_t B,
-                      T* c, cudaStream_t s);
+                      T* c, cudaStream_t s, T* rhs_scratch = nullptr);
 // M_k = A_k^{-1} for SPD A_k (FP32, p x p each) by block Schur-complement recursion
 // with FP32-accurate tensor-core GEMMs (gemm_tc.cu); A is left unchanged.
 bool inverse_tc_available();
@@ -143,7 +144,7 @@ void spd_inverse_tc(const float* A, int64_t p, int32_t G, float* M, DevStatus* s
 // c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].
 template <typename T>
 void inverse_and_rhs(const T* L, const double* Bm, const double* nk, int64_t p, int64_t r,
-                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s);
+                     int32_t B, T* Linv, T* M, T* c, cudaStream_t s, T* rhs_scratch = nullptr);
 // XtY[j*r + e] = sum_t X[t,j] Y[t,e] for few responses (split over rows, fixed order).
 void xty_small(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
                int64_t r, double* XtY, cudaStream_t s);

@@ -1,12 +1,13 @@
 // noalloc.cu -- lasso_admm_batch_noalloc: the batched LASSO-ADMM solver for callers
 // that must not allocate device memory.
 //
-// Some callers cannot let a library call cudaMalloc: code running inside a
-// stream capture that forbids allocation, applications that reserve all device
-// memory up front through their own allocator, and latency-critical loops where
-// an allocation (and the implicit device synchronisation of cudaFree) is not
-// acceptable.  This entry point takes its working memory from one file-scope
-// device array instead, so it allocates nothing.
+// Some callers cannot let a library allocate device memory: applications that
+// reserve all of the device's memory at start-up for their own allocator (so a
+// library allocation fails or steals from a budget the application manages),
+// hosts that run under a fixed device-memory quota, and latency-critical loops
+// where an allocation may block and a free synchronises the device.  This entry
+// point takes its working memory from one file-scope device array instead, so it
+// allocates nothing.
 //
 // The array lives in every GPU that loads the library, for the life of the
 // process.  In host code its name is only a host-side stand-in, so its device
@@ -15,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -27,22 +29,27 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 void* g_scratch_dev[kMaxDevices] = {};
+std::once_flag g_scratch_once[kMaxDevices];
 
+// Device address of the scratch array on the current device, looked up once per
+// device (std::call_once: concurrent first calls wait for one lookup; a failed
+// lookup throws and leaves the flag unset, so the next call tries again).
 void* scratch_for_current_device()
 {
     int dev = 0;
     UOI_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) throw Error(UOI_ERR_UNSUPPORTED, "device index out of range");
-    if (!g_scratch_dev[dev]) {
+    std::call_once(g_scratch_once[dev], [dev] {
         void* ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr)
             throw Error(UOI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_scratch_dev[dev] = ptr;
-    }
+    });
     return g_scratch_dev[dev];
 }
 
+// True for device memory of the current device, or managed memory.
 bool on_device(const void* p)
 {
     if (!p) return false;
@@ -51,7 +58,11 @@ bool on_device(const void* p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return at.device == dev;
 }
 
 __global__ void k_fill(double* out, int n, double v)
@@ -113,10 +124,12 @@ extern "C" int lasso_admm_batch_noalloc(const double* X, const double* Y, int64_
             (converged_out && !on_device(converged_out)))
             throw Error(UOI_ERR_INVALID_ARG, "every buffer must be device memory");
         const int64_t ncol = (int64_t)B * q * r;
-        // working set: G/A, L^-1, M (B p p each), moments and right-hand sides (B p r each),
-        // n_k, chain counters, status, convergence flags and a counter
+        // working set: G (B p p; reused for L^-1 once the system is built), A and M
+        // (B p p each), moments and right-hand sides (B p r each), b_k / n_k for
+        // r = 1 (B p), n_k, chain counters, status, convergence flags and a counter
         const size_t need = 3 * (sizeof(double) * (size_t)(B * p * p) + 256) +
                             2 * (sizeof(double) * (size_t)(B * p * r) + 256) +
+                            sizeof(double) * (size_t)(B * p) + 256 +
                             sizeof(double) * B + sizeof(int32_t) * B + sizeof(DevStatus) +
                             (size_t)ncol + sizeof(int32_t) + 6 * 256;
         if (need > kScratchBytes)
@@ -125,15 +138,18 @@ extern "C" int lasso_admm_batch_noalloc(const double* X, const double* Y, int64_
         cudaStream_t s = (cudaStream_t)stream;
         Carver cv{ static_cast<unsigned char*>(scratch_for_current_device()) };
         double* G = cv.take<double>((size_t)(B * p * p));
-        double* Linv = cv.take<double>((size_t)(B * p * p));
+        double* A = cv.take<double>((size_t)(B * p * p));
         double* M = cv.take<double>((size_t)(B * p * p));
         double* Bm = cv.take<double>((size_t)(B * p * r));
         double* c = cv.take<double>((size_t)(B * p * r));
+        double* bs = cv.take<double>((size_t)(B * p));
         double* nk = cv.take<double>((size_t)B);
         int32_t* chains = cv.take<int32_t>((size_t)B);
         DevStatus* st = cv.take<DevStatus>(1);
         uint8_t* conv = cv.take<uint8_t>((size_t)ncol);
         int32_t* noncon = cv.take<int32_t>(1);
+        if (cv.used > kScratchBytes)
+            throw Error(UOI_ERR_INVALID_ARG, "problem needs more than the 16 MiB no-allocation scratch");
 
         // the array keeps the previous call's contents: clear what must start at zero
         UOI_CUDA(cudaMemsetAsync(chains, 0, sizeof(int32_t) * B, s));
@@ -147,12 +163,13 @@ extern "C" int lasso_admm_batch_noalloc(const double* X, const double* Y, int64_
             k_fill<<<1, 32, 0, s>>>(nk, 1, (double)n);
             UOI_CHECK_LAUNCH();
         }
-        build_and_factor<double>(G, nk, rho, p, B, G, st, s);
+        build_and_factor<double>(G, nk, rho, p, B, A, st, s);
         DevStatus hs{};
         UOI_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
         UOI_CUDA(cudaStreamSynchronize(s));
         if (hs.code != 0) throw Error(hs.code, "Cholesky of G/n + rho I failed");
-        inverse_and_rhs<double>(G, Bm, nk, p, r, B, Linv, M, c, s);
+        // G is no longer read: its space holds L^-1
+        inverse_and_rhs<double>(A, Bm, nk, p, r, B, G, M, c, s, bs);
 
         AdmmProblem<double> P;
         P.G = B; P.p = p; P.r = r; P.q = q;

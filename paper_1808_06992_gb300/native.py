@@ -323,8 +323,10 @@ def weighted_moments(X, Y, weights, precision=PREC_FP64, stream=None):
 
 
 def lasso_admm_batch_noalloc(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6,
-                             max_iter=1000, warm_start=WARM_PATH, stream=None):
-    """lasso_admm_batch without device allocation; every array must be a CUDA tensor."""
+                             max_iter=1000, warm_start=WARM_PATH, stream=None, out=None):
+    """lasso_admm_batch without device allocation; every array must be a CUDA tensor.
+    out: optional dict(beta, iters, conv) of preallocated CUDA tensors to write into
+    (then this binding allocates nothing either)."""
     X = _prep(X, np.float64)
     Y = _prep(Y, np.float64)
     if Y.ndim == 1:
@@ -338,9 +340,12 @@ def lasso_admm_batch_noalloc(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_
     else:
         w = _prep(weights, np.uint32).reshape(-1, n)
         B = w.shape[0]
-    beta = _empty(X, (B, q, r, p), np.float64)
-    iters = _empty(X, (B, q, r), np.int32)
-    conv = _empty(X, (B, q, r), np.uint8)
+    if out is not None:
+        beta, iters, conv = out["beta"], out["iters"], out["conv"]
+    else:
+        beta = _empty(X, (B, q, r, p), np.float64)
+        iters = _empty(X, (B, q, r), np.int32)
+        conv = _empty(X, (B, q, r), np.uint8)
     st = lib().lasso_admm_batch_noalloc(_ptr(X), _ptr(Y), n, p, r, _ptr(w), B, _ptr(lam), q, rho,
                                         abs_tol, rel_tol, max_iter, warm_start, _ptr(beta),
                                         _ptr(iters), _ptr(conv), stream)
