@@ -7,6 +7,7 @@ plain C (``uoi_oracle.c``) written from the paper (arXiv 1808.06992, Alg. 1-2,
 Eq. 1-9) plus Philox4x64-10 (Salmon et al., SC'11), loaded here with ctypes.
 
 Parity status: every stage function is pinned by ``tests/test_oracle_pins.py``
+(``kkt_polish``, ``kkt_residual`` and the bounds by ``tests/test_oracle_kkt.py``)
 (numpy Philox, closed forms, KKT, lambda_max, brute force over supports,
 sklearn, lstsq, brute-force set logic).  ``uoi_fit`` as a whole is pinned
 through those parts, the noiseless recovery special case and the cases whose
@@ -117,6 +118,7 @@ def lib():
                                                P(C.c_uint32), i32, P(d), i32, d, d, d, i32, i32,
                                                P(i64), i64, P(d), P(i32), P(C.c_uint8), P(d)]
             L.ref_ols_support.argtypes = [P(d), P(d), i64, i64, P(u64), P(d)]
+            L.ref_kkt_polish.argtypes = [P(d), P(d), i64, i64, d, d, P(d), i32, P(d), P(d), P(i32)]
             L.ref_lasso_admm_intercept.argtypes = [P(d), i64, P(d), i64, i64, i64, i64,
                                                    P(C.c_uint32), P(d), i32, d, d, d, i32, i32,
                                                    P(d), P(d), P(i32), P(C.c_uint8), P(d)]
@@ -318,6 +320,61 @@ def ols_support(G, b, support_bits):
     fb = lib().ref_ols_support(_p(G, C.c_double), _p(b, C.c_double), 1, p, _p(S, C.c_uint64),
                                _p(beta, C.c_double))
     return beta, bool(fb)
+
+
+def kkt_polish(G, b, nk, lam, z_start, max_moves=None):
+    """Exact minimiser of (1/2nk)||y - X beta||_W^2 + lam ||beta||_1 from the support
+    and signs of z_start (ref_kkt_polish).  G = X^T W X, b = X^T W y.
+    Returns dict(beta, grad (= (b - G beta)/nk), certified, moves, status)."""
+    G = _f64(G)
+    b = _f64(b).reshape(-1)
+    z = _f64(z_start).reshape(-1)
+    p = G.shape[0]
+    beta = np.zeros(p)
+    grad = np.zeros(p)
+    mv = C.c_int32(0)
+    st = lib().ref_kkt_polish(_p(G, C.c_double), _p(b, C.c_double), 1, p, float(nk), float(lam),
+                              _p(z, C.c_double), int(4 * p if max_moves is None else max_moves),
+                              _p(beta, C.c_double), _p(grad, C.c_double), C.byref(mv))
+    return dict(beta=beta, grad=grad, certified=st == 0, moves=int(mv.value), status=int(st))
+
+
+def kkt_residual(G, b, nk, lam, z):
+    """dist(0, dF(z)) for F(beta) = (1/2) beta^T H beta - c^T beta + lam ||beta||_1,
+    H = G/nk, c = b/nk: the smallest ||c - H z - s|| over s in lam d||z||_1
+    (s_i = lam sign z_i where z_i != 0, s_i = clip(g_i, -lam, lam) elsewhere).
+    Any z is the exact minimiser of F - xi^T beta for some xi of this norm."""
+    H = _f64(G) / nk
+    g = _f64(b).reshape(-1) / nk - H @ _f64(z)
+    on = z != 0
+    xi = np.where(on, g - lam * np.sign(z), g - np.clip(g, -lam, lam))
+    return float(np.linalg.norm(xi))
+
+
+def admm_stop_bound(H_norm, p, z, lam, rho=1.0, abs_tol=1e-6, rel_tol=1e-6, eta=0.0, c_norm=0.0):
+    """Bound on kkt_residual of an ADMM iterate z that met the stopping rule of Eq. 5
+    (primal ||x - z|| <= eps_pri, dual rho ||z - z_prev|| <= eps_dual).  At the stop
+    c - H z - rho u = H (x - z) + rho (z - z_prev) with rho u in lam d||z||_1, so the
+    residual is at most ||H|| eps_pri + eps_dual; eps_pri uses ||x|| <= ||z|| + eps_pri
+    and eps_dual uses rho ||u|| <= lam sqrt(p) (|rho u_i| <= lam).  eta > 0 adds
+    arithmetic that is accurate to eta relative (x-update, moments):
+    eta ((||H|| + rho) (||z|| + eps_pri) + ||c||)."""
+    zn = float(np.linalg.norm(z))
+    sp = np.sqrt(p)
+    eps_pri = (sp * abs_tol + rel_tol * zn) / (1.0 - rel_tol)
+    eps_dual = sp * abs_tol + rel_tol * lam * sp
+    return H_norm * eps_pri + eps_dual + eta * ((H_norm + rho) * (zn + eps_pri) + c_norm)
+
+
+def support_band(beta_hat, grad_hat, lam, kappa, mu, H_norm):
+    """Features whose membership in the support of a point with kkt_residual <= kappa
+    is not decided by the exact minimiser beta_hat (gradient grad_hat): such a point z
+    satisfies ||z - beta_hat|| <= kappa / mu (mu = smallest eigenvalue of H), so
+    |beta_hat_i| > kappa / mu forces z_i != 0 with the same sign, and
+    |grad_hat_i| < lam - kappa (1 + ||H|| / mu) forces z_i = 0."""
+    delta = kappa / mu
+    on = beta_hat != 0
+    return (on & (np.abs(beta_hat) <= delta)) | (~on & (lam - np.abs(grad_hat) <= kappa + H_norm * delta))
 
 
 def make_params(B1, B2, q, lambdas=None, lambda_min_ratio=1e-3, rho=1.0, abs_tol=1e-6,

@@ -287,6 +287,86 @@ int ref_admm_column(const double* L, const double* bn, int64_t p, double lambda,
     return converged;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Exact minimiser by KKT polish (optimality conditions of Eq. 2)            */
+/* ------------------------------------------------------------------------- */
+/* Solves H_AA b_A = c_A - lambda s_A for the active set A (H = G/nk, c = b/nk);
+ * returns 0, or REF_ERR_NOT_PD when H_AA is not positive definite. */
+static int active_set_solve(const double* G, const double* b, int64_t ldb, int64_t p, double nk,
+                            double lambda, const int8_t* s, double* beta)
+{
+    int64_t* idx = (int64_t*)malloc((size_t)p * sizeof(int64_t));
+    int64_t na = 0;
+    for (int64_t i = 0; i < p; ++i)
+        if (s[i]) idx[na++] = i;
+    memset(beta, 0, (size_t)p * sizeof(double));
+    int st = 0;
+    if (na > 0) {
+        double* H = (double*)malloc((size_t)(na * na) * sizeof(double));
+        double* L = (double*)malloc((size_t)(na * na) * sizeof(double));
+        double* rhs = (double*)malloc((size_t)na * sizeof(double));
+        double* x = (double*)malloc((size_t)na * sizeof(double));
+        for (int64_t a = 0; a < na; ++a) {
+            for (int64_t c = 0; c < na; ++c) H[a * na + c] = G[idx[a] * p + idx[c]] / nk;
+            rhs[a] = b[idx[a] * ldb] / nk - lambda * (double)s[idx[a]];
+        }
+        if (ref_cholesky(H, na, L) != 0) {
+            st = REF_ERR_NOT_PD;
+        } else {
+            ref_cholesky_solve(L, na, rhs, x);
+            for (int64_t a = 0; a < na; ++a) beta[idx[a]] = x[a];
+        }
+        free(H); free(L); free(rhs); free(x);
+    }
+    free(idx);
+    return st;
+}
+
+int ref_kkt_polish(const double* G, const double* b, int64_t ldb, int64_t p, double nk,
+                   double lambda, const double* z_start, int32_t max_moves,
+                   double* beta, double* grad, int32_t* moves)
+{
+    int8_t* s = (int8_t*)malloc((size_t)p);
+    for (int64_t i = 0; i < p; ++i)
+        s[i] = z_start[i] > 0.0 ? 1 : (z_start[i] < 0.0 ? -1 : 0);
+    int32_t mv = 0;
+    int status = 1;
+    for (;;) {
+        int st = active_set_solve(G, b, ldb, p, nk, lambda, s, beta);
+        if (st != 0) { status = st; break; }
+        /* g = c - H beta */
+        for (int64_t i = 0; i < p; ++i) {
+            double hb = 0.0;
+            for (int64_t j = 0; j < p; ++j) hb += G[i * p + j] * beta[j];
+            grad[i] = (b[i * ldb] - hb) / nk;
+        }
+        /* sign condition on A */
+        int flipped = 0;
+        for (int64_t i = 0; i < p; ++i)
+            if (s[i] && !((double)s[i] * beta[i] > 0.0)) flipped = 1;
+        /* inactive condition off A: the largest violation */
+        int64_t worst = -1;
+        double worst_excess = 0.0;
+        for (int64_t i = 0; i < p; ++i) {
+            if (s[i]) continue;
+            double excess = fabs(grad[i]) - lambda * (1.0 + 1e-10);
+            if (excess > worst_excess) { worst_excess = excess; worst = i; }
+        }
+        if (!flipped && worst < 0) { status = 0; break; }
+        if (mv >= max_moves) break;
+        ++mv;
+        if (flipped) {
+            for (int64_t i = 0; i < p; ++i)
+                if (s[i] && !((double)s[i] * beta[i] > 0.0)) s[i] = 0;
+        } else {
+            s[worst] = grad[worst] > 0.0 ? 1 : -1;
+        }
+    }
+    if (moves) *moves = mv;
+    free(s);
+    return status;
+}
+
 /* A = G / nk + rho I */
 static void admm_system(const double* G, int64_t p, double nk, double rho, double* A)
 {

@@ -23,7 +23,8 @@
  * (non-converged ADMM column or min-norm OLS fallback), <0 error.
  *
  * Parity status per function: every function is pinned by a test in
- * tests/test_oracle_pins.py except ref_uoi_fit as a whole, which is pinned
+ * tests/test_oracle_pins.py (ref_kkt_polish in tests/test_oracle_kkt.py)
+ * except ref_uoi_fit as a whole, which is pinned
  * through its parts, the noiseless-recovery special case and the cases whose
  * selection is decided in advance (tests/test_oracle_whole_fit.py: least
  * squares on the training draws, held-out losses, argmin and bagging by an
@@ -123,6 +124,25 @@ void ref_lambda_grid(double lmax, int32_t q, double ratio, double* lambdas);
 int ref_admm_column(const double* L, const double* bn, int64_t p, double lambda, double rho,
                     double abs_tol, double rel_tol, int32_t max_iter,
                     double* z, double* u, double* x_out, double* v_out, int32_t* iters);
+
+/* Exact LASSO minimiser by KKT polish (reference for the error statements of
+ * forms that stop ADMM at a tolerance).  With H = G/nk and c = b/nk (reading 1's
+ * scaling of Eq. 2), b* minimises (1/2) b^T H b - c^T b + lambda ||b||_1 exactly
+ * when, with g = c - H b*,
+ *   g_i = lambda sign(b*_i) on the support A of b*,  |g_i| <= lambda off it.
+ * Given A and the signs s from z_start (the nonzeros of an ADMM iterate), the
+ * rows of the first condition are the active-set equation H_AA b_A = c_A - lambda s_A,
+ * solved by Cholesky in FP64.  The result is certified when every b_A has the
+ * sign s and |g_i| <= lambda (1 + 1e-10) off A.  Otherwise one move is made and the
+ * equation solved again: features whose sign flipped leave A; if none did, the
+ * inactive feature with the largest |g_i| - lambda > 0 enters with the sign of
+ * g_i (an active-set method, Osborne, Presnell and Turlach 2000).
+ * G: p x p, b: p (stride ldb).  beta, grad: p.  moves (nullable): moves made.
+ * Returns 0 when certified, 1 when max_moves ran out (beta then holds the last
+ * solve), REF_ERR_NOT_PD when an active-set matrix is singular. */
+int ref_kkt_polish(const double* G, const double* b, int64_t ldb, int64_t p, double nk,
+                   double lambda, const double* z_start, int32_t max_moves,
+                   double* beta, double* grad, int32_t* moves);
 
 /* Batched LASSO-ADMM: for each bootstrap weight vector k (weights B x m, NULL =
  * one unweighted problem), each response column e < r and each lambda_j, one
