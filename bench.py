@@ -26,6 +26,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "UoI fits/s & ADMM LASSO solves/s vs plain FP64 GPU form at ≤1e-5 coef error"
+DTYPE_MIXED = ("mixed: Gram bf16 2-piece/3 products, inverse + x-update fp16 2-piece/3 products, "
+               "f32 accumulation and ADMM state, f64 OLS refinement and bagging")
 
 
 def parse():
@@ -38,6 +40,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--warm", default="none", choices=["none", "path"])
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed fits of the plain FP64 GPU form on the same inputs (mixed runs only; "
+                         "0 skips the baseline and the coefficient-error comparison)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # size overrides for profiling captures on a small case (the line is then not a
     # bench line: config.overrides says so)
@@ -173,61 +178,93 @@ def algorithmic_gram_flops(m, p, r, rows):
 # ----------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # ----------------------------------------------------------------------------
-def cpu_sample(w, X, Y, support_size=100):
-    """Times oracle stages on bootstrap 0 and extrapolates to one full fit.
+def host_cores():
+    """Threads this process may run on, and the host's logical CPU count from /proc/cpuinfo."""
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except AttributeError:
+        avail = os.cpu_count() or 1
+    listed = 0
+    try:
+        with open("/proc/cpuinfo") as f:
+            listed = sum(1 for ln in f if ln.startswith("processor"))
+    except OSError:
+        pass
+    return avail, listed or avail
 
-    Stages timed: the weighted Gram over a row sample (per multiply-add rate),
-    one p x p Cholesky, path-warm ADMM columns of one bootstrap over a lambda
-    sample, and one OLS on a support of ``support_size`` features.  The fit time
-    is rebuilt from the workload's operation counts.  Single thread.
+
+def cpu_sample(w, X, Y, threads=1, support_size=100):
+    """Times oracle stages and extrapolates to one full fit on ``threads`` cores.
+
+    Each of ``threads`` concurrent workers times the stages of its own selection
+    bootstrap k (the oracle's OpenMP loop runs bootstraps in parallel, one per
+    thread): the weighted Gram over a row sample (per multiply-add rate), one
+    Cholesky of order min(p, 1000) scaled by p^3, path-warm ADMM columns over a
+    lambda sample, and one OLS on a support of ``support_size`` features.  The
+    fit time is rebuilt from the workload's operation counts, with B1 and B2
+    bootstraps spread over the threads (ceil(B / threads) rounds each).
     Returns (fits_per_s, solves_per_s, description)."""
+    import concurrent.futures as cf
+
     import oracle
     m, p = X.shape
     r = Y.shape[1]
     t_all = time.time()
-    rows = min(m, max(200, int(2.0e9 / (p * (p + r)))))
-    w0 = oracle.selection_weights(m, w.block_len, 0, 0, 0)
-    ws = w0.copy()
-    ws[rows:] = 0
-    nz_rows = int(np.count_nonzero(ws))
-    t = time.time()
-    G, B = oracle.weighted_moments(X, Y, ws)
-    t_fma = (time.time() - t) / max(nz_rows * p * (p + r), 1)
-    nz_sel = int(np.count_nonzero(w0))
-    nk = float(ws.sum())
-    A = G / nk + np.eye(p)
-    t = time.time()
-    L, _ = oracle.cholesky(A)
-    t_chol = time.time() - t
+    rows = min(m, max(200, int(1.0e9 / (p * (p + r)))))
     lam = oracle.lambda_grid(oracle.lambda_max(X, Y), w.q)
     jsel = list(range(0, w.q, max(1, w.q // 4)))
-    t = time.time()
-    its = 0
-    z = np.zeros(p)
-    u = np.zeros(p)
-    for j in jsel:
-        res = oracle.admm_column(L, B[:, 0] / nk, lam[j], z0=z, u0=u)
-        z, u = res["z"], res["u"]
-        its += res["iters"]
-    t_admm_col = (time.time() - t) / len(jsel)
-    s = min(p, support_size)
+    pc = min(p, 1000)
+    s_ols = min(p, support_size)
     bits = np.zeros((p + 63) // 64, dtype=np.uint64)
-    for i in range(s):
+    for i in range(s_ols):
         bits[i // 64] |= np.uint64(1) << np.uint64(i % 64)
-    t = time.time()
-    oracle.ols_support(G, B[:, 0], bits)
-    t_ols = time.time() - t
+
+    def stages(k):
+        w0 = oracle.selection_weights(m, w.block_len, 0, 0, k)
+        ws = w0.copy()
+        ws[rows:] = 0
+        nz_rows = int(np.count_nonzero(ws))
+        t = time.time()
+        G, B = oracle.weighted_moments(X, Y, ws)
+        t_fma = (time.time() - t) / max(nz_rows * p * (p + r), 1)
+        nk = float(ws.sum())
+        A = G / nk + np.eye(p)
+        t = time.time()
+        L_c, _ = oracle.cholesky(A[:pc, :pc])
+        t_chol = (time.time() - t) * (p / pc) ** 3
+        L, _ = oracle.cholesky(A) if pc < p else (L_c, 0)
+        t = time.time()
+        its = 0
+        z = np.zeros(p)
+        u = np.zeros(p)
+        for j in jsel:
+            res = oracle.admm_column(L, B[:, 0] / nk, lam[j], z0=z, u0=u)
+            z, u = res["z"], res["u"]
+            its += res["iters"]
+        t_admm_col = (time.time() - t) / len(jsel)
+        t = time.time()
+        oracle.ols_support(G, B[:, 0], bits)
+        t_ols = time.time() - t
+        return dict(t_fma=t_fma, t_chol=t_chol, t_admm_col=t_admm_col, t_ols=t_ols, its=its,
+                    nz_rows=nz_rows, nz_sel=int(np.count_nonzero(w0)))
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        res = list(ex.map(stages, range(threads)))
+    mean = {key: float(np.mean([rr[key] for rr in res])) for key in res[0]}
     n_eval = m - int(np.floor(0.8 * m))
-    t_loss = n_eval * p * t_fma
+    t_loss = n_eval * p * mean["t_fma"]
     train_rows = int(0.8 * m * (1 - np.exp(-1)))
     n_cols = w.B1 * w.q * r
-    t_sel = w.B1 * (nz_sel * p * (p + r) * t_fma + t_chol) + n_cols * t_admm_col
-    t_est = w.B2 * (train_rows * p * (p + r) * t_fma + w.q * r * (t_ols + t_loss))
-    t_fit = t_sel + t_est
-    desc = (f"FP64 oracle, 1 thread, stages of bootstrap 0: Gram over {nz_rows} of {m} rows, "
-            f"one {p}x{p} Cholesky, {len(jsel)} path-warm ADMM columns ({its} iterations), one "
-            f"OLS on {s} features; extrapolated by operation counts to B1={w.B1}, q={w.q}, "
-            f"B2={w.B2} ({t_fit:.0f} s per fit); sample took {time.time() - t_all:.1f} s")
+    t_sel_boot = mean["nz_sel"] * p * (p + r) * mean["t_fma"] + mean["t_chol"] + w.q * r * mean["t_admm_col"]
+    t_est_boot = train_rows * p * (p + r) * mean["t_fma"] + w.q * r * (mean["t_ols"] + t_loss)
+    rounds1 = -(-w.B1 // threads)
+    rounds2 = -(-w.B2 // threads)
+    t_fit = rounds1 * t_sel_boot + rounds2 * t_est_boot
+    desc = (f"FP64 oracle on {threads} thread(s), each timing the stages of its own selection bootstrap: "
+            f"Gram over {int(mean['nz_rows'])} of {m} rows, one {pc}x{pc} Cholesky scaled by (p/{pc})^3, "
+            f"{len(jsel)} path-warm ADMM columns ({int(mean['its'])} iterations), one OLS on {s_ols} features; "
+            f"extrapolated by operation counts to B1={w.B1}, q={w.q}, B2={w.B2} with ceil(B/{threads}) "
+            f"bootstrap rounds per thread ({t_fit:.0f} s per fit); sample took {time.time() - t_all:.1f} s")
     return 1.0 / t_fit, n_cols / t_fit, desc
 
 
@@ -250,19 +287,23 @@ def run_reference(args):
     w, X, Y = workload(args.workload, args.order if synth.WORKLOADS[args.workload].kind == "var" else 1)
     import oracle
     oracle.build_oracle()
-    vals = []
+    threads, listed = host_cores()
+    vals, secs = [], []
     desc = ""
     for i in range(args.warmup + args.steps):
-        fps, sps, desc = cpu_sample(w, X, Y)
+        t0 = time.time()
+        fps, sps, desc = cpu_sample(w, X, Y, threads=threads)
         if i >= args.warmup:
             vals.append(fps)
+            secs.append(time.time() - t0)
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fits/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name},
-            "cpu_baseline": {"value": v, "unit": "fits/s", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "fits/s", "cores": threads, "host_cpus": listed,
+                             "kind": "oracle", "sample": desc,
+                             "sample_wall_s_per_step": float(np.mean(secs))},
             "e2e": {"value": v, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -402,16 +443,27 @@ def main():
         t1 = time.perf_counter()
         e2e = {"value": args.e2e_steps / (t1 - t0), "unit": "fits/s",
                "h2d_bytes_per_step": int(X.nbytes + Y.nbytes), "d2h_bytes_per_step": int(r * p * 8)}
+    # the metric's baseline: the plain FP64 GPU form on the same device-resident
+    # inputs, and the coefficient error of the timed form against it
+    base = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        base = fp64_baseline(args, native, torch, Xd, Yd, kw, stream, out, fits_s, world)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        fps, sps, desc = cpu_sample(w, X, Y)
-        cpu = {"value": fps, "unit": "fits/s", "cores": 1, "kind": "oracle", "sample": desc,
-               "solves_per_s": sps}
+        threads, listed = host_cores()
+        fps, sps, desc = cpu_sample(w, X, Y, threads=threads)
+        fps1, sps1, desc1 = cpu_sample(w, X, Y, threads=1)
+        cpu = {"value": fps, "unit": "fits/s", "cores": threads, "host_cpus": listed, "kind": "oracle",
+               "sample": desc, "solves_per_s": sps,
+               "single_thread": {"value": fps1, "unit": "fits/s", "cores": 1, "solves_per_s": sps1,
+                                 "sample": desc1}}
     if rank == 0:
         line = {"metric": METRIC, "value": fits_s, "unit": "fits/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x4+f32+f64" if args.precision == "mixed" else "f64",
+                "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": base["vs_fp64_gpu"] if base else None,
+                "baseline": base,
+                "dtype": DTYPE_MIXED if args.precision == "mixed" else "f64",
                 "data": "synthetic",
                 "config": {"workload": w.name, "n": m, "p": p, "r": r, "B1": w.B1, "q": w.q,
                            "B2": w.B2, "precision": args.precision, "warm_start": args.warm,
@@ -426,6 +478,48 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def fp64_baseline(args, native, torch, Xd, Yd, kw, stream, out_mixed, fits_mixed, world):
+    """Times the plain FP64 GPU form (UOI_PREC_FP64) on the same device inputs and
+    compares the bagged estimate, the family and j* of the timed mixed fit with it.
+    The first (untimed) FP64 fit is traced and gives the reference values; an untimed
+    traced mixed fit gives the mixed family and j* (its beta* must equal the timed
+    fits' bit for bit: the fit is deterministic)."""
+    kw64 = dict(kw, precision=native.PREC_FP64)
+    ref = native.uoi_fit_traced(Xd, Yd, trace=True, stream=stream, **kw64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.fp64_steps):
+        native.uoi_fit_traced(Xd, Yd, trace=False, stream=stream, **kw64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.fp64_steps
+    mix = native.uoi_fit_traced(Xd, Yd, trace=True, stream=stream, **kw)
+    bm = mix["beta"].double().cpu().numpy()
+    bf = ref["beta"].double().cpu().numpy()
+    nb = float(np.linalg.norm(bf))
+    err = float(np.linalg.norm(bm - bf) / nb) if nb > 0 else float(np.linalg.norm(bm - bf))
+    fm = mix["family"].cpu().numpy().view(np.uint64)
+    ff = ref["family"].cpu().numpy().view(np.uint64)
+    differ = int(sum(bin(int(x)).count("1") for x in np.bitwise_xor(fm, ff).ravel()))
+    total = int(sum(bin(int(x)).count("1") for x in ff.ravel()))
+    sm = mix["sel_beta"].cpu().numpy()
+    sf = ref["sel_beta"].cpu().numpy()
+    num = np.linalg.norm(sm - sf, axis=-1)
+    den = np.linalg.norm(sf, axis=-1)
+    sel_rel = float(np.max(np.where(den > 0, num / np.where(den > 0, den, 1.0), num)))
+    fps = world * 1e3 / ms
+    return {"form": "plain FP64 GPU (UOI_PREC_FP64), same device-resident inputs",
+            "value": fps, "unit": "fits/s", "ms_per_step": ms, "steps": args.fp64_steps, "warmup": 1,
+            "vs_fp64_gpu": fits_mixed / fps,
+            "coef_rel_l2": err, "coef_tol": 1e-5, "coef_within_tol": err <= 1e-5,
+            "family_bits_differ": differ, "family_bits_fp64": total,
+            "jstar_identical": bool(np.array_equal(mix["est_jstar"].cpu().numpy(), ref["est_jstar"].cpu().numpy())),
+            "timed_beta_identical": bool(np.array_equal(out_mixed["beta"].double().cpu().numpy(), bm)),
+            "selection_max_rel_l2_vs_fp64": sel_rel,
+            "fp64_stage_ms": {k: float(ref["diag"][f"ms_{k}"]) for k in ("gram", "factor", "admm", "estimation")}}
 
 
 def bench_batch(args, torch, rank, world, local, dist):
@@ -508,10 +602,12 @@ def bench_batch(args, torch, rank, world, local, dist):
         # the oracle on the median problem (by n p^2), scaled to the batch by n p^2
         work = [pb.X.shape[0] * pb.X.shape[1] ** 2 for pb in probs]
         k = int(np.argsort(work)[len(work) // 2])
+        threads, listed = host_cores()
         fps, sps, desc = cpu_sample(w, np.ascontiguousarray(probs[k].X),
-                                    np.ascontiguousarray(probs[k].y.reshape(-1, 1)))
+                                    np.ascontiguousarray(probs[k].y.reshape(-1, 1)), threads=threads)
         t_batch = sum(work) / work[k] / fps
-        cpu = {"value": count / t_batch, "unit": "fits/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": count / t_batch, "unit": "fits/s", "cores": threads, "host_cpus": listed,
+               "kind": "oracle",
                "sample": f"problem {k} of the batch ({desc}), scaled by n p^2 to all {count}"}
     if rank == 0:
         ns = [pb.X.shape[0] for pb in probs]
@@ -519,7 +615,7 @@ def bench_batch(args, torch, rank, world, local, dist):
         line = {"metric": METRIC, "value": fits_s, "unit": "fits/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x4+f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "dtype": DTYPE_MIXED if args.precision == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": w.name, "problems": count, "n_range": [min(ns), max(ns)],
                            "p_range": [min(ps), max(ps)], "B1": w.B1, "q": w.q, "B2": w.B2,
                            "precision": args.precision, "warm_start": args.warm, "streams": args.streams,

@@ -8,6 +8,7 @@ form (FP32 ADMM) is held to 1e-5 relative l2 on the bagged estimate.
 import numpy as np
 import pytest
 
+import mixed_check
 import oracle
 from paper_1808_06992_gb300 import native, synth
 
@@ -226,9 +227,11 @@ def test_mixed_form_c1_within_1e5():
 
 @pytest.mark.parametrize("warm", [0, 1])
 def test_mixed_tensor_core_xupdate_vs_oracle(warm):
-    # p > 192 in the mixed form takes the tensor-core x-update (3-piece bf16 split,
-    # six products, compensated accumulation); it must reach the oracle's ADMM
-    # solutions to the level of the stopping tolerance.
+    # p > 192 in the mixed form takes the tensor-core x-update (two-piece fp16 split,
+    # three products, compensated accumulation); every column must meet the stopping
+    # rule in exact arithmetic up to the mixed form's rounding, sit within its KKT
+    # residual / lambda_min(H) of the exact minimiser, and share its support outside
+    # the band that residual leaves open (mixed_check).
     d = synth.lasso_problem(1200, 300, 20, seed=31, sigma=0.5, toeplitz_rho=0.5)
     n = d.X.shape[0]
     w = np.stack([oracle.selection_weights(n, 0, 0, 0, k) for k in range(3)])
@@ -236,11 +239,8 @@ def test_mixed_tensor_core_xupdate_vs_oracle(warm):
     ref = oracle.lasso_admm_batch(d.X, d.y, w, lam, warm_start=warm)
     gpu = native.lasso_admm_batch(d.X, d.y, w, lam, warm_start=warm, precision=native.PREC_MIXED)
     assert gpu["conv"].all()
-    worst = max(rel_l2(gpu["beta"][idx], ref["beta"][idx]) for idx in np.ndindex(*ref["beta"].shape[:3]))
-    assert worst <= 1e-4, worst
-    thr = lam[None, :, None, None]
-    amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
-    assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
+    rep = mixed_check.check_batch(d.X, d.y, w, lam, gpu["beta"], ref["beta"], mixed_check.ETA_MIXED)
+    print(rep)
     assert np.abs(gpu["iters"].astype(int) - ref["iters"]).max() <= max(3, int(0.1 * ref["iters"].max()))
 
 
@@ -286,8 +286,7 @@ def test_ols_duplicate_column_goes_to_fp64_factor(prec):
 def test_mixed_tensor_core_inverse_vs_oracle():
     # p >= 512 in the mixed form inverts G/n + rho I by the block Schur-complement
     # recursion on FP32-accurate tensor-core GEMMs (p = 700 recurses twice, with
-    # ragged 316- and 60-order blocks); the ADMM solutions must match the oracle's
-    # Cholesky-based FP64 solutions to the level of the stopping tolerance.
+    # ragged 316- and 60-order blocks); held to the exact minimiser as above.
     d = synth.lasso_problem(2500, 700, 40, seed=33, sigma=0.5, toeplitz_rho=0.5)
     n = d.X.shape[0]
     w = np.stack([oracle.selection_weights(n, 0, 0, 0, k) for k in range(3)])
@@ -295,11 +294,8 @@ def test_mixed_tensor_core_inverse_vs_oracle():
     ref = oracle.lasso_admm_batch(d.X, d.y, w, lam, warm_start=0)
     gpu = native.lasso_admm_batch(d.X, d.y, w, lam, warm_start=0, precision=native.PREC_MIXED)
     assert gpu["conv"].all()
-    worst = max(rel_l2(gpu["beta"][idx], ref["beta"][idx]) for idx in np.ndindex(*ref["beta"].shape[:3]))
-    assert worst <= 1e-4, worst
-    thr = lam[None, :, None, None]
-    amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
-    assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
+    rep = mixed_check.check_batch(d.X, d.y, w, lam, gpu["beta"], ref["beta"], mixed_check.ETA_MIXED)
+    print(rep)
     assert np.abs(gpu["iters"].astype(int) - ref["iters"]).max() <= max(3, int(0.1 * ref["iters"].max()))
 
 
@@ -316,11 +312,8 @@ def test_mixed_tensor_core_xupdate_many_chain_tiles():
     ref = oracle.lasso_admm_batch(d.X, Y, w, lam, warm_start=0)
     gpu = native.lasso_admm_batch(d.X, Y, w, lam, warm_start=0, precision=native.PREC_MIXED)
     assert gpu["conv"].all()
-    worst = max(rel_l2(gpu["beta"][idx], ref["beta"][idx]) for idx in np.ndindex(*ref["beta"].shape[:3]))
-    assert worst <= 1e-4, worst
-    thr = lam[None, :, None, None]
-    amb = (np.abs(np.abs(ref["v"]) - thr) <= 1e-5) | ((np.abs(ref["beta"]) <= 1e-5) & (ref["beta"] != 0))
-    assert int(((gpu["beta"] != 0) != (ref["beta"] != 0))[~amb].sum()) == 0
+    rep = mixed_check.check_batch(d.X, Y, w, lam, gpu["beta"], ref["beta"], mixed_check.ETA_MIXED)
+    print(rep)
 
 
 def test_large_supports_factor_outside_shared_memory():
