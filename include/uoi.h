@@ -101,6 +101,9 @@ typedef struct uoi_params {
 typedef struct uoi_diag {
     uint32_t struct_size;
     float    ms_total, ms_bootstrap, ms_gram, ms_factor, ms_admm, ms_support, ms_estimation;
+                                  /* ms_support: supports are ANDed into the family at ADMM
+                                     column completion, so this is only what follows the
+                                     ADMM launches (the family's tail mask)              */
     int64_t  admm_columns;        /* (bootstrap, equation, lambda) columns solved        */
     int64_t  admm_nonconverged;   /* columns that stopped at max_iter                    */
     int64_t  admm_iterations;     /* sum of iterations over all columns                  */
@@ -121,6 +124,14 @@ typedef struct uoi_diag {
     int64_t  ols_fp64;            /* OLS solves refused by the FP32-factor + FP64-refinement
                                      solver (small pivot or stalled refinement) and
                                      factored in FP64 instead                            */
+    /* The fields below are written when struct_size covers them (or is 0). */
+    int64_t  admm_near_threshold; /* features of finished selection columns whose final
+                                     margin |v_i| - lambda/rho (v = z + u) lies within 1e-6
+                                     of zero: the support test of Eq. 3 is decided by less
+                                     than that at those features                         */
+    int64_t  admm_iter_hist[8];   /* selection columns by ADMM iterations: <= 16, 17-32,
+                                     33-64, 65-128, 129-256, 257-512, > 512 (converged),
+                                     and stopped at max_iter without converging          */
 } uoi_diag;
 
 /* Optional intermediate results of a fit, for testing (every pointer nullable,
@@ -292,6 +303,18 @@ int uoi_ws_dataset(const double* X, const double* Y, int64_t n, int64_t p, int64
                    const uint32_t* weights, int32_t B, const double* lambdas, int32_t q,
                    double rho, double abs_tol, double rel_tol, int32_t max_iter,
                    float* features_out, float* targets_out, void* stream);
+
+/* Test support for the fault path of the tensor-core kernels (the paper has no
+ * counterpart).  Every mbarrier wait of those kernels is bounded (one second by
+ * default); when a limit runs out the kernel records UOI_ERR_TIMEOUT in its
+ * error word and returns, leaving the context usable, and the call returns
+ * UOI_ERR_TIMEOUT.  This runs that bounded wait alone: one thread waits, with
+ * limit_ns (0 < limit_ns <= 10 s, else UOI_ERR_INVALID_ARG), for an arrival on
+ * an mbarrier that nothing arrives on (arrive = 0: returns UOI_ERR_TIMEOUT once
+ * the limit has passed) or that it arrives on itself first (arrive = 1: returns
+ * UOI_OK).  waited_ms (host, nullable): the time the wait took, by the GPU's
+ * global timer. */
+int uoi_selftest_wait(uint64_t limit_ns, int32_t arrive, double* waited_ms, void* stream);
 
 /* Text of a status code (static storage). */
 const char* uoi_status_string(int status);

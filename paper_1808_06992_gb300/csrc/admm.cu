@@ -45,6 +45,7 @@ struct AdmmDev {
     double* u_out;       // final scaled dual per column (nullable)
     const float* z0;     // initial state per column, cold schedule only (nullable)
     const float* u0;
+    unsigned long long* near_count;   // near-threshold features (nullable)
 };
 
 template <typename T>
@@ -195,6 +196,12 @@ __global__ void __launch_bounds__(256, 1) k_admm_resident(AdmmDev<T> P, int32_t*
                         const unsigned bal = __ballot_sync(0xffffffffu, i < p && z[a][b] != T(0));
                         if (lane == 0 && 32 * a < p) and_family_bits(P, col_je, a, bal);
                     }
+                }
+                if (P.near_count) {
+#pragma unroll
+                    for (int a = 0; a < A; ++a)
+                        count_near_threshold<T>(lane + 32 * a < p, z[a][b], u[a][b], kappa[b],
+                                                (T)kNearThreshold, P.near_count);
                 }
                 if (lane == 0) {
                     if (P.iters) P.iters[col] = it_[b];
@@ -511,6 +518,9 @@ __global__ void k_stream_check(AdmmDev<T> P, StreamState S, int cur, T* z, T* u,
                 const unsigned bal = __ballot_sync(0xffffffffu, zi != T(0));
                 if (lane == 0) and_family_bits(P, col_je, a, bal);
             }
+            if (P.near_count)
+                count_near_threshold<T>(i < p, zi, i < p ? us[i] : T(0), (T)(P.lambdas[j] / (double)P.rho),
+                                        (T)kNearThreshold, P.near_count);
         }
         if (lane == 0) {
             if (P.iters) P.iters[col] = it;
@@ -575,7 +585,7 @@ AdmmDev<T> to_dev(const AdmmProblem<T>& P)
     d.rho = (T)P.rho; d.abs_tol = (T)P.abs_tol; d.rel_tol = (T)P.rel_tol;
     d.sqrtp = (T)sqrt((double)P.p);
     d.beta = P.beta; d.iters = P.iters; d.conv = P.conv; d.family = P.family;
-    d.u_out = P.u_out; d.z0 = P.z0; d.u0 = P.u0;
+    d.u_out = P.u_out; d.z0 = P.z0; d.u0 = P.u0; d.near_count = P.near_count;
     return d;
 }
 

@@ -276,7 +276,8 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                     const double* lam, int32_t q, double rho, double abs_tol, double rel_tol,
                     int32_t max_iter, int32_t warm, double* beta, int32_t* iters, uint8_t* conv,
                     uint64_t* family, cudaStream_t s, StageTimer* tm, int* marks, bool icpt,
-                    WsModel* ws = nullptr, const float* X32 = nullptr)
+                    WsModel* ws = nullptr, const float* X32 = nullptr,
+                    unsigned long long* near_count = nullptr)
 {
     int t0 = tm ? tm->mark() : 0;
     DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
@@ -350,13 +351,18 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     P.rho = rho; P.abs_tol = abs_tol; P.rel_tol = rel_tol; P.max_iter = max_iter;
     P.warm = ws ? 0 : (warm == UOI_WARM_LEARNED ? 1 : warm);
     P.beta = beta; P.iters = iters; P.conv = conv; P.family = family;
+    P.near_count = near_count;
     if (ws) { P.z0 = z0.as<float>(); P.u0 = u0.as<float>(); }
     admm_solve<T>(P, s);
     int t3 = tm ? tm->mark() : 0;
     if (marks) { marks[0] = t0; marks[1] = t1; marks[2] = t2; marks[3] = t3; }
 }
 
-struct IterStats { int64_t cols = 0, noncon = 0, iters = 0, group_iters = 0; int32_t maxit = 0; };
+struct IterStats {
+    int64_t cols = 0, noncon = 0, iters = 0, group_iters = 0;
+    int32_t maxit = 0;
+    int64_t hist[8] = { 0, 0, 0, 0, 0, 0, 0, 0 };   // uoi_diag.admm_iter_hist
+};
 
 // Column statistics; group_iters = sum over groups of the iterations during which
 // the group had an active column (a path chain runs its lambdas back to back).
@@ -374,6 +380,12 @@ IterStats iteration_stats(const int32_t* iters_d, const uint8_t* conv_d, int64_t
         st.iters += it[i];
         st.maxit = std::max(st.maxit, it[i]);
         st.noncon += cv[i] ? 0 : 1;
+        int b = 7;                                  // stopped at max_iter without converging
+        if (cv[i]) {
+            b = 0;
+            while (b < 6 && it[i] > (16 << b)) ++b;  // <= 16, <= 32, ..., <= 512, > 512
+        }
+        st.hist[b] += 1;
     }
     if (G > 0 && (int64_t)G * q * r == n) {
         for (int32_t g = 0; g < G; ++g) {
@@ -503,6 +515,8 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     DevBuf iters_b(sizeof(int32_t) * ncol, s), conv_b(ncol, s);
     DevBuf fam(sizeof(uint64_t) * (size_t)(q * r * W), s);
     family_init(fam.as<uint64_t>(), q * r * W, s);
+    DevBuf near_b(sizeof(unsigned long long), s);
+    UOI_CUDA(cudaMemsetAsync(near_b.ptr, 0, near_b.bytes, s));
     int marks[4] = { 0, 0, 0, 0 };
     WsModel* ws = prm->warm_start == UOI_WARM_LEARNED ? ws_for_path(prm->mlp_weights_path, s) : nullptr;
     const int32_t warm_used = prm->warm_start == UOI_WARM_LEARNED ? (ws ? UOI_WARM_LEARNED : UOI_WARM_PATH)
@@ -518,12 +532,13 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
                               lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                               prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, icpt, ws,
-                              X32.ptr ? X32.as<float>() : nullptr);
+                              X32.ptr ? X32.as<float>() : nullptr, near_b.as<unsigned long long>());
     else
         selection_admm<double>(prm->precision, Xd, ldx, Yd, ldy, m, p, r, wsel.as<uint32_t>(), B1,
                                lam.as<double>(), q, prm->rho, prm->abs_tol, prm->rel_tol,
                                prm->max_iter, prm->warm_start, sel_beta.dev, iters_b.as<int32_t>(),
-                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, icpt, ws);
+                               conv_b.as<uint8_t>(), fam.as<uint64_t>(), s, &tm, marks, icpt, ws,
+                               nullptr, near_b.as<unsigned long long>());
     family_mask_tail(fam.as<uint64_t>(), q * r, p, s);
     const int t_sel2 = tm.mark();
 
@@ -623,6 +638,8 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     }
     std::vector<int32_t> sg((size_t)(B2 * q * r));
     UOI_CUDA(cudaMemcpyAsync(sg.data(), sing.ptr, sizeof(int32_t) * sg.size(), cudaMemcpyDeviceToHost, s));
+    unsigned long long near_h = 0;
+    UOI_CUDA(cudaMemcpyAsync(&near_h, near_b.ptr, sizeof(near_h), cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));
     int64_t nsing = 0;
     for (auto v : sg) nsing += v;
@@ -632,7 +649,9 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         diag->ms_gram = tm.ms(marks[0], marks[1]);
         diag->ms_factor = tm.ms(marks[1], marks[2]);
         diag->ms_admm = tm.ms(marks[2], marks[3]);
-        diag->ms_support = 0.f;
+        // supports are taken at ADMM column completion (ballot bitsets ANDed into the
+        // family); what remains after the ADMM launches is the family's tail mask
+        diag->ms_support = tm.ms(marks[3], t_sel2);
         diag->ms_estimation = tm.ms(t_sel2, t_end);
         (void)t_est1;
         diag->admm_columns = its.cols;
@@ -641,7 +660,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         diag->admm_max_iterations = its.maxit;
         diag->ols_singular = nsing;
         diag->gpu_launches = g_launches - launches0;
-        if (diag->struct_size == 0 || diag->struct_size >= sizeof(uoi_diag)) {
+        if (diag->struct_size == 0 || diag->struct_size >= offsetof(uoi_diag, ols_fp64) + sizeof(int64_t)) {
             const KernelTotals g = ktimer_total(TK_GRAM_TC), x = ktimer_total(TK_XUPDATE);
             diag->ms_gram_tc = g.ms;
             diag->n_gram_tc = g.launches;
@@ -652,6 +671,10 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
             diag->bytes_xupdate = x.bytes;
             diag->warm_start_used = warm_used;
             diag->ols_fp64 = n_ols64;
+        }
+        if (diag->struct_size == 0 || diag->struct_size >= offsetof(uoi_diag, admm_iter_hist) + sizeof(diag->admm_iter_hist)) {
+            diag->admm_near_threshold = (int64_t)near_h;
+            for (int b = 0; b < 8; ++b) diag->admm_iter_hist[b] = its.hist[b];
         }
     }
     return (its.noncon > 0 || nsing > 0) ? UOI_OK_WITH_WARNINGS : UOI_OK;

@@ -109,6 +109,22 @@ __device__ __forceinline__ float f64_to_f32_int(double x)
     return __uint_as_float(sign | ((unsigned int)e32 << 23) | m);
 }
 
+// Warp-wide count of near-threshold features at column completion: lane i holds the
+// final z_i, u_i of a column with threshold kappa = lambda/rho (v = z + u, so the
+// margin |v_i| - kappa is |z_i| where z_i != 0 and |u_i| - kappa where z_i = 0).
+// Lane 0 adds the count to *out.  Every lane of the warp must call it.
+template <typename T>
+__device__ __forceinline__ void count_near_threshold(bool valid, T zi, T ui, T kappa, T band,
+                                                     unsigned long long* out)
+{
+    const T az = zi < T(0) ? -zi : zi;
+    const T au = ui < T(0) ? -ui : ui;
+    const T gap = au > kappa ? au - kappa : kappa - au;
+    const bool near = valid && (zi != T(0) ? az <= band : gap <= band);
+    const unsigned bal = __ballot_sync(0xffffffffu, near);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(out, (unsigned long long)__popc(bal));
+}
+
 // Device-side error word: kernels record the first error here and return.
 struct DevStatus {
     int32_t code;      // 0 = ok, else a UOI_ERR_* value

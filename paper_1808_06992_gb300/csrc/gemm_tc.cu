@@ -61,6 +61,7 @@ struct GemmArgs {
     const float* binv;                                 // G: 1 / scale of B_g
     uint32_t* dmax;                                    // G: largest |D_g| (float bits), nullable
     int32_t* err;
+    uint64_t wait_ns = tc::kWaitLimitNs;   // limit of every bounded mbarrier wait
 };
 
 __device__ __forceinline__ void split2(float x, __half& h, __half& l)
@@ -116,7 +117,7 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         const int blkB = ((g * a.NT + nt) * a.kst) * GT_PIECES;
         for (int s_ = 0; s_ < a.kst; ++s_) {
             const int s = s_ % GT_STAGES;
-            if (s_ >= GT_STAGES && !mbar_wait(&empty_bar[s], ((s_ / GT_STAGES) - 1) & 1, &abort_flag)) {
+            if (s_ >= GT_STAGES && !mbar_wait(&empty_bar[s], ((s_ / GT_STAGES) - 1) & 1, &abort_flag, a.wait_ns)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -128,14 +129,14 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         }
         if (abort_flag)
             for (int s_ = max(0, a.kst - GT_STAGES); s_ < a.kst; ++s_)
-                mbar_wait(&full_bar[s_ % GT_STAGES], (s_ / GT_STAGES) & 1, &abort_flag);
+                mbar_wait(&full_bar[s_ % GT_STAGES], (s_ / GT_STAGES) & 1, &abort_flag, a.wait_ns);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer: all three products into accumulator b ----------------
         const uint32_t idesc = idesc_f16(GT_TM, GT_TN);
         int s_ = 0;
         for (int c = 0; c < nchunks && !abort_flag; ++c) {
             const int b = c & 1;
-            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
+            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag, a.wait_ns)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -146,7 +147,7 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             bool first = true;
             for (; s_ < send; ++s_) {
                 const int s = s_ % GT_STAGES;
-                if (!mbar_wait(&full_bar[s], (s_ / GT_STAGES) & 1, &abort_flag)) {
+                if (!mbar_wait(&full_bar[s], (s_ / GT_STAGES) & 1, &abort_flag, a.wait_ns)) {
                     abort_flag = 1;
                     atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                     break;
@@ -172,7 +173,7 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         }
         mma_commit(&done_bar);
         int dummy = 0;
-        mbar_wait(&done_bar, 0, &dummy);
+        mbar_wait(&done_bar, 0, &dummy, a.wait_ns);
     } else if (warp >= 2) {
         // ---------------- epilogue: TMEM -> FP32 running sums -> D ----------------
         const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
@@ -183,7 +184,7 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         for (int t = 0; t < 128; ++t) acc[t] = 0.f;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
-            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag);
+            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag, a.wait_ns);
             if (!__all_sync(0xffffffffu, okw)) {               // warp-uniform exit
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
@@ -202,7 +203,7 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         }
         {
             int dummy = 0;
-            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);   // the ring is idle from here
+            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy, a.wait_ns);   // the ring is idle from here
         }
         __syncwarp();
         // stage the warp's 32 x 128 block in shared memory, then write whole rows

@@ -73,6 +73,7 @@ struct GramTcArgs {
     double* G;                // items x p_out x p_out
     double* Bm;               // items x p_out x r
     int32_t* err;
+    uint64_t wait_ns = tc::kWaitLimitNs;   // limit of every bounded mbarrier wait
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -123,7 +124,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
         const int jb = tj * TN + rank * (TN / 2);    // this CTA's half of the column tile
         for (int g = 0; g < kstages; ++g) {
             const int s = g % STAGES;
-            if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1, &abort_flag)) {
+            if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1, &abort_flag, a.wait_ns)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -140,7 +141,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
         if (abort_flag && rank == 0) {
             // let the copies already issued land before the CTA releases its memory
             for (int g = max(0, kstages - STAGES); g < kstages; ++g)
-                mbar_wait(&full_bar[g % STAGES], (g / STAGES) & 1, &abort_flag);
+                mbar_wait(&full_bar[g % STAGES], (g / STAGES) & 1, &abort_flag, a.wait_ns);
         }
     } else if (warp == 1 && lane == 0 && kstages > 0 && rank == 0) {
         // ---------------- MMA issuer (first CTA, for the pair) ----------------
@@ -148,7 +149,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
         int g = 0;
         for (int c = 0; c < nchunks && !abort_flag; ++c) {
             const int b = c & 1;
-            if (c >= 2 && !mbar_wait_cluster(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
+            if (c >= 2 && !mbar_wait_cluster(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag, a.wait_ns)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -159,7 +160,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
             bool first = true;
             for (; g < gend; ++g) {
                 const int s = g % STAGES;
-                if (!mbar_wait(&full_bar[s], (g / STAGES) & 1, &abort_flag)) {
+                if (!mbar_wait(&full_bar[s], (g / STAGES) & 1, &abort_flag, a.wait_ns)) {
                     abort_flag = 1;
                     atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                     break;
@@ -184,11 +185,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
         }
         mma_commit_pair(&done_bar);                 // every MMA issued above has completed
         int dummy = 0;
-        mbar_wait(&done_bar, 0, &dummy);
+        mbar_wait(&done_bar, 0, &dummy, a.wait_ns);
     } else if (warp == 1 && lane == 0 && kstages > 0) {
         // second CTA: its TMEM is written by the first CTA's MMAs until this arrives
         int dummy = 0;
-        mbar_wait(&done_bar, 0, &dummy);
+        mbar_wait(&done_bar, 0, &dummy, a.wait_ns);
     } else if (warp >= 2) {
         // ---------------- epilogue: TMEM -> FP32 running sums (both CTAs) ----------------
         const int quad = warp & 3;                       // TMEM lanes 32*quad .. +31
@@ -200,7 +201,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
         for (int t = 0; t < 128; ++t) acc[t] = 0.f;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
-            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag);
+            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag, a.wait_ns);
             if (!__all_sync(0xffffffffu, okw)) {               // warp-uniform exit
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);

@@ -169,7 +169,13 @@ struct AdmmProblem {
     double* u_out = nullptr;  // G x q x r x p final scaled dual (nullable)
     const float* z0 = nullptr;    // G x q x r x p initial z, cold schedule only (nullable)
     const float* u0 = nullptr;    // initial u, same layout
+    // count of near-threshold features over all finished columns (nullable): the
+    // margin |v_i| - lambda/rho of the final iterate (|z_i| where z_i != 0, |u_i| -
+    // lambda/rho where z_i = 0, since v = z + u) lies within kNearThreshold of zero
+    unsigned long long* near_count = nullptr;
 };
+// Half-width of the near-threshold band counted at column completion.
+constexpr double kNearThreshold = 1e-6;
 template <typename T>
 void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
 // Streaming schedule with the tensor-core x-update (FP32 state, p > resident limit).

@@ -55,8 +55,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after ~1 s or when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
+// Default limit of every bounded mbarrier wait of the tensor-core kernels (each
+// kernel takes its limit as an argument, set to this by its launcher).
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+// Bounded wait: gives up after limit_ns of the global timer or when another role
+// has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = now_ns();
@@ -64,7 +70,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 255u) {
             if (*abort_flag) return false;
-            if (now_ns() - t0 > 1000000000ull) return false;
+            if (now_ns() - t0 > limit_ns) return false;
         }
     }
 }
@@ -121,7 +127,8 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
 }
 
 // Bounded wait (as mbar_wait) for arrivals that come from the other CTA of the pair.
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                  uint64_t limit_ns)
 {
     if (mbar_try_wait_cluster(bar, parity)) return true;
     const uint64_t t0 = now_ns();
@@ -129,7 +136,7 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
         if (mbar_try_wait_cluster(bar, parity)) return true;
         if ((it & 255u) == 255u) {
             if (*abort_flag) return false;
-            if (now_ns() - t0 > 1000000000ull) return false;
+            if (now_ns() - t0 > limit_ns) return false;
         }
     }
 }

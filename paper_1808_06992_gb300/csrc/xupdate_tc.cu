@@ -73,6 +73,7 @@ struct XtArgs {
     const int32_t* tiles;         // live (group, chain tile) list, or null: grid y, z = tile, group
     const int32_t* ntiles;        // entries of the list in use
     int32_t nct;                  // chain tiles per group
+    uint64_t wait_ns = tc::kWaitLimitNs;   // limit of every bounded mbarrier wait
 };
 
 // 4-byte asynchronous copy global -> shared (completion waited for by the issuing thread).
@@ -164,7 +165,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         const int rowB = g * a.nchains + n0;
         for (int s_ = 0; s_ < a.kst; ++s_) {
             const int s = s_ % nst;
-            if (s_ >= nst && !mbar_wait(&empty_bar[s], ((s_ / nst) - 1) & 1, &abort_flag)) {
+            if (s_ >= nst && !mbar_wait(&empty_bar[s], ((s_ / nst) - 1) & 1, &abort_flag, a.wait_ns)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -178,7 +179,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         }
         if (abort_flag)
             for (int s_ = max(0, a.kst - nst); s_ < a.kst; ++s_)
-                mbar_wait(&full_bar[s_ % nst], (s_ / nst) & 1, &abort_flag);
+                mbar_wait(&full_bar[s_ % nst], (s_ / nst) & 1, &abort_flag, a.wait_ns);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_f16(XT_TM, a.NT);
@@ -187,7 +188,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         int s_ = 0;
         for (int c = 0; c < nchunks && !abort_flag; ++c) {
             const int b = c & 1;
-            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag)) {
+            if (c >= 2 && !mbar_wait(&acce_bar[b], ((c >> 1) - 1) & 1, &abort_flag, a.wait_ns)) {
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                 break;
@@ -198,7 +199,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             bool first1 = true;
             for (; s_ < send; ++s_) {
                 const int s = s_ % nst;
-                if (!mbar_wait(&full_bar[s], (s_ / nst) & 1, &abort_flag)) {
+                if (!mbar_wait(&full_bar[s], (s_ / nst) & 1, &abort_flag, a.wait_ns)) {
                     abort_flag = 1;
                     atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
                     break;
@@ -224,7 +225,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         }
         mma_commit(&done_bar);
         int dummy = 0;
-        mbar_wait(&done_bar, 0, &dummy);
+        mbar_wait(&done_bar, 0, &dummy, a.wait_ns);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
         const int quad = warp & 3;
@@ -251,7 +252,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         for (int t = 0; t < 64; ++t) { acc[t] = 0.f; cmp[t] = 0.f; }
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
-            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag);
+            const bool okw = mbar_wait(&accf_bar[b], (c >> 1) & 1, &abort_flag, a.wait_ns);
             if (!__all_sync(0xffffffffu, okw)) {               // warp-uniform exit
                 abort_flag = 1;
                 atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
@@ -281,7 +282,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
         // small products, once all MMAs are done
         {
             int dummy = 0;
-            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy);
+            if (!abort_flag) mbar_wait(&done_bar, 0, &dummy, a.wait_ns);
         }
         __syncwarp();
         tc_fence_after();
@@ -520,7 +521,8 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
                            float sqrtp, const float* z, const float* norms, int32_t* slot_j,
                            const int32_t* slot_jend, int32_t* slot_it, uint8_t* live, double* beta,
                            int32_t* iters, uint8_t* conv, uint64_t* family, int32_t W,
-                           int32_t* live_count, const float* cn, float* vs_next)
+                           int32_t* live_count, const float* cn, float* vs_next, const float* u,
+                           const double* lambdas, unsigned long long* near_count)
 {
     const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -559,6 +561,10 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
                               (unsigned long long)mask);
                 }
             }
+            if (near_count)
+                count_near_threshold<float>(i < p, zi, i < p ? u[sl * p + i] : 0.f,
+                                            (float)(lambdas[j] / (double)rho), (float)kNearThreshold,
+                                            near_count);
         }
         if (lane == 0) {
             if (iters) iters[col] = it;
@@ -719,7 +725,8 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
                                           sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>(),
                                           live.as<uint8_t>(), P.beta, P.iters, P.conv, P.family, W,
                                           cnt.as<int32_t>(), cn.as<float>(),
-                                          (even ? vs0 : vs1).as<float>());
+                                          (even ? vs0 : vs1).as<float>(), ub.as<float>(), P.lambdas,
+                                          P.near_count);
             UOI_CHECK_LAUNCH();
             count_launch(2);
             if (use_list) {

@@ -47,11 +47,18 @@ class UoiDiag(C.Structure):
         ("ms_gram_tc", C.c_float), ("n_gram_tc", C.c_int64), ("flops_gram_tc", C.c_double),
         ("ms_xupdate", C.c_float), ("n_xupdate", C.c_int64), ("flops_xupdate", C.c_double),
         ("bytes_xupdate", C.c_double), ("warm_start_used", C.c_int32),
-        ("ols_fp64", C.c_int64),
+        ("ols_fp64", C.c_int64), ("admm_near_threshold", C.c_int64),
+        ("admm_iter_hist", C.c_int64 * 8),
     ]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "struct_size"}
+        out = {}
+        for name, _ in self._fields_:
+            if name == "struct_size":
+                continue
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, C.Array) else v
+        return out
 
 
 class UoiTrace(C.Structure):
@@ -94,6 +101,7 @@ def lib():
         L.uoi_ws_loss_grad.argtypes = [vp, vp, vp, i64, C.POINTER(d), vp]
         L.uoi_ws_train.argtypes = [vp, vp, vp, i64, i32, i32, C.c_float, C.c_uint64, C.POINTER(d)]
         L.uoi_ws_dataset.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d, i32, vp, vp, vp]
+        L.uoi_selftest_wait.argtypes = [C.c_uint64, i32, C.POINTER(d), vp]
         L.uoi_status_string.argtypes = [C.c_int]
         L.uoi_status_string.restype = C.c_char_p
         L.uoi_get_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
@@ -106,7 +114,8 @@ EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_lasso_fit_batch", "uoi_v
             "lasso_admm_batch", "lasso_admm_batch_noalloc", "uoi_weighted_moments",
             "uoi_ws_param_count", "uoi_ws_create", "uoi_ws_load", "uoi_ws_save", "uoi_ws_free",
             "uoi_ws_set_params", "uoi_ws_get_params", "uoi_ws_forward", "uoi_ws_loss_grad",
-            "uoi_ws_train", "uoi_ws_dataset", "uoi_status_string", "uoi_get_last_error_detail", "uoi_shutdown")
+            "uoi_ws_train", "uoi_ws_dataset", "uoi_selftest_wait", "uoi_status_string", "uoi_get_last_error_detail",
+            "uoi_shutdown")
 
 
 class UoiError(RuntimeError):
@@ -443,6 +452,18 @@ def ws_dataset(X, Y, weights, lambdas, rho=1.0, abs_tol=1e-6, rel_tol=1e-6, max_
     _check(lib().uoi_ws_dataset(_ptr(X), _ptr(Y), n, p, r, _ptr(w), B, _ptr(lam), q, rho, abs_tol,
                                 rel_tol, max_iter, _ptr(F), _ptr(T), None))
     return F, T
+
+
+def selftest_wait(limit_ns, arrive=False, stream=None):
+    """Bounded mbarrier wait on the GPU (see uoi_selftest_wait); returns the
+    milliseconds the wait took, raises UoiError(ERR_TIMEOUT) when it ran out."""
+    ms = C.c_double(0.0)
+    st = lib().uoi_selftest_wait(int(limit_ns), 1 if arrive else 0, C.byref(ms), stream)
+    if st < 0:
+        err = UoiError(st, last_error())
+        err.waited_ms = float(ms.value)
+        raise err
+    return float(ms.value)
 
 
 def shutdown():

@@ -92,6 +92,17 @@ def compare_fit(ref, gpu, X, Y, lam_tol=1e-13, coef_tol=1e-6, check_weights=True
     return report
 
 
+def iteration_histogram(iters, conv):
+    """uoi_diag.admm_iter_hist from per-column iteration counts and flags."""
+    it = np.asarray(iters).ravel()
+    cv = np.asarray(conv).ravel().astype(bool)
+    edges = [16, 32, 64, 128, 256, 512]
+    h = [int(np.sum(cv & (it <= edges[0])))]
+    h += [int(np.sum(cv & (it > lo) & (it <= hi))) for lo, hi in zip(edges[:-1], edges[1:])]
+    h += [int(np.sum(cv & (it > edges[-1]))), int(np.sum(~cv))]
+    return h
+
+
 def test_c1_fp64_parity_full_trace():
     d = synth.workload_data(1)
     kw = dict(B1=20, B2=10, q=16)
@@ -100,7 +111,14 @@ def test_c1_fp64_parity_full_trace():
     rep = compare_fit(ref, gpu, d.X, d.y.reshape(-1, 1), **kw)
     assert rep["family_clean"]
     assert gpu["status"] == ref["status"] == 0
-    assert gpu["diag"]["admm_iterations"] == int(ref["sel_iters"].sum())
+    dg = gpu["diag"]
+    assert dg["admm_iterations"] == int(ref["sel_iters"].sum())
+    # diagnostics: iteration histogram and the near-threshold count (margin
+    # ||v_i| - lambda/rho| <= 1e-6 of the final iterate, v = x + u) against the oracle's
+    assert dg["admm_iter_hist"] == iteration_histogram(ref["sel_iters"], ref["sel_conv"])
+    near = int(np.sum(np.abs(np.abs(ref["sel_v"]) - ref["lambdas"][None, :, None, None]) <= 1e-6))
+    assert dg["admm_near_threshold"] == near
+    assert dg["ms_support"] >= 0.0
 
 
 def test_c1_device_pointers_match_host_pointers():
@@ -207,6 +225,8 @@ def test_max_iter_one_warns_and_nan_rejected():
     assert out["status"] == native.OK_WITH_WARNINGS
     assert np.all(out["sel_iters"] == 1)
     assert out["diag"]["admm_nonconverged"] > 0
+    assert out["diag"]["admm_iter_hist"] == iteration_histogram(out["sel_iters"], out["sel_conv"])
+    assert out["diag"]["admm_iter_hist"][7] == out["diag"]["admm_nonconverged"]
     Xn = d.X.copy()
     Xn[5, 7] = np.inf
     with pytest.raises(native.UoiError) as ei:
@@ -219,6 +239,7 @@ def test_mixed_form_c1_within_1e5():
     kw = dict(B1=20, B2=10, q=16)
     ref = oracle.uoi_lasso_fit(d.X, d.y, **kw)
     gpu = native.uoi_fit_traced(d.X, d.y, precision=native.PREC_MIXED, **kw)
+    assert gpu["diag"]["admm_iter_hist"] == iteration_histogram(gpu["sel_iters"], gpu["sel_conv"])
     fam_g = bits_to_bool(gpu["family"], 50)
     fam_r = bits_to_bool(ref["family"], 50)
     assert (fam_g != fam_r).sum() == 0
