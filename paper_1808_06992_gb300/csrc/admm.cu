@@ -509,6 +509,8 @@ __global__ void k_stream_check(AdmmDev<T> P, StreamState S, int cur, T* z, T* u,
         const int64_t col = (int64_t)g * P.q * P.r + col_je;
         const T* zs = z + (size_t)sl * p;
         const T* us = u + (size_t)sl * p;
+        // threshold lambda_j / rho, once per column (FP64 division off the loop)
+        const T kappa_j = P.near_count ? (T)(P.lambdas[j] / (double)P.rho) : T(0);
         for (int a = 0; 32 * a < p; ++a) {
             const int i = lane + 32 * a;
             const T zi = i < p ? zs[i] : T(0);
@@ -519,8 +521,8 @@ __global__ void k_stream_check(AdmmDev<T> P, StreamState S, int cur, T* z, T* u,
                 if (lane == 0) and_family_bits(P, col_je, a, bal);
             }
             if (P.near_count)
-                count_near_threshold<T>(i < p, zi, i < p ? us[i] : T(0), (T)(P.lambdas[j] / (double)P.rho),
-                                        (T)kNearThreshold, P.near_count);
+                count_near_threshold<T>(i < p, zi, i < p ? us[i] : T(0), kappa_j, (T)kNearThreshold,
+                                        P.near_count);
         }
         if (lane == 0) {
             if (P.iters) P.iters[col] = it;

@@ -260,12 +260,13 @@ void validate(const uoi_params* prm)
 }
 
 // Moments for B weight vectors in the precision of the fit.
+// lower_only (tensor-core form): G's upper triangle may be left unwritten.
 void moments(int precision, const double* X, int64_t ldx, const double* Y, int64_t ldy,
              int64_t m, int64_t p, int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B,
-             double* G, double* Bm, cudaStream_t s, const float* X32 = nullptr)
+             double* G, double* Bm, cudaStream_t s, const float* X32 = nullptr, bool lower_only = false)
 {
     if (precision == UOI_PREC_MIXED && gram_tc_available())
-        moments_tc(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, s, X32);
+        moments_tc(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, s, X32, lower_only);
     else
         moments_fp64(X, ldx, Y, ldy, m, p, r, w, mask, B, G, Bm, 0, s);
 }
@@ -280,6 +281,12 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                     unsigned long long* near_count = nullptr)
 {
     int t0 = tm ? tm->mark() : 0;
+    // mixed form, large p: the block inverse on tensor cores; when nothing but the
+    // FP32 system reads G (no intercept elimination, no learned start), the Gram's
+    // lower triangle is enough and the system is built from it
+    bool tc_inverse = false;
+    if constexpr (sizeof(T) == 4) tc_inverse = p >= 512 && inverse_tc_available();
+    const bool lower_only = tc_inverse && !icpt && !ws && precision == UOI_PREC_MIXED && gram_tc_available();
     DevBuf G(sizeof(double) * (size_t)(B * p * p), s), Bm(sizeof(double) * (size_t)(B * p * r), s);
     DevBuf nk(sizeof(double) * B, s);
     if (w) {
@@ -298,7 +305,8 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
         schur_intercept(Ga.as<double>(), Ba.as<double>(), nk.as<double>(), w ? B : 1, p, r, B, G.as<double>(),
                         Bm.as<double>(), s);
     } else {
-        moments(precision, Xd, ldx, Yd, ldy, m, p, r, w, nullptr, B, G.as<double>(), Bm.as<double>(), s, X32);
+        moments(precision, Xd, ldx, Yd, ldy, m, p, r, w, nullptr, B, G.as<double>(), Bm.as<double>(), s, X32,
+                lower_only);
     }
     int t1 = tm ? tm->mark() : 0;
     DevBuf st(sizeof(DevStatus), s);
@@ -306,16 +314,17 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
     DevBuf A(sizeof(T) * (size_t)(B * p * p), s);
     DevBuf M(sizeof(T) * (size_t)(B * p * p), s);
     DevBuf c(sizeof(T) * (size_t)(B * p * r), s);
-    bool tc_inverse = false;
     if constexpr (sizeof(T) == 4) {
         // mixed form, large p: block inverse with tensor-core GEMMs
-        if (p >= 512 && inverse_tc_available()) {
-            build_system<float>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<float>(), s);
+        if (tc_inverse) {
+            if (lower_only)
+                build_system_lower(G.as<double>(), nk.as<double>(), rho, p, B, A.as<float>(), s);
+            else
+                build_system<float>(G.as<double>(), nk.as<double>(), rho, p, B, A.as<float>(), s);
             if (!ws) G.release();
             spd_inverse_tc(A.as<float>(), p, B, M.as<float>(), st.as<DevStatus>(), s);
             check_status(st.as<DevStatus>(), s, "inverse of G/n + rho I");
             rhs_from_inverse<float>(M.as<float>(), Bm.as<double>(), nk.as<double>(), p, r, B, c.as<float>(), s);
-            tc_inverse = true;
         }
     }
     if (!tc_inverse) {

@@ -56,6 +56,36 @@ __global__ void k_build_system(const double* __restrict__ G, const double* nk, d
     }
 }
 
+// FP32 system from the lower triangle of G: 32 x 32 tiles through shared memory;
+// each lower tile is written in place and, transposed, to its mirror (the
+// diagonal tile's upper half from its lower half).  Block (32, 8), grid
+// (tiles, tiles, B).
+__global__ void k_build_system_lower(const double* __restrict__ G, const double* nk, double rho, int64_t p,
+                                     float* __restrict__ A)
+{
+    __shared__ float tile[32][33];
+    const int64_t k = blockIdx.z;
+    const int bx = blockIdx.x, by = blockIdx.y;        // source tile: rows by*32.., columns bx*32..
+    if (bx > by) return;                               // lower tiles only
+    const float inv_n = (float)(1.0 / nk[k]);
+    const double* g = G + k * p * p;
+    float* a = A + k * p * p;
+    const int tx = threadIdx.x;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int64_t r = (int64_t)by * 32 + yy, c = (int64_t)bx * 32 + tx;
+        if (r < p && c < p && c <= r) {
+            const float v = system_entry<float>(__ldg(g + r * p + c), (double)inv_n, rho, r == c);
+            tile[yy][tx] = v;
+            a[r * p + c] = v;
+        }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {     // mirror: rows bx*32 + yy, columns by*32 + tx
+        const int64_t r = (int64_t)bx * 32 + yy, c = (int64_t)by * 32 + tx;
+        if (r < p && c < p && c > r) a[r * p + c] = tile[tx][yy];
+    }
+}
+
 // Factor the nb x nb diagonal block at j0 (one block per matrix).
 template <typename T>
 __global__ void k_chol_diag(T* A, int64_t p, int64_t j0, int nb, DevStatus* st)
@@ -346,6 +376,15 @@ void build_system(const double* G, const double* nk, double rho, int64_t p, int3
 {
     dim3 gb((unsigned)std::min<int64_t>(p, 1024), (unsigned)B);
     k_build_system<T><<<gb, 256, 0, s>>>(G, nk, rho, p, A);
+    UOI_CHECK_LAUNCH();
+    count_launch();
+}
+
+void build_system_lower(const double* G, const double* nk, double rho, int64_t p, int32_t B, float* A,
+                        cudaStream_t s)
+{
+    const unsigned tt = (unsigned)ceil_div(p, 32);
+    k_build_system_lower<<<dim3(tt, tt, (unsigned)B), dim3(32, 8), 0, s>>>(G, nk, rho, p, A);
     UOI_CHECK_LAUNCH();
     count_launch();
 }

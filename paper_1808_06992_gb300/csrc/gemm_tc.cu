@@ -25,6 +25,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "kernels.h"
 #include "tc_common.cuh"
@@ -402,115 +403,163 @@ void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, fl
     count_launch();
 }
 
-// In-place Gauss-Jordan inverse of one SPD block per CTA (n <= INV_BASE = 192).
-// 1024 threads; thread (ty, tx) owns the elements (ty + 32u, tx + 32v), held in
-// registers.  A pivot <= 0 sets status UOI_ERR_NOT_PD (where = group).
-// GJ_R rows / columns per thread: 2 (n <= 64), 4 (n <= 128) or 6 (n <= 192).
-template <int GJ_R>
-__global__ void __launch_bounds__(1024) k_spd_inverse_smem(const float* A, int64_t lda, int64_t gsa,
-                                                           float* M, int64_t ldm, int64_t gsm, int n,
-                                                           DevStatus* st)
+// In-place blocked Gauss-Jordan inverse of one SPD block per CTA (n <= INV_BASE =
+// 192), in steps of 32 pivots (no pivoting: the pivots are Schur-complement
+// diagonals, positive for SPD A).  1024 threads; thread (ty, tx) owns the
+// elements (ty + 32u, tx + 32w), u, w < R, in registers.  Step K works on row and
+// column block K (indices 32K .. 32K + 31):
+//   P = A_KK^{-1}                        (one warp, in registers, by shuffles)
+//   A_KJ <- P A_KJ             (J != K)  (block row K; each warp one of its rows)
+//   A_IJ <- A_IJ - A_IK A_KJ   (I, J != K; A_IK before the step, A_KJ after it)
+//   A_IK <- -A_IK P            (I != K)
+//   A_KK <- P
+// which leaves A^{-1} after the last step (the block form of the pivot-by-pivot
+// Gauss-Jordan elimination: the same products, four barriers per 32 pivots
+// instead of one per pivot).  Rows and columns past n hold zeros and the padded
+// part of the last diagonal block is inverted as the identity, so they never
+// reach the n x n result.  A pivot <= 0 sets status UOI_ERR_NOT_PD (where = group).
+constexpr int GJ_LD = 33;                              // shared rows: conflict-free columns
+template <int R>
+constexpr size_t gj_smem_bytes() { return sizeof(float) * (size_t)(3 * 32 * R * GJ_LD + 32 * GJ_LD); }
+
+// P = inverse of the bk x bk diagonal block whose row k, column l is at
+// D[k * GJ_LD + l] (identity past bk), by one warp: lane l holds column l in
+// registers and each of the 32 pivots is one round of shuffles.  Returns false
+// when a pivot is not positive.  Not inlined, so that the caller's register tile
+// is saved around it by the one warp that calls it instead of being squeezed.
+__device__ __noinline__ bool gj_invert_diag(const float* D, float* P, int bk)
 {
-    // The matrix lives in the threads' registers; step k needs only row k and
-    // column k (before the step), which their owners publish into shared
-    // memory, double-buffered so one barrier per step suffices.
+    const int tx = threadIdx.x & 31;
+    float d[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) d[k] = (k < bk && tx < bk) ? D[k * GJ_LD + tx] : (k == tx ? 1.f : 0.f);
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float piv = __shfl_sync(0xffffffffu, d[k], k);
+        ok = ok && piv > 0.f;
+        const float inv = 1.f / piv;
+        const float r = (tx == k) ? inv : d[k] * inv;           // row k / pivot
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float c = __shfl_sync(0xffffffffu, d[i], k);   // column k
+            d[i] = (i == k) ? r : fmaf(-c, r, tx == k ? 0.f : d[i]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) P[k * GJ_LD + tx] = d[k];
+    return ok;
+}
+
+template <int R>
+__global__ void __launch_bounds__(1024) k_spd_inverse_blocked(const float* A, int64_t lda, int64_t gsa,
+                                                              float* M, int64_t ldm, int64_t gsm, int n,
+                                                              DevStatus* st)
+{
     extern __shared__ float sm[];
-    float* colb = sm;                       // [2][n] column k
-    float* rowb = sm + 2 * n;               // [2][n] row k
+    float* colK = sm;                           // [32R][LD]: colK[i][k] = A(i, 32K + k) before step K
+    float* rowT = colK + 32 * R * GJ_LD;        // [32R][LD]: rowT[j][k] = A(32K + k, j) before step K
+    float* rowN = rowT + 32 * R * GJ_LD;        // [32R][LD]: rowN[j][k] = (P A_K.)(k, j)
+    float* P = rowN + 32 * R * GJ_LD;           // [32][LD]:  P[k][l] = (A_KK^{-1})(k, l)
+    __shared__ int bad;
     const int g = blockIdx.x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const float* a = A + (int64_t)g * gsa;
-    float v[GJ_R][GJ_R];
+    float v[R][R];
 #pragma unroll
-    for (int u = 0; u < GJ_R; ++u)
+    for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int w = 0; w < GJ_R; ++w) {
+        for (int w = 0; w < R; ++w) {
             const int i = ty + 32 * u, j = tx + 32 * w;
             v[u][w] = (i < n && j < n) ? a[(int64_t)i * lda + j] : 0.f;
-            if (i == 0 && j < n) rowb[j] = v[u][w];
-            if (j == 0 && i < n) colb[i] = v[u][w];
         }
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        const float* col = colb + (k & 1) * n;
-        const float* row = rowb + (k & 1) * n;
-        float* ncol = colb + ((k + 1) & 1) * n;
-        float* nrow = rowb + ((k + 1) & 1) * n;
-        const float piv = col[k];
-        if (!(piv > 0.f)) {
-            if (threadIdx.x == 0) dev_fail(st, UOI_ERR_NOT_PD, g);
-            return;                         // same decision in every thread
-        }
-        const float inv = 1.f / piv;
-        // r = row k / pivot (with 1 / pivot at column k), c = column k; then
-        // every element: (column k reset to 0) - c_i r_j, and row k := r
-        float r[GJ_R], c[GJ_R];
+    if (threadIdx.x == 0) bad = 0;
+    const int nblk = (n + 31) / 32;
 #pragma unroll
-        for (int w = 0; w < GJ_R; ++w) {
-            const int j = tx + 32 * w;
-            r[w] = j < n ? (j == k ? inv : row[j] * inv) : 0.f;
-        }
+    for (int K = 0; K < R; ++K) {
+        if (K >= nblk) break;
+        __syncthreads();                        // the last step's readers are done
 #pragma unroll
-        for (int u = 0; u < GJ_R; ++u) {
-            const int i = ty + 32 * u;
-            c[u] = i < n ? col[i] : 0.f;
-        }
+        for (int u = 0; u < R; ++u) colK[(ty + 32 * u) * GJ_LD + tx] = v[u][K];
 #pragma unroll
-        for (int u = 0; u < GJ_R; ++u) {
-            const bool own_row = ty + 32 * u == k;
-#pragma unroll
-            for (int w = 0; w < GJ_R; ++w) {
-                const float base = (tx + 32 * w == k) ? 0.f : v[u][w];
-                const float x = fmaf(-c[u], r[w], base);
-                v[u][w] = own_row ? r[w] : x;
-            }
-        }
-        // publish row and column k + 1 for the next step
-        const int k1 = k + 1;
-        if (ty == (k1 & 31)) {                       // the warp holding row k + 1
-#pragma unroll
-            for (int u = 0; u < GJ_R; ++u) {
-                if (ty + 32 * u != k1) continue;
-#pragma unroll
-                for (int w = 0; w < GJ_R; ++w) {
-                    const int j = tx + 32 * w;
-                    if (j < n) nrow[j] = v[u][w];
-                }
-            }
-        }
-        if (tx == (k1 & 31)) {                       // the lane holding column k + 1
-#pragma unroll
-            for (int w = 0; w < GJ_R; ++w) {
-                if (tx + 32 * w != k1) continue;
-#pragma unroll
-                for (int u = 0; u < GJ_R; ++u) {
-                    const int i = ty + 32 * u;
-                    if (i < n) ncol[i] = v[u][w];
-                }
-            }
+        for (int w = 0; w < R; ++w) rowT[(tx + 32 * w) * GJ_LD + ty] = v[K][w];
+        __syncthreads();
+        if (ty == 0) {
+            const bool ok = gj_invert_diag(colK + 32 * K * GJ_LD, P, min(32, n - 32 * K));
+            if (!ok && tx == 0) bad = 1;
         }
         __syncthreads();
+        if (bad) {
+            if (threadIdx.x == 0) dev_fail(st, UOI_ERR_NOT_PD, g);
+            return;                             // same decision in every thread
+        }
+        // block row K: this warp's row 32K + ty becomes row ty of P A_K.
+#pragma unroll
+        for (int w = 0; w < R; ++w)
+            if (w != K) v[K][w] = 0.f;
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+            const float pk = P[ty * GJ_LD + k];
+#pragma unroll
+            for (int w = 0; w < R; ++w)
+                if (w != K) v[K][w] = fmaf(pk, rowT[(tx + 32 * w) * GJ_LD + k], v[K][w]);
+        }
+#pragma unroll
+        for (int w = 0; w < R; ++w)
+            if (w != K) rowN[(tx + 32 * w) * GJ_LD + ty] = v[K][w];
+        v[K][K] = P[ty * GJ_LD + tx];
+        __syncthreads();
+        // every other block row: A_IJ -= A_IK (P A_KJ), A_IK = -A_IK P
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+            if (u != K) v[u][K] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < 32; ++k) {
+            float r[R];
+#pragma unroll
+            for (int w = 0; w < R; ++w)
+                r[w] = (w == K) ? P[k * GJ_LD + tx] : rowN[(tx + 32 * w) * GJ_LD + k];
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                if (u == K) continue;
+                const float c = colK[(ty + 32 * u) * GJ_LD + k];
+#pragma unroll
+                for (int w = 0; w < R; ++w) v[u][w] = fmaf(-c, r[w], v[u][w]);
+            }
+        }
     }
     float* mo = M + (int64_t)g * gsm;
 #pragma unroll
-    for (int u = 0; u < GJ_R; ++u)
+    for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int w = 0; w < GJ_R; ++w) {
+        for (int w = 0; w < R; ++w) {
             const int i = ty + 32 * u, j = tx + 32 * w;
             if (i < n && j < n) mo[(int64_t)i * ldm + j] = v[u][w];
         }
 }
 
+template <int R>
+void launch_inverse_blocked(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM, int64_t gsM,
+                            int64_t n, int32_t G, DevStatus* st, cudaStream_t s)
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        UOI_CUDA(cudaFuncSetAttribute(k_spd_inverse_blocked<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)gj_smem_bytes<R>()));
+    });
+    k_spd_inverse_blocked<R><<<(unsigned)G, 1024, gj_smem_bytes<R>(), s>>>(A, ldA, gsA, Mout, ldM, gsM,
+                                                                           (int)n, st);
+}
+
 void inv_base(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM, int64_t gsM,
               int64_t n, int32_t G, DevStatus* st, cudaStream_t s)
 {
-    const size_t smem = sizeof(float) * (size_t)(4 * n);
     if (n <= 64)
-        k_spd_inverse_smem<2><<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
+        launch_inverse_blocked<2>(A, ldA, gsA, Mout, ldM, gsM, n, G, st, s);
     else if (n <= 128)
-        k_spd_inverse_smem<4><<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
+        launch_inverse_blocked<4>(A, ldA, gsA, Mout, ldM, gsM, n, G, st, s);
     else
-        k_spd_inverse_smem<6><<<(unsigned)G, 1024, smem, s>>>(A, ldA, gsA, Mout, ldM, gsM, (int)n, st);
+        launch_inverse_blocked<6>(A, ldA, gsA, Mout, ldM, gsM, n, G, st, s);
     UOI_CHECK_LAUNCH();
     count_launch();
 }

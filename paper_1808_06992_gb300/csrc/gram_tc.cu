@@ -449,11 +449,28 @@ __global__ void k_diag_lo(const float* losq, int32_t row_tiles, int32_t pz_x,
     const int item = blockIdx.y;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= pz_x) return;
-    const int tiles = (nrows[item] + 63) / 64;
+    const int tiles = min((nrows[item] + 63) / 64, row_tiles);
+    const float* src = losq + (int64_t)item * row_tiles * pz_x + c;
     double s = 0.0;
-    for (int t = 0; t < tiles && t < row_tiles; ++t)
-        s += (double)losq[((int64_t)item * row_tiles + t) * pz_x + c];
+    int t = 0;
+    // eight loads in flight before their (in-order) additions
+    for (; t + 8 <= tiles; t += 8) {
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = src[(int64_t)(t + u) * pz_x];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)x[u];
+    }
+    for (; t < tiles; ++t) s += (double)src[(int64_t)t * pz_x];
     corr[(int64_t)item * pz_x + c] = s;
+}
+
+// Add the diagonal correction only (the caller reads the lower triangle alone).
+__global__ void k_add_diag(double* G, int64_t p_out, int32_t pz_x, const double* corr)
+{
+    const int item = blockIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < pz_x) G[(size_t)item * p_out * p_out + (size_t)c * p_out + c] += corr[(int64_t)item * pz_x + c];
 }
 
 // Add the diagonal correction and fill the upper triangle from the lower one
@@ -495,7 +512,7 @@ bool gram_tc_available()
 void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m,
                      int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
                      const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
-                     cudaStream_t s, const float* X32, int64_t ld32, bool x32_compact)
+                     cudaStream_t s, const float* X32, int64_t ld32, bool x32_compact, bool lower_only)
 {
     if (ld32 == 0) ld32 = ldx;
     if (!gram_tc_available()) throw Error(UOI_ERR_UNSUPPORTED, "tcgen05 Gram needs sm_103a");
@@ -584,7 +601,10 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
         k_diag_lo<<<gd, 256, 0, s>>>(losq.as<float>(), row_tiles, pz_x, nrows.as<int32_t>() + b0,
                                      corr.as<double>());
         UOI_CHECK_LAUNCH();
-        if (colmap) {
+        if (lower_only && !colmap) {
+            k_add_diag<<<dim3((unsigned)ceil_div(pz_x, 256), (unsigned)nb), 256, 0, s>>>(
+                G + (size_t)b0 * p_out * p_out, p_out, pz_x, corr.as<double>());
+        } else if (colmap) {
             dim3 gm((unsigned)std::min<int64_t>(ceil_div((int64_t)pz_x * pz_x, 256), 2048), (unsigned)nb);
             k_mirror<<<gm, 256, 0, s>>>(G + (size_t)b0 * p_out * p_out, p_out, colmap, pz_x,
                                         corr.as<double>());
@@ -610,9 +630,10 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
 
 void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
                 int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
-                double* Bm, cudaStream_t s, const float* X32)
+                double* Bm, cudaStream_t s, const float* X32, bool lower_only)
 {
-    moments_tc_cols(X, ldx, Y, ldy, m, p, r, (int32_t)p, nullptr, w, mask, B, G, Bm, s, X32, 0, false);
+    moments_tc_cols(X, ldx, Y, ldy, m, p, r, (int32_t)p, nullptr, w, mask, B, G, Bm, s, X32, 0, false,
+                    lower_only);
 }
 
 namespace {

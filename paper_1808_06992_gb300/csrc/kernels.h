@@ -98,9 +98,11 @@ void check_finite(const double* X, int64_t ldx, int64_t m, int64_t cols, int32_t
 // Mixed form: split-bf16 tensor-core Gram (gram_tc.cu).
 bool gram_tc_available();
 // X32: optional FP32 copy of X (same leading dimension), read instead of X.
+// lower_only: G's upper triangle is left unwritten (for a caller that reads the
+// lower triangle alone, build_system_lower).
 void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
                 int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
-                double* Bm, cudaStream_t s, const float* X32 = nullptr);
+                double* Bm, cudaStream_t s, const float* X32 = nullptr, bool lower_only = false);
 // out[i*ldx + j] = X[i*ldx + j] rounded to FP32, i < m, j < p.
 void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cudaStream_t s);
 
@@ -110,7 +112,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                      int64_t p_out, int64_t r, int32_t pz_x, const int32_t* colmap,
                      const uint32_t* w, const uint8_t* mask, int32_t B, double* G, double* Bm,
                      cudaStream_t s, const float* X32 = nullptr, int64_t ld32 = 0,
-                     bool x32_compact = false);
+                     bool x32_compact = false, bool lower_only = false);
 // out[i*nu + t] = X32[i*ld + cols[t]]: the FP32 design restricted to the listed columns
 // (X32_compact form for moments_tc_cols: column t of the copy is colmap[t] of X).
 void gather_cols_f32(const float* X32, int64_t ld, int64_t m, const int32_t* cols, int64_t nu, float* out,
@@ -122,6 +124,10 @@ void gather_cols_f32(const float* X32, int64_t ld, int64_t m, const int32_t* col
 template <typename T>
 void build_and_factor(const double* G, const double* nk, double rho, int64_t p, int32_t B,
                       T* A, DevStatus* status, cudaStream_t s);
+// A_k = G_k / nk[k] + rho I in FP32 from the lower triangle of G_k alone (the
+// upper triangle is not read); equal to build_system<float> on the mirrored G.
+void build_system_lower(const double* G, const double* nk, double rho, int64_t p, int32_t B, float* A,
+                        cudaStream_t s);
 // The two halves of build_and_factor.
 template <typename T>
 void build_system(const double* G, const double* nk, double rho, int64_t p, int32_t B, T* A,

@@ -548,23 +548,37 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
         const int j = slot_j[sl];
         const int64_t col_je = (int64_t)j * r + e;
         const int64_t col = (int64_t)g * q * r + col_je;
-        for (int a0 = 0; 32 * a0 < p; ++a0) {
-            const int i = lane + 32 * a0;
-            const float zi = i < p ? z[sl * p + i] : 0.f;
-            if (beta && i < p) beta[col * p + i] = (double)zi;
-            if (family) {
-                const unsigned bal = __ballot_sync(0xffffffffu, zi != 0.f);
-                if (lane == 0) {
-                    const int shift = (a0 & 1) * 32;
-                    const uint64_t mask = ((uint64_t)bal << shift) | ~(0xFFFFFFFFull << shift);
-                    atomicAnd((unsigned long long*)&family[col_je * W + (a0 >> 1)],
-                              (unsigned long long)mask);
-                }
+        // threshold lambda_j / rho, once per column (FP64 division off the loop)
+        const float kappa = near_count ? (float)(lambdas[j] / (double)rho) : 0.f;
+        // eight 32-feature chunks of z and u loaded before their ballots, so the
+        // loads of a finishing column overlap instead of queueing behind the atomics
+        for (int b0 = 0; 32 * b0 < p; b0 += 8) {
+            float zc[8], uc[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int i = lane + 32 * (b0 + t);
+                zc[t] = i < p ? z[sl * p + i] : 0.f;
+                uc[t] = (near_count && i < p) ? u[sl * p + i] : 0.f;
             }
-            if (near_count)
-                count_near_threshold<float>(i < p, zi, i < p ? u[sl * p + i] : 0.f,
-                                            (float)(lambdas[j] / (double)rho), (float)kNearThreshold,
-                                            near_count);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int a0 = b0 + t;
+                if (32 * a0 >= p) break;                         // warp-uniform
+                const int i = lane + 32 * a0;
+                const float zi = zc[t];
+                if (beta && i < p) beta[col * p + i] = (double)zi;
+                if (family) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, zi != 0.f);
+                    if (lane == 0) {
+                        const int shift = (a0 & 1) * 32;
+                        const uint64_t mask = ((uint64_t)bal << shift) | ~(0xFFFFFFFFull << shift);
+                        atomicAnd((unsigned long long*)&family[col_je * W + (a0 >> 1)],
+                                  (unsigned long long)mask);
+                    }
+                }
+                if (near_count)
+                    count_near_threshold<float>(i < p, zi, uc[t], kappa, (float)kNearThreshold, near_count);
+            }
         }
         if (lane == 0) {
             if (iters) iters[col] = it;
