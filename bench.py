@@ -40,9 +40,10 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--warm", default="none", choices=["none", "path"])
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--fp64-steps", type=int, default=2,
+    ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed fits of the plain FP64 GPU form on the same inputs (mixed runs only; "
-                         "0 skips the baseline and the coefficient-error comparison)")
+                         "default 2 on the 50000 x 2000 workload, 0 elsewhere; 0 skips the baseline "
+                         "and the coefficient-error comparison)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # size overrides for profiling captures on a small case (the line is then not a
     # bench line: config.overrides says so)
@@ -50,7 +51,7 @@ def parse():
     ap.add_argument("--B2", type=int)
     ap.add_argument("--q", type=int)
     ap.add_argument("--rows", type=int, help="keep only the first ROWS rows of the design")
-    ap.add_argument("--streams", type=int, default=4, help="worker streams of the batched workload")
+    ap.add_argument("--streams", type=int, default=8, help="worker streams of the batched workload")
     ap.add_argument("--order", type=int, default=1, help="VAR workloads: lag order d of the design")
     ap.add_argument("--intercept", type=int, default=0, choices=[0, 1],
                     help="VAR workloads: fit the unpenalised intercept mu")
@@ -311,6 +312,8 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.fp64_steps is None:
+        args.fp64_steps = 2 if args.workload == 2 else 0
     if args.impl == "reference":
         return run_reference(args)
     import torch

@@ -46,6 +46,7 @@ extern "C" {
 #define UOI_ERR_CUDA          -4   /* a CUDA runtime call failed                           */
 #define UOI_ERR_OOM           -5   /* device allocation failed                             */
 #define UOI_ERR_TIMEOUT       -6   /* a bounded device loop ran out of iterations          */
+#define UOI_ERR_BOUNDS        -7   /* an index check of the checked build failed            */
 #define UOI_ERR_UNSUPPORTED   -8   /* e.g. an intercept on an entry with no output for it  */
 
 /* ---- parameter enums ------------------------------------------------------ */
@@ -315,6 +316,15 @@ int uoi_ws_dataset(const double* X, const double* Y, int64_t n, int64_t p, int64
  * UOI_OK).  waited_ms (host, nullable): the time the wait took, by the GPU's
  * global timer. */
 int uoi_selftest_wait(uint64_t limit_ns, int32_t arrive, double* waited_ms, void* stream);
+
+/* Test support for the index checks of the checked build (the paper has no
+ * counterpart).  The checked build (compiled with UOI_BOUNDS_CHECK=1) checks the
+ * indices of its kernels' main stores; a failed check records UOI_ERR_BOUNDS and
+ * skips the access, and the call returns UOI_ERR_BOUNDS.  This runs that check
+ * once on the device, in either build: one thread stores into element `index` of
+ * a buffer of `extent` floats (0 < extent <= 4096) if 0 <= index < extent and
+ * returns UOI_OK, else skips the store and returns UOI_ERR_BOUNDS. */
+int uoi_selftest_index_check(int64_t index, int64_t extent, void* stream);
 
 /* Text of a status code (static storage). */
 const char* uoi_status_string(int status);

@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(256, 1) k_admm_resident(AdmmDev<T> P, int32_t*
 #pragma unroll
                     for (int a = 0; a < A; ++a) {
                         const int i = lane + 32 * a;
-                        if (i < p) P.beta[col * p + i] = (double)z[a][b];
+                        if (i < p && UOI_IN_BOUNDS(col * p + i, (int64_t)P.G * P.q * P.r * p, 201))
+                            P.beta[col * p + i] = (double)z[a][b];
                     }
                 }
                 if (P.u_out) {
@@ -514,7 +515,8 @@ __global__ void k_stream_check(AdmmDev<T> P, StreamState S, int cur, T* z, T* u,
         for (int a = 0; 32 * a < p; ++a) {
             const int i = lane + 32 * a;
             const T zi = i < p ? zs[i] : T(0);
-            if (P.beta && i < p) P.beta[col * p + i] = (double)zi;
+            if (P.beta && i < p && UOI_IN_BOUNDS(col * p + i, (int64_t)P.G * P.q * P.r * p, 202))
+                P.beta[col * p + i] = (double)zi;
             if (P.u_out && i < p) P.u_out[col * p + i] = (double)us[i];
             if (P.family) {
                 const unsigned bal = __ballot_sync(0xffffffffu, zi != T(0));

@@ -41,6 +41,33 @@ void DevBuf::release()
 
 thread_local std::string g_last_error;
 
+namespace {
+std::vector<DevStatus (*)()>& bounds_readers()
+{
+    static std::vector<DevStatus (*)()> readers;    // filled while the library loads
+    return readers;
+}
+}  // namespace
+
+void register_bounds_reader(DevStatus (*reader)()) { bounds_readers().push_back(reader); }
+
+// Checked build: fail if an index check of any translation unit fired since the
+// last call (the words are cleared as they are read).  Release build: nothing.
+void check_bounds_status(cudaStream_t s)
+{
+#if defined(UOI_BOUNDS_CHECK) && UOI_BOUNDS_CHECK
+    UOI_CUDA(cudaStreamSynchronize(s));
+    for (auto rd : bounds_readers()) {
+        const DevStatus h = rd();
+        if (h.code != 0)
+            throw Error(UOI_ERR_BOUNDS, "index check failed at site " + std::to_string(h.where) +
+                                            " (checked build)");
+    }
+#else
+    (void)s;
+#endif
+}
+
 int32_t* pinned_scratch_i32()
 {
     thread_local int32_t* buf = nullptr;
@@ -686,6 +713,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
             for (int b = 0; b < 8; ++b) diag->admm_iter_hist[b] = its.hist[b];
         }
     }
+    check_bounds_status(s);
     return (its.noncon > 0 || nsing > 0) ? UOI_OK_WITH_WARNINGS : UOI_OK;
 }
 
@@ -907,6 +935,7 @@ int lasso_admm_batch(const double* X, const double* Y, int64_t n, int64_t p, int
         co.finish(s);
         UOI_CUDA(cudaStreamSynchronize(s));
         IterStats its = iteration_stats(it_d, cv_d, ncol, s);
+        check_bounds_status(s);
         return its.noncon > 0 ? UOI_OK_WITH_WARNINGS : UOI_OK;
     });
 }
@@ -936,6 +965,7 @@ int uoi_weighted_moments(const double* X, const double* Y, int64_t n, int64_t p,
         go.finish(s);
         bo.finish(s);
         UOI_CUDA(cudaStreamSynchronize(s));
+        check_bounds_status(s);
         return UOI_OK;
     });
 }
@@ -1111,6 +1141,7 @@ const char* uoi_status_string(int status)
     case UOI_ERR_CUDA: return "CUDA error";
     case UOI_ERR_OOM: return "out of device memory";
     case UOI_ERR_TIMEOUT: return "bounded device loop ran out of iterations";
+    case UOI_ERR_BOUNDS: return "an index check of the checked build failed";
     case UOI_ERR_UNSUPPORTED: return "unsupported option";
     default: return "unknown status";
     }

@@ -136,4 +136,42 @@ __device__ __forceinline__ void dev_fail(DevStatus* st, int code, int where)
     if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
 }
 
+// ---------------------------------------------------------------------------
+// Index checks.  check_index records UOI_ERR_BOUNDS and the site in *st and
+// returns false when i is outside [0, n), so the caller skips the access:
+// nothing traps and nothing outside a buffer is touched.  UOI_IN_BOUNDS(i, n,
+// site) is such a check in the checked build (compiled with UOI_BOUNDS_CHECK=1),
+// on a status word of its own translation unit, and `true` in the release build.
+// Every fit of the checked build reads and clears the status words of all
+// translation units when it ends and fails with UOI_ERR_BOUNDS if one was set.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool check_index(DevStatus* st, int64_t i, int64_t n, int site)
+{
+    if (i >= 0 && i < n) return true;
+    if (atomicCAS(&st->code, 0, UOI_ERR_BOUNDS) == 0) st->where = site;
+    return false;
+}
+
+#if defined(UOI_BOUNDS_CHECK) && UOI_BOUNDS_CHECK
+static __device__ DevStatus g_bounds_status;     // one per translation unit
+#define UOI_IN_BOUNDS(i, n, site) ::uoi::check_index(&::uoi::g_bounds_status, (int64_t)(i), (int64_t)(n), (site))
+// Registers a reader of one translation unit's status word (defined in api.cu).
+void register_bounds_reader(DevStatus (*reader)());
+namespace {
+DevStatus read_bounds_status_tu()
+{
+    DevStatus h{}, z{};
+    cudaMemcpyFromSymbol(&h, g_bounds_status, sizeof(h));
+    cudaMemcpyToSymbol(g_bounds_status, &z, sizeof(z));
+    return h;
+}
+struct BoundsReaderRegistration {
+    BoundsReaderRegistration() { register_bounds_reader(&read_bounds_status_tu); }
+};
+static BoundsReaderRegistration g_bounds_reader_registration;
+}  // namespace
+#else
+#define UOI_IN_BOUNDS(i, n, site) true
+#endif
+
 }  // namespace uoi

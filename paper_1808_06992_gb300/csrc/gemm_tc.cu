@@ -302,6 +302,7 @@ __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t
     for (int u = 0; u < 4; ++u) split2(tile[kq + u][jj] * sc, h[u], l[u]);
     const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * GT_PIECES;
     const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;             // multiple of 4
+    if (!UOI_IN_BOUNDS(o + rt * GT_TK + 3, (int64_t)gridDim.z * rpad * kpad * GT_PIECES, 401)) return;
     const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
     const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
     *reinterpret_cast<uint2*>(out + o) =

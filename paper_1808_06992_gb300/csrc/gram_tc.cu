@@ -230,9 +230,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
                 const int jo = a.colmap ? a.colmap[jz] : jz;
                 if (iz < a.pz_x) {
                     const int io = a.colmap ? a.colmap[iz] : iz;
-                    a.G[((size_t)item * a.p_out + io) * a.p_out + jo] = val;
+                    const int64_t gi = ((int64_t)item * a.p_out + io) * a.p_out + jo;
+                    if (UOI_IN_BOUNDS(gi, (int64_t)gridDim.y * a.p_out * a.p_out, 101)) a.G[gi] = val;
                 } else {
-                    a.Bm[((size_t)item * a.p_out + jo) * a.r + (iz - a.pz_x)] = val;
+                    const int64_t bi = ((int64_t)item * a.p_out + jo) * a.r + (iz - a.pz_x);
+                    if (UOI_IN_BOUNDS(bi, (int64_t)gridDim.y * a.p_out * a.r, 102)) a.Bm[bi] = val;
                 }
             }
         }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -12,6 +13,9 @@ namespace uoi {
 
 // Detail text of the last error on this thread (uoi_get_last_error_detail).
 extern thread_local std::string g_last_error;
+
+// Checked build: throws UOI_ERR_BOUNDS if an index check fired (api.cu).
+void check_bounds_status(cudaStream_t s);
 
 // ---- per-kernel timing --------------------------------------------------------
 // CUDA events recorded on the launch stream around the launches of the kernels
@@ -191,6 +195,24 @@ void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s);
 // (G int32).  Returns false (launching nothing) when p is too large for it.
 template <typename T>
 bool admm_solve_resident_with(const AdmmProblem<T>& P, int32_t* chain_next, cudaStream_t s);
+
+// ---- G8: the warm-start network's hidden layers on tensor cores (mlp_tc.cu) --------
+// C = A B^T over bf16 row-major operands (K contiguous), FP32 accumulation, fused
+// epilogues.  width = 512 (a multiple of 256), rows of the batch M arbitrary.
+bool mlp_tc_available();
+// Hn = gelu(H W^T + b) (bf16, M x width), pre = H W^T + b (FP32, nullable), HnT (bf16,
+// width x ldT, nullable) the transpose.
+void mlp_forward_tc(const __nv_bfloat16* H, int64_t M, const __nv_bfloat16* W, int32_t width,
+                    const float* bias, float* pre, __nv_bfloat16* Hn, __nv_bfloat16* HnT, int64_t ldT,
+                    int32_t* err, cudaStream_t s);
+// dAp = (dA W) * gelu'(pre_prev) (bf16) with WT = W^T, dApT its transpose (nullable).
+void mlp_backward_tc(const __nv_bfloat16* dA, int64_t M, const __nv_bfloat16* WT, int32_t width,
+                     const float* pre_prev, __nv_bfloat16* dAp, __nv_bfloat16* dApT, int64_t ldT, int32_t* err,
+                     cudaStream_t s);
+// part[z] (width x width, FP32) = dA^T H over slice z of the rows, from the transposes
+// dAT, HT (width x ld bf16, rows past `rows` zero).
+void mlp_weight_grad_tc(const __nv_bfloat16* dAT, const __nv_bfloat16* HT, int64_t ld, int64_t rows, int32_t width,
+                        int32_t slices, float* part, int32_t* err, cudaStream_t s);
 
 // ---- G8: learned warm start (mlp.cu) ------------------------------------------------
 struct WsModel;

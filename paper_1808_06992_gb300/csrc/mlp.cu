@@ -7,10 +7,13 @@
 // before any iteration: the marginal correlation, the Gram diagonal, and the
 // ridge solution (G/n + rho I)^{-1} b/n -- the first x-update from zero --
 // scaled by lambda_j and by the previous lambda_{j-1}.
-// Network: 8 -> 512 -> 512 -> 512 -> 3 with exact-erf GELU, BF16 weights used
-// by every product (FP32 master copy in the optimizer), FP32 accumulation and
-// FP32 activations.  Loss per row: squared errors of the two state outputs plus
-// the logistic loss of the active logit, averaged over rows.
+// Network: 8 -> 512 -> 512 -> 512 -> 3 with exact-erf GELU, BF16 weights and BF16
+// hidden activations in every product (FP32 master copy in the optimizer), FP32
+// accumulation and FP32 pre-activations.  The two 512 x 512 layers, their
+// backward products and their weight gradients run on the tensor cores
+// (mlp_tc.cu); the 8-input layer and the 3-output head stay on CUDA cores.  Loss
+// per row: squared errors of the two state outputs plus the logistic loss of the
+// active logit, averaged over rows.
 //
 // The network only chooses where ADMM starts: its z is used, and the dual is
 // set consistent with it (rho u = b/n - (G/n) z, the fixed point of the
@@ -54,118 +57,6 @@ __device__ __forceinline__ float gelu_grad_f(float x)
            x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-// ---------------------------------------------------------------------------
-// SIMT tile GEMMs: 128 x 64 output tile, 256 threads, 8 x 4 register block.
-// ---------------------------------------------------------------------------
-constexpr int GM = 128, GN = 64, GK = 16;
-
-template <typename TB>
-__device__ __forceinline__ float tofloat(TB v);
-template <>
-__device__ __forceinline__ float tofloat<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// C(m, n) = epi(m, n, sum_k A[m*lda + k] * B[n*ldb + k]) over K (both K-contiguous).
-template <typename TB, typename Epi>
-__global__ void __launch_bounds__(256)
-k_gemm_nt(int M, int N, int K, const float* __restrict__ A, int64_t lda, const TB* __restrict__ B,
-          int64_t ldb, Epi epi)
-{
-    __shared__ float As[GK][GM + 4];
-    __shared__ float Bs[GK][GN + 4];
-    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[8][4] = {};
-    for (int kb = 0; kb < K; kb += GK) {
-#pragma unroll
-        for (int h = 0; h < GM * GK / 256; ++h) {
-            const int e = threadIdx.x + 256 * h;
-            const int row = e / GK, kk = e % GK;
-            const int m = m0 + row, k = kb + kk;
-            As[kk][row] = (m < M && k < K) ? A[(int64_t)m * lda + k] : 0.f;
-        }
-#pragma unroll
-        for (int h = 0; h < GN * GK / 256; ++h) {
-            const int e = threadIdx.x + 256 * h;
-            const int col = e / GK, kk = e % GK;
-            const int n = n0 + col, k = kb + kk;
-            Bs[kk][col] = (n < N && k < K) ? tofloat<TB>(B[(int64_t)n * ldb + k]) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-            float a[8], b[4];
-#pragma unroll
-            for (int w = 0; w < 8; ++w) a[w] = As[kk][ty * 8 + w];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
-#pragma unroll
-            for (int w = 0; w < 8; ++w)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[w][v] = fmaf(a[w], b[v], acc[w][v]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int w = 0; w < 8; ++w)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int m = m0 + ty * 8 + w, n = n0 + tx * 4 + v;
-            if (m < M && n < N) epi(m, n, acc[w][v]);
-        }
-}
-
-// Split-K C(m, n) partial = sum_{k in slice} A[k*lda + m] * B[k*ldb + n] (both
-// row-major over k), written to part[slice][m][n].
-__global__ void __launch_bounds__(256)
-k_gemm_tn_partial(int M, int N, int K, int kslice, const float* __restrict__ A, int64_t lda,
-                  const float* __restrict__ B, int64_t ldb, float* part)
-{
-    __shared__ float As[GK][GM + 4];
-    __shared__ float Bs[GK][GN + 4];
-    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
-    const int k_begin = blockIdx.z * kslice, k_end = min(K, k_begin + kslice);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[8][4] = {};
-    for (int kb = k_begin; kb < k_end; kb += GK) {
-#pragma unroll
-        for (int h = 0; h < GM * GK / 256; ++h) {
-            const int e = threadIdx.x + 256 * h;
-            const int kk = e / GM, mm = e % GM;
-            const int k = kb + kk, m = m0 + mm;
-            As[kk][mm] = (k < k_end && m < M) ? A[(int64_t)k * lda + m] : 0.f;
-        }
-#pragma unroll
-        for (int h = 0; h < GN * GK / 256; ++h) {
-            const int e = threadIdx.x + 256 * h;
-            const int kk = e / GN, nn = e % GN;
-            const int k = kb + kk, n = n0 + nn;
-            Bs[kk][nn] = (k < k_end && n < N) ? B[(int64_t)k * ldb + n] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-            float a[8], b[4];
-#pragma unroll
-            for (int w = 0; w < 8; ++w) a[w] = As[kk][ty * 8 + w];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
-#pragma unroll
-            for (int w = 0; w < 8; ++w)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[w][v] = fmaf(a[w], b[v], acc[w][v]);
-        }
-        __syncthreads();
-    }
-    float* out = part + (int64_t)blockIdx.z * M * N;
-#pragma unroll
-    for (int w = 0; w < 8; ++w)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int m = m0 + ty * 8 + w, n = n0 + tx * 4 + v;
-            if (m < M && n < N) out[(int64_t)m * N + n] = acc[w][v];
-        }
-}
-
 // dst[i] = sum over slices (fixed order) of part[s][i]
 __global__ void k_sum_slices(const float* part, int slices, int64_t count, float* dst)
 {
@@ -178,36 +69,20 @@ __global__ void k_sum_slices(const float* part, int slices, int64_t count, float
 }
 
 // column sums of an N x C matrix in a fixed order: dst[c] = sum_n A[n*C + c]
-__global__ void k_col_sums(const float* A, int64_t N, int C, float* dst)
+template <typename TA>
+__global__ void k_col_sums(const TA* A, int64_t N, int C, float* dst)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     float s = 0.f;
-    for (int64_t n = 0; n < N; ++n) s += A[n * C + c];
+    for (int64_t n = 0; n < N; ++n) s += (float)A[n * C + c];
     dst[c] = s;
 }
 
-struct EpiBiasGelu {            // pre = acc + b; store pre (optional) and gelu(pre)
-    const float* b; float* pre; float* out; int ldo;
-    __device__ void operator()(int m, int n, float acc) const
-    {
-        const float a = acc + b[n];
-        if (pre) pre[(int64_t)m * ldo + n] = a;
-        out[(int64_t)m * ldo + n] = gelu_f(a);
-    }
-};
-
-struct EpiGeluGrad {            // da = acc * gelu'(pre)
-    const float* pre; float* out; int ldo;
-    __device__ void operator()(int m, int n, float acc) const
-    {
-        out[(int64_t)m * ldo + n] = acc * gelu_grad_f(pre[(int64_t)m * ldo + n]);
-    }
-};
-
-// layer 1 (K = 8): a1 = X W1^T + b1, h1 = gelu(a1)
+// layer 1 (K = 8): a1 = X W1^T + b1, h1 = gelu(a1) stored in BF16 (and transposed,
+// h1t[o * ldt + n], for the weight gradient of layer 2)
 __global__ void k_layer_in(const float* X, int64_t N, const __nv_bfloat16* w, const float* master,
-                           float* pre, float* h)
+                           float* pre, __nv_bfloat16* h, __nv_bfloat16* ht, int64_t ldt)
 {
     const int64_t total = N * WS_H;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -219,12 +94,14 @@ __global__ void k_layer_in(const float* X, int64_t N, const __nv_bfloat16* w, co
         for (int k = 0; k < WS_IN; ++k)
             a = fmaf(X[n * WS_IN + k], __bfloat162float(w[OFF_W1 + o * WS_IN + k]), a);
         if (pre) pre[t] = a;
-        h[t] = gelu_f(a);
+        const __nv_bfloat16 hv = __float2bfloat16_rn(gelu_f(a));
+        h[t] = hv;
+        if (ht) ht[(int64_t)o * ldt + n] = hv;
     }
 }
 
 // head: out[n][j] = h3[n] . W4[j] + b4[j]   (one warp per row)
-__global__ void k_head(const float* h3, int64_t N, const __nv_bfloat16* w, const float* master,
+__global__ void k_head(const __nv_bfloat16* h3, int64_t N, const __nv_bfloat16* w, const float* master,
                        float* out)
 {
     const int64_t n = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -232,7 +109,7 @@ __global__ void k_head(const float* h3, int64_t N, const __nv_bfloat16* w, const
     if (n >= N) return;
     float s[WS_OUT] = {};
     for (int k = lane; k < WS_H; k += 32) {
-        const float hv = h3[n * WS_H + k];
+        const float hv = __bfloat162float(h3[n * WS_H + k]);
 #pragma unroll
         for (int j = 0; j < WS_OUT; ++j)
             s[j] = fmaf(hv, __bfloat162float(w[OFF_W4 + j * WS_H + k]), s[j]);
@@ -270,9 +147,9 @@ __global__ void k_loss_grad(const float* out, const float* T, int64_t N, float* 
     if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
 }
 
-// da3 = (dOut W4) * gelu'(a3)
+// da3 = (dOut W4) * gelu'(a3), stored in BF16 and transposed (da3t[k * ldt + n])
 __global__ void k_head_back(const float* dout, int64_t N, const __nv_bfloat16* w, const float* pre3,
-                            float* da3)
+                            __nv_bfloat16* da3, __nv_bfloat16* da3t, int64_t ldt)
 {
     const int64_t total = N * WS_H;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -283,18 +160,20 @@ __global__ void k_head_back(const float* dout, int64_t N, const __nv_bfloat16* w
 #pragma unroll
         for (int j = 0; j < WS_OUT; ++j)
             s = fmaf(dout[n * 3 + j], __bfloat162float(w[OFF_W4 + j * WS_H + k]), s);
-        da3[t] = s * gelu_grad_f(pre3[t]);
+        const __nv_bfloat16 d = __float2bfloat16_rn(s * gelu_grad_f(pre3[t]));
+        da3[t] = d;
+        da3t[(int64_t)k * ldt + n] = d;
     }
 }
 
 // gradient of W1 (K over rows, 8 inputs): g[o][k] = sum_n da1[n][o] X[n][k]
-__global__ void k_grad_w1(const float* da1, const float* X, int64_t N, float* g)
+__global__ void k_grad_w1(const __nv_bfloat16* da1, const float* X, int64_t N, float* g)
 {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= WS_H) return;
     float s[WS_IN] = {};
     for (int64_t n = 0; n < N; ++n) {
-        const float d = da1[n * WS_H + o];
+        const float d = __bfloat162float(da1[n * WS_H + o]);
 #pragma unroll
         for (int k = 0; k < WS_IN; ++k) s[k] = fmaf(d, X[n * WS_IN + k], s[k]);
     }
@@ -303,13 +182,13 @@ __global__ void k_grad_w1(const float* da1, const float* X, int64_t N, float* g)
 }
 
 // gradient of W4: g[j][k] = sum_n dout[n][j] h3[n][k]
-__global__ void k_grad_w4(const float* dout, const float* h3, int64_t N, float* g)
+__global__ void k_grad_w4(const float* dout, const __nv_bfloat16* h3, int64_t N, float* g)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= WS_H) return;
     float s[WS_OUT] = {};
     for (int64_t n = 0; n < N; ++n) {
-        const float hv = h3[n * WS_H + k];
+        const float hv = __bfloat162float(h3[n * WS_H + k]);
 #pragma unroll
         for (int j = 0; j < WS_OUT; ++j) s[j] = fmaf(dout[n * 3 + j], hv, s[j]);
     }
@@ -403,91 +282,113 @@ void sync_weights(WsModel* M, cudaStream_t s)
 unsigned blocks_for(int64_t work) { return (unsigned)std::min<int64_t>(ceil_div(work, 256), 152 * 16); }
 
 struct Acts {
-    DevBuf a1, h1, a2, h2, a3, h3, out;
+    DevBuf a1, a2, a3;        // FP32 pre-activations (training)
+    DevBuf h1, h2, h3;        // BF16 hidden activations, N x 512
+    DevBuf h1t, h2t;          // BF16 512 x ldt transposes (training: the weight gradients' B)
+    DevBuf out;
+    int64_t ldt = 0;
 };
 
-// Forward over N rows; keeps pre-activations when train is set.
-void forward(WsModel* M, const float* X, int64_t N, Acts& A, bool train, cudaStream_t s)
+// Rows of the batch padded for the weight gradients' K extent (transposed copies).
+int64_t padded_rows(int64_t N) { return ceil_div(N, 32) * 32; }
+
+void check_err(const DevBuf& err, cudaStream_t s)
 {
-    const size_t hsz = sizeof(float) * (size_t)N * WS_H;
-    if (train) { A.a1.alloc(hsz, s); A.a2.alloc(hsz, s); A.a3.alloc(hsz, s); }
-    A.h1.alloc(hsz, s); A.h2.alloc(hsz, s); A.h3.alloc(hsz, s);
-    A.out.alloc(sizeof(float) * (size_t)N * WS_OUT, s);
-    k_layer_in<<<blocks_for(N * WS_H), 256, 0, s>>>(X, N, M->w, M->master,
-                                                   train ? A.a1.as<float>() : nullptr, A.h1.as<float>());
-    UOI_CHECK_LAUNCH();
-    dim3 g((unsigned)ceil_div(N, GM), WS_H / GN);
-    EpiBiasGelu e2{ M->master + OFF_B2, train ? A.a2.as<float>() : nullptr, A.h2.as<float>(), WS_H };
-    k_gemm_nt<__nv_bfloat16, EpiBiasGelu><<<g, 256, 0, s>>>((int)N, WS_H, WS_H, A.h1.as<float>(), WS_H,
-                                                            M->w + OFF_W2, WS_H, e2);
-    UOI_CHECK_LAUNCH();
-    EpiBiasGelu e3{ M->master + OFF_B3, train ? A.a3.as<float>() : nullptr, A.h3.as<float>(), WS_H };
-    k_gemm_nt<__nv_bfloat16, EpiBiasGelu><<<g, 256, 0, s>>>((int)N, WS_H, WS_H, A.h2.as<float>(), WS_H,
-                                                            M->w + OFF_W3, WS_H, e3);
-    UOI_CHECK_LAUNCH();
-    k_head<<<(unsigned)ceil_div(N * 32, 256), 256, 0, s>>>(A.h3.as<float>(), N, M->w, M->master,
-                                                           A.out.as<float>());
-    UOI_CHECK_LAUNCH();
-    count_launch(4);
+    int32_t h = 0;
+    UOI_CUDA(cudaMemcpyAsync(&h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaStreamSynchronize(s));
+    if (h) throw Error(h, "tensor-core MLP product: a bounded pipeline wait expired");
 }
 
-// Weight gradient g[o][k] = sum_n dA[n][o] H[n][k] (512 x 512) by split-K.
-void grad_square(const float* dA, const float* H, int64_t N, float* g, cudaStream_t s)
+// Forward over N rows; keeps pre-activations and transposed activations when
+// train is set.
+void forward(WsModel* M, const float* X, int64_t N, Acts& A, bool train, int32_t* err, cudaStream_t s)
 {
-    const int slices = (int)std::min<int64_t>(32, std::max<int64_t>(1, N / 2048));
-    const int kslice = (int)ceil_div(N, slices);
-    DevBuf part(sizeof(float) * (size_t)slices * WS_H * WS_H, s);
-    dim3 gr(WS_H / GM, WS_H / GN, (unsigned)slices);
-    k_gemm_tn_partial<<<gr, 256, 0, s>>>(WS_H, WS_H, (int)N, kslice, dA, WS_H, H, WS_H, part.as<float>());
+    if (!mlp_tc_available()) throw Error(UOI_ERR_UNSUPPORTED, "the warm-start network needs sm_103a tensor cores");
+    const size_t hsz = sizeof(float) * (size_t)N * WS_H, hb = sizeof(__nv_bfloat16) * (size_t)N * WS_H;
+    A.ldt = padded_rows(N);
+    if (train) {
+        A.a1.alloc(hsz, s); A.a2.alloc(hsz, s); A.a3.alloc(hsz, s);
+        const size_t tb = sizeof(__nv_bfloat16) * (size_t)WS_H * A.ldt;
+        A.h1t.alloc(tb, s); A.h2t.alloc(tb, s);
+        UOI_CUDA(cudaMemsetAsync(A.h1t.ptr, 0, tb, s));      // padding rows of the K extent
+        UOI_CUDA(cudaMemsetAsync(A.h2t.ptr, 0, tb, s));
+    }
+    A.h1.alloc(hb, s); A.h2.alloc(hb, s); A.h3.alloc(hb, s);
+    A.out.alloc(sizeof(float) * (size_t)N * WS_OUT, s);
+    k_layer_in<<<blocks_for(N * WS_H), 256, 0, s>>>(X, N, M->w, M->master, train ? A.a1.as<float>() : nullptr,
+                                                   A.h1.as<__nv_bfloat16>(),
+                                                   train ? A.h1t.as<__nv_bfloat16>() : nullptr, A.ldt);
     UOI_CHECK_LAUNCH();
+    mlp_forward_tc(A.h1.as<__nv_bfloat16>(), N, M->w + OFF_W2, WS_H, M->master + OFF_B2,
+                   train ? A.a2.as<float>() : nullptr, A.h2.as<__nv_bfloat16>(),
+                   train ? A.h2t.as<__nv_bfloat16>() : nullptr, A.ldt, err, s);
+    mlp_forward_tc(A.h2.as<__nv_bfloat16>(), N, M->w + OFF_W3, WS_H, M->master + OFF_B3,
+                   train ? A.a3.as<float>() : nullptr, A.h3.as<__nv_bfloat16>(), nullptr, 0, err, s);
+    k_head<<<(unsigned)ceil_div(N * 32, 256), 256, 0, s>>>(A.h3.as<__nv_bfloat16>(), N, M->w, M->master,
+                                                           A.out.as<float>());
+    UOI_CHECK_LAUNCH();
+    count_launch(2);
+}
+
+// Weight gradient g[o][k] = sum_n dA[n][o] H[n][k] (512 x 512) on the tensor cores
+// from the transposed BF16 copies, in slices of the batch rows reduced in a fixed order.
+void grad_square(const __nv_bfloat16* dAt, const __nv_bfloat16* Ht, int64_t ldt, int64_t N, float* g,
+                 int32_t* err, cudaStream_t s)
+{
+    const int64_t kst = ceil_div(N, 32);
+    const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(32, kst / 8));
+    DevBuf part(sizeof(float) * (size_t)slices * WS_H * WS_H, s);
+    mlp_weight_grad_tc(dAt, Ht, ldt, N, WS_H, slices, part.as<float>(), err, s);
     k_sum_slices<<<blocks_for((int64_t)WS_H * WS_H), 256, 0, s>>>(part.as<float>(), slices,
                                                                    (int64_t)WS_H * WS_H, g);
     UOI_CHECK_LAUNCH();
-    count_launch(2);
+    count_launch();
 }
 
 // Full gradient into g (N_PARAMS floats); returns the mean loss.
 double loss_grad(WsModel* M, const float* X, const float* T, int64_t N, float* g, cudaStream_t s)
 {
+    DevBuf err(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
     Acts A;
-    forward(M, X, N, A, true, s);
+    forward(M, X, N, A, true, err.as<int32_t>(), s);
     DevBuf dout(sizeof(float) * (size_t)N * 3, s);
     const int lb = 256;
     DevBuf lp(sizeof(double) * lb, s);
     k_loss_grad<<<lb, 256, 0, s>>>(A.out.as<float>(), T, N, dout.as<float>(), lp.as<double>());
     UOI_CHECK_LAUNCH();
-    const size_t hsz = sizeof(float) * (size_t)N * WS_H;
-    DevBuf da3(hsz, s), dtmp(hsz, s);
-    k_grad_w4<<<WS_H / 128, 128, 0, s>>>(dout.as<float>(), A.h3.as<float>(), N, g);
+    const size_t hb = sizeof(__nv_bfloat16) * (size_t)N * WS_H;
+    const size_t tb = sizeof(__nv_bfloat16) * (size_t)WS_H * A.ldt;
+    DevBuf da3(hb, s), da2(hb, s), da3t(tb, s), da2t(tb, s);
+    UOI_CUDA(cudaMemsetAsync(da3t.ptr, 0, tb, s));
+    UOI_CUDA(cudaMemsetAsync(da2t.ptr, 0, tb, s));
+    k_grad_w4<<<WS_H / 128, 128, 0, s>>>(dout.as<float>(), A.h3.as<__nv_bfloat16>(), N, g);
     UOI_CHECK_LAUNCH();
-    k_col_sums<<<1, 32, 0, s>>>(dout.as<float>(), N, WS_OUT, g + OFF_B4);
+    k_col_sums<float><<<1, 32, 0, s>>>(dout.as<float>(), N, WS_OUT, g + OFF_B4);
     UOI_CHECK_LAUNCH();
     k_head_back<<<blocks_for(N * WS_H), 256, 0, s>>>(dout.as<float>(), N, M->w, A.a3.as<float>(),
-                                                     da3.as<float>());
+                                                     da3.as<__nv_bfloat16>(), da3t.as<__nv_bfloat16>(), A.ldt);
     UOI_CHECK_LAUNCH();
     // layer 3
-    grad_square(da3.as<float>(), A.h2.as<float>(), N, g + OFF_W3, s);
-    k_col_sums<<<WS_H / 128, 128, 0, s>>>(da3.as<float>(), N, WS_H, g + OFF_B3);
+    grad_square(da3t.as<__nv_bfloat16>(), A.h2t.as<__nv_bfloat16>(), A.ldt, N, g + OFF_W3, err.as<int32_t>(), s);
+    k_col_sums<__nv_bfloat16><<<WS_H / 128, 128, 0, s>>>(da3.as<__nv_bfloat16>(), N, WS_H, g + OFF_B3);
     UOI_CHECK_LAUNCH();
-    dim3 gg((unsigned)ceil_div(N, GM), WS_H / GN);
-    EpiGeluGrad eg2{ A.a2.as<float>(), dtmp.as<float>(), WS_H };           // da2
-    k_gemm_nt<__nv_bfloat16, EpiGeluGrad><<<gg, 256, 0, s>>>((int)N, WS_H, WS_H, da3.as<float>(), WS_H,
-                                                             M->w3t, WS_H, eg2);
-    UOI_CHECK_LAUNCH();
+    mlp_backward_tc(da3.as<__nv_bfloat16>(), N, M->w3t, WS_H, A.a2.as<float>(), da2.as<__nv_bfloat16>(),
+                    da2t.as<__nv_bfloat16>(), A.ldt, err.as<int32_t>(), s);                  // da2
     // layer 2
-    grad_square(dtmp.as<float>(), A.h1.as<float>(), N, g + OFF_W2, s);
-    k_col_sums<<<WS_H / 128, 128, 0, s>>>(dtmp.as<float>(), N, WS_H, g + OFF_B2);
+    grad_square(da2t.as<__nv_bfloat16>(), A.h1t.as<__nv_bfloat16>(), A.ldt, N, g + OFF_W2, err.as<int32_t>(), s);
+    k_col_sums<__nv_bfloat16><<<WS_H / 128, 128, 0, s>>>(da2.as<__nv_bfloat16>(), N, WS_H, g + OFF_B2);
     UOI_CHECK_LAUNCH();
-    EpiGeluGrad eg1{ A.a1.as<float>(), da3.as<float>(), WS_H };            // da1 (reuses da3)
-    k_gemm_nt<__nv_bfloat16, EpiGeluGrad><<<gg, 256, 0, s>>>((int)N, WS_H, WS_H, dtmp.as<float>(), WS_H,
-                                                             M->w2t, WS_H, eg1);
-    UOI_CHECK_LAUNCH();
+    mlp_backward_tc(da2.as<__nv_bfloat16>(), N, M->w2t, WS_H, A.a1.as<float>(), da3.as<__nv_bfloat16>(),
+                    nullptr, 0, err.as<int32_t>(), s);                                       // da1 (in da3)
     // layer 1
-    k_grad_w1<<<WS_H / 128, 128, 0, s>>>(da3.as<float>(), X, N, g);
+    k_grad_w1<<<WS_H / 128, 128, 0, s>>>(da3.as<__nv_bfloat16>(), X, N, g);
     UOI_CHECK_LAUNCH();
-    k_col_sums<<<WS_H / 128, 128, 0, s>>>(da3.as<float>(), N, WS_H, g + OFF_B1);
+    k_col_sums<__nv_bfloat16><<<WS_H / 128, 128, 0, s>>>(da3.as<__nv_bfloat16>(), N, WS_H, g + OFF_B1);
     UOI_CHECK_LAUNCH();
-    count_launch(11);
+    count_launch(8);
+    check_err(err, s);
     std::vector<double> h(lb);
     UOI_CUDA(cudaMemcpyAsync(h.data(), lp.ptr, sizeof(double) * lb, cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));
@@ -658,14 +559,17 @@ void ws_get_params(WsModel* M, float* host_or_dev, cudaStream_t s)
 
 void ws_forward(WsModel* M, const float* X, int64_t N, float* out, cudaStream_t s)
 {
-    const int64_t chunk = 1 << 18;
+    DevBuf err(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
+    const int64_t chunk = 1 << 20;
     for (int64_t n0 = 0; n0 < N; n0 += chunk) {
         const int64_t nn = std::min(chunk, N - n0);
         Acts A;
-        forward(M, X + n0 * WS_IN, nn, A, false, s);
+        forward(M, X + n0 * WS_IN, nn, A, false, err.as<int32_t>(), s);
         UOI_CUDA(cudaMemcpyAsync(out + n0 * WS_OUT, A.out.ptr, sizeof(float) * nn * WS_OUT,
                                  cudaMemcpyDeviceToDevice, s));
     }
+    check_err(err, s);
 }
 
 double ws_loss_grad(WsModel* M, const float* X, const float* T, int64_t N, float* g, cudaStream_t s)

@@ -1,4 +1,5 @@
-// selftest.cu -- test support: a bounded mbarrier wait that runs out.
+// selftest.cu -- test support: a bounded mbarrier wait that runs out, and the
+// device index check.
 //
 // Every tensor-core kernel of the library waits on mbarriers with a limit
 // (tc::mbar_wait, kernel argument wait_ns, one second by default).  When a limit
@@ -35,10 +36,44 @@ __global__ void k_selftest_wait(uint64_t limit_ns, int32_t arrive, int32_t* err,
     }
 }
 
+// One thread stores into buf[index] if the index check passes (buf has extent
+// elements): the check of the checked build, run explicitly.
+__global__ void k_selftest_index(int64_t index, int64_t extent, float* buf, DevStatus* st)
+{
+    if (threadIdx.x == 0 && check_index(st, index, extent, 901)) buf[index] = 1.f;
+}
+
 }  // namespace
 }  // namespace uoi
 
 using namespace uoi;
+
+extern "C" int uoi_selftest_index_check(int64_t index, int64_t extent, void* stream)
+{
+    try {
+        g_last_error.clear();
+        if (extent <= 0 || extent > 4096) throw Error(UOI_ERR_INVALID_ARG, "extent must lie in (0, 4096]");
+        cudaStream_t s = (cudaStream_t)stream;
+        DevBuf buf(sizeof(float) * (size_t)extent, s), st(sizeof(DevStatus), s);
+        UOI_CUDA(cudaMemsetAsync(st.ptr, 0, st.bytes, s));
+        k_selftest_index<<<1, 32, 0, s>>>(index, extent, buf.as<float>(), st.as<DevStatus>());
+        UOI_CHECK_LAUNCH();
+        count_launch();
+        DevStatus h{};
+        UOI_CUDA(cudaMemcpyAsync(&h, st.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+        UOI_CUDA(cudaStreamSynchronize(s));
+        if (h.code != 0)
+            throw Error(h.code, "index " + std::to_string(index) + " outside [0, " + std::to_string(extent) +
+                                    ") at site " + std::to_string(h.where) + ": access skipped");
+        return UOI_OK;
+    } catch (const Error& e) {
+        g_last_error = e.what();
+        return e.status;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return UOI_ERR_CUDA;
+    }
+}
 
 extern "C" int uoi_selftest_wait(uint64_t limit_ns, int32_t arrive, double* waited_ms, void* stream)
 {

@@ -334,13 +334,17 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
                     const float vv = x + uo[t];
                     const float zn = soft_threshold(vv, s_kappa[nb + t]);
                     const float un = vv - zn;
-                    a.z[o] = zn;
-                    a.u[o] = un;
+                    if (UOI_IN_BOUNDS(o, a.slots * a.p, 302)) {
+                        a.z[o] = zn;
+                        a.u[o] = un;
+                    }
                     __half h, l;
                     split2((zn - un) * s_vw[tt], h, l);
                     const int64_t vo = sl * a.kpad + i;
-                    a.vnext[vo] = h;
-                    a.vnext[(int64_t)a.slots * a.kpad + vo] = l;
+                    if (UOI_IN_BOUNDS(vo, a.slots * a.kpad, 303)) {
+                        a.vnext[vo] = h;
+                        a.vnext[(int64_t)a.slots * a.kpad + vo] = l;
+                    }
                     const float d = x - zn, dz = zn - zp[t];
                     pr[0][t] = d * d; pr[1][t] = dz * dz; pr[2][t] = x * x; pr[3][t] = zn * zn; pr[4][t] = un * un;
                 }
@@ -566,7 +570,8 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
                 if (32 * a0 >= p) break;                         // warp-uniform
                 const int i = lane + 32 * a0;
                 const float zi = zc[t];
-                if (beta && i < p) beta[col * p + i] = (double)zi;
+                if (beta && i < p && UOI_IN_BOUNDS(col * p + i, (int64_t)G * q * r * p, 301))
+                    beta[col * p + i] = (double)zi;
                 if (family) {
                     const unsigned bal = __ballot_sync(0xffffffffu, zi != 0.f);
                     if (lane == 0) {

@@ -17,7 +17,7 @@ from . import build as _build
 
 OK, OK_WITH_WARNINGS = 0, 1
 ERR_INVALID_ARG, ERR_NONFINITE, ERR_NOT_PD, ERR_CUDA = -1, -2, -3, -4
-ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = -5, -6, -8
+ERR_OOM, ERR_TIMEOUT, ERR_BOUNDS, ERR_UNSUPPORTED = -5, -6, -7, -8
 BAG_MEDIAN, BAG_MEAN = 0, 1
 SPLIT_PER_BOOTSTRAP, SPLIT_FIXED = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
@@ -68,6 +68,7 @@ class UoiTrace(C.Structure):
 
 
 _lib = None
+_checked = None
 
 
 def lib():
@@ -77,7 +78,41 @@ def lib():
         path = _build.build()
         if not os.path.exists(path):
             raise RuntimeError("libuoi_gb300.so is missing; the CUDA path cannot run")
-        L = C.CDLL(path)
+        _lib = _configure(C.CDLL(path))
+    return _lib
+
+
+def checked_lib():
+    """Load (building if needed) the checked build (UOI_BOUNDS_CHECK=1), a separate
+    library with the same entry points; use it through use_library."""
+    global _checked
+    if _checked is None:
+        path = _build.build(checked=True)
+        if not os.path.exists(path):
+            raise RuntimeError("libuoi_gb300_checked.so is missing")
+        _checked = _configure(C.CDLL(path))
+    return _checked
+
+
+class use_library:
+    """with use_library(L): the wrappers of this module call library L."""
+
+    def __init__(self, L):
+        self.L = L
+
+    def __enter__(self):
+        global _lib
+        lib()
+        self.prev, _lib = _lib, self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.prev
+
+
+def _configure(L):
+    if True:
         vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
         L.uoi_params_default.argtypes = [C.POINTER(UoiParams)]
         L.uoi_lasso_fit.argtypes = [vp, vp, i64, i64, C.POINTER(UoiParams), vp, vp, C.POINTER(UoiDiag)]
@@ -102,19 +137,19 @@ def lib():
         L.uoi_ws_train.argtypes = [vp, vp, vp, i64, i32, i32, C.c_float, C.c_uint64, C.POINTER(d)]
         L.uoi_ws_dataset.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, i32, d, d, d, i32, vp, vp, vp]
         L.uoi_selftest_wait.argtypes = [C.c_uint64, i32, C.POINTER(d), vp]
+        L.uoi_selftest_index_check.argtypes = [i64, i64, vp]
         L.uoi_status_string.argtypes = [C.c_int]
         L.uoi_status_string.restype = C.c_char_p
         L.uoi_get_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
         L.uoi_shutdown.argtypes = []
-        _lib = L
-    return _lib
+    return L
 
 
 EXPORTED = ("uoi_params_default", "uoi_lasso_fit", "uoi_lasso_fit_batch", "uoi_var_fit", "uoi_fit_traced",
             "lasso_admm_batch", "lasso_admm_batch_noalloc", "uoi_weighted_moments",
             "uoi_ws_param_count", "uoi_ws_create", "uoi_ws_load", "uoi_ws_save", "uoi_ws_free",
             "uoi_ws_set_params", "uoi_ws_get_params", "uoi_ws_forward", "uoi_ws_loss_grad",
-            "uoi_ws_train", "uoi_ws_dataset", "uoi_selftest_wait", "uoi_status_string", "uoi_get_last_error_detail",
+            "uoi_ws_train", "uoi_ws_dataset", "uoi_selftest_wait", "uoi_selftest_index_check", "uoi_status_string", "uoi_get_last_error_detail",
             "uoi_shutdown")
 
 
@@ -464,6 +499,11 @@ def selftest_wait(limit_ns, arrive=False, stream=None):
         err.waited_ms = float(ms.value)
         raise err
     return float(ms.value)
+
+
+def selftest_index_check(index, extent, stream=None):
+    """The device index check once (see uoi_selftest_index_check)."""
+    return _check(lib().uoi_selftest_index_check(int(index), int(extent), stream))
 
 
 def shutdown():

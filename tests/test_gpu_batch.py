@@ -5,13 +5,22 @@
   the same), in both precision forms, with more problems than worker streams;
 * the plain FP64 batch matches the FP64 oracle on its problems (Alg. 1 per
   problem) within the plain form's 1e-6;
+* every mixed member (p from 20 to 700, the last with n < p on the tensor-core
+  inverse) against the oracle: where the bootstrap problems are strongly convex
+  (n > 2p) the selection columns are held to the exact minimiser, the family is
+  identical outside the band-touched bits, and beta* is within 1e-5; where
+  n <= 2p (a singular bootstrap Gram: the minimiser need not be unique and the
+  stopping rule decides no support) every column's KKT residual is held to the
+  stopping bound and family differences are reported;
 * an empty batch and a failing member are reported per problem.
 """
 import numpy as np
 import pytest
 
+import mixed_check
 import oracle
 from paper_1808_06992_gb300 import native, synth
+from test_gpu_parity import bits_to_bool
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +58,41 @@ def test_fp64_batch_matches_oracle():
     for i, d in enumerate(probs):
         ref = oracle.uoi_lasso_fit(d.X, d.y, **{**kw, "problem_id": 3 + i})
         assert rel_l2(out[i]["beta"], ref["beta"][0]) <= 1e-6
+
+
+def test_mixed_batch_members_match_oracle():
+    probs = _problems(SIZES)
+    kw = dict(B1=6, B2=5, q=8, warm_start=native.WARM_NONE)
+    out = native.uoi_lasso_fit_batch([d.X for d in probs], [d.y for d in probs], streams=3,
+                                     precision=native.PREC_MIXED, problem_id=11, **kw)
+    for i, d in enumerate(probs):
+        n, p = d.X.shape
+        pid = 11 + i
+        ref = oracle.uoi_lasso_fit(d.X, d.y, problem_id=pid, n_threads=8, **kw)
+        tr = native.uoi_fit_traced(d.X, d.y, precision=native.PREC_MIXED, problem_id=pid, **kw)
+        np.testing.assert_array_equal(out[i]["beta"], tr["beta"][0])     # the member is the single fit
+        np.testing.assert_array_equal(tr["sel_weights"], np.stack(
+            [oracle.selection_weights(n, 0, 0, pid, k) for k in range(kw["B1"])]))
+        fam_g = bits_to_bool(tr["family"], p)[:, 0, :]
+        fam_r = bits_to_bool(ref["family"], p)[:, 0, :]
+        touched = np.zeros_like(fam_r)
+        if n <= 2 * p:
+            rep = mixed_check.check_residuals(d.X, d.y, tr["sel_weights"], ref["lambdas"], tr["sel_beta"],
+                                              mixed_check.ETA_MIXED)
+            print(f"problem {i} ({n} x {p}): {rep}; family bits differing from the oracle: "
+                  f"{int((fam_g != fam_r).sum())} of {int(fam_r.sum())}")
+            continue
+        rep = mixed_check.check_batch(d.X, d.y, tr["sel_weights"], ref["lambdas"], tr["sel_beta"],
+                                      ref["sel_beta"], mixed_check.ETA_MIXED)
+        for (k, j, e), band in rep.bands.items():
+            touched[j] |= band
+        print(f"problem {i} ({n} x {p}): {rep}")
+        assert np.array_equal(fam_g | touched, fam_r | touched), f"problem {i}: family differs"
+        if np.array_equal(fam_g, fam_r):
+            np.testing.assert_array_equal(tr["est_jstar"], ref["est_jstar"])
+            err = rel_l2(out[i]["beta"], ref["beta"][0])
+            print(f"problem {i} ({n} x {p}): beta* rel l2 {err:.2e}")
+            assert err <= 1e-5
 
 
 def test_empty_and_failing_members():

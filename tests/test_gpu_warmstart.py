@@ -1,8 +1,11 @@
 """Learned warm start (GPU): kernels vs the FP64 reference, training, gain, judge.
 
-* forward and loss gradient of the CUDA network vs oracle/mlp.py (FP64) on
-  BF16-representable weights: the GPU keeps FP32 activations, so both agree to
-  FP32 rounding (bound 1e-4 relative);
+* forward and loss gradient of the CUDA network (hidden layers on tcgen05 with
+  BF16 weights and activations) vs oracle/mlp.py (FP64) on BF16-representable
+  weights, with the reference rounding its hidden activations and
+  back-propagated gradients to BF16 where the GPU stores them: both then agree
+  to the FP32 accumulation and the rare BF16 rounding that FP32 and FP64 values
+  decide differently (bound 5e-4 relative);
 * training on rows from the method's own path-warm ADMM solutions (problems
   with seeds disjoint from the test problem) lowers the loss;
 * on the test problem the learned start needs fewer ADMM iterations than the
@@ -45,17 +48,19 @@ def test_forward_and_gradient_match_fp64_reference():
     m.set_params(params)
     X, T = _batch(300, 11)
     P = mlp.unflatten(params.astype(np.float64))
-    ref, _ = mlp.forward(P, X.astype(np.float64))
+    ref, _ = mlp.forward(P, X.astype(np.float64), round_act=mlp.bf16_round)
     out = m.forward(X)
-    assert rel_l2(out.astype(np.float64), ref) <= 1e-4
+    assert rel_l2(out.astype(np.float64), ref) <= 5e-4
     L, g = m.loss_grad(X, T)
-    Lr, gr = mlp.loss_and_grad(P, X.astype(np.float64), T.astype(np.float64))
-    assert abs(L - Lr) <= 1e-5 * abs(Lr)
+    Lr, gr = mlp.loss_and_grad(P, X.astype(np.float64), T.astype(np.float64), round_act=mlp.bf16_round)
+    assert abs(L - Lr) <= 5e-5 * abs(Lr)
     flat = mlp.flatten(gr)
     o = 0
     for sh in mlp.shapes():
         n = int(np.prod(sh))
-        assert rel_l2(g[o:o + n].astype(np.float64), flat[o:o + n]) <= 1e-4, sh
+        err = rel_l2(g[o:o + n].astype(np.float64), flat[o:o + n])
+        print(sh, f"{err:.2e}")
+        assert err <= 5e-4, sh
         o += n
 
 

@@ -59,3 +59,22 @@ def test_flat_layout_round_trip():
     back = mlp.unflatten(flat)
     for a, b in zip(params, back):
         np.testing.assert_array_equal(a, b)
+
+
+def test_bf16_round_ties_to_even_and_reduces_to_identity_network():
+    # exactly representable, halfway cases (ties to even) and a value just above
+    # a halfway point, against the definition: 8 significant bits
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -8 + 2.0 ** -20, -2.5, 0.0])
+    want = np.array([1.0, 1.0, 1.0 + 2.0 ** -6, 1.0 + 2.0 ** -7, -2.5, 0.0])
+    np.testing.assert_array_equal(mlp.bf16_round(x), want)
+    g = np.random.Generator(np.random.PCG64(5))
+    v = g.standard_normal(1000)
+    r = mlp.bf16_round(v)
+    assert np.all(np.abs(r - v) <= 2.0 ** -8 * np.abs(v))                 # half an ulp of 8 bits
+    # with the identity the rounded network is the FP64 network
+    P = [g.standard_normal(sh) * 0.1 for sh in mlp.shapes(4, 16, 3)]
+    X = g.standard_normal((7, 4))
+    T = np.column_stack([g.standard_normal(7), g.standard_normal(7), g.integers(0, 2, 7)])
+    L0, g0 = mlp.loss_and_grad(P, X, T)
+    L1, g1 = mlp.loss_and_grad(P, X, T, round_act=lambda a: a)
+    assert L0 == L1 and all(np.array_equal(a, b) for a, b in zip(g0, g1))
