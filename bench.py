@@ -38,7 +38,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--warm", default="none", choices=["none", "path"])
+    ap.add_argument("--warm", default="none", choices=["none", "path", "learned"],
+                    help="ADMM start: cold lambda batch, path warm start, or the learned start (a network "
+                         "trained first, outside the timed region, on problems with disjoint seeds)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed fits of the plain FP64 GPU form on the same inputs (mixed runs only; "
@@ -141,12 +143,38 @@ def workload(wid, order=1):
 def fit_kwargs(w, args):
     from paper_1808_06992_gb300 import native
     bag = w.bagging if args.bagging is None else (1 if args.bagging == "mean" else 0)
-    return dict(B1=args.B1 or w.B1, B2=args.B2 or w.B2, q=args.q or w.q, block_len=w.block_len,
-                bagging=bag, block_mode=1 if args.block_mode == "moving" else 0,
-                split_mode=native.SPLIT_FIXED if args.split == "fixed" else native.SPLIT_PER_BOOTSTRAP,
-                precision=native.PREC_MIXED if args.precision == "mixed" else native.PREC_FP64,
-                warm_start=native.WARM_PATH if args.warm == "path" else native.WARM_NONE,
-                intercept=args.intercept if w.kind == "var" else 0)
+    warm = {"none": native.WARM_NONE, "path": native.WARM_PATH, "learned": native.WARM_LEARNED}[args.warm]
+    kw = dict(B1=args.B1 or w.B1, B2=args.B2 or w.B2, q=args.q or w.q, block_len=w.block_len,
+              bagging=bag, block_mode=1 if args.block_mode == "moving" else 0,
+              split_mode=native.SPLIT_FIXED if args.split == "fixed" else native.SPLIT_PER_BOOTSTRAP,
+              precision=native.PREC_MIXED if args.precision == "mixed" else native.PREC_FP64,
+              warm_start=warm, intercept=args.intercept if w.kind == "var" else 0)
+    if args.warm == "learned":
+        kw["mlp_weights_path"] = args.mlp_weights
+    return kw
+
+
+def train_warm_start(w, args):
+    """Trains the learned start's network before the timed region on rows from the
+    method's own path-warm solutions of problems shaped like the workload (seeds
+    disjoint from the workload's); returns a description for the bench line."""
+    import tempfile
+
+    from paper_1808_06992_gb300 import warm_start
+    t0 = time.time()
+    args.mlp_weights = os.path.join(tempfile.mkdtemp(prefix="uoi_ws_"), "ws.bin")
+    prm = w.params
+    if w.kind == "var":
+        p = min(int(prm["p"]), 200)
+        F, T = warm_start.var_training_rows(p, 2000, max(prm["density"], 0.05), prm["spectral_radius"],
+                                            w.block_len, args.q or w.q)
+        what = f"VAR(1) p={p}, 2 series"
+    else:
+        F, T = warm_start.lasso_training_rows(200, 50, 10, args.q or w.q)
+        what = "24 LASSO problems 200 x 50"
+    L0, L1 = warm_start.train(F, T, args.mlp_weights)
+    return {"rows": int(F.shape[0]), "problems": what, "loss_initial": L0, "loss_final": L1,
+            "seconds": time.time() - t0}
 
 
 def traffic_per_launch(kernel, applies=True):
@@ -334,6 +362,7 @@ def main():
         X, Y = np.ascontiguousarray(X[:args.rows]), np.ascontiguousarray(Y[:args.rows])
     m, p = X.shape
     r = Y.shape[1]
+    ws_train = train_warm_start(w, args) if args.warm == "learned" else None
     kw = fit_kwargs(w, args)
     overrides = {k: getattr(args, k) for k in ("B1", "B2", "q", "rows") if getattr(args, k)}
     if w.kind == "var" and (args.order != 1 or args.intercept):
@@ -470,10 +499,14 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": w.name, "n": m, "p": p, "r": r, "B1": w.B1, "q": w.q,
                            "B2": w.B2, "precision": args.precision, "warm_start": args.warm,
+                           **({"warm_start_training": ws_train} if ws_train else {}),
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "inputs larger than L2 (X is %.0f MB)" % (X.nbytes / 1e6),
                            **({"overrides": overrides} if overrides else {})},
                 "solves_per_s": fits_s * cols,
+                "admm": {"iterations_per_fit": float(np.mean([d["admm_iterations"] for d in diags])),
+                         "nonconverged_per_fit": float(np.mean([d["admm_nonconverged"] for d in diags])),
+                         "warm_start_used": ["none", "path", "learned"][diags[-1]["warm_start_used"]]},
                 "roofline": roofline, "roofline_other": kernels[1:], "stage_ms": stage_ms,
                 "clocks": clocks, "gpu_launches": launches * args.steps,
                 "e2e": e2e, "cpu_baseline": cpu,

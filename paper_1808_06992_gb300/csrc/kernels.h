@@ -205,6 +205,11 @@ bool mlp_tc_available();
 void mlp_forward_tc(const __nv_bfloat16* H, int64_t M, const __nv_bfloat16* W, int32_t width,
                     const float* bias, float* pre, __nv_bfloat16* Hn, __nv_bfloat16* HnT, int64_t ldT,
                     int32_t* err, cudaStream_t s);
+// Inference through the last hidden layer and the head: h = gelu(H W^T + b) rounded
+// to bf16, head_part[slot][m][j] = sum over the slot's 128 columns c of h[m][c] w4[j][c]
+// (width / 128 slots, 3 outputs j; w4 is 3 x width bf16).  h is not stored.
+void mlp_forward_head_tc(const __nv_bfloat16* H, int64_t M, const __nv_bfloat16* W, int32_t width,
+                         const float* bias, const __nv_bfloat16* w4, float* head_part, int32_t* err, cudaStream_t s);
 // dAp = (dA W) * gelu'(pre_prev) (bf16) with WT = W^T, dApT its transpose (nullable).
 void mlp_backward_tc(const __nv_bfloat16* dA, int64_t M, const __nv_bfloat16* WT, int32_t width,
                      const float* pre_prev, __nv_bfloat16* dAp, __nv_bfloat16* dApT, int64_t ldT, int32_t* err,

@@ -7,11 +7,13 @@
 // before any iteration: the marginal correlation, the Gram diagonal, and the
 // ridge solution (G/n + rho I)^{-1} b/n -- the first x-update from zero --
 // scaled by lambda_j and by the previous lambda_{j-1}.
-// Network: 8 -> 512 -> 512 -> 512 -> 3 with exact-erf GELU, BF16 weights and BF16
-// hidden activations in every product (FP32 master copy in the optimizer), FP32
-// accumulation and FP32 pre-activations.  The two 512 x 512 layers, their
-// backward products and their weight gradients run on the tensor cores
-// (mlp_tc.cu); the 8-input layer and the 3-output head stay on CUDA cores.  Loss
+// Network: 8 -> 512 -> 512 -> 512 -> 3 with GELU (Phi to 7e-8, gelu.cuh), BF16
+// weights and BF16 hidden activations in every product (FP32 master copy in the
+// optimizer), FP32 accumulation and FP32 pre-activations.  The two 512 x 512
+// layers, their backward products and their weight gradients run on the tensor
+// cores (mlp_tc.cu); the 8-input layer stays on CUDA cores, and so does the
+// 3-output head in training (in inference it is folded into the last hidden
+// layer's epilogue).  Loss
 // per row: squared errors of the two state outputs plus the logistic loss of the
 // active logit, averaged over rows.
 //
@@ -27,6 +29,7 @@
 #include <cstring>
 #include <vector>
 
+#include "gelu.cuh"
 #include "kernels.h"
 
 namespace uoi {
@@ -45,17 +48,6 @@ constexpr int64_t OFF_B3 = OFF_W3 + (int64_t)WS_H * WS_H;
 constexpr int64_t OFF_W4 = OFF_B3 + WS_H;
 constexpr int64_t OFF_B4 = OFF_W4 + (int64_t)WS_OUT * WS_H;
 constexpr int64_t N_PARAMS = OFF_B4 + WS_OUT;
-
-__device__ __forceinline__ float gelu_f(float x)
-{
-    return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
-}
-
-__device__ __forceinline__ float gelu_grad_f(float x)
-{
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) +
-           x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
 
 // dst[i] = sum over slices (fixed order) of part[s][i]
 __global__ void k_sum_slices(const float* part, int slices, int64_t count, float* dst)
@@ -80,23 +72,66 @@ __global__ void k_col_sums(const TA* A, int64_t N, int C, float* dst)
 }
 
 // layer 1 (K = 8): a1 = X W1^T + b1, h1 = gelu(a1) stored in BF16 (and transposed,
-// h1t[o * ldt + n], for the weight gradient of layer 2)
-__global__ void k_layer_in(const float* X, int64_t N, const __nv_bfloat16* w, const float* master,
-                           float* pre, __nv_bfloat16* h, __nv_bfloat16* ht, int64_t ldt)
+// h1t[o * ldt + n], for the weight gradient of layer 2).  W1 and b1 are staged in
+// shared memory; a warp takes one group of 64 outputs for 32 consecutive rows
+// (lane = row: the weights it reads are the same for every lane), reads each row's
+// 8 inputs once and writes 64 consecutive BF16 outputs as 16-byte vectors.
+constexpr int LIN_GROUP = 64;
+__global__ void __launch_bounds__(256)
+k_layer_in(const float* X, int64_t N, const __nv_bfloat16* w, const float* master, float* pre,
+           __nv_bfloat16* h, __nv_bfloat16* ht, int64_t ldt)
 {
-    const int64_t total = N * WS_H;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+    __shared__ float sw[WS_H * WS_IN];
+    __shared__ float sb[WS_H];
+    for (int i = threadIdx.x; i < WS_H * WS_IN; i += blockDim.x) sw[i] = __bfloat162float(w[OFF_W1 + i]);
+    for (int i = threadIdx.x; i < WS_H; i += blockDim.x) sb[i] = master[OFF_B1 + i];
+    __syncthreads();
+    constexpr int groups = WS_H / LIN_GROUP;                   // 8 per row
+    const int64_t items = ((N + 31) / 32) * 32 * groups;       // (32-row tile, group, lane)
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < items;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = t / WS_H;
-        const int o = (int)(t % WS_H);
-        float a = master[OFF_B1 + o];
+        const int64_t n = (t / (32 * groups)) * 32 + (t & 31);
+        const int o0 = (int)((t >> 5) % groups) * LIN_GROUP;
+        if (n >= N) continue;
+        const float4 x0 = *reinterpret_cast<const float4*>(X + n * WS_IN);
+        const float4 x1 = *reinterpret_cast<const float4*>(X + n * WS_IN + 4);
+        const float xv[WS_IN] = { x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w };
+#pragma unroll 2
+        for (int v = 0; v < LIN_GROUP; v += 8) {
+            uint32_t packed[4];
 #pragma unroll
-        for (int k = 0; k < WS_IN; ++k)
-            a = fmaf(X[n * WS_IN + k], __bfloat162float(w[OFF_W1 + o * WS_IN + k]), a);
-        if (pre) pre[t] = a;
-        const __nv_bfloat16 hv = __float2bfloat16_rn(gelu_f(a));
-        h[t] = hv;
-        if (ht) ht[(int64_t)o * ldt + n] = hv;
+            for (int u = 0; u < 8; u += 2) {
+                float r2[2];
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int o = o0 + v + u + h2;
+                    float acc = sb[o];
+#pragma unroll
+                    for (int k = 0; k < WS_IN; ++k) acc = fmaf(xv[k], sw[o * WS_IN + k], acc);
+                    if (pre) pre[n * WS_H + o] = acc;
+                    r2[h2] = gelu_f(acc);
+                    if (ht) ht[(int64_t)o * ldt + n] = __float2bfloat16_rn(r2[h2]);
+                }
+                const __nv_bfloat162 hb = __floats2bfloat162_rn(r2[0], r2[1]);
+                packed[u / 2] = *reinterpret_cast<const uint32_t*>(&hb);
+            }
+            *reinterpret_cast<uint4*>(h + n * WS_H + o0 + v) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+    }
+}
+
+// head of the inference forward: out[n][j] = b4[j] + the partial products of the
+// last hidden layer's epilogue, summed over its slots in a fixed order.
+constexpr int HEAD_SLOTS = WS_H / 128;
+__global__ void k_head_sum(const float* part, int64_t N, const float* master, float* out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N * WS_OUT;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % WS_OUT);
+        float v = part[i];
+#pragma unroll
+        for (int sl = 1; sl < HEAD_SLOTS; ++sl) v += part[(int64_t)sl * N * WS_OUT + i];
+        out[i] = v + master[OFF_B4 + j];
     }
 }
 
@@ -285,6 +320,7 @@ struct Acts {
     DevBuf a1, a2, a3;        // FP32 pre-activations (training)
     DevBuf h1, h2, h3;        // BF16 hidden activations, N x 512
     DevBuf h1t, h2t;          // BF16 512 x ldt transposes (training: the weight gradients' B)
+    DevBuf head;              // inference: the head's partial sums, HEAD_SLOTS x N x 3
     DevBuf out;
     int64_t ldt = 0;
 };
@@ -314,15 +350,26 @@ void forward(WsModel* M, const float* X, int64_t N, Acts& A, bool train, int32_t
         UOI_CUDA(cudaMemsetAsync(A.h1t.ptr, 0, tb, s));      // padding rows of the K extent
         UOI_CUDA(cudaMemsetAsync(A.h2t.ptr, 0, tb, s));
     }
-    A.h1.alloc(hb, s); A.h2.alloc(hb, s); A.h3.alloc(hb, s);
+    A.h1.alloc(hb, s); A.h2.alloc(hb, s);
+    if (train) A.h3.alloc(hb, s);
+    else A.head.alloc(sizeof(float) * (size_t)HEAD_SLOTS * N * WS_OUT, s);
     A.out.alloc(sizeof(float) * (size_t)N * WS_OUT, s);
-    k_layer_in<<<blocks_for(N * WS_H), 256, 0, s>>>(X, N, M->w, M->master, train ? A.a1.as<float>() : nullptr,
+    k_layer_in<<<blocks_for(N * (WS_H / LIN_GROUP)), 256, 0, s>>>(X, N, M->w, M->master, train ? A.a1.as<float>() : nullptr,
                                                    A.h1.as<__nv_bfloat16>(),
                                                    train ? A.h1t.as<__nv_bfloat16>() : nullptr, A.ldt);
     UOI_CHECK_LAUNCH();
     mlp_forward_tc(A.h1.as<__nv_bfloat16>(), N, M->w + OFF_W2, WS_H, M->master + OFF_B2,
                    train ? A.a2.as<float>() : nullptr, A.h2.as<__nv_bfloat16>(),
                    train ? A.h2t.as<__nv_bfloat16>() : nullptr, A.ldt, err, s);
+    if (!train) {
+        // inference: the head is fused into the last hidden layer's epilogue
+        mlp_forward_head_tc(A.h2.as<__nv_bfloat16>(), N, M->w + OFF_W3, WS_H, M->master + OFF_B3,
+                            M->w + OFF_W4, A.head.as<float>(), err, s);
+        k_head_sum<<<blocks_for(N * WS_OUT), 256, 0, s>>>(A.head.as<float>(), N, M->master, A.out.as<float>());
+        UOI_CHECK_LAUNCH();
+        count_launch(2);
+        return;
+    }
     mlp_forward_tc(A.h2.as<__nv_bfloat16>(), N, M->w + OFF_W3, WS_H, M->master + OFF_B3,
                    train ? A.a3.as<float>() : nullptr, A.h3.as<__nv_bfloat16>(), nullptr, 0, err, s);
     k_head<<<(unsigned)ceil_div(N * 32, 256), 256, 0, s>>>(A.h3.as<__nv_bfloat16>(), N, M->w, M->master,

@@ -8,11 +8,16 @@
 //   backward  da = acc * gelu'(pre): da (bf16, row-major: the next backward
 //             product's A) and da^T (bf16: the weight gradient's A);
 //   gradient  the FP32 partial sums of one slice of K (rows of the batch), reduced
-//             over slices afterwards in a fixed order.
+//             over slices afterwards in a fixed order;
+//   forward + head (inference, last hidden layer)  h = gelu(acc + b_n) rounded to
+//             bf16 as the forward stores it, then its products with the head's
+//             weights, one partial sum per (row, 128 columns): h is never written.
 // Tile 128 x 256 (UMMA M = 128, N = 256), k = 32 per stage (64 B of bf16 per row,
-// 64-byte swizzle), a 6-stage TMA ring, one CTA per tile (cta_group::1) with 256
-// TMEM columns.  Warp 0 issues the TMA loads, warp 1 the MMAs, warps 2-5 drain
-// the accumulator (one tile row per thread) and apply the epilogue.  Rows past M
+// 64-byte swizzle), a 3-stage TMA ring (K is 512: sixteen stages), one CTA per
+// tile (cta_group::1) with 256 TMEM columns, two CTAs per SM.  Warp 0 issues the
+// TMA loads, warp 1 the MMAs, warps 2-9 drain the accumulator (one tile row and
+// half of its columns per thread) and apply the epilogue -- the GELU and the
+// stores are the bulk of a layer's time, so eight warps take them.  Rows past M
 // are read as zeros (the tensor maps' out-of-range fill) and not written.  Every
 // wait is bounded (wait_ns) and reports UOI_ERR_TIMEOUT.
 #include <cuda_bf16.h>
@@ -20,6 +25,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "gelu.cuh"
 #include "kernels.h"
 #include "tc_common.cuh"
 
@@ -31,15 +37,16 @@ using namespace tc;
 constexpr int MT_TM = 128;
 constexpr int MT_TN = 256;
 constexpr int MT_TK = 32;
-constexpr int MT_STAGES = 6;
+constexpr int MT_STAGES = 3;
 constexpr int MT_A_BYTES = MT_TM * MT_TK * 2;             // 8 KB
 constexpr int MT_B_BYTES = MT_TN * MT_TK * 2;             // 16 KB
 constexpr int MT_STAGE = MT_A_BYTES + MT_B_BYTES;         // 24 KB
 constexpr int MT_SMEM = MT_STAGES * MT_STAGE + 1024;
-constexpr int MT_THREADS = 64 + 128;                      // TMA, MMA, 4 epilogue warps
+constexpr int MT_THREADS = 64 + 256;                      // TMA, MMA, 8 epilogue warps
 constexpr uint32_t MT_TMEM_COLS = 256;
+constexpr int WS_OUT = 3;                                 // outputs of the head (forward + head mode)
 
-enum MlpEpilogue : int32_t { MLP_FORWARD = 0, MLP_BACKWARD = 1, MLP_GRAD_PARTIAL = 2 };
+enum MlpEpilogue : int32_t { MLP_FORWARD = 0, MLP_BACKWARD = 1, MLP_GRAD_PARTIAL = 2, MLP_FORWARD_HEAD = 3 };
 
 struct MlpGemmArgs {
     int32_t M, N;                 // rows of A / C, columns of C (rows of B)
@@ -52,21 +59,13 @@ struct MlpGemmArgs {
     __nv_bfloat16* outT;          // forward / backward: N x ldT (nullable)
     int64_t ldT;
     float* part;                  // gradient: slices x M x N
+    const __nv_bfloat16* w4;      // forward + head: head weights, WS_OUT rows of N
+    float* head;                  // forward + head: (N / 128) slots x M x WS_OUT partial sums
     int32_t* err;
     uint64_t wait_ns = tc::kWaitLimitNs;   // limit of every bounded mbarrier wait
 };
 
-__device__ __forceinline__ float gelu_t(float x)
-{
-    return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
-}
-
-__device__ __forceinline__ float gelu_grad_t(float x)
-{
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
-
-__global__ void __launch_bounds__(MT_THREADS, 1)
+__global__ void __launch_bounds__(MT_THREADS, 2)
 k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MlpGemmArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -74,7 +73,7 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * MT_TM, n0 = blockIdx.y * MT_TN;
+    const int m0 = blockIdx.y * MT_TM, n0 = blockIdx.x * MT_TN;   // N tiles adjacent: they share A
     const int g0 = blockIdx.z * a.kst_slice;
     const int g1 = min(a.kst_total, g0 + a.kst_slice);
     const int nst = max(0, g1 - g0);
@@ -142,6 +141,7 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     } else if (warp >= 2) {
         // ---------------- epilogue: one tile row per thread ----------------
         const int quad = warp & 3;                        // TMEM lanes 32*quad .. +31
+        const int half = (warp - 2) >> 2;                 // columns 128*half .. +127
         const int m = m0 + quad * 32 + lane;
         bool ok = true;
         if (nst > 0) ok = mbar_wait(&acc_bar, 0, &abort_flag, a.wait_ns);
@@ -150,7 +150,8 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
         } else {
             tc_fence_after();
-            for (int cb = 0; cb < MT_TN / 16; ++cb) {
+            float hsum[WS_OUT] = {};
+            for (int cb = half * 8; cb < half * 8 + 8; ++cb) {
                 float v[16];
                 if (nst > 0) {
                     tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16), v);
@@ -168,27 +169,67 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             *reinterpret_cast<float4*>(dst + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
                     continue;
                 }
+                // 16-byte vector loads and stores: a thread owns 16 consecutive columns
+                // of one row, so each bf16 row segment is one full 32-byte sector and
+                // each FP32 one two.
                 float r[16];
-                if (a.mode == MLP_FORWARD) {
+                const int64_t off = (int64_t)m * a.N + nb;
+                if (a.mode == MLP_FORWARD || a.mode == MLP_FORWARD_HEAD) {
+                    const float4* bias4 = reinterpret_cast<const float4*>(a.bias + nb);
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const float pre = v[t] + a.bias[nb + t];
-                        if (a.pre) a.pre[(int64_t)m * a.N + nb + t] = pre;
-                        r[t] = gelu_t(pre);
+                    for (int t = 0; t < 16; t += 4) {
+                        const float4 b = __ldg(bias4 + t / 4);
+                        const float4 pre = make_float4(v[t] + b.x, v[t + 1] + b.y, v[t + 2] + b.z, v[t + 3] + b.w);
+                        if (a.pre) *reinterpret_cast<float4*>(a.pre + off + t) = pre;
+                        r[t] = gelu_f(pre.x);
+                        r[t + 1] = gelu_f(pre.y);
+                        r[t + 2] = gelu_f(pre.z);
+                        r[t + 3] = gelu_f(pre.w);
                     }
                 } else {
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) r[t] = v[t] * gelu_grad_t(a.pre[(int64_t)m * a.N + nb + t]);
+                    for (int t = 0; t < 16; t += 4) {
+                        const float4 pre = *reinterpret_cast<const float4*>(a.pre + off + t);
+                        r[t] = v[t] * gelu_grad_f(pre.x);
+                        r[t + 1] = v[t + 1] * gelu_grad_f(pre.y);
+                        r[t + 2] = v[t + 2] * gelu_grad_f(pre.z);
+                        r[t + 3] = v[t + 3] * gelu_grad_f(pre.w);
+                    }
                 }
-                __nv_bfloat16* orow = a.out + (int64_t)m * a.N + nb;
+                uint32_t packed[8];
 #pragma unroll
-                for (int t = 0; t < 16; t += 2)
-                    *reinterpret_cast<__nv_bfloat162*>(orow + t) = __floats2bfloat162_rn(r[t], r[t + 1]);
+                for (int t = 0; t < 16; t += 2) {
+                    const __nv_bfloat162 hb = __floats2bfloat162_rn(r[t], r[t + 1]);
+                    packed[t / 2] = *reinterpret_cast<const uint32_t*>(&hb);
+                }
+                if (a.mode == MLP_FORWARD_HEAD) {
+                    // the head reads the activations as stored (BF16), so it takes them
+                    // after the rounding; h itself is not written
+#pragma unroll
+                    for (int t = 0; t < 16; t += 2) {
+                        const float2 hv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&packed[t / 2]));
+#pragma unroll
+                        for (int j = 0; j < WS_OUT; ++j) {
+                            const float2 wv = __bfloat1622float2(
+                                __ldg(reinterpret_cast<const __nv_bfloat162*>(a.w4 + (int64_t)j * a.N + nb + t)));
+                            hsum[j] = fmaf(hv.y, wv.y, fmaf(hv.x, wv.x, hsum[j]));
+                        }
+                    }
+                    continue;
+                }
+                uint4* orow = reinterpret_cast<uint4*>(a.out + off);
+                orow[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                orow[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                 if (a.outT) {
                     // column-major copy: the warp's 32 consecutive rows are adjacent
 #pragma unroll
                     for (int t = 0; t < 16; ++t) a.outT[(int64_t)(nb + t) * a.ldT + m] = __float2bfloat16_rn(r[t]);
                 }
+            }
+            if (a.mode == MLP_FORWARD_HEAD && m < a.M) {
+                float* dst = a.head + (((int64_t)blockIdx.x * 2 + half) * a.M + m) * WS_OUT;
+#pragma unroll
+                for (int j = 0; j < WS_OUT; ++j) dst[j] = hsum[j];
             }
         }
         tc_fence_before();
@@ -231,7 +272,9 @@ void launch(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t
     a.N = N;
     a.kst_total = K / MT_TK;
     a.kst_slice = (int32_t)ceil_div(a.kst_total, slices);
-    const dim3 grid((unsigned)ceil_div(M, MT_TM), (unsigned)(N / MT_TN), (unsigned)slices);
+    if (ceil_div(M, MT_TM) > 65535)
+        throw Error(UOI_ERR_INVALID_ARG, "tensor-core MLP product: at most 65535 row tiles per launch");
+    const dim3 grid((unsigned)(N / MT_TN), (unsigned)ceil_div(M, MT_TM), (unsigned)slices);
     k_mlp_gemm_tc<<<grid, MT_THREADS, MT_SMEM, s>>>(mA, mB, a);
     UOI_CHECK_LAUNCH();
     count_launch();
@@ -248,6 +291,17 @@ void mlp_forward_tc(const __nv_bfloat16* H, int64_t M, const __nv_bfloat16* W, i
     MlpGemmArgs a;
     a.mode = MLP_FORWARD;
     a.bias = bias; a.pre = pre; a.out = Hn; a.outT = HnT; a.ldT = ldT; a.part = nullptr; a.err = err;
+    a.w4 = nullptr; a.head = nullptr;
+    launch(H, width, W, width, (int32_t)M, width, width, 1, a, s);
+}
+
+void mlp_forward_head_tc(const __nv_bfloat16* H, int64_t M, const __nv_bfloat16* W, int32_t width,
+                         const float* bias, const __nv_bfloat16* w4, float* head_part, int32_t* err, cudaStream_t s)
+{
+    MlpGemmArgs a;
+    a.mode = MLP_FORWARD_HEAD;
+    a.bias = bias; a.pre = nullptr; a.out = nullptr; a.outT = nullptr; a.ldT = 0; a.part = nullptr; a.err = err;
+    a.w4 = w4; a.head = head_part;
     launch(H, width, W, width, (int32_t)M, width, width, 1, a, s);
 }
 
@@ -258,7 +312,7 @@ void mlp_backward_tc(const __nv_bfloat16* dA, int64_t M, const __nv_bfloat16* WT
     MlpGemmArgs a;
     a.mode = MLP_BACKWARD;
     a.bias = nullptr; a.pre = const_cast<float*>(pre_prev); a.out = dAp; a.outT = dApT; a.ldT = ldT;
-    a.part = nullptr; a.err = err;
+    a.part = nullptr; a.err = err; a.w4 = nullptr; a.head = nullptr;
     launch(dA, width, WT, width, (int32_t)M, width, width, 1, a, s);
 }
 
@@ -268,6 +322,7 @@ void mlp_weight_grad_tc(const __nv_bfloat16* dAT, const __nv_bfloat16* HT, int64
     MlpGemmArgs a;
     a.mode = MLP_GRAD_PARTIAL;
     a.bias = nullptr; a.pre = nullptr; a.out = nullptr; a.outT = nullptr; a.ldT = 0; a.part = part; a.err = err;
+    a.w4 = nullptr; a.head = nullptr;
     launch(dAT, ld, HT, ld, width, width, (int32_t)ceil_div(rows, MT_TK) * MT_TK, slices, a, s);
 }
 

@@ -209,3 +209,50 @@ def test_var2_intercept_p192_fullsize_sampled_mixed():
                 res = Y[ev, e] - Xa[ev] @ beta
                 want = float(res @ res)
                 assert abs(out["est_loss"][k, j, e] - want) <= 2e-5 * max(want, 1e-12)
+
+
+def test_var_p1000_fullsize_sampled_mixed():
+    # workload 5 (VAR(1), p = 1000, T = 20000, B1 = B2 = 32, q = 40) in the mixed form
+    # with path warm start (its fastest schedule): bootstrap indices of sampled
+    # bootstraps bit-exact; selection columns of sampled (bootstrap, equation) paths
+    # against the exact minimiser; the intersection / argmin / median properties;
+    # OLS and held-out losses of sampled (k, j, e) against the oracle
+    w = synth.WORKLOADS[5]
+    S = synth.workload_data(5).series
+    X, Y = np.ascontiguousarray(S[:-1]), np.ascontiguousarray(S[1:])
+    m, p = X.shape
+    kw = dict(B1=w.B1, B2=w.B2, q=w.q, block_len=w.block_len, warm_start=native.WARM_PATH)
+    out = _gpu_fit(X, Y, native.PREC_MIXED, **kw)
+    _check_properties(out, p, p)
+    ks, eqs = [w.B1 - 1], [7, 512]
+    for k in (0, w.B1 - 1):
+        np.testing.assert_array_equal(out["sel_weights"][k], oracle.selection_weights(m, w.block_len, 0, 0, k))
+    conv = out["sel_conv"][ks][:, :, eqs]
+    wsel = np.stack([out["sel_weights"][k] for k in ks]).astype(np.uint32)
+    ref = oracle.lasso_admm_batch(X, np.ascontiguousarray(Y[:, eqs]), wsel, out["lambdas"], warm_start=1,
+                                  max_iter=5000)
+    assert ref["conv"].all()
+    # columns the GPU finished within max_iter: held to the exact minimiser
+    rep = mixed_check.Report()
+    for a, k in enumerate(ks):
+        G, Bm, nk = mixed_check.moments(X, Y[:, eqs], out["sel_weights"][k])
+        ev = np.linalg.eigvalsh(G / nk)
+        for b, e in enumerate(eqs):
+            for j in range(w.q):
+                if not conv[a, j, b]:
+                    continue
+                mixed_check.check_column(G, Bm[:, b], nk, out["lambdas"][j], out["sel_beta"][k, j, e],
+                                         ref["beta"][a, j, b], mixed_check.ETA_MIXED, float(ev[0]),
+                                         float(ev[-1]), rep)
+    print(rep, f"; columns stopped at max_iter: {int((~conv.astype(bool)).sum())} of {conv.size}")
+    assert rep.columns >= conv.size // 2
+    for k in (w.B2 - 1,):
+        wt = out["est_weights"][k]
+        ev = out["est_eval"][k].astype(bool)
+        G, B, _ = mixed_check.moments(X, Y[:, eqs], wt)
+        for j in (0, w.q // 2, w.q - 1):
+            for b, e in enumerate(eqs):
+                beta, _ = oracle.ols_support(G, B[:, b], out["family"][j, e].astype(np.uint64))
+                res = Y[ev, e] - X[ev] @ beta
+                want = float(res @ res)
+                assert abs(out["est_loss"][k, j, e] - want) <= 2e-5 * max(want, 1e-12)
