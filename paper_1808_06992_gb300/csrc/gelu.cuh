@@ -19,18 +19,33 @@ struct NormalCdfPdf {
     float pdf;      // phi(x)
 };
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float exp2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// With z = |x| / sqrt 2: t = 1 / (1 + (p / sqrt 2) |x|), e^(-z^2) = 2^(x * x * (-log2(e) / 2)),
+// and the coefficients halved, so the polynomial times e is Phi(-|x|) directly.
 __device__ __forceinline__ NormalCdfPdf normal_cdf_pdf(float x)
 {
-    constexpr float p = 0.3275911f;
-    constexpr float a1 = 0.254829592f, a2 = -0.284496736f, a3 = 1.421413741f, a4 = -1.453152027f,
-                    a5 = 1.061405429f;
-    const float z = fabsf(x) * 0.70710678118654752f;
-    const float t = __fdividef(1.0f, fmaf(p, z, 1.0f));
-    const float e = __expf(-z * z);
-    const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, a5, a4), a3), a2), a1);
-    const float half_erfc = 0.5f * poly * e;                 // Phi(-|x|)
+    constexpr float p_s = 0.3275911f * 0.70710678118654752f;
+    constexpr float h1 = 0.5f * 0.254829592f, h2 = 0.5f * -0.284496736f, h3 = 0.5f * 1.421413741f,
+                    h4 = 0.5f * -1.453152027f, h5 = 0.5f * 1.061405429f;
+    constexpr float c = -0.72134752044448170f;               // -log2(e) / 2
+    const float t = rcp_approx(fmaf(p_s, fabsf(x), 1.0f));
+    const float e = exp2_approx(x * (x * c));                 // e^(-x^2 / 2)
+    const float tail = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, h5, h4), h3), h2), h1) * e;   // Phi(-|x|)
     NormalCdfPdf r;
-    r.cdf = x >= 0.0f ? 1.0f - half_erfc : half_erfc;
+    r.cdf = x >= 0.0f ? 1.0f - tail : tail;
     r.pdf = e * 0.39894228040143268f;
     return r;
 }

@@ -71,7 +71,7 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[MT_STAGES], empty_bar[MT_STAGES], acc_bar;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
+    __shared__ int abort_flag, epi_ok;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * MT_TM, n0 = blockIdx.x * MT_TN;   // N tiles adjacent: they share A
     const int g0 = blockIdx.z * a.kst_slice;
@@ -143,23 +143,25 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int quad = warp & 3;                        // TMEM lanes 32*quad .. +31
         const int half = (warp - 2) >> 2;                 // columns 128*half .. +127
         const int m = m0 + quad * 32 + lane;
-        bool ok = true;
-        if (nst > 0) ok = mbar_wait(&acc_bar, 0, &abort_flag, a.wait_ns);
-        if (!__all_sync(0xffffffffu, ok)) {
-            abort_flag = 1;
-            atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+        // One thread waits for the accumulator while the other epilogue warps sleep
+        // on a named barrier: warps that poll take issue slots from the epilogue of
+        // the SM's other CTA.
+        if (warp == 2 && lane == 0) epi_ok = (nst == 0 || mbar_wait(&acc_bar, 0, &abort_flag, a.wait_ns)) ? 1 : 0;
+        named_barrier_sync(1, MT_THREADS - 64);
+        if (!epi_ok) {
+            if (warp == 2 && lane == 0) {
+                abort_flag = 1;
+                atomicCAS(a.err, 0, UOI_ERR_TIMEOUT);
+            }
         } else {
             tc_fence_after();
             float hsum[WS_OUT] = {};
-            for (int cb = half * 8; cb < half * 8 + 8; ++cb) {
+            // one chunk of 16 columns, its accumulators in rv
+            auto chunk = [&](const uint32_t (&rv)[16], int cb) {
+                if (m >= a.M) return;
                 float v[16];
-                if (nst > 0) {
-                    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16), v);
-                } else {
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) v[t] = 0.f;
-                }
-                if (m >= a.M) continue;
+                for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(rv[t]);
                 const int nb = n0 + cb * 16;
                 if (a.mode == MLP_GRAD_PARTIAL) {
                     float* dst = a.part + ((int64_t)blockIdx.z * a.M + m) * a.N + nb;
@@ -167,7 +169,7 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     for (int t = 0; t < 16; t += 4)
                         if (nb + t + 3 < a.N)
                             *reinterpret_cast<float4*>(dst + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
-                    continue;
+                    return;
                 }
                 // 16-byte vector loads and stores: a thread owns 16 consecutive columns
                 // of one row, so each bf16 row segment is one full 32-byte sector and
@@ -215,7 +217,7 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             hsum[j] = fmaf(hv.y, wv.y, fmaf(hv.x, wv.x, hsum[j]));
                         }
                     }
-                    continue;
+                    return;
                 }
                 uint4* orow = reinterpret_cast<uint4*>(a.out + off);
                 orow[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -225,6 +227,28 @@ k_mlp_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                     for (int t = 0; t < 16; ++t) a.outT[(int64_t)(nb + t) * a.ldT + m] = __float2bfloat16_rn(r[t]);
                 }
+            };
+            // TMEM loads double-buffered: chunk cb + 1 is in flight while cb is computed
+            const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+            auto issue = [&](int cb, uint32_t (&rv)[16]) {
+                if (nst > 0) {
+                    tmem_ld16_issue(trow + (uint32_t)(cb * 16), rv);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) rv[t] = 0u;
+                }
+            };
+            const int cb0 = half * 8;
+            uint32_t ra[16], rb[16];
+            issue(cb0, ra);
+            tmem_wait16(ra);
+            for (int cb = cb0; cb < cb0 + 8; cb += 2) {
+                issue(cb + 1, rb);
+                chunk(ra, cb);
+                tmem_wait16(rb);
+                if (cb + 2 < cb0 + 8) issue(cb + 2, ra);
+                chunk(rb, cb + 1);
+                if (cb + 2 < cb0 + 8) tmem_wait16(ra);
             }
             if (a.mode == MLP_FORWARD_HEAD && m < a.M) {
                 float* dst = a.head + (((int64_t)blockIdx.x * 2 + half) * a.M + m) * WS_OUT;
