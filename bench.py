@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--B2", type=int)
     ap.add_argument("--q", type=int)
     ap.add_argument("--rows", type=int, help="keep only the first ROWS rows of the design")
-    ap.add_argument("--streams", type=int, default=8, help="worker streams of the batched workload")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="batched workload: 0 = grouped ADMM over all problems, N > 0 = N worker streams")
     ap.add_argument("--order", type=int, default=1, help="VAR workloads: lag order d of the design")
     ap.add_argument("--intercept", type=int, default=0, choices=[0, 1],
                     help="VAR workloads: fit the unpenalised intercept mu")
@@ -619,7 +620,8 @@ def bench_batch(args, torch, rank, world, local, dist):
                         "peak": hp, "unit": "GB/s", "frac": gbs / hp, "traffic": None,
                         "launches_per_step": sum(d["n_xupdate"] for d in diags), "ms_per_step": ms_x,
                         "peak_source": "measured HBM copy" if hbm else "fallback 6.8 TB/s",
-                        "note": "kernel times of concurrent streams summed"})
+                        "note": ("grouped replays (x-update and check launches of all problems) timed whole"
+                                 if args.streams == 0 else "kernel times of concurrent streams summed")})
     kernels.sort(key=lambda k: -k["ms_per_step"])
     e2e = None
     if args.e2e_steps > 0:
@@ -654,7 +656,8 @@ def bench_batch(args, torch, rank, world, local, dist):
                 "dtype": DTYPE_MIXED if args.precision == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": w.name, "problems": count, "n_range": [min(ns), max(ns)],
                            "p_range": [min(ps), max(ps)], "B1": w.B1, "q": w.q, "B2": w.B2,
-                           "precision": args.precision, "warm_start": args.warm, "streams": args.streams,
+                           "precision": args.precision, "warm_start": args.warm,
+                           "batch_mode": "grouped" if args.streams == 0 else f"{args.streams} worker streams",
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "inputs larger than L2 (%.0f MB of designs)" % (sum(pb.X.nbytes for pb in probs) / 1e6)},
                 "solves_per_s": fits_s * w.B1 * w.q,

@@ -169,13 +169,27 @@ int uoi_lasso_fit(const double* X, const double* y, int64_t n, int64_t p,
  * or device, per problem.  One parameter set for all; prm->lambdas must be NULL
  * (each problem gets its own grid from its lambda_max) and problem i draws its
  * bootstraps with problem_id = prm->problem_id + i, so its result equals
- * uoi_lasso_fit on that problem with that problem_id.  The problems run on
- * `streams` worker streams of the calling thread's device (0 = 4), largest n*p^2
- * first, each worker fitting one problem at a time; the call returns once all
- * are done.  status_out (count, nullable) receives each problem's status and
- * diags (count, nullable) each problem's diagnostics.  Returns UOI_OK, or
- * UOI_OK_WITH_WARNINGS if any problem warned, or the first failing problem's
- * error (the others still ran and their outputs are valid). */
+ * uoi_lasso_fit on that problem with that problem_id.
+ *   streams == 0 (grouped): every problem is fitted on its own stream by its own
+ *     host thread (in waves of at most 128 problems, largest n*p^2 first), and the
+ *     ADMM selection solves (Alg. 1's B1 x q LASSO problems, Eq. 5) of all the
+ *     problems whose solve runs on the tensor cores (mixed precision, p above the
+ *     shared-memory schedule's limit) iterate together: each step is one x-update
+ *     launch over every live (problem, bootstrap, row tile, chain tile) and one
+ *     convergence-check launch over every live chain tile, replayed eight steps
+ *     at a time as a CUDA graph; a problem joins as soon as its inverse is ready
+ *     and leaves, to its estimation, as soon as its columns have finished.  The
+ *     chain tile and the pipeline depth are chosen by timing the first replays of
+ *     a batch shape and reused by later calls with that shape.  Each problem's
+ *     iterates are those of its own solve, so results do not change.
+ *   streams > 0: `streams` worker streams, largest n*p^2 first, each worker
+ *     fitting one problem at a time.
+ * The call returns once all are done.  status_out (count, nullable) receives each
+ * problem's status and diags (count, nullable) each problem's diagnostics (in the
+ * grouped form each replay's launches and time are counted in the diagnostics of
+ * one problem it advanced).  Returns UOI_OK, or UOI_OK_WITH_WARNINGS if any
+ * problem warned, or the first failing problem's error (the others still ran and
+ * their outputs are valid). */
 int uoi_lasso_fit_batch(int32_t count, const double* const* X, const double* const* y,
                         const int64_t* n, const int64_t* p, const uoi_params* prm,
                         double* const* beta_out, int32_t* status_out, uoi_diag* diags,

@@ -645,7 +645,9 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s)
     }
     if constexpr (sizeof(T) == 4) {
         if (admm_tc_available()) {               // FP32 state: x-update on the tensor cores
-            admm_solve_tc(reinterpret_cast<const AdmmProblem<float>&>(P), s);
+            const AdmmProblem<float>& Pf = reinterpret_cast<const AdmmProblem<float>&>(P);
+            if (admm_batch_try_join(Pf, s)) return;   // solved with the rest of a batch
+            admm_solve_tc(Pf, s);
             return;
         }
     }

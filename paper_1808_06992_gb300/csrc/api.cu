@@ -91,6 +91,7 @@ struct PendingTimes {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     KernelTotals tot;
     cudaEvent_t open = nullptr;
+    double extra_ms = 0.0;          // time measured elsewhere and credited to this thread
 };
 thread_local PendingTimes g_kt[TK_COUNT];   // per host thread, like the fit using it
 }  // namespace
@@ -101,6 +102,7 @@ void ktimer_reset()
         for (auto& e : k.ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         k.ev.clear();
         k.tot = KernelTotals{};
+        k.extra_ms = 0.0;
         if (k.open) { cudaEventDestroy(k.open); k.open = nullptr; }
     }
 }
@@ -125,6 +127,12 @@ void ktimer_end(TimedKernel k, cudaStream_t s, double flops, double bytes)
     g_kt[k].tot.bytes += bytes;
 }
 
+void ktimer_credit(TimedKernel k, double ms, int64_t launches)
+{
+    g_kt[k].extra_ms += ms;
+    g_kt[k].tot.launches += launches;
+}
+
 void ktimer_add_work(TimedKernel k, double flops, double bytes)
 {
     g_kt[k].tot.flops += flops;
@@ -134,7 +142,7 @@ void ktimer_add_work(TimedKernel k, double flops, double bytes)
 KernelTotals ktimer_total(TimedKernel k)
 {
     KernelTotals t = g_kt[k].tot;
-    t.ms = 0.f;
+    t.ms = (float)g_kt[k].extra_ms;
     for (auto& e : g_kt[k].ev) {
         cudaEventSynchronize(e.second);
         float ms = 0.f;
@@ -801,34 +809,58 @@ int uoi_lasso_fit_batch(int32_t count, const double* const* X, const double* con
         std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
             return (double)n[a] * p[a] * p[a] > (double)n[b] * p[b] * p[b];
         });
-        const int nw = std::max(1, std::min<int32_t>(streams > 0 ? streams : 4, count));
+        // streams > 0: that many workers, each fitting one problem at a time.
+        // streams == 0 (grouped): one worker per problem, in waves of at most kWave
+        // problems, and the selection solves of the problems that reach the
+        // tensor-core ADMM iterate together (AdmmBatch).
+        constexpr int32_t kWave = 128;
+        const bool grouped = streams == 0;
         std::vector<int32_t> st((size_t)count, UOI_OK);
         std::vector<std::string> detail((size_t)count);
         std::atomic<int32_t> next(0);
+        int32_t wave_end = count;
+        uoi::AdmmBatch* batch = nullptr;
         auto worker = [&]() {
             cudaSetDevice(dev);
             cudaStream_t ws = nullptr;
             if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
-                for (int32_t t; (t = next.fetch_add(1)) < count;) st[(size_t)order[(size_t)t]] = UOI_ERR_CUDA;
+                for (int32_t t; (t = next.fetch_add(1)) < wave_end;) {
+                    st[(size_t)order[(size_t)t]] = UOI_ERR_CUDA;
+                    if (batch) {                  // the batch counts every problem once
+                        uoi::admm_batch_enter(batch);
+                        uoi::admm_batch_leave();
+                    }
+                }
                 return;
             }
-            for (int32_t t; (t = next.fetch_add(1)) < count;) {
+            for (int32_t t; (t = next.fetch_add(1)) < wave_end;) {
                 const int32_t i = order[(size_t)t];
                 uoi_params q = *prm;
                 q.stream = ws;
                 q.problem_id = prm->problem_id + (uint64_t)i;
+                if (batch) uoi::admm_batch_enter(batch);
                 st[(size_t)i] = uoi::guarded([&] {
                     return uoi::fit_core(X[i], p[i], y[i], 1, n[i], p[i], 1, &q, beta_out[i], nullptr,
                                          diags ? &diags[i] : nullptr);
                 });
                 if (st[(size_t)i] < 0) detail[(size_t)i] = uoi::g_last_error;
+                if (batch) uoi::admm_batch_leave();     // counts a problem that never joined
             }
             cudaStreamSynchronize(ws);
             cudaStreamDestroy(ws);
         };
-        std::vector<std::thread> pool;
-        for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
-        for (auto& th : pool) th.join();
+        for (int32_t w0 = 0; w0 < count;) {
+            const int32_t w1 = grouped ? std::min(count, w0 + kWave) : count;
+            const int nw = grouped ? w1 - w0 : std::max(1, std::min<int32_t>(streams, count));
+            next = w0;
+            wave_end = w1;
+            batch = grouped ? uoi::admm_batch_create(w1 - w0) : nullptr;
+            std::vector<std::thread> pool;
+            for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+            for (auto& th : pool) th.join();
+            if (batch) uoi::admm_batch_destroy(batch);
+            w0 = w1;
+        }
         int ret = UOI_OK;
         int32_t first_bad = -1;
         for (int32_t i = 0; i < count; ++i) {

@@ -26,6 +26,7 @@ struct KernelTotals { float ms = 0.f; int64_t launches = 0; double flops = 0.0; 
 void ktimer_reset();
 void ktimer_begin(TimedKernel k, cudaStream_t s);
 void ktimer_end(TimedKernel k, cudaStream_t s, double flops, double bytes);
+void ktimer_credit(TimedKernel k, double ms, int64_t launches);   // work timed on another thread
 void ktimer_add_work(TimedKernel k, double flops, double bytes);
 KernelTotals ktimer_total(TimedKernel k);   // synchronises on the recorded events
 
@@ -191,6 +192,19 @@ void admm_solve(const AdmmProblem<T>& P, cudaStream_t s);
 // Streaming schedule with the tensor-core x-update (FP32 state, p > resident limit).
 bool admm_tc_available();
 void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s);
+// Grouped solve of a batch of problems.  Each batch worker thread enters the batch
+// before a fit and leaves it after; the fit's first tensor-core ADMM solve
+// (admm_solve<float> past the resident schedule) joins the batch instead of
+// running alone: its state is prepared on the worker's stream, a solver thread
+// iterates it together with the other members (grouped launches replayed as CUDA
+// graphs, tiles chosen by timing) and releases the worker once its columns have
+// finished.  Each problem's iterates are those of its own solve.
+struct AdmmBatch;
+AdmmBatch* admm_batch_create(int32_t expected);
+void admm_batch_destroy(AdmmBatch* b);
+void admm_batch_enter(AdmmBatch* b);
+void admm_batch_leave();
+bool admm_batch_try_join(const AdmmProblem<float>& P, cudaStream_t s);
 // Resident schedule only, with the caller's zeroed per-group chain counters
 // (G int32).  Returns false (launching nothing) when p is too large for it.
 template <typename T>

@@ -29,6 +29,13 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.h"
@@ -51,7 +58,6 @@ constexpr int XT_THREADS = 192;
 constexpr uint32_t XT_TMEM_COLS = 256;                 // A1[0] at 0, A1[1] at 64, A2 at 128
 constexpr int XT_CHUNK_STAGES = 4;                     // drain h.H every 128 k
 constexpr int XT_SCALE_EXP = 10;                       // scaled magnitudes stay below 2^10
-static_assert(3 * XT_NT_MAX * XT_TM * 4 <= XT_STAGES * XT_STAGE_MAX, "epilogue staging fits the ring");
 
 struct XtArgs {
     int32_t G, q, r, p, nchains, NT, kst, RT, warm;
@@ -97,12 +103,15 @@ __device__ __forceinline__ float pow2_scale(float bound)
     return ldexpf(1.f, min(120, max(-120, XT_SCALE_EXP - e)));
 }
 
-__global__ void __launch_bounds__(XT_THREADS, 2)
-k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CUtensorMap tmV,
-             XtArgs a)
+// One CTA of the x-update: row tile rt, chain tile ct of group g, with a ring of
+// STAGES slots (at least 4: the epilogue stages z, u and c in the idle ring).
+template <int STAGES>
+__device__ __forceinline__ void xupdate_tile(const CUtensorMap* tmM, const CUtensorMap* tmV, const XtArgs& a,
+                                             int rt, int ct, int g)
 {
+    static_assert(3 * XT_NT_MAX * XT_TM * 4 <= STAGES * XT_STAGE_MAX, "epilogue staging fits the ring");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t full_bar[XT_STAGES], empty_bar[XT_STAGES], accf_bar[2], acce_bar[2], done_bar;
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float red[4][XT_NT_MAX][5];
@@ -113,21 +122,13 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     __shared__ uint8_t s_live[XT_NT_MAX];          // chain exists and is still iterating
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int ct = blockIdx.y, g = blockIdx.z;
-    if (a.tiles) {                                     // only the tiles with a live chain
-        if ((int)blockIdx.y >= *a.ntiles) return;
-        const int tl = a.tiles[blockIdx.y];
-        g = tl / a.nct;
-        ct = tl % a.nct;
-    }
-    const int rt = blockIdx.x;
     const int i0 = rt * XT_TM, n0 = ct * a.NT;
     const int nchunks = (a.kst + XT_CHUNK_STAGES - 1) / XT_CHUNK_STAGES;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t b_bytes = (uint32_t)a.NT * XT_TK * 2;
     const uint32_t stage_tx = XT_PIECES * XT_A_BYTES + XT_PIECES * b_bytes;
     const uint32_t stage_bytes = (stage_tx + 1023u) & ~1023u;
-    const int nst = XT_STAGES;
+    const int nst = STAGES;
 
     // A tile whose chains have all stopped has nothing to update: skip it whole.
     // (Only the live flags are read before the pipeline starts; the epilogue
@@ -141,7 +142,7 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     }
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < XT_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
@@ -173,9 +174,9 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
             const uint32_t st = sbase + s * stage_bytes;
             mbar_expect_tx(&full_bar[s], stage_tx);
             const int k0 = s_ * XT_TK;
-            tma_load_3d(st, &tmM, &full_bar[s], 0, 0, blkA + XT_PIECES * s_);   // 2 pieces, 16 KB contiguous
+            tma_load_3d(st, tmM, &full_bar[s], 0, 0, blkA + XT_PIECES * s_);    // 2 pieces, 16 KB contiguous
             for (int pc = 0; pc < XT_PIECES; ++pc)
-                tma_load_3d(st + XT_PIECES * XT_A_BYTES + pc * b_bytes, &tmV, &full_bar[s], k0, rowB, pc);
+                tma_load_3d(st + XT_PIECES * XT_A_BYTES + pc * b_bytes, tmV, &full_bar[s], k0, rowB, pc);
         }
         if (abort_flag)
             for (int s_ = max(0, a.kst - nst); s_ < a.kst; ++s_)
@@ -394,6 +395,22 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     }
 }
 
+// One problem: grid (row tiles, chain tiles, groups), or (row tiles, entries of
+// the live tile list) when a.tiles is set.
+__global__ void __launch_bounds__(XT_THREADS, 2)
+k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CUtensorMap tmV,
+             XtArgs a)
+{
+    int ct = blockIdx.y, g = blockIdx.z;
+    if (a.tiles) {                                     // only the tiles with a live chain
+        if ((int)blockIdx.y >= *a.ntiles) return;
+        const int tl = a.tiles[blockIdx.y];
+        g = tl / a.nct;
+        ct = tl % a.nct;
+    }
+    xupdate_tile<XT_STAGES>(&tmM, &tmV, a, (int)blockIdx.x, ct, g);
+}
+
 // Per-row scale of M_g: row_scale = 2^(10 - e) for the row's largest |M_ik| =
 // f 2^e (1 for an all-zero or padding row), row_inv = 1 / row_scale.  One warp per row.
 __global__ void k_row_scale(const float* M, int32_t G, int64_t p, int64_t ppad, float* row_scale,
@@ -520,16 +537,50 @@ __global__ void k_xt_init(int64_t slots, int64_t p, int64_t kpad, const float* z
 // Convergence check of every live slot (one warp each): fixed-order sum of the
 // row-tile norms, stopping test of Eq. 5's ADMM, output of finished columns,
 // path advance, live count for the host.
-__global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t nchains, int32_t RT,
-                           int32_t warm, int32_t max_iter, float rho, float abs_tol, float rel_tol,
-                           float sqrtp, const float* z, const float* norms, int32_t* slot_j,
-                           const int32_t* slot_jend, int32_t* slot_it, uint8_t* live, double* beta,
-                           int32_t* iters, uint8_t* conv, uint64_t* family, int32_t W,
-                           int32_t* live_count, const float* cn, float* vs_next, const float* u,
-                           const double* lambdas, unsigned long long* near_count)
+struct XtCheck {
+    int32_t G, q, r, p, nchains, RT, warm, max_iter;
+    float rho, abs_tol, rel_tol, sqrtp;
+    const float* z;
+    const float* norms;
+    int32_t* slot_j;
+    const int32_t* slot_jend;
+    int32_t* slot_it;
+    uint8_t* live;
+    double* beta;
+    int32_t* iters;
+    uint8_t* conv;
+    uint64_t* family;
+    int32_t W;
+    int32_t* live_count;          // incremented once per slot still iterating
+    const float* cn;
+    float* vs_next;
+    const float* u;
+    const double* lambdas;
+    unsigned long long* near_count;
+};
+
+// Slot sl of one problem, by one warp.
+__device__ __forceinline__ void xt_check_slot(const XtCheck& ca, int64_t sl, int lane)
 {
-    const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int32_t G = ca.G, q = ca.q, r = ca.r, p = ca.p, nchains = ca.nchains, RT = ca.RT, warm = ca.warm,
+                  max_iter = ca.max_iter, W = ca.W;
+    const float rho = ca.rho, abs_tol = ca.abs_tol, rel_tol = ca.rel_tol, sqrtp = ca.sqrtp;
+    const float* z = ca.z;
+    const float* norms = ca.norms;
+    int32_t* slot_j = ca.slot_j;
+    const int32_t* slot_jend = ca.slot_jend;
+    int32_t* slot_it = ca.slot_it;
+    uint8_t* live = ca.live;
+    double* beta = ca.beta;
+    int32_t* iters = ca.iters;
+    uint8_t* conv = ca.conv;
+    uint64_t* family = ca.family;
+    int32_t* live_count = ca.live_count;
+    const float* cn = ca.cn;
+    float* vs_next = ca.vs_next;
+    const float* u = ca.u;
+    const double* lambdas = ca.lambdas;
+    unsigned long long* near_count = ca.near_count;
     if (sl >= (int64_t)G * nchains || !live[sl]) return;
     float tot[5] = { 0.f, 0.f, 0.f, 0.f, 0.f };
     for (int t0 = 0; t0 < RT; t0 += 32) {
@@ -610,6 +661,83 @@ __global__ void k_xt_check(int32_t G, int32_t q, int32_t r, int32_t p, int32_t n
     }
 }
 
+__global__ void k_xt_check(XtCheck ca)
+{
+    xt_check_slot(ca, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
+}
+
+// ---- grouped form: many problems' solves in the same launches ----------------------
+//
+// A batch of independent problems (different p, groups, right-hand sides) iterates
+// together: each step is one x-update launch over the live (problem, group, row
+// tile, chain tile) items of every problem and one check launch over the live
+// chain tiles of every problem.  A problem's tensor maps and arguments sit in a
+// device table (XtMemberDev) that the kernels index by the item's problem; the
+// arithmetic of an item is the single-problem kernel's, so each problem's iterates
+// are those of its own solve.
+
+struct XtItem {
+    int32_t member, g, rt, ct;
+};
+
+struct __align__(64) XtMemberDev {
+    CUtensorMap mM;               // the problem's split inverse
+    CUtensorMap mV[2];            // V pieces read on even / odd steps
+    XtArgs args[2];               // x-update arguments of even / odd steps
+    XtCheck check[2];             // check arguments after even / odd steps
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(XT_THREADS, STAGES <= 4 ? 2 : 1)
+k_xupdate_tc_grouped(const XtMemberDev* mem, const XtItem* items, const int32_t* nitems, int32_t parity)
+{
+    if ((int)blockIdx.x >= *nitems) return;
+    const XtItem it = items[blockIdx.x];
+    const XtMemberDev& m = mem[it.member];
+    // the arguments in shared memory: read there, they cannot alias the tile's stores
+    __shared__ XtArgs sa;
+    if (threadIdx.x == 0) sa = m.args[parity];
+    __syncthreads();
+    xupdate_tile<STAGES>(&m.mM, &m.mV[parity], sa, it.rt, it.ct, it.g);
+}
+
+constexpr int XT_CHECK_WARPS = 16;
+
+// One block per live chain tile (an item with rt = 0 stands for its tile); warp w
+// checks the tile's chains w, w + 16, ...
+__global__ void __launch_bounds__(32 * XT_CHECK_WARPS)
+k_xt_check_tiles(const XtMemberDev* mem, const XtItem* tiles, const int32_t* ntiles, int32_t parity)
+{
+    if ((int)blockIdx.x >= *ntiles) return;
+    const XtItem t = tiles[blockIdx.x];
+    const XtMemberDev& m = mem[t.member];
+    const int NT = m.args[0].NT, nchains = m.args[0].nchains;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = warp; c < NT; c += XT_CHECK_WARPS) {
+        const int chain = t.ct * NT + c;
+        if (chain >= nchains) break;
+        xt_check_slot(m.check[parity], (int64_t)t.g * nchains + chain, lane);
+    }
+}
+
+// The items whose chain tile still has a live chain, and those tiles (one thread
+// per item; the order of the lists is unspecified: items are independent).
+__global__ void k_xt_items(const XtMemberDev* mem, const XtItem* all, int64_t nall, XtItem* out, int32_t* nout,
+                           XtItem* tiles, int32_t* ntiles)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nall) return;
+    const XtItem it = all[t];
+    const XtArgs& a = mem[it.member].args[0];
+    const int64_t s0 = (int64_t)it.g * a.nchains + (int64_t)it.ct * a.NT;
+    const int cend = min(a.NT, a.nchains - it.ct * a.NT);
+    bool any = false;
+    for (int c = 0; c < cend && !any; ++c) any = a.live[s0 + c] != 0;
+    if (!any) return;
+    out[atomicAdd(nout, 1)] = it;
+    if (it.rt == 0) tiles[atomicAdd(ntiles, 1)] = it;
+}
+
 // List of the (group, chain tile) pairs with a live chain (order unspecified:
 // tiles are independent), one thread per pair.
 __global__ void k_xt_tiles(int32_t G, int32_t nchains, int32_t NT, int32_t nct, const uint8_t* live,
@@ -640,137 +768,613 @@ __global__ void k_xt_slots(int32_t G, int32_t nchains, int32_t r, int32_t q, int
 
 bool admm_tc_available() { return gram_tc_available(); }
 
+namespace {
+
+// Host state of one problem's streaming ADMM on the tensor cores: geometry,
+// device buffers and the tensor map of its split inverse.
+struct XtMember {
+    AdmmProblem<float> P;
+    int32_t nchains = 0, p = 0, RT = 0, kst = 0, W = 0;
+    int64_t slots = 0, ppad = 0, kpad = 0;
+    DevBuf rs, rinv, mp, zb, ub, v0, v1, vs0, vs1, cn, nb, sj, sje, sit, live;
+    CUtensorMap mM;
+};
+
+// Everything before the first iteration: row scales and fp16 pieces of M, the
+// initial state and its V pieces, the per-slot path positions.
+void xt_prepare(const AdmmProblem<float>& P, cudaStream_t s, XtMember& m)
+{
+    m.P = P;
+    m.nchains = P.warm ? (int32_t)P.r : (int32_t)(P.r * P.q);
+    m.slots = (int64_t)P.G * m.nchains;
+    m.p = (int)P.p;
+    m.ppad = ceil_div(m.p, XT_TM) * XT_TM;
+    m.kpad = ceil_div(m.p, XT_TK) * XT_TK;
+    m.RT = (int)(m.ppad / XT_TM);
+    m.kst = (int)(m.kpad / XT_TK);
+    m.W = (int)((m.p + 63) / 64);
+    const int p = m.p;
+    const int64_t ppad = m.ppad, kpad = m.kpad, slots = m.slots;
+    m.rs.alloc(sizeof(float) * (size_t)P.G * ppad, s);
+    m.rinv.alloc(sizeof(float) * (size_t)P.G * ppad, s);
+    k_row_scale<<<(unsigned)ceil_div((int64_t)P.G * ppad * 32, 256), 256, 0, s>>>(P.M, P.G, p, ppad,
+                                                                                m.rs.as<float>(), m.rinv.as<float>());
+    UOI_CHECK_LAUNCH();
+    m.mp.alloc(sizeof(__half) * XT_PIECES * (size_t)P.G * ppad * kpad, s);
+    k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad / 8, 256), 8192), 256, 0, s>>>(
+        P.M, P.G, p, ppad, kpad, m.rs.as<float>(), m.mp.as<__half>());
+    UOI_CHECK_LAUNCH();
+    m.zb.alloc(sizeof(float) * (size_t)slots * p, s);
+    m.ub.alloc(sizeof(float) * (size_t)slots * p, s);
+    m.v0.alloc(sizeof(__half) * XT_PIECES * (size_t)slots * kpad, s);
+    m.v1.alloc(sizeof(__half) * XT_PIECES * (size_t)slots * kpad, s);
+    m.vs0.alloc(sizeof(float) * (size_t)slots, s);
+    m.vs1.alloc(sizeof(float) * (size_t)slots, s);
+    m.cn.alloc(sizeof(float) * (size_t)P.G * P.r, s);
+    m.nb.alloc(sizeof(float) * (size_t)slots * m.RT * 5, s);
+    m.sj.alloc(sizeof(int32_t) * slots, s);
+    m.sje.alloc(sizeof(int32_t) * slots, s);
+    m.sit.alloc(sizeof(int32_t) * slots, s);
+    m.live.alloc(slots, s);
+    const bool start = P.z0 && !P.warm;
+    k_c_norms<<<(unsigned)ceil_div((int64_t)P.G * P.r * 32, 256), 256, 0, s>>>(P.c, (int64_t)P.G * P.r, p,
+                                                                               m.cn.as<float>());
+    UOI_CHECK_LAUNCH();
+    k_xt_vscale_init<<<(unsigned)ceil_div(slots * 32, 256), 256, 0, s>>>(
+        slots, p, m.nchains, (int32_t)P.r, P.warm, start ? P.z0 : nullptr, start ? P.u0 : nullptr,
+        m.cn.as<float>(), m.vs0.as<float>(), m.vs1.as<float>());
+    UOI_CHECK_LAUNCH();
+    k_xt_init<<<(unsigned)std::min<int64_t>(ceil_div(slots * kpad, 256), 8192), 256, 0, s>>>(
+        slots, p, kpad, start ? P.z0 : nullptr, start ? P.u0 : nullptr, m.vs0.as<float>(), m.zb.as<float>(),
+        m.ub.as<float>(), m.v0.as<__half>(), m.live.as<uint8_t>());
+    UOI_CHECK_LAUNCH();
+    // v1 holds the pieces of V for slots that do not change in an iteration
+    UOI_CUDA(cudaMemcpyAsync(m.v1.ptr, m.v0.ptr, m.v0.bytes, cudaMemcpyDeviceToDevice, s));
+    k_xt_slots<<<(unsigned)std::min<int64_t>(ceil_div(slots, 256), 4096), 256, 0, s>>>(
+        P.G, m.nchains, (int32_t)P.r, P.q, P.warm, m.sj.as<int32_t>(), m.sje.as<int32_t>(), m.sit.as<int32_t>());
+    UOI_CHECK_LAUNCH();
+    count_launch(6);
+    m.mM = make_map_bf16_blocks32(m.mp.ptr, (int64_t)P.G * m.RT * m.kst * XT_PIECES, XT_PIECES,
+                                  CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+}
+
+// The V pieces an x-update reads on even (parity 0) or odd steps, in boxes of NT chains.
+CUtensorMap xt_map_v(const XtMember& m, int parity, int NT)
+{
+    return make_map_bf16_k32((parity ? m.v1 : m.v0).ptr, m.kpad, m.slots, XT_PIECES, NT,
+                             CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+}
+
+// Arguments of the x-update on even (parity 0) or odd steps: read V_t with its
+// scale, write V_{t+1} into the other buffer.
+XtArgs xt_args(const XtMember& m, int parity, int NT, int32_t* err)
+{
+    const AdmmProblem<float>& P = m.P;
+    XtArgs a;
+    a.G = P.G; a.q = P.q; a.r = (int32_t)P.r; a.p = m.p; a.nchains = m.nchains; a.NT = NT; a.kst = m.kst;
+    a.RT = m.RT; a.warm = P.warm; a.ppad = m.ppad; a.kpad = m.kpad; a.slots = m.slots;
+    a.c = P.c; a.lambdas = P.lambdas; a.rho = (float)P.rho;
+    a.z = m.zb.as<float>(); a.u = m.ub.as<float>();
+    a.vnext = (parity ? m.v0 : m.v1).as<__half>();
+    a.row_inv = m.rinv.as<float>();
+    a.vs_r = (parity ? m.vs1 : m.vs0).as<float>();
+    a.vs_w = (parity ? m.vs0 : m.vs1).as<float>();
+    a.slot_j = m.sj.as<int32_t>(); a.live = m.live.as<uint8_t>(); a.norms = m.nb.as<float>();
+    a.err = err;
+    a.tiles = nullptr;
+    a.ntiles = nullptr;
+    a.nct = (int32_t)ceil_div(m.nchains, NT);
+    return a;
+}
+
+// Arguments of the convergence check after an even (parity 0) or odd step.
+XtCheck xt_check_args(const XtMember& m, int parity, int32_t* live_count)
+{
+    const AdmmProblem<float>& P = m.P;
+    XtCheck ca;
+    ca.G = P.G; ca.q = P.q; ca.r = (int32_t)P.r; ca.p = m.p; ca.nchains = m.nchains; ca.RT = m.RT;
+    ca.warm = P.warm; ca.max_iter = P.max_iter;
+    ca.rho = (float)P.rho; ca.abs_tol = (float)P.abs_tol; ca.rel_tol = (float)P.rel_tol;
+    ca.sqrtp = (float)sqrt((double)m.p);
+    ca.z = m.zb.as<float>(); ca.norms = m.nb.as<float>();
+    ca.slot_j = m.sj.as<int32_t>(); ca.slot_jend = m.sje.as<int32_t>(); ca.slot_it = m.sit.as<int32_t>();
+    ca.live = m.live.as<uint8_t>(); ca.beta = P.beta; ca.iters = P.iters; ca.conv = P.conv;
+    ca.family = P.family; ca.W = m.W; ca.live_count = live_count; ca.cn = m.cn.as<float>();
+    ca.vs_next = (parity ? m.vs1 : m.vs0).as<float>(); ca.u = m.ub.as<float>(); ca.lambdas = P.lambdas;
+    ca.near_count = P.near_count;
+    return ca;
+}
+
+}  // namespace
+
 // Streaming ADMM with the tensor-core x-update (FP32 state).  Same outputs as
 // admm_solve<float>.
 void admm_solve_tc(const AdmmProblem<float>& P, cudaStream_t s)
 {
-    const int32_t nchains = P.warm ? (int32_t)P.r : (int32_t)(P.r * P.q);
-    const int64_t slots = (int64_t)P.G * nchains;
-    const int p = (int)P.p;
-    const int64_t ppad = ceil_div(p, XT_TM) * XT_TM;
-    const int64_t kpad = ceil_div(p, XT_TK) * XT_TK;
-    const int RT = (int)(ppad / XT_TM);
+    XtMember m;
+    xt_prepare(P, s, m);
+    const int32_t nchains = m.nchains;
     const int NT = (int)std::min<int64_t>(XT_NT_MAX, ceil_div(nchains, 16) * 16);
-    const int kst = (int)(kpad / XT_TK);
-    DevBuf rs(sizeof(float) * (size_t)P.G * ppad, s), rinv(sizeof(float) * (size_t)P.G * ppad, s);
-    k_row_scale<<<(unsigned)ceil_div((int64_t)P.G * ppad * 32, 256), 256, 0, s>>>(P.M, P.G, p, ppad,
-                                                                                rs.as<float>(), rinv.as<float>());
-    UOI_CHECK_LAUNCH();
-    DevBuf mp(sizeof(__half) * XT_PIECES * (size_t)P.G * ppad * kpad, s);
-    k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad / 8, 256), 8192), 256, 0, s>>>(
-        P.M, P.G, p, ppad, kpad, rs.as<float>(), mp.as<__half>());
-    UOI_CHECK_LAUNCH();
-    DevBuf zb(sizeof(float) * (size_t)slots * p, s), ub(sizeof(float) * (size_t)slots * p, s);
-    DevBuf v0(sizeof(__half) * XT_PIECES * (size_t)slots * kpad, s);
-    DevBuf v1(sizeof(__half) * XT_PIECES * (size_t)slots * kpad, s);
-    DevBuf vs0(sizeof(float) * (size_t)slots, s), vs1(sizeof(float) * (size_t)slots, s);
-    DevBuf cn(sizeof(float) * (size_t)P.G * P.r, s);
-    DevBuf nb(sizeof(float) * (size_t)slots * RT * 5, s);
-    DevBuf sj(sizeof(int32_t) * slots, s), sje(sizeof(int32_t) * slots, s), sit(sizeof(int32_t) * slots, s);
-    DevBuf live(slots, s), cnt(sizeof(int32_t), s), err(sizeof(int32_t), s);
+    DevBuf cnt(sizeof(int32_t), s), err(sizeof(int32_t), s);
     UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
-    const bool start = P.z0 && !P.warm;
-    k_c_norms<<<(unsigned)ceil_div((int64_t)P.G * P.r * 32, 256), 256, 0, s>>>(P.c, (int64_t)P.G * P.r, p,
-                                                                               cn.as<float>());
-    UOI_CHECK_LAUNCH();
-    k_xt_vscale_init<<<(unsigned)ceil_div(slots * 32, 256), 256, 0, s>>>(
-        slots, p, nchains, (int32_t)P.r, P.warm, start ? P.z0 : nullptr, start ? P.u0 : nullptr,
-        cn.as<float>(), vs0.as<float>(), vs1.as<float>());
-    UOI_CHECK_LAUNCH();
-    k_xt_init<<<(unsigned)std::min<int64_t>(ceil_div(slots * kpad, 256), 8192), 256, 0, s>>>(
-        slots, p, kpad, start ? P.z0 : nullptr, start ? P.u0 : nullptr, vs0.as<float>(), zb.as<float>(),
-        ub.as<float>(), v0.as<__half>(), live.as<uint8_t>());
-    UOI_CHECK_LAUNCH();
-    // v1 holds the pieces of V for slots that do not change in an iteration
-    UOI_CUDA(cudaMemcpyAsync(v1.ptr, v0.ptr, v0.bytes, cudaMemcpyDeviceToDevice, s));
-    k_xt_slots<<<(unsigned)std::min<int64_t>(ceil_div(slots, 256), 4096), 256, 0, s>>>(
-        P.G, nchains, (int32_t)P.r, P.q, P.warm, sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>());
-    UOI_CHECK_LAUNCH();
-    count_launch(6);
-    const CUtensorMap mM = make_map_bf16_blocks32(mp.ptr, (int64_t)P.G * RT * kst * XT_PIECES, XT_PIECES,
-                                                   CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-    const CUtensorMap mV0 = make_map_bf16_k32(v0.ptr, kpad, slots, XT_PIECES, NT, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-    const CUtensorMap mV1 = make_map_bf16_k32(v1.ptr, kpad, slots, XT_PIECES, NT, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const CUtensorMap mV0 = xt_map_v(m, 0, NT), mV1 = xt_map_v(m, 1, NT);
     UOI_CUDA(cudaFuncSetAttribute(k_xupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM));
-    XtArgs a;
-    a.G = P.G; a.q = P.q; a.r = (int32_t)P.r; a.p = p; a.nchains = nchains; a.NT = NT; a.kst = kst;
-    a.RT = RT; a.warm = P.warm; a.ppad = ppad; a.kpad = kpad; a.slots = slots;
-    a.c = P.c; a.lambdas = P.lambdas; a.rho = (float)P.rho;
-    a.z = zb.as<float>(); a.u = ub.as<float>();
-    a.row_inv = rinv.as<float>();
-    a.slot_j = sj.as<int32_t>(); a.live = live.as<uint8_t>(); a.norms = nb.as<float>();
-    a.err = err.as<int32_t>();
-    const int32_t nct = (int32_t)ceil_div(nchains, NT);
+    XtArgs ae = xt_args(m, 0, NT, err.as<int32_t>()), ao = xt_args(m, 1, NT, err.as<int32_t>());
+    const XtCheck ce = xt_check_args(m, 0, cnt.as<int32_t>()), co = xt_check_args(m, 1, cnt.as<int32_t>());
+    const int32_t nct = ae.nct;
     // wide right-hand sides: launch only the tiles that still have a live chain
     const bool use_list = nct >= 4 && (int64_t)P.G * nct <= 65535;
     DevBuf tlist, tcount;
     int64_t tiles_bound = (int64_t)P.G * nct;
-    a.nct = nct;
-    a.tiles = nullptr;
-    a.ntiles = nullptr;
     if (use_list) {
         tlist.alloc(sizeof(int32_t) * (size_t)P.G * nct, s);
         tcount.alloc(sizeof(int32_t), s);
         UOI_CUDA(cudaMemsetAsync(tcount.ptr, 0, sizeof(int32_t), s));
         k_xt_tiles<<<(unsigned)ceil_div((int64_t)P.G * nct, 256), 256, 0, s>>>(
-            P.G, nchains, NT, nct, live.as<uint8_t>(), tlist.as<int32_t>(), tcount.as<int32_t>());
+            P.G, nchains, NT, nct, m.live.as<uint8_t>(), tlist.as<int32_t>(), tcount.as<int32_t>());
         UOI_CHECK_LAUNCH();
         count_launch();
-        a.tiles = tlist.as<int32_t>();
-        a.ntiles = tcount.as<int32_t>();
+        ae.tiles = ao.tiles = tlist.as<int32_t>();
+        ae.ntiles = ao.ntiles = tcount.as<int32_t>();
     }
-    const dim3 gc((unsigned)ceil_div(slots * 32, 256));
+    const dim3 gc((unsigned)ceil_div(m.slots * 32, 256));
     int32_t* host_cnt = pinned_scratch_i32();
     const int64_t bound = (int64_t)(P.warm ? P.q : 1) * P.max_iter + 2;
-    const int W = (int)((p + 63) / 64);
     bool done = false;
-    try {
-        for (int64_t it = 0; it < bound && !done; ++it) {
-            const bool even = (it & 1) == 0;
-            // read V_t (buffer 0 on even steps) with its scale, write V_{t+1} into the other
-            a.vnext = (even ? v1 : v0).as<__half>();
-            a.vs_r = (even ? vs0 : vs1).as<float>();
-            a.vs_w = (even ? vs1 : vs0).as<float>();
-            UOI_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int32_t), s));
-            ktimer_begin(TK_XUPDATE, s);
-            const dim3 grid = use_list ? dim3((unsigned)RT, (unsigned)std::max<int64_t>(1, tiles_bound), 1u)
-                                       : dim3((unsigned)RT, (unsigned)nct, (unsigned)P.G);
-            k_xupdate_tc<<<grid, XT_THREADS, XT_SMEM, s>>>(mM, even ? mV0 : mV1, a);
+    for (int64_t it = 0; it < bound && !done; ++it) {
+        const bool even = (it & 1) == 0;
+        UOI_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int32_t), s));
+        ktimer_begin(TK_XUPDATE, s);
+        const dim3 grid = use_list ? dim3((unsigned)m.RT, (unsigned)std::max<int64_t>(1, tiles_bound), 1u)
+                                   : dim3((unsigned)m.RT, (unsigned)nct, (unsigned)P.G);
+        k_xupdate_tc<<<grid, XT_THREADS, XT_SMEM, s>>>(m.mM, even ? mV0 : mV1, even ? ae : ao);
+        UOI_CHECK_LAUNCH();
+        ktimer_end(TK_XUPDATE, s, 0.0, 0.0);
+        k_xt_check<<<gc, 256, 0, s>>>(even ? ce : co);
+        UOI_CHECK_LAUNCH();
+        count_launch(2);
+        if (use_list) {
+            UOI_CUDA(cudaMemsetAsync(tcount.ptr, 0, sizeof(int32_t), s));
+            k_xt_tiles<<<(unsigned)ceil_div((int64_t)P.G * nct, 256), 256, 0, s>>>(
+                P.G, nchains, NT, nct, m.live.as<uint8_t>(), tlist.as<int32_t>(), tcount.as<int32_t>());
             UOI_CHECK_LAUNCH();
-            ktimer_end(TK_XUPDATE, s, 0.0, 0.0);
-            k_xt_check<<<gc, 256, 0, s>>>(P.G, P.q, (int32_t)P.r, p, nchains, RT, P.warm, P.max_iter,
-                                          (float)P.rho, (float)P.abs_tol, (float)P.rel_tol,
-                                          (float)sqrt((double)p), zb.as<float>(), nb.as<float>(),
-                                          sj.as<int32_t>(), sje.as<int32_t>(), sit.as<int32_t>(),
-                                          live.as<uint8_t>(), P.beta, P.iters, P.conv, P.family, W,
-                                          cnt.as<int32_t>(), cn.as<float>(),
-                                          (even ? vs0 : vs1).as<float>(), ub.as<float>(), P.lambdas,
-                                          P.near_count);
-            UOI_CHECK_LAUNCH();
-            count_launch(2);
-            if (use_list) {
-                UOI_CUDA(cudaMemsetAsync(tcount.ptr, 0, sizeof(int32_t), s));
-                k_xt_tiles<<<(unsigned)ceil_div((int64_t)P.G * nct, 256), 256, 0, s>>>(
-                    P.G, nchains, NT, nct, live.as<uint8_t>(), tlist.as<int32_t>(), tcount.as<int32_t>());
-                UOI_CHECK_LAUNCH();
-                count_launch();
-            }
-            if ((it + 1) % 8 == 0 || it + 1 == bound) {
-                int32_t herr = 0;
-                UOI_CUDA(cudaMemcpyAsync(host_cnt, cnt.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-                if (use_list)
-                    UOI_CUDA(cudaMemcpyAsync(host_cnt + 1, tcount.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-                UOI_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-                UOI_CUDA(cudaStreamSynchronize(s));
-                if (herr) throw Error(herr, "tensor-core x-update: a bounded pipeline wait expired");
-                done = *host_cnt == 0;
-                if (use_list) tiles_bound = host_cnt[1];       // tiles only die: a bound for later steps
-            }
+            count_launch();
         }
-    } catch (...) {
-        throw;
+        if ((it + 1) % 8 == 0 || it + 1 == bound) {
+            int32_t herr = 0;
+            UOI_CUDA(cudaMemcpyAsync(host_cnt, cnt.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            if (use_list)
+                UOI_CUDA(cudaMemcpyAsync(host_cnt + 1, tcount.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            UOI_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            UOI_CUDA(cudaStreamSynchronize(s));
+            if (herr) throw Error(herr, "tensor-core x-update: a bounded pipeline wait expired");
+            done = *host_cnt == 0;
+            if (use_list) tiles_bound = host_cnt[1];       // tiles only die: a bound for later steps
+        }
     }
     if (!done) throw Error(UOI_ERR_TIMEOUT, "ADMM loop exceeded its iteration bound");
+}
+
+// ---- grouped solve of a batch of problems -------------------------------------------
+
+namespace {
+
+// Tile choices of the grouped solve, picked by timing: the chain tile NT (chains
+// per CTA, hence how often a row tile of M is streamed per step) and the ring
+// depth (4 stages at two CTAs per SM, or 6 at one).  Each candidate runs one
+// replay of real iterations (every candidate gives the same iterates); the score
+// is the replay's wall time per live item at its start.  The winner is kept per
+// batch shape for the life of the process.
+struct XtTileChoice {
+    int NT = 32;
+    int stages = 4;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, XtTileChoice>& tune_cache()
+{
+    static std::map<std::string, XtTileChoice> c;
+    return c;
+}
+
+constexpr int XT_CHUNK = 8;            // steps per graph replay (even: each replay starts on parity 0)
+
+template <int STAGES>
+constexpr int xt_smem() { return STAGES * XT_STAGE_MAX + 1024; }
+
+}  // namespace
+
+// A batch of problems whose tensor-core ADMM solves iterate together.  Members
+// join from their own threads once their state is prepared; a solver thread,
+// started by the first join, adds the members that have joined at every replay
+// boundary, replays XT_CHUNK steps of all of them as one CUDA graph (grouped
+// x-update and check launches), and releases each member as soon as none of its
+// columns is still iterating, so that its thread goes on with the estimation while
+// the others iterate.  Released members' device state stays in the table (their
+// slots are no longer live, so no kernel touches their buffers) until the batch
+// ends.
+struct AdmmBatch {
+    struct Slot {
+        std::unique_ptr<XtMember> m;
+        bool done = false;
+        int32_t status = 0;
+        std::string error;
+        double ms = 0.0;            // replay time credited to this member
+        int64_t launches = 0;       // launches credited to this member
+    };
+
+    AdmmBatch(int32_t expected, int device) : expected(expected), device(device) {}
+    ~AdmmBatch()
+    {
+        if (solver.joinable()) solver.join();    // ends once every member has arrived and finished
+    }
+
+    std::mutex mu;
+    std::condition_variable cv_members, cv_solver;
+    int32_t expected, arrived = 0;
+    int device;
+    std::vector<Slot*> incoming;                 // joined, not yet in the solver's table
+    std::vector<std::unique_ptr<Slot>> held;     // released members, kept until the batch ends
+    std::thread solver;
+    bool started = false;
+
+    void hold(std::unique_ptr<Slot> sl)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        held.push_back(std::move(sl));
+    }
+
+    void arrive_locked(Slot* slot)
+    {
+        ++arrived;
+        if (slot) {
+            incoming.push_back(slot);
+            if (!started) {
+                started = true;
+                solver = std::thread([this] { run(); });
+            }
+        }
+        cv_solver.notify_one();
+    }
+
+    void release(Slot* sl, int32_t st, const std::string& msg)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        sl->status = st;
+        sl->error = msg;
+        sl->done = true;
+        cv_members.notify_all();
+    }
+
+    void run();
+};
+
+namespace {
+
+// The solver's device-side table of the members and their work items.  Counters
+// (device, and their pinned copy): [0, cap) live slots per member, cap live items,
+// cap + 1 live chain tiles, cap + 2 error.
+struct GroupTable {
+    std::vector<AdmmBatch::Slot*> slots;    // members in join order (index = table row)
+    std::vector<bool> released;
+    DevBuf d_mem, d_all, d_live, d_tiles, d_ctr;
+    std::vector<XtMemberDev> hmem;
+    int64_t nall = 0;
+    int32_t cap = 0;
+    int32_t* host = nullptr;
+    int NT = 0;
+    int32_t* ctr() const { return d_ctr.as<int32_t>(); }
+
+    // Rebuilds the table and the item list for chain tile NT, then the live lists.
+    void build(int nt, cudaStream_t s)
+    {
+        NT = nt;
+        const int32_t n = (int32_t)slots.size();
+        hmem.resize((size_t)n);
+        std::vector<XtItem> items;
+        for (int32_t i = 0; i < n; ++i) {
+            const XtMember& m = *slots[(size_t)i]->m;
+            const int t = (int)std::min<int64_t>(nt, ceil_div(m.nchains, 16) * 16);
+            XtMemberDev& d = hmem[(size_t)i];
+            d.mM = m.mM;
+            for (int par = 0; par < 2; ++par) {
+                d.mV[par] = xt_map_v(m, par, t);
+                d.args[par] = xt_args(m, par, t, ctr() + cap + 2);
+                d.check[par] = xt_check_args(m, par, ctr() + i);
+            }
+            if (released[(size_t)i]) continue;           // its items are all dead
+            const int nct = (int)ceil_div(m.nchains, t);
+            for (int g = 0; g < m.P.G; ++g)
+                for (int ct = 0; ct < nct; ++ct)
+                    for (int rt = 0; rt < m.RT; ++rt) items.push_back(XtItem{ i, g, rt, ct });
+        }
+        d_mem.alloc(sizeof(XtMemberDev) * (size_t)std::max(1, n), s);
+        UOI_CUDA(cudaMemcpyAsync(d_mem.ptr, hmem.data(), sizeof(XtMemberDev) * (size_t)n, cudaMemcpyHostToDevice, s));
+        nall = (int64_t)items.size();
+        d_all.alloc(sizeof(XtItem) * (size_t)std::max<int64_t>(1, nall), s);
+        d_live.alloc(sizeof(XtItem) * (size_t)std::max<int64_t>(1, nall), s);
+        d_tiles.alloc(sizeof(XtItem) * (size_t)std::max<int64_t>(1, nall), s);
+        if (nall > 0)
+            UOI_CUDA(cudaMemcpyAsync(d_all.ptr, items.data(), sizeof(XtItem) * (size_t)nall, cudaMemcpyHostToDevice, s));
+        UOI_CUDA(cudaMemsetAsync(ctr() + cap, 0, 2 * sizeof(int32_t), s));
+        if (nall > 0) {
+            k_xt_items<<<(unsigned)ceil_div(nall, 256), 256, 0, s>>>(d_mem.as<XtMemberDev>(), d_all.as<XtItem>(), nall,
+                                                                      d_live.as<XtItem>(), ctr() + cap,
+                                                                      d_tiles.as<XtItem>(), ctr() + cap + 1);
+            UOI_CHECK_LAUNCH();
+        }
+        UOI_CUDA(cudaMemcpyAsync(host + cap, ctr() + cap, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        UOI_CUDA(cudaStreamSynchronize(s));
+    }
+};
+
+struct GroupGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t grid = 0, tgrid = 0;
+    XtTileChoice cfg;
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        grid = tgrid = 0;
+    }
+    ~GroupGraph() { reset(); }
+
+    // XT_CHUNK steps of every member in the table (grids bounded by the live items
+    // and tiles at capture; lists only shrink), then the next live lists and the
+    // counters' copy to the host.
+    void capture(GroupTable& T, const XtTileChoice& c, int64_t g, int64_t tg, cudaStream_t s)
+    {
+        reset();
+        int32_t* ctr = T.ctr();
+        UOI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < XT_CHUNK; ++k) {
+            const int par = k & 1;
+            cudaMemsetAsync(ctr, 0, sizeof(int32_t) * (size_t)T.cap, s);
+            if (c.stages == 4)
+                k_xupdate_tc_grouped<4><<<(unsigned)g, XT_THREADS, xt_smem<4>(), s>>>(
+                    T.d_mem.as<XtMemberDev>(), T.d_live.as<XtItem>(), ctr + T.cap, par);
+            else
+                k_xupdate_tc_grouped<6><<<(unsigned)g, XT_THREADS, xt_smem<6>(), s>>>(
+                    T.d_mem.as<XtMemberDev>(), T.d_live.as<XtItem>(), ctr + T.cap, par);
+            k_xt_check_tiles<<<(unsigned)tg, 32 * XT_CHECK_WARPS, 0, s>>>(T.d_mem.as<XtMemberDev>(),
+                                                                          T.d_tiles.as<XtItem>(), ctr + T.cap + 1, par);
+        }
+        cudaMemsetAsync(ctr + T.cap, 0, 2 * sizeof(int32_t), s);
+        k_xt_items<<<(unsigned)std::max<int64_t>(1, ceil_div(T.nall, 256)), 256, 0, s>>>(
+            T.d_mem.as<XtMemberDev>(), T.d_all.as<XtItem>(), T.nall, T.d_live.as<XtItem>(), ctr + T.cap,
+            T.d_tiles.as<XtItem>(), ctr + T.cap + 1);
+        cudaMemcpyAsync(T.host, ctr, sizeof(int32_t) * (size_t)(T.cap + 3), cudaMemcpyDeviceToHost, s);
+        const cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess)
+            throw Error(UOI_ERR_CUDA, std::string("graph capture of the grouped ADMM: ") + cudaGetErrorString(e));
+        UOI_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        grid = g;
+        tgrid = tg;
+        cfg = c;
+    }
+};
+
+}  // namespace
+
+void AdmmBatch::run()
+{
+    cudaSetDevice(device);
+    cudaStream_t s = nullptr;
+    int32_t fail = 0;
+    std::string fail_msg;
+    GroupTable T;
+    GroupGraph gg;
+    try {
+        UOI_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        static std::once_flag once;
+        std::call_once(once, [] {
+            UOI_CUDA(cudaFuncSetAttribute(k_xupdate_tc_grouped<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          xt_smem<4>()));
+            UOI_CUDA(cudaFuncSetAttribute(k_xupdate_tc_grouped<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          xt_smem<6>()));
+        });
+        T.cap = expected;
+        T.d_ctr.alloc(sizeof(int32_t) * (size_t)(T.cap + 3), s);
+        UOI_CUDA(cudaMemsetAsync(T.d_ctr.ptr, 0, T.d_ctr.bytes, s));
+        UOI_CUDA(cudaMallocHost(&T.host, sizeof(int32_t) * (size_t)(T.cap + 3)));
+    } catch (const Error& e) {
+        fail = e.status;
+        fail_msg = e.what();
+    }
+    std::vector<XtTileChoice> cands;
+    std::vector<double> score;
+    size_t next_cand = 0;
+    bool tuned = false;
+    XtTileChoice best;
+    std::string key;
+    int active = 0;                    // members in the table not yet released
+    for (;;) {
+        std::vector<Slot*> fresh;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_solver.wait(lk, [&] { return !incoming.empty() || active > 0 || arrived == expected; });
+            fresh.swap(incoming);
+            if (fresh.empty() && active == 0 && arrived == expected) break;
+        }
+        if (fail) {
+            for (Slot* sl : fresh) {
+                T.slots.push_back(sl);             // its buffers are freed with the others below
+                T.released.push_back(true);
+                release(sl, fail, fail_msg);
+            }
+            continue;
+        }
+        try {
+            if (!fresh.empty()) {
+                for (Slot* sl : fresh) {
+                    T.slots.push_back(sl);
+                    T.released.push_back(false);
+                }
+                active += (int)fresh.size();
+                if (key.empty()) {
+                    // the batch shape as the first member gives it
+                    const AdmmProblem<float>& P = T.slots[0]->m->P;
+                    key = std::to_string(expected) + "/" + std::to_string(P.G) + "/" + std::to_string(P.q) + "/" +
+                          std::to_string(P.r) + "/" + std::to_string(P.warm);
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    auto f = tune_cache().find(key);
+                    if (f != tune_cache().end()) { best = f->second; tuned = true; }
+                    const int ntmax = (int)std::min<int64_t>(XT_NT_MAX, ceil_div(T.slots[0]->m->nchains, 16) * 16);
+                    for (int nt = 16; nt <= ntmax; nt *= 2)
+                        for (int st : { 4, 6 }) cands.push_back(XtTileChoice{ nt, st });
+                    if (cands.empty()) cands.push_back(XtTileChoice{ 16, 4 });
+                    score.assign(cands.size(), 0.0);
+                }
+                T.NT = 0;                                   // table rebuilt below
+            }
+            const bool trial = !tuned && next_cand < cands.size();
+            const XtTileChoice c = trial ? cands[next_cand] : best;
+            if (T.NT != c.NT) {
+                T.build(c.NT, s);
+                gg.reset();
+            }
+            const int64_t grid = std::max<int32_t>(1, T.host[T.cap]), tgrid = std::max<int32_t>(1, T.host[T.cap + 1]);
+            if (!gg.exec || gg.cfg.NT != c.NT || gg.cfg.stages != c.stages || grid > gg.grid || tgrid > gg.tgrid ||
+                2 * grid < gg.grid)
+                gg.capture(T, c, grid, tgrid, s);
+            const int32_t at_start = T.host[T.cap];
+            const auto t0 = std::chrono::steady_clock::now();
+            UOI_CUDA(cudaGraphLaunch(gg.exec, s));
+            UOI_CUDA(cudaStreamSynchronize(s));
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (T.host[T.cap + 2])
+                throw Error(T.host[T.cap + 2], "tensor-core x-update: a bounded pipeline wait expired");
+            if (trial) {
+                score[next_cand] = ms / std::max(1, at_start);
+                if (++next_cand == cands.size()) {
+                    size_t bi = 0;
+                    for (size_t k = 1; k < cands.size(); ++k)
+                        if (score[k] < score[bi]) bi = k;
+                    best = cands[bi];
+                    tuned = true;
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    tune_cache()[key] = best;
+                }
+            }
+            // credit the replay to the first member still iterating, then release the finished
+            bool credited = false;
+            for (size_t i = 0; i < T.slots.size(); ++i) {
+                if (T.released[i]) continue;
+                Slot* sl = T.slots[i];
+                if (!credited) {
+                    sl->ms += ms;
+                    sl->launches += 2 * XT_CHUNK + 1;
+                    credited = true;
+                }
+                if (T.host[i] == 0) {
+                    T.released[i] = true;
+                    --active;
+                    release(sl, 0, std::string());
+                }
+            }
+        } catch (const Error& e) {
+            fail = e.status;
+            fail_msg = e.what();
+        } catch (const std::exception& e) {
+            fail = UOI_ERR_CUDA;
+            fail_msg = e.what();
+        }
+        if (fail) {
+            // every member still waiting gets the error
+            for (size_t i = 0; i < T.slots.size(); ++i)
+                if (!T.released[i]) {
+                    T.released[i] = true;
+                    --active;
+                    release(T.slots[i], fail, fail_msg);
+                }
+        }
+    }
+    gg.reset();
+    if (s) cudaStreamSynchronize(s);
+    // the members' ADMM state, freed on this thread's stream now that nothing reads it
+    for (Slot* sl : T.slots) {
+        XtMember& m = *sl->m;
+        for (DevBuf* b : { &m.rs, &m.rinv, &m.mp, &m.zb, &m.ub, &m.v0, &m.v1, &m.vs0, &m.vs1, &m.cn, &m.nb, &m.sj,
+                           &m.sje, &m.sit, &m.live }) {
+            b->stream = s;
+            b->release();
+        }
+    }
+    for (DevBuf* b : { &T.d_mem, &T.d_all, &T.d_live, &T.d_tiles, &T.d_ctr }) b->release();
+    if (T.host) cudaFreeHost(T.host);
+    if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+}
+
+namespace {
+thread_local AdmmBatch* t_batch = nullptr;
+thread_local bool t_batch_arrived = false;
+}  // namespace
+
+AdmmBatch* admm_batch_create(int32_t expected)
+{
+    int dev = 0;
+    UOI_CUDA(cudaGetDevice(&dev));
+    return new AdmmBatch(expected, dev);
+}
+
+void admm_batch_destroy(AdmmBatch* b) { delete b; }
+
+void admm_batch_enter(AdmmBatch* b)
+{
+    t_batch = b;
+    t_batch_arrived = false;
+}
+
+void admm_batch_leave()
+{
+    AdmmBatch* b = t_batch;
+    t_batch = nullptr;
+    if (!b || t_batch_arrived) return;
+    t_batch_arrived = true;
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->arrive_locked(nullptr);
+}
+
+bool admm_batch_try_join(const AdmmProblem<float>& P, cudaStream_t s)
+{
+    AdmmBatch* b = t_batch;
+    if (!b || t_batch_arrived) return false;
+    t_batch_arrived = true;
+    auto slot = std::make_unique<AdmmBatch::Slot>();
+    slot->m = std::make_unique<XtMember>();
+    int32_t st = 0;
+    std::string msg;
+    try {
+        xt_prepare(P, s, *slot->m);
+        UOI_CUDA(cudaStreamSynchronize(s));
+    } catch (const Error& e) {
+        st = e.status;
+        msg = e.what();
+    }
+    if (st != 0) {
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->arrive_locked(nullptr);
+        throw Error(st, msg);
+    }
+    AdmmBatch::Slot* sl = slot.get();
+    {
+        std::unique_lock<std::mutex> lk(b->mu);
+        b->arrive_locked(sl);
+        b->cv_members.wait(lk, [&] { return sl->done; });
+    }
+    // the solver keeps this member's state until the batch ends: hand the slot over
+    b->hold(std::move(slot));
+    ktimer_credit(TK_XUPDATE, sl->ms, sl->launches);
+    count_launch(sl->launches);
+    if (sl->status != 0) throw Error(sl->status, sl->error);
+    return true;
 }
 
 }  // namespace uoi

@@ -2,7 +2,11 @@
 
 * every problem's result is bitwise the result of uoi_lasso_fit on that problem
   alone with problem_id = base + i (the batch only schedules; the arithmetic is
-  the same), in both precision forms, with more problems than worker streams;
+  the same), in both precision forms, with more problems than worker streams,
+  and in the grouped form (streams = 0: the tensor-core ADMM solves of all
+  members iterated together, tiles chosen by timing), whose first call tunes and
+  whose second reuses the choice -- both bitwise the single fits, with cold and
+  with path warm starts;
 * the plain FP64 batch matches the FP64 oracle on its problems (Alg. 1 per
   problem) within the plain form's 1e-6;
 * every mixed member (p from 20 to 700, the last with n < p on the tensor-core
@@ -37,15 +41,29 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a - b)
 
 
-@pytest.mark.parametrize("prec", [native.PREC_MIXED, native.PREC_FP64])
-def test_batch_equals_single_fits(prec):
+@pytest.mark.parametrize("prec,streams", [(native.PREC_MIXED, 3), (native.PREC_FP64, 3), (native.PREC_MIXED, 0),
+                                          (native.PREC_FP64, 0)])
+def test_batch_equals_single_fits(prec, streams):
     probs = _problems(SIZES if prec == native.PREC_MIXED else SIZES[:6])
     kw = dict(B1=6, B2=5, q=8, precision=prec, problem_id=11, warm_start=native.WARM_NONE)
-    out = native.uoi_lasso_fit_batch([d.X for d in probs], [d.y for d in probs], streams=3, **kw)
-    assert len(out) == len(probs)
+    runs = [native.uoi_lasso_fit_batch([d.X for d in probs], [d.y for d in probs], streams=streams, **kw)
+            for _ in range(2 if streams == 0 else 1)]
+    for out in runs:
+        assert len(out) == len(probs)
+        for i, d in enumerate(probs):
+            one = native.uoi_lasso_fit(d.X, d.y, **{**kw, "problem_id": 11 + i})
+            assert out[i]["status"] in (native.OK, native.OK_WITH_WARNINGS)
+            np.testing.assert_array_equal(out[i]["beta"], one["beta"])
+            assert out[i]["diag"]["admm_iterations"] == one["diag"]["admm_iterations"]
+
+
+def test_grouped_batch_path_warm_start():
+    # path warm start: chains advance through the lambdas inside the grouped check
+    probs = _problems(SIZES[1:4] + SIZES[6:])
+    kw = dict(B1=4, B2=4, q=6, precision=native.PREC_MIXED, problem_id=5, warm_start=native.WARM_PATH)
+    out = native.uoi_lasso_fit_batch([d.X for d in probs], [d.y for d in probs], streams=0, **kw)
     for i, d in enumerate(probs):
-        one = native.uoi_lasso_fit(d.X, d.y, **{**kw, "problem_id": 11 + i})
-        assert out[i]["status"] in (native.OK, native.OK_WITH_WARNINGS)
+        one = native.uoi_lasso_fit(d.X, d.y, **{**kw, "problem_id": 5 + i})
         np.testing.assert_array_equal(out[i]["beta"], one["beta"])
         assert out[i]["diag"]["admm_iterations"] == one["diag"]["admm_iterations"]
 
@@ -60,10 +78,11 @@ def test_fp64_batch_matches_oracle():
         assert rel_l2(out[i]["beta"], ref["beta"][0]) <= 1e-6
 
 
-def test_mixed_batch_members_match_oracle():
+@pytest.mark.parametrize("streams", [3, 0])
+def test_mixed_batch_members_match_oracle(streams):
     probs = _problems(SIZES)
     kw = dict(B1=6, B2=5, q=8, warm_start=native.WARM_NONE)
-    out = native.uoi_lasso_fit_batch([d.X for d in probs], [d.y for d in probs], streams=3,
+    out = native.uoi_lasso_fit_batch([d.X for d in probs], [d.y for d in probs], streams=streams,
                                      precision=native.PREC_MIXED, problem_id=11, **kw)
     for i, d in enumerate(probs):
         n, p = d.X.shape
@@ -102,4 +121,12 @@ def test_empty_and_failing_members():
     bad[3, 2] = np.nan
     with pytest.raises(native.UoiError) as ei:
         native.uoi_lasso_fit_batch([good.X, bad], [good.y, good.y], B1=2, B2=2, q=3)
+    assert ei.value.status == native.ERR_NONFINITE
+    # grouped: members that reach the tensor-core solve still finish beside a failing one
+    big = synth.lasso_problem(900, 260, 10, seed=6, sigma=0.5)
+    bad2 = big.X.copy()
+    bad2[0, 0] = np.inf
+    with pytest.raises(native.UoiError) as ei:
+        native.uoi_lasso_fit_batch([big.X, bad2, big.X], [big.y, big.y, big.y], streams=0, B1=3, B2=2, q=4,
+                                   precision=native.PREC_MIXED, problem_id=9)
     assert ei.value.status == native.ERR_NONFINITE
