@@ -275,40 +275,65 @@ __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t
                                int32_t trans, int32_t rt, int64_t rpad, int64_t kpad,
                                const uint32_t* smax, float* sinv, __half* out)
 {
-    __shared__ float tile[32][33];                      // [k local][i local]
+    // a block covers 32 rows x SPLIT_KC blocks of 32 k: every thread issues all of its
+    // 4 x SPLIT_KC loads before its first store, so more bytes are in flight per SM
+    constexpr int SPLIT_KC = 4;
+    __shared__ float tile[SPLIT_KC][32][33];            // [k block][k local][i local]
     const int64_t g = blockIdx.z;
-    const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+    const int64_t i0 = (int64_t)blockIdx.x * 32, kb0 = (int64_t)blockIdx.y * SPLIT_KC;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const float* sg = src + g * gs;
     const float sc = pow2_scale(__uint_as_float(smax[g]));
     if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0 && ty == 0) sinv[g] = 1.f / sc;
-    for (int j = ty; j < 32; j += 8) {
-        if (trans) {
-            const int64_t i = i0 + tx, k = k0 + j;
-            tile[j][tx] = (i < rows && k < K) ? sg[k * ld + i] : 0.f;
-        } else {
-            const int64_t i = i0 + j, k = k0 + tx;
-            tile[tx][j] = (i < rows && k < K) ? sg[i * ld + k] : 0.f;
+    const int64_t kst = kpad / GT_TK;
+    float v[SPLIT_KC][4];
+#pragma unroll
+    for (int c = 0; c < SPLIT_KC; ++c) {
+        const int64_t k0 = (kb0 + c) * 32;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = ty + 8 * u;
+            if (trans) {
+                const int64_t i = i0 + tx, k = k0 + j;
+                v[c][u] = (i < rows && k < K) ? sg[k * ld + i] : 0.f;
+            } else {
+                const int64_t i = i0 + j, k = k0 + tx;
+                v[c][u] = (i < rows && k < K) ? sg[i * ld + k] : 0.f;
+            }
         }
     }
+#pragma unroll
+    for (int c = 0; c < SPLIT_KC; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = ty + 8 * u;
+            if (trans) tile[c][j][tx] = v[c][u];
+            else tile[c][tx][j] = v[c][u];
+        }
     __syncthreads();
     // write: thread (row jj, k quad kq) splits four consecutive k of one row and
     // stores 8-byte runs of each piece (conflict-free reads: bank = kq + u + jj)
-    const int64_t RT = rpad / rt, kst = kpad / GT_TK;
+    const int64_t RT = rpad / rt;
     const int t = ty * 32 + tx, jj = t >> 3, kq = (t & 7) << 2;
-    const int64_t i = i0 + jj, k = k0 + kq;
-    __half h[4], l[4];
+    const int64_t i = i0 + jj;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) split2(tile[kq + u][jj] * sc, h[u], l[u]);
-    const int64_t blk = ((g * RT + i / rt) * kst + k / GT_TK) * GT_PIECES;
-    const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;             // multiple of 4
-    if (!UOI_IN_BOUNDS(o + rt * GT_TK + 3, (int64_t)gridDim.z * rpad * kpad * GT_PIECES, 401)) return;
-    const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
-    const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
-    *reinterpret_cast<uint2*>(out + o) =
-        make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
-    *reinterpret_cast<uint2*>(out + o + rt * GT_TK) =
-        make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+    for (int c = 0; c < SPLIT_KC; ++c) {
+        const int64_t kb = kb0 + c;
+        if (kb >= kst) break;
+        const int64_t k = kb * 32 + kq;
+        __half h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) split2(tile[c][kq + u][jj] * sc, h[u], l[u]);
+        const int64_t blk = ((g * RT + i / rt) * kst + kb) * GT_PIECES;
+        const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;             // multiple of 4
+        if (!UOI_IN_BOUNDS(o + rt * GT_TK + 3, (int64_t)gridDim.z * rpad * kpad * GT_PIECES, 401)) return;
+        const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
+        const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
+        *reinterpret_cast<uint2*>(out + o) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+        *reinterpret_cast<uint2*>(out + o + rt * GT_TK) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+    }
 }
 
 // out[g] = largest diagonal entry of the SPD block A_g (n x n), as float bits:
@@ -364,7 +389,7 @@ void make_pieces(Pieces& P, const float* src, int64_t ld, int64_t gs, int32_t ro
     P.kst = (int32_t)(kpad / GT_TK);
     P.buf.alloc(sizeof(__half) * GT_PIECES * (size_t)G * rpad * kpad, s);
     P.sinv.alloc(sizeof(float) * (size_t)G, s);
-    k_split_blocks<<<dim3((unsigned)(rpad / 32), (unsigned)(kpad / 32), (unsigned)G), dim3(32, 8), 0, s>>>(
+    k_split_blocks<<<dim3((unsigned)(rpad / 32), (unsigned)ceil_div(kpad / 32, 4), (unsigned)G), dim3(32, 8), 0, s>>>(
         src, ld, gs, rows, K, trans ? 1 : 0, rt, rpad, kpad, smax, P.sinv.as<float>(), P.buf.as<__half>());
     UOI_CHECK_LAUNCH();
     count_launch();
