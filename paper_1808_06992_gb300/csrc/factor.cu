@@ -63,26 +63,59 @@ __global__ void k_build_system(const double* __restrict__ G, const double* nk, d
 __global__ void k_build_system_lower(const double* __restrict__ G, const double* nk, double rho, int64_t p,
                                      float* __restrict__ A)
 {
-    __shared__ float tile[32][33];
-    const int64_t k = blockIdx.z;
-    const int bx = blockIdx.x, by = blockIdx.y;        // source tile: rows by*32.., columns bx*32..
-    if (bx > by) return;                               // lower tiles only
+    // blockIdx.x enumerates the lower 32 x 32 tiles (by, bx), bx <= by, in groups of
+    // LOWER_TILES consecutive tiles of one row of tiles; every thread issues its
+    // loads for all of them before any store
+    constexpr int LOWER_TILES = 4;
+    __shared__ float tile[LOWER_TILES][32][33];
+    const int64_t k = blockIdx.y;
+    const int64_t tt = (p + 31) / 32;
+    // row of tiles by holds ceil((by + 1) / LOWER_TILES) groups; find (by, first bx)
+    int64_t grp = blockIdx.x, by = 0;
+    for (;; ++by) {
+        const int64_t ng = (by + LOWER_TILES) / LOWER_TILES;      // ceil((by + 1) / LOWER_TILES)
+        if (grp < ng) break;
+        grp -= ng;
+    }
+    if (by >= tt) return;
+    const int64_t bx0 = grp * LOWER_TILES;
     const float inv_n = (float)(1.0 / nk[k]);
     const double* g = G + k * p * p;
     float* a = A + k * p * p;
     const int tx = threadIdx.x;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int64_t r = (int64_t)by * 32 + yy, c = (int64_t)bx * 32 + tx;
-        if (r < p && c < p && c <= r) {
-            const float v = system_entry<float>(__ldg(g + r * p + c), (double)inv_n, rho, r == c);
-            tile[yy][tx] = v;
-            a[r * p + c] = v;
+    double v[LOWER_TILES][4];
+#pragma unroll
+    for (int q = 0; q < LOWER_TILES; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t r = by * 32 + threadIdx.y + 8 * u, c = (bx0 + q) * 32 + tx;
+            v[q][u] = (bx0 + q <= by && r < p && c < p && c <= r) ? __ldg(g + r * p + c) : 0.0;
+        }
+#pragma unroll
+    for (int q = 0; q < LOWER_TILES; ++q) {
+        if (bx0 + q > by) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int yy = threadIdx.y + 8 * u;
+            const int64_t r = by * 32 + yy, c = (bx0 + q) * 32 + tx;
+            if (r < p && c < p && c <= r) {
+                const float e = system_entry<float>(v[q][u], (double)inv_n, rho, r == c);
+                tile[q][yy][tx] = e;
+                a[r * p + c] = e;
+            }
         }
     }
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {     // mirror: rows bx*32 + yy, columns by*32 + tx
-        const int64_t r = (int64_t)bx * 32 + yy, c = (int64_t)by * 32 + tx;
-        if (r < p && c < p && c > r) a[r * p + c] = tile[tx][yy];
+#pragma unroll
+    for (int q = 0; q < LOWER_TILES; ++q) {
+        const int64_t bx = bx0 + q;
+        if (bx > by) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {                    // mirror: rows bx*32 + yy, columns by*32 + tx
+            const int yy = threadIdx.y + 8 * u;
+            const int64_t r = bx * 32 + yy, c = by * 32 + tx;
+            if (r < p && c < p && c > r) a[r * p + c] = tile[q][tx][yy];
+        }
     }
 }
 
@@ -383,8 +416,10 @@ void build_system(const double* G, const double* nk, double rho, int64_t p, int3
 void build_system_lower(const double* G, const double* nk, double rho, int64_t p, int32_t B, float* A,
                         cudaStream_t s)
 {
-    const unsigned tt = (unsigned)ceil_div(p, 32);
-    k_build_system_lower<<<dim3(tt, tt, (unsigned)B), dim3(32, 8), 0, s>>>(G, nk, rho, p, A);
+    const int64_t tt = ceil_div(p, 32);
+    int64_t groups = 0;                                  // groups of 4 lower tiles per row of tiles
+    for (int64_t by = 0; by < tt; ++by) groups += (by + 4) / 4;
+    k_build_system_lower<<<dim3((unsigned)groups, (unsigned)B), dim3(32, 8), 0, s>>>(G, nk, rho, p, A);
     UOI_CHECK_LAUNCH();
     count_launch();
 }

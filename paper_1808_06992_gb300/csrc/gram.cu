@@ -180,17 +180,26 @@ __global__ void k_xty_partial(const double* X, int64_t ldx, const double* Y, int
     const int64_t t0 = c * XTY_ROWS, t1 = min(m, t0 + XTY_ROWS);
     double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
     if (j < p) {
-        // batches of 8 rows: all eight loads issued before the multiply-adds
+        // batches of 16 rows: all sixteen loads of X and of y issued before the
+        // multiply-adds
         int64_t t = t0;
-        for (; t + 8 <= t1; t += 8) {
-            double xv[8];
+        for (; t + 16 <= t1; t += 16) {
+            double xv[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) xv[u] = __ldg(X + (t + u) * ldx + j);
+            for (int u = 0; u < 16; ++u) xv[u] = __ldg(X + (t + u) * ldx + j);
+            if (r == 1) {
+                double yv[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+                for (int u = 0; u < 16; ++u) yv[u] = __ldg(Y + (t + u) * ldy);
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (e < r) acc[e] = fma(xv[u], __ldg(Y + (t + u) * ldy + e), acc[e]);
+                for (int u = 0; u < 16; ++u) acc[0] = fma(xv[u], yv[u], acc[0]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (e < r) acc[e] = fma(xv[u], __ldg(Y + (t + u) * ldy + e), acc[e]);
+            }
         }
         for (; t < t1; ++t) {
             const double x = X[t * ldx + j];
