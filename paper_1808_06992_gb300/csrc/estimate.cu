@@ -59,6 +59,10 @@ struct OlsArgs {
     float* fscratch;                         // mixed pass: global packed factor (per CTA), or null
     const int32_t* je_list;                  // mixed loss pass: the (j*r + e) it covers (else all)
     int32_t n_je;
+    // mixed loss pass with je_list: when set, CTAs take solves in order from this
+    // counter (preset to 0), support-major (t = rank of je in je_list * B2 + k), so a
+    // list sorted by decreasing support size runs the largest factors first
+    unsigned long long* next;
 };
 
 __global__ void __launch_bounds__(256) k_ols(OlsArgs a)
@@ -316,15 +320,25 @@ __global__ void __launch_bounds__(256, MINB) k_ols_mixed(OlsArgs a)
     float* dinv = w + sm2;                                              // 1 / diagonal of the factor
     float* L = a.fscratch ? a.fscratch + (size_t)blockIdx.x * ((size_t)a.smax * (a.smax + 1) / 2) : dinv + sm2;
     __shared__ int s_count;
+    __shared__ int64_t s_next;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // the next solve of this CTA: a fixed stride, or the shared counter (block-uniform)
+    auto fetch = [&](int64_t cur) -> int64_t {
+        if (!a.next) return cur < 0 ? (int64_t)blockIdx.x : cur + gridDim.x;
+        __syncthreads();                               // every thread is done with s_next
+        if (threadIdx.x == 0) s_next = (int64_t)atomicAdd(a.next, 1ull);
+        __syncthreads();
+        return s_next;
+    };
 
-    for (int64_t t = blockIdx.x; t < a.solves; t += gridDim.x) {
+    for (int64_t t = fetch(-1); t < a.solves; t = fetch(t)) {
         int k, j, e;
         if (a.jstar) { k = (int)(t / a.r); e = (int)(t % a.r); j = a.jstar[k]; }
         else if (a.je_list) {
-            k = (int)(t / a.n_je);
-            const int32_t je = a.je_list[t % a.n_je];
+            int32_t je;
+            if (a.next) { k = (int)(t % a.B2); je = a.je_list[t / a.B2]; }
+            else { k = (int)(t / a.n_je); je = a.je_list[t % a.n_je]; }
             j = (int)(je / a.r); e = (int)(je % a.r);
         } else { k = (int)(t / ((int64_t)a.q * a.r)); const int64_t rem = t % ((int64_t)a.q * a.r);
                j = (int)(rem / a.r); e = (int)(rem % a.r);
@@ -915,6 +929,13 @@ int64_t ols_losses(const double* Gt, const double* Bt, const double* Ge, const d
     if (std::max(smax_small, smax_large) > 46000)
         throw Error(UOI_ERR_UNSUPPORTED, "OLS support larger than 46000 columns");
     int64_t nfb = 0;
+    // largest supports first within each class, taken from a counter as CTAs free up
+    // (the factor costs grow as the cube of the support size)
+    auto by_size = [&](int32_t x, int32_t y) { return hsz[(size_t)x] > hsz[(size_t)y]; };
+    std::stable_sort(small_je.begin(), small_je.end(), by_size);
+    std::stable_sort(large_je.begin(), large_je.end(), by_size);
+    DevBuf ctr(sizeof(unsigned long long) * 2, s);
+    UOI_CUDA(cudaMemsetAsync(ctr.ptr, 0, ctr.bytes, s));
     for (int cls = 0; cls < 2; ++cls) {
         const std::vector<int32_t>& lst = cls == 0 ? small_je : large_je;
         if (lst.empty()) continue;
@@ -923,6 +944,7 @@ int64_t ols_losses(const double* Gt, const double* Bt, const double* Ge, const d
         OlsArgs b = a;
         b.je_list = jl.as<int32_t>();
         b.n_je = (int32_t)lst.size();
+        b.next = ctr.as<unsigned long long>() + cls;
         b.solves = (int64_t)B2 * b.n_je;
         b.smax = cls == 0 ? smax_small : smax_large;
         nfb += launch_ols_mixed(b, s);
