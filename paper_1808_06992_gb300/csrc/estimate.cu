@@ -718,11 +718,18 @@ void launch_ols_fp64(OlsArgs a, cudaStream_t s)
     }
 }
 
-// Mixed pass: FP32 factor + FP64 refinement for every solve, then the FP64
-// kernel for the solves it handed back.
-int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
+// Mixed pass: FP32 factor + FP64 refinement for every solve (ols_mixed_start,
+// asynchronous on s), then the FP64 kernel for the solves it handed back
+// (ols_mixed_finish, which waits for the count).
+struct OlsMixedRun {
+    OlsArgs a{};                  // solves = 0 until started: finish does nothing
+    DevBuf fscratch, fbl, fbc;
+};
+
+void ols_mixed_start(OlsArgs a, cudaStream_t s, OlsMixedRun& R)
 {
-    if (a.solves == 0) return 0;
+    R.a = a;
+    if (a.solves == 0) return;
     const int sm2 = (a.smax + 1) & ~1;
     const size_t base = sizeof(int) * sm2 + 2 * sizeof(double) * sm2 + 32 * sizeof(double) +
                         2 * sizeof(float) * sm2;
@@ -740,30 +747,51 @@ int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
     UOI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     UOI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem));
     const int grid = (int)std::min<int64_t>(a.solves, (int64_t)nsm * std::max(1, per));
-    DevBuf fscratch;
     if (!in_smem) {
-        fscratch.alloc(lbytes * (size_t)grid, s);
-        a.fscratch = fscratch.as<float>();
+        R.fscratch.alloc(lbytes * (size_t)grid, s);
+        R.a.fscratch = R.fscratch.as<float>();
     }
-    DevBuf fbl(sizeof(int32_t) * (size_t)std::max<int64_t>(a.solves, (int64_t)a.B2 * a.q * a.r), s);
-    DevBuf fbc(sizeof(int32_t), s);
-    UOI_CUDA(cudaMemsetAsync(fbc.ptr, 0, sizeof(int32_t), s));
-    a.fb_list = fbl.as<int32_t>();
-    a.fb_count = fbc.as<int32_t>();
-    if (small) k_ols_mixed<2, 4><<<grid, 256, smem, s>>>(a);
-    else k_ols_mixed<8, 1><<<grid, 256, smem, s>>>(a);
+    R.fbl.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(a.solves, (int64_t)a.B2 * a.q * a.r), s);
+    R.fbc.alloc(sizeof(int32_t), s);
+    UOI_CUDA(cudaMemsetAsync(R.fbc.ptr, 0, sizeof(int32_t), s));
+    R.a.fb_list = R.fbl.as<int32_t>();
+    R.a.fb_count = R.fbc.as<int32_t>();
+    if (small) k_ols_mixed<2, 4><<<grid, 256, smem, s>>>(R.a);
+    else k_ols_mixed<8, 1><<<grid, 256, smem, s>>>(R.a);
     UOI_CHECK_LAUNCH();
     count_launch();
+}
+
+int64_t ols_mixed_finish(OlsMixedRun& R, cudaStream_t s)
+{
+    if (R.a.solves == 0) return 0;
     int32_t nfb = 0;
-    UOI_CUDA(cudaMemcpyAsync(&nfb, fbc.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UOI_CUDA(cudaMemcpyAsync(&nfb, R.fbc.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));
     if (nfb > 0) {
-        a.list = fbl.as<int32_t>();
+        OlsArgs a = R.a;
+        a.list = R.fbl.as<int32_t>();
         a.solves = nfb;
         a.fscratch = nullptr;
         launch_ols_fp64(a, s);
     }
     return nfb;
+}
+
+int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
+{
+    OlsMixedRun R;
+    ols_mixed_start(a, s, R);
+    return ols_mixed_finish(R, s);
+}
+
+// A second stream per host thread for the small-support class of the loss pass,
+// which runs beside the large class (created once, kept for the thread's life).
+cudaStream_t side_stream()
+{
+    thread_local cudaStream_t side = nullptr;
+    if (!side) UOI_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    return side;
 }
 
 int64_t run_ols(OlsArgs a, cudaStream_t s)
@@ -936,18 +964,39 @@ int64_t ols_losses(const double* Gt, const double* Bt, const double* Ge, const d
     std::stable_sort(large_je.begin(), large_je.end(), by_size);
     DevBuf ctr(sizeof(unsigned long long) * 2, s);
     UOI_CUDA(cudaMemsetAsync(ctr.ptr, 0, ctr.bytes, s));
+    // the two classes run side by side: the large class on s, the small one on a
+    // second stream that starts after everything s has queued so far
+    cudaStream_t side = (small_je.empty() || large_je.empty()) ? s : side_stream();
+    cudaEvent_t ready = nullptr, side_done = nullptr;
+    if (side != s) {
+        UOI_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        UOI_CUDA(cudaEventCreateWithFlags(&side_done, cudaEventDisableTiming));
+        UOI_CUDA(cudaEventRecord(ready, s));
+        UOI_CUDA(cudaStreamWaitEvent(side, ready, 0));
+    }
+    OlsMixedRun runs[2];
+    DevBuf jl[2];
     for (int cls = 0; cls < 2; ++cls) {
         const std::vector<int32_t>& lst = cls == 0 ? small_je : large_je;
         if (lst.empty()) continue;
-        DevBuf jl(sizeof(int32_t) * lst.size(), s);
-        UOI_CUDA(cudaMemcpyAsync(jl.ptr, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, s));
+        cudaStream_t cs = cls == 0 ? side : s;
+        jl[cls].alloc(sizeof(int32_t) * lst.size(), cs);
+        UOI_CUDA(cudaMemcpyAsync(jl[cls].ptr, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice, cs));
         OlsArgs b = a;
-        b.je_list = jl.as<int32_t>();
+        b.je_list = jl[cls].as<int32_t>();
         b.n_je = (int32_t)lst.size();
         b.next = ctr.as<unsigned long long>() + cls;
         b.solves = (int64_t)B2 * b.n_je;
         b.smax = cls == 0 ? smax_small : smax_large;
-        nfb += launch_ols_mixed(b, s);
+        ols_mixed_start(b, cs, runs[cls]);
+    }
+    for (int cls = 1; cls >= 0; --cls) nfb += ols_mixed_finish(runs[cls], cls == 0 ? side : s);
+    if (side != s) {
+        // everything that follows on s (the duplicates' losses, the argmin) sees the side's results
+        UOI_CUDA(cudaEventRecord(side_done, side));
+        UOI_CUDA(cudaStreamWaitEvent(s, side_done, 0));
+        cudaEventDestroy(ready);
+        cudaEventDestroy(side_done);
     }
     const unsigned gf = (unsigned)std::min<int64_t>(ceil_div(a.solves, 256), 4096);
     k_fill_duplicates<<<gf, 256, 0, s>>>(dup.as<int32_t>(), B2, q, r, losses, singular);
