@@ -316,6 +316,8 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                     unsigned long long* near_count = nullptr)
 {
     int t0 = tm ? tm->mark() : 0;
+    std::optional<NvtxRange> stage;
+    stage.emplace("uoi:selection:moments");
     // mixed form, large p: the block inverse on tensor cores; when nothing but the
     // FP32 system reads G (no intercept elimination, no learned start), the Gram's
     // lower triangle is enough and the system is built from it
@@ -344,6 +346,8 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
                 lower_only);
     }
     int t1 = tm ? tm->mark() : 0;
+    stage.reset();
+    stage.emplace("uoi:selection:factor");
     DevBuf st(sizeof(DevStatus), s);
     UOI_CUDA(cudaMemsetAsync(st.ptr, 0, st.bytes, s));
     DevBuf A(sizeof(T) * (size_t)(B * p * p), s);
@@ -389,6 +393,8 @@ void selection_admm(int precision, const double* Xd, int64_t ldx, const double* 
         G.release();
     }
     int t2 = tm ? tm->mark() : 0;
+    stage.reset();
+    stage.emplace("uoi:selection:admm");
     AdmmProblem<T> P;
     P.G = B; P.p = p; P.r = r; P.q = q;
     P.M = M.as<T>(); P.c = c.as<T>(); P.lambdas = lam;
@@ -486,6 +492,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     const int64_t launches0 = g_launches;
     ktimer_reset();
     StageTimer tm(s);
+    NvtxRange fit_range("uoi:fit");
     const int tstart = tm.mark();
     const int32_t B1 = prm->B1, B2 = prm->B2, q = prm->q;
     const int64_t W = (p + 63) / 64;
@@ -550,6 +557,8 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
 
     // ---- selection ----
     const int t_sel0 = tm.mark();
+    std::optional<NvtxRange> phase;
+    phase.emplace("uoi:selection");
     DevBuf wsel(sizeof(uint32_t) * (size_t)(B1 * m), s);
     selection_weights(m, prm->block_len, key, B1, wsel.as<uint32_t>(), s, param_block_mode(prm));
     const int t_sel1 = tm.mark();
@@ -585,6 +594,8 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
                                nullptr, near_b.as<unsigned long long>());
     family_mask_tail(fam.as<uint64_t>(), q * r, p, s);
     const int t_sel2 = tm.mark();
+    phase.reset();
+    phase.emplace("uoi:estimation");
 
     // ---- estimation ----
     // with an intercept every support also holds the ones column (index p)
@@ -648,6 +659,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     bo.init(beta_out, (size_t)(r * pe), s);
     bagging(chosen.as<double>(), B2, r * pe, prm->bagging, bo.dev, s);
     const int t_end = tm.mark();
+    phase.reset();
 
     // ---- outputs ----
     bo.finish(s);

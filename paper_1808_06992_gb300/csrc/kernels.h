@@ -7,6 +7,10 @@
 
 #include "common.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <optional>
+
 #include <string>
 
 namespace uoi {
@@ -23,6 +27,15 @@ void check_bounds_status(cudaStream_t s);
 // algorithmic work.  Resolved after the fit's final synchronisation.
 enum TimedKernel { TK_GRAM_TC = 0, TK_XUPDATE = 1, TK_COUNT = 2 };
 struct KernelTotals { float ms = 0.f; int64_t launches = 0; double flops = 0.0; double bytes = 0.0; };
+// A named range on the host timeline (NVTX), from construction to destruction: the
+// stages of a fit, for profilers that group or filter kernels by range.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void ktimer_reset();
 void ktimer_begin(TimedKernel k, cudaStream_t s);
 void ktimer_end(TimedKernel k, cudaStream_t s, double flops, double bytes);
