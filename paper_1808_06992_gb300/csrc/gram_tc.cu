@@ -266,7 +266,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmA, GramTcArgs a)
 // column over each 64 rows (losq[(item*row_tiles + tile)*pz_x + col], a fixed
 // order), from which the diagonal correction is reduced in a fixed order.
 constexpr int SPLIT_ROWS = 128;
-constexpr int SPLIT_COLS = 32;
+constexpr int SPLIT_COLS = 32;                  // columns of one half of a block
+constexpr int SPLIT_HALVES = 2;                 // a block covers 64 columns: its loads of both halves in flight together
 constexpr int SPLIT_LD = SPLIT_ROWS + 4;
 __global__ void __launch_bounds__(256)
 k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, int32_t x32_compact,
@@ -276,7 +277,7 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
                   int32_t pz_pad, int32_t row_tiles, __nv_bfloat16* out, float* losq,
                   const float* zrow)
 {
-    __shared__ __align__(16) float tile[SPLIT_COLS][SPLIT_LD];      // [column][row]
+    __shared__ __align__(16) float tile[SPLIT_HALVES][SPLIT_COLS][SPLIT_LD];      // [half][column][row]
     __shared__ int64_t rowoff[SPLIT_ROWS];
     __shared__ const float* rowptr[SPLIT_ROWS];     // row of the FP32 copy, or a row of zeros
     __shared__ float rowsc[SPLIT_ROWS];
@@ -284,7 +285,7 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
     // the same pace, so CTAs launched together read the same rows (L2 hits)
     const int item = blockIdx.x;
     const int64_t t0 = (int64_t)blockIdx.y * SPLIT_ROWS;
-    const int c0 = blockIdx.z * SPLIT_COLS;
+    const int cb = blockIdx.z * SPLIT_COLS * SPLIT_HALVES;
     const int nr = nrows[item];
     const int pz = pz_x + r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,79 +297,89 @@ k_split_transpose(const double* X, int64_t ldx, const float* X32, int64_t ld32, 
         rowsc[threadIdx.x] = t < nr ? rowscale[(int64_t)item * m + t] : 0.f;
     }
     __syncthreads();
-    // read: warp w takes rows 16w .. 16w + 15; lane = column.  Blocks whose 32
-    // columns all come from the FP32 copy without a column map (all but the last
-    // block of a fit) take a path with no per-element branch.
-    const bool fast = X32 != nullptr && (colmap == nullptr || x32_compact) && c0 + SPLIT_COLS <= pz_x;
+    // four consecutive rows of one column, scaled, as one 16-byte vector of the tile
+    auto put = [&](int h, const float (&q)[16]) {
+#pragma unroll
+        for (int i4 = 0; i4 < 4; ++i4) {
+            const int tl = 16 * warp + 4 * i4;
+            *reinterpret_cast<float4*>(&tile[h][lane][tl]) =
+                make_float4(q[4 * i4] * rowsc[tl], q[4 * i4 + 1] * rowsc[tl + 1], q[4 * i4 + 2] * rowsc[tl + 2],
+                            q[4 * i4 + 3] * rowsc[tl + 3]);
+        }
+    };
+    // read: warp w takes rows 16w .. 16w + 15; lane = column of each half.  Blocks
+    // whose columns all come from the FP32 copy without a column map (all but the
+    // last block of a fit) take a path with no per-element branch, with the loads of
+    // both halves issued before any store.
+    const bool fast = X32 != nullptr && (colmap == nullptr || x32_compact) &&
+                      cb + SPLIT_COLS * SPLIT_HALVES <= pz_x;
     if (fast) {
-        float q[16];
+        float q[SPLIT_HALVES][16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) q[i] = __ldg(rowptr[16 * warp + i] + c0 + lane);
+        for (int h = 0; h < SPLIT_HALVES; ++h)
 #pragma unroll
-        for (int i4 = 0; i4 < 4; ++i4) {
-            const int tl = 16 * warp + 4 * i4;
-            *reinterpret_cast<float4*>(&tile[lane][tl]) =
-                make_float4(q[4 * i4] * rowsc[tl], q[4 * i4 + 1] * rowsc[tl + 1], q[4 * i4 + 2] * rowsc[tl + 2],
-                            q[4 * i4 + 3] * rowsc[tl + 3]);
-        }
+            for (int i = 0; i < 16; ++i) q[h][i] = __ldg(rowptr[16 * warp + i] + cb + SPLIT_COLS * h + lane);
+#pragma unroll
+        for (int h = 0; h < SPLIT_HALVES; ++h) put(h, q[h]);
     } else {
-        const int c = c0 + lane;
-        const int64_t col = colmap && c < pz_x ? colmap[c] : c;      // column of X
-        const int64_t col32 = x32_compact ? c : col;                 // column of the FP32 copy
-        float q[16];
+#pragma unroll 1
+        for (int h = 0; h < SPLIT_HALVES; ++h) {
+            const int c = cb + SPLIT_COLS * h + lane;
+            const int64_t col = colmap && c < pz_x ? colmap[c] : c;      // column of X
+            const int64_t col32 = x32_compact ? c : col;                 // column of the FP32 copy
+            float q[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int64_t row = rowoff[16 * warp + i];
-            float v = 0.f;
-            if (row >= 0 && c < pz) {
-                if (c < pz_x)
-                    v = X32 ? __ldg(X32 + row * ld32 + col32) : f64_to_f32_int(__ldg(X + row * ldx + col));
-                else
-                    v = f64_to_f32_int(__ldg(Y + row * ldy + (c - pz_x)));
+            for (int i = 0; i < 16; ++i) {
+                const int64_t row = rowoff[16 * warp + i];
+                float v = 0.f;
+                if (row >= 0 && c < pz) {
+                    if (c < pz_x)
+                        v = X32 ? __ldg(X32 + row * ld32 + col32) : f64_to_f32_int(__ldg(X + row * ldx + col));
+                    else
+                        v = f64_to_f32_int(__ldg(Y + row * ldy + (c - pz_x)));
+                }
+                q[i] = v;
             }
-            q[i] = v;
-        }
-#pragma unroll
-        for (int i4 = 0; i4 < 4; ++i4) {
-            const int tl = 16 * warp + 4 * i4;
-            *reinterpret_cast<float4*>(&tile[lane][tl]) =
-                make_float4(q[4 * i4] * rowsc[tl], q[4 * i4 + 1] * rowsc[tl + 1], q[4 * i4 + 2] * rowsc[tl + 2],
-                            q[4 * i4 + 3] * rowsc[tl + 3]);
+            put(h, q);
         }
     }
     __syncthreads();
-    // write: warp w takes columns w, w + 8, w + 16, w + 24; lane covers rows
-    // 4*lane .. 4*lane + 3 (lanes 0-15: the first 64 rows, 16-31: the second)
+    // write: warp w takes columns w, w + 8, w + 16, w + 24 of each half; lane covers
+    // rows 4*lane .. 4*lane + 3 (lanes 0-15: the first 64 rows, 16-31: the second)
     const int64_t piece = (int64_t)pz_pad * n_pad;                 // elements per piece
-    __nv_bfloat16* out_hi = out + ((int64_t)item * 2 * pz_pad + c0 + warp) * n_pad + t0 + 4 * lane;
-    float* losq_c = losq + ((int64_t)item * row_tiles + (t0 / 64) + (lane >> 4)) * pz_x + c0 + warp;
 #pragma unroll
-    for (int j = 0; j < SPLIT_COLS / 8; ++j) {
-        const int cl = warp + 8 * j;
-        const int cc = c0 + cl;
-        if (cc >= pz_pad) break;
-        const float4 v = *reinterpret_cast<const float4*>(&tile[cl][4 * lane]);
-        // two values per conversion (round to nearest even, as one at a time)
-        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
-        const float2 hf01 = __bfloat1622float2(h01), hf23 = __bfloat1622float2(h23);
-        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - hf01.x, v.y - hf01.y);   // exact differences
-        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - hf23.x, v.w - hf23.y);
-        const float2 lf01 = __bfloat1622float2(l01), lf23 = __bfloat1622float2(l23);
-        float sq = 0.f;
-        sq += lf01.x * lf01.x;
-        sq += lf01.y * lf01.y;
-        sq += lf23.x * lf23.x;
-        sq += lf23.y * lf23.y;
-        __nv_bfloat16* base_hi = out_hi + (int64_t)(8 * j) * n_pad;
-        *reinterpret_cast<uint2*>(base_hi) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
-        *reinterpret_cast<uint2*>(base_hi + piece) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
-        if (cc < pz_x) {
-            // sum over the 16 lanes of each 64-row half (fixed order)
+    for (int h = 0; h < SPLIT_HALVES; ++h) {
+        const int c0 = cb + SPLIT_COLS * h;
+        __nv_bfloat16* out_hi = out + ((int64_t)item * 2 * pz_pad + c0 + warp) * n_pad + t0 + 4 * lane;
+        float* losq_c = losq + ((int64_t)item * row_tiles + (t0 / 64) + (lane >> 4)) * pz_x + c0 + warp;
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if ((lane & 15) == 0) losq_c[8 * j] = sq;
+        for (int j = 0; j < SPLIT_COLS / 8; ++j) {
+            const int cl = warp + 8 * j;
+            const int cc = c0 + cl;
+            if (cc >= pz_pad) break;
+            const float4 v = *reinterpret_cast<const float4*>(&tile[h][cl][4 * lane]);
+            // two values per conversion (round to nearest even, as one at a time)
+            const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+            const float2 hf01 = __bfloat1622float2(h01), hf23 = __bfloat1622float2(h23);
+            const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - hf01.x, v.y - hf01.y);   // exact differences
+            const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - hf23.x, v.w - hf23.y);
+            const float2 lf01 = __bfloat1622float2(l01), lf23 = __bfloat1622float2(l23);
+            float sq = 0.f;
+            sq += lf01.x * lf01.x;
+            sq += lf01.y * lf01.y;
+            sq += lf23.x * lf23.x;
+            sq += lf23.y * lf23.y;
+            __nv_bfloat16* base_hi = out_hi + (int64_t)(8 * j) * n_pad;
+            *reinterpret_cast<uint2*>(base_hi) =
+                make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+            *reinterpret_cast<uint2*>(base_hi + piece) =
+                make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+            if (cc < pz_x) {
+                // sum over the 16 lanes of each 64-row half (fixed order)
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                if ((lane & 15) == 0) losq_c[8 * j] = sq;
+            }
         }
     }
 }
@@ -566,7 +577,7 @@ void moments_tc_cols(const double* X, int64_t ldx, const double* Y, int64_t ldy,
     UOI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     for (int b0 = 0; b0 < B; b0 += group) {
         const int nb = std::min(group, B - b0);
-        dim3 gs((unsigned)nb, (unsigned)(n_pad / SPLIT_ROWS), (unsigned)ceil_div(pz_pad, SPLIT_COLS));
+        dim3 gs((unsigned)nb, (unsigned)(n_pad / SPLIT_ROWS), (unsigned)ceil_div(pz_pad, SPLIT_COLS * SPLIT_HALVES));
         k_split_transpose<<<gs, 256, 0, s>>>(X, ldx, X32, ld32, x32_compact ? 1 : 0, Y, ldy, pz_x,
                                              (int32_t)r, colmap,
                                              rows.as<int32_t>() + (size_t)b0 * m,
