@@ -304,15 +304,29 @@ __device__ __forceinline__ void xupdate_tile(const CUtensorMap* tmM, const CUten
                 cp_async4(smem_u32(stg + (2 * a.NT + n) * XT_TM + r128), a.c + (int64_t)s_coff[n] * a.p + i);
             }
         }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        // The folded sums go back to TMEM, into the first drain buffer (columns
+        // 0..NT-1, idle once all products are done), so that the update below is a
+        // rolled loop over groups of 8 chains with one copy of its body: each pass
+        // reads 8 columns of h.H and of the small products.
 #pragma unroll
         for (int cb = 0; cb < 2; ++cb) {
             if (cb * 32 >= a.NT) break;
-            float v2[32];
-            tmem_ld32(tmem + lanes + (uint32_t)(128 + cb * 32), v2);
+            float w[32];
 #pragma unroll
-            for (int t8 = 0; t8 < 32; t8 += 8) {
-                const int nb = cb * 32 + t8;                         // first chain of the group of 8
+            for (int t = 0; t < 32; ++t) w[t] = acc[cb * 32 + t];
+            tmem_st32(tmem + lanes + (uint32_t)(cb * 32), w);
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+#pragma unroll 1
+        for (int nb = 0; nb < a.NT; nb += 8) {                       // first chain of the group of 8
+            float hv[8];                                             // h.H + small products
+            {
+                float hh[8], v2[8];
+                tmem_ld8x2(tmem + lanes + (uint32_t)nb, tmem + lanes + (uint32_t)(128 + nb), hh, v2);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) hv[t] = hh[t] + v2[t];
+            }
+            {
                 float zp[8], uo[8], cc[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
@@ -328,7 +342,7 @@ __device__ __forceinline__ void xupdate_tile(const CUtensorMap* tmM, const CUten
                     for (int qq = 0; qq < 5; ++qq) pr[qq][t] = 0.f;
                     if (!(rowok && s_live[nb + t])) continue;
                     const int tt = nb + t;
-                    const float prod = (acc[tt] + v2[t8 + t]) * (rinv * s_vrinv[tt]);
+                    const float prod = hv[t] * (rinv * s_vrinv[tt]);
                     const float x = cc[t] + a.rho * prod;
                     const int64_t sl = (int64_t)g * a.nchains + n0 + nb + t;
                     const int64_t o = sl * a.p + i;
