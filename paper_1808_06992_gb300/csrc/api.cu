@@ -22,6 +22,7 @@
 namespace uoi {
 
 thread_local int64_t g_launches = 0;
+thread_local bool g_fit_in_batch = false;
 
 void DevBuf::alloc(size_t n, cudaStream_t s)
 {
@@ -834,6 +835,7 @@ int uoi_lasso_fit_batch(int32_t count, const double* const* X, const double* con
         uoi::AdmmBatch* batch = nullptr;
         auto worker = [&]() {
             cudaSetDevice(dev);
+            uoi::g_fit_in_batch = true;
             cudaStream_t ws = nullptr;
             if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
                 for (int32_t t; (t = next.fetch_add(1)) < wave_end;) {

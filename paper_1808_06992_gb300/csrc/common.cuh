@@ -34,6 +34,9 @@ struct Error : std::runtime_error {
 // uoi_diag.gpu_launches; one fit runs on one thread).
 extern thread_local int64_t g_launches;
 inline void count_launch(int64_t n = 1) { g_launches += n; }
+// True on the worker threads of a batch of fits, whose fits share the device with
+// one another (a fit then adds no concurrency of its own).
+extern thread_local bool g_fit_in_batch;
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -785,15 +785,6 @@ int64_t launch_ols_mixed(OlsArgs a, cudaStream_t s)
     return ols_mixed_finish(R, s);
 }
 
-// A second stream per host thread for the small-support class of the loss pass,
-// which runs beside the large class (created once, kept for the thread's life).
-cudaStream_t side_stream()
-{
-    thread_local cudaStream_t side = nullptr;
-    if (!side) UOI_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    return side;
-}
-
 int64_t run_ols(OlsArgs a, cudaStream_t s)
 {
     a.smax = std::max(1, (int)family_support_max(a, s));
@@ -832,6 +823,16 @@ __global__ void k_union_cols(const uint64_t* fam, int64_t count, int W, int64_t 
 }
 
 }  // namespace
+
+// A second stream per host thread, for work that runs beside the thread's main
+// stream (the small-support class of the loss pass, half of the batch of the
+// tensor-core inverse); created once and kept for the thread's life.
+cudaStream_t side_stream()
+{
+    thread_local cudaStream_t side = nullptr;
+    if (!side) UOI_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    return side;
+}
 
 int32_t union_columns(const uint64_t* family, int64_t count, int64_t p, int32_t* cols,
                       cudaStream_t s)

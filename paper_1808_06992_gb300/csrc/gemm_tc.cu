@@ -25,6 +25,8 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <exception>
+#include <future>
 #include <mutex>
 
 #include "kernels.h"
@@ -372,25 +374,51 @@ __global__ void k_transpose_block(const float* src, int64_t lds, float* dst, int
     }
 }
 
+// Device scratch of one run of the recursion, taken in last-in-first-out order
+// from one allocation sized beforehand by inv_scratch_bytes: nothing is allocated
+// or freed inside the recursion.  Taking more than the capacity throws.
+struct InvScratch {
+    char* base = nullptr;
+    size_t cap = 0, top = 0;
+    template <typename T> T* take(int64_t count)
+    {
+        const size_t bytes = ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
+        if (top + bytes > cap) throw Error(UOI_ERR_OOM, "tensor-core inverse: scratch plan exceeded");
+        T* q = reinterpret_cast<T*>(base + top);
+        top += bytes;
+        return q;
+    }
+};
+
+size_t scratch_round(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+
 struct Pieces {
-    DevBuf buf;
-    DevBuf sinv;                   // G: 1 / scale
+    __half* buf = nullptr;
+    float* sinv = nullptr;         // G: 1 / scale
     CUtensorMap map;
     int32_t tiles = 0, kst = 0;
 };
 
+// Scratch bytes of one operand's pieces (the fp16 pieces and the G inverse scales).
+size_t pieces_bytes(int64_t rows, int64_t K, int32_t rt, int32_t G)
+{
+    const int64_t rpad = ceil_div(rows, rt) * rt, kpad = ceil_div(K, GT_TK) * GT_TK;
+    return scratch_round(sizeof(__half) * GT_PIECES * (size_t)G * rpad * kpad) +
+           scratch_round(sizeof(float) * (size_t)G);
+}
+
 // Split op(S) into scaled pieces for a GEMM operand with row tiles of rt; smax
 // (G, float bits) holds each S_g's largest magnitude.
-void make_pieces(Pieces& P, const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K, bool trans,
-                 int32_t rt, int32_t G, const uint32_t* smax, cudaStream_t s)
+void make_pieces(Pieces& P, InvScratch& W, const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K,
+                 bool trans, int32_t rt, int32_t G, const uint32_t* smax, cudaStream_t s)
 {
     const int64_t rpad = ceil_div(rows, rt) * rt, kpad = ceil_div(K, GT_TK) * GT_TK;
     P.tiles = (int32_t)(rpad / rt);
     P.kst = (int32_t)(kpad / GT_TK);
-    P.buf.alloc(sizeof(__half) * GT_PIECES * (size_t)G * rpad * kpad, s);
-    P.sinv.alloc(sizeof(float) * (size_t)G, s);
+    P.buf = W.take<__half>(GT_PIECES * (int64_t)G * rpad * kpad);
+    P.sinv = W.take<float>(G);
     k_split_blocks<<<dim3((unsigned)(rpad / 32), (unsigned)ceil_div(kpad / 32, 4), (unsigned)G), dim3(32, 8), 0, s>>>(
-        src, ld, gs, rows, K, trans ? 1 : 0, rt, rpad, kpad, smax, P.sinv.as<float>(), P.buf.as<__half>());
+        src, ld, gs, rows, K, trans ? 1 : 0, rt, rpad, kpad, smax, P.sinv, P.buf);
     UOI_CHECK_LAUNCH();
     count_launch();
     // blocks of rt x 32 fp16 (64-byte rows); two consecutive blocks per stage
@@ -399,7 +427,7 @@ void make_pieces(Pieces& P, const float* src, int64_t ld, int64_t gs, int32_t ro
     cuuint64_t strides[2] = { 64u, (cuuint64_t)rt * 64u };
     cuuint32_t box[3] = { 32u, (cuuint32_t)rt, (cuuint32_t)GT_PIECES };
     cuuint32_t estr[3] = { 1, 1, 1 };
-    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P.buf.ptr, dims, strides, box,
+    CUresult res = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, P.buf, dims, strides, box,
                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -413,14 +441,17 @@ void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, fl
            cudaStream_t s, uint32_t* dmax = nullptr)
 {
     if (A.kst != B.kst) throw Error(UOI_ERR_INVALID_ARG, "gemm3: operand k extents differ");
-    UOI_CUDA(cudaFuncSetAttribute(k_gemm3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM));
+    static std::once_flag once;
+    std::call_once(once, [] {
+        UOI_CUDA(cudaFuncSetAttribute(k_gemm3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM));
+    });
     GemmArgs a;
     a.m = m; a.n = n; a.kst = A.kst; a.MT = A.tiles; a.NT = B.tiles;
     a.alpha = alpha; a.beta = beta;
     a.C = C; a.ldc = ldc; a.gsc = gsc;
     a.D = D; a.ldd = ldd; a.gsd = gsd;
-    a.ainv = A.sinv.as<float>();
-    a.binv = B.sinv.as<float>();
+    a.ainv = A.sinv;
+    a.binv = B.sinv;
     a.dmax = dmax;
     a.err = err;
     const dim3 grid((unsigned)ceil_div(m, GT_TM), (unsigned)ceil_div(n, GT_TN), (unsigned)G);
@@ -443,7 +474,7 @@ void gemm3(const Pieces& A, const Pieces& B, int32_t m, int32_t n, int32_t G, fl
 // Gauss-Jordan elimination: the same products, four barriers per 32 pivots
 // instead of one per pivot).  Rows and columns past n hold zeros and the padded
 // part of the last diagonal block is inverted as the identity, so they never
-// reach the n x n result.  A pivot <= 0 sets status UOI_ERR_NOT_PD (where = group).
+// reach the n x n result.  A pivot <= 0 sets status UOI_ERR_NOT_PD (where = g0 + group).
 constexpr int GJ_LD = 33;                              // shared rows: conflict-free columns
 template <int R>
 constexpr size_t gj_smem_bytes() { return sizeof(float) * (size_t)(3 * 32 * R * GJ_LD + 32 * GJ_LD); }
@@ -480,7 +511,7 @@ __device__ __noinline__ bool gj_invert_diag(const float* D, float* P, int bk)
 template <int R>
 __global__ void __launch_bounds__(1024) k_spd_inverse_blocked(const float* A, int64_t lda, int64_t gsa,
                                                               float* M, int64_t ldm, int64_t gsm, int n,
-                                                              DevStatus* st)
+                                                              int g0, DevStatus* st)
 {
     extern __shared__ float sm[];
     float* colK = sm;                           // [32R][LD]: colK[i][k] = A(i, 32K + k) before step K
@@ -516,7 +547,7 @@ __global__ void __launch_bounds__(1024) k_spd_inverse_blocked(const float* A, in
         }
         __syncthreads();
         if (bad) {
-            if (threadIdx.x == 0) dev_fail(st, UOI_ERR_NOT_PD, g);
+            if (threadIdx.x == 0) dev_fail(st, UOI_ERR_NOT_PD, g0 + g);
             return;                             // same decision in every thread
         }
         // block row K: this warp's row 32K + ty becomes row ty of P A_K.
@@ -566,7 +597,7 @@ __global__ void __launch_bounds__(1024) k_spd_inverse_blocked(const float* A, in
 
 template <int R>
 void launch_inverse_blocked(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM, int64_t gsM,
-                            int64_t n, int32_t G, DevStatus* st, cudaStream_t s)
+                            int64_t n, int32_t G, int32_t g0, DevStatus* st, cudaStream_t s)
 {
     static std::once_flag once;
     std::call_once(once, [] {
@@ -574,18 +605,18 @@ void launch_inverse_blocked(const float* A, int64_t ldA, int64_t gsA, float* Mou
                                       (int)gj_smem_bytes<R>()));
     });
     k_spd_inverse_blocked<R><<<(unsigned)G, 1024, gj_smem_bytes<R>(), s>>>(A, ldA, gsA, Mout, ldM, gsM,
-                                                                           (int)n, st);
+                                                                           (int)n, g0, st);
 }
 
 void inv_base(const float* A, int64_t ldA, int64_t gsA, float* Mout, int64_t ldM, int64_t gsM,
-              int64_t n, int32_t G, DevStatus* st, cudaStream_t s)
+              int64_t n, int32_t G, int32_t g0, DevStatus* st, cudaStream_t s)
 {
     if (n <= 64)
-        launch_inverse_blocked<2>(A, ldA, gsA, Mout, ldM, gsM, n, G, st, s);
+        launch_inverse_blocked<2>(A, ldA, gsA, Mout, ldM, gsM, n, G, g0, st, s);
     else if (n <= 128)
-        launch_inverse_blocked<4>(A, ldA, gsA, Mout, ldM, gsM, n, G, st, s);
+        launch_inverse_blocked<4>(A, ldA, gsA, Mout, ldM, gsM, n, G, g0, st, s);
     else
-        launch_inverse_blocked<6>(A, ldA, gsA, Mout, ldM, gsM, n, G, st, s);
+        launch_inverse_blocked<6>(A, ldA, gsA, Mout, ldM, gsM, n, G, g0, st, s);
     UOI_CHECK_LAUNCH();
     count_launch();
 }
@@ -597,14 +628,37 @@ void diag_max(const float* A, int64_t lda, int64_t gsa, int64_t n, int32_t G, ui
     count_launch();
 }
 
+// Split point of the recursion: the leading block, a multiple of the GEMM's row tile.
+int64_t inv_split(int64_t n) { return ceil_div(n / 2, GT_TM) * GT_TM; }
+
+// Peak scratch of inv_rec(n, G): the same takes in the same order as inv_rec.
+size_t inv_scratch_bytes(int64_t n, int32_t G)
+{
+    if (n <= INV_BASE) return 0;
+    const int64_t p1 = inv_split(n), p2 = n - p1;
+    const size_t mx = scratch_round(sizeof(uint32_t) * 5 * (size_t)G);
+    const size_t U = scratch_round(sizeof(float) * (size_t)G * p2 * p1);
+    const size_t S = scratch_round(sizeof(float) * (size_t)G * p2 * p2);
+    const size_t prod_u_s = pieces_bytes(p2, p1, GT_TM, G) + pieces_bytes(p1, p1, GT_TN, G) +
+                            pieces_bytes(p2, p1, GT_TN, G);                       // pa, pb, pu
+    const size_t prod_m21 = pieces_bytes(p2, p2, GT_TM, G) + pieces_bytes(p1, p2, GT_TN, G);   // py, put
+    const size_t prod_m11 = pieces_bytes(p1, p2, GT_TM, G) + pieces_bytes(p1, p2, GT_TN, G);   // pua, pmt
+    size_t peak = inv_scratch_bytes(p1, G);                                     // X = A11^{-1}
+    peak = std::max(peak, U + S + std::max(prod_u_s, inv_scratch_bytes(p2, G)));  // U, S, then Y = S^{-1}
+    peak = std::max(peak, U + std::max(prod_m21, prod_m11));
+    return mx + peak;
+}
+
+// g0: index of the first of the G systems in the caller's batch (for error reports).
 void inv_rec(const float* A, int64_t ldA, int64_t gsA, float* M, int64_t ldM, int64_t gsM, int64_t n,
-             int32_t G, DevStatus* st, int32_t* err, cudaStream_t s)
+             int32_t G, int32_t g0, DevStatus* st, int32_t* err, InvScratch& W, cudaStream_t s)
 {
     if (n <= INV_BASE) {
-        inv_base(A, ldA, gsA, M, ldM, gsM, n, G, st, s);
+        inv_base(A, ldA, gsA, M, ldM, gsM, n, G, g0, st, s);
         return;
     }
-    const int64_t p1 = ceil_div(n / 2, GT_TM) * GT_TM, p2 = n - p1;
+    const size_t top0 = W.top;
+    const int64_t p1 = inv_split(n), p2 = n - p1;
     const float* A21 = A + p1 * ldA;
     const float* A22 = A + p1 * ldA + p1;
     float* X = M;                                  // M11 block, holds X = A11^{-1} first
@@ -613,54 +667,69 @@ void inv_rec(const float* A, int64_t ldA, int64_t gsA, float* M, int64_t ldM, in
     float* Y = M + p1 * ldM + p1;
     // largest magnitudes of the split operands (float bits per group): A, X, Y are
     // SPD (their largest diagonal entry), U and M21 come from the GEMM epilogues
-    DevBuf mx(sizeof(uint32_t) * 5 * (size_t)G, s);
-    UOI_CUDA(cudaMemsetAsync(mx.ptr, 0, mx.bytes, s));
-    uint32_t* mA = mx.as<uint32_t>();
+    uint32_t* mA = W.take<uint32_t>(5 * (int64_t)G);
+    UOI_CUDA(cudaMemsetAsync(mA, 0, sizeof(uint32_t) * 5 * (size_t)G, s));
     uint32_t* mX = mA + G;
     uint32_t* mU = mA + 2 * G;
     uint32_t* mY = mA + 3 * G;
     uint32_t* mM21 = mA + 4 * G;
     diag_max(A, ldA, gsA, n, G, mA, s);
     // X = A11^{-1}
-    inv_rec(A, ldA, gsA, X, ldM, gsM, p1, G, st, err, s);
+    inv_rec(A, ldA, gsA, X, ldM, gsM, p1, G, g0, st, err, W, s);
     diag_max(X, ldM, gsM, p1, G, mX, s);
     // U = A21 X   (p2 x p1)
-    DevBuf U(sizeof(float) * (size_t)(G * p2 * p1), s), S(sizeof(float) * (size_t)(G * p2 * p2), s);
+    float* U = W.take<float>((int64_t)G * p2 * p1);
+    const size_t top_u = W.top;
+    float* S = W.take<float>((int64_t)G * p2 * p2);
+    const size_t top_s = W.top;
     {
         Pieces pa, pb;
-        make_pieces(pa, A21, ldA, gsA, (int32_t)p2, (int32_t)p1, false, GT_TM, G, mA, s);
-        make_pieces(pb, X, ldM, gsM, (int32_t)p1, (int32_t)p1, false, GT_TN, G, mX, s);
-        gemm3(pa, pb, (int32_t)p2, (int32_t)p1, G, 1.f, 0.f, nullptr, 0, 0, U.as<float>(), p1, p2 * p1,
-              err, s, mU);
+        make_pieces(pa, W, A21, ldA, gsA, (int32_t)p2, (int32_t)p1, false, GT_TM, G, mA, s);
+        make_pieces(pb, W, X, ldM, gsM, (int32_t)p1, (int32_t)p1, false, GT_TN, G, mX, s);
+        gemm3(pa, pb, (int32_t)p2, (int32_t)p1, G, 1.f, 0.f, nullptr, 0, 0, U, p1, p2 * p1, err, s, mU);
         // S = A22 - A21 U^T   (p2 x p2)
         Pieces pu;
-        make_pieces(pu, U.as<float>(), p1, p2 * p1, (int32_t)p2, (int32_t)p1, false, GT_TN, G, mU, s);
-        gemm3(pa, pu, (int32_t)p2, (int32_t)p2, G, -1.f, 1.f, A22, ldA, gsA, S.as<float>(), p2, p2 * p2,
-              err, s);
+        make_pieces(pu, W, U, p1, p2 * p1, (int32_t)p2, (int32_t)p1, false, GT_TN, G, mU, s);
+        gemm3(pa, pu, (int32_t)p2, (int32_t)p2, G, -1.f, 1.f, A22, ldA, gsA, S, p2, p2 * p2, err, s);
     }
+    W.top = top_s;
     // Y = S^{-1}
-    inv_rec(S.as<float>(), p2, p2 * p2, Y, ldM, gsM, p2, G, st, err, s);
-    S.release();
+    inv_rec(S, p2, p2 * p2, Y, ldM, gsM, p2, G, g0, st, err, W, s);
+    W.top = top_u;                                 // S is no longer needed
     diag_max(Y, ldM, gsM, p2, G, mY, s);
     {
         // M21 = -Y U   (p2 x p1): A = Y (p2 x p2), B rows = columns of U
         Pieces py, put;
-        make_pieces(py, Y, ldM, gsM, (int32_t)p2, (int32_t)p2, false, GT_TM, G, mY, s);
-        make_pieces(put, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mU, s);
+        make_pieces(py, W, Y, ldM, gsM, (int32_t)p2, (int32_t)p2, false, GT_TM, G, mY, s);
+        make_pieces(put, W, U, p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mU, s);
         gemm3(py, put, (int32_t)p2, (int32_t)p1, G, -1.f, 0.f, nullptr, 0, 0, M21, ldM, gsM, err, s, mM21);
     }
+    W.top = top_u;
     {
         // M11 = X - U^T M21   (p1 x p1): A rows = columns of U, B rows = columns of M21
         Pieces pua, pmt;
-        make_pieces(pua, U.as<float>(), p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TM, G, mU, s);
-        make_pieces(pmt, M21, ldM, gsM, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mM21, s);
+        make_pieces(pua, W, U, p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TM, G, mU, s);
+        make_pieces(pmt, W, M21, ldM, gsM, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mM21, s);
         gemm3(pua, pmt, (int32_t)p1, (int32_t)p1, G, -1.f, 1.f, X, ldM, gsM, X, ldM, gsM, err, s);
     }
+    W.top = top0;
     // M12 = M21^T
     k_transpose_block<<<dim3((unsigned)ceil_div(p1, 32), (unsigned)ceil_div(p2, 32), (unsigned)G),
                         dim3(32, 8), 0, s>>>(M21, ldM, M12, ldM, gsM, (int32_t)p1, (int32_t)p2);
     UOI_CHECK_LAUNCH();
     count_launch();
+}
+
+// The recursion for G systems on stream s, with its scratch taken from one
+// allocation on s.
+void inv_chain(const float* A, int64_t p, int32_t G, int32_t g0, float* M, DevStatus* st, int32_t* err,
+               cudaStream_t s)
+{
+    InvScratch W;
+    W.cap = inv_scratch_bytes(p, G);
+    DevBuf ws(W.cap, s);
+    W.base = ws.as<char>();
+    inv_rec(A, p, p * p, M, p, p * p, p, G, g0, st, err, W, s);
 }
 
 }  // namespace
@@ -671,7 +740,51 @@ void spd_inverse_tc(const float* A, int64_t p, int32_t G, float* M, DevStatus* s
 {
     DevBuf err(sizeof(int32_t), s);
     UOI_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), s));
-    inv_rec(A, p, p * p, M, p, p * p, p, G, st, err.as<int32_t>(), s);
+    // Below the top levels the recursion is a chain of short launches (leaves of one
+    // CTA per system, GEMMs of one tile per system) whose time does not shrink with
+    // the batch.  Two halves of a batch of 8 or more therefore run as two chains side
+    // by side, each enqueued by its own host thread: the short launches of one fill
+    // the SMs the other leaves idle.  Each system's arithmetic is unchanged.  Not on
+    // the workers of a batch of fits, which already share the device.
+    const int32_t G2 = (G >= 8 && p > INV_BASE && !g_fit_in_batch) ? G / 2 : 0, G1 = G - G2;
+    if (G2 == 0) {
+        inv_chain(A, p, G, 0, M, st, err.as<int32_t>(), s);
+    } else {
+        const int64_t pp = p * p;
+        cudaStream_t side = side_stream();
+        int dev = 0;
+        UOI_CUDA(cudaGetDevice(&dev));
+        cudaEvent_t ready = nullptr, done = nullptr;
+        UOI_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        UOI_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        UOI_CUDA(cudaEventRecord(ready, s));
+        UOI_CUDA(cudaStreamWaitEvent(side, ready, 0));
+        int32_t* e = err.as<int32_t>();
+        std::future<int64_t> second = std::async(std::launch::async, [=]() -> int64_t {
+            UOI_CUDA(cudaSetDevice(dev));
+            const int64_t l0 = g_launches;               // this thread's own counter
+            inv_chain(A + G1 * pp, p, G2, G1, M + G1 * pp, st, e, side);
+            return g_launches - l0;
+        });
+        std::exception_ptr first_err;
+        try {
+            inv_chain(A, p, G1, 0, M, st, e, s);
+        } catch (...) {
+            first_err = std::current_exception();
+        }
+        std::exception_ptr second_err;
+        try {
+            count_launch(second.get());
+        } catch (...) {
+            second_err = std::current_exception();
+        }
+        UOI_CUDA(cudaEventRecord(done, side));
+        UOI_CUDA(cudaStreamWaitEvent(s, done, 0));
+        cudaEventDestroy(ready);
+        cudaEventDestroy(done);
+        if (first_err) std::rethrow_exception(first_err);
+        if (second_err) std::rethrow_exception(second_err);
+    }
     int32_t herr = 0;
     UOI_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     UOI_CUDA(cudaStreamSynchronize(s));

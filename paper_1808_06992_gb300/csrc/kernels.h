@@ -161,9 +161,14 @@ template <typename T>
 void rhs_from_inverse(const T* M, const double* Bm, const double* nk, int64_t p, int64_t r, int32_t B,
                       T* c, cudaStream_t s, T* rhs_scratch = nullptr);
 // M_k = A_k^{-1} for SPD A_k (FP32, p x p each) by block Schur-complement recursion
-// with FP32-accurate tensor-core GEMMs (gemm_tc.cu); A is left unchanged.
+// with FP32-accurate tensor-core GEMMs (gemm_tc.cu); A is left unchanged.  A batch
+// of 8 or more runs as two halves side by side, on s and on the calling thread's
+// side stream (the second half enqueued by a helper thread; not on the workers of
+// a batch of fits); s waits for both.
 bool inverse_tc_available();
 void spd_inverse_tc(const float* A, int64_t p, int32_t G, float* M, DevStatus* status, cudaStream_t s);
+// The calling host thread's second stream (estimate.cu).
+cudaStream_t side_stream();
 // M_k = A_k^{-1} from the factor L (lower triangle of A), then
 // c_k[e][i] = (M_k Bm_k)[i][e] / nk[k].
 template <typename T>
