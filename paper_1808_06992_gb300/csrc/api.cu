@@ -512,10 +512,18 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
         Xd = dev_in(X, (size_t)((m - 1) * ldx + p), hx, s);
         Yd = dev_in(Y, (size_t)((m - 1) * ldy + r), hy, s);
     }
+    // mixed form: one FP32 copy of X feeds every tensor-core moment pass; without an
+    // intercept (X used as given) it is made here, in the same pass as X's check
+    DevBuf X32;
     {
         DevBuf flag(sizeof(int32_t), s);
         UOI_CUDA(cudaMemsetAsync(flag.ptr, 0, sizeof(int32_t), s));
-        check_finite(Xd, ldx, m, p, flag.as<int32_t>(), s);
+        if (tc_moments && param_intercept(prm) == 0) {
+            X32.alloc(sizeof(float) * (size_t)(m * ldx), s);
+            to_f32(Xd, ldx, m, p, X32.as<float>(), s, flag.as<int32_t>());
+        } else {
+            check_finite(Xd, ldx, m, p, flag.as<int32_t>(), s);
+        }
         check_finite(Yd, ldy, m, r, flag.as<int32_t>(), s);
         int32_t h = 0;
         UOI_CUDA(cudaMemcpyAsync(&h, flag.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -575,9 +583,7 @@ int fit_core(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t
     WsModel* ws = prm->warm_start == UOI_WARM_LEARNED ? ws_for_path(prm->mlp_weights_path, s) : nullptr;
     const int32_t warm_used = prm->warm_start == UOI_WARM_LEARNED ? (ws ? UOI_WARM_LEARNED : UOI_WARM_PATH)
                                                                   : prm->warm_start;
-    // mixed form: one FP32 copy of X feeds every tensor-core moment pass
-    DevBuf X32;
-    if (tc_moments) {
+    if (tc_moments && !X32.ptr) {                   // with an intercept: the centred design
         X32.alloc(sizeof(float) * (size_t)(m * ldx), s);
         to_f32(Xd, ldx, m, pe, X32.as<float>(), s);
     }

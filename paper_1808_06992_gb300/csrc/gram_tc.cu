@@ -671,30 +671,42 @@ void gather_cols_f32(const float* X32, int64_t ld, int64_t m, const int32_t* col
 
 namespace {
 // Contiguous rows (ldx == p): one flat loop; otherwise rows over blocks and
-// columns over threads.  No division per element.
+// columns over threads.  No division per element.  With a flag, each value's
+// exponent field is also tested (all ones = Inf or NaN): one flag write per warp
+// that saw a non-finite value.
 __global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, int64_t m, int64_t p,
-                         float* __restrict__ out)
+                         float* __restrict__ out, int32_t* flag)
 {
+    bool bad = false;
     if (ldx == p) {
         const int64_t total = m * p;
 #pragma unroll 4
         for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-             t += (int64_t)gridDim.x * blockDim.x)
-            out[t] = f64_to_f32_int(__ldg(X + t));
-        return;
-    }
-    for (int64_t row = blockIdx.x; row < m; row += gridDim.x) {
-        const double* xr = X + row * ldx;
-        float* orow = out + row * ldx;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const double x = __ldg(X + t);
+            bad |= ((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF;
+            out[t] = f64_to_f32_int(x);
+        }
+    } else {
+        for (int64_t row = blockIdx.x; row < m; row += gridDim.x) {
+            const double* xr = X + row * ldx;
+            float* orow = out + row * ldx;
 #pragma unroll 4
-        for (int64_t j = threadIdx.x; j < p; j += blockDim.x) orow[j] = f64_to_f32_int(__ldg(xr + j));
+            for (int64_t j = threadIdx.x; j < p; j += blockDim.x) {
+                const double x = __ldg(xr + j);
+                bad |= ((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF;
+                orow[j] = f64_to_f32_int(x);
+            }
+        }
     }
+    if (flag && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
 }
 }  // namespace
 
-void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cudaStream_t s)
+void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cudaStream_t s, int32_t* flag)
 {
-    k_to_f32<<<(unsigned)std::min<int64_t>(ceil_div(m * p, 256), 152 * 64), 256, 0, s>>>(X, ldx, m, p, out);
+    k_to_f32<<<(unsigned)std::min<int64_t>(ceil_div(m * p, 256), 152 * 64), 256, 0, s>>>(X, ldx, m, p, out,
+                                                                                          flag);
     UOI_CHECK_LAUNCH();
     count_launch();
 }

@@ -121,8 +121,10 @@ bool gram_tc_available();
 void moments_tc(const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t m, int64_t p,
                 int64_t r, const uint32_t* w, const uint8_t* mask, int32_t B, double* G,
                 double* Bm, cudaStream_t s, const float* X32 = nullptr, bool lower_only = false);
-// out[i*ldx + j] = X[i*ldx + j] rounded to FP32, i < m, j < p.
-void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cudaStream_t s);
+// out[i*ldx + j] = X[i*ldx + j] rounded to FP32, i < m, j < p; with a flag, also
+// *flag = 1 if any of those X entries is NaN or Inf (the same test as check_finite).
+void to_f32(const double* X, int64_t ldx, int64_t m, int64_t p, float* out, cudaStream_t s,
+            int32_t* flag = nullptr);
 
 // Tensor-core moments restricted to the pz_x X columns listed in colmap (written
 // into p_out x p_out / p_out x r outputs at the original feature indices).

@@ -425,41 +425,33 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     xupdate_tile<XT_STAGES>(&tmM, &tmV, a, (int)blockIdx.x, ct, g);
 }
 
-// Per-row scale of M_g: row_scale = 2^(10 - e) for the row's largest |M_ik| =
-// f 2^e (1 for an all-zero or padding row), row_inv = 1 / row_scale.  One warp per row.
-__global__ void k_row_scale(const float* M, int32_t G, int64_t p, int64_t ppad, float* row_scale,
-                            float* row_inv)
+// M_g (FP32, p x p) -> per-row scales and the two fp16 pieces of each row times its
+// scale, one warp per row.  row_scale = 2^(10 - e) for the row's largest |M_ik| =
+// f 2^e (1 for an all-zero or padding row), row_inv = 1 / row_scale.  The pieces go
+// to 128 x 32 blocks ordered [g][row tile][k block][piece][128][32] (zero padded), so
+// that the x-update streams each row tile as one contiguous run of 16 KB stages.
+// The row is read from DRAM once for its largest magnitude and again, from L2, for
+// the split: each lane takes 8 consecutive k at a time and writes 16 bytes per piece.
+__global__ void k_scale_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
+                                float* row_scale, float* row_inv, __half* out)
 {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= (int64_t)G * ppad) return;
     const int64_t g = row / ppad, i = row % ppad;
+    const float* mr = M + ((size_t)g * p + (i < p ? i : 0)) * p;
     float mx = 0.f;
     if (i < p)
-        for (int64_t k = lane; k < p; k += 32) mx = fmaxf(mx, fabsf(M[((size_t)g * p + i) * p + k]));
+        for (int64_t k = lane; k < p; k += 32) mx = fmaxf(mx, fabsf(mr[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float sc = pow2_scale(mx);
     if (lane == 0) {
-        const float sc = pow2_scale(mx);
         row_scale[row] = sc;
         row_inv[row] = 1.f / sc;
     }
-}
-
-// M_g (FP32, p x p), each row times its scale -> two fp16 pieces in 128 x 32
-// blocks, ordered [g][row tile][k block][piece][128][32] (zero padded), so that
-// the x-update streams each row tile as one contiguous run of 16 KB stages.  One
-// thread per 8 consecutive k: a 32-byte read and one 16-byte write per piece.
-__global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
-                          const float* row_scale, __half* out)
-{
-    const int64_t per8 = (int64_t)G * ppad * (kpad / 8);
     const int64_t RT = ppad / XT_TM, kst = kpad / XT_TK;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per8;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k8 = (t % (kpad / 8)) * 8, row = t / (kpad / 8);
-        const int64_t g = row / ppad, i = row % ppad;
-        const float sc = row_scale[row];
+    for (int64_t k8 = (int64_t)lane * 8; k8 < kpad; k8 += 256) {
         uint32_t ph[4], pl[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -467,7 +459,7 @@ __global__ void k_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, in
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int64_t k = k8 + 2 * q + u;
-                const float x = (i < p && k < p) ? M[((size_t)g * p + i) * p + k] * sc : 0.f;
+                const float x = (i < p && k < p) ? mr[k] * sc : 0.f;
                 split2(x, h[u], l[u]);
             }
             ph[q] = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
@@ -811,12 +803,9 @@ void xt_prepare(const AdmmProblem<float>& P, cudaStream_t s, XtMember& m)
     const int64_t ppad = m.ppad, kpad = m.kpad, slots = m.slots;
     m.rs.alloc(sizeof(float) * (size_t)P.G * ppad, s);
     m.rinv.alloc(sizeof(float) * (size_t)P.G * ppad, s);
-    k_row_scale<<<(unsigned)ceil_div((int64_t)P.G * ppad * 32, 256), 256, 0, s>>>(P.M, P.G, p, ppad,
-                                                                                m.rs.as<float>(), m.rinv.as<float>());
-    UOI_CHECK_LAUNCH();
     m.mp.alloc(sizeof(__half) * XT_PIECES * (size_t)P.G * ppad * kpad, s);
-    k_split_m<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)P.G * ppad * kpad / 8, 256), 8192), 256, 0, s>>>(
-        P.M, P.G, p, ppad, kpad, m.rs.as<float>(), m.mp.as<__half>());
+    k_scale_split_m<<<(unsigned)ceil_div((int64_t)P.G * ppad * 32, 256), 256, 0, s>>>(
+        P.M, P.G, p, ppad, kpad, m.rs.as<float>(), m.rinv.as<float>(), m.mp.as<__half>());
     UOI_CHECK_LAUNCH();
     m.zb.alloc(sizeof(float) * (size_t)slots * p, s);
     m.ub.alloc(sizeof(float) * (size_t)slots * p, s);
@@ -847,7 +836,7 @@ void xt_prepare(const AdmmProblem<float>& P, cudaStream_t s, XtMember& m)
     k_xt_slots<<<(unsigned)std::min<int64_t>(ceil_div(slots, 256), 4096), 256, 0, s>>>(
         P.G, m.nchains, (int32_t)P.r, P.q, P.warm, m.sj.as<int32_t>(), m.sje.as<int32_t>(), m.sit.as<int32_t>());
     UOI_CHECK_LAUNCH();
-    count_launch(6);
+    count_launch(5);
     m.mM = make_map_bf16_blocks32(m.mp.ptr, (int64_t)P.G * m.RT * m.kst * XT_PIECES, XT_PIECES,
                                   CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
 }
