@@ -266,27 +266,50 @@ k_gemm3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
 }
 
-// Two fp16 pieces of op(S_g) (rows x K; op = transpose if trans), scaled by the
-// power of two of S_g's largest magnitude smax[g] (float bits), in blocks of
-// rt x 32, ordered [g][row tile][k block][piece][rt][32], zero padded to the tile
-// multiples; sinv[g] = 1 / scale.  S_g element (i, k) is at src[g*gs + i*ld + k]
-// (or src[g*gs + k*ld + i] transposed).  32 x 32 tiles through shared memory, so
-// that both the read (along the source's contiguous index) and the write (along
-// k) are coalesced.  Block (32, 8); grid (rpad/32, kpad/32, G).
-__global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K,
-                               int32_t trans, int32_t rt, int64_t rpad, int64_t kpad,
-                               const uint32_t* smax, float* sinv, __half* out)
+// One operand split: the two fp16 pieces of op(S_g) (rows x K; op = transpose if
+// trans), scaled by the power of two of S_g's largest magnitude smax[g] (float
+// bits), in blocks of rt x 32, ordered [g][row tile][k block][piece][rt][32], zero
+// padded to the tile multiples; sinv[g] = 1 / scale.  S_g element (i, k) is at
+// src[g*gs + i*ld + k] (or src[g*gs + k*ld + i] transposed).
+constexpr int SPLIT_KC = 4;                            // 32-k blocks per CTA
+struct SplitJob {
+    const float* src;
+    int64_t ld, gs;
+    int32_t rows, K, trans, rt;
+    int64_t rpad, kpad;
+    const uint32_t* smax;
+    float* sinv;
+    __half* out;
+    int32_t nbx, nby;                                  // CTAs per group: rpad / 32 x ceil(kpad / (32 SPLIT_KC))
+};
+// Up to two independent splits in one launch: CTA b < first1 works on job 0, the
+// rest on job 1 (each job's CTAs ordered [g][k group][row block]).
+struct SplitJobs {
+    SplitJob j[2];
+    int64_t first1;
+};
+
+// 32 x 32 tiles through shared memory, so that both the read (along the source's
+// contiguous index) and the write (along k) are coalesced.  Block (32, 8); a CTA
+// covers 32 rows x SPLIT_KC blocks of 32 k, and every thread issues all of its
+// 4 x SPLIT_KC loads before its first store, so more bytes are in flight per SM.
+__global__ void k_split_blocks(const __grid_constant__ SplitJobs J, int32_t G)
 {
-    // a block covers 32 rows x SPLIT_KC blocks of 32 k: every thread issues all of its
-    // 4 x SPLIT_KC loads before its first store, so more bytes are in flight per SM
-    constexpr int SPLIT_KC = 4;
     __shared__ float tile[SPLIT_KC][32][33];            // [k block][k local][i local]
-    const int64_t g = blockIdx.z;
-    const int64_t i0 = (int64_t)blockIdx.x * 32, kb0 = (int64_t)blockIdx.y * SPLIT_KC;
+    const int64_t b = blockIdx.x;
+    const int jj = b < J.first1 ? 0 : 1;
+    const SplitJob& P = J.j[jj];
+    const int64_t local = b - (jj ? J.first1 : 0);
+    const int64_t per_g = (int64_t)P.nbx * P.nby;
+    const int64_t g = local / per_g, rem = local % per_g;
+    const int64_t bx = rem % P.nbx, by = rem / P.nbx;
+    const int64_t i0 = bx * 32, kb0 = by * SPLIT_KC;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const float* sg = src + g * gs;
-    const float sc = pow2_scale(__uint_as_float(smax[g]));
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0 && ty == 0) sinv[g] = 1.f / sc;
+    const int32_t rows = P.rows, K = P.K, rt = P.rt;
+    const int64_t ld = P.ld, rpad = P.rpad, kpad = P.kpad;
+    const float* sg = P.src + g * P.gs;
+    const float sc = pow2_scale(__uint_as_float(P.smax[g]));
+    if (bx == 0 && by == 0 && tx == 0 && ty == 0) P.sinv[g] = 1.f / sc;
     const int64_t kst = kpad / GT_TK;
     float v[SPLIT_KC][4];
 #pragma unroll
@@ -295,7 +318,7 @@ __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = ty + 8 * u;
-            if (trans) {
+            if (P.trans) {
                 const int64_t i = i0 + tx, k = k0 + j;
                 v[c][u] = (i < rows && k < K) ? sg[k * ld + i] : 0.f;
             } else {
@@ -309,15 +332,15 @@ __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = ty + 8 * u;
-            if (trans) tile[c][j][tx] = v[c][u];
+            if (P.trans) tile[c][j][tx] = v[c][u];
             else tile[c][tx][j] = v[c][u];
         }
     __syncthreads();
-    // write: thread (row jj, k quad kq) splits four consecutive k of one row and
-    // stores 8-byte runs of each piece (conflict-free reads: bank = kq + u + jj)
+    // write: thread (row r, k quad kq) splits four consecutive k of one row and
+    // stores 8-byte runs of each piece (conflict-free reads: bank = kq + u + r)
     const int64_t RT = rpad / rt;
-    const int t = ty * 32 + tx, jj = t >> 3, kq = (t & 7) << 2;
-    const int64_t i = i0 + jj;
+    const int t = ty * 32 + tx, r = t >> 3, kq = (t & 7) << 2;
+    const int64_t i = i0 + r;
 #pragma unroll
     for (int c = 0; c < SPLIT_KC; ++c) {
         const int64_t kb = kb0 + c;
@@ -325,15 +348,15 @@ __global__ void k_split_blocks(const float* src, int64_t ld, int64_t gs, int32_t
         const int64_t k = kb * 32 + kq;
         __half h[4], l[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) split2(tile[c][kq + u][jj] * sc, h[u], l[u]);
+        for (int u = 0; u < 4; ++u) split2(tile[c][kq + u][r] * sc, h[u], l[u]);
         const int64_t blk = ((g * RT + i / rt) * kst + kb) * GT_PIECES;
         const int64_t o = (blk * rt + i % rt) * GT_TK + k % GT_TK;             // multiple of 4
-        if (!UOI_IN_BOUNDS(o + rt * GT_TK + 3, (int64_t)gridDim.z * rpad * kpad * GT_PIECES, 401)) return;
+        if (!UOI_IN_BOUNDS(o + rt * GT_TK + 3, (int64_t)G * rpad * kpad * GT_PIECES, 401)) return;
         const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
         const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
-        *reinterpret_cast<uint2*>(out + o) =
+        *reinterpret_cast<uint2*>(P.out + o) =
             make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
-        *reinterpret_cast<uint2*>(out + o + rt * GT_TK) =
+        *reinterpret_cast<uint2*>(P.out + o + rt * GT_TK) =
             make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
     }
 }
@@ -407,20 +430,23 @@ size_t pieces_bytes(int64_t rows, int64_t K, int32_t rt, int32_t G)
            scratch_round(sizeof(float) * (size_t)G);
 }
 
-// Split op(S) into scaled pieces for a GEMM operand with row tiles of rt; smax
-// (G, float bits) holds each S_g's largest magnitude.
-void make_pieces(Pieces& P, InvScratch& W, const float* src, int64_t ld, int64_t gs, int32_t rows, int32_t K,
-                 bool trans, int32_t rt, int32_t G, const uint32_t* smax, cudaStream_t s)
+// Plan the split of op(S) into scaled pieces for a GEMM operand with row tiles of
+// rt: scratch for the pieces and scales, the launch job (smax: G, float bits, each
+// S_g's largest magnitude) and the tensor map.  split_pieces launches the jobs.
+void plan_pieces(Pieces& P, SplitJob& J, InvScratch& W, const float* src, int64_t ld, int64_t gs, int32_t rows,
+                 int32_t K, bool trans, int32_t rt, int32_t G, const uint32_t* smax)
 {
     const int64_t rpad = ceil_div(rows, rt) * rt, kpad = ceil_div(K, GT_TK) * GT_TK;
     P.tiles = (int32_t)(rpad / rt);
     P.kst = (int32_t)(kpad / GT_TK);
     P.buf = W.take<__half>(GT_PIECES * (int64_t)G * rpad * kpad);
     P.sinv = W.take<float>(G);
-    k_split_blocks<<<dim3((unsigned)(rpad / 32), (unsigned)ceil_div(kpad / 32, 4), (unsigned)G), dim3(32, 8), 0, s>>>(
-        src, ld, gs, rows, K, trans ? 1 : 0, rt, rpad, kpad, smax, P.sinv, P.buf);
-    UOI_CHECK_LAUNCH();
-    count_launch();
+    J.src = src; J.ld = ld; J.gs = gs;
+    J.rows = rows; J.K = K; J.trans = trans ? 1 : 0; J.rt = rt;
+    J.rpad = rpad; J.kpad = kpad;
+    J.smax = smax; J.sinv = P.sinv; J.out = P.buf;
+    J.nbx = (int32_t)(rpad / 32);
+    J.nby = (int32_t)ceil_div(kpad / 32, SPLIT_KC);
     // blocks of rt x 32 fp16 (64-byte rows); two consecutive blocks per stage
     CUtensorMap m;
     cuuint64_t dims[3] = { 32u, (cuuint64_t)rt, (cuuint64_t)((int64_t)G * P.tiles * P.kst * GT_PIECES) };
@@ -432,6 +458,19 @@ void make_pieces(Pieces& P, InvScratch& W, const float* src, int64_t ld, int64_t
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (res != CUDA_SUCCESS) throw Error(UOI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     P.map = m;
+}
+
+// One launch for one or two planned splits (independent of each other).
+void split_pieces(const SplitJob& a, const SplitJob* b, int32_t G, cudaStream_t s)
+{
+    SplitJobs J;
+    J.j[0] = a;
+    J.j[1] = b ? *b : a;
+    J.first1 = (int64_t)G * a.nbx * a.nby;
+    const int64_t total = J.first1 + (b ? (int64_t)G * b->nbx * b->nby : 0);
+    k_split_blocks<<<(unsigned)total, dim3(32, 8), 0, s>>>(J, G);
+    UOI_CHECK_LAUNCH();
+    count_launch();
 }
 
 // D = alpha A B^T + beta C with A (m x k) and B (n x k) in pieces; dmax (G,
@@ -684,12 +723,16 @@ void inv_rec(const float* A, int64_t ldA, int64_t gsA, float* M, int64_t ldM, in
     const size_t top_s = W.top;
     {
         Pieces pa, pb;
-        make_pieces(pa, W, A21, ldA, gsA, (int32_t)p2, (int32_t)p1, false, GT_TM, G, mA, s);
-        make_pieces(pb, W, X, ldM, gsM, (int32_t)p1, (int32_t)p1, false, GT_TN, G, mX, s);
+        SplitJob ja, jb;
+        plan_pieces(pa, ja, W, A21, ldA, gsA, (int32_t)p2, (int32_t)p1, false, GT_TM, G, mA);
+        plan_pieces(pb, jb, W, X, ldM, gsM, (int32_t)p1, (int32_t)p1, false, GT_TN, G, mX);
+        split_pieces(ja, &jb, G, s);
         gemm3(pa, pb, (int32_t)p2, (int32_t)p1, G, 1.f, 0.f, nullptr, 0, 0, U, p1, p2 * p1, err, s, mU);
         // S = A22 - A21 U^T   (p2 x p2)
         Pieces pu;
-        make_pieces(pu, W, U, p1, p2 * p1, (int32_t)p2, (int32_t)p1, false, GT_TN, G, mU, s);
+        SplitJob ju;
+        plan_pieces(pu, ju, W, U, p1, p2 * p1, (int32_t)p2, (int32_t)p1, false, GT_TN, G, mU);
+        split_pieces(ju, nullptr, G, s);
         gemm3(pa, pu, (int32_t)p2, (int32_t)p2, G, -1.f, 1.f, A22, ldA, gsA, S, p2, p2 * p2, err, s);
     }
     W.top = top_s;
@@ -700,16 +743,20 @@ void inv_rec(const float* A, int64_t ldA, int64_t gsA, float* M, int64_t ldM, in
     {
         // M21 = -Y U   (p2 x p1): A = Y (p2 x p2), B rows = columns of U
         Pieces py, put;
-        make_pieces(py, W, Y, ldM, gsM, (int32_t)p2, (int32_t)p2, false, GT_TM, G, mY, s);
-        make_pieces(put, W, U, p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mU, s);
+        SplitJob jy, jut;
+        plan_pieces(py, jy, W, Y, ldM, gsM, (int32_t)p2, (int32_t)p2, false, GT_TM, G, mY);
+        plan_pieces(put, jut, W, U, p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mU);
+        split_pieces(jy, &jut, G, s);
         gemm3(py, put, (int32_t)p2, (int32_t)p1, G, -1.f, 0.f, nullptr, 0, 0, M21, ldM, gsM, err, s, mM21);
     }
     W.top = top_u;
     {
         // M11 = X - U^T M21   (p1 x p1): A rows = columns of U, B rows = columns of M21
         Pieces pua, pmt;
-        make_pieces(pua, W, U, p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TM, G, mU, s);
-        make_pieces(pmt, W, M21, ldM, gsM, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mM21, s);
+        SplitJob jua, jmt;
+        plan_pieces(pua, jua, W, U, p1, p2 * p1, (int32_t)p1, (int32_t)p2, true, GT_TM, G, mU);
+        plan_pieces(pmt, jmt, W, M21, ldM, gsM, (int32_t)p1, (int32_t)p2, true, GT_TN, G, mM21);
+        split_pieces(jua, &jmt, G, s);
         gemm3(pua, pmt, (int32_t)p1, (int32_t)p1, G, -1.f, 1.f, X, ldM, gsM, X, ldM, gsM, err, s);
     }
     W.top = top0;

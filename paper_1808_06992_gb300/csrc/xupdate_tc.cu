@@ -425,13 +425,35 @@ k_xupdate_tc(const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CU
     xupdate_tile<XT_STAGES>(&tmM, &tmV, a, (int)blockIdx.x, ct, g);
 }
 
+// Two fp16 pieces of 8 consecutive scaled values of row i of M_g, stored as 16 bytes
+// per piece at column k8 of the [g][row tile][k block][piece][128][32] block order.
+__device__ __forceinline__ void store_m_pieces8(const float (&x)[8], int64_t g, int64_t i, int64_t k8,
+                                                int64_t RT, int64_t kst, __half* out)
+{
+    uint32_t ph[4], pl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        __half h[2], l[2];
+        split2(x[2 * q], h[0], l[0]);
+        split2(x[2 * q + 1], h[1], l[1]);
+        ph[q] = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+        pl[q] = (uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16);
+    }
+    const int64_t blk = ((g * RT + i / XT_TM) * kst + k8 / XT_TK) * XT_PIECES;
+    const int64_t o = (blk * XT_TM + i % XT_TM) * XT_TK + k8 % XT_TK;    // multiple of 8: 16 B aligned
+    *reinterpret_cast<uint4*>(out + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(out + o + XT_TM * XT_TK) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+}
+
 // M_g (FP32, p x p) -> per-row scales and the two fp16 pieces of each row times its
 // scale, one warp per row.  row_scale = 2^(10 - e) for the row's largest |M_ik| =
 // f 2^e (1 for an all-zero or padding row), row_inv = 1 / row_scale.  The pieces go
 // to 128 x 32 blocks ordered [g][row tile][k block][piece][128][32] (zero padded), so
 // that the x-update streams each row tile as one contiguous run of 16 KB stages.
-// The row is read from DRAM once for its largest magnitude and again, from L2, for
-// the split: each lane takes 8 consecutive k at a time and writes 16 bytes per piece.
+// Each lane takes 8 consecutive k at a time and writes 16 bytes per piece.  Rows of
+// up to 256 x SSM_REG_GROUPS columns stay in registers between the maximum and the
+// split; longer rows are read twice (the second time from L2).
+constexpr int SSM_REG_GROUPS = 8;
 __global__ void k_scale_split_m(const float* M, int32_t G, int64_t p, int64_t ppad, int64_t kpad,
                                 float* row_scale, float* row_inv, __half* out)
 {
@@ -439,9 +461,40 @@ __global__ void k_scale_split_m(const float* M, int32_t G, int64_t p, int64_t pp
     const int lane = threadIdx.x & 31;
     if (row >= (int64_t)G * ppad) return;
     const int64_t g = row / ppad, i = row % ppad;
-    const float* mr = M + ((size_t)g * p + (i < p ? i : 0)) * p;
+    const bool real = i < p;
+    const float* mr = M + ((size_t)g * p + (real ? i : 0)) * p;
+    const int64_t RT = ppad / XT_TM, kst = kpad / XT_TK;
     float mx = 0.f;
-    if (i < p)
+    if (kpad <= 256 * SSM_REG_GROUPS) {
+        float v[SSM_REG_GROUPS][8];
+#pragma unroll
+        for (int q = 0; q < SSM_REG_GROUPS; ++q) {
+            const int64_t k8 = (int64_t)lane * 8 + 256 * q;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                v[q][u] = (real && k8 + u < p) ? mr[k8 + u] : 0.f;
+                mx = fmaxf(mx, fabsf(v[q][u]));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = pow2_scale(mx);
+        if (lane == 0) {
+            row_scale[row] = sc;
+            row_inv[row] = 1.f / sc;
+        }
+#pragma unroll
+        for (int q = 0; q < SSM_REG_GROUPS; ++q) {
+            const int64_t k8 = (int64_t)lane * 8 + 256 * q;
+            if (k8 >= kpad) break;
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = (real && k8 + u < p) ? v[q][u] * sc : 0.f;
+            store_m_pieces8(x, g, i, k8, RT, kst, out);
+        }
+        return;
+    }
+    if (real)
         for (int64_t k = lane; k < p; k += 32) mx = fmaxf(mx, fabsf(mr[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -450,25 +503,11 @@ __global__ void k_scale_split_m(const float* M, int32_t G, int64_t p, int64_t pp
         row_scale[row] = sc;
         row_inv[row] = 1.f / sc;
     }
-    const int64_t RT = ppad / XT_TM, kst = kpad / XT_TK;
     for (int64_t k8 = (int64_t)lane * 8; k8 < kpad; k8 += 256) {
-        uint32_t ph[4], pl[4];
+        float x[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            __half h[2], l[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int64_t k = k8 + 2 * q + u;
-                const float x = (i < p && k < p) ? mr[k] * sc : 0.f;
-                split2(x, h[u], l[u]);
-            }
-            ph[q] = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
-            pl[q] = (uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16);
-        }
-        const int64_t blk = ((g * RT + i / XT_TM) * kst + k8 / XT_TK) * XT_PIECES;
-        const int64_t o = (blk * XT_TM + i % XT_TM) * XT_TK + k8 % XT_TK;    // multiple of 8: 16 B aligned
-        *reinterpret_cast<uint4*>(out + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-        *reinterpret_cast<uint4*>(out + o + XT_TM * XT_TK) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        for (int u = 0; u < 8; ++u) x[u] = (real && k8 + u < p) ? mr[k8 + u] * sc : 0.f;
+        store_m_pieces8(x, g, i, k8, RT, kst, out);
     }
 }
 
