@@ -87,3 +87,38 @@ def test_reference_arm_rank0_prints_one_line(monkeypatch):
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "fits/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def _fake_tree(tmp_path, source_text, recorded_sha):
+    csrc = tmp_path / "paper_1808_06992_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "gram_tc.cu").write_bytes(source_text)
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.txt").write_text(
+        "# comment line\n"
+        f"kernel=k_gram_tc source_sha={recorded_sha} dram_bytes_per_launch=1234000 capture=x.md\n")
+
+
+def test_traffic_figure_used_only_while_the_source_hash_matches(tmp_path, monkeypatch):
+    import hashlib
+    src = b"__global__ void k_gram_tc() {}\n"
+    _fake_tree(tmp_path, src, hashlib.sha256(src).hexdigest()[:16])
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_per_launch("k_gram_tc") == 1234000.0
+    # another workload than the one the figure was scaled to: no figure
+    assert bench.traffic_per_launch("k_gram_tc", applies=False) is None
+    # the source changed since the capture: no figure
+    (tmp_path / "paper_1808_06992_gb300" / "csrc" / "gram_tc.cu").write_bytes(src + b"// edit\n")
+    assert bench.traffic_per_launch("k_gram_tc") is None
+
+
+def test_committed_traffic_record_has_no_stale_line():
+    # a line whose kernel source changed since its capture would be silently
+    # ignored by the bench: re-capture it (or drop the line) when the kernel changes
+    with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+        kernels = [dict(kv.split("=", 1) for kv in ln.split() if "=" in kv).get("kernel")
+                   for ln in f if ln.startswith("kernel=")]
+    assert kernels
+    for k in kernels:
+        assert bench.traffic_per_launch(k) is not None, k
