@@ -10,10 +10,12 @@ Parity status: every stage function is pinned by ``tests/test_oracle_pins.py``
 (``kkt_polish``, ``kkt_residual`` and the bounds by ``tests/test_oracle_kkt.py``)
 (numpy Philox, closed forms, KKT, lambda_max, brute force over supports,
 sklearn, lstsq, brute-force set logic).  ``uoi_fit`` as a whole is pinned
-through those parts, the noiseless recovery special case and the cases whose
-selection is decided in advance (``tests/test_oracle_whole_fit.py``: least
-squares on the training draws, held-out losses, argmin and bagging by an
-independent numpy route); beyond those it is "parity unpinned".
+through those parts, the noiseless recovery special case, the cases whose
+selection is decided in advance, and the general case on LASSO and VAR(1)
+fixtures with varying supports (``tests/test_oracle_whole_fit.py``: selection by
+scikit-learn's LASSO on the bootstrap rows repeated by multiplicity, then
+intersection, least squares on the training draws, held-out losses, argmin and
+median by numpy, with the fixtures' KKT margins asserted).
 """
 from __future__ import annotations
 

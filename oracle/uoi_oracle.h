@@ -23,12 +23,14 @@
  * (non-converged ADMM column or min-norm OLS fallback), <0 error.
  *
  * Parity status per function: every function is pinned by a test in
- * tests/test_oracle_pins.py (ref_kkt_polish in tests/test_oracle_kkt.py)
- * except ref_uoi_fit as a whole, which is pinned
- * through its parts, the noiseless-recovery special case and the cases whose
- * selection is decided in advance (tests/test_oracle_whole_fit.py: least
- * squares on the training draws, held-out losses, argmin and bagging by an
- * independent numpy route); beyond those it is "parity unpinned".
+ * tests/test_oracle_pins.py (ref_kkt_polish in tests/test_oracle_kkt.py).
+ * ref_uoi_fit as a whole is pinned through its parts, the noiseless-recovery
+ * special case, the cases whose selection is decided in advance, and the
+ * general case on LASSO and VAR(1) fixtures with varying supports
+ * (tests/test_oracle_whole_fit.py): an independent route of scikit-learn's
+ * LASSO on the bootstrap rows repeated by multiplicity, then intersection,
+ * least squares on the training draws, held-out losses, argmin and median in
+ * numpy, with the fixtures' KKT margins asserted so the comparison is decided.
  */
 #ifndef UOI_ORACLE_H
 #define UOI_ORACLE_H

@@ -1,4 +1,5 @@
-"""Pins of the oracle's whole UoI_LASSO fit (Alg. 1) in cases where the selection
+"""Pins of the oracle's whole UoI fit (Alg. 1, Alg. 2).  The general case, with
+real selection, is at the end of this file.  First the cases where the selection
 step is decided in advance, so that the estimation step has an independent
 route: at an explicit lambda far below every |Xᵀy|/n the LASSO keeps every
 feature in every bootstrap (the intersection, Eq. 3, is the full set); at a
@@ -121,3 +122,107 @@ def test_var_dense_support_reduces_to_per_equation_least_squares(order, intercep
     np.testing.assert_allclose(fit["A"], A_want, rtol=1e-8, atol=1e-10)
     if intercept:
         np.testing.assert_allclose(fit["mu"], want[:, order * p], rtol=1e-8, atol=1e-10)
+
+
+# ---- the general case: selection by an independent LASSO solver --------------------
+# With real selection (supports that vary with lambda and bootstrap) the whole fit has
+# an independent route too: each selection bootstrap's LASSO (Eq. 1, the weighted
+# least squares over n_k = sum(w) draws plus lambda ||beta||_1) solved by
+# scikit-learn's coordinate descent on the bootstrap's rows repeated by multiplicity;
+# supports, their intersection (Eq. 3), least squares on each estimation bootstrap's
+# training draws, held-out losses, argmin and the median by numpy.  The fixtures are
+# chosen so that the comparison is decided: every active coefficient is far from
+# zero and every inactive feature's correlation far from lambda, relative to the
+# solvers' errors, and the two smallest distinct losses of each estimation bootstrap
+# are apart.  Both margins are asserted.
+
+
+def _sk_lasso(Xk, yk, lam):
+    lm = pytest.importorskip("sklearn.linear_model")
+    b = lm.Lasso(alpha=lam, fit_intercept=False, tol=1e-14, max_iter=10**6).fit(Xk, yk).coef_
+    grad = Xk.T @ (yk - Xk @ b) / Xk.shape[0]
+    act = b != 0
+    assert np.all(np.abs(b[act]) > 1e-5)                       # active: clear of zero
+    assert np.all(np.abs(grad[~act]) < lam * (1 - 1e-4))       # inactive: clear of lambda
+    return b
+
+
+def _independent_uoi(X, Y, lambdas, B1, B2, block_len):
+    """Alg. 1 per response column of Y, every step outside the oracle."""
+    m, p = X.shape
+    q, r = len(lambdas), Y.shape[1]
+    fam = np.ones((q, r, p), dtype=bool)
+    for k in range(B1):
+        rows = np.repeat(np.arange(m), oracle.selection_weights(m, block_len, SEED, 0, k).astype(np.int64))
+        for e in range(r):
+            for j, lam in enumerate(lambdas):
+                fam[j, e] &= _sk_lasso(X[rows], Y[rows, e], lam) != 0
+    chosen = np.zeros((B2, r, p))
+    jstar = np.zeros(B2, dtype=int)
+    for k in range(B2):
+        w, ev, _ = oracle.estimation_weights(m, block_len, 0.8, 0, SEED, 0, k)
+        sw, ev = np.sqrt(w.astype(np.float64)), ev.astype(bool)
+        losses = np.zeros(q)
+        ests = np.zeros((q, r, p))
+        for j in range(q):
+            for e in range(r):
+                S = np.flatnonzero(fam[j, e])
+                if S.size:
+                    ests[j, e, S] = np.linalg.lstsq(X[:, S] * sw[:, None], Y[:, e] * sw, rcond=None)[0]
+                losses[j] += np.sum((Y[ev, e] - X[ev] @ ests[j, e]) ** 2)
+        jstar[k] = int(np.argmin(losses))                      # first of equal losses
+        distinct = np.unique(losses)
+        if distinct.size > 1:
+            assert distinct[1] - distinct[0] > 1e-9 * distinct[0]
+        chosen[k] = ests[jstar[k]]
+    return fam, jstar, np.median(chosen, axis=0)
+
+
+def _family_bits(fam):
+    q, r, p = fam.shape
+    return np.array([[sum(1 << i for i in range(p) if fam[j, e, i]) for e in range(r)] for j in range(q)])
+
+
+def test_general_lasso_fit_matches_an_independent_route():
+    g = np.random.Generator(np.random.PCG64(21))
+    n, p = 400, 10
+    X = g.standard_normal((n, p))
+    truth = np.zeros(p)
+    truth[[0, 3, 7]] = [1.5, -1.0, 0.6]
+    y = X @ truth + 0.5 * g.standard_normal(n)
+    lmax = np.max(np.abs(X.T @ y)) / n
+    lambdas = lmax * np.array([0.6, 0.3, 0.1, 0.03, 0.01])
+    B1, B2 = 5, 4
+    fit = oracle.uoi_lasso_fit(X, y, B1, B2, len(lambdas), lambdas=lambdas, seed=SEED, max_iter=100000,
+                               abs_tol=1e-11, rel_tol=1e-11)
+    assert fit["status"] == 0 and np.all(fit["sel_conv"] == 1)
+    fam, jstar, beta = _independent_uoi(X, y[:, None], lambdas, B1, B2, 0)
+    assert len({tuple(f) for f in fam[:, 0]}) >= 3              # the family really varies with lambda
+    assert np.array_equal(fit["family"][:, :, 0].astype(np.int64), _family_bits(fam))
+    assert np.array_equal(fit["est_jstar"], jstar)
+    np.testing.assert_allclose(fit["beta"][0], beta[0], rtol=1e-9, atol=1e-12)
+
+
+def test_general_var_fit_matches_an_independent_route():
+    # Alg. 2: p equations sharing the lagged design (Eq. 7-9), block bootstrap draws,
+    # one lambda grid; j* is chosen once per estimation bootstrap over the summed
+    # losses of all equations
+    g = np.random.Generator(np.random.PCG64(33))
+    p, N, L = 4, 500, 25
+    A1 = np.diag([0.6, -0.5, 0.4, 0.3])
+    A1[0, 2], A1[3, 1] = 0.35, -0.3
+    S = np.zeros((N, p))
+    for t in range(1, N):
+        S[t] = A1 @ S[t - 1] + 0.5 * g.standard_normal(p)
+    X, Y = _lagged(S, 1)
+    lmax = np.max(np.abs(X.T @ Y)) / X.shape[0]
+    lambdas = lmax * np.array([0.5, 0.2, 0.08, 0.03])
+    B1, B2 = 4, 3
+    fit = oracle.uoi_var_fit(S, B1, B2, len(lambdas), order=1, lambdas=lambdas, block_len=L, seed=SEED,
+                             max_iter=100000, abs_tol=1e-11, rel_tol=1e-11)
+    assert fit["status"] == 0
+    fam, jstar, beta = _independent_uoi(X, Y, lambdas, B1, B2, L)
+    assert len({fam[j].tobytes() for j in range(len(lambdas))}) >= 3
+    assert np.array_equal(fit["family"][:, :, 0].astype(np.int64), _family_bits(fam))
+    assert np.array_equal(fit["est_jstar"], jstar)
+    np.testing.assert_allclose(fit["A"][0], beta, rtol=1e-9, atol=1e-12)
