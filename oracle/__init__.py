@@ -11,8 +11,8 @@ Parity status: every stage function is pinned by ``tests/test_oracle_pins.py``
 (numpy Philox, closed forms, KKT, lambda_max, brute force over supports,
 sklearn, lstsq, brute-force set logic).  ``uoi_fit`` as a whole is pinned
 through those parts, the noiseless recovery special case, the cases whose
-selection is decided in advance, and the general case on LASSO and VAR(1)
-fixtures with varying supports (``tests/test_oracle_whole_fit.py``: selection by
+selection is decided in advance, and the general case on LASSO (with and
+without an intercept) and VAR(1) fixtures with varying supports (``tests/test_oracle_whole_fit.py``: selection by
 scikit-learn's LASSO on the bootstrap rows repeated by multiplicity, then
 intersection, least squares on the training draws, held-out losses, argmin and
 median by numpy, with the fixtures' KKT margins asserted).

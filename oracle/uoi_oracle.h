@@ -26,11 +26,12 @@
  * tests/test_oracle_pins.py (ref_kkt_polish in tests/test_oracle_kkt.py).
  * ref_uoi_fit as a whole is pinned through its parts, the noiseless-recovery
  * special case, the cases whose selection is decided in advance, and the
- * general case on LASSO and VAR(1) fixtures with varying supports
- * (tests/test_oracle_whole_fit.py): an independent route of scikit-learn's
- * LASSO on the bootstrap rows repeated by multiplicity, then intersection,
- * least squares on the training draws, held-out losses, argmin and median in
- * numpy, with the fixtures' KKT margins asserted so the comparison is decided.
+ * general case on LASSO (with and without an intercept) and VAR(1) fixtures
+ * with varying supports (tests/test_oracle_whole_fit.py): an independent route
+ * of scikit-learn's LASSO on the bootstrap rows repeated by multiplicity, then
+ * intersection, least squares on the training draws, held-out losses, argmin
+ * and median in numpy, with the fixtures' KKT margins asserted so that the
+ * comparison is decided.
  */
 #ifndef UOI_ORACLE_H
 #define UOI_ORACLE_H

@@ -137,9 +137,11 @@ def test_var_dense_support_reduces_to_per_equation_least_squares(order, intercep
 # are apart.  Both margins are asserted.
 
 
-def _sk_lasso(Xk, yk, lam):
+def _sk_lasso(Xk, yk, lam, intercept=False):
     lm = pytest.importorskip("sklearn.linear_model")
-    b = lm.Lasso(alpha=lam, fit_intercept=False, tol=1e-14, max_iter=10**6).fit(Xk, yk).coef_
+    b = lm.Lasso(alpha=lam, fit_intercept=intercept, tol=1e-14, max_iter=10**6).fit(Xk, yk).coef_
+    if intercept:                                              # the unpenalised mean, eliminated
+        Xk, yk = Xk - Xk.mean(axis=0), yk - yk.mean()
     grad = Xk.T @ (yk - Xk @ b) / Xk.shape[0]
     act = b != 0
     assert np.all(np.abs(b[act]) > 1e-5)                       # active: clear of zero
@@ -147,29 +149,32 @@ def _sk_lasso(Xk, yk, lam):
     return b
 
 
-def _independent_uoi(X, Y, lambdas, B1, B2, block_len):
-    """Alg. 1 per response column of Y, every step outside the oracle."""
+def _independent_uoi(X, Y, lambdas, B1, B2, block_len, intercept=False):
+    """Alg. 1 per response column of Y, every step outside the oracle; with an
+    intercept, estimates carry the unpenalised mean as their last entry."""
     m, p = X.shape
     q, r = len(lambdas), Y.shape[1]
+    pa = p + (1 if intercept else 0)
     fam = np.ones((q, r, p), dtype=bool)
     for k in range(B1):
         rows = np.repeat(np.arange(m), oracle.selection_weights(m, block_len, SEED, 0, k).astype(np.int64))
         for e in range(r):
             for j, lam in enumerate(lambdas):
-                fam[j, e] &= _sk_lasso(X[rows], Y[rows, e], lam) != 0
-    chosen = np.zeros((B2, r, p))
+                fam[j, e] &= _sk_lasso(X[rows], Y[rows, e], lam, intercept) != 0
+    chosen = np.zeros((B2, r, pa))
     jstar = np.zeros(B2, dtype=int)
     for k in range(B2):
         w, ev, _ = oracle.estimation_weights(m, block_len, 0.8, 0, SEED, 0, k)
         sw, ev = np.sqrt(w.astype(np.float64)), ev.astype(bool)
         losses = np.zeros(q)
-        ests = np.zeros((q, r, p))
+        ests = np.zeros((q, r, pa))
         for j in range(q):
             for e in range(r):
-                S = np.flatnonzero(fam[j, e])
-                if S.size:
-                    ests[j, e, S] = np.linalg.lstsq(X[:, S] * sw[:, None], Y[:, e] * sw, rcond=None)[0]
-                losses[j] += np.sum((Y[ev, e] - X[ev] @ ests[j, e]) ** 2)
+                cols = list(np.flatnonzero(fam[j, e])) + ([p] if intercept else [])
+                Z = np.hstack([X, np.ones((m, 1))]) if intercept else X
+                if cols:
+                    ests[j, e, cols] = np.linalg.lstsq(Z[:, cols] * sw[:, None], Y[:, e] * sw, rcond=None)[0]
+                losses[j] += np.sum((Y[ev, e] - Z[ev] @ ests[j, e]) ** 2)
         jstar[k] = int(np.argmin(losses))                      # first of equal losses
         distinct = np.unique(losses)
         if distinct.size > 1:
@@ -198,6 +203,28 @@ def test_general_lasso_fit_matches_an_independent_route():
     assert fit["status"] == 0 and np.all(fit["sel_conv"] == 1)
     fam, jstar, beta = _independent_uoi(X, y[:, None], lambdas, B1, B2, 0)
     assert len({tuple(f) for f in fam[:, 0]}) >= 3              # the family really varies with lambda
+    assert np.array_equal(fit["family"][:, :, 0].astype(np.int64), _family_bits(fam))
+    assert np.array_equal(fit["est_jstar"], jstar)
+    np.testing.assert_allclose(fit["beta"][0], beta[0], rtol=1e-9, atol=1e-12)
+
+
+def test_general_lasso_fit_with_intercept_matches_an_independent_route():
+    # the unpenalised intercept: selection with the means eliminated, estimation by
+    # least squares on [X_S 1], mu the last entry of beta*
+    g = np.random.Generator(np.random.PCG64(41))
+    n, p = 400, 8
+    X = g.standard_normal((n, p)) + 0.7
+    truth = np.zeros(p)
+    truth[[1, 4, 6]] = [1.2, -0.8, 0.5]
+    y = 2.0 + X @ truth + 0.5 * g.standard_normal(n)
+    Xc, yc = X - X.mean(axis=0), y - y.mean()
+    lambdas = np.max(np.abs(Xc.T @ yc)) / n * np.array([0.6, 0.3, 0.1, 0.03])
+    B1, B2 = 4, 3
+    fit = oracle.uoi_lasso_fit(X, y, B1, B2, len(lambdas), lambdas=lambdas, seed=SEED, max_iter=100000,
+                               abs_tol=1e-11, rel_tol=1e-11, intercept=1)
+    assert fit["status"] == 0
+    fam, jstar, beta = _independent_uoi(X, y[:, None], lambdas, B1, B2, 0, intercept=True)
+    assert len({tuple(f) for f in fam[:, 0]}) >= 3
     assert np.array_equal(fit["family"][:, :, 0].astype(np.int64), _family_bits(fam))
     assert np.array_equal(fit["est_jstar"], jstar)
     np.testing.assert_allclose(fit["beta"][0], beta[0], rtol=1e-9, atol=1e-12)
