@@ -71,29 +71,45 @@ def parse():
 # clocks sampled during the timed region
 # ----------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi polled every 50 ms in a child process; each line is stamped with
+    the host's monotonic clock when it arrives, so that the summary keeps only the
+    samples taken inside the timed region (mark_start / mark_stop).  start() waits
+    for the first sample, so that sampling is running before the region opens."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, cmd=None):
         self.gpu = gpu_index
+        self.cmd = cmd or ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                           "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)]
         self.proc = None
-        self.lines = []
+        self.lines = []                                  # (host time, line)
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, ready_timeout=5.0):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
+            return
+        end = time.monotonic() + ready_timeout
+        while not self.lines and time.monotonic() < end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+            self.lines.append((time.monotonic(), ln.strip()))
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_stop(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if not self.proc:
@@ -103,9 +119,18 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.t.join(timeout=5)
+        return self.summary()
+
+    def summary(self):
+        lines = list(self.lines)
+        if self.t0 is not None and self.t1 is not None:
+            # a line arrives up to one period after the sample it reports
+            inside = [(t, ln) for t, ln in lines if self.t0 <= t <= self.t1 + self.PERIOD_MS / 1e3]
+            lines = inside or lines
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -389,6 +414,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark_start()
     ev0.record()
     diags = []
     for _ in range(args.steps):
@@ -396,6 +422,7 @@ def main():
         diags.append(out["diag"])
     ev1.record()
     torch.cuda.synchronize()
+    sampler.mark_stop()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
@@ -582,12 +609,14 @@ def bench_batch(args, torch, rank, world, local, dist):
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark_start()
     ev0.record()
     outs = []
     for _ in range(args.steps):
         outs.append(step())          # returns once every worker stream has finished
     ev1.record()
     torch.cuda.synchronize()
+    sampler.mark_stop()
     if dist:
         dist.barrier()
     clocks = sampler.stop()

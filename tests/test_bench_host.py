@@ -122,3 +122,48 @@ def test_committed_traffic_record_has_no_stale_line():
     assert kernels
     for k in kernels:
         assert bench.traffic_per_launch(k) is not None, k
+
+
+_FAKE_SMI = r"""
+import sys, time
+flag = sys.argv[1]
+while True:
+    phase = open(flag).read().strip()
+    if phase == "before":
+        print("0, 1000, 2070, 300.0, 0x8, Active, Not Active, Not Active, Not Active", flush=True)
+    elif phase == "during":
+        print("0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active", flush=True)
+    else:
+        print("0, 1500, 2070, 200.0, 0x0, Not Active, Not Active, Not Active, Not Active", flush=True)
+    time.sleep(0.02)
+"""
+
+
+def test_clock_sampler_summarises_only_the_timed_region(tmp_path):
+    import time
+    fake = tmp_path / "fake_smi.py"
+    fake.write_text(_FAKE_SMI)
+    flag = tmp_path / "phase"
+    flag.write_text("before")
+    smp = bench.ClockSampler(0, cmd=[sys.executable, str(fake), str(flag)])
+    smp.start()
+    assert smp.lines                                  # sampling runs before the region opens
+    time.sleep(0.2)
+    flag.write_text("during")
+    time.sleep(0.1)
+    smp.mark_start()
+    time.sleep(0.5)
+    smp.mark_stop()
+    flag.write_text("after")
+    time.sleep(0.2)
+    c = smp.stop()
+    assert c["samples"] >= 10
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]           # the hw_slowdown before the region is not counted
+
+
+def test_clock_sampler_without_nvidia_smi_says_so():
+    smp = bench.ClockSampler(0, cmd=["/nonexistent/nvidia-smi"])
+    smp.start()
+    c = smp.stop()
+    assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
