@@ -33,7 +33,9 @@ DTYPE_MIXED = ("mixed: Gram bf16 2-piece/3 products, inverse + x-update fp16 2-p
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 20 on the workloads whose fit takes well under a "
+                         "second, 5 on the VAR p = 1000 workload and in the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=2)
@@ -366,6 +368,8 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = 5 if (args.impl == "reference" or args.workload == 5) else 20
     if args.fp64_steps is None:
         args.fp64_steps = 2 if args.workload == 2 else 0
     if args.impl == "reference":
