@@ -17,7 +17,10 @@
 // drains every 128 k into compensated FP32 pairs (the tensor core's FP32
 // accumulation truncates about a third of an ulp per K=16 step); the two small
 // products, 2^-11 smaller, share one accumulator read once at the end.  The
-// x-update is then accurate to a few 1e-7 relative.
+// x-update is then accurate to a few 1e-7 relative.  Once the products are done
+// the folded sums go back to TMEM beside them, so that the update runs as a
+// rolled loop over groups of 8 chains (one copy of its code in the instruction
+// cache) reading 8 columns of each per pass.
 //
 // Work per launch: every chain of every group (converged chains are skipped in
 // the epilogue and keep their state; tiles with no live chain exit at once).
