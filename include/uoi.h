@@ -22,7 +22,12 @@
  *    returns it.
  *  - Work is issued on prm->stream / the stream argument (NULL = the legacy
  *    default stream); every entry point returns after the results are in the
- *    output buffers (it synchronises that stream).
+ *    output buffers (it synchronises that stream).  Inside a mixed fit some
+ *    independent work also runs on a second stream the library keeps per
+ *    calling thread, ordered against the caller's stream by events (the small
+ *    supports of the estimation's loss pass; half of the selection's systems in
+ *    the tensor-core inverse, enqueued by a helper thread that ends before the
+ *    inverse returns).
  *  - Outputs are written only when the status is UOI_OK or
  *    UOI_OK_WITH_WARNINGS.  No C++ exception crosses the boundary.
  *  - Not thread-safe per device: calls on one device must not overlap.
